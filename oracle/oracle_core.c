@@ -1,0 +1,945 @@
+/* ORACLE (test infrastructure only; only tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load it). A plain sequential CPU restatement of one UGKWP-LTS steady-iteration step, checked against
+ * the paper's fixed points by the `-m "not gpu"` tests. It shares no code with the CUDA library.
+ *
+ * Paper sections cited: Sec. 2 (kinetic model, Eqs. 1-8), Sec. 3 (UGKWP, Eqs. 9-23), Sec. 3.3 (algorithm
+ * steps 1-4), Sec. 4 (LTS: Eqs. 24-25 time steps; Eq. 37 proportional scaling; Eqs. 40-46 LTS form).
+ *
+ * Readings of points the paper leaves open (each is a reading, not a statement of the paper):
+ *  - units rho_inf = T_inf = 1, R = 1/2; monatomic, three velocity components, D = 0;
+ *  - mu_inf from Kn by the VHS mean-free-path relation; mu = mu_inf T^omega; tau = mu / p (Sec. 2);
+ *  - tau_i from the total W^n_i at the start of the step;
+ *  - reconstruction is first order (piecewise constant): the initial distribution has no slope; the
+ *    equilibrium g_0 has normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on
+ *    u.n < 0, no tangential slope; A from the compatibility condition with both half slopes (Sec. 3.1);
+ *  - Prandtl fix applied to a through d(lambda)/Pr; wave fluxes use the Maxwellian g_0 (Sec. 3.1);
+ *  - wall faces: incoming half from the fluid cell (first order), outgoing half a wall Maxwellian at T_w
+ *    whose density zeroes the wave mass flux; far-field ghost = freestream on inflow, the cell state on
+ *    outflow, with the full free-transport coefficient on the ghost side (no particles are injected);
+ *  - the particle w-momentum (and in 1-D the v-momentum) is not part of W.
+ */
+#include "oracle_internal.h"
+#include <stdio.h>
+#include <string.h>
+
+static const double OR_PI = 3.14159265358979323846;
+
+void or_set_error(or_ctx* cx, int code, const char* msg)
+{
+    if (cx->err == OR_OK) {
+        cx->err = code;
+        snprintf(cx->msg, sizeof cx->msg, "%s", msg);
+    }
+}
+
+static void* zalloc(size_t n, size_t sz)
+{
+    void* p = calloc(n ? n : 1, sz);
+    return p;
+}
+
+/* ---------------------------------------------------------------- kinetic model helpers (Sec. 2) */
+
+/* conservative (rho, rho U, rho V, rho E) of a primitive state; E = |U|^2/2 + (3/2) R T */
+static void prim_to_cons(double rho, double U, double V, double T, double W[4])
+{
+    W[0] = rho;
+    W[1] = rho * U;
+    W[2] = rho * V;
+    W[3] = rho * (0.5 * (U * U + V * V) + 1.5 * OR_R * T);
+}
+
+double oracle_mu_inf(double Kn, double omega)
+{
+    /* VHS: lambda = 2 (5 - 2w)(7 - 2w) / 15 * mu / (rho sqrt(2 pi R T)), solved for mu at rho = T = 1 */
+    return (15.0 * sqrt(2.0 * OR_PI * OR_R) * Kn) / (2.0 * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega));
+}
+
+static double tau_of(const or_ctx* cx, const double W[4])
+{
+    const double rho = W[0], U = W[1] / rho, V = W[2] / rho;
+    const double RT = (W[3] / rho - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+    const double T = RT / OR_R;
+    const double mu = cx->mu_inf * or_powd(T, cx->omega);
+    return mu / (rho * RT);
+}
+
+/* ---------------------------------------------- time-integration coefficients (Eq. 14, Eqs. 40-41) */
+
+/* out = (dbar_a, dbar_b, dbar_c, dbar_d, dbar_e, dbar_d - e^{-x}, dbar_e + dt/2 e^{-x}),
+ * the coefficients of Eq. 14 evaluated with (dt, tau) and divided by dt (Eq. 41). With x = dt/tau and the
+ * entire functions phi1 = (1-e^-x)/x, psi2 = (e^-x - 1 + x)/x^2, psi3 = (x^2/2 - x + 1 - e^-x)/x^3,
+ * chi = (phi1 - e^-x)/x, beta = (1 + e^-x - 2 phi1)/x^2, kappa = (chi - e^-x/2)/x:
+ *   dbar_a = x psi2, dbar_b = -dt x beta, dbar_c = dt x psi3, dbar_d = phi1, dbar_e = -dt chi,
+ *   dbar_d - e^-x = x chi, dbar_e + dt e^-x / 2 = -dt x kappa.
+ * Each function is summed from its Taylor series for x < 1 (no cancellation) and from the closed form
+ * otherwise. */
+static void lts_coeffs(double dt, double tau, double e, double out[7])
+{
+    const double x = dt / tau;
+    double phi1, psi2, psi3, chi, beta, kappa;
+    if (x < 1.0) {
+        /* term k of each series carries (-x)^k / (k + j)! with a polynomial weight in k */
+        phi1 = psi2 = psi3 = chi = beta = kappa = 0.0;
+        double pw = 1.0;               /* (-x)^k */
+        double f1 = 1.0, f2 = 2.0, f3 = 6.0;   /* (k+1)!, (k+2)!, (k+3)! */
+        for (int k = 0; k <= 24; ++k) {
+            phi1 += pw / f1;
+            psi2 += pw / f2;
+            psi3 += pw / f3;
+            chi += pw * (double)(k + 1) / f2;
+            beta += pw * (double)(k + 1) / f3;
+            kappa += pw * (double)((k + 1) * (k + 2)) / (2.0 * f3);
+            pw *= -x;
+            f1 *= (double)(k + 2);
+            f2 *= (double)(k + 3);
+            f3 *= (double)(k + 4);
+        }
+    } else {
+        phi1 = (1.0 - e) / x;
+        psi2 = (e - 1.0 + x) / (x * x);
+        psi3 = (0.5 * x * x - x + 1.0 - e) / (x * x * x);
+        chi = (phi1 - e) / x;
+        beta = (1.0 + e - 2.0 * phi1) / (x * x);
+        kappa = (chi - 0.5 * e) / x;
+    }
+    out[0] = x * psi2;
+    out[1] = -dt * x * beta;
+    out[2] = dt * x * psi3;
+    out[3] = phi1;
+    out[4] = -dt * chi;
+    out[5] = x * chi;
+    out[6] = -dt * x * kappa;
+}
+
+void oracle_coeffs(double dt, double tau, double* out)
+{
+    lts_coeffs(dt, tau, or_expd(-dt / tau), out);
+}
+
+/* ------------------------------------------------------- Maxwellian moments (Sec. 3.1, Eqs. 26-31) */
+
+typedef struct { double rho, U, V, lam; } or_prim;          /* face frame: U normal, V tangential */
+typedef struct { double uf[9], up[9], um[9], v[7], xi2, xi4; } or_mom;
+
+/* W in the face frame -> primitive; lambda = 1 / (2 R T); returns 0 if not physical */
+static int frame_prim(const double W[4], or_prim* p)
+{
+    p->rho = W[0];
+    if (!(W[0] > 0.0)) return 0;
+    p->U = W[1] / W[0];
+    p->V = W[2] / W[0];
+    const double e = W[3] / W[0] - 0.5 * (p->U * p->U + p->V * p->V);   /* (3/2) R T */
+    if (!(e > 0.0)) return 0;
+    p->lam = 0.75 / e;
+    return 1;
+}
+
+/* <u^k> over all u, over u > 0 and over u < 0, per unit density; <v^k>; <w^2>, <w^4> (w: the
+ * out-of-plane component, which enters only through |u|^2 like one internal degree of freedom) */
+static void moments(const or_prim* p, or_mom* M)
+{
+    const double U = p->U, V = p->V, lam = p->lam, th = 0.5 / lam;
+    const double ex = exp(-lam * U * U) / (2.0 * sqrt(OR_PI * lam));
+    M->uf[0] = 1.0;
+    M->uf[1] = U;
+    M->up[0] = 0.5 * erfc(-sqrt(lam) * U);
+    M->up[1] = U * M->up[0] + ex;
+    M->um[0] = 0.5 * erfc(sqrt(lam) * U);
+    M->um[1] = U * M->um[0] - ex;
+    for (int k = 2; k < 9; ++k) {
+        M->uf[k] = U * M->uf[k - 1] + (double)(k - 1) * th * M->uf[k - 2];
+        M->up[k] = U * M->up[k - 1] + (double)(k - 1) * th * M->up[k - 2];
+        M->um[k] = U * M->um[k - 1] + (double)(k - 1) * th * M->um[k - 2];
+    }
+    M->v[0] = 1.0;
+    M->v[1] = V;
+    for (int k = 2; k < 7; ++k) M->v[k] = V * M->v[k - 1] + (double)(k - 1) * th * M->v[k - 2];
+    M->xi2 = th;
+    M->xi4 = 3.0 * th * th;
+}
+
+/* <psi u^a v^b w^(2c)> with psi = (1, u, v, (u^2 + v^2 + w^2)/2); Mu selects the u range */
+static void psi_mom(const double* Mu, const or_mom* M, int a, int b, int c, double out[4])
+{
+    const double w0 = c == 0 ? 1.0 : M->xi2, w2 = c == 0 ? M->xi2 : M->xi4;
+    out[0] = Mu[a] * M->v[b] * w0;
+    out[1] = Mu[a + 1] * M->v[b] * w0;
+    out[2] = Mu[a] * M->v[b + 1] * w0;
+    out[3] = 0.5 * (Mu[a + 2] * M->v[b] * w0 + Mu[a] * M->v[b + 2] * w0 + Mu[a] * M->v[b] * w2);
+}
+
+/* <psi u^a v^b (c0 + c1 u + c2 v + c3 (u^2+v^2+w^2)/2)> */
+static void psi_poly_mom(const double* Mu, const or_mom* M, int a, int b, const double cf[4], double out[4])
+{
+    double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
+    psi_mom(Mu, M, a, b, 0, t0);
+    psi_mom(Mu, M, a + 1, b, 0, t1);
+    psi_mom(Mu, M, a, b + 1, 0, t2);
+    psi_mom(Mu, M, a + 2, b, 0, t3);
+    psi_mom(Mu, M, a, b + 2, 0, t4);
+    psi_mom(Mu, M, a, b, 1, t5);
+    for (int k = 0; k < 4; ++k)
+        out[k] = cf[0] * t0[k] + cf[1] * t1[k] + cf[2] * t2[k] + cf[3] * 0.5 * (t3[k] + t4[k] + t5[k]);
+}
+
+/* Solve <psi (a0 + a1 u + a2 v + a3 (u^2+v^2+w^2)/2)> = dw for the Maxwellian p (Eq. 28 / Eq. 31),
+ * closed form of the 4 x 4 moment system (three velocity dimensions). */
+static void micro_slope(const or_prim* p, const double dw[4], double a[4])
+{
+    const double U = p->U, V = p->V, lam = p->lam;
+    const double R4 = 2.0 * dw[3] - 2.0 * U * dw[1] - 2.0 * V * dw[2] + (U * U + V * V) * dw[0]
+                      - (1.5 / lam) * dw[0];
+    a[3] = (4.0 * lam * lam / 3.0) * R4;
+    a[1] = 2.0 * lam * (dw[1] - U * dw[0]) - a[3] * U;
+    a[2] = 2.0 * lam * (dw[2] - V * dw[0]) - a[3] * V;
+    a[0] = dw[0] - a[3] * 0.75 / lam - a[1] * U - a[2] * V - a[3] * 0.5 * (U * U + V * V);
+}
+
+/* Prandtl correction (Sec. 3.1): d(lambda)/dx -> d(lambda)/dx / Pr inside a */
+static void pr_fix(const or_prim* p, double a[4], double Pr)
+{
+    if (Pr == 1.0) return;
+    const double U = p->U, V = p->V, lam = p->lam;
+    const double dlam = -0.5 * a[3];
+    const double dU = (a[1] + U * a[3]) / (2.0 * lam), dV = (a[2] + V * a[3]) / (2.0 * lam);
+    const double drho = a[0] - 1.5 * dlam / lam + dlam * (U * U + V * V) + 2.0 * lam * (U * dU + V * dV);
+    const double dl = dlam / Pr;
+    a[3] = -2.0 * dl;
+    a[1] = 2.0 * lam * dU + 2.0 * U * dl;
+    a[2] = 2.0 * lam * dV + 2.0 * V * dl;
+    a[0] = drho + 1.5 * dl / lam - dl * (U * U + V * V) - 2.0 * lam * (U * dU + V * dV);
+}
+
+/* Time-averaged wave flux through one face in the face frame (normal from L to R):
+ * equilibrium part (Eq. 42) from g_0 and its slopes, plus the analytic free-transport part of the
+ * hydrodynamic wave (Eq. 43, first order so only its dbar_d - e^{-x} term). cL/cR are the 7 normalised
+ * coefficients of each side; frL/frR the coefficient used for each side's g^h (x chi, or the full dbar_d
+ * on a ghost side or without particles). Returns W_0 and the slopes for the pins. */
+static void face_flux(const double WL[4], const double WR[4], const double WhL[4], const double WhR[4],
+                      int hL, int hR, const double cL[7], const double cR[7], double frL, double frR,
+                      double dL, double dR, double Pr, double F[4], double W0o[4], double aLo[4],
+                      double aRo[4], double Ao[4])
+{
+    or_prim pL, pR, p0, phL, phR;
+    or_mom mL, mR, m0, mhL, mhR;
+    frame_prim(WL, &pL);
+    frame_prim(WR, &pR);
+    moments(&pL, &mL);
+    moments(&pR, &mR);
+    double t1[4], t2[4], W0[4];
+    psi_mom(mL.up, &mL, 0, 0, 0, t1);
+    psi_mom(mR.um, &mR, 0, 0, 0, t2);
+    for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];      /* Eq. 26 */
+    frame_prim(W0, &p0);
+    moments(&p0, &m0);
+    double dwL[4], dwR[4], aL[4], aR[4], dA[4], A[4];
+    for (int k = 0; k < 4; ++k) {
+        dwL[k] = (W0[k] - WL[k]) / (dL * p0.rho);
+        dwR[k] = (WR[k] - W0[k]) / (dR * p0.rho);
+    }
+    micro_slope(&p0, dwL, aL);
+    micro_slope(&p0, dwR, aR);
+    pr_fix(&p0, aL, Pr);
+    pr_fix(&p0, aR, Pr);
+    psi_poly_mom(m0.up, &m0, 1, 0, aL, t1);
+    psi_poly_mom(m0.um, &m0, 1, 0, aR, t2);
+    for (int k = 0; k < 4; ++k) dA[k] = -(t1[k] + t2[k]);                    /* Eq. 31 */
+    micro_slope(&p0, dA, A);
+    double fa_p[4], fa_m[4], fb_p[4], fb_m[4], fc_p[4], fc_m[4];
+    psi_mom(m0.up, &m0, 1, 0, 0, fa_p);
+    psi_mom(m0.um, &m0, 1, 0, 0, fa_m);
+    psi_poly_mom(m0.up, &m0, 2, 0, aL, fb_p);
+    psi_poly_mom(m0.um, &m0, 2, 0, aR, fb_m);
+    psi_poly_mom(m0.up, &m0, 1, 0, A, fc_p);
+    psi_poly_mom(m0.um, &m0, 1, 0, A, fc_m);
+    for (int k = 0; k < 4; ++k)
+        F[k] = p0.rho * (cL[0] * fa_p[k] + cL[1] * fb_p[k] + cL[2] * fc_p[k]
+                         + cR[0] * fa_m[k] + cR[1] * fb_m[k] + cR[2] * fc_m[k]);
+    if (hL && frame_prim(WhL, &phL)) {
+        moments(&phL, &mhL);
+        psi_mom(mhL.up, &mhL, 1, 0, 0, t1);
+        for (int k = 0; k < 4; ++k) F[k] += frL * phL.rho * t1[k];
+    }
+    if (hR && frame_prim(WhR, &phR)) {
+        moments(&phR, &mhR);
+        psi_mom(mhR.um, &mhR, 1, 0, 0, t2);
+        for (int k = 0; k < 4; ++k) F[k] += frR * phR.rho * t2[k];
+    }
+    if (W0o) for (int k = 0; k < 4; ++k) W0o[k] = W0[k];
+    if (aLo) for (int k = 0; k < 4; ++k) aLo[k] = aL[k];
+    if (aRo) for (int k = 0; k < 4; ++k) aRo[k] = aR[k];
+    if (Ao) for (int k = 0; k < 4; ++k) Ao[k] = A[k];
+}
+
+void oracle_face_flux_test(const double* WL, const double* WR, const double* WhL, const double* WhR,
+                           const double* cL, const double* cR, double dL, double dR, double Pr,
+                           double* F, double* W0, double* aL, double* aR, double* A)
+{
+    face_flux(WL, WR, WhL, WhR, WhL != NULL, WhR != NULL, cL, cR, cL[5], cR[5], dL, dR, Pr, F, W0, aL, aR, A);
+}
+
+/* diffuse isothermal wall (reading): incoming half of the fluid cell's g and g^h, outgoing wall
+ * Maxwellian at T_w with the density that makes the wave mass flux zero */
+static void wall_flux(const or_ctx* cx, const double WL[4], const double WhL[4], int hL, const double cL[7],
+                      double frL, double F[4])
+{
+    or_prim pL, ph, pw;
+    or_mom mL, mh, mw;
+    double t[4], o[4];
+    frame_prim(WL, &pL);
+    moments(&pL, &mL);
+    psi_mom(mL.up, &mL, 1, 0, 0, t);
+    for (int k = 0; k < 4; ++k) F[k] = cL[0] * pL.rho * t[k];
+    if (hL && frame_prim(WhL, &ph)) {
+        moments(&ph, &mh);
+        psi_mom(mh.up, &mh, 1, 0, 0, t);
+        for (int k = 0; k < 4; ++k) F[k] += frL * ph.rho * t[k];
+    }
+    pw.rho = 1.0; pw.U = 0.0; pw.V = 0.0; pw.lam = 0.5 / (OR_R * cx->Tw);
+    moments(&pw, &mw);
+    psi_mom(mw.um, &mw, 1, 0, 0, o);
+    const double rw = -F[0] / o[0];
+    for (int k = 0; k < 4; ++k) F[k] += rw * o[k];
+}
+
+static void to_frame(const double W[4], double nx, double ny, double out[4])
+{
+    out[0] = W[0];
+    out[1] = W[1] * nx + W[2] * ny;
+    out[2] = -W[1] * ny + W[2] * nx;
+    out[3] = W[3];
+}
+
+/* ------------------------------------------------------------------------------- set-up (a0) */
+
+static int build_geometry(or_ctx* cx, const oracle_mesh* m)
+{
+    const int ni = m->ni, nj = m->nj, C = ni * nj;
+    cx->ni = ni; cx->nj = nj; cx->C = C; cx->dim = m->dim; cx->periodic_j = m->periodic_j;
+    int periodic_i = m->dim == 1 && m->bc_imin[0] == OR_BC_PERIODIC;
+    if (m->dim == 1) {
+        if (nj != 1) return OR_EINVAL;
+        if ((m->bc_imin[0] == OR_BC_PERIODIC) != (m->bc_imax[0] == OR_BC_PERIODIC)) return OR_EINVAL;
+        cx->F = periodic_i ? ni : ni + 1;
+    } else {
+        cx->F = (ni + 1) * nj + ni * (m->periodic_j ? nj : nj + 1);
+    }
+    const int F = cx->F;
+    cx->vol = zalloc(C, 8); cx->inv_vol = zalloc(C, 8); cx->xc = zalloc(C, 8); cx->yc = zalloc(C, 8);
+    cx->nfc = zalloc(C, 4);
+    cx->cface = zalloc(4 * C, 4); cx->csgn = zalloc(4 * C, 4); cx->cnbr = zalloc(4 * C, 4);
+    cx->cnk = zalloc(4 * C, 4); cx->cbc = zalloc(4 * C, 4);
+    cx->cnx = zalloc(4 * C, 8); cx->cny = zalloc(4 * C, 8); cx->cd = zalloc(4 * C, 8);
+    cx->cshift = zalloc(4 * C, 8); cx->cvx = zalloc(4 * C, 8); cx->cvy = zalloc(4 * C, 8);
+    cx->xl = zalloc(C, 8); cx->xr = zalloc(C, 8);
+    cx->fL = zalloc(F, 4); cx->fR = zalloc(F, 4); cx->fbc = zalloc(F, 4); cx->fwall = zalloc(F, 4);
+    cx->fnx = zalloc(F, 8); cx->fny = zalloc(F, 8); cx->fs = zalloc(F, 8); cx->fdL = zalloc(F, 8);
+    cx->fdR = zalloc(F, 8); cx->finv_s = zalloc(F, 8);
+    double* fd = zalloc(F, 8);
+    if (m->dim == 1) {
+        const double* xs = m->xv;
+        for (int i = 0; i < ni; ++i) {
+            cx->xl[i] = xs[i];
+            cx->xr[i] = xs[i + 1];
+            cx->vol[i] = xs[i + 1] - xs[i];
+            cx->xc[i] = 0.5 * (xs[i] + xs[i + 1]);
+            cx->nfc[i] = 2;
+        }
+        for (int f = 0; f < F; ++f) {
+            cx->fnx[f] = 1.0; cx->fny[f] = 0.0; cx->fs[f] = 1.0;
+            if (f == 0 && periodic_i) {
+                cx->fL[f] = ni - 1; cx->fR[f] = 0; cx->fbc[f] = OR_BC_PERIODIC;
+                cx->fdL[f] = xs[ni] - cx->xc[ni - 1]; cx->fdR[f] = cx->xc[0] - xs[0];
+            } else if (f == 0) {
+                cx->fL[f] = 0; cx->fR[f] = -1; cx->fbc[f] = m->bc_imin[0]; cx->fnx[f] = -1.0;
+                cx->fdL[f] = cx->fdR[f] = cx->xc[0] - xs[0];
+            } else if (f == ni) {
+                cx->fL[f] = ni - 1; cx->fR[f] = -1; cx->fbc[f] = m->bc_imax[0];
+                cx->fdL[f] = cx->fdR[f] = xs[ni] - cx->xc[ni - 1];
+            } else {
+                cx->fL[f] = f - 1; cx->fR[f] = f; cx->fbc[f] = 0;
+                cx->fdL[f] = xs[f] - cx->xc[f - 1]; cx->fdR[f] = cx->xc[f] - xs[f];
+            }
+        }
+        for (int i = 0; i < ni; ++i) {
+            /* local face 0: left end (outward -x), local face 1: right end (outward +x) */
+            const int fl = (i == 0 && periodic_i) ? 0 : i;
+            const int fr = (i == ni - 1 && periodic_i) ? 0 : i + 1;
+            const int q0 = 4 * i, q1 = 4 * i + 1;
+            cx->cface[q0] = fl; cx->cface[q1] = fr;
+            cx->cnx[q0] = -1.0; cx->cny[q0] = 0.0; cx->cd[q0] = -xs[i];
+            cx->cnx[q1] = 1.0; cx->cny[q1] = 0.0; cx->cd[q1] = xs[i + 1];
+            /* left face */
+            if (i > 0) { cx->cnbr[q0] = i - 1; cx->cnk[q0] = 1; cx->csgn[q0] = -1; cx->cbc[q0] = 0; }
+            else if (periodic_i) {
+                cx->cnbr[q0] = ni - 1; cx->cnk[q0] = 1; cx->csgn[q0] = -1; cx->cbc[q0] = OR_BC_PERIODIC;
+                cx->cshift[q0] = xs[ni] - xs[0];
+            } else { cx->cnbr[q0] = -1; cx->cnk[q0] = -1; cx->csgn[q0] = 1; cx->cbc[q0] = m->bc_imin[0]; }
+            /* right face */
+            if (i < ni - 1) { cx->cnbr[q1] = i + 1; cx->cnk[q1] = 0; cx->csgn[q1] = 1; cx->cbc[q1] = 0; }
+            else if (periodic_i) {
+                cx->cnbr[q1] = 0; cx->cnk[q1] = 0; cx->csgn[q1] = 1; cx->cbc[q1] = OR_BC_PERIODIC;
+                cx->cshift[q1] = xs[0] - xs[ni];
+            } else { cx->cnbr[q1] = -1; cx->cnk[q1] = -1; cx->csgn[q1] = 1; cx->cbc[q1] = m->bc_imax[0]; }
+        }
+    } else {
+        const int nvi = ni + 1;
+#define VID(i, j) ((i) + nvi * ((m->periodic_j && (j) == nj) ? 0 : (j)))
+        const int njf = m->periodic_j ? nj : nj + 1;
+        const int joff = (ni + 1) * nj;
+        /* i-faces: from vertex (i, j) to (i, j+1), normal toward +i */
+        for (int j = 0; j < nj; ++j) {
+            for (int i = 0; i <= ni; ++i) {
+                const int f = i + (ni + 1) * j;
+                const int a = VID(i, j), b = VID(i, j + 1);
+                const double ex = m->xv[b] - m->xv[a], ey = m->yv[b] - m->yv[a];
+                const double len = sqrt(ex * ex + ey * ey);
+                double nx = ey / len, ny = -ex / len;
+                cx->fs[f] = len;
+                if (i == 0) {
+                    nx = -nx; ny = -ny;
+                    cx->fL[f] = i + ni * j; cx->fR[f] = -1; cx->fbc[f] = m->bc_imin[j];
+                } else if (i == ni) {
+                    cx->fL[f] = (i - 1) + ni * j; cx->fR[f] = -1; cx->fbc[f] = m->bc_imax[j];
+                } else {
+                    cx->fL[f] = (i - 1) + ni * j; cx->fR[f] = i + ni * j; cx->fbc[f] = 0;
+                }
+                cx->fnx[f] = nx; cx->fny[f] = ny;
+                fd[f] = nx * m->xv[a] + ny * m->yv[a];
+            }
+        }
+        /* j-faces: from vertex (i, j) to (i+1, j), normal toward +j */
+        for (int j = 0; j < njf; ++j) {
+            for (int i = 0; i < ni; ++i) {
+                const int f = joff + i + ni * j;
+                const int a = VID(i, j), b = VID(i + 1, j);
+                const double ex = m->xv[b] - m->xv[a], ey = m->yv[b] - m->yv[a];
+                const double len = sqrt(ex * ex + ey * ey);
+                double nx = -ey / len, ny = ex / len;
+                cx->fs[f] = len;
+                if (m->periodic_j) {
+                    cx->fL[f] = i + ni * ((j + nj - 1) % nj); cx->fR[f] = i + ni * j; cx->fbc[f] = 0;
+                } else if (j == 0) {
+                    nx = -nx; ny = -ny;
+                    cx->fL[f] = i; cx->fR[f] = -1; cx->fbc[f] = m->bc_jmin[i];
+                } else if (j == nj) {
+                    cx->fL[f] = i + ni * (nj - 1); cx->fR[f] = -1; cx->fbc[f] = m->bc_jmax[i];
+                } else {
+                    cx->fL[f] = i + ni * (j - 1); cx->fR[f] = i + ni * j; cx->fbc[f] = 0;
+                }
+                cx->fnx[f] = nx; cx->fny[f] = ny;
+                fd[f] = nx * m->xv[a] + ny * m->yv[a];
+            }
+        }
+        for (int j = 0; j < nj; ++j) {
+            for (int i = 0; i < ni; ++i) {
+                const int c = i + ni * j;
+                const int v[4] = {VID(i, j), VID(i + 1, j), VID(i + 1, j + 1), VID(i, j + 1)};
+                double X[4], Y[4];
+                for (int q = 0; q < 4; ++q) {
+                    X[q] = m->xv[v[q]]; Y[q] = m->yv[v[q]];
+                    cx->cvx[4 * c + q] = X[q]; cx->cvy[4 * c + q] = Y[q];
+                }
+                cx->vol[c] = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[1]) - (X[3] - X[1]) * (Y[2] - Y[0]));
+                const double A1 = 0.5 * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+                const double A2 = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+                cx->xc[c] = (A1 * (X[0] + X[1] + X[2]) + A2 * (X[0] + X[2] + X[3])) / (3.0 * (A1 + A2));
+                cx->yc[c] = (A1 * (Y[0] + Y[1] + Y[2]) + A2 * (Y[0] + Y[2] + Y[3])) / (3.0 * (A1 + A2));
+                cx->nfc[c] = 4;
+                const int jm = m->periodic_j ? j : j;
+                const int fq[4] = {i + (ni + 1) * j, (i + 1) + (ni + 1) * j, joff + i + ni * jm,
+                                   joff + i + ni * ((m->periodic_j && j + 1 == nj) ? 0 : j + 1)};
+                for (int k = 0; k < 4; ++k) {
+                    const int f = fq[k], q = 4 * c + k;
+                    const int isL = cx->fL[f] == c && !(cx->fR[f] == c && (k == 0 || k == 2));
+                    cx->cface[q] = f;
+                    cx->csgn[q] = isL ? 1 : -1;
+                    cx->cnx[q] = isL ? cx->fnx[f] : -cx->fnx[f];
+                    cx->cny[q] = isL ? cx->fny[f] : -cx->fny[f];
+                    cx->cd[q] = isL ? fd[f] : -fd[f];
+                    if (cx->fR[f] < 0) {
+                        cx->cnbr[q] = -1; cx->cnk[q] = -1; cx->cbc[q] = cx->fbc[f];
+                    } else {
+                        cx->cnbr[q] = isL ? cx->fR[f] : cx->fL[f];
+                        cx->cbc[q] = 0;
+                        /* local index of the same face in the neighbour: -i <-> +i, -j <-> +j */
+                        cx->cnk[q] = k ^ 1;
+                    }
+                }
+            }
+        }
+        for (int f = 0; f < F; ++f) {
+            const int L = cx->fL[f], R = cx->fR[f];
+            cx->fdL[f] = fd[f] - (cx->fnx[f] * cx->xc[L] + cx->fny[f] * cx->yc[L]);
+            cx->fdR[f] = R >= 0 ? (cx->fnx[f] * cx->xc[R] + cx->fny[f] * cx->yc[R]) - fd[f] : cx->fdL[f];
+        }
+#undef VID
+    }
+    free(fd);
+    for (int c = 0; c < C; ++c) {
+        if (!(cx->vol[c] > 0.0)) return OR_EINVAL;
+        cx->inv_vol[c] = 1.0 / cx->vol[c];
+    }
+    cx->nwall = 0;
+    for (int f = 0; f < F; ++f) {
+        cx->finv_s[f] = 1.0 / cx->fs[f];
+        cx->fwall[f] = -1;
+        if (cx->fbc[f] == OR_BC_WALL) cx->fwall[f] = cx->nwall++;
+    }
+    cx->wall_face = zalloc(cx->nwall, 4);
+    for (int f = 0; f < F; ++f) if (cx->fwall[f] >= 0) cx->wall_face[cx->fwall[f]] = f;
+    return OR_OK;
+}
+
+/* local time steps (Eq. 24) from the initial freestream field, then the global one (Eq. 25) */
+static void init_time_steps(or_ctx* cx)
+{
+    const double cs = cx->U_inf + 3.0 * sqrt(OR_R * 1.0);
+    cx->dtG = 0.0;
+    for (int c = 0; c < cx->C; ++c) {
+        double perim = 0.0;
+        for (int k = 0; k < cx->nfc[c]; ++k) perim += cx->fs[cx->cface[4 * c + k]];
+        cx->dt[c] = (cx->cfl * cx->vol[c]) / (cs * perim);
+        if (c == 0 || cx->dt[c] < cx->dtG) cx->dtG = cx->dt[c];
+    }
+    if (cx->gts)
+        for (int c = 0; c < cx->C; ++c) cx->dt[c] = cx->dtG;
+    for (int c = 0; c < cx->C; ++c)
+        for (int k = 0; k < cx->nfc[c]; ++k) {
+            const int q = 4 * c + k;
+            cx->ratio[q] = cx->cnbr[q] >= 0 ? cx->dt[cx->cnbr[q]] / cx->dt[c] : 1.0;
+        }
+}
+
+/* ceil(log2(x)) for x > 0, exact through frexp */
+static int ceil_log2(double x)
+{
+    int e;
+    const double m = frexp(x, &e);
+    return m == 0.5 ? e - 1 : e;
+}
+
+/* Fixed-point exponents of the particle tallies (a build choice, not the paper's): a cell may hold up to
+ * 1024 times the freestream density in the largest cell, particles move at most U_inf + 10 sqrt(R T_max);
+ * each per-cell sum then stays below 2^61. */
+static void fixed_exponents(or_ctx* cx, double T_fix)
+{
+    double vmax = 0.0;
+    for (int c = 0; c < cx->C; ++c) if (cx->vol[c] > vmax) vmax = cx->vol[c];
+    double Tmax = 1.0;
+    if (cx->Tw > Tmax) Tmax = cx->Tw;
+    if (T_fix > Tmax) Tmax = T_fix;
+    const double speed = cx->U_inf + 10.0 * sqrt(OR_R * Tmax);
+    const double b0 = 1024.0 * vmax;
+    cx->fx[0] = 61 - ceil_log2(b0);
+    cx->fx[1] = 61 - ceil_log2(b0 * speed);
+    cx->fx[2] = 61 - ceil_log2(b0 * (0.5 * (speed * speed)));
+}
+
+int oracle_fixed_exponents(oracle_ctx* cx, int32_t* out)
+{
+    out[0] = cx->fx[0]; out[1] = cx->fx[1]; out[2] = cx->fx[2];
+    return OR_OK;
+}
+
+int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, double Ma, double Tw,
+                  double cfl, int32_t gts, const oracle_opts* opts, oracle_ctx** out)
+{
+    if (!mesh || !gas || !opts || !out || mesh->ni <= 0 || mesh->nj <= 0) return OR_EINVAL;
+    if (mesh->ni * (int64_t)mesh->nj >= (1 << 21)) return OR_EINVAL;
+    or_ctx* cx = zalloc(1, sizeof(or_ctx));
+    int st = build_geometry(cx, mesh);
+    if (st) { oracle_destroy(cx); return st; }
+    const int C = cx->C, F = cx->F;
+    cx->prec = opts->precision; cx->wave_only = opts->wave_only; cx->record_faces = opts->record_faces;
+    cx->gts = gts; cx->n_ref = opts->n_ref; cx->seed = opts->seed; cx->case_id = opts->case_id;
+    cx->Kn = Kn; cx->Ma = Ma; cx->Tw = Tw; cx->cfl = cfl; cx->omega = gas->omega; cx->Pr = gas->Pr;
+    cx->mu_inf = oracle_mu_inf(Kn, gas->omega);
+    cx->U_inf = Ma * sqrt((5.0 / 3.0) * OR_R * 1.0);
+    cx->m2RTw = -2.0 * OR_R * Tw;
+    cx->sig_w = sqrt(OR_R * Tw);
+    prim_to_cons(1.0, cx->U_inf, 0.0, 1.0, cx->W_inf);
+    prim_to_cons(opts->ghost_state[0], opts->ghost_state[1], opts->ghost_state[2], opts->ghost_state[3], cx->W_fix);
+    cx->dt = zalloc(C, 8); cx->ratio = zalloc(4 * C, 8);
+    init_time_steps(cx);
+    fixed_exponents(cx, opts->ghost_state[3]);
+    cx->W = zalloc(4 * C, 8); cx->wret_prev = zalloc(5 * C, 8);
+    cx->tau = zalloc(C, 8); cx->xr_t = zalloc(C, 8); cx->emx = zalloc(C, 8);
+    cx->Wp = zalloc(4 * C, 8); cx->Wh = zalloc(4 * C, 8); cx->mnew = zalloc(C, 8); cx->co = zalloc(7 * C, 8);
+    cx->samp = zalloc(3 * C, 8);
+    cx->nhp = zalloc(C, 4); cx->hphys = zalloc(C, 4); cx->nhp_off = zalloc(C + 1, 8);
+    cx->wm = zalloc(5 * C, 8); cx->wpl = zalloc(5 * C, 8); cx->wrt = zalloc(5 * C, 8);
+    cx->cross = zalloc(2 * F, 8); cx->wallt = zalloc(3 * cx->nwall, 8); cx->frec_d = zalloc(4 * F, 8);
+    cx->flux = zalloc(4 * F, 8);
+    cx->chi_ema = zalloc(C, 8);
+    cx->surf_sum = zalloc(3 * cx->nwall, 8); cx->surf_last = zalloc(3 * cx->nwall, 8);
+    cx->cap = 1024;
+    cx->p = zalloc(cx->cap, sizeof(or_particle));
+    for (int c = 0; c < C; ++c)
+        for (int k = 0; k < 4; ++k) cx->W[4 * c + k] = cx->W_inf[k];
+    *out = cx;
+    return OR_OK;
+}
+
+void oracle_destroy(oracle_ctx* cx)
+{
+    if (!cx) return;
+    void* ptrs[] = {cx->vol, cx->inv_vol, cx->xc, cx->yc, cx->nfc, cx->cface, cx->csgn, cx->cnbr, cx->cnk,
+                    cx->cbc, cx->cnx, cx->cny, cx->cd, cx->cshift, cx->cvx, cx->cvy, cx->xl, cx->xr, cx->fL,
+                    cx->fR, cx->fbc, cx->fwall, cx->fnx, cx->fny, cx->fs, cx->fdL, cx->fdR, cx->finv_s,
+                    cx->wall_face, cx->dt, cx->ratio, cx->W, cx->wret_prev, cx->tau, cx->xr_t, cx->emx, cx->Wp,
+                    cx->Wh, cx->mnew, cx->co, cx->samp, cx->nhp, cx->hphys, cx->nhp_off, cx->wm, cx->wpl,
+                    cx->wrt, cx->cross, cx->wallt, cx->frec_d, cx->flux, cx->chi_ema, cx->surf_sum,
+                    cx->surf_last, cx->p};
+    for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
+    free(cx);
+}
+
+/* ------------------------------------------------------------------ a1: decomposition (Sec. 4.2) */
+
+static void decompose(or_ctx* cx)
+{
+    const double s0 = ldexp(1.0, -cx->fx[0]), s1 = ldexp(1.0, -cx->fx[1]), s4 = ldexp(1.0, -cx->fx[2]);
+    for (int c = 0; c < cx->C; ++c) {
+        const double* W = cx->W + 4 * c;
+        const int64_t* r = cx->wret_prev + 5 * c;
+        double* Wp = cx->Wp + 4 * c;
+        double* Wh = cx->Wh + 4 * c;
+        const double tau = tau_of(cx, W);
+        /* W^p from the particles retained at the end of the previous step; W^h = W - W^p (Eq. 15) */
+        Wp[0] = ((double)r[0] * s0) / cx->vol[c];
+        Wp[1] = ((double)r[1] * s1) / cx->vol[c];
+        Wp[2] = cx->dim == 1 ? 0.0 : ((double)r[2] * s1) / cx->vol[c];
+        Wp[3] = ((double)r[4] * s4) / cx->vol[c];
+        for (int k = 0; k < 4; ++k) Wh[k] = W[k] - Wp[k];
+        const double x = cx->dt[c] / tau;
+        const double e = or_expd(-x);
+        cx->tau[c] = tau;
+        cx->xr_t[c] = x;
+        cx->emx[c] = e;
+        lts_coeffs(cx->dt[c], tau, e, cx->co + 7 * c);
+        cx->hphys[c] = Wh[0] > 0.0 && (Wh[3] - 0.5 * (Wh[1] * Wh[1] + Wh[2] * Wh[2]) / Wh[0]) > 0.0;
+        cx->nhp[c] = 0;
+        cx->mnew[c] = 0.0;
+        cx->samp[3 * c] = cx->samp[3 * c + 1] = cx->samp[3 * c + 2] = 0.0;
+        if (!cx->wave_only && cx->hphys[c]) {
+            /* W^hp = W^h e^{-dt_i / tau_i}; N^hp = ceil(rho^hp / rho N_ref); m = rho^hp Omega / N^hp (Eq. 17) */
+            const double rho_hp = Wh[0] * e;
+            if (rho_hp > 0.0) {
+                const double q = ceil((rho_hp / W[0]) * (double)cx->n_ref);
+                if (q > (double)OR_MAX_NEW) {
+                    or_set_error(cx, OR_ELIMIT, "more than 2047 new particles in one cell");
+                    continue;
+                }
+                cx->nhp[c] = (int)q;
+                cx->mnew[c] = (rho_hp * cx->vol[c]) / q;
+                const double Uh = Wh[1] / Wh[0], Vh = Wh[2] / Wh[0];
+                const double RTh = (Wh[3] / Wh[0] - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
+                cx->samp[3 * c] = Uh;
+                cx->samp[3 * c + 1] = Vh;
+                cx->samp[3 * c + 2] = RTh;
+            }
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------- a9: wave fluxes */
+
+static void wave_fluxes(or_ctx* cx)
+{
+    for (int f = 0; f < cx->F; ++f) {
+        const int L = cx->fL[f], R = cx->fR[f], bc = cx->fbc[f];
+        const double nx = cx->fnx[f], ny = cx->fny[f];
+        double WL[4], WhL[4], WR[4], WhR[4], F[4];
+        to_frame(cx->W + 4 * L, nx, ny, WL);
+        to_frame(cx->Wh + 4 * L, nx, ny, WhL);
+        const double* cL = cx->co + 7 * L;
+        const double frL = cx->wave_only ? cL[3] : cL[5];
+        if (bc == 0 || bc == OR_BC_PERIODIC) {
+            to_frame(cx->W + 4 * R, nx, ny, WR);
+            to_frame(cx->Wh + 4 * R, nx, ny, WhR);
+            const double* cR = cx->co + 7 * R;
+            const double frR = cx->wave_only ? cR[3] : cR[5];
+            face_flux(WL, WR, WhL, WhR, cx->hphys[L], cx->hphys[R], cL, cR, frL, frR, cx->fdL[f], cx->fdR[f],
+                      cx->Pr, F, NULL, NULL, NULL, NULL);
+        } else if (bc == OR_BC_WALL) {
+            wall_flux(cx, WL, WhL, cx->hphys[L], cL, frL, F);
+        } else if (bc == OR_BC_SYMMETRY) {
+            /* mirror ghost: same state with the normal velocity reversed, same coefficients */
+            double Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
+            face_flux(WL, Wm, WhL, Whm, cx->hphys[L], cx->hphys[L], cL, cL, frL, frL, cx->fdL[f], cx->fdL[f],
+                      cx->Pr, F, NULL, NULL, NULL, NULL);
+        } else {
+            /* far-field / fixed ghost: pure wave, evaluated with the fluid cell's time step (Sec. 4.2) */
+            double Wg[4];
+            if (bc == OR_BC_FIXED) {
+                for (int k = 0; k < 4; ++k) Wg[k] = cx->W_fix[k];
+            } else {
+                const double un_inf = cx->W_inf[1] * nx + cx->W_inf[2] * ny;
+                const double* src = un_inf < 0.0 ? cx->W_inf : cx->W + 4 * L;
+                for (int k = 0; k < 4; ++k) Wg[k] = src[k];
+            }
+            to_frame(Wg, nx, ny, WR);
+            double cR[7];
+            lts_coeffs(cx->dt[L], tau_of(cx, Wg), or_expd(-cx->dt[L] / tau_of(cx, Wg)), cR);
+            face_flux(WL, WR, WhL, WR, cx->hphys[L], 1, cL, cR, frL, cR[3], cx->fdL[f], cx->fdL[f], cx->Pr, F,
+                      NULL, NULL, NULL, NULL);
+        }
+        /* back to the global frame: momentum = F_n n + F_t t, t = (-n_y, n_x) */
+        cx->flux[4 * f + 0] = F[0];
+        cx->flux[4 * f + 1] = F[1] * nx - F[2] * ny;
+        cx->flux[4 * f + 2] = F[1] * ny + F[2] * nx;
+        cx->flux[4 * f + 3] = F[3];
+    }
+}
+
+/* -------------------------------------------------------------------- a10: update (Eq. 46) */
+
+static void update(or_ctx* cx)
+{
+    const double sc[4] = {ldexp(1.0, -cx->fx[0]), ldexp(1.0, -cx->fx[1]), ldexp(1.0, -cx->fx[1]),
+                          ldexp(1.0, -cx->fx[2])};
+    const int tk[4] = {0, 1, 2, 4};
+    double rs[4] = {0, 0, 0, 0};
+    const double alpha = 2.0 / 1001.0;
+    for (int c = 0; c < cx->C; ++c) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int k = 0; k < cx->nfc[c]; ++k) {
+            const int f = cx->cface[4 * c + k];
+            for (int q = 0; q < 4; ++q) {
+                const double t = cx->flux[4 * f + q] * cx->fs[f];
+                acc[q] += cx->csgn[4 * c + k] > 0 ? t : -t;
+            }
+        }
+        const double coef = cx->dt[c] / cx->vol[c];
+        double* W = cx->W + 4 * c;
+        double Wn[4];
+        for (int q = 0; q < 4; ++q) {
+            const int64_t d = cx->wpl[5 * c + tk[q]] - cx->wm[5 * c + tk[q]];
+            Wn[q] = (W[q] - coef * acc[q]) + ((double)d * sc[q]) / cx->vol[c];
+        }
+        if (cx->dim == 1) Wn[2] = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const double r = (Wn[q] - W[q]) / cx->dt[c];
+            rs[q] += cx->vol[c] * (r * r);
+            W[q] = Wn[q];
+        }
+        const double e = W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0];
+        if (!(W[0] > 0.0) || !(e > 0.0) || !isfinite(W[3]))
+            or_set_error(cx, OR_ENONPHYS, "non-physical cell state after the update");
+        const double chi = (((double)cx->wpl[5 * c] * sc[0]) / cx->vol[c]) / W[0];
+        cx->chi_ema[c] = cx->step == 0 ? chi : cx->chi_ema[c] + alpha * (chi - cx->chi_ema[c]);
+    }
+    for (int q = 0; q < 4; ++q) cx->res[q] = sqrt(rs[q]);
+    if (!cx->have_res0) {
+        for (int q = 0; q < 4; ++q) cx->res0[q] = cx->res[q] > 0.0 ? cx->res[q] : 1.0;
+        cx->have_res0 = 1;
+    }
+}
+
+/* ------------------------------------------------------------ a11: surface quantities (Sec. 5.1) */
+
+static void surface(or_ctx* cx)
+{
+    const double s1 = ldexp(1.0, -cx->fx[1]), s4 = ldexp(1.0, -cx->fx[2]);
+    for (int iw = 0; iw < cx->nwall; ++iw) {
+        const int f = cx->wall_face[iw], c = cx->fL[f];
+        const double nx = cx->fnx[f], ny = cx->fny[f], tx = -ny, ty = nx;
+        const double* F = cx->flux + 4 * f;
+        const double sdt = cx->fs[f] * cx->dt[c];
+        const double px = ((double)cx->wallt[3 * iw] * s1) / sdt;
+        const double py = ((double)cx->wallt[3 * iw + 1] * s1) / sdt;
+        const double pe = ((double)cx->wallt[3 * iw + 2] * s4) / sdt;
+        const double p = (F[1] + px) * nx + (F[2] + py) * ny;
+        const double tw = (F[1] + px) * tx + (F[2] + py) * ty;
+        const double q = F[3] + pe;
+        cx->surf_last[3 * iw] = p; cx->surf_last[3 * iw + 1] = tw; cx->surf_last[3 * iw + 2] = q;
+        cx->surf_sum[3 * iw] += p; cx->surf_sum[3 * iw + 1] += tw; cx->surf_sum[3 * iw + 2] += q;
+    }
+    cx->nsurf += 1;
+}
+
+/* ----------------------------------------------------------------------------------- one step */
+
+static int one_step(or_ctx* cx)
+{
+    const int C = cx->C;
+    memset(cx->wm, 0, 5 * (size_t)C * 8);
+    memset(cx->wpl, 0, 5 * (size_t)C * 8);
+    memset(cx->wrt, 0, 5 * (size_t)C * 8);
+    memset(cx->cross, 0, 2 * (size_t)cx->F * 8);
+    memset(cx->wallt, 0, 3 * (size_t)cx->nwall * 8);
+    for (int k = 2; k < 8; ++k) cx->stats[k] = 0;
+    /* step 1: decomposition and sampling; step 2: free transport and tallies (Sec. 3.3, Sec. 4.2) */
+    decompose(cx);
+    if (cx->err) return cx->err;
+    if (cx->prec == 0) or_particles_step_f32(cx); else or_particles_step_f64(cx);
+    /* step 3: wave fluxes from the step-start W and W^h, then the conservative update (Eq. 46) */
+    wave_fluxes(cx);
+    update(cx);
+    surface(cx);
+    memcpy(cx->wret_prev, cx->wrt, 5 * (size_t)C * 8);
+    cx->step += 1;
+    cx->stats[0] = cx->step;
+    cx->stats[1] = cx->np;
+    return cx->err;
+}
+
+int oracle_step(oracle_ctx* cx, int32_t n)
+{
+    if (!cx || n < 0) return OR_EINVAL;
+    if (cx->err) return cx->err;
+    for (int32_t s = 0; s < n; ++s) {
+        int st = one_step(cx);
+        if (st) return st;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------- accessors */
+
+int oracle_set_field(oracle_ctx* cx, const double* prim)
+{
+    for (int c = 0; c < cx->C; ++c) {
+        const double* p = prim + 4 * c;
+        if (!(p[0] > 0.0) || !(p[3] > 0.0)) return OR_EINVAL;
+        prim_to_cons(p[0], p[1], p[2], p[3], cx->W + 4 * c);
+    }
+    memset(cx->wret_prev, 0, 5 * (size_t)cx->C * 8);
+    cx->np = 0;
+    return OR_OK;
+}
+
+int oracle_get_field(oracle_ctx* cx, double* W, double* Wp)
+{
+    memcpy(W, cx->W, 4 * (size_t)cx->C * 8);
+    if (Wp) {
+        for (int c = 0; c < cx->C; ++c) {
+            const int64_t* r = cx->wret_prev + 5 * c;
+            Wp[4 * c] = ((double)r[0] * ldexp(1.0, -cx->fx[0])) / cx->vol[c];
+            Wp[4 * c + 1] = ((double)r[1] * ldexp(1.0, -cx->fx[1])) / cx->vol[c];
+            Wp[4 * c + 2] = ((double)r[2] * ldexp(1.0, -cx->fx[1])) / cx->vol[c];
+            Wp[4 * c + 3] = ((double)r[4] * ldexp(1.0, -cx->fx[2])) / cx->vol[c];
+        }
+    }
+    return OR_OK;
+}
+
+int oracle_residual(oracle_ctx* cx, double* out)
+{
+    for (int q = 0; q < 4; ++q) {
+        out[q] = cx->res[q] / cx->res0[q];
+        out[4 + q] = cx->res[q];
+    }
+    return OR_OK;
+}
+
+int oracle_surface(oracle_ctx* cx, double* p, double* tau, double* q, int32_t n_wall, int32_t averaged)
+{
+    if (n_wall != cx->nwall) return OR_EINVAL;
+    const double* src = averaged ? cx->surf_sum : cx->surf_last;
+    const double d = averaged ? (cx->nsurf > 0 ? (double)cx->nsurf : 1.0) : 1.0;
+    for (int i = 0; i < n_wall; ++i) {
+        p[i] = src[3 * i] / d;
+        tau[i] = src[3 * i + 1] / d;
+        q[i] = src[3 * i + 2] / d;
+    }
+    return OR_OK;
+}
+
+int oracle_stats(oracle_ctx* cx, int64_t* out)
+{
+    memcpy(out, cx->stats, sizeof cx->stats);
+    return OR_OK;
+}
+
+int64_t oracle_num_particles(oracle_ctx* cx) { return cx->np; }
+
+int oracle_get_particles(oracle_ctx* cx, int64_t cap, uint64_t* pid, int32_t* cell, double* x, double* y,
+                         double* u, double* v, double* w, double* m)
+{
+    if (cap < cx->np) return OR_EINVAL;
+    for (int64_t i = 0; i < cx->np; ++i) {
+        const or_particle* P = &cx->p[i];
+        pid[i] = P->pid; cell[i] = P->cell;
+        x[i] = P->x; y[i] = P->y; u[i] = P->u; v[i] = P->v; w[i] = P->w; m[i] = P->m;
+    }
+    return OR_OK;
+}
+
+int oracle_set_state(oracle_ctx* cx, int64_t step, const double* W, const int64_t* wret, int64_t np,
+                     const uint64_t* pid, const int32_t* cell, const double* x, const double* y,
+                     const double* u, const double* v, const double* w, const double* m)
+{
+    cx->step = step;
+    memcpy(cx->W, W, 4 * (size_t)cx->C * 8);
+    memcpy(cx->wret_prev, wret, 5 * (size_t)cx->C * 8);
+    if (np > cx->cap) {
+        cx->cap = np;
+        cx->p = (or_particle*)realloc(cx->p, (size_t)np * sizeof(or_particle));
+    }
+    for (int64_t i = 0; i < np; ++i) {
+        or_particle* P = &cx->p[i];
+        memset(P, 0, sizeof *P);
+        P->pid = pid[i]; P->cell = cell[i];
+        P->x = x[i]; P->y = y[i]; P->u = u[i]; P->v = v[i]; P->w = w[i]; P->m = m[i];
+    }
+    cx->np = np;
+    return OR_OK;
+}
+
+int oracle_get_tallies(oracle_ctx* cx, int64_t* wm, int64_t* wpl, int64_t* wret, int64_t* cross, int64_t* wall,
+                       int64_t* frec)
+{
+    const size_t C = (size_t)cx->C;
+    if (wm) memcpy(wm, cx->wm, 5 * C * 8);
+    if (wpl) memcpy(wpl, cx->wpl, 5 * C * 8);
+    if (wret) memcpy(wret, cx->wrt, 5 * C * 8);
+    if (cross) memcpy(cross, cx->cross, 2 * (size_t)cx->F * 8);
+    if (wall) memcpy(wall, cx->wallt, 3 * (size_t)cx->nwall * 8);
+    if (frec) memcpy(frec, cx->frec_d, 4 * (size_t)cx->F * 8);
+    return OR_OK;
+}
+
+/* per cell: tau, x = dt/tau, e^{-x}, N^hp, m_new, U^h, V^h, R T^h of the last decomposition */
+int oracle_get_cell_data(oracle_ctx* cx, double* out)
+{
+    for (int c = 0; c < cx->C; ++c) {
+        double* o = out + 8 * c;
+        o[0] = cx->tau[c]; o[1] = cx->xr_t[c]; o[2] = cx->emx[c]; o[3] = (double)cx->nhp[c];
+        o[4] = cx->mnew[c]; o[5] = cx->samp[3 * c]; o[6] = cx->samp[3 * c + 1]; o[7] = cx->samp[3 * c + 2];
+    }
+    return OR_OK;
+}
+
+int oracle_get_flux(oracle_ctx* cx, double* flux)
+{
+    memcpy(flux, cx->flux, 4 * (size_t)cx->F * 8);
+    return OR_OK;
+}
+
+int oracle_get_geometry(oracle_ctx* cx, double* dt, double* vol, int32_t* nfaces, int32_t* nwall)
+{
+    if (dt) memcpy(dt, cx->dt, (size_t)cx->C * 8);
+    if (vol) memcpy(vol, cx->vol, (size_t)cx->C * 8);
+    if (nfaces) *nfaces = cx->F;
+    if (nwall) *nwall = cx->nwall;
+    return OR_OK;
+}
+
+const char* oracle_last_error(oracle_ctx* cx) { return cx->msg; }
+
+/* Sec. 4.1, Eq. 39 with constant transported mass: left- and right-hand sides of the balance condition
+ * sum(dt_R) / sum(dt_L) and (1/M) sum(dt_R / dt_L) for a sequence of M step pairs. */
+void oracle_balance_condition(int32_t M, const double* dtL, const double* dtR, double* out)
+{
+    double sL = 0.0, sR = 0.0, q = 0.0;
+    for (int32_t l = 0; l < M; ++l) {
+        sL += dtL[l];
+        sR += dtR[l];
+        q += dtR[l] / dtL[l];
+    }
+    out[0] = sR / sL;
+    out[1] = q / (double)M;
+}

@@ -1,0 +1,104 @@
+/* ORACLE (test infrastructure only): internal declarations shared by the oracle's own translation units. */
+#ifndef ORACLE_INTERNAL_H
+#define ORACLE_INTERNAL_H
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include "oracle.h"
+
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_ELIMIT = 4, OR_ENONPHYS = 5, OR_EOVERFLOW = 6 };
+enum { OR_BC_WALL = 1, OR_BC_FARFIELD = 2, OR_BC_FIXED = 3, OR_BC_SYMMETRY = 4, OR_BC_PERIODIC = 5 };
+
+#define OR_R 0.5                 /* gas constant in the reference units (2 R T_inf = 1) */
+#define OR_MAX_ITERS 256         /* face crossings + wall hits per particle per step */
+#define OR_MAX_NEW 2047          /* new particles per cell per step (11-bit index in the id) */
+
+
+typedef struct {
+    double x, y, u, v, w, m;     /* FP32-representable values in production emulation */
+    int32_t cell;
+    uint64_t pid;
+    /* per-step scratch */
+    double tf;
+    int32_t is_new, collide, alive, iters;
+} or_particle;
+
+struct oracle_ctx {
+    /* configuration */
+    int dim, ni, nj, periodic_j, C, F;
+    int prec, wave_only, record_faces, gts, n_ref;
+    uint64_t seed;
+    uint32_t case_id;
+    int64_t step;
+    double Kn, Ma, Tw, cfl, omega, Pr, mu_inf, U_inf;
+    double W_inf[4], W_fix[4];
+    int fx[3];                                   /* fixed-point exponents: mass, momentum, energy */
+    /* cells */
+    double *vol, *inv_vol, *xc, *yc;
+    int *nfc;
+    int *cface, *csgn, *cnbr, *cnk, *cbc;        /* [4C] */
+    double *cnx, *cny, *cd, *cshift;             /* [4C] outward normal, plane offset, periodic shift */
+    double *cvx, *cvy;                           /* [4C] vertices, counter-clockwise */
+    double *xl, *xr;                             /* 1-D cell ends */
+    /* faces */
+    int *fL, *fR, *fbc, *fwall;
+    double *fnx, *fny, *fs, *fdL, *fdR, *finv_s;
+    int nwall;
+    int *wall_face;
+    /* time steps */
+    double *dt, *ratio;                          /* dt[C]; ratio[4C] = dt[nbr] / dt[c] */
+    double dtG;
+    /* state */
+    double *W;                                   /* [4C] */
+    int64_t *wret_prev;                          /* [5C] retained tally of the previous step */
+    /* per-step cell data */
+    double *tau, *xr_t, *emx, *Wp, *Wh, *mnew, *co;   /* co: [7C] normalised coefficients */
+    double* samp;                                /* [3C] U^h, V^h, R T^h for sampling */
+    double m2RTw, sig_w;                         /* -2 R T_w and sqrt(R T_w) */
+    int *nhp, *hphys;
+    int64_t *nhp_off;
+    /* tallies */
+    int64_t *wm, *wpl, *wrt, *cross, *wallt;
+    double* frec_d;                              /* [4F] side-recorded crossing masses (diagnostic) */
+    double *flux;                                /* [4F] */
+    /* particles */
+    int64_t np, cap;
+    or_particle* p;
+    /* diagnostics */
+    double res[4], res0[4];
+    int have_res0;
+    double* chi_ema;
+    double *surf_sum, *surf_last;
+    int64_t nsurf;
+    int64_t stats[8];
+    int err;
+    char msg[256];
+};
+typedef struct oracle_ctx or_ctx;
+
+/* rng */
+void   or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void   or_draw(const or_ctx* cx, uint64_t pid, uint32_t draw, uint32_t out[4]);
+float  or_u01f(uint32_t w);
+double or_u01d(uint32_t lo, uint32_t hi);
+void   or_uniforms_f(const or_ctx* cx, uint64_t pid, uint32_t base, int n, float* u);
+void   or_uniforms_d(const or_ctx* cx, uint64_t pid, uint32_t base, int n, double* u);
+/* deterministic math */
+float  or_logf(float x);
+double or_logd(double x);
+double or_expd(double x);
+double or_powd(double x, double y);
+void   or_sincos2pif(float u, float* s, float* c);
+void   or_sincos2pid(double u, double* s, double* c);
+/* particles (float and double instantiations) */
+void or_particles_step_f32(or_ctx* cx);
+void or_particles_step_f64(or_ctx* cx);
+void or_set_error(or_ctx* cx, int code, const char* msg);
+
+/* Philox draw layout: the first counter word of each draw group */
+#define OR_DRAW_POS 0u
+#define OR_DRAW_VEL 2u
+#define OR_DRAW_TF 5u
+#define OR_DRAW_WALL(h) (8u + 2u * (uint32_t)(h))
+
+#endif

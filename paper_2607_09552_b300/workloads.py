@@ -1,0 +1,209 @@
+"""Seeded synthetic inputs for the UGKWP-LTS step: meshes, boundary tags, gas and flow states.
+
+This module defines *workloads* only. It holds none of the method's arithmetic (no time steps, relaxation
+times, fluxes, sampling or transport): it produces the vertex coordinates, boundary-condition tags and
+reference states that both the CUDA library and the CPU oracle take as inputs, so that both sides see the
+identical mesh.
+
+Non-dimensionalisation (a reading; the paper does not state one): rho_inf = 1, T_inf = 1, R = 1/2, so that
+2 R T_inf = 1, and U_inf = Ma * sqrt(gamma R T_inf) with gamma = 5/3 (monatomic gas, three translational
+degrees of freedom, no internal ones; Sec. 2 "Gas-kinetic theory", eq. (1) with D = 0).
+
+Meshes are structured: ni x nj quadrilaterals with vertex (i, j) stored at index i + (ni + 1) * j. For a
+1-D line mesh nj = 1 and only the x coordinates matter.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+R_GAS = 0.5
+GAMMA = 5.0 / 3.0
+
+# boundary-condition tags shared by the C ABI of the library and of the oracle (plain integers)
+BC_WALL = 1        # diffuse isothermal wall at T_w
+BC_FARFIELD = 2    # freestream ghost on inflow, zero-gradient ghost on outflow; particles leaving are deleted
+BC_FIXED = 3       # ghost fixed at the second reference state (1-D downstream state); particles deleted
+BC_SYMMETRY = 4    # specular mirror
+BC_PERIODIC = 5    # 1-D only: the two ends of the line are joined
+
+MESH_LINE = 0
+MESH_OMESH = 1
+MESH_PLATE = 2
+
+
+@dataclass
+class Mesh:
+    kind: int
+    ni: int
+    nj: int
+    dim: int
+    periodic_j: int
+    xv: np.ndarray
+    yv: np.ndarray
+    bc_imin: np.ndarray
+    bc_imax: np.ndarray
+    bc_jmin: np.ndarray
+    bc_jmax: np.ndarray
+    info: dict = field(default_factory=dict)
+
+    @property
+    def ncells(self) -> int:
+        return self.ni * self.nj
+
+
+def freestream_speed(Ma: float) -> float:
+    return Ma * math.sqrt(GAMMA * R_GAS * 1.0)
+
+
+def geometric_sizes(n: int, h1: float, ratio: float) -> np.ndarray:
+    return h1 * ratio ** np.arange(n, dtype=np.float64)
+
+
+def solve_ratio(n: int, h1: float, span: float) -> float:
+    """Geometric ratio r with sum_{k<n} h1 r^k == span (bisection; workload geometry, not the method)."""
+    lo, hi = 1.0 + 1e-12, 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if h1 * (mid ** n - 1.0) / (mid - 1.0) > span:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+def line_mesh(ni: int, x0: float, x1: float, end_ratio: float = 1.0, bc_left: int = BC_FARFIELD,
+              bc_right: int = BC_FIXED) -> Mesh:
+    """1-D line [x0, x1] with ni cells whose sizes grow geometrically from left to right by end_ratio."""
+    if end_ratio == 1.0:
+        xs = np.linspace(x0, x1, ni + 1)
+    else:
+        r = end_ratio ** (1.0 / (ni - 1))
+        h = geometric_sizes(ni, 1.0, r)
+        h *= (x1 - x0) / h.sum()
+        xs = np.concatenate([[x0], x0 + np.cumsum(h)])
+        xs[-1] = x1
+    xv = np.zeros((2, ni + 1))
+    xv[0] = xs
+    xv[1] = xs
+    yv = np.zeros((2, ni + 1))
+    yv[1] = 1.0
+    return Mesh(MESH_LINE, ni, 1, 1, 0, xv.reshape(-1).copy(), yv.reshape(-1).copy(),
+                np.array([bc_left], np.int32), np.array([bc_right], np.int32),
+                np.zeros(ni, np.int32), np.zeros(ni, np.int32), info={"x0": x0, "x1": x1})
+
+
+def omesh(ni: int, nj: int, h1: float, r_out: float, r_cyl: float = 0.5) -> Mesh:
+    """Body-fitted O-mesh around a cylinder of radius r_cyl: i radial (wall at i = 0), j circumferential.
+
+    The radial stretching ratio is solved so that ni cells of first height h1 reach r_out exactly.
+    Vertex angle theta_j = 2 pi j / nj (counter-clockwise), so theta = pi (the stagnation point of a
+    +x freestream) is a vertex whenever nj is even.
+    """
+    ratio = solve_ratio(ni, h1, r_out - r_cyl)
+    h = geometric_sizes(ni, h1, ratio)
+    r = np.concatenate([[r_cyl], r_cyl + np.cumsum(h)])
+    r[-1] = r_out
+    th = 2.0 * np.pi * np.arange(nj + 1) / nj
+    th[-1] = 0.0
+    xv = (r[None, :] * np.cos(th)[:, None]).reshape(-1)
+    yv = (r[None, :] * np.sin(th)[:, None]).reshape(-1)
+    return Mesh(MESH_OMESH, ni, nj, 2, 1, xv.copy(), yv.copy(),
+                np.full(nj, BC_WALL, np.int32), np.full(nj, BC_FARFIELD, np.int32),
+                np.zeros(ni, np.int32), np.zeros(ni, np.int32),
+                info={"ratio": ratio, "r_cyl": r_cyl, "r_out": r_out, "h1": h1})
+
+
+def plate_mesh(ni: int = 240, nj: int = 120, h1: float = 1e-4, ratio: float = 1.06, L: float = 1.0,
+               x_lead: float = -0.1, x_trail: float = 1.1) -> Mesh:
+    """Cartesian mesh over a sharp flat plate of length L on y = 0 (wall for 0 <= x <= L, mirror elsewhere)."""
+    xs = np.linspace(x_lead * L, x_trail * L, ni + 1)
+    hy = geometric_sizes(nj, h1 * L, ratio)
+    ys = np.concatenate([[0.0], np.cumsum(hy)])
+    xv = np.tile(xs, nj + 1)
+    yv = np.repeat(ys, ni + 1)
+    xc = 0.5 * (xs[:-1] + xs[1:])
+    bc_jmin = np.where((xc >= 0.0) & (xc <= L), BC_WALL, BC_SYMMETRY).astype(np.int32)
+    return Mesh(MESH_PLATE, ni, nj, 2, 0, xv, yv,
+                np.full(nj, BC_FARFIELD, np.int32), np.full(nj, BC_FARFIELD, np.int32),
+                bc_jmin, np.full(ni, BC_FARFIELD, np.int32), info={"L": L, "ratio": ratio})
+
+
+def rankine_hugoniot(Ma: float, gamma: float = GAMMA):
+    """Downstream (rho, u, T) of a normal shock for upstream (1, U_inf(Ma), 1): textbook jump relations."""
+    rho2 = (gamma + 1.0) * Ma ** 2 / ((gamma - 1.0) * Ma ** 2 + 2.0)
+    p2 = (2.0 * gamma * Ma ** 2 - (gamma - 1.0)) / (gamma + 1.0)
+    u1 = freestream_speed(Ma)
+    u2 = u1 / rho2
+    T2 = p2 / rho2
+    return rho2, u2, T2
+
+
+def shock_initial_field(mesh: Mesh, Ma: float) -> np.ndarray:
+    """Per-cell primitive (rho, U, V, T): the Rankine-Hugoniot step at x = 0."""
+    xs = mesh.xv[: mesh.ni + 1]
+    xc = 0.5 * (xs[:-1] + xs[1:])
+    rho2, u2, T2 = rankine_hugoniot(Ma)
+    prim = np.zeros((mesh.ni, 4))
+    up = xc < 0.0
+    prim[up] = [1.0, freestream_speed(Ma), 0.0, 1.0]
+    prim[~up] = [rho2, u2, 0.0, T2]
+    return prim
+
+
+@dataclass
+class Case:
+    name: str
+    mesh: Mesh
+    Kn: float
+    Ma: float
+    Tw: float
+    cfl: float
+    omega: float = 0.81
+    Pr: float = 1.0
+    n_ref: int = 100
+    seed: int = 0
+    ghost_state: tuple = (1.0, 0.0, 0.0, 1.0)   # (rho, U, V, T) used by BC_FIXED faces
+    init_prim: np.ndarray | None = None
+
+
+def case_shock1d(ni: int = 200, n_ref: int = 100, Ma: float = 3.0, Pr: float = 2.0 / 3.0) -> Case:
+    """1-D normal shock, Ma 3, 200 cells stretched 50x, x in [-30, 30] mean free paths (Kn = 1 on lambda)."""
+    m = line_mesh(ni, -30.0, 30.0, end_ratio=50.0, bc_left=BC_FARFIELD, bc_right=BC_FIXED)
+    rho2, u2, T2 = rankine_hugoniot(Ma)
+    c = Case("shock1d", m, Kn=1.0, Ma=Ma, Tw=1.0, cfl=0.5, omega=0.81, Pr=Pr, n_ref=n_ref,
+             ghost_state=(rho2, u2, 0.0, T2))
+    c.init_prim = shock_initial_field(m, Ma)
+    return c
+
+
+def case_cylinder(ni: int = 120, nj: int = 160, h1: float = 1e-3, r_out: float = 15.0, Kn: float = 0.1,
+                  Ma: float = 5.0, Tw: float = 1.0, n_ref: int = 100, cfl: float = 0.8) -> Case:
+    """Hypersonic cylinder (diameter 1) on a body-fitted O-mesh; Kn on the diameter."""
+    return Case(f"cylinder_{ni}x{nj}_Kn{Kn}_Ma{Ma}", omesh(ni, nj, h1, r_out), Kn=Kn, Ma=Ma, Tw=Tw, cfl=cfl,
+                n_ref=n_ref)
+
+
+def case_cylinder_kn01() -> Case:
+    return case_cylinder(120, 160, 1e-3, 15.0, Kn=0.1, Ma=5.0, n_ref=100)
+
+
+def case_cylinder_kn001() -> Case:
+    return case_cylinder(240, 320, 1e-4, 20.0, Kn=0.01, Ma=15.0, n_ref=150)
+
+
+def case_periodic_box(ni: int = 16, end_ratio: float = 50.0, n_ref: int = 50, Kn: float = 0.05,
+                      seed: int = 0) -> Case:
+    """Closed periodic 1-D box with cell sizes varying end_ratio times: a smooth density/temperature wave."""
+    m = line_mesh(ni, 0.0, 1.0, end_ratio=end_ratio, bc_left=BC_PERIODIC, bc_right=BC_PERIODIC)
+    xs = m.xv[: ni + 1]
+    xc = 0.5 * (xs[:-1] + xs[1:])
+    prim = np.zeros((ni, 4))
+    prim[:, 0] = 1.0 + 0.2 * np.sin(2 * np.pi * xc)
+    prim[:, 1] = 0.3 * np.cos(2 * np.pi * xc)
+    prim[:, 3] = 1.0 + 0.1 * np.cos(2 * np.pi * xc)
+    c = Case("periodic_box", m, Kn=Kn, Ma=0.0, Tw=1.0, cfl=0.5, n_ref=n_ref, seed=seed)
+    c.init_prim = prim
+    return c
