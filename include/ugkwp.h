@@ -1,0 +1,163 @@
+/* UGKWP-LTS steady-iteration step on one B300 GPU: C ABI of libugkwp.so.
+ *
+ * One step (ugkwp_step) runs, in hand-written sm_103a CUDA kernels on the context's stream:
+ *   decomposition W = W^h + W^p and the collisionless fraction e^{-dt_i/tau_i}    (Sec. 3.2, Sec. 4.2)
+ *   re-sampling of the hydrodynamic part as new particles                          (Eqs. 16-17, Sec. 4.2)
+ *   free-flight times t_f = min(-tau_i ln eps, dt_i)                                (Eq. 18, Sec. 4.2)
+ *   free transport; at every face crossing L -> R the particle mass and its remaining free-transport time
+ *     are multiplied by dt_R / dt_L                                                (Eqs. 19, 37, 45)
+ *   before/after particle tallies W^{fr,p} = W^{p,+} - W^{p,-}, removal of collided particles (Eqs. 20-21)
+ *   time-averaged equilibrium and free-transport wave fluxes with side-normalised coefficients
+ *                                                                                   (Eqs. 14, 26-31, 40-43)
+ *   the conservative update W^{n+1} = W^n - dt_i/Omega_i sum_j F_j s_j + W^{fr,p}  (Eq. 46)
+ *   wall pressure, shear stress and heat flux                                       (Sec. 5.1)
+ * Local time steps come from the CFL condition on the initial freestream field and stay fixed (Eqs. 24-25);
+ * GTS mode gives every cell the global minimum.
+ *
+ * Conventions.
+ *  - Every function returns ugkwp_status (0 = OK). ugkwp_last_error gives a message for the last failure.
+ *  - The context owns all device memory. Host pointers passed in are owned by the caller and only read or
+ *    written during the call.
+ *  - ugkwp_step is asynchronous on the context's stream; calls that return host data synchronise it and
+ *    report any sticky device-side error (crossing cap, non-physical state, tally overflow). After such an
+ *    error the context can only be inspected or destroyed.
+ *  - A context is not thread-safe. Units: rho_inf = T_inf = 1, R = 1/2, lengths in the mesh's units.
+ *  - Particle order inside a cell after a step is unspecified; the particle set, all integer tallies and
+ *    all cell states are deterministic for a given seed.
+ */
+#ifndef UGKWP_H
+#define UGKWP_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ugkwp_ctx ugkwp_ctx;
+
+typedef enum {
+    UGKWP_OK = 0,
+    UGKWP_EINVAL = 1,     /* bad argument or mesh */
+    UGKWP_ENOMEM = 2,     /* device allocation failed */
+    UGKWP_ECUDA = 3,      /* CUDA runtime error */
+    UGKWP_ELIMIT = 4,     /* crossing cap (256 per particle per step), particle capacity, > 2047 new / cell */
+    UGKWP_ENONPHYS = 5,   /* a non-finite cell state after the update */
+    UGKWP_EOVERFLOW = 6   /* a fixed-point tally contribution beyond 2^62 */
+} ugkwp_status;
+
+typedef enum { UGKWP_LTS = 0, UGKWP_GTS = 1 } ugkwp_tstep;
+
+/* boundary tags of the mesh's boundary faces */
+enum { UGKWP_BC_WALL = 1,      /* diffuse isothermal wall at T_w */
+       UGKWP_BC_FARFIELD = 2,  /* freestream ghost on inflow, zero-gradient ghost on outflow; particles leave */
+       UGKWP_BC_FIXED = 3,     /* ghost at opts.ghost_state; particles leave */
+       UGKWP_BC_SYMMETRY = 4,  /* specular mirror */
+       UGKWP_BC_PERIODIC = 5   /* 1-D only: both ends of the line, joined */ };
+
+/* Structured mesh of ni x nj cells (cell (i, j) -> index i + ni j). Vertex (i, j) is at index
+ * i + (ni + 1) j of xv/yv ((ni+1)(nj+1) entries). dim = 1: a line of ni cells (nj = 1); only xv[0..ni]
+ * is read and cells are unbounded in y. dim = 2: quadrilaterals (v(i,j), v(i+1,j), v(i+1,j+1), v(i,j+1))
+ * counter-clockwise; periodic_j joins row nj to row 0 (O-mesh). Boundary tags: bc_imin/bc_imax have nj
+ * entries, bc_jmin/bc_jmax ni entries (ignored when periodic_j or dim = 1). At most 2^21 - 1 cells. */
+typedef struct {
+    int32_t ni, nj, dim, periodic_j;
+    const double* xv;
+    const double* yv;
+    const int32_t* bc_imin;
+    const int32_t* bc_imax;
+    const int32_t* bc_jmin;
+    const int32_t* bc_jmax;
+} ugkwp_mesh;
+
+/* VHS exponent (mu ~ T^omega) and Prandtl number (Prandtl fix of the wave slopes; 1 = BGK) */
+typedef struct { double omega, Pr; } ugkwp_gas;
+
+typedef struct {
+    uint64_t seed;            /* Philox key (low word xor case_id, high word) */
+    uint32_t case_id;
+    int32_t n_ref;            /* reference particles per cell, N_ref of Eq. 17 */
+    int32_t precision;        /* 0: FP32 particles, FP32 interior wave fluxes, FP64 cell update and wall
+                                 fluxes; 1: everything FP64 */
+    int32_t wave_only;        /* 1: no particles (GKS limit, deterministic) */
+    int32_t record_faces;     /* reserved (0) */
+    int32_t capacity;         /* particle capacity; 0 = 4 n_ref cells */
+    double ghost_state[4];    /* (rho, U, V, T) of UGKWP_BC_FIXED ghosts */
+    void* stream;             /* cudaStream_t to run on (NULL: the legacy default stream) */
+    int32_t use_graph;        /* 1: capture one step into a CUDA graph on the first ugkwp_step, replay it */
+    int32_t reserved;
+} ugkwp_opts;
+
+/* Build the context: geometry, fixed local time steps (Eqs. 24-25), uniform freestream state, no
+ * particles. Kn is the freestream mean free path over the mesh's length unit (VHS); Ma the freestream
+ * Mach number along +x; Tw the wall temperature over T_inf; cfl the CFL number N_CFL of Eq. 24. */
+ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double Kn, double Ma, double Tw,
+                          double cfl, ugkwp_tstep mode, const ugkwp_opts* opts, ugkwp_ctx** out);
+void ugkwp_destroy(ugkwp_ctx* ctx);
+
+/* Advance n_steps steps (asynchronous). */
+ugkwp_status ugkwp_step(ugkwp_ctx* ctx, int32_t n_steps);
+
+/* out[0..3]: residual of the last step per conservative component, normalised by the first step's;
+ * out[4..7]: raw, sqrt(sum_i Omega_i ((W^{n+1} - W^n) / dt_i)^2). Synchronises. */
+ugkwp_status ugkwp_residual(ugkwp_ctx* ctx, double* out);
+
+/* Wall pressure, shear stress (along t = (-n_y, n_x), n the outward normal of the fluid cell) and heat
+ * flux into the wall on each of n_wall wall faces (in face order), either of the last step (averaged = 0)
+ * or averaged over all steps since the last reset (averaged = 1). Synchronises. */
+ugkwp_status ugkwp_surface(ugkwp_ctx* ctx, double* p, double* tau_w, double* q, int32_t n_wall,
+                           int32_t averaged);
+ugkwp_status ugkwp_reset_surface(ugkwp_ctx* ctx);
+
+/* Set the cell state from host primitives (rho, U, V, T) per cell (4 C doubles); removes all particles
+ * (W^p = 0). The local time steps are unchanged. */
+ugkwp_status ugkwp_set_field(ugkwp_ctx* ctx, const double* prim);
+/* W (4 C doubles: rho, rho U, rho V, rho E) and, if Wp != NULL, W^p of the retained particles. */
+ugkwp_status ugkwp_get_field(ugkwp_ctx* ctx, double* W, double* Wp);
+
+/* out[11]: steps taken, particles, new in the last step, removed (collided), left the domain, face
+ * crossings, wall hits, largest crossings + hits of one particle in the last step; then, cumulative since
+ * creation, particle-steps processed (retained + new particles of every step) and new particles; then the
+ * cells reset to the vacuum floor in the last step: a cell state outside the realizable set (density
+ * above 1e-12, 0.01 min(1, T_w, T_fixed) <= T <= T_cap = 10 max(1 + Ma^2/3, T_w, T_fixed),
+ * |U| <= U_inf + 10 sqrt(R T_cap)) restarts from rho = 1e-12 at rest at T_inf; a hydrodynamic part W^h
+ * outside that set is not sampled and has no free-transport wave flux. */
+ugkwp_status ugkwp_stats(ugkwp_ctx* ctx, int64_t* out);
+int64_t ugkwp_num_particles(ugkwp_ctx* ctx);
+
+/* Particle snapshot to host arrays of length >= cap (values widened to double in FP32 mode). */
+ugkwp_status ugkwp_get_particles(ugkwp_ctx* ctx, int64_t cap, uint64_t* pid, int32_t* cell, double* x,
+                                 double* y, double* u, double* v, double* w, double* m);
+/* Replace the whole state: step counter, W (4 C), the retained tally of the previous step (5 C int64,
+ * fixed point, see ugkwp_fixed_exponents), and np particles (values must be FP32-representable in FP32
+ * mode). */
+ugkwp_status ugkwp_set_state(ugkwp_ctx* ctx, int64_t step, const double* W, const int64_t* wret, int64_t np,
+                             const uint64_t* pid, const int32_t* cell, const double* x, const double* y,
+                             const double* u, const double* v, const double* w, const double* m);
+/* Integer tallies of the last step (any pointer may be NULL): W^{p,-} and W^{p,+} and the retained part
+ * (5 C each: sum of m, m u, m v, m w, m |u|^2/2 in fixed point), face crossings (2 F: L->R, R->L),
+ * wall momentum/energy transfer (3 per wall face). frec is reserved (NULL). */
+ugkwp_status ugkwp_get_tallies(ugkwp_ctx* ctx, int64_t* wm, int64_t* wpl, int64_t* wret, int64_t* cross,
+                               int64_t* wall, int64_t* frec);
+/* Per cell (8 C doubles) of the last decomposition: tau, dt/tau, e^{-dt/tau}, N^hp, new-particle mass,
+ * U^h, V^h, R T^h. */
+ugkwp_status ugkwp_get_cell_data(ugkwp_ctx* ctx, double* out);
+/* Time-averaged wave flux of the last step per face (4 F doubles, global frame, along the face normal). */
+ugkwp_status ugkwp_get_flux(ugkwp_ctx* ctx, double* flux);
+/* Local time steps and cell areas (C doubles each, nullable), face and wall-face counts (nullable). */
+ugkwp_status ugkwp_get_geometry(ugkwp_ctx* ctx, double* dt, double* vol, int32_t* nfaces, int32_t* nwall);
+/* Fixed-point exponents F of the mass, momentum and energy tallies: value = integer * 2^-F. */
+ugkwp_status ugkwp_fixed_exponents(ugkwp_ctx* ctx, int32_t* out);
+/* Per-stage device timing with CUDA events recorded on the context's stream around each stage of every
+ * step taken while enabled (graph replay is bypassed meanwhile). ugkwp_profile synchronises, returns the
+ * summed milliseconds of the 6 stages (ms[0..5]: decomposition + slot scan, new-particle sampling,
+ * particle transport, tallies and compaction, wave fluxes, the periodic counting sort of the particles by
+ * cell, conservative update + surface quantities + step bookkeeping) and the number of profiled steps, and
+ * clears the record (ms needs room for 8 values). */
+ugkwp_status ugkwp_set_profiling(ugkwp_ctx* ctx, int32_t enable);
+ugkwp_status ugkwp_profile(ugkwp_ctx* ctx, double* ms, int64_t* steps);
+const char* ugkwp_last_error(const ugkwp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

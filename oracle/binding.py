@@ -167,7 +167,8 @@ class Oracle:
         return p, t, q
 
     def stats(self):
-        out = np.zeros(8, dtype=np.int64)
+        """[steps, particles, new, removed, left, crossings, wall hits, max iterations, floored cells]"""
+        out = np.zeros(9, dtype=np.int64)
         lib().oracle_stats(self.ctx, _p(out, C.c_int64))
         return out
 

@@ -231,7 +231,12 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
     psi_mom(mL.up, &mL, 0, 0, 0, t1);
     psi_mom(mR.um, &mR, 0, 0, 0, t2);
     for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];      /* Eq. 26 */
-    frame_prim(W0, &p0);
+    for (int k = 0; k < 4; ++k) F[k] = 0.0;
+    if (!frame_prim(W0, &p0)) {
+        /* vacuum interface (reading): no molecule of either side reaches the face (the half-range masses
+         * underflow), so there is no equilibrium state and no equilibrium flux */
+        goto free_transport;
+    }
     moments(&p0, &m0);
     double dwL[4], dwR[4], aL[4], aR[4], dA[4], A[4];
     for (int k = 0; k < 4; ++k) {
@@ -256,6 +261,11 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
     for (int k = 0; k < 4; ++k)
         F[k] = p0.rho * (cL[0] * fa_p[k] + cL[1] * fb_p[k] + cL[2] * fc_p[k]
                          + cR[0] * fa_m[k] + cR[1] * fb_m[k] + cR[2] * fc_m[k]);
+    if (W0o) for (int k = 0; k < 4; ++k) W0o[k] = W0[k];
+    if (aLo) for (int k = 0; k < 4; ++k) aLo[k] = aL[k];
+    if (aRo) for (int k = 0; k < 4; ++k) aRo[k] = aR[k];
+    if (Ao) for (int k = 0; k < 4; ++k) Ao[k] = A[k];
+free_transport:
     if (hL && frame_prim(WhL, &phL)) {
         moments(&phL, &mhL);
         psi_mom(mhL.up, &mhL, 1, 0, 0, t1);
@@ -266,10 +276,6 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
         psi_mom(mhR.um, &mhR, 1, 0, 0, t2);
         for (int k = 0; k < 4; ++k) F[k] += frR * phR.rho * t2[k];
     }
-    if (W0o) for (int k = 0; k < 4; ++k) W0o[k] = W0[k];
-    if (aLo) for (int k = 0; k < 4; ++k) aLo[k] = aL[k];
-    if (aRo) for (int k = 0; k < 4; ++k) aRo[k] = aR[k];
-    if (Ao) for (int k = 0; k < 4; ++k) Ao[k] = A[k];
 }
 
 void oracle_face_flux_test(const double* WL, const double* WR, const double* WhL, const double* WhR,
@@ -564,6 +570,17 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     cx->dt = zalloc(C, 8); cx->ratio = zalloc(4 * C, 8);
     init_time_steps(cx);
     fixed_exponents(cx, opts->ghost_state[3]);
+    {
+        double Tc = 1.0 + Ma * Ma / 3.0;
+        if (Tw > Tc) Tc = Tw;
+        if (opts->ghost_state[3] > Tc) Tc = opts->ghost_state[3];
+        cx->T_cap = 10.0 * Tc;
+        double Tm = 1.0;
+        if (Tw < Tm) Tm = Tw;
+        if (opts->ghost_state[3] > 0.0 && opts->ghost_state[3] < Tm) Tm = opts->ghost_state[3];
+        cx->T_min = 0.01 * Tm;
+        cx->U_cap = cx->U_inf + 10.0 * sqrt(OR_R * cx->T_cap);
+    }
     cx->W = zalloc(4 * C, 8); cx->wret_prev = zalloc(5 * C, 8);
     cx->tau = zalloc(C, 8); cx->xr_t = zalloc(C, 8); cx->emx = zalloc(C, 8);
     cx->Wp = zalloc(4 * C, 8); cx->Wh = zalloc(4 * C, 8); cx->mnew = zalloc(C, 8); cx->co = zalloc(7 * C, 8);
@@ -596,6 +613,21 @@ void oracle_destroy(oracle_ctx* cx)
     free(cx);
 }
 
+/* Realizability of a cell state (reading): density above the vacuum floor, temperature between
+ * T_min = 0.01 min(1, T_w, T_fix) and T_cap = 10 max(T_0, T_w, T_fix) with T_0 = 1 + Ma^2 / 3 the
+ * freestream stagnation temperature, speed at most U_inf + 10 sqrt(R T_cap). States outside arise only
+ * from statistical noise in cells that have (nearly) no gas. */
+static int realizable(const or_ctx* cx, const double W[4])
+{
+    if (!(W[0] > OR_RHO_FLOOR)) return 0;
+    const double U = W[1] / W[0], V = W[2] / W[0];
+    const double q = U * U + V * V;
+    const double e = W[3] / W[0] - 0.5 * q;
+    if (!(e > 0.0)) return 0;
+    const double T = (e * (2.0 / 3.0)) / OR_R;
+    return T >= cx->T_min && T <= cx->T_cap && q <= cx->U_cap * cx->U_cap;
+}
+
 /* ------------------------------------------------------------------ a1: decomposition (Sec. 4.2) */
 
 static void decompose(or_ctx* cx)
@@ -619,7 +651,7 @@ static void decompose(or_ctx* cx)
         cx->xr_t[c] = x;
         cx->emx[c] = e;
         lts_coeffs(cx->dt[c], tau, e, cx->co + 7 * c);
-        cx->hphys[c] = Wh[0] > 0.0 && (Wh[3] - 0.5 * (Wh[1] * Wh[1] + Wh[2] * Wh[2]) / Wh[0]) > 0.0;
+        cx->hphys[c] = realizable(cx, Wh);
         cx->nhp[c] = 0;
         cx->mnew[c] = 0.0;
         cx->samp[3 * c] = cx->samp[3 * c + 1] = cx->samp[3 * c + 2] = 0.0;
@@ -720,14 +752,19 @@ static void update(or_ctx* cx)
             Wn[q] = (W[q] - coef * acc[q]) + ((double)d * sc[q]) / cx->vol[c];
         }
         if (cx->dim == 1) Wn[2] = 0.0;
+        if (!isfinite(Wn[0]) || !isfinite(Wn[1]) || !isfinite(Wn[2]) || !isfinite(Wn[3]))
+            or_set_error(cx, OR_ENONPHYS, "non-finite cell state after the update");
+        /* vacuum floor (reading): a cell emptied of particles whose small wave remainder the outflow drove
+         * out of the realizable set restarts from a near-vacuum state at rest at T_inf */
+        if (!realizable(cx, Wn)) {
+            Wn[0] = OR_RHO_FLOOR; Wn[1] = 0.0; Wn[2] = 0.0; Wn[3] = OR_RHO_FLOOR * (1.5 * OR_R);
+            cx->stats[8] += 1;
+        }
         for (int q = 0; q < 4; ++q) {
             const double r = (Wn[q] - W[q]) / cx->dt[c];
             rs[q] += cx->vol[c] * (r * r);
             W[q] = Wn[q];
         }
-        const double e = W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0];
-        if (!(W[0] > 0.0) || !(e > 0.0) || !isfinite(W[3]))
-            or_set_error(cx, OR_ENONPHYS, "non-physical cell state after the update");
         const double chi = (((double)cx->wpl[5 * c] * sc[0]) / cx->vol[c]) / W[0];
         cx->chi_ema[c] = cx->step == 0 ? chi : cx->chi_ema[c] + alpha * (chi - cx->chi_ema[c]);
     }
@@ -770,7 +807,7 @@ static int one_step(or_ctx* cx)
     memset(cx->wrt, 0, 5 * (size_t)C * 8);
     memset(cx->cross, 0, 2 * (size_t)cx->F * 8);
     memset(cx->wallt, 0, 3 * (size_t)cx->nwall * 8);
-    for (int k = 2; k < 8; ++k) cx->stats[k] = 0;
+    for (int k = 2; k < 9; ++k) cx->stats[k] = 0;
     /* step 1: decomposition and sampling; step 2: free transport and tallies (Sec. 3.3, Sec. 4.2) */
     decompose(cx);
     if (cx->err) return cx->err;

@@ -12,6 +12,7 @@ enum { OR_BC_WALL = 1, OR_BC_FARFIELD = 2, OR_BC_FIXED = 3, OR_BC_SYMMETRY = 4, 
 #define OR_R 0.5                 /* gas constant in the reference units (2 R T_inf = 1) */
 #define OR_MAX_ITERS 256         /* face crossings + wall hits per particle per step */
 #define OR_MAX_NEW 2047          /* new particles per cell per step (11-bit index in the id) */
+#define OR_RHO_FLOOR 1e-12       /* vacuum floor of the cell density (units of rho_inf) */
 
 
 typedef struct {
@@ -33,6 +34,7 @@ struct oracle_ctx {
     double Kn, Ma, Tw, cfl, omega, Pr, mu_inf, U_inf;
     double W_inf[4], W_fix[4];
     int fx[3];                                   /* fixed-point exponents: mass, momentum, energy */
+    double T_cap, U_cap, T_min;                  /* realizability bounds of a cell state */
     /* cells */
     double *vol, *inv_vol, *xc, *yc;
     int *nfc;
@@ -70,7 +72,7 @@ struct oracle_ctx {
     double* chi_ema;
     double *surf_sum, *surf_last;
     int64_t nsurf;
-    int64_t stats[8];
+    int64_t stats[9];                            /* [8]: cells set to the vacuum floor in the last step */
     int err;
     char msg[256];
 };

@@ -1,0 +1,1666 @@
+// UGKWP-LTS steady-iteration step on one GPU: set-up, cell, particle and bookkeeping kernels and the C ABI.
+//
+// Compiled with -fmad=false: every floating-point operation on the particle path and in the cell
+// decomposition is an individually rounded IEEE operation, in the order written, so that integer outcomes
+// (cell indices, new-particle counts, fixed-point tallies) are reproducible bit for bit.
+//
+// Per step, on the context stream (all sizes device-resident, so one step can be captured in a graph):
+//   k_begin_step       zero the step's crossing, wall and counter tallies; sort-step flag
+//   k_decompose   a1   per cell: tau, W^p from the retained tally, W^h, e^{-dt/tau}, N^hp, coefficients
+//   scan(N^hp)         new-particle slots (and the capacity check)
+//   k_sample      a2   warp per cell: new particles appended after the retained ones, their W^{p,-}
+//   k_particles   a3-a7 per particle: t_f, transport with dt_R/dt_L scaling, W^{p,+}, retained tally, removal
+//                      (survivors compacted into the other particle buffer)
+//   k_wave_flux   a9   per face (ugkwp_flux.cu): FP32 interior faces, FP64 wall/boundary faces
+//   scan + k_scatter   every sort_every-th step: counting sort of the survivors by cell
+//   k_update      a10, a11  per cell: Eq. 46, residual, particle-mass-ratio EMA; per wall face: p, tau_w, q;
+//                      the last block closes the step
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "ugkwp_internal.h"
+#include "ugkwp_detmath.cuh"
+
+namespace ugk {
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kMaxCells = 1 << 20;
+
+// ------------------------------------------------------------------------------------------ scan
+__device__ __forceinline__ int block_excl_scan(int v, int* total)
+{
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int before = wid > 0 ? warp_sums[wid - 1] : 0;
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_blocks(const int* in, int* out, int* tmp, int n, const int* active)
+{
+    if (active && !*active) return;
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    int tot;
+    const int e = block_excl_scan(i < n ? in[i] : 0, &tot);
+    if (i < n) out[i] = e;
+    if (threadIdx.x == 0) tmp[blockIdx.x] = tot;
+}
+
+// exclusive scan of the block totals (one block); out[n] and *total receive the grand total. With `cap`,
+// the total is the number of new particles of the step: if the retained ones (cap[0]) plus them exceed the
+// capacity (cap[3]) the error is flagged and none are sampled (the wave keeps that mass), so every slot the
+// later kernels touch holds a valid particle; cap[4] receives the particles processed this step.
+__global__ void k_scan_tops(int* tmp, int nb, int* out, int n, int* total, int* cap, int* err, const int* active)
+{
+    if (active && !*active) return;
+    int tot;
+    const int v = threadIdx.x < nb ? tmp[threadIdx.x] : 0;
+    const int e = block_excl_scan(v, &tot);
+    if (threadIdx.x < nb) tmp[threadIdx.x] = e;
+    if (threadIdx.x == 0) {
+        out[n] = tot;
+        if (cap) {
+            if ((long long)cap[0] + tot > (long long)cap[3]) {
+                atomicOr(err, ERR_CAPACITY);
+                tot = 0;
+            }
+            cap[4] = cap[0] + tot;
+        }
+        if (total) *total = tot;
+    }
+}
+
+__global__ void k_scan_add(int* out, const int* tmp, int n, const int* active)
+{
+    if (active && !*active) return;
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < n) out[i] += tmp[blockIdx.x];
+}
+
+// exclusive scan of n ints (n <= 2^20); `active` (nullable) skips it when *active == 0
+void exclusive_scan(const int* in, int* out, int* tmp, int n, int* total, cudaStream_t s, int* cap = nullptr,
+                    int* err = nullptr, const int* active = nullptr)
+{
+    const int nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_blocks<<<nb, kScanBlock, 0, s>>>(in, out, tmp, n, active);
+    k_scan_tops<<<1, kScanBlock, 0, s>>>(tmp, nb, out, n, total, cap, err, active);
+    k_scan_add<<<nb, kScanBlock, 0, s>>>(out, tmp, n, active);
+}
+
+// ------------------------------------------------------------------------------ set-up (a0)
+struct MeshDev {
+    int ni, nj, dim, periodic_j, periodic_i, F;
+    const double *xv, *yv;
+    const int *bc_imin, *bc_imax, *bc_jmin, *bc_jmax;
+};
+
+__device__ __forceinline__ int vid(const MeshDev& m, int i, int j)
+{
+    return i + (m.ni + 1) * ((m.periodic_j && j == m.nj) ? 0 : j);
+}
+
+// one face: cells on each side (L always a fluid cell; n from L to R, outward from L on a boundary),
+// boundary tag, unit normal, length, plane offset n.x = d
+__global__ void k_setup_faces(const MeshDev m, Dev d, double* fd)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= m.F) return;
+    const int ni = m.ni, nj = m.nj;
+    if (m.dim == 1) {
+        const double* xs = m.xv;
+        d.fnx[f] = 1.0; d.fny[f] = 0.0; d.fs[f] = 1.0;
+        if (f == 0 && m.periodic_i) { d.fL[f] = ni - 1; d.fR[f] = 0; d.fbc[f] = UGKWP_BC_PERIODIC; fd[f] = xs[0]; }
+        else if (f == 0) { d.fL[f] = 0; d.fR[f] = -1; d.fbc[f] = m.bc_imin[0]; d.fnx[f] = -1.0; fd[f] = -xs[0]; }
+        else if (f == ni) { d.fL[f] = ni - 1; d.fR[f] = -1; d.fbc[f] = m.bc_imax[0]; fd[f] = xs[ni]; }
+        else { d.fL[f] = f - 1; d.fR[f] = f; d.fbc[f] = 0; fd[f] = xs[f]; }
+        return;
+    }
+    const int nif = (ni + 1) * nj;
+    double nx, ny, len;
+    int a;
+    if (f < nif) {
+        const int i = f % (ni + 1), j = f / (ni + 1);
+        a = vid(m, i, j);
+        const int b = vid(m, i, j + 1);
+        const double ex = m.xv[b] - m.xv[a], ey = m.yv[b] - m.yv[a];
+        len = sqrt(ex * ex + ey * ey);
+        nx = ey / len; ny = -ex / len;
+        if (i == 0) { nx = -nx; ny = -ny; d.fL[f] = i + ni * j; d.fR[f] = -1; d.fbc[f] = m.bc_imin[j]; }
+        else if (i == ni) { d.fL[f] = (i - 1) + ni * j; d.fR[f] = -1; d.fbc[f] = m.bc_imax[j]; }
+        else { d.fL[f] = (i - 1) + ni * j; d.fR[f] = i + ni * j; d.fbc[f] = 0; }
+    } else {
+        const int g = f - nif, i = g % ni, j = g / ni;
+        a = vid(m, i, j);
+        const int b = vid(m, i + 1, j);
+        const double ex = m.xv[b] - m.xv[a], ey = m.yv[b] - m.yv[a];
+        len = sqrt(ex * ex + ey * ey);
+        nx = -ey / len; ny = ex / len;
+        if (m.periodic_j) { d.fL[f] = i + ni * ((j + nj - 1) % nj); d.fR[f] = i + ni * j; d.fbc[f] = 0; }
+        else if (j == 0) { nx = -nx; ny = -ny; d.fL[f] = i; d.fR[f] = -1; d.fbc[f] = m.bc_jmin[i]; }
+        else if (j == nj) { d.fL[f] = i + ni * (nj - 1); d.fR[f] = -1; d.fbc[f] = m.bc_jmax[i]; }
+        else { d.fL[f] = i + ni * (j - 1); d.fR[f] = i + ni * j; d.fbc[f] = 0; }
+    }
+    d.fs[f] = len;
+    d.fnx[f] = nx; d.fny[f] = ny;
+    fd[f] = nx * m.xv[a] + ny * m.yv[a];
+}
+
+// one cell: area, centroid, vertices, local faces (-i, +i, -j, +j) with outward normals and planes
+__global__ void k_setup_cells(const MeshDev m, Dev d, const double* fd, int* cface, int* csgn, int* cnbr, int* cnk,
+                              int* cbc, double* cnx, double* cny, double* cd)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ni = m.ni, nj = m.nj;
+    if (c >= ni * nj) return;
+    if (m.dim == 1) {
+        const double* xs = m.xv;
+        const int i = c;
+        d.vol[c] = xs[i + 1] - xs[i];
+        d.xc[c] = 0.5 * (xs[i] + xs[i + 1]);
+        d.yc[c] = 0.0;
+        d.cvx[4 * c] = xs[i]; d.cvx[4 * c + 1] = xs[i + 1];
+        d.nfc[c] = 2;
+        const int q0 = 4 * c, q1 = 4 * c + 1;
+        cface[q0] = (i == 0 && m.periodic_i) ? 0 : i;
+        cface[q1] = (i == ni - 1 && m.periodic_i) ? 0 : i + 1;
+        cnx[q0] = -1.0; cny[q0] = 0.0; cd[q0] = -xs[i];
+        cnx[q1] = 1.0; cny[q1] = 0.0; cd[q1] = xs[i + 1];
+        d.cshift[q0] = 0.0; d.cshift[q1] = 0.0;
+        if (i > 0) { cnbr[q0] = i - 1; cnk[q0] = 1; csgn[q0] = -1; cbc[q0] = 0; }
+        else if (m.periodic_i) { cnbr[q0] = ni - 1; cnk[q0] = 1; csgn[q0] = -1; cbc[q0] = UGKWP_BC_PERIODIC; d.cshift[q0] = xs[ni] - xs[0]; }
+        else { cnbr[q0] = -1; cnk[q0] = 0; csgn[q0] = 1; cbc[q0] = m.bc_imin[0]; }
+        if (i < ni - 1) { cnbr[q1] = i + 1; cnk[q1] = 0; csgn[q1] = 1; cbc[q1] = 0; }
+        else if (m.periodic_i) { cnbr[q1] = 0; cnk[q1] = 0; csgn[q1] = 1; cbc[q1] = UGKWP_BC_PERIODIC; d.cshift[q1] = xs[0] - xs[ni]; }
+        else { cnbr[q1] = -1; cnk[q1] = 0; csgn[q1] = 1; cbc[q1] = m.bc_imax[0]; }
+        for (int k = 2; k < 4; ++k) { cface[4 * c + k] = 0; cnbr[4 * c + k] = -1; cnx[4 * c + k] = 0; cny[4 * c + k] = 0; cd[4 * c + k] = 0; cnk[4 * c + k] = 0; csgn[4 * c + k] = 1; cbc[4 * c + k] = 0; d.cshift[4 * c + k] = 0; }
+        return;
+    }
+    const int i = c % ni, j = c / ni;
+    const int v[4] = {vid(m, i, j), vid(m, i + 1, j), vid(m, i + 1, j + 1), vid(m, i, j + 1)};
+    double X[4], Y[4];
+    for (int q = 0; q < 4; ++q) {
+        X[q] = m.xv[v[q]]; Y[q] = m.yv[v[q]];
+        d.cvx[4 * c + q] = X[q]; d.cvy[4 * c + q] = Y[q];
+    }
+    d.vol[c] = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[1]) - (X[3] - X[1]) * (Y[2] - Y[0]));
+    const double A1 = 0.5 * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+    const double A2 = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+    d.xc[c] = (A1 * (X[0] + X[1] + X[2]) + A2 * (X[0] + X[2] + X[3])) / (3.0 * (A1 + A2));
+    d.yc[c] = (A1 * (Y[0] + Y[1] + Y[2]) + A2 * (Y[0] + Y[2] + Y[3])) / (3.0 * (A1 + A2));
+    d.nfc[c] = 4;
+    const int nif = (ni + 1) * nj;
+    const int jp = (m.periodic_j && j + 1 == nj) ? 0 : j + 1;
+    const int fq[4] = {i + (ni + 1) * j, (i + 1) + (ni + 1) * j, nif + i + ni * j, nif + i + ni * jp};
+    for (int k = 0; k < 4; ++k) {
+        const int f = fq[k], q = 4 * c + k;
+        const bool isL = d.fL[f] == c;
+        cface[q] = f;
+        csgn[q] = isL ? 1 : -1;
+        cnx[q] = isL ? d.fnx[f] : -d.fnx[f];
+        cny[q] = isL ? d.fny[f] : -d.fny[f];
+        cd[q] = isL ? fd[f] : -fd[f];
+        d.cshift[q] = 0.0;
+        if (d.fR[f] < 0) { cnbr[q] = -1; cnk[q] = 0; cbc[q] = d.fbc[f]; }
+        else { cnbr[q] = isL ? d.fR[f] : d.fL[f]; cnk[q] = k ^ 1; cbc[q] = 0; }
+    }
+}
+
+__global__ void k_setup_face_dist(const MeshDev m, Dev d, const double* fd)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= m.F) return;
+    const int L = d.fL[f], R = d.fR[f];
+    if (m.dim == 1) {
+        const double* xs = m.xv;
+        if (d.fbc[f] == UGKWP_BC_PERIODIC) { d.fdL[f] = xs[m.ni] - d.xc[m.ni - 1]; d.fdR[f] = d.xc[0] - xs[0]; }
+        else if (R < 0) { d.fdL[f] = d.fdR[f] = (f == 0) ? d.xc[0] - xs[0] : xs[m.ni] - d.xc[m.ni - 1]; }
+        else { d.fdL[f] = xs[f] - d.xc[L]; d.fdR[f] = d.xc[R] - xs[f]; }
+        return;
+    }
+    d.fdL[f] = fd[f] - (d.fnx[f] * d.xc[L] + d.fny[f] * d.yc[L]);
+    d.fdR[f] = R >= 0 ? (d.fnx[f] * d.xc[R] + d.fny[f] * d.yc[R]) - fd[f] : d.fdL[f];
+}
+
+// Eq. 24 on the freestream field: dt_i = N_CFL Omega_i / ((|U_inf| + 3 sqrt(R T_inf)) sum_j s_j)
+__global__ void k_setup_dt(Dev d, int C, const int* cface, double cfl, double cs, double* dtmin_part)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 1e300;
+    if (c < C) {
+        double perim = 0.0;
+        for (int k = 0; k < d.nfc[c]; ++k) perim += d.fs[cface[4 * c + k]];
+        const double dt = (cfl * d.vol[c]) / (cs * perim);
+        d.dt[c] = dt;
+        v = dt;
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __shared__ double sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = sm[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmin(b, sm[w]);
+        dtmin_part[blockIdx.x] = b;
+    }
+}
+
+// Eq. 25: dt_G = min dt_i, given to every cell under GTS
+__global__ void k_setup_gts(Dev d, int C, const double* dtmin_part, int nb)
+{
+    double g = dtmin_part[0];
+    for (int b = 1; b < nb; ++b) g = fmin(g, dtmin_part[b]);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) d.dt[c] = g;
+}
+
+__global__ void k_setup_tables(Dev d, int C, const int* cface, const int* csgn, const int* cnbr, const int* cnk,
+                               const int* cbc, const double* cnx, const double* cny, const double* cd, int prod)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    CellFaces<float> a;
+    CellFaces<double> b;
+    for (int k = 0; k < 4; ++k) {
+        const int q = 4 * c + k;
+        const int nb = (k < d.nfc[c]) ? cnbr[q] : -1;
+        const double r = nb >= 0 ? d.dt[nb] / d.dt[c] : 1.0;
+        const int meta = (cface[q] & 0xffffff) | ((cnk[q] & 3) << 24) | ((cbc[q] & 7) << 26) | ((csgn[q] > 0 ? 1 : 0) << 29);
+        b.nx[k] = cnx[q]; b.ny[k] = cny[q]; b.d[k] = cd[q]; b.ratio[k] = r; b.nbr[k] = nb; b.meta[k] = meta;
+        a.nx[k] = (float)cnx[q]; a.ny[k] = (float)cny[q]; a.d[k] = (float)cd[q]; a.ratio[k] = (float)r;
+        a.nbr[k] = nb; a.meta[k] = meta;
+    }
+    d.cf32[c] = a;
+    d.cf64[c] = b;
+    // faces next to a wall cell are evaluated in FP64 in production mode
+    for (int k = 0; k < d.nfc[c]; ++k)
+        if (cbc[4 * c + k] == UGKWP_BC_WALL)
+            for (int q = 0; q < d.nfc[c]; ++q) d.face_f64[cface[4 * c + q]] = 1;
+    (void)prod;
+}
+
+__global__ void k_wall_flags(const Dev d, int F, int* flag)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < F) flag[f] = d.fbc[f] == UGKWP_BC_WALL ? 1 : 0;
+}
+
+__global__ void k_wall_index(Dev d, int F, const int* idx)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    if (d.fbc[f] == UGKWP_BC_WALL) { d.fwall[f] = idx[f]; d.wall_face[idx[f]] = f; }
+    else d.fwall[f] = -1;
+}
+
+// Realizable cell state: density above the vacuum floor, temperature in [T_min, T_cap] and speed at most
+// U_cap (bounds fixed at creation from the freestream stagnation temperature, T_w and the fixed ghost
+// temperature). Outside it the state is noise of a cell with (nearly) no gas.
+__device__ __forceinline__ bool realizable(const StepConsts& K, const double* W)
+{
+    if (!(W[0] > kRhoFloor)) return false;
+    const double U = W[1] / W[0], V = W[2] / W[0];
+    const double q = U * U + V * V;
+    const double e = W[3] / W[0] - 0.5 * q;
+    if (!(e > 0.0)) return false;
+    const double T = (e * (2.0 / 3.0)) / kR;
+    return T >= K.T_min && T <= K.T_cap && q <= K.U_cap * K.U_cap;
+}
+
+// ------------------------------------------------------------------ a1: decomposition (Sec. 4.2)
+__device__ __forceinline__ double tau_of(const StepConsts& K, const double* W)
+{
+    const double rho = W[0], U = W[1] / rho, V = W[2] / rho;
+    const double RT = (W[3] / rho - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+    const double T = RT / kR;
+    const double mu = K.mu_inf * dpow(T, K.omega);
+    return mu / (rho * RT);
+}
+
+// Taylor weights of the six entire functions behind the normalised coefficients, k = 0..19:
+// 1/(k+1)!, 1/(k+2)!, 1/(k+3)!, (k+1)/(k+2)!, (k+1)/(k+3)!, (k+1)(k+2)/(2 (k+3)!)
+constexpr int kSeries = 20;
+__constant__ double c_series[6][kSeries];
+
+// Normalised time-integration coefficients (Eq. 14 divided by dt, Eq. 41), x = dt/tau:
+//   dbar_a = x psi2, dbar_b = -dt x beta, dbar_c = dt x psi3, dbar_d = phi1, dbar_e = -dt chi,
+//   dbar_d - e^-x = x chi, dbar_e + dt e^-x / 2 = -dt x kappa, with phi1 = (1-e^-x)/x,
+//   psi2 = (e^-x - 1 + x)/x^2, psi3 = (x^2/2 - x + 1 - e^-x)/x^3, chi = (phi1 - e^-x)/x,
+//   beta = (1 + e^-x - 2 phi1)/x^2, kappa = (chi - e^-x/2)/x; Taylor series (Horner) for x < 1.
+__device__ void lts_coeffs(double dt, double tau, double e, double* out)
+{
+    const double x = dt / tau;
+    double phi1, psi2, psi3, chi, beta, kappa;
+    if (x < 1.0) {
+        const double mx = -x;
+        phi1 = psi2 = psi3 = chi = beta = kappa = 0.0;
+#pragma unroll
+        for (int k = kSeries - 1; k >= 0; --k) {
+            phi1 = fma(mx, phi1, c_series[0][k]);
+            psi2 = fma(mx, psi2, c_series[1][k]);
+            psi3 = fma(mx, psi3, c_series[2][k]);
+            chi = fma(mx, chi, c_series[3][k]);
+            beta = fma(mx, beta, c_series[4][k]);
+            kappa = fma(mx, kappa, c_series[5][k]);
+        }
+    } else {
+        phi1 = (1.0 - e) / x;
+        psi2 = (e - 1.0 + x) / (x * x);
+        psi3 = (0.5 * x * x - x + 1.0 - e) / (x * x * x);
+        chi = (phi1 - e) / x;
+        beta = (1.0 + e - 2.0 * phi1) / (x * x);
+        kappa = (chi - 0.5 * e) / x;
+    }
+    out[0] = x * psi2;
+    out[1] = -dt * x * beta;
+    out[2] = dt * x * psi3;
+    out[3] = phi1;
+    out[4] = -dt * chi;
+    out[5] = x * chi;
+    out[6] = -dt * x * kappa;
+}
+
+__global__ void k_decompose(const StepConsts K, Dev d)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K.C) return;
+    const double* W = d.W + 4 * c;
+    long long* r = d.wrt + 5 * c;
+    const double vol = d.vol[c];
+    const double s0 = ldexp(1.0, -K.fx0), s1 = ldexp(1.0, -K.fx1), s4 = ldexp(1.0, -K.fx4);
+    const double tau = tau_of(K, W);
+    double Wp[4], Wh[4];
+    Wp[0] = ((double)r[0] * s0) / vol;
+    Wp[1] = ((double)r[1] * s1) / vol;
+    Wp[2] = K.dim == 1 ? 0.0 : ((double)r[2] * s1) / vol;
+    Wp[3] = ((double)r[4] * s4) / vol;
+    // W^{p,-} of the retained particles is exactly the retained tally of the previous step (same particles,
+    // masses, velocities and cell); k_sample adds the new particles
+    for (int k = 0; k < 5; ++k) { d.wprev[5 * c + k] = r[k]; d.wm[5 * c + k] = r[k]; r[k] = 0; d.wpl[5 * c + k] = 0; }
+    for (int k = 0; k < 4; ++k) { Wh[k] = W[k] - Wp[k]; d.Wh[4 * c + k] = Wh[k]; }
+    const double dt = d.dt[c];
+    const double x = dt / tau;
+    const double e = dexp(-x);
+    d.tau[c] = tau;
+    d.xr[c] = x;
+    d.emx[c] = e;
+    lts_coeffs(dt, tau, e, d.co + 7 * c);
+    const int phys = realizable(K, Wh);
+    d.hphys[c] = phys;
+    int n = 0;
+    double m = 0.0, Uh = 0.0, Vh = 0.0, RTh = 0.0;
+    if (!K.wave_only && phys) {
+        // W^hp = W^h e^{-dt_i/tau_i}, N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp (Eq. 17)
+        const double rho_hp = Wh[0] * e;
+        if (rho_hp > 0.0) {
+            const double q = ceil((rho_hp / W[0]) * (double)K.n_ref);
+            if (q > (double)kMaxNew) {
+                atomicOr(d.err, ERR_LIMIT);
+            } else {
+                n = (int)q;
+                m = (rho_hp * vol) / q;
+                Uh = Wh[1] / Wh[0];
+                Vh = Wh[2] / Wh[0];
+                RTh = (Wh[3] / Wh[0] - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
+            }
+        }
+    }
+    d.nhp[c] = n;
+    d.mnew[c] = m;
+    d.samp[3 * c] = Uh; d.samp[3 * c + 1] = Vh; d.samp[3 * c + 2] = RTh;
+    d.tau32[c] = (float)tau;
+    d.dt32[c] = (float)dt;
+    d.mnew32[c] = (float)m;
+    d.samp32[3 * c] = (float)Uh; d.samp32[3 * c + 1] = (float)Vh; d.samp32[3 * c + 2] = (float)RTh;
+    d.cnt[c] = 0;
+    d.cur[c] = 0;
+}
+
+// per-step zeroing of face crossings, wall tallies and counters; the sort flag of this step
+__global__ void k_begin_step(const StepConsts K, Dev d)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int q = t; q < 2 * K.F; q += nt) d.cross[q] = 0u;
+    for (int q = t; q < 3 * K.nwall; q += nt) d.wallt[q] = 0;
+    if (t == 0) {
+        for (int k = 2; k < 8; ++k) d.stats[k] = 0;
+        d.stats[11] = 0;
+        d.counts[2] = 0;
+        *d.nretry = 0;
+        *d.done = 0u;
+        d.flags[0] = (int)(*d.dstep % K.sort_every == (long long)(K.sort_every - 1));
+    }
+}
+
+// per-cell particle-precision views
+template <typename T> struct PCell;
+template <> struct PCell<float> {
+    const float *tau, *dt, *mnew, *samp;
+    __device__ float tau_(int c) const { return tau[c]; }
+    __device__ float dt_(int c) const { return dt[c]; }
+    __device__ float m_(int c) const { return mnew[c]; }
+    __device__ float s_(int c, int k) const { return samp[3 * c + k]; }
+};
+template <> struct PCell<double> {
+    const double *tau, *dt, *mnew, *samp;
+    __device__ double tau_(int c) const { return tau[c]; }
+    __device__ double dt_(int c) const { return dt[c]; }
+    __device__ double m_(int c) const { return mnew[c]; }
+    __device__ double s_(int c, int k) const { return samp[3 * c + k]; }
+};
+
+__device__ __forceinline__ float fsqrt_(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ double fsqrt_(double x) { return __dsqrt_rn(x); }
+// float -> int64, IEEE round-half-even, with 32-bit integer operations only (B300 executes 64-bit
+// float<->integer conversions on its narrow FP64 pipe). Exact for |x| < 2^63.
+__device__ __forceinline__ long long rint_ll(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const int ex = (int)((b >> 23) & 0xffu);
+    if (ex == 0) return 0;
+    const uint32_t mant = (b & 0x7fffffu) | 0x800000u;
+    const int sh = ex - 150;                 // |x| = mant 2^sh
+    long long r;
+    if (sh >= 0) {
+        r = (long long)mant << sh;
+    } else if (sh >= -24) {
+        const int k = -sh;
+        uint32_t q = mant >> k;
+        const uint32_t rem = mant & ((1u << k) - 1u), half = 1u << (k - 1);
+        if (rem > half || (rem == half && (q & 1u))) q += 1u;
+        r = (long long)q;
+    } else {
+        r = 0;
+    }
+    return (b >> 31) ? -r : r;
+}
+__device__ __forceinline__ long long rint_ll(double x) { return __double2ll_rn(x); }
+
+// ----------------------------------------------------------- fixed-point tallies (Eq. 21)
+template <typename T>
+__device__ __forceinline__ long long fixp(T v, T scale, int* err)
+{
+    const T s = v * scale;
+    if (!(fabs(s) < T(4.611686018427387904e18))) { atomicOr(err, ERR_OVERFLOW); return 0; }
+    return rint_ll(s);
+}
+
+// the five tallied moments of one particle, m (1, u, v, w, |u|^2/2), as fixed-point integers
+template <typename T>
+__device__ __forceinline__ void fix5(T m, T u, T v, T w, T s0, T s1, T s4, int* err, long long o[5])
+{
+    const T e = T(0.5) * ((u * u + v * v) + w * w);
+    o[0] = fixp(m, s0, err);
+    o[1] = fixp(m * u, s1, err);
+    o[2] = fixp(m * v, s1, err);
+    o[3] = fixp(m * w, s1, err);
+    o[4] = fixp(m * e, s4, err);
+}
+
+// Warp-wide sums over runs of equal keys (consecutive lanes with the same cell), then one atomic per run
+// and value from the run's last lane. Keys < 0 are skipped. All 32 lanes must call it.
+template <int NV>
+__device__ __forceinline__ void run_reduce(int key, long long (&v)[NV], int lane, int* start_out)
+{
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    int start = (lane == 0 || prev != key) ? lane : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start = max(start, t);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        long long x = v[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane - o >= start) x += t;
+        }
+        v[k] = x;
+    }
+    *start_out = start;
+}
+
+// ----------------------------------------------------- a2: new collisionless particles (Eq. 17)
+// One warp per cell. Velocities: Box-Muller normals shifted and scaled so that the cell's new particles
+// carry exactly the momentum and energy of W^hp (sums in index order, accumulated by lane 0).
+template <typename T>
+__global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
+                                                ParticleSoA<T> PB, PCell<T> pc, const long long* dstep)
+{
+    const ParticleSoA<T> A = *d.bufsel ? PB : PA;   // the buffer holding this step's particles
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= K.C) return;
+    const int c = warp;
+    const int N = d.nhp[c];
+    if (N == 0 || d.counts[1] == 0) return;
+    const int nret = d.counts[0];
+    const long long base_i = (long long)nret + d.nhp_off[c];
+    const int cap_left = d.counts[3] - nret;
+    if (d.nhp_off[c] + N > cap_left) {
+        if (lane == 0) atomicOr(d.err, ERR_CAPACITY);
+        return;
+    }
+    const Rng g{K.k0, K.k1, (uint32_t)*dstep};
+    const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)c << 11);
+    T su = 0, sv = 0, sw = 0;
+    for (int k0 = 0; k0 < N; k0 += 32) {
+        const int k = k0 + lane;
+        T z0 = 0, z1 = 0, z2 = 0;
+        if (k < N) {
+            T U[4];
+            Unif<T>::get(g, pbase | (uint64_t)k, DRAW_VEL, 4, U);
+            const T r0 = fsqrt_(T(-2) * dlog(U[0]));
+            T s0, c0, s1, c1;
+            dsincos2pi(U[1], &s0, &c0);
+            const T r1 = fsqrt_(T(-2) * dlog(U[2]));
+            dsincos2pi(U[3], &s1, &c1);
+            z0 = r0 * c0; z1 = r0 * s0; z2 = r1 * c1;
+            A.u[base_i + k] = z0; A.v[base_i + k] = z1; A.w[base_i + k] = z2;
+        }
+        const int nk = min(32, N - k0);
+        for (int j = 0; j < nk; ++j) {
+            const T a = __shfl_sync(0xffffffffu, z0, j), b = __shfl_sync(0xffffffffu, z1, j),
+                    e = __shfl_sync(0xffffffffu, z2, j);
+            if (lane == 0) { su += a; sv += b; sw += e; }
+        }
+    }
+    const T inv = T(1) / T(N);
+    T mu = su * inv, mv = sv * inv, mw = sw * inv;
+    mu = __shfl_sync(0xffffffffu, mu, 0); mv = __shfl_sync(0xffffffffu, mv, 0); mw = __shfl_sync(0xffffffffu, mw, 0);
+    T ss = 0;
+    for (int k0 = 0; k0 < N; k0 += 32) {
+        const int k = k0 + lane;
+        T q = 0;
+        if (k < N) {
+            const T du = A.u[base_i + k] - mu, dv = A.v[base_i + k] - mv, dw = A.w[base_i + k] - mw;
+            q = (du * du + dv * dv) + dw * dw;
+        }
+        const int nk = min(32, N - k0);
+        for (int j = 0; j < nk; ++j) {
+            const T a = __shfl_sync(0xffffffffu, q, j);
+            if (lane == 0) ss += a;
+        }
+    }
+    const T Uh = pc.s_(c, 0), Vh = pc.s_(c, 1), RTh = pc.s_(c, 2);
+    T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTh) / ss) : T(0);
+    sc = __shfl_sync(0xffffffffu, sc, 0);
+    const T m = pc.m_(c);
+    const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+    long long acc[5] = {0, 0, 0, 0, 0};
+    for (int k = lane; k < N; k += 32) {
+        const uint64_t pid = pbase | (uint64_t)k;
+        const long long i = base_i + k;
+        T U[3], x, y;
+        Unif<T>::get(g, pid, DRAW_POS, 3, U);
+        if (K.dim == 1) {
+            const T xa = T(d.cvx[4 * c]), xb = T(d.cvx[4 * c + 1]);
+            x = xa + U[0] * (xb - xa);
+            y = T(0);
+        } else {
+            T X[4], Y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { X[q] = T(d.cvx[4 * c + q]); Y[q] = T(d.cvy[4 * c + q]); }
+            const T A1 = T(0.5) * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+            const T A2 = T(0.5) * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+            const bool first = U[0] * (A1 + A2) < A1;
+            const int bi = first ? 1 : 2, ci = first ? 2 : 3;
+            const T sq = fsqrt_(U[1]);
+            const T wa = T(1) - sq, wb = sq * (T(1) - U[2]), wc = sq * U[2];
+            x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
+            y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
+        }
+        const T z0 = A.u[i], z1 = A.v[i], z2 = A.w[i];
+        const T un = Uh + sc * (z0 - mu), vn = Vh + sc * (z1 - mv), wn = sc * (z2 - mw);
+        A.x[i] = x; A.y[i] = y;
+        A.u[i] = un;
+        A.v[i] = vn;
+        A.w[i] = wn;
+        A.m[i] = m;
+        A.cell[i] = c;
+        A.pid[i] = pid;
+        long long f[5];
+        fix5(m, un, vn, wn, s0, s1, s4, d.err, f);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] += f[q];
+    }
+    // W^{p,-} of the new particles: this warp owns the cell, so a butterfly sum and one plain update
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0)
+        for (int q = 0; q < 5; ++q) d.wm[5 * c + q] += acc[q];
+}
+
+// ------------------------------------------------- a3-a6: free flight, transport and tallies
+// One thread per particle (warp-uniform grid-stride loop). Retained particles draw t_f (Eq. 18 with dt_i),
+// new ones fly the whole dt_i; free transport through the cell faces (Eq. 19) with mass and remaining time
+// scaled by dt_R / dt_L at every crossing (Eqs. 37, 45), diffuse re-emission at walls, specular mirrors,
+// deletion at far-field and fixed ghosts. Then W^{p,+} and the retained tally (run-reduced per warp) and
+// the survivors: compacted into the other buffer (warp-aggregated slots), or, on sort steps, written in
+// place for the counting sort.
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const Dev d, ParticleSoA<T> PA,
+                                                   ParticleSoA<T> PB, const CellFaces<T>* __restrict__ cf,
+                                                   PCell<T> pc, const long long* dstep)
+{
+    const int sel = *d.bufsel;
+    const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
+    const bool sort_step = d.flags[0] != 0;
+    const int nret = d.counts[0];
+    const int n = nret + d.counts[1];
+    const Rng g{K.k0, K.k1, (uint32_t)*dstep};
+    const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+    const T m2RTw = T(K.m2RTw), sigw = T(K.sig_w);
+    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0;
+    int max_it = 0;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    // each warp walks a contiguous range of the (cell-ordered) particle array, 32 particles at a time,
+    // prefetching the next 32 records into L1 while it works on the current ones
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int per = ((n + nwarps - 1) / nwarps + 31) & ~31;
+    const int wbeg = min(n, gw * per), wend = min(n, wbeg + per);
+    for (int base = wbeg; base < wend; base += 32) {
+        const int i = base + lane;
+        const int inext = i + 32;
+        if (inext < wend) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.x + inext));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.y + inext));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.u + inext));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.v + inext));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.w + inext));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.m + inext));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.cell + inext));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.pid + inext));
+        }
+        long long fx[5] = {0, 0, 0, 0, 0};
+        int end_cell = -1;
+        bool kept = false;
+        T x = 0, y = 0, u = 0, v = 0, w = 0, m = 0;
+        uint64_t pid = 0;
+        if (i < wend) {
+            x = A.x[i]; y = A.y[i]; u = A.u[i]; v = A.v[i]; w = A.w[i]; m = A.m[i];
+            int c = A.cell[i];
+            pid = A.pid[i];
+            const T dtc = pc.dt_(c);
+            T tr;
+            bool collide = false;
+            if (i >= nret) {
+                tr = dtc;
+            } else {
+                T U[1];
+                Unif<T>::get(g, pid, DRAW_TF, 1, U);
+                const T a = -(pc.tau_(c) * dlog(U[0]));
+                collide = a < dtc;
+                tr = collide ? a : dtc;
+            }
+            int entry = -1, hits = 0, it = 0;
+            bool alive = true;
+            for (;;) {
+                const CellFaces<T>& F = cf[c];
+                const int nf = d.nfc[c];
+                int kb = -1;
+                T best = T(0);
+                for (int k = 0; k < nf; ++k) {
+                    if (k == entry) continue;
+                    const T un = F.nx[k] * u + F.ny[k] * v;
+                    if (!(un > T(0))) continue;
+                    T t = (F.d[k] - (F.nx[k] * x + F.ny[k] * y)) / un;
+                    if (t < T(0)) t = T(0);
+                    if (kb < 0 || t < best) { best = t; kb = k; }
+                }
+                if (kb < 0 || tr <= best) {
+                    x = x + u * tr;
+                    y = y + v * tr;
+                    break;
+                }
+                x = x + u * best;
+                y = y + v * best;
+                tr = tr - best;
+                if (++it > kMaxIters) { atomicOr(d.err, ERR_LIMIT); break; }
+                const int meta = F.meta[kb];
+                const int bc = (meta >> 26) & 7;
+                const int nb = F.nbr[kb];
+                if (nb >= 0) {
+                    const int f = meta & 0xffffff, dir = ((meta >> 29) & 1) ? 0 : 1;
+                    atomicAdd(d.cross + 2 * f + dir, 1u);
+                    n_cross++;
+                    const T r = F.ratio[kb];
+                    m = m * r;
+                    tr = tr * r;
+                    if (bc == UGKWP_BC_PERIODIC) x = x + T(d.cshift[4 * c + kb]);
+                    entry = (meta >> 24) & 3;
+                    c = nb;
+                } else if (bc == UGKWP_BC_WALL) {
+                    T U[3];
+                    Unif<T>::get(g, pid, draw_wall(hits), 3, U);
+                    const T nx = F.nx[kb], ny = F.ny[kb];
+                    const T un = fsqrt_(m2RTw * dlog(U[0]));
+                    const T rad = fsqrt_(T(-2) * dlog(U[1]));
+                    T sn, cs;
+                    dsincos2pi(U[2], &sn, &cs);
+                    const T vt = sigw * (rad * cs), wz = sigw * (rad * sn);
+                    const T tx = -ny, ty = nx;
+                    const T uo = vt * tx - un * nx, vo = vt * ty - un * ny;
+                    const int iw = d.fwall[meta & 0xffffff];
+                    const T ein = T(0.5) * ((u * u + v * v) + w * w);
+                    const T eout = T(0.5) * ((uo * uo + vo * vo) + wz * wz);
+                    unsigned long long* wa = reinterpret_cast<unsigned long long*>(d.wallt + 3 * (size_t)iw);
+                    atomicAdd(wa + 0, (unsigned long long)fixp(m * (u - uo), s1, d.err));
+                    atomicAdd(wa + 1, (unsigned long long)fixp(m * (v - vo), s1, d.err));
+                    atomicAdd(wa + 2, (unsigned long long)fixp(m * (ein - eout), s4, d.err));
+                    u = uo; v = vo; w = wz;
+                    entry = kb;
+                    hits++;
+                    n_hits++;
+                } else if (bc == UGKWP_BC_SYMMETRY) {
+                    const T un = F.nx[kb] * u + F.ny[kb] * v;
+                    const T t2 = T(2) * un;
+                    u = u - t2 * F.nx[kb];
+                    v = v - t2 * F.ny[kb];
+                    entry = kb;
+                } else {
+                    alive = false;
+                    break;
+                }
+            }
+            max_it = max(max_it, it);
+            if (alive) {
+                fix5(m, u, v, w, s0, s1, s4, d.err, fx);
+                end_cell = c;
+                kept = !collide;
+                if (collide) n_removed++;
+            } else {
+                n_left++;
+            }
+        }
+        // survivors
+        if (sort_step) {
+            if (i < wend) {
+                B.x[i] = x; B.y[i] = y; B.u[i] = u; B.v[i] = v; B.w[i] = w; B.m[i] = m;
+                B.cell[i] = kept ? end_cell : -1;
+                B.pid[i] = pid;
+            }
+        } else {
+            const unsigned km = __ballot_sync(0xffffffffu, kept);
+            int slot0 = 0;
+            if (lane == 0 && km) slot0 = atomicAdd(d.counts + 2, __popc(km));
+            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            if (kept) {
+                const int j = slot0 + __popc(km & lt_mask);
+                B.x[j] = x; B.y[j] = y; B.u[j] = u; B.v[j] = v; B.w[j] = w; B.m[j] = m;
+                B.cell[j] = end_cell;
+                B.pid[j] = pid;
+            }
+        }
+        // W^{p,+} (every particle still in the domain, in its final cell) and the retained part per run
+        // of equal final cell; when no particle of the warp collided both sums coincide
+        const bool any_removed = __any_sync(0xffffffffu, end_cell >= 0 && !kept);
+        const int next = __shfl_down_sync(0xffffffffu, end_cell, 1);
+        const bool tail = (lane == 31 || next != end_cell) && end_cell >= 0;
+        int start;
+        if (!any_removed) {
+            run_reduce<5>(end_cell, fx, lane, &start);
+            if (tail) {
+                unsigned long long* ap = reinterpret_cast<unsigned long long*>(d.wpl + 5 * (size_t)end_cell);
+                unsigned long long* ar = reinterpret_cast<unsigned long long*>(d.wrt + 5 * (size_t)end_cell);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if (fx[k]) {
+                        atomicAdd(ap + k, (unsigned long long)fx[k]);
+                        atomicAdd(ar + k, (unsigned long long)fx[k]);
+                    }
+                }
+                atomicAdd(d.cnt + end_cell, lane - start + 1);
+            }
+        } else {
+            long long vals[11];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) { vals[k] = fx[k]; vals[5 + k] = kept ? fx[k] : 0; }
+            vals[10] = kept ? 1 : 0;
+            run_reduce<11>(end_cell, vals, lane, &start);
+            if (tail) {
+                unsigned long long* ap = reinterpret_cast<unsigned long long*>(d.wpl + 5 * (size_t)end_cell);
+                unsigned long long* ar = reinterpret_cast<unsigned long long*>(d.wrt + 5 * (size_t)end_cell);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if (vals[k]) atomicAdd(ap + k, (unsigned long long)vals[k]);
+                    if (vals[5 + k]) atomicAdd(ar + k, (unsigned long long)vals[5 + k]);
+                }
+                if (vals[10]) atomicAdd(d.cnt + end_cell, (int)vals[10]);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
+        n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
+        n_removed += __shfl_xor_sync(0xffffffffu, n_removed, o);
+        n_left += __shfl_xor_sync(0xffffffffu, n_left, o);
+        max_it = max(max_it, __shfl_xor_sync(0xffffffffu, max_it, o));
+    }
+    if (lane == 0) {
+        if (n_removed) atomicAdd(d.stats + 3, n_removed);
+        if (n_left) atomicAdd(d.stats + 4, n_left);
+        if (n_cross) atomicAdd(d.stats + 5, n_cross);
+        if (n_hits) atomicAdd(d.stats + 6, n_hits);
+        if (max_it) atomicMax(d.stats + 7, (unsigned long long)max_it);
+    }
+}
+
+// --------------------------------------------------------------------- a7: counting sort
+// sort steps only: counting sort of the survivors by cell, from the staging buffer back into the buffer that
+// held this step's particles (which then stays the current one)
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB)
+{
+    if (!d.flags[0]) return;
+    const int sel = *d.bufsel;
+    const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
+    const int n = d.counts[4];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = B.cell[i];
+        if (c < 0) continue;
+        const int slot = d.off[c] + atomicAdd(d.cur + c, 1);
+        A.x[slot] = B.x[i]; A.y[slot] = B.y[i]; A.u[slot] = B.u[i]; A.v[slot] = B.v[i]; A.w[slot] = B.w[i];
+        A.m[slot] = B.m[i]; A.cell[slot] = c; A.pid[slot] = B.pid[i];
+    }
+}
+
+// ---------------------------------------------------------------- a10: update (Eq. 46)
+// Threads [0, C): conservative update of one cell, residual term, particle-mass-ratio EMA, vacuum floor.
+// Threads [C, C + n_wall): wall pressure, shear stress and heat flux of one wall face (a11, Sec. 5.1).
+// The last block to finish reduces the residual partials in block order and closes the step.
+__global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long long* dstep)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double r2[4] = {0, 0, 0, 0};
+    if (t < K.C) {
+        const int c = t;
+        const CellFaces<float>& Fc = d.cf32[c];
+        double acc[4] = {0, 0, 0, 0};
+        for (int k = 0; k < d.nfc[c]; ++k) {
+            const int meta = Fc.meta[k];
+            const int f = meta & 0xffffff;
+            const bool isL = (meta >> 29) & 1;
+            const double s = d.fs[f];
+            for (int q = 0; q < 4; ++q) {
+                const double tt = d.flux[4 * (size_t)f + q] * s;
+                acc[q] += isL ? tt : -tt;
+            }
+        }
+        const double vol = d.vol[c], dt = d.dt[c];
+        const double coef = dt / vol;
+        const double sc[4] = {ldexp(1.0, -K.fx0), ldexp(1.0, -K.fx1), ldexp(1.0, -K.fx1), ldexp(1.0, -K.fx4)};
+        const int tk[4] = {0, 1, 2, 4};
+        double* W = d.W + 4 * c;
+        double Wn[4];
+        for (int q = 0; q < 4; ++q) {
+            const long long dd = d.wpl[5 * c + tk[q]] - d.wm[5 * c + tk[q]];
+            Wn[q] = (W[q] - coef * acc[q]) + ((double)dd * sc[q]) / vol;
+        }
+        if (K.dim == 1) Wn[2] = 0.0;
+        if (!isfinite(Wn[0]) || !isfinite(Wn[1]) || !isfinite(Wn[2]) || !isfinite(Wn[3])) atomicOr(d.err, ERR_NONPHYS);
+        // vacuum floor: a cell emptied of particles whose small wave remainder the outflow drove out of the
+        // realizable set restarts from a near-vacuum state at rest at T_inf
+        if (!realizable(K, Wn)) {
+            Wn[0] = kRhoFloor; Wn[1] = 0.0; Wn[2] = 0.0; Wn[3] = kRhoFloor * (1.5 * kR);
+            atomicAdd(d.stats + 11, 1ull);
+        }
+        for (int q = 0; q < 4; ++q) {
+            const double r = (Wn[q] - W[q]) / dt;
+            r2[q] = vol * (r * r);
+            W[q] = Wn[q];
+        }
+        const double chi = (((double)d.wpl[5 * c] * sc[0]) / vol) / W[0];
+        d.chi_ema[c] = *dstep == 0 ? chi : d.chi_ema[c] + (2.0 / 1001.0) * (chi - d.chi_ema[c]);
+    } else if (t < K.C + K.nwall) {
+        const int iw = t - K.C;
+        const int f = d.wall_face[iw], c = d.fL[f];
+        const double nx = d.fnx[f], ny = d.fny[f], tx = -ny, ty = nx;
+        const double* F = d.flux + 4 * (size_t)f;
+        const double s1 = ldexp(1.0, -K.fx1), s4 = ldexp(1.0, -K.fx4);
+        const double sdt = d.fs[f] * d.dt[c];
+        const double px = ((double)d.wallt[3 * iw] * s1) / sdt;
+        const double py = ((double)d.wallt[3 * iw + 1] * s1) / sdt;
+        const double pe = ((double)d.wallt[3 * iw + 2] * s4) / sdt;
+        const double p = (F[1] + px) * nx + (F[2] + py) * ny;
+        const double tw = (F[1] + px) * tx + (F[2] + py) * ty;
+        const double q = F[3] + pe;
+        d.surf_last[3 * iw] = p; d.surf_last[3 * iw + 1] = tw; d.surf_last[3 * iw + 2] = q;
+        d.surf_sum[3 * iw] += p; d.surf_sum[3 * iw + 1] += tw; d.surf_sum[3 * iw + 2] += q;
+    }
+    // residual partial sums in a fixed tree order
+    __shared__ double sm[4][256];
+    __shared__ bool last;
+    for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = r2[q];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; ++q) d.res_part[4 * blockIdx.x + q] = sm[q][0];
+        __threadfence();
+        last = atomicAdd(d.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    // the step's last block: residual (partials summed in block order), counters, next step
+    __threadfence();
+    double s[4] = {0, 0, 0, 0};
+    for (int b = 0; b < (int)gridDim.x; ++b)
+        for (int q = 0; q < 4; ++q) s[q] += __ldcg(d.res_part + 4 * b + q);
+    for (int q = 0; q < 4; ++q) d.res[q] = sqrt(s[q]);
+    if (*dstep == 0)
+        for (int q = 0; q < 4; ++q) d.res[4 + q] = d.res[q] > 0.0 ? d.res[q] : 1.0;
+    const int kept = __ldcg(d.counts + 2);
+    d.counts[0] = kept;
+    if (!d.flags[0]) *d.bufsel = 1 - *d.bufsel;
+    *dstep += 1;
+    d.stats[0] = (unsigned long long)*dstep;
+    d.stats[1] = (unsigned long long)kept;
+    d.stats[2] = (unsigned long long)d.counts[1];
+    d.stats[8] += 1;  // surface samples
+    d.stats[9] += (unsigned long long)d.counts[4];
+    d.stats[10] += (unsigned long long)d.counts[1];
+}
+
+// ------------------------------------------------------------------ state transfer helpers
+template <typename T>
+__global__ void k_put_particles(ParticleSoA<T> A, int n, const double* x, const double* y, const double* u,
+                                const double* v, const double* w, const double* m, const int* cell,
+                                const unsigned long long* pid)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    A.x[i] = T(x[i]); A.y[i] = T(y[i]); A.u[i] = T(u[i]); A.v[i] = T(v[i]); A.w[i] = T(w[i]); A.m[i] = T(m[i]);
+    A.cell[i] = cell[i];
+    A.pid[i] = pid[i];
+}
+
+template <typename T>
+__global__ void k_get_particles(ParticleSoA<T> A, int n, double* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = double(A.x[i]); out[n + i] = double(A.y[i]); out[2 * n + i] = double(A.u[i]);
+    out[3 * n + i] = double(A.v[i]); out[4 * n + i] = double(A.w[i]); out[5 * n + i] = double(A.m[i]);
+}
+
+__global__ void k_set_prim(Dev d, int C, const double* prim)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const double rho = prim[4 * c], U = prim[4 * c + 1], V = prim[4 * c + 2], T = prim[4 * c + 3];
+    d.W[4 * c] = rho;
+    d.W[4 * c + 1] = rho * U;
+    d.W[4 * c + 2] = rho * V;
+    d.W[4 * c + 3] = rho * (0.5 * (U * U + V * V) + 1.5 * kR * T);
+    for (int k = 0; k < 5; ++k) d.wrt[5 * c + k] = 0;
+}
+
+__global__ void k_cell_data(Dev d, int C, double* out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    double* o = out + 8 * c;
+    o[0] = d.tau[c]; o[1] = d.xr[c]; o[2] = d.emx[c]; o[3] = (double)d.nhp[c]; o[4] = d.mnew[c];
+    o[5] = d.samp[3 * c]; o[6] = d.samp[3 * c + 1]; o[7] = d.samp[3 * c + 2];
+}
+
+__global__ void k_wp_field(Dev d, int C, int fx0, int fx1, int fx4, double* out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const long long* r = d.wrt + 5 * c;
+    out[4 * c] = ((double)r[0] * ldexp(1.0, -fx0)) / d.vol[c];
+    out[4 * c + 1] = ((double)r[1] * ldexp(1.0, -fx1)) / d.vol[c];
+    out[4 * c + 2] = ((double)r[2] * ldexp(1.0, -fx1)) / d.vol[c];
+    out[4 * c + 3] = ((double)r[4] * ldexp(1.0, -fx4)) / d.vol[c];
+}
+
+// ---------------------------------------------------------------------------- host helpers
+int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+ugkwp_status fail(Ctx& c, ugkwp_status st, const char* what)
+{
+    c.msg = what;
+    return st;
+}
+
+#define CK(expr)                                                                    \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ctx.msg = std::string(#expr) + ": " + cudaGetErrorString(e_);           \
+            return UGKWP_ECUDA;                                                     \
+        }                                                                           \
+    } while (0)
+
+template <typename P> cudaError_t dalloc(Ctx& ctx, P** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(P));
+    if (e != cudaSuccess) return e;
+    cudaMemsetAsync(q, 0, (n ? n : 1) * sizeof(P), ctx.stream);
+    ctx.allocs.push_back(q);
+    *p = static_cast<P*>(q);
+    return cudaSuccess;
+}
+
+template <typename T> cudaError_t alloc_particles(Ctx& ctx, ParticleSoA<T>& P, size_t cap)
+{
+    cudaError_t e;
+    if ((e = dalloc(ctx, &P.x, cap)) || (e = dalloc(ctx, &P.y, cap)) || (e = dalloc(ctx, &P.u, cap)) ||
+        (e = dalloc(ctx, &P.v, cap)) || (e = dalloc(ctx, &P.w, cap)) || (e = dalloc(ctx, &P.m, cap)) ||
+        (e = dalloc(ctx, &P.cell, cap)) || (e = dalloc(ctx, &P.pid, cap)))
+        return e;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// the per-step kernel sequence (enqueued on s; capturable)
+static void enqueue_step(Ctx& ctx, cudaStream_t s, bool prof)
+{
+    const StepConsts& K = ctx.k;
+    Dev& d = ctx.d;
+    const int C = K.C;
+    cudaEvent_t ev[kStages + 1];
+    auto mark = [&](int k) {
+        if (!prof) return;
+        if (k == 0)
+            for (int q = 0; q <= kStages; ++q) cudaEventCreate(&ev[q]);
+        cudaEventRecord(ev[k], s);
+        if (k == kStages)
+            for (int q = 0; q <= kStages; ++q) ctx.prof_events.push_back(ev[q]);
+    };
+    mark(0);
+    k_begin_step<<<nblk(2LL * K.F, 256), 256, 0, s>>>(K, d);
+    k_decompose<<<nblk(C, 128), 128, 0, s>>>(K, d);
+    exclusive_scan(d.nhp, d.nhp_off, d.scan_tmp, C, d.counts + 1, s, d.counts, d.err);
+    mark(1);
+    PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32};
+    PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp};
+    if (K.prec == 0) k_sample<float><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
+    else k_sample<double><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
+    mark(2);
+    if (K.prec == 0) k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
+    else k_particles<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64, d.cf64, pc64, d.dstep);
+    mark(3);
+    launch_wave_flux(K, d, ctx.sms, s);
+    mark(4);
+    // counting sort every sort_every-th step (kernels return at once on the other steps)
+    exclusive_scan(d.cnt, d.off, d.scan_tmp, C, d.counts + 2, s, nullptr, nullptr, d.flags);
+    if (K.prec == 0) k_scatter<float><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa32, d.pb32);
+    else k_scatter<double><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa64, d.pb64);
+    mark(5);
+    k_update<<<ctx.res_blocks, 256, 0, s>>>(K, d, d.dstep);
+    mark(6);
+}
+
+}  // namespace ugk
+
+using namespace ugk;
+
+namespace {
+ugkwp_status check_device_error(Ctx& ctx)
+{
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx.d.err, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    if (h & ERR_NONPHYS) return fail(ctx, UGKWP_ENONPHYS, "non-physical cell state after the update");
+    if (h & ERR_OVERFLOW) return fail(ctx, UGKWP_EOVERFLOW, "fixed-point tally overflow");
+    if (h & ERR_CAPACITY) return fail(ctx, UGKWP_ELIMIT, "particle capacity exceeded");
+    if (h & ERR_LIMIT) return fail(ctx, UGKWP_ELIMIT, "crossing cap or new-particle cap reached");
+    return UGKWP_OK;
+}
+
+int ceil_log2(double x)
+{
+    int e;
+    const double m = frexp(x, &e);
+    return m == 0.5 ? e - 1 : e;
+}
+}  // namespace
+
+extern "C" {
+
+ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double Kn, double Ma, double Tw, double cfl,
+                          ugkwp_tstep mode, const ugkwp_opts* opts, ugkwp_ctx** out)
+{
+    if (!mesh || !gas || !opts || !out || mesh->ni <= 0 || mesh->nj <= 0 || !mesh->xv) return UGKWP_EINVAL;
+    if ((long long)mesh->ni * mesh->nj > kMaxCells || opts->n_ref <= 0 || !(cfl > 0.0)) return UGKWP_EINVAL;
+    if (mesh->dim != 1 && mesh->dim != 2) return UGKWP_EINVAL;
+    if (mesh->dim == 1 && (mesh->nj != 1 || !mesh->bc_imin || !mesh->bc_imax)) return UGKWP_EINVAL;
+    if (mesh->dim == 2 && (!mesh->yv || (mesh->periodic_j && mesh->nj < 2))) return UGKWP_EINVAL;
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return UGKWP_ECUDA;
+    ugkwp_ctx* h = new (std::nothrow) ugkwp_ctx;
+    if (!h) return UGKWP_ENOMEM;
+    Ctx& ctx = h->c;
+    *out = nullptr;
+    ctx.stream = static_cast<cudaStream_t>(opts->stream);
+    ctx.use_graph = opts->use_graph;
+    const int ni = mesh->ni, nj = mesh->nj, C = ni * nj;
+    const int periodic_i = mesh->dim == 1 && mesh->bc_imin[0] == UGKWP_BC_PERIODIC;
+    if (mesh->dim == 1 && ((mesh->bc_imin[0] == UGKWP_BC_PERIODIC) != (mesh->bc_imax[0] == UGKWP_BC_PERIODIC))) {
+        delete h;
+        return UGKWP_EINVAL;
+    }
+    const int F = mesh->dim == 1 ? (periodic_i ? ni : ni + 1) : (ni + 1) * nj + ni * (mesh->periodic_j ? nj : nj + 1);
+    ctx.ni = ni; ctx.nj = nj; ctx.periodic_j = mesh->periodic_j;
+    StepConsts& K = ctx.k;
+    K.C = C; K.F = F; K.dim = mesh->dim; K.n_ref = opts->n_ref; K.wave_only = opts->wave_only;
+    K.prec = opts->precision ? 1 : 0;
+    K.omega = gas->omega; K.Pr = gas->Pr; K.Tw = Tw;
+    K.mu_inf = (15.0 * sqrt(2.0 * 3.14159265358979323846 * 0.5) * Kn) / (2.0 * (5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega));
+    K.U_inf = Ma * sqrt((5.0 / 3.0) * 0.5 * 1.0);
+    K.m2RTw = -2.0 * 0.5 * Tw;
+    {
+        double Tc = 1.0 + Ma * Ma / 3.0;
+        if (Tw > Tc) Tc = Tw;
+        if (opts->ghost_state[3] > Tc) Tc = opts->ghost_state[3];
+        K.T_cap = 10.0 * Tc;
+        double Tm = 1.0;
+        if (Tw < Tm) Tm = Tw;
+        if (opts->ghost_state[3] > 0.0 && opts->ghost_state[3] < Tm) Tm = opts->ghost_state[3];
+        K.T_min = 0.01 * Tm;
+        K.U_cap = Ma * sqrt((5.0 / 3.0) * 0.5 * 1.0) + 10.0 * sqrt(0.5 * K.T_cap);
+    }
+    K.sig_w = sqrt(0.5 * Tw);
+    auto cons = [](double rho, double U, double V, double T, double* W) {
+        W[0] = rho; W[1] = rho * U; W[2] = rho * V; W[3] = rho * (0.5 * (U * U + V * V) + 1.5 * 0.5 * T);
+    };
+    cons(1.0, K.U_inf, 0.0, 1.0, K.W_inf);
+    cons(opts->ghost_state[0], opts->ghost_state[1], opts->ghost_state[2], opts->ghost_state[3], K.W_fix);
+    K.k0 = (uint32_t)opts->seed ^ opts->case_id;
+    K.k1 = (uint32_t)(opts->seed >> 32);
+    ctx.capacity = opts->capacity > 0 ? opts->capacity : (int)std::min<long long>(4LL * opts->n_ref * C, 0x7fffffffLL - 64);
+    ugkwp_status st = UGKWP_OK;
+    auto build = [&]() -> ugkwp_status {
+        Dev& d = ctx.d;
+        // host mesh -> device
+        const int nv = mesh->dim == 1 ? ni + 1 : (ni + 1) * (nj + 1);
+        double *xv, *yv;
+        int *bci, *bco, *bcjl, *bcjh;
+        CK(dalloc(ctx, &xv, nv)); CK(dalloc(ctx, &yv, nv));
+        CK(dalloc(ctx, &bci, nj)); CK(dalloc(ctx, &bco, nj)); CK(dalloc(ctx, &bcjl, ni)); CK(dalloc(ctx, &bcjh, ni));
+        CK(cudaMemcpyAsync(xv, mesh->xv, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx.stream));
+        if (mesh->dim == 2) CK(cudaMemcpyAsync(yv, mesh->yv, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx.stream));
+        CK(cudaMemcpyAsync(bci, mesh->bc_imin, sizeof(int) * nj, cudaMemcpyHostToDevice, ctx.stream));
+        CK(cudaMemcpyAsync(bco, mesh->bc_imax, sizeof(int) * nj, cudaMemcpyHostToDevice, ctx.stream));
+        if (mesh->dim == 2 && !mesh->periodic_j) {
+            if (!mesh->bc_jmin || !mesh->bc_jmax) return fail(ctx, UGKWP_EINVAL, "missing j boundary tags");
+            CK(cudaMemcpyAsync(bcjl, mesh->bc_jmin, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
+            CK(cudaMemcpyAsync(bcjh, mesh->bc_jmax, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
+        }
+        MeshDev m{ni, nj, mesh->dim, mesh->periodic_j, periodic_i, F, xv, yv, bci, bco, bcjl, bcjh};
+        CK(dalloc(ctx, &d.vol, C)); CK(dalloc(ctx, &d.xc, C)); CK(dalloc(ctx, &d.yc, C)); CK(dalloc(ctx, &d.dt, C));
+        CK(dalloc(ctx, &d.nfc, C)); CK(dalloc(ctx, &d.cf32, C)); CK(dalloc(ctx, &d.cf64, C));
+        CK(dalloc(ctx, &d.cshift, 4 * C)); CK(dalloc(ctx, &d.cvx, 4 * C)); CK(dalloc(ctx, &d.cvy, 4 * C));
+        CK(dalloc(ctx, &d.fL, F)); CK(dalloc(ctx, &d.fR, F)); CK(dalloc(ctx, &d.fbc, F)); CK(dalloc(ctx, &d.fwall, F));
+        CK(dalloc(ctx, &d.fnx, F)); CK(dalloc(ctx, &d.fny, F)); CK(dalloc(ctx, &d.fs, F));
+        CK(dalloc(ctx, &d.fdL, F)); CK(dalloc(ctx, &d.fdR, F)); CK(dalloc(ctx, &d.face_f64, F));
+        double *fd, *cnx, *cny, *cd, *dtpart;
+        int *cface, *csgn, *cnbr, *cnk, *cbc, *flag, *widx;
+        CK(dalloc(ctx, &fd, F)); CK(dalloc(ctx, &cnx, 4 * C)); CK(dalloc(ctx, &cny, 4 * C)); CK(dalloc(ctx, &cd, 4 * C));
+        CK(dalloc(ctx, &cface, 4 * C)); CK(dalloc(ctx, &csgn, 4 * C)); CK(dalloc(ctx, &cnbr, 4 * C));
+        CK(dalloc(ctx, &cnk, 4 * C)); CK(dalloc(ctx, &cbc, 4 * C)); CK(dalloc(ctx, &flag, F)); CK(dalloc(ctx, &widx, F + 1));
+        const int nbdt = nblk(C, 256);
+        CK(dalloc(ctx, &dtpart, nbdt));
+        CK(dalloc(ctx, &d.scan_tmp, kScanBlock));
+        k_setup_faces<<<nblk(F, 128), 128, 0, ctx.stream>>>(m, d, fd);
+        k_setup_cells<<<nblk(C, 128), 128, 0, ctx.stream>>>(m, d, fd, cface, csgn, cnbr, cnk, cbc, cnx, cny, cd);
+        k_setup_face_dist<<<nblk(F, 128), 128, 0, ctx.stream>>>(m, d, fd);
+        const double cs = K.U_inf + 3.0 * sqrt(0.5 * 1.0);
+        k_setup_dt<<<nbdt, 256, 0, ctx.stream>>>(d, C, cface, cfl, cs, dtpart);
+        if (mode == UGKWP_GTS) k_setup_gts<<<nblk(C, 256), 256, 0, ctx.stream>>>(d, C, dtpart, nbdt);
+        k_setup_tables<<<nblk(C, 128), 128, 0, ctx.stream>>>(d, C, cface, csgn, cnbr, cnk, cbc, cnx, cny, cd, K.prec == 0);
+        k_wall_flags<<<nblk(F, 128), 128, 0, ctx.stream>>>(d, F, flag);
+        int* nwall_d;
+        CK(dalloc(ctx, &nwall_d, 1));
+        exclusive_scan(flag, widx, d.scan_tmp, F, nwall_d, ctx.stream);
+        int nwall = 0;
+        CK(cudaMemcpyAsync(&nwall, nwall_d, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));
+        K.nwall = nwall;
+        CK(dalloc(ctx, &d.wall_face, nwall));
+        k_wall_index<<<nblk(F, 128), 128, 0, ctx.stream>>>(d, F, widx);
+        // fixed-point exponents: per-cell sums stay below 2^61 for up to 1024 x freestream density in the
+        // largest cell and speeds up to U_inf + 10 sqrt(R T_max)
+        std::vector<double> vol(C);
+        CK(cudaMemcpyAsync(vol.data(), d.vol, sizeof(double) * C, cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));
+        double vmax = 0.0;
+        for (int c = 0; c < C; ++c) {
+            if (!(vol[c] > 0.0)) return fail(ctx, UGKWP_EINVAL, "cell with non-positive area");
+            if (vol[c] > vmax) vmax = vol[c];
+        }
+        double Tmax = 1.0;
+        if (Tw > Tmax) Tmax = Tw;
+        if (opts->ghost_state[3] > Tmax) Tmax = opts->ghost_state[3];
+        const double speed = K.U_inf + 10.0 * sqrt(0.5 * Tmax);
+        const double b0 = 1024.0 * vmax;
+        K.fx0 = 61 - ceil_log2(b0);
+        K.fx1 = 61 - ceil_log2(b0 * speed);
+        K.fx4 = 61 - ceil_log2(b0 * (0.5 * (speed * speed)));
+        {
+            double tab[6][kSeries];
+            double f1 = 1.0;   // (k+1)!
+            for (int k = 0; k < kSeries; ++k) {
+                if (k > 0) f1 *= (double)(k + 1);
+                const double f2 = f1 * (double)(k + 2), f3 = f2 * (double)(k + 3);
+                tab[0][k] = 1.0 / f1;
+                tab[1][k] = 1.0 / f2;
+                tab[2][k] = 1.0 / f3;
+                tab[3][k] = (double)(k + 1) / f2;
+                tab[4][k] = (double)(k + 1) / f3;
+                tab[5][k] = (double)((k + 1) * (k + 2)) / (2.0 * f3);
+            }
+            CK(cudaMemcpyToSymbol(c_series, tab, sizeof tab));
+            double tf[4][kSeries];
+            for (int k = 0; k < kSeries; ++k) { tf[0][k] = tab[0][k]; tf[1][k] = tab[1][k]; tf[2][k] = tab[2][k]; tf[3][k] = tab[4][k]; }
+            CK(flux_set_tables(&tf[0][0], ctx.stream));
+            CK(cudaStreamSynchronize(ctx.stream));
+        }
+        // state and per-step arrays
+        CK(dalloc(ctx, &d.W, 4 * C)); CK(dalloc(ctx, &d.wrt, 5 * C)); CK(dalloc(ctx, &d.wprev, 5 * C));
+        CK(dalloc(ctx, &d.wm, 5 * C)); CK(dalloc(ctx, &d.wpl, 5 * C)); CK(dalloc(ctx, &d.cross, 2 * F));
+        CK(dalloc(ctx, &d.wallt, 3 * std::max(nwall, 1)));
+        CK(dalloc(ctx, &d.tau, C)); CK(dalloc(ctx, &d.xr, C)); CK(dalloc(ctx, &d.emx, C)); CK(dalloc(ctx, &d.Wh, 4 * C));
+        CK(dalloc(ctx, &d.co, 7 * C)); CK(dalloc(ctx, &d.mnew, C)); CK(dalloc(ctx, &d.samp, 3 * C));
+        CK(dalloc(ctx, &d.hphys, C)); CK(dalloc(ctx, &d.nhp, C)); CK(dalloc(ctx, &d.nhp_off, C + 1));
+        CK(dalloc(ctx, &d.cnt, C)); CK(dalloc(ctx, &d.off, C + 1)); CK(dalloc(ctx, &d.cur, C));
+        CK(dalloc(ctx, &d.flux, 4 * F));
+        ctx.res_blocks = nblk((long long)C + nwall, 256);
+        CK(dalloc(ctx, &d.res_part, 4 * ctx.res_blocks)); CK(dalloc(ctx, &d.res, 8));
+        CK(dalloc(ctx, &d.chi_ema, C));
+        CK(dalloc(ctx, &d.surf_sum, 3 * std::max(nwall, 1))); CK(dalloc(ctx, &d.surf_last, 3 * std::max(nwall, 1)));
+        CK(dalloc(ctx, &d.counts, 8)); CK(dalloc(ctx, &d.stats, 16)); CK(dalloc(ctx, &d.err, 1));
+        CK(dalloc(ctx, &d.bufsel, 1)); CK(dalloc(ctx, &d.flags, 4)); CK(dalloc(ctx, &d.nretry, 1));
+        CK(dalloc(ctx, &d.retry, F)); CK(dalloc(ctx, &d.done, 1));
+        {
+            // faces evaluated in FP64: all in the FP64 mode; otherwise the faces of wall cells
+            std::vector<int> ff(F), fb(F);
+            CK(cudaMemcpyAsync(ff.data(), d.face_f64, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaMemcpyAsync(fb.data(), d.fR, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaStreamSynchronize(ctx.stream));
+            std::vector<int> list;
+            for (int f = 0; f < F; ++f) {
+                if (K.prec == 1) ff[f] = 1;
+                if (ff[f]) list.push_back(f);
+            }
+            K.n_f64 = (int)list.size();
+            CK(dalloc(ctx, &d.f64list, std::max(K.n_f64, 1)));
+            CK(cudaMemcpyAsync(d.face_f64, ff.data(), sizeof(int) * F, cudaMemcpyHostToDevice, ctx.stream));
+            if (K.n_f64)
+                CK(cudaMemcpyAsync(d.f64list, list.data(), sizeof(int) * K.n_f64, cudaMemcpyHostToDevice, ctx.stream));
+            CK(cudaStreamSynchronize(ctx.stream));
+        }
+        K.sort_every = 8;
+        CK(dalloc(ctx, &d.tau32, C)); CK(dalloc(ctx, &d.dt32, C)); CK(dalloc(ctx, &d.mnew32, C));
+        CK(dalloc(ctx, &d.samp32, 3 * C));
+        CK(dalloc(ctx, &d.dstep, 1));
+        int sms = 148;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ctx.grid_particles = sms * 4;
+        ctx.sms = sms;
+        if (!K.wave_only) {
+            if (K.prec == 0) { CK(alloc_particles(ctx, d.pa32, ctx.capacity)); CK(alloc_particles(ctx, d.pb32, ctx.capacity)); }
+            else { CK(alloc_particles(ctx, d.pa64, ctx.capacity)); CK(alloc_particles(ctx, d.pb64, ctx.capacity)); }
+        }
+        const int cnt_init[8] = {0, 0, 0, K.wave_only ? 0 : ctx.capacity, 0, 0, 0, 0};
+        CK(cudaMemcpyAsync(d.counts, cnt_init, sizeof cnt_init, cudaMemcpyHostToDevice, ctx.stream));
+        // freestream initial state
+        std::vector<double> prim(4 * (size_t)C);
+        for (int c = 0; c < C; ++c) { prim[4 * c] = 1.0; prim[4 * c + 1] = K.U_inf; prim[4 * c + 2] = 0.0; prim[4 * c + 3] = 1.0; }
+        double* dprim;
+        CK(dalloc(ctx, &dprim, 4 * C));
+        CK(cudaMemcpyAsync(dprim, prim.data(), sizeof(double) * 4 * C, cudaMemcpyHostToDevice, ctx.stream));
+        k_set_prim<<<nblk(C, 128), 128, 0, ctx.stream>>>(d, C, dprim);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx.stream));
+        return UGKWP_OK;
+    };
+    st = build();
+    if (st != UGKWP_OK) {
+        *out = h;   // let the caller read the message, then destroy
+        return st;
+    }
+    *out = h;
+    return UGKWP_OK;
+}
+
+void ugkwp_destroy(ugkwp_ctx* h)
+{
+    if (!h) return;
+    Ctx& ctx = h->c;
+    if (ctx.stream) cudaStreamSynchronize(ctx.stream);
+    else cudaDeviceSynchronize();
+    if (ctx.graph) cudaGraphExecDestroy(ctx.graph);
+    for (cudaEvent_t e : ctx.prof_events) cudaEventDestroy(e);
+    for (void* p : ctx.allocs) cudaFree(p);
+    delete h;
+}
+
+ugkwp_status ugkwp_step(ugkwp_ctx* h, int32_t n)
+{
+    if (!h || n < 0) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    if (ctx.use_graph && !ctx.profiling) {
+        if (!ctx.graph) {
+            cudaStream_t cap;
+            CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            enqueue_step(ctx, cap, false);
+            CK(cudaStreamEndCapture(cap, &g));
+            CK(cudaGraphInstantiate(&ctx.graph, g, 0));
+            cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+        }
+        for (int32_t s = 0; s < n; ++s) CK(cudaGraphLaunch(ctx.graph, ctx.stream));
+    } else {
+        for (int32_t s = 0; s < n; ++s) enqueue_step(ctx, ctx.stream, ctx.profiling != 0);
+    }
+    CK(cudaGetLastError());
+    ctx.step += n;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_residual(ugkwp_ctx* h, double* out)
+{
+    if (!h || !out) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    double r[8];
+    CK(cudaMemcpyAsync(r, ctx.d.res, sizeof r, cudaMemcpyDeviceToHost, ctx.stream));
+    ugkwp_status st = check_device_error(ctx);
+    for (int q = 0; q < 4; ++q) { out[q] = r[q] / r[4 + q]; out[4 + q] = r[q]; }
+    return st;
+}
+
+ugkwp_status ugkwp_surface(ugkwp_ctx* h, double* p, double* tau, double* q, int32_t n_wall, int32_t averaged)
+{
+    if (!h || !p || !tau || !q) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    if (n_wall != ctx.k.nwall) return fail(ctx, UGKWP_EINVAL, "n_wall does not match the mesh");
+    std::vector<double> s(3 * (size_t)std::max(n_wall, 1));
+    unsigned long long st_h[16];
+    CK(cudaMemcpyAsync(s.data(), averaged ? ctx.d.surf_sum : ctx.d.surf_last, sizeof(double) * 3 * n_wall,
+                       cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(st_h, ctx.d.stats, sizeof st_h, cudaMemcpyDeviceToHost, ctx.stream));
+    ugkwp_status st = check_device_error(ctx);
+    const double dv = averaged && st_h[8] > 0 ? (double)st_h[8] : 1.0;
+    for (int i = 0; i < n_wall; ++i) { p[i] = s[3 * i] / dv; tau[i] = s[3 * i + 1] / dv; q[i] = s[3 * i + 2] / dv; }
+    return st;
+}
+
+ugkwp_status ugkwp_reset_surface(ugkwp_ctx* h)
+{
+    if (!h) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    CK(cudaMemsetAsync(ctx.d.surf_sum, 0, sizeof(double) * 3 * std::max(ctx.k.nwall, 1), ctx.stream));
+    CK(cudaMemsetAsync(ctx.d.stats + 8, 0, sizeof(unsigned long long), ctx.stream));
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_set_field(ugkwp_ctx* h, const double* prim)
+{
+    if (!h || !prim) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C;
+    for (int c = 0; c < C; ++c)
+        if (!(prim[4 * c] > 0.0) || !(prim[4 * c + 3] > 0.0)) return fail(ctx, UGKWP_EINVAL, "non-positive density or temperature");
+    double* dp = nullptr;
+    CK(cudaMalloc(&dp, sizeof(double) * 4 * C));
+    CK(cudaMemcpyAsync(dp, prim, sizeof(double) * 4 * C, cudaMemcpyHostToDevice, ctx.stream));
+    k_set_prim<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, dp);
+    int zero = 0;
+    CK(cudaMemcpyAsync(ctx.d.counts, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    cudaFree(dp);
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_get_field(ugkwp_ctx* h, double* W, double* Wp)
+{
+    if (!h || !W) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C;
+    CK(cudaMemcpyAsync(W, ctx.d.W, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    if (Wp) {
+        double* dp = nullptr;
+        CK(cudaMalloc(&dp, sizeof(double) * 4 * C));
+        k_wp_field<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, ctx.k.fx0, ctx.k.fx1, ctx.k.fx4, dp);
+        CK(cudaMemcpyAsync(Wp, dp, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));
+        cudaFree(dp);
+    }
+    return check_device_error(ctx);
+}
+
+ugkwp_status ugkwp_stats(ugkwp_ctx* h, int64_t* out)
+{
+    if (!h || !out) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    unsigned long long s[16];
+    CK(cudaMemcpyAsync(s, ctx.d.stats, sizeof s, cudaMemcpyDeviceToHost, ctx.stream));
+    ugkwp_status st = check_device_error(ctx);
+    for (int k = 0; k < 8; ++k) out[k] = (int64_t)s[k];
+    out[8] = (int64_t)s[9];
+    out[9] = (int64_t)s[10];
+    out[10] = (int64_t)s[11];
+    return st;
+}
+
+int64_t ugkwp_num_particles(ugkwp_ctx* h)
+{
+    if (!h) return -1;
+    Ctx& ctx = h->c;
+    int n = 0;
+    if (cudaMemcpyAsync(&n, ctx.d.counts, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(ctx.stream) != cudaSuccess) return -1;
+    return n;
+}
+
+ugkwp_status ugkwp_get_particles(ugkwp_ctx* h, int64_t cap, uint64_t* pid, int32_t* cell, double* x, double* y,
+                                 double* u, double* v, double* w, double* m)
+{
+    if (!h) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int64_t n = ugkwp_num_particles(h);
+    if (n < 0) return fail(ctx, UGKWP_ECUDA, "reading the particle count");
+    if (cap < n) return fail(ctx, UGKWP_EINVAL, "host arrays too short");
+    if (n == 0) return UGKWP_OK;
+    double* tmp = nullptr;
+    int sel = 0;
+    CK(cudaMemcpyAsync(&sel, ctx.d.bufsel, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    CK(cudaMalloc(&tmp, sizeof(double) * 6 * n));
+    if (ctx.k.prec == 0) {
+        const ParticleSoA<float>& A = sel ? ctx.d.pb32 : ctx.d.pa32;
+        k_get_particles<float><<<nblk(n, 256), 256, 0, ctx.stream>>>(A, (int)n, tmp);
+        CK(cudaMemcpyAsync(pid, A.pid, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaMemcpyAsync(cell, A.cell, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
+    } else {
+        const ParticleSoA<double>& A = sel ? ctx.d.pb64 : ctx.d.pa64;
+        k_get_particles<double><<<nblk(n, 256), 256, 0, ctx.stream>>>(A, (int)n, tmp);
+        CK(cudaMemcpyAsync(pid, A.pid, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaMemcpyAsync(cell, A.cell, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
+    }
+    double* dst[6] = {x, y, u, v, w, m};
+    for (int k = 0; k < 6; ++k)
+        CK(cudaMemcpyAsync(dst[k], tmp + (size_t)k * n, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    cudaFree(tmp);
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_set_state(ugkwp_ctx* h, int64_t step, const double* W, const int64_t* wret, int64_t np,
+                             const uint64_t* pid, const int32_t* cell, const double* x, const double* y, const double* u,
+                             const double* v, const double* w, const double* m)
+{
+    if (!h || !W || !wret || np < 0) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C;
+    if (np > ctx.capacity || (ctx.k.wave_only && np > 0)) return fail(ctx, UGKWP_ELIMIT, "particle capacity exceeded");
+    for (int64_t i = 0; i < np; ++i)
+        if (cell[i] < 0 || cell[i] >= C) return fail(ctx, UGKWP_EINVAL, "particle cell index out of range");
+    CK(cudaMemcpyAsync(ctx.d.W, W, sizeof(double) * 4 * C, cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(ctx.d.wrt, wret, sizeof(int64_t) * 5 * C, cudaMemcpyHostToDevice, ctx.stream));
+    long long st = step;
+    CK(cudaMemcpyAsync(ctx.d.dstep, &st, sizeof st, cudaMemcpyHostToDevice, ctx.stream));
+    int n32 = (int)np, zero = 0;
+    CK(cudaMemcpyAsync(ctx.d.counts, &n32, sizeof(int), cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(ctx.d.bufsel, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx.stream));
+    if (np > 0) {
+        double* tmp = nullptr;
+        int* tc = nullptr;
+        unsigned long long* tp = nullptr;
+        CK(cudaMalloc(&tmp, sizeof(double) * 6 * np));
+        CK(cudaMalloc(&tc, sizeof(int) * np));
+        CK(cudaMalloc(&tp, sizeof(unsigned long long) * np));
+        const double* src[6] = {x, y, u, v, w, m};
+        for (int k = 0; k < 6; ++k)
+            CK(cudaMemcpyAsync(tmp + (size_t)k * np, src[k], sizeof(double) * np, cudaMemcpyHostToDevice, ctx.stream));
+        CK(cudaMemcpyAsync(tc, cell, sizeof(int) * np, cudaMemcpyHostToDevice, ctx.stream));
+        CK(cudaMemcpyAsync(tp, pid, sizeof(unsigned long long) * np, cudaMemcpyHostToDevice, ctx.stream));
+        const int n = (int)np;
+        if (ctx.k.prec == 0)
+            k_put_particles<float><<<nblk(n, 256), 256, 0, ctx.stream>>>(ctx.d.pa32, n, tmp, tmp + np, tmp + 2 * np,
+                                                                       tmp + 3 * np, tmp + 4 * np, tmp + 5 * np, tc, tp);
+        else
+            k_put_particles<double><<<nblk(n, 256), 256, 0, ctx.stream>>>(ctx.d.pa64, n, tmp, tmp + np, tmp + 2 * np,
+                                                                        tmp + 3 * np, tmp + 4 * np, tmp + 5 * np, tc, tp);
+        CK(cudaStreamSynchronize(ctx.stream));
+        cudaFree(tmp); cudaFree(tc); cudaFree(tp);
+    }
+    CK(cudaStreamSynchronize(ctx.stream));
+    ctx.step = step;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_get_tallies(ugkwp_ctx* h, int64_t* wm, int64_t* wpl, int64_t* wret, int64_t* cross, int64_t* wall,
+                               int64_t* frec)
+{
+    if (!h) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const size_t C = ctx.k.C, F = ctx.k.F;
+    if (wm) CK(cudaMemcpyAsync(wm, ctx.d.wm, 8 * 5 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    if (wpl) CK(cudaMemcpyAsync(wpl, ctx.d.wpl, 8 * 5 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    if (wret) CK(cudaMemcpyAsync(wret, ctx.d.wrt, 8 * 5 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    if (wall && ctx.k.nwall) CK(cudaMemcpyAsync(wall, ctx.d.wallt, 8 * 3 * (size_t)ctx.k.nwall, cudaMemcpyDeviceToHost, ctx.stream));
+    if (cross) {
+        std::vector<unsigned int> cr(2 * F);
+        CK(cudaMemcpyAsync(cr.data(), ctx.d.cross, 4 * 2 * F, cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));
+        for (size_t i = 0; i < 2 * F; ++i) cross[i] = cr[i];
+    }
+    (void)frec;
+    return check_device_error(ctx);
+}
+
+ugkwp_status ugkwp_get_cell_data(ugkwp_ctx* h, double* out)
+{
+    if (!h || !out) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C;
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, sizeof(double) * 8 * C));
+    k_cell_data<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, tmp);
+    CK(cudaMemcpyAsync(out, tmp, sizeof(double) * 8 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    cudaFree(tmp);
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_get_flux(ugkwp_ctx* h, double* flux)
+{
+    if (!h || !flux) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    CK(cudaMemcpyAsync(flux, ctx.d.flux, sizeof(double) * 4 * ctx.k.F, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_get_geometry(ugkwp_ctx* h, double* dt, double* vol, int32_t* nfaces, int32_t* nwall)
+{
+    if (!h) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    if (dt) CK(cudaMemcpyAsync(dt, ctx.d.dt, sizeof(double) * ctx.k.C, cudaMemcpyDeviceToHost, ctx.stream));
+    if (vol) CK(cudaMemcpyAsync(vol, ctx.d.vol, sizeof(double) * ctx.k.C, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    if (nfaces) *nfaces = ctx.k.F;
+    if (nwall) *nwall = ctx.k.nwall;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_fixed_exponents(ugkwp_ctx* h, int32_t* out)
+{
+    if (!h || !out) return UGKWP_EINVAL;
+    out[0] = h->c.k.fx0; out[1] = h->c.k.fx1; out[2] = h->c.k.fx4;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_set_profiling(ugkwp_ctx* h, int32_t enable)
+{
+    if (!h) return UGKWP_EINVAL;
+    h->c.profiling = enable ? 1 : 0;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_profile(ugkwp_ctx* h, double* ms, int64_t* steps)
+{
+    if (!h || !ms || !steps) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    CK(cudaStreamSynchronize(ctx.stream));
+    for (int k = 0; k < kStages; ++k) ms[k] = 0.0;
+    const size_t per = kStages + 1, n = ctx.prof_events.size() / per;
+    for (size_t i = 0; i < n; ++i)
+        for (int k = 0; k < kStages; ++k) {
+            float t = 0.0f;
+            CK(cudaEventElapsedTime(&t, ctx.prof_events[i * per + k], ctx.prof_events[i * per + k + 1]));
+            ms[k] += t;
+        }
+    for (cudaEvent_t e : ctx.prof_events) cudaEventDestroy(e);
+    ctx.prof_events.clear();
+    *steps = (int64_t)n;
+    return UGKWP_OK;
+}
+
+const char* ugkwp_last_error(const ugkwp_ctx* h)
+{
+    return h ? h->c.msg.c_str() : "null context";
+}
+
+}  // extern "C"

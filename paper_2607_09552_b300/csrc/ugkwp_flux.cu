@@ -1,0 +1,362 @@
+// Time-averaged wave fluxes of one UGKWP-LTS step (a9), one thread per face.
+//
+//  F = F^eq + F^fr,wave through face j with unit normal n from L to R (Eqs. 40-43):
+//   F^eq: the interface equilibrium g_0 from the half-range moments of the Maxwellians of W_L and W_R
+//     (Eq. 26); its normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on u.n < 0
+//     (Eq. 28 with the Prandtl fix of Sec. 3.1), and A from the compatibility condition (Eq. 31); each half
+//     weighted with its own cell's normalised coefficients dbar_{a,b,c} (Eq. 41).
+//   F^fr,wave: the hydrodynamic wave's Maxwellian g^h of each side over its half, weighted with
+//     dbar_d - e^{-dt/tau} (the part not carried by new particles, Eq. 43); first-order reconstruction, so
+//     the slope term of Eq. 43 vanishes.
+//  Boundary faces (n points out of the fluid cell L): a diffuse wall returns a wall Maxwellian at T_w with
+//  the density that zeroes the wave mass flux; far-field / fixed ghosts carry their full free-transport
+//  part (no particles are injected) and use the fluid cell's time step on both halves (Sec. 4.2); a
+//  symmetry face mirrors L.
+//  The moment algebra is a dense 4x4 closed form per face, so it runs on the FP32/FP64 pipes; faces
+//  flagged face_f64 (next to walls) are always evaluated in FP64.
+#include <cuda_runtime.h>
+#include <cmath>
+#include "ugkwp_internal.h"
+#include "ugkwp_detmath.cuh"
+
+namespace ugk {
+namespace {
+
+template <typename R> struct Prim { R rho, U, V, lam; };
+template <typename R> struct Mom { R up[9], um[9], v[7], xi2, xi4; };
+
+template <typename R> __device__ __forceinline__ bool frame_prim(const R W[4], Prim<R>& p)
+{
+    p.rho = W[0];
+    if (!(W[0] > R(0))) return false;
+    p.U = W[1] / W[0];
+    p.V = W[2] / W[0];
+    const R e = W[3] / W[0] - R(0.5) * (p.U * p.U + p.V * p.V);
+    if (!(e > R(0))) return false;
+    p.lam = R(0.75) / e;
+    return true;
+}
+
+template <typename R> __device__ __forceinline__ void moments(const Prim<R>& p, Mom<R>& M)
+{
+    const R U = p.U, V = p.V, lam = p.lam, th = R(0.5) / lam;
+    const R sl = sqrt(lam);
+    const R ex = exp(-lam * U * U) / (R(2) * sqrt(R(3.14159265358979323846) * lam));
+    M.up[0] = R(0.5) * erfc(-sl * U);
+    M.um[0] = R(0.5) * erfc(sl * U);
+    M.up[1] = U * M.up[0] + ex;
+    M.um[1] = U * M.um[0] - ex;
+#pragma unroll
+    for (int k = 2; k < 9; ++k) {
+        M.up[k] = U * M.up[k - 1] + R(k - 1) * th * M.up[k - 2];
+        M.um[k] = U * M.um[k - 1] + R(k - 1) * th * M.um[k - 2];
+    }
+    M.v[0] = R(1);
+    M.v[1] = V;
+#pragma unroll
+    for (int k = 2; k < 7; ++k) M.v[k] = V * M.v[k - 1] + R(k - 1) * th * M.v[k - 2];
+    M.xi2 = th;
+    M.xi4 = R(3) * th * th;
+}
+
+// <psi u^a v^b w^(2c)>, psi = (1, u, v, |u|^2/2)
+template <typename R>
+__device__ __forceinline__ void psi_mom(const R* Mu, const Mom<R>& M, int a, int b, int c, R o[4])
+{
+    const R w0 = c == 0 ? R(1) : M.xi2, w2 = c == 0 ? M.xi2 : M.xi4;
+    o[0] = Mu[a] * M.v[b] * w0;
+    o[1] = Mu[a + 1] * M.v[b] * w0;
+    o[2] = Mu[a] * M.v[b + 1] * w0;
+    o[3] = R(0.5) * (Mu[a + 2] * M.v[b] * w0 + Mu[a] * M.v[b + 2] * w0 + Mu[a] * M.v[b] * w2);
+}
+
+template <typename R>
+__device__ __forceinline__ void psi_poly(const R* Mu, const Mom<R>& M, int a, int b, const R cf[4], R o[4])
+{
+    R t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
+    psi_mom(Mu, M, a, b, 0, t0);
+    psi_mom(Mu, M, a + 1, b, 0, t1);
+    psi_mom(Mu, M, a, b + 1, 0, t2);
+    psi_mom(Mu, M, a + 2, b, 0, t3);
+    psi_mom(Mu, M, a, b + 2, 0, t4);
+    psi_mom(Mu, M, a, b, 1, t5);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        o[k] = cf[0] * t0[k] + cf[1] * t1[k] + cf[2] * t2[k] + cf[3] * R(0.5) * (t3[k] + t4[k] + t5[k]);
+}
+
+template <typename R> __device__ __forceinline__ void slope(const Prim<R>& p, const R dw[4], R a[4])
+{
+    const R U = p.U, V = p.V, lam = p.lam;
+    const R R4 = R(2) * dw[3] - R(2) * U * dw[1] - R(2) * V * dw[2] + (U * U + V * V) * dw[0] - (R(1.5) / lam) * dw[0];
+    a[3] = (R(4) * lam * lam / R(3)) * R4;
+    a[1] = R(2) * lam * (dw[1] - U * dw[0]) - a[3] * U;
+    a[2] = R(2) * lam * (dw[2] - V * dw[0]) - a[3] * V;
+    a[0] = dw[0] - a[3] * R(0.75) / lam - a[1] * U - a[2] * V - a[3] * R(0.5) * (U * U + V * V);
+}
+
+template <typename R> __device__ __forceinline__ void pr_fix(const Prim<R>& p, R a[4], R Pr)
+{
+    if (Pr == R(1)) return;
+    const R U = p.U, V = p.V, lam = p.lam;
+    const R dlam = R(-0.5) * a[3];
+    const R dU = (a[1] + U * a[3]) / (R(2) * lam), dV = (a[2] + V * a[3]) / (R(2) * lam);
+    const R drho = a[0] - R(1.5) * dlam / lam + dlam * (U * U + V * V) + R(2) * lam * (U * dU + V * dV);
+    const R dl = dlam / Pr;
+    a[3] = R(-2) * dl;
+    a[1] = R(2) * lam * dU + R(2) * U * dl;
+    a[2] = R(2) * lam * dV + R(2) * V * dl;
+    a[0] = drho + R(1.5) * dl / lam - dl * (U * U + V * V) - R(2) * lam * (U * dU + V * dV);
+}
+
+// equilibrium part of Eq. 42 given the interface state W_0 (primitive p0); c[0..2] = dbar_a, dbar_b,
+// dbar_c of each side
+template <typename R>
+__device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], const Prim<R>& p0, const R cL[3],
+                                 const R cR[3], R dL, R dR, R Pr, R F[4])
+{
+    Mom<R> m0;
+    moments(p0, m0);
+    R t1[4], t2[4];
+    R dw[4], aL[4], aR[4], A[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dw[k] = (W0[k] - WL[k]) / (dL * p0.rho);
+    slope(p0, dw, aL);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dw[k] = (WR[k] - W0[k]) / (dR * p0.rho);
+    slope(p0, dw, aR);
+    pr_fix(p0, aL, Pr);
+    pr_fix(p0, aR, Pr);
+    psi_poly(m0.up, m0, 1, 0, aL, t1);
+    psi_poly(m0.um, m0, 1, 0, aR, t2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dw[k] = -(t1[k] + t2[k]);
+    slope(p0, dw, A);
+    R f[4];
+    psi_mom(m0.up, m0, 1, 0, 0, f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = cL[0] * f[k];
+    psi_mom(m0.um, m0, 1, 0, 0, f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] += cR[0] * f[k];
+    psi_poly(m0.up, m0, 2, 0, aL, f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] += cL[1] * f[k];
+    psi_poly(m0.um, m0, 2, 0, aR, f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] += cR[1] * f[k];
+    psi_poly(m0.up, m0, 1, 0, A, f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] += cL[2] * f[k];
+    psi_poly(m0.um, m0, 1, 0, A, f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = p0.rho * (F[k] + cR[2] * f[k]);
+}
+
+// interior-type face; frL/frR weight each side's g^h. Returns false if a side state is not a valid
+// Maxwellian in precision R (the caller then uses FP64).
+template <typename R>
+__device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], bool hL, bool hR,
+                          const R cL[3], const R cR[3], R frL, R frR, R dL, R dR, R Pr, R F[4])
+{
+    Prim<R> pL, pR, p0;
+    Mom<R> mL, mR;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = R(0);
+    if (!frame_prim(WL, pL) || !frame_prim(WR, pR)) return false;
+    moments(pL, mL);
+    moments(pR, mR);
+    R t1[4], t2[4], W0[4];
+    psi_mom(mL.up, mL, 0, 0, 0, t1);
+    psi_mom(mR.um, mR, 0, 0, 0, t2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];
+    // vacuum interface: no molecule of either side reaches the face, no equilibrium flux
+    if (frame_prim(W0, p0)) equilibrium_part(W0, WL, WR, p0, cL, cR, dL, dR, Pr, F);
+    R f[4];
+    Prim<R> ph;
+    Mom<R> mh;
+    if (hL && frame_prim(WhL, ph)) {
+        moments(ph, mh);
+        psi_mom(mh.up, mh, 1, 0, 0, f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) F[k] += frL * ph.rho * f[k];
+    }
+    if (hR && frame_prim(WhR, ph)) {
+        moments(ph, mh);
+        psi_mom(mh.um, mh, 1, 0, 0, f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) F[k] += frR * ph.rho * f[k];
+    }
+    return true;
+}
+
+template <typename R>
+__device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, R caL, R frL, R lam_w, R F[4])
+{
+    Prim<R> p;
+    Mom<R> m;
+    R t[4];
+    if (!frame_prim(WL, p)) return false;
+    moments(p, m);
+    psi_mom(m.up, m, 1, 0, 0, t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = caL * p.rho * t[k];
+    if (hL && frame_prim(WhL, p)) {
+        moments(p, m);
+        psi_mom(m.up, m, 1, 0, 0, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) F[k] += frL * p.rho * t[k];
+    }
+    p.rho = R(1); p.U = R(0); p.V = R(0); p.lam = lam_w;
+    moments(p, m);
+    psi_mom(m.um, m, 1, 0, 0, t);
+    const R rw = -F[0] / t[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] += rw * t[k];
+    return true;
+}
+
+// Taylor weights of phi1, psi2, psi3, beta (see the cell decomposition), k = 0..19
+constexpr int kSeriesF = 20;
+__constant__ double c_series_f[4][kSeriesF];
+
+// normalised coefficients (dbar_a, dbar_b, dbar_c, dbar_d) of a ghost side (Eq. 41), FP64
+__device__ void ghost_coeffs(double dt, double tau, double c[4])
+{
+    const double x = dt / tau;
+    const double e = dexp(-x);
+    double phi1, psi2, psi3, beta;
+    if (x < 1.0) {
+        const double mx = -x;
+        phi1 = psi2 = psi3 = beta = 0.0;
+#pragma unroll
+        for (int k = kSeriesF - 1; k >= 0; --k) {
+            phi1 = fma(mx, phi1, c_series_f[0][k]);
+            psi2 = fma(mx, psi2, c_series_f[1][k]);
+            psi3 = fma(mx, psi3, c_series_f[2][k]);
+            beta = fma(mx, beta, c_series_f[3][k]);
+        }
+    } else {
+        phi1 = (1.0 - e) / x;
+        psi2 = (e - 1.0 + x) / (x * x);
+        psi3 = (0.5 * x * x - x + 1.0 - e) / (x * x * x);
+        beta = (1.0 + e - 2.0 * phi1) / (x * x);
+    }
+    c[0] = x * psi2;
+    c[1] = -dt * x * beta;
+    c[2] = dt * x * psi3;
+    c[3] = phi1;
+}
+
+__device__ double tau_of(const StepConsts& K, const double W[4])
+{
+    const double rho = W[0], U = W[1] / rho, V = W[2] / rho;
+    const double RT = (W[3] / rho - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+    const double mu = K.mu_inf * dpow(RT / kR, K.omega);
+    return mu / (rho * RT);
+}
+
+template <typename R>
+__device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4])
+{
+    const int L = c.fL[f], Rc = c.fR[f], bc = c.fbc[f];
+    const double nx = c.fnx[f], ny = c.fny[f];
+    const R nxr = R(nx), nyr = R(ny);
+    auto rot = [&](const double* W, R o[4]) {
+        const R a = R(W[1]), b = R(W[2]);
+        o[0] = R(W[0]);
+        o[1] = a * nxr + b * nyr;
+        o[2] = -a * nyr + b * nxr;
+        o[3] = R(W[3]);
+    };
+    R WL[4], WhL[4], WR[4], WhR[4], F[4];
+    bool ok;
+    rot(c.W + 4 * L, WL);
+    rot(c.Wh + 4 * L, WhL);
+    const double* coL = c.co + 7 * L;
+    const R cL[3] = {R(coL[0]), R(coL[1]), R(coL[2])};
+    const R frL = R(K.wave_only ? coL[3] : coL[5]);
+    const bool hL = c.hphys[L] != 0;
+    if (bc == 0 || bc == UGKWP_BC_PERIODIC) {
+        rot(c.W + 4 * Rc, WR);
+        rot(c.Wh + 4 * Rc, WhR);
+        const double* coR = c.co + 7 * Rc;
+        const R cR[3] = {R(coR[0]), R(coR[1]), R(coR[2])};
+        const R frR = R(K.wave_only ? coR[3] : coR[5]);
+        ok = face_flux<R>(WL, WR, WhL, WhR, hL, c.hphys[Rc] != 0, cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]),
+                          R(K.Pr), F);
+    } else if (bc == UGKWP_BC_WALL) {
+        ok = wall_flux<R>(WL, WhL, hL, cL[0], frL, R(0.5 / (kR * K.Tw)), F);
+    } else if (bc == UGKWP_BC_SYMMETRY) {
+        const R Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
+        ok = face_flux<R>(WL, Wm, WhL, Whm, hL, hL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
+    } else {
+        double Wg[4];
+        if (bc == UGKWP_BC_FIXED) {
+            for (int k = 0; k < 4; ++k) Wg[k] = K.W_fix[k];
+        } else {
+            const double un = K.W_inf[1] * nx + K.W_inf[2] * ny;
+            const double* src = un < 0.0 ? K.W_inf : c.W + 4 * L;
+            for (int k = 0; k < 4; ++k) Wg[k] = src[k];
+        }
+        rot(Wg, WR);
+        double cg[4];
+        ghost_coeffs(c.dt[L], tau_of(K, Wg), cg);
+        const R cR[3] = {R(cg[0]), R(cg[1]), R(cg[2])};
+        ok = face_flux<R>(WL, WR, WhL, WR, hL, true, cL, cR, frL, R(cg[3]), R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
+    }
+    out[0] = double(F[0]);
+    out[1] = double(F[1] * nxr - F[2] * nyr);
+    out[2] = double(F[1] * nyr + F[2] * nxr);
+    out[3] = double(F[3]);
+    return ok && isfinite(out[0]) && isfinite(out[1]) && isfinite(out[2]) && isfinite(out[3]);
+}
+
+__device__ __forceinline__ void store_flux(const Dev& c, int f, const double out[4])
+{
+    double2* o = reinterpret_cast<double2*>(c.flux + 4 * (size_t)f);
+    o[0] = make_double2(out[0], out[1]);
+    o[1] = make_double2(out[2], out[3]);
+}
+
+// interior faces in FP32 (production mode); a face whose FP32 evaluation under- or overflows (near-vacuum
+// neighbours with extreme moments) is queued for the FP64 kernel
+__global__ void __launch_bounds__(128) k_wave_flux32(const StepConsts K, const Dev c)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= K.F || c.face_f64[f]) return;
+    double out[4];
+    if (one_face<float>(K, c, f, out)) store_flux(c, f, out);
+    else c.retry[atomicAdd(c.nretry, 1)] = f;
+}
+
+// FP64 faces: the static list (faces of wall cells; every face in the FP64 mode), then the faces queued by
+// the FP32 kernel. FP64 throughput per SM is small on this part, so consecutive faces go to different blocks
+// (and SMs): face j is taken by lane j / gridDim of block j % gridDim.
+__global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c)
+{
+    const int n = K.n_f64 + *c.nretry;
+    for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int f = j < K.n_f64 ? c.f64list[j] : c.retry[j - K.n_f64];
+        double out[4];
+        one_face<double>(K, c, f, out);
+        store_flux(c, f, out);
+    }
+}
+
+}  // namespace
+
+void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s)
+{
+    if (k.prec == 0) k_wave_flux32<<<(k.F + 127) / 128, 128, 0, s>>>(k, d);
+    const int blocks = k.prec == 0 ? 2 * sms : (k.F + 31) / 32;
+    k_wave_flux64<<<blocks, 32, 0, s>>>(k, d);
+}
+
+cudaError_t flux_set_tables(const double* tab, cudaStream_t s)
+{
+    return cudaMemcpyToSymbolAsync(c_series_f, tab, sizeof(double) * 4 * kSeriesF, 0, cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace ugk

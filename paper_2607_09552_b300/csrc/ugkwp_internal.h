@@ -1,0 +1,112 @@
+// Internal layout of a UGKWP-LTS context on the device. Shared by the translation units of libugkwp.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include "../../include/ugkwp.h"
+
+namespace ugk {
+
+constexpr int kMaxIters = 256;   // face crossings + wall hits per particle per step
+constexpr int kMaxNew = 2047;    // new particles per cell per step (11-bit index inside the particle id)
+constexpr double kR = 0.5;       // gas constant in the reference units
+constexpr double kRhoFloor = 1e-12;   // vacuum floor of the cell density (units of rho_inf)
+
+// device error word bits
+enum : int { ERR_LIMIT = 1, ERR_NONPHYS = 2, ERR_OVERFLOW = 4, ERR_CAPACITY = 8 };
+
+// Per-cell face table used by the particle kernels: outward normal, plane offset (n.x <= d inside),
+// dt_neighbour / dt_cell, and a packed word: face id (bits 0-23), local index of the face in the
+// neighbour (24-25), boundary tag (26-28), 1 if the cell is the face's L side (bit 29). nbr < 0 on a
+// boundary face.
+template <typename T> struct alignas(16) CellFaces {
+    T nx[4], ny[4], d[4], ratio[4];
+    int nbr[4], meta[4];
+};
+
+template <typename T> struct ParticleSoA {
+    T *x, *y, *u, *v, *w, *m;
+    int32_t* cell;
+    uint64_t* pid;
+};
+
+// fixed-size description of the per-step kernels' inputs (passed by value)
+struct StepConsts {
+    int C, F, dim, nwall, n_ref, wave_only, prec;
+    int fx0, fx1, fx4;              // fixed-point exponents: mass, momentum, energy
+    int n_f64, sort_every;          // faces in f64list; counting sort of the particles every sort_every steps
+    double mu_inf, omega, Pr, Tw, U_inf, m2RTw, sig_w;
+    double T_cap, U_cap, T_min;     // realizability bounds of a cell state
+    double W_inf[4], W_fix[4];
+    uint32_t k0, k1;                // Philox key
+};
+
+// all device pointers of a context (trivially copyable: passed to kernels by value)
+struct Dev {
+    // geometry
+    double *vol, *xc, *yc, *dt;
+    int* nfc;
+    CellFaces<float>* cf32;
+    CellFaces<double>* cf64;
+    double* cshift;                    // [4C] periodic shift (1-D)
+    double *cvx, *cvy;                 // [4C] vertices
+    int *fL, *fR, *fbc, *fwall, *wall_face;
+    double *fnx, *fny, *fs, *fdL, *fdR;
+    int* face_f64;                     // 1: evaluate this face's flux in FP64 (production mode)
+    // state
+    double* W;                         // [4C]
+    long long *wrt, *wprev, *wm, *wpl; // [5C]
+    unsigned int* cross;               // [2F]
+    long long* wallt;                  // [3 nwall]
+    // per-step cell data
+    double *tau, *xr, *emx, *Wh, *co, *mnew;
+    double* samp;                      // [3C] U^h, V^h, R T^h
+    int *hphys, *nhp, *nhp_off, *cnt, *off, *cur;
+    int* scan_tmp;
+    double* flux;                      // [4F]
+    double *res_part, *res;            // residual: per-block partials; [8] = raw of this step, first step's
+    double* chi_ema;
+    double *surf_sum, *surf_last;      // [3 nwall]
+    // particles: A holds the cell-sorted retained set between steps, B is the staging buffer
+    ParticleSoA<float> pa32, pb32;
+    ParticleSoA<double> pa64, pb64;
+    float *tau32, *dt32, *mnew32, *samp32;   // particle-precision copies of tau, dt, m_new, (U^h, V^h, R T^h)
+    long long* dstep;                  // step counter (Philox counter word)
+    int* bufsel;                       // which particle buffer (A: 0, B: 1) holds the current particles
+    int* flags;                        // [0]: this step sorts the particles by cell
+    int *nretry, *retry;               // faces whose FP32 flux failed this step (re-evaluated in FP64)
+    int* f64list;                      // faces always evaluated in FP64
+    unsigned int* done;                // blocks of k_update finished (last-block reduction)
+    int* counts;                       // [0] retained, [1] new this step, [2] kept after the step, [3] capacity
+    unsigned long long* stats;         // [0..7] per step (see ugkwp_stats), [8] surface samples,
+                                       // [9] cumulative particle-steps, [10] cumulative new particles,
+                                       // [11] cells set to the vacuum floor in the last step
+    int* err;
+};
+
+struct Ctx {
+    StepConsts k{};
+    Dev d{};
+    int ni = 0, nj = 0, periodic_j = 0, capacity = 0, res_blocks = 0, grid_particles = 0, sms = 148;
+    cudaStream_t stream = nullptr;
+    int64_t step = 0;
+    int use_graph = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::string msg;
+    std::vector<void*> allocs;
+    int profiling = 0;
+    std::vector<cudaEvent_t> prof_events;   // kStages + 1 per profiled step, in stream order
+};
+
+constexpr int kStages = 6;   // decompose+scan, sample, particles, wave flux, sort, update+surface+close
+
+// launchers implemented in ugkwp_flux.cu
+void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s);
+cudaError_t flux_set_tables(const double* tab, cudaStream_t s);   // [4][20]: phi1, psi2, psi3, beta weights
+
+}  // namespace ugk
+
+struct ugkwp_ctx {
+    ugk::Ctx c;
+};

@@ -1,0 +1,212 @@
+"""Thin ctypes binding of libugkwp.so (include/ugkwp.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module only converts numpy arrays and
+Python scalars to the C ABI. Importing it loads the in-tree library and raises if it is missing or was
+built without a usable CUDA device; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libugkwp.so")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ELIMIT", 5: "ENONPHYS", 6: "EOVERFLOW"}
+LTS, GTS = 0, 1
+
+# every entry point declared in include/ugkwp.h
+EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugkwp_surface", "ugkwp_reset_surface",
+           "ugkwp_set_field", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
+           "ugkwp_set_state", "ugkwp_get_tallies", "ugkwp_get_cell_data", "ugkwp_get_flux", "ugkwp_get_geometry",
+           "ugkwp_fixed_exponents", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_last_error"]
+STAGES = ["decompose", "sample", "particles", "wave_flux", "sort", "update"]
+
+
+class UgkwpMesh(C.Structure):
+    _fields_ = [("ni", C.c_int32), ("nj", C.c_int32), ("dim", C.c_int32), ("periodic_j", C.c_int32),
+                ("xv", C.POINTER(C.c_double)), ("yv", C.POINTER(C.c_double)),
+                ("bc_imin", C.POINTER(C.c_int32)), ("bc_imax", C.POINTER(C.c_int32)),
+                ("bc_jmin", C.POINTER(C.c_int32)), ("bc_jmax", C.POINTER(C.c_int32))]
+
+
+class UgkwpGas(C.Structure):
+    _fields_ = [("omega", C.c_double), ("Pr", C.c_double)]
+
+
+class UgkwpOpts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("case_id", C.c_uint32), ("n_ref", C.c_int32), ("precision", C.c_int32),
+                ("wave_only", C.c_int32), ("record_faces", C.c_int32), ("capacity", C.c_int32),
+                ("ghost_state", C.c_double * 4), ("stream", C.c_void_p), ("use_graph", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libugkwp.so from the package directory (raises if it is absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2607_09552_b300.build`")
+        lib = C.CDLL(LIB_PATH)
+        lib.ugkwp_last_error.restype = C.c_char_p
+        lib.ugkwp_num_particles.restype = C.c_int64
+        lib.ugkwp_destroy.restype = None
+        _lib = lib
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def _d(a):
+    return _p(a, C.c_double)
+
+
+class UgkwpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Solver:
+    """One UGKWP-LTS context on the current CUDA device for a workload `Case`."""
+
+    def __init__(self, case, gts: bool = False, precision: int = 0, wave_only: bool = False, seed: int | None = None,
+                 case_id: int = 0, capacity: int = 0, use_graph: bool = False, stream=None):
+        L = load()
+        m = case.mesh
+        self._keep = [np.ascontiguousarray(m.xv, dtype=np.float64), np.ascontiguousarray(m.yv, dtype=np.float64)]
+        self._keep += [np.ascontiguousarray(a, dtype=np.int32) for a in (m.bc_imin, m.bc_imax, m.bc_jmin, m.bc_jmax)]
+        mesh = UgkwpMesh(m.ni, m.nj, m.dim, m.periodic_j, _d(self._keep[0]), _d(self._keep[1]),
+                         *[_p(a, C.c_int32) for a in self._keep[2:]])
+        gas = UgkwpGas(case.omega, case.Pr)
+        opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only), 0,
+                         capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream), int(use_graph), 0)
+        self.ctx = C.c_void_p()
+        st = L.ugkwp_create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
+                            C.c_double(case.Tw), C.c_double(case.cfl), C.c_int32(GTS if gts else LTS), C.byref(opts),
+                            C.byref(self.ctx))
+        if st != 0:
+            msg = L.ugkwp_last_error(self.ctx).decode() if self.ctx else ""
+            if self.ctx:
+                L.ugkwp_destroy(self.ctx)
+                self.ctx = None
+            raise UgkwpError(st, f"ugkwp_create: {msg}")
+        self.C = m.ni * m.nj
+        nf, nw = C.c_int32(), C.c_int32()
+        self._check(L.ugkwp_get_geometry(self.ctx, None, None, C.byref(nf), C.byref(nw)))
+        self.F, self.nwall = nf.value, nw.value
+        fx = (C.c_int32 * 3)()
+        self._check(L.ugkwp_fixed_exponents(self.ctx, fx))
+        self.fx = list(fx)
+        if case.init_prim is not None:
+            self.set_field(case.init_prim)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().ugkwp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, st):
+        if st != 0:
+            raise UgkwpError(st, load().ugkwp_last_error(self.ctx).decode())
+
+    def step(self, n: int = 1):
+        self._check(load().ugkwp_step(self.ctx, C.c_int32(n)))
+
+    def set_field(self, prim):
+        a = np.ascontiguousarray(prim, dtype=np.float64).reshape(-1)
+        self._check(load().ugkwp_set_field(self.ctx, _d(a)))
+
+    def field(self):
+        W = np.zeros(4 * self.C)
+        Wp = np.zeros(4 * self.C)
+        self._check(load().ugkwp_get_field(self.ctx, _d(W), _d(Wp)))
+        return W.reshape(self.C, 4), Wp.reshape(self.C, 4)
+
+    def residual(self):
+        out = np.zeros(8)
+        self._check(load().ugkwp_residual(self.ctx, _d(out)))
+        return out
+
+    def surface(self, averaged: bool = True):
+        p, t, q = (np.zeros(max(self.nwall, 1)) for _ in range(3))
+        self._check(load().ugkwp_surface(self.ctx, _d(p), _d(t), _d(q), C.c_int32(self.nwall), C.c_int32(int(averaged))))
+        return p[:self.nwall], t[:self.nwall], q[:self.nwall]
+
+    def reset_surface(self):
+        self._check(load().ugkwp_reset_surface(self.ctx))
+
+    def stats(self):
+        """[steps, particles, new, removed, left, crossings, wall hits, max iterations, cumulative
+        particle-steps, cumulative new particles, cells floored in the last step]"""
+        out = np.zeros(11, dtype=np.int64)
+        self._check(load().ugkwp_stats(self.ctx, _p(out, C.c_int64)))
+        return out
+
+    def set_profiling(self, on: bool):
+        self._check(load().ugkwp_set_profiling(self.ctx, C.c_int32(int(on))))
+
+    def profile(self):
+        """(per-stage milliseconds summed over the profiled steps, number of profiled steps)"""
+        ms = np.zeros(8)
+        n = C.c_int64()
+        self._check(load().ugkwp_profile(self.ctx, _d(ms), C.byref(n)))
+        return dict(zip(STAGES, ms[:6])), n.value
+
+    def num_particles(self) -> int:
+        return int(load().ugkwp_num_particles(self.ctx))
+
+    def geometry(self):
+        dt = np.zeros(self.C)
+        vol = np.zeros(self.C)
+        self._check(load().ugkwp_get_geometry(self.ctx, _d(dt), _d(vol), None, None))
+        return dt, vol
+
+    def particles(self):
+        n = self.num_particles()
+        pid = np.zeros(max(n, 1), dtype=np.uint64)
+        cell = np.zeros(max(n, 1), dtype=np.int32)
+        f = [np.zeros(max(n, 1)) for _ in range(6)]
+        self._check(load().ugkwp_get_particles(self.ctx, C.c_int64(n), _p(pid, C.c_uint64), _p(cell, C.c_int32),
+                                               *[_d(a) for a in f]))
+        return dict(pid=pid[:n], cell=cell[:n], x=f[0][:n], y=f[1][:n], u=f[2][:n], v=f[3][:n], w=f[4][:n],
+                    m=f[5][:n])
+
+    def set_state(self, step, W, wret, parts):
+        W = np.ascontiguousarray(W, dtype=np.float64).reshape(-1)
+        wret = np.ascontiguousarray(wret, dtype=np.int64).reshape(-1)
+        n = len(parts["pid"])
+        arrs = [np.ascontiguousarray(parts[k], dtype=np.float64) for k in ("x", "y", "u", "v", "w", "m")]
+        pid = np.ascontiguousarray(parts["pid"], dtype=np.uint64)
+        cell = np.ascontiguousarray(parts["cell"], dtype=np.int32)
+        self._check(load().ugkwp_set_state(self.ctx, C.c_int64(step), _d(W), _p(wret, C.c_int64), C.c_int64(n),
+                                           _p(pid, C.c_uint64), _p(cell, C.c_int32), *[_d(a) for a in arrs]))
+
+    def tallies(self):
+        wm, wpl, wret = (np.zeros(5 * self.C, dtype=np.int64) for _ in range(3))
+        cross = np.zeros(2 * self.F, dtype=np.int64)
+        wall = np.zeros(max(3 * self.nwall, 1), dtype=np.int64)
+        self._check(load().ugkwp_get_tallies(self.ctx, _p(wm, C.c_int64), _p(wpl, C.c_int64), _p(wret, C.c_int64),
+                                             _p(cross, C.c_int64), _p(wall, C.c_int64), None))
+        return dict(wm=wm.reshape(self.C, 5), wpl=wpl.reshape(self.C, 5), wret=wret.reshape(self.C, 5),
+                    cross=cross.reshape(self.F, 2), wall=wall[:3 * self.nwall].reshape(self.nwall, 3))
+
+    def cell_data(self):
+        out = np.zeros(8 * self.C)
+        self._check(load().ugkwp_get_cell_data(self.ctx, _d(out)))
+        return out.reshape(self.C, 8)
+
+    def flux(self):
+        out = np.zeros(4 * self.F)
+        self._check(load().ugkwp_get_flux(self.ctx, _d(out)))
+        return out.reshape(self.F, 4)
