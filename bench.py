@@ -24,6 +24,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -132,7 +133,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) if rank == 0 else None
+    clocks = Clocks(local, os.path.join(tempfile.gettempdir(), f"ugkwp_clocks_rank{rank}_{os.getpid()}.csv")) \
+        if rank == 0 else None
     time.sleep(0.5)
     t_epoch0 = time.time()
     t_wall = time.perf_counter()
@@ -152,14 +154,7 @@ def run_ours(args):
     s1 = solver.stats()
     psteps = int(s1[8] - s0[8])
     ncells_steps = case.mesh.ncells * args.steps
-    t = torch.tensor([ms, float(psteps)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        ms_all, ps_all = float(tmax[0]), float(t[1])
-    else:
-        ms_all, ps_all = ms, float(psteps)
+    ms_all, ps_all = reduce_over_ranks(ms, float(psteps), world, "cuda")
     e2e = run_e2e(args, solver, stream) if rank == 0 and not args.no_e2e else None
     if rank == 0:
         peaks, which = _peaks()
@@ -198,10 +193,24 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def reduce_over_ranks(ms: float, work: float, world: int, device: str):
+    """Job time = max over ranks of the timed milliseconds; job work = sum over ranks (independent replicas,
+    no data-path collective: this is the only cross-rank communication)."""
+    if world <= 1:
+        return ms, work
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    w = torch.tensor([work], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(w[0])
+
+
 def gpu_launches_per_step(case):
-    # decompose, 3 scan kernels, capacity check, sample, particles, wave flux, update, 3 scan kernels,
-    # scatter, surface (wall cases), finish
-    return 14 + (1 if case.mesh.bc_imin[0] == wl.BC_WALL else 0)
+    # begin-step, decompose, 3 scan kernels, sample, particles, 2 wave-flux kernels, 3 scan kernels and the
+    # scatter (they return at once except on sort steps), update
+    return 13
 
 
 def run_e2e(args, solver, stream):
@@ -281,6 +290,131 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def stagnation_pair(case):
+    """Wall-face indices adjacent to theta = pi (the stagnation point of the +x freestream on the O-mesh)."""
+    nj = case.mesh.nj
+    return nj // 2 - 1, nj // 2
+
+
+def steady_step(hist, alpha=2.0 / 1001.0, tol=0.01, window=0.2):
+    """First step after which the EMA (alpha = 2/1001) of a monitored history stays within tol of the mean
+    of its final window (fraction `window` of the run)."""
+    h = np.asarray(hist, dtype=np.float64)
+    ema = np.empty_like(h)
+    e = h[0]
+    for k, v in enumerate(h):
+        e = e + alpha * (v - e) if k else v
+        ema[k] = e
+    ref = ema[int(len(h) * (1 - window)):].mean()
+    bad = np.nonzero(np.abs(ema - ref) > tol * abs(ref))[0]
+    return int(bad[-1] + 1) if bad.size else 0, ema
+
+
+def run_convergence(args):
+    """Steps and wall-clock to convergence, LTS vs GTS, on the bench workload (and the dense-regime
+    cylinder with --case kn001): (i) the deterministic particle-free mode (GKS limit) to a 1e-6 residual;
+    (ii) the full stochastic method to "steady" by the EMA of the stagnation-point pressure and heat flux."""
+    import torch
+    from paper_2607_09552_b300 import ugkwp
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    case = wl.case_cylinder_kn001() if args.case == "kn001" else bench_case()
+    out = {"mode": "convergence", "workload": config_dict(case, 0, "n/a")["workload"] if args.case != "kn001" else
+           "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8", "results": {}}
+    for ts in ("LTS", "GTS"):
+        gts = ts == "GTS"
+        r = {}
+        # (i) particle-free, to 1e-6 in every conservative component (checked every 200 steps)
+        s = ugkwp.Solver(case, gts=gts, precision=0, wave_only=True, stream=stream.cuda_stream, use_graph=True)
+        t0 = time.perf_counter()
+        steps, res = 0, 1.0
+        while steps < args.max_wave_steps:
+            s.step(200)
+            steps += 200
+            res = float(np.max(s.residual()[:4]))
+            if res < 1e-6:
+                break
+        r["wave_only_steps_to_1e-6"] = steps if res < 1e-6 else None
+        r["wave_only_wall_s"] = time.perf_counter() - t0
+        r["wave_only_final_residual"] = res
+        s.close()
+        # (ii) stochastic: stagnation p and q per step, steady by EMA
+        n = args.lts_steps if not gts else args.gts_steps
+        s = ugkwp.Solver(case, gts=gts, precision=0, stream=stream.cuda_stream, use_graph=True)
+        j0, j1 = stagnation_pair(case)
+        hp, hq, hres, hnp = [], [], [], []
+        t0 = time.perf_counter()
+        for k in range(n):
+            s.step(1)
+            p, _, q = s.surface(averaged=False)
+            hp.append(0.5 * (p[j0] + p[j1]))
+            hq.append(0.5 * (q[j0] + q[j1]))
+            if k % 50 == 0:
+                hres.append(float(np.max(s.residual()[:4])))
+                hnp.append(s.num_particles())
+        wall = time.perf_counter() - t0
+        kp, _ = steady_step(hp)
+        kq, _ = steady_step(hq)
+        k_st = max(kp, kq)
+        U = wl.freestream_speed(case.Ma)
+        r.update({"stochastic_steps_run": n, "steps_to_steady": k_st, "wall_s_run": wall,
+                  "wall_s_to_steady_est": wall * k_st / n, "ms_per_step": 1e3 * wall / n,
+                  "residual_plateau": float(np.median(hres[len(hres) // 2:])),
+                  "particles_mean": float(np.mean(hnp[len(hnp) // 2:])),
+                  "stagnation_Cp": float((np.mean(hp[-n // 5:]) - 0.5) / (0.5 * U * U)),
+                  "stagnation_CQ": float(np.mean(hq[-n // 5:]) / (0.5 * U ** 3))})
+        s.close()
+        out["results"][ts] = r
+    L, G = out["results"]["LTS"], out["results"]["GTS"]
+    if L["wave_only_steps_to_1e-6"] and G["wave_only_steps_to_1e-6"]:
+        out["wave_only_speedup_steps"] = G["wave_only_steps_to_1e-6"] / L["wave_only_steps_to_1e-6"]
+        out["wave_only_speedup_wall"] = G["wave_only_wall_s"] / L["wave_only_wall_s"]
+    if L["steps_to_steady"]:
+        out["stochastic_speedup_steps"] = G["steps_to_steady"] / max(L["steps_to_steady"], 1)
+        out["stochastic_speedup_wall"] = G["wall_s_to_steady_est"] / max(L["wall_s_to_steady_est"], 1e-9)
+    print(json.dumps(out))
+
+
+def run_batch(args):
+    """The seeded 16-case sweep (cylinders and plates, Kn, Ma, T_w drawn from seed 0) advanced by one graph
+    launch per step, against the same cases stepped one after another (each with its own graph)."""
+    import torch
+    from paper_2607_09552_b300 import ugkwp
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    cases = wl.batch_sweep(0, scale=args.batch_scale)
+    solvers = [ugkwp.Solver(c, precision=0, stream=stream.cuda_stream, use_graph=True) for c in cases]
+    for s in solvers:
+        s.step(args.burn)
+    torch.cuda.synchronize()
+    b = ugkwp.Batch(solvers, stream=stream.cuda_stream)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    p0 = sum(int(s.stats()[8]) for s in solvers)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    p1 = sum(int(s.stats()[8]) for s in solvers)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for s in solvers:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    p2 = sum(int(s.stats()[8]) for s in solvers)
+    b.close()
+    out = {"mode": "batch", "cases": [{"name": c.name, "Kn": c.Kn, "Ma": c.Ma, "Tw": c.Tw, "n_ref": c.n_ref,
+                                       "particles": s.num_particles()} for c, s in zip(cases, solvers)],
+           "steps": args.steps, "batched_particle_steps_per_s": (p1 - p0) / (ms_b * 1e-3),
+           "sequential_particle_steps_per_s": (p2 - p1) / (ms_s * 1e-3),
+           "batched_ms_per_step": ms_b / args.steps, "sequential_ms_per_step": ms_s / args.steps}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,12 +425,21 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch"])
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--case", default="kn01", choices=["kn01", "kn001"])
+    ap.add_argument("--max-wave-steps", type=int, default=400000)
+    ap.add_argument("--lts-steps", type=int, default=12000)
+    ap.add_argument("--gts-steps", type=int, default=40000)
     args = ap.parse_args()
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "convergence":
+        run_convergence(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -1,17 +1,17 @@
 /* UGKWP-LTS steady-iteration step on one B300 GPU: C ABI of libugkwp.so.
  *
  * One step (ugkwp_step) runs, in hand-written sm_103a CUDA kernels on the context's stream:
- *   decomposition W = W^h + W^p and the collisionless fraction e^{-dt_i/tau_i}    (Sec. 3.2, Sec. 4.2)
- *   re-sampling of the hydrodynamic part as new particles                          (Eqs. 16-17, Sec. 4.2)
- *   free-flight times t_f = min(-tau_i ln eps, dt_i)                                (Eq. 18, Sec. 4.2)
+ *   decomposition W = W^h + W^p and the collisionless fraction e^{-dt_i/tau_i}    (Sec. III B, Sec. IV B)
+ *   re-sampling of the hydrodynamic part as new particles                          (Eqs. 25-26, Sec. IV B)
+ *   free-flight times t_f = min(-tau_i ln eps, dt_i)                                (Eq. 27, Sec. IV B)
  *   free transport; at every face crossing L -> R the particle mass and its remaining free-transport time
- *     are multiplied by dt_R / dt_L                                                (Eqs. 19, 37, 45)
- *   before/after particle tallies W^{fr,p} = W^{p,+} - W^{p,-}, removal of collided particles (Eqs. 20-21)
+ *     are multiplied by dt_R / dt_L                                                (Eqs. 28, 41, 52)
+ *   before/after particle tallies W^{fr,p} = W^{p,+} - W^{p,-}, removal of collided particles (Eqs. 29-30)
  *   time-averaged equilibrium and free-transport wave fluxes with side-normalised coefficients
- *                                                                                   (Eqs. 14, 26-31, 40-43)
- *   the conservative update W^{n+1} = W^n - dt_i/Omega_i sum_j F_j s_j + W^{fr,p}  (Eq. 46)
- *   wall pressure, shear stress and heat flux                                       (Sec. 5.1)
- * Local time steps come from the CFL condition on the initial freestream field and stay fixed (Eqs. 24-25);
+ *                                                                                   (Eqs. 16, 17-22, 47-50)
+ *   the conservative update W^{n+1} = W^n - dt_i/Omega_i sum_j F_j s_j + W^{fr,p}  (Eq. 53)
+ *   wall pressure, shear stress and heat flux                                       (Sec. V A)
+ * Local time steps come from the CFL condition on the initial freestream field and stay fixed (Eqs. 33-34);
  * GTS mode gives every cell the global minimum.
  *
  * Conventions.
@@ -75,7 +75,7 @@ typedef struct { double omega, Pr; } ugkwp_gas;
 typedef struct {
     uint64_t seed;            /* Philox key (low word xor case_id, high word) */
     uint32_t case_id;
-    int32_t n_ref;            /* reference particles per cell, N_ref of Eq. 17 */
+    int32_t n_ref;            /* reference particles per cell, N_ref of Eq. 26 */
     int32_t precision;        /* 0: FP32 particles, FP32 interior wave fluxes, FP64 cell update and wall
                                  fluxes; 1: everything FP64 */
     int32_t wave_only;        /* 1: no particles (GKS limit, deterministic) */
@@ -87,9 +87,9 @@ typedef struct {
     int32_t reserved;
 } ugkwp_opts;
 
-/* Build the context: geometry, fixed local time steps (Eqs. 24-25), uniform freestream state, no
+/* Build the context: geometry, fixed local time steps (Eqs. 33-34), uniform freestream state, no
  * particles. Kn is the freestream mean free path over the mesh's length unit (VHS); Ma the freestream
- * Mach number along +x; Tw the wall temperature over T_inf; cfl the CFL number N_CFL of Eq. 24. */
+ * Mach number along +x; Tw the wall temperature over T_inf; cfl the CFL number N_CFL of Eq. 33. */
 ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double Kn, double Ma, double Tw,
                           double cfl, ugkwp_tstep mode, const ugkwp_opts* opts, ugkwp_ctx** out);
 void ugkwp_destroy(ugkwp_ctx* ctx);
@@ -147,6 +147,23 @@ ugkwp_status ugkwp_get_flux(ugkwp_ctx* ctx, double* flux);
 ugkwp_status ugkwp_get_geometry(ugkwp_ctx* ctx, double* dt, double* vol, int32_t* nfaces, int32_t* nwall);
 /* Fixed-point exponents F of the mass, momentum and energy tallies: value = integer * 2^-F. */
 ugkwp_status ugkwp_fixed_exponents(ugkwp_ctx* ctx, int32_t* out);
+/* Batched launch: one CUDA graph that advances every listed context by one step per launch, each case's
+ * kernels on streams of their own so that the cases' (latency-bound) kernels overlap on the GPU. The
+ * contexts must be distinct, on the current device, and stay alive while the batch exists; their own
+ * streams are ordered before and after each ugkwp_batch_step. `stream` (nullable) is the stream the graph
+ * is launched on. Cases may differ in mesh, gas, Kn, Ma, T_w, mode and particle count. */
+typedef struct ugkwp_batch ugkwp_batch;
+ugkwp_status ugkwp_batch_create(ugkwp_ctx* const* ctxs, int32_t n, void* stream, ugkwp_batch** out);
+ugkwp_status ugkwp_batch_step(ugkwp_batch* batch, int32_t n_steps);
+void ugkwp_batch_destroy(ugkwp_batch* batch);
+
+/* Checkpoint: the whole state (step counter, W, retained tally, particles, residual normalisation,
+ * particle-mass-ratio EMA, surface sums and counters) to a binary file, and back into a context created
+ * with the same mesh, gas, mode and precision. Steps after ugkwp_load reproduce the uninterrupted run
+ * (the particle draws are keyed by particle id and step). Both synchronise. */
+ugkwp_status ugkwp_save(ugkwp_ctx* ctx, const char* path);
+ugkwp_status ugkwp_load(ugkwp_ctx* ctx, const char* path);
+
 /* Per-stage device timing with CUDA events recorded on the context's stream around each stage of every
  * step taken while enabled (graph replay is bypassed meanwhile). ugkwp_profile synchronises, returns the
  * summed milliseconds of the 6 stages (ms[0..5]: decomposition + slot scan, new-particle sampling,

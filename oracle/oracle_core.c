@@ -2,17 +2,17 @@
  * load it). A plain sequential CPU restatement of one UGKWP-LTS steady-iteration step, checked against
  * the paper's fixed points by the `-m "not gpu"` tests. It shares no code with the CUDA library.
  *
- * Paper sections cited: Sec. 2 (kinetic model, Eqs. 1-8), Sec. 3 (UGKWP, Eqs. 9-23), Sec. 3.3 (algorithm
- * steps 1-4), Sec. 4 (LTS: Eqs. 24-25 time steps; Eq. 37 proportional scaling; Eqs. 40-46 LTS form).
+ * Paper sections cited: Sec. II (kinetic model, Eqs. 1-8), Sec. III (UGKWP, Eqs. 9-32), Sec. III C (algorithm
+ * steps 1-4), Sec. IV (LTS: Eqs. 33-34 time steps; Eq. 41 proportional scaling; Eqs. 47-53 LTS form).
  *
  * Readings of points the paper leaves open (each is a reading, not a statement of the paper):
  *  - units rho_inf = T_inf = 1, R = 1/2; monatomic, three velocity components, D = 0;
- *  - mu_inf from Kn by the VHS mean-free-path relation; mu = mu_inf T^omega; tau = mu / p (Sec. 2);
+ *  - mu_inf from Kn by the VHS mean-free-path relation; mu = mu_inf T^omega; tau = mu / p (Sec. II);
  *  - tau_i from the total W^n_i at the start of the step;
  *  - reconstruction is first order (piecewise constant): the initial distribution has no slope; the
  *    equilibrium g_0 has normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on
- *    u.n < 0, no tangential slope; A from the compatibility condition with both half slopes (Sec. 3.1);
- *  - Prandtl fix applied to a through d(lambda)/Pr; wave fluxes use the Maxwellian g_0 (Sec. 3.1);
+ *    u.n < 0, no tangential slope; A from the compatibility condition with both half slopes (Sec. III A);
+ *  - Prandtl fix applied to a through d(lambda)/Pr; wave fluxes use the Maxwellian g_0 (Sec. III A);
  *  - wall faces: incoming half from the fluid cell (first order), outgoing half a wall Maxwellian at T_w
  *    whose density zeroes the wave mass flux; far-field ghost = freestream on inflow, the cell state on
  *    outflow, with the full free-transport coefficient on the ghost side (no particles are injected);
@@ -38,7 +38,7 @@ static void* zalloc(size_t n, size_t sz)
     return p;
 }
 
-/* ---------------------------------------------------------------- kinetic model helpers (Sec. 2) */
+/* ---------------------------------------------------------------- kinetic model helpers (Sec. II) */
 
 /* conservative (rho, rho U, rho V, rho E) of a primitive state; E = |U|^2/2 + (3/2) R T */
 static void prim_to_cons(double rho, double U, double V, double T, double W[4])
@@ -64,10 +64,10 @@ static double tau_of(const or_ctx* cx, const double W[4])
     return mu / (rho * RT);
 }
 
-/* ---------------------------------------------- time-integration coefficients (Eq. 14, Eqs. 40-41) */
+/* ---------------------------------------------- time-integration coefficients (Eq. 16, Eqs. 47-48) */
 
 /* out = (dbar_a, dbar_b, dbar_c, dbar_d, dbar_e, dbar_d - e^{-x}, dbar_e + dt/2 e^{-x}),
- * the coefficients of Eq. 14 evaluated with (dt, tau) and divided by dt (Eq. 41). With x = dt/tau and the
+ * the coefficients of Eq. 16 evaluated with (dt, tau) and divided by dt (Eq. 48). With x = dt/tau and the
  * entire functions phi1 = (1-e^-x)/x, psi2 = (e^-x - 1 + x)/x^2, psi3 = (x^2/2 - x + 1 - e^-x)/x^3,
  * chi = (phi1 - e^-x)/x, beta = (1 + e^-x - 2 phi1)/x^2, kappa = (chi - e^-x/2)/x:
  *   dbar_a = x psi2, dbar_b = -dt x beta, dbar_c = dt x psi3, dbar_d = phi1, dbar_e = -dt chi,
@@ -117,7 +117,7 @@ void oracle_coeffs(double dt, double tau, double* out)
     lts_coeffs(dt, tau, or_expd(-dt / tau), out);
 }
 
-/* ------------------------------------------------------- Maxwellian moments (Sec. 3.1, Eqs. 26-31) */
+/* ------------------------------------------------------- Maxwellian moments (Sec. III A, Eqs. 17-22) */
 
 typedef struct { double rho, U, V, lam; } or_prim;          /* face frame: U normal, V tangential */
 typedef struct { double uf[9], up[9], um[9], v[7], xi2, xi4; } or_mom;
@@ -183,7 +183,7 @@ static void psi_poly_mom(const double* Mu, const or_mom* M, int a, int b, const 
         out[k] = cf[0] * t0[k] + cf[1] * t1[k] + cf[2] * t2[k] + cf[3] * 0.5 * (t3[k] + t4[k] + t5[k]);
 }
 
-/* Solve <psi (a0 + a1 u + a2 v + a3 (u^2+v^2+w^2)/2)> = dw for the Maxwellian p (Eq. 28 / Eq. 31),
+/* Solve <psi (a0 + a1 u + a2 v + a3 (u^2+v^2+w^2)/2)> = dw for the Maxwellian p (Eq. 20 / Eq. 22),
  * closed form of the 4 x 4 moment system (three velocity dimensions). */
 static void micro_slope(const or_prim* p, const double dw[4], double a[4])
 {
@@ -196,7 +196,7 @@ static void micro_slope(const or_prim* p, const double dw[4], double a[4])
     a[0] = dw[0] - a[3] * 0.75 / lam - a[1] * U - a[2] * V - a[3] * 0.5 * (U * U + V * V);
 }
 
-/* Prandtl correction (Sec. 3.1): d(lambda)/dx -> d(lambda)/dx / Pr inside a */
+/* Prandtl correction (Sec. III A): d(lambda)/dx -> d(lambda)/dx / Pr inside a */
 static void pr_fix(const or_prim* p, double a[4], double Pr)
 {
     if (Pr == 1.0) return;
@@ -212,8 +212,8 @@ static void pr_fix(const or_prim* p, double a[4], double Pr)
 }
 
 /* Time-averaged wave flux through one face in the face frame (normal from L to R):
- * equilibrium part (Eq. 42) from g_0 and its slopes, plus the analytic free-transport part of the
- * hydrodynamic wave (Eq. 43, first order so only its dbar_d - e^{-x} term). cL/cR are the 7 normalised
+ * equilibrium part (Eq. 49) from g_0 and its slopes, plus the analytic free-transport part of the
+ * hydrodynamic wave (Eq. 50, first order so only its dbar_d - e^{-x} term). cL/cR are the 7 normalised
  * coefficients of each side; frL/frR the coefficient used for each side's g^h (x chi, or the full dbar_d
  * on a ghost side or without particles). Returns W_0 and the slopes for the pins. */
 static void face_flux(const double WL[4], const double WR[4], const double WhL[4], const double WhR[4],
@@ -230,7 +230,7 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
     double t1[4], t2[4], W0[4];
     psi_mom(mL.up, &mL, 0, 0, 0, t1);
     psi_mom(mR.um, &mR, 0, 0, 0, t2);
-    for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];      /* Eq. 26 */
+    for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];      /* Eq. 17 */
     for (int k = 0; k < 4; ++k) F[k] = 0.0;
     if (!frame_prim(W0, &p0)) {
         /* vacuum interface (reading): no molecule of either side reaches the face (the half-range masses
@@ -249,7 +249,7 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
     pr_fix(&p0, aR, Pr);
     psi_poly_mom(m0.up, &m0, 1, 0, aL, t1);
     psi_poly_mom(m0.um, &m0, 1, 0, aR, t2);
-    for (int k = 0; k < 4; ++k) dA[k] = -(t1[k] + t2[k]);                    /* Eq. 31 */
+    for (int k = 0; k < 4; ++k) dA[k] = -(t1[k] + t2[k]);                    /* Eq. 22 */
     micro_slope(&p0, dA, A);
     double fa_p[4], fa_m[4], fb_p[4], fb_m[4], fc_p[4], fc_m[4];
     psi_mom(m0.up, &m0, 1, 0, 0, fa_p);
@@ -498,7 +498,7 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
     return OR_OK;
 }
 
-/* local time steps (Eq. 24) from the initial freestream field, then the global one (Eq. 25) */
+/* local time steps (Eq. 33) from the initial freestream field, then the global one (Eq. 34) */
 static void init_time_steps(or_ctx* cx)
 {
     const double cs = cx->U_inf + 3.0 * sqrt(OR_R * 1.0);
@@ -628,7 +628,7 @@ static int realizable(const or_ctx* cx, const double W[4])
     return T >= cx->T_min && T <= cx->T_cap && q <= cx->U_cap * cx->U_cap;
 }
 
-/* ------------------------------------------------------------------ a1: decomposition (Sec. 4.2) */
+/* ------------------------------------------------------------------ a1: decomposition (Sec. IV B) */
 
 static void decompose(or_ctx* cx)
 {
@@ -639,7 +639,7 @@ static void decompose(or_ctx* cx)
         double* Wp = cx->Wp + 4 * c;
         double* Wh = cx->Wh + 4 * c;
         const double tau = tau_of(cx, W);
-        /* W^p from the particles retained at the end of the previous step; W^h = W - W^p (Eq. 15) */
+        /* W^p from the particles retained at the end of the previous step; W^h = W - W^p (Eq. 24) */
         Wp[0] = ((double)r[0] * s0) / cx->vol[c];
         Wp[1] = ((double)r[1] * s1) / cx->vol[c];
         Wp[2] = cx->dim == 1 ? 0.0 : ((double)r[2] * s1) / cx->vol[c];
@@ -656,7 +656,7 @@ static void decompose(or_ctx* cx)
         cx->mnew[c] = 0.0;
         cx->samp[3 * c] = cx->samp[3 * c + 1] = cx->samp[3 * c + 2] = 0.0;
         if (!cx->wave_only && cx->hphys[c]) {
-            /* W^hp = W^h e^{-dt_i / tau_i}; N^hp = ceil(rho^hp / rho N_ref); m = rho^hp Omega / N^hp (Eq. 17) */
+            /* W^hp = W^h e^{-dt_i / tau_i}; N^hp = ceil(rho^hp / rho N_ref); m = rho^hp Omega / N^hp (Eq. 26) */
             const double rho_hp = Wh[0] * e;
             if (rho_hp > 0.0) {
                 const double q = ceil((rho_hp / W[0]) * (double)cx->n_ref);
@@ -703,7 +703,7 @@ static void wave_fluxes(or_ctx* cx)
             face_flux(WL, Wm, WhL, Whm, cx->hphys[L], cx->hphys[L], cL, cL, frL, frL, cx->fdL[f], cx->fdL[f],
                       cx->Pr, F, NULL, NULL, NULL, NULL);
         } else {
-            /* far-field / fixed ghost: pure wave, evaluated with the fluid cell's time step (Sec. 4.2) */
+            /* far-field / fixed ghost: pure wave, evaluated with the fluid cell's time step (Sec. IV B) */
             double Wg[4];
             if (bc == OR_BC_FIXED) {
                 for (int k = 0; k < 4; ++k) Wg[k] = cx->W_fix[k];
@@ -726,7 +726,7 @@ static void wave_fluxes(or_ctx* cx)
     }
 }
 
-/* -------------------------------------------------------------------- a10: update (Eq. 46) */
+/* -------------------------------------------------------------------- a10: update (Eq. 53) */
 
 static void update(or_ctx* cx)
 {
@@ -775,7 +775,7 @@ static void update(or_ctx* cx)
     }
 }
 
-/* ------------------------------------------------------------ a11: surface quantities (Sec. 5.1) */
+/* ------------------------------------------------------------ a11: surface quantities (Sec. V A) */
 
 static void surface(or_ctx* cx)
 {
@@ -808,11 +808,11 @@ static int one_step(or_ctx* cx)
     memset(cx->cross, 0, 2 * (size_t)cx->F * 8);
     memset(cx->wallt, 0, 3 * (size_t)cx->nwall * 8);
     for (int k = 2; k < 9; ++k) cx->stats[k] = 0;
-    /* step 1: decomposition and sampling; step 2: free transport and tallies (Sec. 3.3, Sec. 4.2) */
+    /* step 1: decomposition and sampling; step 2: free transport and tallies (Sec. III C, Sec. IV B) */
     decompose(cx);
     if (cx->err) return cx->err;
     if (cx->prec == 0) or_particles_step_f32(cx); else or_particles_step_f64(cx);
-    /* step 3: wave fluxes from the step-start W and W^h, then the conservative update (Eq. 46) */
+    /* step 3: wave fluxes from the step-start W and W^h, then the conservative update (Eq. 53) */
     wave_fluxes(cx);
     update(cx);
     surface(cx);
@@ -967,7 +967,7 @@ int oracle_get_geometry(oracle_ctx* cx, double* dt, double* vol, int32_t* nfaces
 
 const char* oracle_last_error(oracle_ctx* cx) { return cx->msg; }
 
-/* Sec. 4.1, Eq. 39 with constant transported mass: left- and right-hand sides of the balance condition
+/* Sec. IV A, Eq. 46 with constant transported mass: left- and right-hand sides of the balance condition
  * sum(dt_R) / sum(dt_L) and (1/M) sum(dt_R / dt_L) for a sequence of M step pairs. */
 void oracle_balance_condition(int32_t M, const double* dtL, const double* dtR, double* out)
 {

@@ -13,7 +13,7 @@
 //                      (survivors compacted into the other particle buffer)
 //   k_wave_flux   a9   per face (ugkwp_flux.cu): FP32 interior faces, FP64 wall/boundary faces
 //   scan + k_scatter   every sort_every-th step: counting sort of the survivors by cell
-//   k_update      a10, a11  per cell: Eq. 46, residual, particle-mass-ratio EMA; per wall face: p, tau_w, q;
+//   k_update      a10, a11  per cell: Eq. 53, residual, particle-mass-ratio EMA; per wall face: p, tau_w, q;
 //                      the last block closes the step
 #include <cuda_runtime.h>
 #include <cmath>
@@ -28,6 +28,7 @@ namespace ugk {
 namespace {
 
 constexpr int kScanBlock = 1024;
+constexpr int kChunk = 256;   // particles per dynamically claimed chunk of k_particles
 constexpr int kMaxCells = 1 << 20;
 
 // ------------------------------------------------------------------------------------------ scan
@@ -245,7 +246,7 @@ __global__ void k_setup_face_dist(const MeshDev m, Dev d, const double* fd)
     d.fdR[f] = R >= 0 ? (d.fnx[f] * d.xc[R] + d.fny[f] * d.yc[R]) - fd[f] : d.fdL[f];
 }
 
-// Eq. 24 on the freestream field: dt_i = N_CFL Omega_i / ((|U_inf| + 3 sqrt(R T_inf)) sum_j s_j)
+// Eq. 33 on the freestream field: dt_i = N_CFL Omega_i / ((|U_inf| + 3 sqrt(R T_inf)) sum_j s_j)
 __global__ void k_setup_dt(Dev d, int C, const int* cface, double cfl, double cs, double* dtmin_part)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,7 +269,7 @@ __global__ void k_setup_dt(Dev d, int C, const int* cface, double cfl, double cs
     }
 }
 
-// Eq. 25: dt_G = min dt_i, given to every cell under GTS
+// Eq. 34: dt_G = min dt_i, given to every cell under GTS
 __global__ void k_setup_gts(Dev d, int C, const double* dtmin_part, int nb)
 {
     double g = dtmin_part[0];
@@ -329,7 +330,7 @@ __device__ __forceinline__ bool realizable(const StepConsts& K, const double* W)
     return T >= K.T_min && T <= K.T_cap && q <= K.U_cap * K.U_cap;
 }
 
-// ------------------------------------------------------------------ a1: decomposition (Sec. 4.2)
+// ------------------------------------------------------------------ a1: decomposition (Sec. IV B)
 __device__ __forceinline__ double tau_of(const StepConsts& K, const double* W)
 {
     const double rho = W[0], U = W[1] / rho, V = W[2] / rho;
@@ -344,7 +345,7 @@ __device__ __forceinline__ double tau_of(const StepConsts& K, const double* W)
 constexpr int kSeries = 20;
 __constant__ double c_series[6][kSeries];
 
-// Normalised time-integration coefficients (Eq. 14 divided by dt, Eq. 41), x = dt/tau:
+// Normalised time-integration coefficients (Eq. 16 divided by dt, Eq. 48), x = dt/tau:
 //   dbar_a = x psi2, dbar_b = -dt x beta, dbar_c = dt x psi3, dbar_d = phi1, dbar_e = -dt chi,
 //   dbar_d - e^-x = x chi, dbar_e + dt e^-x / 2 = -dt x kappa, with phi1 = (1-e^-x)/x,
 //   psi2 = (e^-x - 1 + x)/x^2, psi3 = (x^2/2 - x + 1 - e^-x)/x^3, chi = (phi1 - e^-x)/x,
@@ -397,8 +398,9 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     Wp[2] = K.dim == 1 ? 0.0 : ((double)r[2] * s1) / vol;
     Wp[3] = ((double)r[4] * s4) / vol;
     // W^{p,-} of the retained particles is exactly the retained tally of the previous step (same particles,
-    // masses, velocities and cell); k_sample adds the new particles
-    for (int k = 0; k < 5; ++k) { d.wprev[5 * c + k] = r[k]; d.wm[5 * c + k] = r[k]; r[k] = 0; d.wpl[5 * c + k] = 0; }
+    // masses, velocities and cell); k_sample adds the new particles. W^{p,+} and the retained tally of this
+    // step start from the same value (every particle unchanged and kept); k_particles adds the changes.
+    for (int k = 0; k < 5; ++k) { d.wprev[5 * c + k] = r[k]; d.wm[5 * c + k] = r[k]; d.wpl[5 * c + k] = r[k]; }
     for (int k = 0; k < 4; ++k) { Wh[k] = W[k] - Wp[k]; d.Wh[4 * c + k] = Wh[k]; }
     const double dt = d.dt[c];
     const double x = dt / tau;
@@ -412,7 +414,7 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     int n = 0;
     double m = 0.0, Uh = 0.0, Vh = 0.0, RTh = 0.0;
     if (!K.wave_only && phys) {
-        // W^hp = W^h e^{-dt_i/tau_i}, N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp (Eq. 17)
+        // W^hp = W^h e^{-dt_i/tau_i}, N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp (Eq. 26)
         const double rho_hp = Wh[0] * e;
         if (rho_hp > 0.0) {
             const double q = ceil((rho_hp / W[0]) * (double)K.n_ref);
@@ -448,6 +450,7 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
         for (int k = 2; k < 8; ++k) d.stats[k] = 0;
         d.stats[11] = 0;
         d.counts[2] = 0;
+        d.counts[5] = 0;
         *d.nretry = 0;
         *d.done = 0u;
         d.flags[0] = (int)(*d.dstep % K.sort_every == (long long)(K.sort_every - 1));
@@ -498,7 +501,7 @@ __device__ __forceinline__ long long rint_ll(float x)
 }
 __device__ __forceinline__ long long rint_ll(double x) { return __double2ll_rn(x); }
 
-// ----------------------------------------------------------- fixed-point tallies (Eq. 21)
+// ----------------------------------------------------------- fixed-point tallies (Eq. 30)
 template <typename T>
 __device__ __forceinline__ long long fixp(T v, T scale, int* err)
 {
@@ -519,32 +522,7 @@ __device__ __forceinline__ void fix5(T m, T u, T v, T w, T s0, T s1, T s4, int* 
     o[4] = fixp(m * e, s4, err);
 }
 
-// Warp-wide sums over runs of equal keys (consecutive lanes with the same cell), then one atomic per run
-// and value from the run's last lane. Keys < 0 are skipped. All 32 lanes must call it.
-template <int NV>
-__device__ __forceinline__ void run_reduce(int key, long long (&v)[NV], int lane, int* start_out)
-{
-    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-    int start = (lane == 0 || prev != key) ? lane : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, start, o);
-        if (lane >= o) start = max(start, t);
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        long long x = v[k];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane - o >= start) x += t;
-        }
-        v[k] = x;
-    }
-    *start_out = start;
-}
-
-// ----------------------------------------------------- a2: new collisionless particles (Eq. 17)
+// ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
 // One warp per cell. Velocities: Box-Muller normals shifted and scaled so that the cell's new particles
 // carry exactly the momentum and energy of W^hp (sums in index order, accumulated by lane 0).
 template <typename T>
@@ -653,13 +631,17 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
     for (int q = 0; q < 5; ++q)
         for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
     if (lane == 0)
-        for (int q = 0; q < 5; ++q) d.wm[5 * c + q] += acc[q];
+        for (int q = 0; q < 5; ++q) {
+            d.wm[5 * c + q] += acc[q];
+            d.wpl[5 * c + q] += acc[q];
+            d.wrt[5 * c + q] += acc[q];
+        }
 }
 
 // ------------------------------------------------- a3-a6: free flight, transport and tallies
-// One thread per particle (warp-uniform grid-stride loop). Retained particles draw t_f (Eq. 18 with dt_i),
-// new ones fly the whole dt_i; free transport through the cell faces (Eq. 19) with mass and remaining time
-// scaled by dt_R / dt_L at every crossing (Eqs. 37, 45), diffuse re-emission at walls, specular mirrors,
+// One thread per particle (warp-uniform grid-stride loop). Retained particles draw t_f (Eq. 27 with dt_i),
+// new ones fly the whole dt_i; free transport through the cell faces (Eq. 28) with mass and remaining time
+// scaled by dt_R / dt_L at every crossing (Eqs. 41, 52), diffuse re-emission at walls, specular mirrors,
 // deletion at far-field and fixed ghosts. Then W^{p,+} and the retained tally (run-reduced per warp) and
 // the survivors: compacted into the other buffer (warp-aggregated slots), or, on sort steps, written in
 // place for the counting sort.
@@ -680,12 +662,15 @@ __global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const 
     int max_it = 0;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    // each warp walks a contiguous range of the (cell-ordered) particle array, 32 particles at a time,
-    // prefetching the next 32 records into L1 while it works on the current ones
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int per = ((n + nwarps - 1) / nwarps + 31) & ~31;
-    const int wbeg = min(n, gw * per), wend = min(n, wbeg + per);
+    // each warp takes chunks of kChunk consecutive particles (of the cell-ordered array) from a global
+    // counter and walks them 32 at a time, prefetching the next 32 records into L1 while it works on the
+    // current ones; dynamic chunks keep all SMs busy when other kernels share the GPU
+    for (;;) {
+    int wbeg = 0;
+    if (lane == 0) wbeg = atomicAdd(d.counts + 5, kChunk);
+    wbeg = __shfl_sync(0xffffffffu, wbeg, 0);
+    if (wbeg >= n) break;
+    const int wend = min(n, wbeg + kChunk);
     for (int base = wbeg; base < wend; base += 32) {
         const int i = base + lane;
         const int inext = i + 32;
@@ -699,7 +684,6 @@ __global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const 
             asm volatile("prefetch.global.L1 [%0];" ::"l"(A.cell + inext));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(A.pid + inext));
         }
-        long long fx[5] = {0, 0, 0, 0, 0};
         int end_cell = -1;
         bool kept = false;
         T x = 0, y = 0, u = 0, v = 0, w = 0, m = 0;
@@ -708,6 +692,8 @@ __global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const 
             x = A.x[i]; y = A.y[i]; u = A.u[i]; v = A.v[i]; w = A.w[i]; m = A.m[i];
             int c = A.cell[i];
             pid = A.pid[i];
+            const int c0 = c;
+            const T m0 = m, u0 = u, v0 = v, w0 = w;
             const T dtc = pc.dt_(c);
             T tr;
             bool collide = false;
@@ -792,12 +778,33 @@ __global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const 
             }
             max_it = max(max_it, it);
             if (alive) {
-                fix5(m, u, v, w, s0, s1, s4, d.err, fx);
                 end_cell = c;
                 kept = !collide;
                 if (collide) n_removed++;
             } else {
                 n_left++;
+            }
+            // W^{p,+} and the retained tally started as W^{p,-} (each particle unchanged in its cell and kept).
+            // A particle that crossed a face, met a boundary or left moves its contribution; a collided one
+            // leaves the retained tally. Integer sums: identical to summing every final contribution.
+            unsigned long long* pl = reinterpret_cast<unsigned long long*>(d.wpl);
+            unsigned long long* rt = reinterpret_cast<unsigned long long*>(d.wrt);
+            if (it > 0) {
+                long long o[5], f[5];
+                fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
+                if (alive) fix5(m, u, v, w, s0, s1, s4, d.err, f);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    atomicAdd(pl + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
+                    atomicAdd(rt + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
+                    if (alive) atomicAdd(pl + 5 * (size_t)c + k, (unsigned long long)f[k]);
+                    if (kept) atomicAdd(rt + 5 * (size_t)c + k, (unsigned long long)f[k]);
+                }
+            } else if (collide) {
+                long long o[5];
+                fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) atomicAdd(rt + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
             }
         }
         // survivors
@@ -819,43 +826,20 @@ __global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const 
                 B.pid[j] = pid;
             }
         }
-        // W^{p,+} (every particle still in the domain, in its final cell) and the retained part per run
-        // of equal final cell; when no particle of the warp collided both sums coincide
-        const bool any_removed = __any_sync(0xffffffffu, end_cell >= 0 && !kept);
-        const int next = __shfl_down_sync(0xffffffffu, end_cell, 1);
-        const bool tail = (lane == 31 || next != end_cell) && end_cell >= 0;
-        int start;
-        if (!any_removed) {
-            run_reduce<5>(end_cell, fx, lane, &start);
-            if (tail) {
-                unsigned long long* ap = reinterpret_cast<unsigned long long*>(d.wpl + 5 * (size_t)end_cell);
-                unsigned long long* ar = reinterpret_cast<unsigned long long*>(d.wrt + 5 * (size_t)end_cell);
+        // survivors per cell for the counting sort (sort steps only), one atomic per run of equal cell
+        if (sort_step) {
+            const int key = kept ? end_cell : -1;
+            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+            int start = (lane == 0 || prev != key) ? lane : 0;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    if (fx[k]) {
-                        atomicAdd(ap + k, (unsigned long long)fx[k]);
-                        atomicAdd(ar + k, (unsigned long long)fx[k]);
-                    }
-                }
-                atomicAdd(d.cnt + end_cell, lane - start + 1);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, start, o);
+                if (lane >= o) start = max(start, t);
             }
-        } else {
-            long long vals[11];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) { vals[k] = fx[k]; vals[5 + k] = kept ? fx[k] : 0; }
-            vals[10] = kept ? 1 : 0;
-            run_reduce<11>(end_cell, vals, lane, &start);
-            if (tail) {
-                unsigned long long* ap = reinterpret_cast<unsigned long long*>(d.wpl + 5 * (size_t)end_cell);
-                unsigned long long* ar = reinterpret_cast<unsigned long long*>(d.wrt + 5 * (size_t)end_cell);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    if (vals[k]) atomicAdd(ap + k, (unsigned long long)vals[k]);
-                    if (vals[5 + k]) atomicAdd(ar + k, (unsigned long long)vals[5 + k]);
-                }
-                if (vals[10]) atomicAdd(d.cnt + end_cell, (int)vals[10]);
-            }
+            const int next = __shfl_down_sync(0xffffffffu, key, 1);
+            if ((lane == 31 || next != key) && key >= 0) atomicAdd(d.cnt + key, lane - start + 1);
         }
+    }
     }
     for (int o = 16; o > 0; o >>= 1) {
         n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
@@ -892,9 +876,9 @@ __global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA,
     }
 }
 
-// ---------------------------------------------------------------- a10: update (Eq. 46)
+// ---------------------------------------------------------------- a10: update (Eq. 53)
 // Threads [0, C): conservative update of one cell, residual term, particle-mass-ratio EMA, vacuum floor.
-// Threads [C, C + n_wall): wall pressure, shear stress and heat flux of one wall face (a11, Sec. 5.1).
+// Threads [C, C + n_wall): wall pressure, shear stress and heat flux of one wall face (a11, Sec. V A).
 // The last block to finish reduces the residual partials in block order and closes the step.
 __global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long long* dstep)
 {
@@ -1088,42 +1072,53 @@ template <typename T> cudaError_t alloc_particles(Ctx& ctx, ParticleSoA<T>& P, s
 }  // namespace
 
 // the per-step kernel sequence (enqueued on s; capturable)
-static void enqueue_step(Ctx& ctx, cudaStream_t s, bool prof)
+static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
 {
     const StepConsts& K = ctx.k;
     Dev& d = ctx.d;
     const int C = K.C;
-    cudaEvent_t ev[kStages + 1];
-    auto mark = [&](int k) {
-        if (!prof) return;
-        if (k == 0)
-            for (int q = 0; q <= kStages; ++q) cudaEventCreate(&ev[q]);
-        cudaEventRecord(ev[k], s);
-        if (k == kStages)
-            for (int q = 0; q <= kStages; ++q) ctx.prof_events.push_back(ev[q]);
+    // stage k timed by the event pair (2k, 2k+1) recorded on the stream that runs it
+    cudaEvent_t ev[2 * kStages];
+    if (prof)
+        for (int q = 0; q < 2 * kStages; ++q) cudaEventCreate(&ev[q]);
+    auto mark = [&](int q, cudaStream_t st) {
+        if (prof) cudaEventRecord(ev[q], st);
     };
-    mark(0);
+    mark(0, s);
     k_begin_step<<<nblk(2LL * K.F, 256), 256, 0, s>>>(K, d);
     k_decompose<<<nblk(C, 128), 128, 0, s>>>(K, d);
     exclusive_scan(d.nhp, d.nhp_off, d.scan_tmp, C, d.counts + 1, s, d.counts, d.err);
-    mark(1);
+    mark(1, s);
+    // the wave fluxes depend only on the decomposition: they run on a second stream, alongside the
+    // particle kernels, and join before the update
+    cudaEventRecord(ctx.ev_fork, s);
+    cudaStreamWaitEvent(s2, ctx.ev_fork, 0);
+    mark(6, s2);
+    launch_wave_flux(K, d, ctx.sms, s2);
+    mark(7, s2);
+    cudaEventRecord(ctx.ev_join, s2);
     PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32};
     PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp};
+    mark(2, s);
     if (K.prec == 0) k_sample<float><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
     else k_sample<double><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
-    mark(2);
+    mark(3, s);
+    mark(4, s);
     if (K.prec == 0) k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
     else k_particles<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64, d.cf64, pc64, d.dstep);
-    mark(3);
-    launch_wave_flux(K, d, ctx.sms, s);
-    mark(4);
+    mark(5, s);
+    mark(8, s);
     // counting sort every sort_every-th step (kernels return at once on the other steps)
     exclusive_scan(d.cnt, d.off, d.scan_tmp, C, d.counts + 2, s, nullptr, nullptr, d.flags);
     if (K.prec == 0) k_scatter<float><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa32, d.pb32);
     else k_scatter<double><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa64, d.pb64);
-    mark(5);
+    mark(9, s);
+    cudaStreamWaitEvent(s, ctx.ev_join, 0);
+    mark(10, s);
     k_update<<<ctx.res_blocks, 256, 0, s>>>(K, d, d.dstep);
-    mark(6);
+    mark(11, s);
+    if (prof)
+        for (int q = 0; q < 2 * kStages; ++q) ctx.prof_events.push_back(ev[q]);
 }
 
 }  // namespace ugk
@@ -1169,6 +1164,12 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     *out = nullptr;
     ctx.stream = static_cast<cudaStream_t>(opts->stream);
     ctx.use_graph = opts->use_graph;
+    if (cudaStreamCreateWithFlags(&ctx.stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        delete h;
+        return UGKWP_ECUDA;
+    }
     const int ni = mesh->ni, nj = mesh->nj, C = ni * nj;
     const int periodic_i = mesh->dim == 1 && mesh->bc_imin[0] == UGKWP_BC_PERIODIC;
     if (mesh->dim == 1 && ((mesh->bc_imin[0] == UGKWP_BC_PERIODIC) != (mesh->bc_imax[0] == UGKWP_BC_PERIODIC))) {
@@ -1369,7 +1370,11 @@ void ugkwp_destroy(ugkwp_ctx* h)
     else cudaDeviceSynchronize();
     if (ctx.graph) cudaGraphExecDestroy(ctx.graph);
     for (cudaEvent_t e : ctx.prof_events) cudaEventDestroy(e);
+    if (ctx.stream2) cudaStreamSynchronize(ctx.stream2);
     for (void* p : ctx.allocs) cudaFree(p);
+    if (ctx.stream2) cudaStreamDestroy(ctx.stream2);
+    if (ctx.ev_fork) cudaEventDestroy(ctx.ev_fork);
+    if (ctx.ev_join) cudaEventDestroy(ctx.ev_join);
     delete h;
 }
 
@@ -1383,7 +1388,7 @@ ugkwp_status ugkwp_step(ugkwp_ctx* h, int32_t n)
             CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-            enqueue_step(ctx, cap, false);
+            enqueue_step(ctx, cap, ctx.stream2, false);
             CK(cudaStreamEndCapture(cap, &g));
             CK(cudaGraphInstantiate(&ctx.graph, g, 0));
             cudaGraphDestroy(g);
@@ -1391,7 +1396,7 @@ ugkwp_status ugkwp_step(ugkwp_ctx* h, int32_t n)
         }
         for (int32_t s = 0; s < n; ++s) CK(cudaGraphLaunch(ctx.graph, ctx.stream));
     } else {
-        for (int32_t s = 0; s < n; ++s) enqueue_step(ctx, ctx.stream, ctx.profiling != 0);
+        for (int32_t s = 0; s < n; ++s) enqueue_step(ctx, ctx.stream, ctx.stream2, ctx.profiling != 0);
     }
     CK(cudaGetLastError());
     ctx.step += n;
@@ -1644,17 +1649,200 @@ ugkwp_status ugkwp_profile(ugkwp_ctx* h, double* ms, int64_t* steps)
     if (!h || !ms || !steps) return UGKWP_EINVAL;
     Ctx& ctx = h->c;
     CK(cudaStreamSynchronize(ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream2));
     for (int k = 0; k < kStages; ++k) ms[k] = 0.0;
-    const size_t per = kStages + 1, n = ctx.prof_events.size() / per;
+    const size_t per = 2 * kStages, n = ctx.prof_events.size() / per;
+    // stages in event-pair order: decompose, sample, particles, wave flux, sort, update
+    const int order[kStages] = {0, 1, 2, 3, 4, 5};
+    const int pair[kStages] = {0, 2, 4, 6, 8, 10};
     for (size_t i = 0; i < n; ++i)
         for (int k = 0; k < kStages; ++k) {
             float t = 0.0f;
-            CK(cudaEventElapsedTime(&t, ctx.prof_events[i * per + k], ctx.prof_events[i * per + k + 1]));
+            const int q = pair[order[k]];
+            CK(cudaEventElapsedTime(&t, ctx.prof_events[i * per + q], ctx.prof_events[i * per + q + 1]));
             ms[k] += t;
         }
     for (cudaEvent_t e : ctx.prof_events) cudaEventDestroy(e);
     ctx.prof_events.clear();
     *steps = (int64_t)n;
+    return UGKWP_OK;
+}
+
+struct ugkwp_batch {
+    std::vector<ugkwp_ctx*> cases;
+    std::vector<cudaStream_t> streams;
+    cudaStream_t root = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraphExec_t graph = nullptr;
+    std::string msg;
+};
+
+ugkwp_status ugkwp_batch_create(ugkwp_ctx* const* ctxs, int32_t n, void* stream, ugkwp_batch** out)
+{
+    if (!ctxs || n <= 0 || !out) return UGKWP_EINVAL;
+    *out = nullptr;
+    ugkwp_batch* b = new (std::nothrow) ugkwp_batch;
+    if (!b) return UGKWP_ENOMEM;
+    b->root = static_cast<cudaStream_t>(stream);
+    auto bail = [&](ugkwp_status st) { ugkwp_batch_destroy(b); return st; };
+    for (int32_t i = 0; i < n; ++i) {
+        if (!ctxs[i]) return bail(UGKWP_EINVAL);
+        for (int32_t j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return bail(UGKWP_EINVAL);
+        b->cases.push_back(ctxs[i]);
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(UGKWP_ECUDA);
+        b->streams.push_back(s);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(UGKWP_ECUDA);
+        b->joins.push_back(e);
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return bail(UGKWP_ECUDA);
+    // one graph: fork every case from a capture stream, each case's step on its own streams, join all
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return bail(UGKWP_ECUDA);
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        cudaEventRecord(b->fork, cap);
+        for (int32_t i = 0; i < n; ++i) {
+            cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+            enqueue_step(b->cases[i]->c, b->streams[i], b->cases[i]->c.stream2, false);
+            cudaEventRecord(b->joins[i], b->streams[i]);
+            cudaStreamWaitEvent(cap, b->joins[i], 0);
+        }
+        ok = cudaStreamEndCapture(cap, &g) == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (!ok) return bail(UGKWP_ECUDA);
+    *out = b;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_batch_step(ugkwp_batch* b, int32_t n_steps)
+{
+    if (!b || n_steps < 0) return UGKWP_EINVAL;
+    // every case's previous work on its own stream completes first
+    for (ugkwp_ctx* c : b->cases) {
+        cudaEventRecord(b->fork, c->c.stream);
+        cudaStreamWaitEvent(b->root, b->fork, 0);
+    }
+    for (int32_t k = 0; k < n_steps; ++k)
+        if (cudaGraphLaunch(b->graph, b->root) != cudaSuccess) return UGKWP_ECUDA;
+    cudaEventRecord(b->fork, b->root);
+    for (ugkwp_ctx* c : b->cases) {
+        cudaStreamWaitEvent(c->c.stream, b->fork, 0);
+        c->c.step += n_steps;
+    }
+    return cudaGetLastError() == cudaSuccess ? UGKWP_OK : UGKWP_ECUDA;
+}
+
+void ugkwp_batch_destroy(ugkwp_batch* b)
+{
+    if (!b) return;
+    if (b->root) cudaStreamSynchronize(b->root);
+    else cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, C, F, nwall, prec, wave_only;
+    int64_t step, np;
+    int32_t fx[3], pad;
+};
+}  // namespace
+
+ugkwp_status ugkwp_save(ugkwp_ctx* h, const char* path)
+{
+    if (!h || !path) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C, nw = ctx.k.nwall;
+    const int64_t np = ugkwp_num_particles(h);
+    if (np < 0) return fail(ctx, UGKWP_ECUDA, "reading the particle count");
+    CkptHeader hd{};
+    memcpy(hd.magic, "UGKWPCK1", 8);
+    hd.version = 1; hd.C = C; hd.F = ctx.k.F; hd.nwall = nw; hd.prec = ctx.k.prec; hd.wave_only = ctx.k.wave_only;
+    long long step = 0;
+    CK(cudaMemcpyAsync(&step, ctx.d.dstep, sizeof step, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    hd.step = step; hd.np = np; hd.fx[0] = ctx.k.fx0; hd.fx[1] = ctx.k.fx1; hd.fx[2] = ctx.k.fx4;
+    std::vector<double> W(4 * (size_t)C), res(8), chi(C), ss(3 * (size_t)std::max(nw, 1));
+    std::vector<long long> wr(5 * (size_t)C);
+    unsigned long long st[16];
+    CK(cudaMemcpyAsync(W.data(), ctx.d.W, 8 * W.size(), cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(wr.data(), ctx.d.wrt, 8 * wr.size(), cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(res.data(), ctx.d.res, 8 * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(chi.data(), ctx.d.chi_ema, 8 * (size_t)C, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(ss.data(), ctx.d.surf_sum, 8 * ss.size(), cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(st, ctx.d.stats, sizeof st, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    std::vector<uint64_t> pid(np > 0 ? np : 1);
+    std::vector<int32_t> cell(np > 0 ? np : 1);
+    std::vector<double> pv(6 * (size_t)(np > 0 ? np : 1));
+    if (np > 0) {
+        ugkwp_status e = ugkwp_get_particles(h, np, pid.data(), cell.data(), pv.data(), pv.data() + np,
+                                             pv.data() + 2 * np, pv.data() + 3 * np, pv.data() + 4 * np, pv.data() + 5 * np);
+        if (e) return e;
+    }
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(ctx, UGKWP_EINVAL, "cannot open the checkpoint file for writing");
+    bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(W.data(), 8, W.size(), f) == W.size() &&
+              fwrite(wr.data(), 8, wr.size(), f) == wr.size() && fwrite(res.data(), 8, 8, f) == 8 &&
+              fwrite(chi.data(), 8, chi.size(), f) == chi.size() && fwrite(ss.data(), 8, ss.size(), f) == ss.size() &&
+              fwrite(st, sizeof st, 1, f) == 1;
+    if (ok && np > 0)
+        ok = fwrite(pid.data(), 8, np, f) == (size_t)np && fwrite(cell.data(), 4, np, f) == (size_t)np &&
+             fwrite(pv.data(), 8, 6 * np, f) == (size_t)(6 * np);
+    ok = (fclose(f) == 0) && ok;
+    return ok ? UGKWP_OK : fail(ctx, UGKWP_EINVAL, "writing the checkpoint file failed");
+}
+
+ugkwp_status ugkwp_load(ugkwp_ctx* h, const char* path)
+{
+    if (!h || !path) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C, nw = ctx.k.nwall;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(ctx, UGKWP_EINVAL, "cannot open the checkpoint file");
+    CkptHeader hd{};
+    bool ok = fread(&hd, sizeof hd, 1, f) == 1 && memcmp(hd.magic, "UGKWPCK1", 8) == 0 && hd.version == 1 &&
+              hd.C == C && hd.F == ctx.k.F && hd.nwall == nw && hd.prec == ctx.k.prec &&
+              hd.fx[0] == ctx.k.fx0 && hd.fx[1] == ctx.k.fx1 && hd.fx[2] == ctx.k.fx4 && hd.np >= 0 &&
+              hd.np <= ctx.capacity;
+    if (!ok) { fclose(f); return fail(ctx, UGKWP_EINVAL, "checkpoint does not match this context"); }
+    const int64_t np = hd.np;
+    std::vector<double> W(4 * (size_t)C), res(8), chi(C), ss(3 * (size_t)std::max(nw, 1));
+    std::vector<long long> wr(5 * (size_t)C);
+    unsigned long long st[16];
+    std::vector<uint64_t> pid(np > 0 ? np : 1);
+    std::vector<int32_t> cell(np > 0 ? np : 1);
+    std::vector<double> pv(6 * (size_t)(np > 0 ? np : 1));
+    ok = fread(W.data(), 8, W.size(), f) == W.size() && fread(wr.data(), 8, wr.size(), f) == wr.size() &&
+         fread(res.data(), 8, 8, f) == 8 && fread(chi.data(), 8, chi.size(), f) == chi.size() &&
+         fread(ss.data(), 8, ss.size(), f) == ss.size() && fread(st, sizeof st, 1, f) == 1;
+    if (ok && np > 0)
+        ok = fread(pid.data(), 8, np, f) == (size_t)np && fread(cell.data(), 4, np, f) == (size_t)np &&
+             fread(pv.data(), 8, 6 * np, f) == (size_t)(6 * np);
+    fclose(f);
+    if (!ok) return fail(ctx, UGKWP_EINVAL, "truncated checkpoint file");
+    ugkwp_status e = ugkwp_set_state(h, hd.step, W.data(), reinterpret_cast<const int64_t*>(wr.data()), np,
+                                     pid.data(), cell.data(), pv.data(), pv.data() + np, pv.data() + 2 * np,
+                                     pv.data() + 3 * np, pv.data() + 4 * np, pv.data() + 5 * np);
+    if (e) return e;
+    CK(cudaMemcpyAsync(ctx.d.res, res.data(), 8 * 8, cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(ctx.d.chi_ema, chi.data(), 8 * (size_t)C, cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(ctx.d.surf_sum, ss.data(), 8 * ss.size(), cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(ctx.d.stats, st, sizeof st, cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
     return UGKWP_OK;
 }
 

@@ -1,16 +1,16 @@
 // Time-averaged wave fluxes of one UGKWP-LTS step (a9), one thread per face.
 //
-//  F = F^eq + F^fr,wave through face j with unit normal n from L to R (Eqs. 40-43):
+//  F = F^eq + F^fr,wave through face j with unit normal n from L to R (Eqs. 47-50):
 //   F^eq: the interface equilibrium g_0 from the half-range moments of the Maxwellians of W_L and W_R
-//     (Eq. 26); its normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on u.n < 0
-//     (Eq. 28 with the Prandtl fix of Sec. 3.1), and A from the compatibility condition (Eq. 31); each half
-//     weighted with its own cell's normalised coefficients dbar_{a,b,c} (Eq. 41).
+//     (Eq. 17); its normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on u.n < 0
+//     (Eq. 20 with the Prandtl fix of Sec. III A), and A from the compatibility condition (Eq. 22); each half
+//     weighted with its own cell's normalised coefficients dbar_{a,b,c} (Eq. 48).
 //   F^fr,wave: the hydrodynamic wave's Maxwellian g^h of each side over its half, weighted with
-//     dbar_d - e^{-dt/tau} (the part not carried by new particles, Eq. 43); first-order reconstruction, so
-//     the slope term of Eq. 43 vanishes.
+//     dbar_d - e^{-dt/tau} (the part not carried by new particles, Eq. 50); first-order reconstruction, so
+//     the slope term of Eq. 50 vanishes.
 //  Boundary faces (n points out of the fluid cell L): a diffuse wall returns a wall Maxwellian at T_w with
 //  the density that zeroes the wave mass flux; far-field / fixed ghosts carry their full free-transport
-//  part (no particles are injected) and use the fluid cell's time step on both halves (Sec. 4.2); a
+//  part (no particles are injected) and use the fluid cell's time step on both halves (Sec. IV B); a
 //  symmetry face mirrors L.
 //  The moment algebra is a dense 4x4 closed form per face, so it runs on the FP32/FP64 pipes; faces
 //  flagged face_f64 (next to walls) are always evaluated in FP64.
@@ -42,8 +42,10 @@ template <typename R> __device__ __forceinline__ void moments(const Prim<R>& p, 
     const R U = p.U, V = p.V, lam = p.lam, th = R(0.5) / lam;
     const R sl = sqrt(lam);
     const R ex = exp(-lam * U * U) / (R(2) * sqrt(R(3.14159265358979323846) * lam));
-    M.up[0] = R(0.5) * erfc(-sl * U);
-    M.um[0] = R(0.5) * erfc(sl * U);
+    // one erfc per Maxwellian: the smaller half-range mass from erfc(sqrt(lambda)|U|), the other as 1 - it
+    const R small = R(0.5) * erfc(sl * fabs(U));
+    M.up[0] = U >= R(0) ? R(1) - small : small;
+    M.um[0] = U >= R(0) ? small : R(1) - small;
     M.up[1] = U * M.up[0] + ex;
     M.um[1] = U * M.um[0] - ex;
 #pragma unroll
@@ -109,7 +111,7 @@ template <typename R> __device__ __forceinline__ void pr_fix(const Prim<R>& p, R
     a[0] = drho + R(1.5) * dl / lam - dl * (U * U + V * V) - R(2) * lam * (U * dU + V * dV);
 }
 
-// equilibrium part of Eq. 42 given the interface state W_0 (primitive p0); c[0..2] = dbar_a, dbar_b,
+// equilibrium part of Eq. 49 given the interface state W_0 (primitive p0); c[0..2] = dbar_a, dbar_b,
 // dbar_c of each side
 template <typename R>
 __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], const Prim<R>& p0, const R cL[3],
@@ -221,7 +223,7 @@ __device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, R caL, R frL, 
 constexpr int kSeriesF = 20;
 __constant__ double c_series_f[4][kSeriesF];
 
-// normalised coefficients (dbar_a, dbar_b, dbar_c, dbar_d) of a ghost side (Eq. 41), FP64
+// normalised coefficients (dbar_a, dbar_b, dbar_c, dbar_d) of a ghost side (Eq. 48), FP64
 __device__ void ghost_coeffs(double dt, double tau, double c[4])
 {
     const double x = dt / tau;
@@ -332,12 +334,14 @@ __global__ void __launch_bounds__(128) k_wave_flux32(const StepConsts K, const D
 }
 
 // FP64 faces: the static list (faces of wall cells; every face in the FP64 mode), then the faces queued by
-// the FP32 kernel. FP64 throughput per SM is small on this part, so consecutive faces go to different blocks
-// (and SMs): face j is taken by lane j / gridDim of block j % gridDim.
-__global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c)
+// the FP32 kernel. The FP64 pipe's cost grows with the active lanes of a warp, so in production mode the
+// faces are spread one per warp (lane 0) over one warp per SM sub-partition; in the all-FP64 mode every
+// lane takes a face.
+__global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c, int lanes)
 {
+    if ((int)threadIdx.x >= lanes) return;
     const int n = K.n_f64 + *c.nretry;
-    for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < n; j += gridDim.x * lanes) {
         const int f = j < K.n_f64 ? c.f64list[j] : c.retry[j - K.n_f64];
         double out[4];
         one_face<double>(K, c, f, out);
@@ -350,8 +354,8 @@ __global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const De
 void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s)
 {
     if (k.prec == 0) k_wave_flux32<<<(k.F + 127) / 128, 128, 0, s>>>(k, d);
-    const int blocks = k.prec == 0 ? 2 * sms : (k.F + 31) / 32;
-    k_wave_flux64<<<blocks, 32, 0, s>>>(k, d);
+    if (k.prec == 0) k_wave_flux64<<<4 * sms, 32, 0, s>>>(k, d, 1);
+    else k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32);
 }
 
 cudaError_t flux_set_tables(const double* tab, cudaStream_t s)

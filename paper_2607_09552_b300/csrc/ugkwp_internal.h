@@ -90,13 +90,15 @@ struct Ctx {
     Dev d{};
     int ni = 0, nj = 0, periodic_j = 0, capacity = 0, res_blocks = 0, grid_particles = 0, sms = 148;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;              // wave fluxes, overlapped with the particle kernels
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t step = 0;
     int use_graph = 0;
     cudaGraphExec_t graph = nullptr;
     std::string msg;
     std::vector<void*> allocs;
     int profiling = 0;
-    std::vector<cudaEvent_t> prof_events;   // kStages + 1 per profiled step, in stream order
+    std::vector<cudaEvent_t> prof_events;   // 2 kStages per profiled step (start, end of each stage)
 };
 
 constexpr int kStages = 6;   // decompose+scan, sample, particles, wave flux, sort, update+surface+close

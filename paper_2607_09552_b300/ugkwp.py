@@ -21,7 +21,8 @@ LTS, GTS = 0, 1
 EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugkwp_surface", "ugkwp_reset_surface",
            "ugkwp_set_field", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
            "ugkwp_set_state", "ugkwp_get_tallies", "ugkwp_get_cell_data", "ugkwp_get_flux", "ugkwp_get_geometry",
-           "ugkwp_fixed_exponents", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_last_error"]
+           "ugkwp_fixed_exponents", "ugkwp_save", "ugkwp_load", "ugkwp_batch_create", "ugkwp_batch_step",
+           "ugkwp_batch_destroy", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_last_error"]
 STAGES = ["decompose", "sample", "particles", "wave_flux", "sort", "update"]
 
 
@@ -56,6 +57,7 @@ def load():
         lib.ugkwp_last_error.restype = C.c_char_p
         lib.ugkwp_num_particles.restype = C.c_int64
         lib.ugkwp_destroy.restype = None
+        lib.ugkwp_batch_destroy.restype = None
         _lib = lib
     return _lib
 
@@ -153,6 +155,12 @@ class Solver:
         self._check(load().ugkwp_stats(self.ctx, _p(out, C.c_int64)))
         return out
 
+    def save(self, path: str):
+        self._check(load().ugkwp_save(self.ctx, os.fsencode(path)))
+
+    def load_checkpoint(self, path: str):
+        self._check(load().ugkwp_load(self.ctx, os.fsencode(path)))
+
     def set_profiling(self, on: bool):
         self._check(load().ugkwp_set_profiling(self.ctx, C.c_int32(int(on))))
 
@@ -210,3 +218,29 @@ class Solver:
         out = np.zeros(4 * self.F)
         self._check(load().ugkwp_get_flux(self.ctx, _d(out)))
         return out.reshape(self.F, 4)
+
+
+class Batch:
+    """Several Solver contexts advanced together by one graph launch per step (ugkwp_batch_*)."""
+
+    def __init__(self, solvers, stream=None):
+        L = load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
+        self.h = C.c_void_p()
+        st = L.ugkwp_batch_create(arr, C.c_int32(len(self.solvers)), C.c_void_p(stream), C.byref(self.h))
+        if st != 0:
+            raise UgkwpError(st, "ugkwp_batch_create")
+
+    def step(self, n: int = 1):
+        st = load().ugkwp_batch_step(self.h, C.c_int32(n))
+        if st != 0:
+            raise UgkwpError(st, "ugkwp_batch_step")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ugkwp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -7,7 +7,7 @@ identical mesh.
 
 Non-dimensionalisation (a reading; the paper does not state one): rho_inf = 1, T_inf = 1, R = 1/2, so that
 2 R T_inf = 1, and U_inf = Ma * sqrt(gamma R T_inf) with gamma = 5/3 (monatomic gas, three translational
-degrees of freedom, no internal ones; Sec. 2 "Gas-kinetic theory", eq. (1) with D = 0).
+degrees of freedom, no internal ones; Sec. II "Gas-kinetic theory", eq. (1) with D = 0).
 
 Meshes are structured: ni x nj quadrilaterals with vertex (i, j) stored at index i + (ni + 1) * j. For a
 1-D line mesh nj = 1 and only the x coordinates matter.
@@ -207,3 +207,34 @@ def case_periodic_box(ni: int = 16, end_ratio: float = 50.0, n_ref: int = 50, Kn
     c = Case("periodic_box", m, Kn=Kn, Ma=0.0, Tw=1.0, cfl=0.5, n_ref=n_ref, seed=seed)
     c.init_prim = prim
     return c
+
+
+def case_plate(Kn: float = 0.0169, Ma: float = 5.0, Tw: float = 1.0, n_ref: int = 50, ni: int = 240, nj: int = 120,
+               h1: float = 1e-4, ratio: float = 1.06, cfl: float = 0.8) -> Case:
+    """Sharp flat plate of length L = 1 on a 240 x 120 Cartesian mesh, Kn on L, wall at T_w for 0 <= x <= 1."""
+    return Case(f"plate_{ni}x{nj}_Kn{Kn:.4g}_Ma{Ma:.3g}", plate_mesh(ni, nj, h1, ratio), Kn=Kn, Ma=Ma, Tw=Tw,
+                cfl=cfl, n_ref=n_ref)
+
+
+def batch_sweep(seed: int = 0, n_cases: int = 16, n_plates: int = 4, scale: float = 1.0):
+    """Seeded sweep of uneven 2-D cases: cylinders (the 120 x 160 or the 240 x 320 O-mesh, chosen by a
+    uniform draw) and flat plates in a fixed split; log10 Kn ~ U[log10 0.005, log10 0.2], Ma ~ U[5, 15],
+    T_w / T_inf ~ U[1, 5]; N_ref per case so that it holds about 2-12 million particles (times `scale`)."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(n_cases):
+        kn = 10.0 ** rng.uniform(math.log10(0.005), math.log10(0.2))
+        ma = rng.uniform(5.0, 15.0)
+        tw = rng.uniform(1.0, 5.0)
+        target = rng.uniform(2e6, 12e6) * scale
+        if k < n_cases - n_plates:
+            big = rng.uniform() < 0.5
+            ni, nj, h1, ro = (240, 320, 1e-4, 20.0) if big else (120, 160, 1e-3, 15.0)
+            n_ref = max(4, int(round(target / (ni * nj))))
+            c = case_cylinder(ni, nj, h1, ro, Kn=kn, Ma=ma, Tw=tw, n_ref=n_ref)
+        else:
+            n_ref = max(4, int(round(target / (240 * 120))))
+            c = case_plate(Kn=kn, Ma=ma, Tw=tw, n_ref=n_ref)
+        c.seed = seed * 1000 + k
+        cases.append(c)
+    return cases

@@ -1,5 +1,5 @@
-"""Pins of the normalised time-integration coefficients (Eq. 14 divided by dt, Eq. 41) against a
-50-digit evaluation of Eq. 14, their limits and the GTS identity dt * dbar = delta (Sec. 4.2)."""
+"""Pins of the normalised time-integration coefficients (Eq. 16 divided by dt, Eq. 48) against a
+50-digit evaluation of Eq. 16, their limits and the GTS identity dt * dbar = delta (Sec. IV B)."""
 import mpmath
 import numpy as np
 import pytest
@@ -10,7 +10,7 @@ mpmath.mp.dps = 50
 
 
 def delta_exact(dt, tau):
-    """Eq. 14 with (dt, tau), 50 digits."""
+    """Eq. 16 with (dt, tau), 50 digits."""
     dt, tau = mpmath.mpf(dt), mpmath.mpf(tau)
     e = mpmath.exp(-dt / tau)
     da = dt - tau * (1 - e)
@@ -36,7 +36,7 @@ def test_normalised_coefficients_match_50_digits(x, dt):
 
 def test_limits():
     dt = 0.01
-    # dt/tau -> infinity (e^{-x} below the double range): the GKS coefficients of Eq. 14 with e = 0,
+    # dt/tau -> infinity (e^{-x} below the double range): the GKS coefficients of Eq. 16 with e = 0,
     # dbar_a = 1 - tau/dt, dbar_b = 2 tau^2/dt - tau, dbar_c = dt/2 - tau + tau^2/dt, dbar_d = tau/dt
     tau = dt / 2000.0
     c = ob.coeffs(dt, tau)
@@ -54,7 +54,7 @@ def test_limits():
 
 
 def test_gts_identity():
-    """With dt_L = dt_R = dt_G, dt_G * dbar = delta of Eq. 14 (the LTS form reduces to GTS)."""
+    """With dt_L = dt_R = dt_G, dt_G * dbar = delta of Eq. 16 (the LTS form reduces to GTS)."""
     for x in (1e-3, 0.5, 3.0, 40.0):
         dt = 0.2
         tau = dt / x

@@ -86,21 +86,21 @@ def test_face_flux_against_quadrature(WL, WR, Pr):
     WhR = cons(0.5, 0.2, 0.1, 1.1)
     dL, dR = 0.013, 0.021
     F, W0, aL, aR, A = ob.face_flux(WL, WR, WhL, WhR, cL, cR, dL, dR, Pr)
-    # Eq. 26: W_0 from the half-range moments of g_L and g_R
+    # Eq. 17: W_0 from the half-range moments of g_L and g_R
     W0q = vec_integral(WL, psi, +1) + vec_integral(WR, psi, -1)
     np.testing.assert_allclose(W0, W0q, rtol=1e-11, atol=1e-13)
     if Pr == 1.0:
-        # Eq. 28: int psi g_0 a = dW/dx on each half-slope
+        # Eq. 20: int psi g_0 a = dW/dx on each half-slope
         np.testing.assert_allclose(vec_integral(W0, lambda u, v, w: psi(u, v, w) * poly(aL, u, v, w), 0),
                                    (W0 - WL) / dL, rtol=1e-10, atol=1e-10)
         np.testing.assert_allclose(vec_integral(W0, lambda u, v, w: psi(u, v, w) * poly(aR, u, v, w), 0),
                                    (WR - W0) / dR, rtol=1e-10, atol=1e-10)
-    # Eq. 31: int psi g_0 A = -int psi g_0 (a . u) with the half slopes
+    # Eq. 22: int psi g_0 A = -int psi g_0 (a . u) with the half slopes
     lhs = vec_integral(W0, lambda u, v, w: psi(u, v, w) * poly(A, u, v, w), 0)
     rhs = -(vec_integral(W0, lambda u, v, w: psi(u, v, w) * u * poly(aL, u, v, w), +1)
             + vec_integral(W0, lambda u, v, w: psi(u, v, w) * u * poly(aR, u, v, w), -1))
     np.testing.assert_allclose(lhs, rhs, rtol=1e-9, atol=1e-9)
-    # Eqs. 42-43: the time-averaged flux, half space by half space
+    # Eqs. 49-50: the time-averaged flux, half space by half space
     Fq = np.zeros(4)
     for side, c, a in ((+1, cL, aL), (-1, cR, aR)):
         Fq += vec_integral(W0, lambda u, v, w: psi(u, v, w) * u * (c[0] + c[1] * u * poly(a, u, v, w)
@@ -111,7 +111,7 @@ def test_face_flux_against_quadrature(WL, WR, Pr):
 
 
 def test_prandtl_fix_rescales_temperature_slope():
-    """With Pr != 1 the slope is that of a Maxwellian whose d(lambda)/dx is divided by Pr (Sec. 3.1)."""
+    """With Pr != 1 the slope is that of a Maxwellian whose d(lambda)/dx is divided by Pr (Sec. III A)."""
     WL, WR = CASES[0]
     cL = ob.coeffs(0.01, 0.004)
     _, W0, a1, _, _ = ob.face_flux(WL, WR, None, None, cL, cL, 0.01, 0.01, 1.0)
@@ -139,7 +139,7 @@ def test_prandtl_fix_rescales_temperature_slope():
 @pytest.mark.parametrize("x", [1e-4, 0.3, 5.0, 900.0])
 def test_uniform_state_flux_is_euler_flux(x):
     """Uniform W with W^h = W (no particles yet): slopes vanish and the total wave flux is
-    (dbar_a + dbar_d - e^{-x}) times the Euler flux = (1 - e^{-x}) F_Euler (Eqs. 14, 42, 43)."""
+    (dbar_a + dbar_d - e^{-x}) times the Euler flux = (1 - e^{-x}) F_Euler (Eqs. 16, 49, 50)."""
     rho, U, V, T = 1.3, 0.7, -0.4, 1.7
     W = cons(rho, U, V, T)
     dt = 0.02

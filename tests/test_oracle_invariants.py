@@ -24,7 +24,7 @@ def total(o, weight):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_gts_conserves_mass_momentum_energy_in_a_closed_box(precision):
-    """Eq. 23 (GTS): sum_i Omega_i W_i is invariant in a periodic box (wave fluxes telescope, particles
+    """Eq. 32 (GTS): sum_i Omega_i W_i is invariant in a periodic box (wave fluxes telescope, particles
     carry their own mass)."""
     case = wl.case_periodic_box(ni=16, end_ratio=20.0, n_ref=40, Kn=0.05)
     o = ob.Oracle(case, gts=True, precision=precision)
@@ -37,7 +37,7 @@ def test_gts_conserves_mass_momentum_energy_in_a_closed_box(precision):
 
 @pytest.mark.parametrize("precision,tol", [(1, 1e-12), (0, 2e-6)])
 def test_lts_conserves_time_weighted_sum(precision, tol):
-    """Eq. 46 with Eq. 37: under LTS, sum_i (Omega_i / dt_i) W_i is invariant in a periodic box (each face
+    """Eq. 53 with Eq. 41: under LTS, sum_i (Omega_i / dt_i) W_i is invariant in a periodic box (each face
     flux enters its two cells as -F s and +F s; a crossing particle contributes -m Psi / dt_L +
     (m dt_R / dt_L) Psi / dt_R = 0), while sum_i Omega_i W_i is not."""
     case = wl.case_periodic_box(ni=16, end_ratio=50.0, n_ref=40, Kn=0.05)
@@ -52,8 +52,8 @@ def test_lts_conserves_time_weighted_sum(precision, tol):
 
 
 def test_lts_with_equal_steps_is_gts_bit_for_bit():
-    """Sec. 4.2 closing remark: with equal local steps the LTS update is the GTS update (cells of exactly
-    equal size 1/16, so that the CFL steps of Eq. 24 are equal to the last bit)."""
+    """Sec. IV B closing remark: with equal local steps the LTS update is the GTS update (cells of exactly
+    equal size 1/16, so that the CFL steps of Eq. 33 are equal to the last bit)."""
     case = wl.case_periodic_box(ni=16, end_ratio=1.0, n_ref=30, Kn=0.05)
     a = ob.Oracle(case, gts=False, precision=0)
     b = ob.Oracle(case, gts=True, precision=0)
@@ -68,7 +68,7 @@ def test_lts_with_equal_steps_is_gts_bit_for_bit():
 
 
 def test_time_averaged_particle_flux_balance():
-    """Sec. 4.1, Eqs. 32-38: with fixed positive local steps and m_R = m_L dt_R / dt_L, the side-recorded
+    """Sec. IV A, Eqs. 35-43: with fixed positive local steps and m_R = m_L dt_R / dt_L, the side-recorded
     time-averaged particle fluxes sum(m_L) / (M dt_L) and sum(m_R) / (M dt_R) agree on every face."""
     case = wl.case_periodic_box(ni=10, end_ratio=50.0, n_ref=40, Kn=0.2)
     o = ob.Oracle(case, gts=False, precision=1, record_faces=True)
@@ -88,7 +88,7 @@ def test_time_averaged_particle_flux_balance():
 
 
 def test_counterexample_for_time_varying_steps():
-    """Sec. 4.1: for M = 2, dt_L = (1, 2), dt_R = (2, 2) the two sides of the unweighted balance condition
+    """Sec. IV A: for M = 2, dt_L = (1, 2), dt_R = (2, 2) the two sides of the unweighted balance condition
     are 4/3 and 3/2, so stepwise scaling alone does not balance time-varying steps."""
     for line in open(os.path.join(GOLD, "balance_counterexample.txt")):
         if line.startswith("#") or not line.strip():
@@ -152,7 +152,7 @@ def test_collisionless_limit_moves_particles_on_straight_rays():
 
 
 def test_sampling_moments():
-    """Eq. 17 with Sec. 4.2: new particles in a cell carry rho^hp Omega in total (N^hp m = rho^hp Omega),
+    """Eq. 26 with Sec. IV B: new particles in a cell carry rho^hp Omega in total (N^hp m = rho^hp Omega),
     and their velocities sample the Maxwellian of W^h (mean U, variance R T) within 5 sigma."""
     case = wl.case_periodic_box(ni=6, end_ratio=1.0, n_ref=2000, Kn=0.05)
     case.init_prim = np.tile([1.0, 0.4, 0.0, 1.3], (6, 1))
@@ -186,7 +186,7 @@ def test_sampling_moments():
 
 
 def test_free_flight_time_law():
-    """Eq. 18 with dt_i (Sec. 4.2): a retained particle collides within the step with probability
+    """Eq. 27 with dt_i (Sec. IV B): a retained particle collides within the step with probability
     1 - e^{-dt_i/tau_i}."""
     case = wl.case_periodic_box(ni=4, end_ratio=1.0, n_ref=3000, Kn=0.05)
     case.init_prim = np.tile([1.0, 0.0, 0.0, 1.0], (4, 1))
@@ -201,7 +201,7 @@ def test_free_flight_time_law():
 
 
 def _exact_path(x0, u, cell, xs, dts, ni):
-    """Brute force of Eqs. 19 and 45 with rationals: move for t_f = dt_cell; at each face crossing scale the
+    """Brute force of Eqs. 28 and 45 with rationals: move for t_f = dt_cell; at each face crossing scale the
     mass and the remaining time by dt_R / dt_L; the line is periodic."""
     L = xs[-1] - xs[0]
     x, tr, m, c = Fraction(x0), Fraction(dts[cell]), Fraction(1), cell
@@ -224,7 +224,7 @@ def _exact_path(x0, u, cell, xs, dts, ni):
 
 @pytest.mark.parametrize("u", [37.0, -23.5, 3.1, -0.7])
 def test_brute_force_single_particle_transport(u):
-    """Eqs. 19, 37, 45: a retained particle that never collides (tau -> infinity) crossing several cells
+    """Eqs. 28, 41, 52: a retained particle that never collides (tau -> infinity) crossing several cells
     of different local time steps, against exact rational arithmetic."""
     case = wl.case_periodic_box(ni=6, end_ratio=30.0, n_ref=5, Kn=1e9)
     o = ob.Oracle(case, gts=False, precision=1)
