@@ -324,6 +324,7 @@ def run_convergence(args):
     for ts in ("LTS", "GTS"):
         gts = ts == "GTS"
         r = {}
+        out["results"][ts] = r
         # (i) particle-free, to 1e-6 in every conservative component (checked every 200 steps)
         s = ugkwp.Solver(case, gts=gts, precision=0, wave_only=True, stream=stream.cuda_stream, use_graph=True)
         t0 = time.perf_counter()
@@ -338,20 +339,29 @@ def run_convergence(args):
         r["wave_only_wall_s"] = time.perf_counter() - t0
         r["wave_only_final_residual"] = res
         s.close()
-        # (ii) stochastic: stagnation p and q per step, steady by EMA
+        print(json.dumps({"phase": f"{ts} wave_only", **r}), flush=True)
+        # (ii) stochastic: stagnation p and q per step, steady by EMA. GTS keeps far more particles (every
+        # cell samples with the global, smallest, time step), hence the larger particle capacity.
         n = args.lts_steps if not gts else args.gts_steps
-        s = ugkwp.Solver(case, gts=gts, precision=0, stream=stream.cuda_stream, use_graph=True)
+        cap = (32 if gts else 8) * case.n_ref * case.mesh.ncells
+        s = ugkwp.Solver(case, gts=gts, precision=0, stream=stream.cuda_stream, use_graph=True, capacity=cap)
         j0, j1 = stagnation_pair(case)
         hp, hq, hres, hnp = [], [], [], []
         t0 = time.perf_counter()
-        for k in range(n):
-            s.step(1)
-            p, _, q = s.surface(averaged=False)
-            hp.append(0.5 * (p[j0] + p[j1]))
-            hq.append(0.5 * (q[j0] + q[j1]))
-            if k % 50 == 0:
-                hres.append(float(np.max(s.residual()[:4])))
-                hnp.append(s.num_particles())
+        try:
+            for k in range(n):
+                s.step(1)
+                p, _, q = s.surface(averaged=False)
+                hp.append(0.5 * (p[j0] + p[j1]))
+                hq.append(0.5 * (q[j0] + q[j1]))
+                if k % 50 == 0:
+                    hres.append(float(np.max(s.residual()[:4])))
+                    hnp.append(s.num_particles())
+        except ugkwp.UgkwpError as e:
+            r["stochastic_error"] = f"step {len(hp)}: {e}; particles {hnp[-3:]}"
+            print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
+            s.close()
+            continue
         wall = time.perf_counter() - t0
         kp, _ = steady_step(hp)
         kq, _ = steady_step(hq)
@@ -361,15 +371,16 @@ def run_convergence(args):
                   "wall_s_to_steady_est": wall * k_st / n, "ms_per_step": 1e3 * wall / n,
                   "residual_plateau": float(np.median(hres[len(hres) // 2:])),
                   "particles_mean": float(np.mean(hnp[len(hnp) // 2:])),
+                  "particles_max": int(np.max(hnp)),
                   "stagnation_Cp": float((np.mean(hp[-n // 5:]) - 0.5) / (0.5 * U * U)),
                   "stagnation_CQ": float(np.mean(hq[-n // 5:]) / (0.5 * U ** 3))})
         s.close()
-        out["results"][ts] = r
+        print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
     L, G = out["results"]["LTS"], out["results"]["GTS"]
-    if L["wave_only_steps_to_1e-6"] and G["wave_only_steps_to_1e-6"]:
+    if L.get("wave_only_steps_to_1e-6") and G.get("wave_only_steps_to_1e-6"):
         out["wave_only_speedup_steps"] = G["wave_only_steps_to_1e-6"] / L["wave_only_steps_to_1e-6"]
         out["wave_only_speedup_wall"] = G["wave_only_wall_s"] / L["wave_only_wall_s"]
-    if L["steps_to_steady"]:
+    if L.get("steps_to_steady") and G.get("steps_to_steady"):
         out["stochastic_speedup_steps"] = G["steps_to_steady"] / max(L["steps_to_steady"], 1)
         out["stochastic_speedup_wall"] = G["wall_s_to_steady_est"] / max(L["wall_s_to_steady_est"], 1e-9)
     print(json.dumps(out))

@@ -172,6 +172,65 @@ ugkwp_status ugkwp_load(ugkwp_ctx* ctx, const char* path);
  * clears the record (ms needs room for 8 values). */
 ugkwp_status ugkwp_set_profiling(ugkwp_ctx* ctx, int32_t enable);
 ugkwp_status ugkwp_profile(ugkwp_ctx* ctx, double* ms, int64_t* steps);
+/* ---- Learned warm start -------------------------------------------------------------------------------
+ * A coordinate MLP maps a cell centroid and the case conditions (x, y, Kn, Ma, T_w) to an initial field
+ * (log rho, u / U_inf, v / U_inf, log T). It only changes the field the steady LTS iteration (Sec. III C,
+ * Sec. IV B) starts from: the local time steps stay those of the freestream (fixed at creation) and the
+ * iteration is unchanged, so the converged state is the method's own. The paper has no such network; it is
+ * an addition for fewer steps to steady state.
+ *
+ * Network: n_features inputs (>= 37), `depth` hidden SiLU layers of `width` units, n_out linear outputs.
+ * Parameters are FP32 master values (one vector: every layer's weight matrix [out][in] row-major in layer
+ * order, then every layer's bias in layer order); every product uses them rounded to BF16, with FP32
+ * activations and accumulation. All device pointers below are caller-owned device memory; calls run on the
+ * network's stream (ugkwp_mlp_create) unless stated otherwise. */
+typedef struct ugkwp_mlp ugkwp_mlp;
+
+/* Feature map of one geometry family: x^ = asinh((x - cx) / ell) / asinh(ext / ell), same for y with cy;
+ * the features of a point are sin/cos(2^k pi x^), sin/cos(2^k pi y^) for k = 0..7 (32 values, in that
+ * block order), x^, y^, log10 Kn, Ma and T_w each mapped linearly from [lo, hi] to [-1, 1], then zeros up
+ * to n_features. */
+typedef struct {
+    double cx, cy, ell, ext;
+    double kn_lo, kn_hi, ma_lo, ma_hi, tw_lo, tw_hi;
+} ugkwp_feature_map;
+
+/* params: host, ugkwp_mlp_num_params floats, or NULL for all zeros. EINVAL on bad sizes. */
+ugkwp_status ugkwp_mlp_create(int32_t n_features, int32_t width, int32_t depth, int32_t n_out, const float* params,
+                              void* stream, ugkwp_mlp** out);
+void ugkwp_mlp_destroy(ugkwp_mlp* mlp);
+int64_t ugkwp_mlp_num_params(const ugkwp_mlp* mlp);
+/* Host copies of the parameters and of the gradient of the last ugkwp_mlp_grad (either may be NULL). */
+ugkwp_status ugkwp_mlp_get_params(ugkwp_mlp* mlp, float* params, float* grad);
+/* Replace the parameters from host memory; resets the Adam state. Synchronises. */
+ugkwp_status ugkwp_mlp_set_params(ugkwp_mlp* mlp, const float* params);
+/* y[n][n_out] = network(x[n][n_features]), device arrays. Asynchronous. */
+ugkwp_status ugkwp_mlp_forward(ugkwp_mlp* mlp, const float* x, int32_t n, float* y);
+/* Gradient of the mean squared error (1 / (n n_out)) sum (y - t)^2 over the points rows[0..n-1] of the
+ * device arrays x[.][n_features] and t[.][n_out] (rows NULL: points 0..n-1), kept on the device for
+ * ugkwp_mlp_adam; loss (host, nullable) receives the loss (then the call synchronises). Deterministic. */
+ugkwp_status ugkwp_mlp_grad(ugkwp_mlp* mlp, const float* x, const float* t, const int32_t* rows, int32_t n,
+                            float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with learning rate lr on the last
+ * gradient. Asynchronous. */
+ugkwp_status ugkwp_mlp_adam(ugkwp_mlp* mlp, float lr);
+/* Feature rows feat[n][n_features] of the points (x[i], y[i]) (device arrays; y NULL: 0) for one case's
+ * conditions, on `stream`. */
+ugkwp_status ugkwp_mlp_features(const ugkwp_feature_map* fmap, const double* x, const double* y, int32_t n,
+                                double Kn, double Ma, double Tw, int32_t n_features, float* feat, void* stream);
+/* acc[4 C] (device) = W (reset != 0) or acc + W: running sums of the conservative field for a time
+ * average. On the context's stream. */
+ugkwp_status ugkwp_field_accumulate(ugkwp_ctx* ctx, double* acc, int32_t reset);
+/* Training pairs of every cell of a context: features of the cell centroids (feat[C][n_features]) and
+ * targets (targ[C][4]) of the field W * scale, W a device array of 4 C conservative values (NULL: the
+ * context's current field, scale ignored). On the context's stream. */
+ugkwp_status ugkwp_mlp_dataset(ugkwp_ctx* ctx, const ugkwp_feature_map* fmap, const double* W, double scale,
+                               int32_t n_features, float* feat, float* targ);
+/* Set the context's field from the network at its cell centroids: rho = exp(y0) in [1e-6, 1e6],
+ * (u, v) = U_inf (y1, y2) with speed at most U_cap / 2, T = exp(y3) in [2 T_min, T_cap / 2] (bounds as in
+ * ugkwp_stats); removes all particles (W^p = 0), as ugkwp_set_field. Synchronises. n_out must be 4. */
+ugkwp_status ugkwp_warm_start(ugkwp_ctx* ctx, ugkwp_mlp* mlp, const ugkwp_feature_map* fmap);
+
 const char* ugkwp_last_error(const ugkwp_ctx* ctx);
 
 #ifdef __cplusplus

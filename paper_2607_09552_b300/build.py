@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libugkwp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
-UNITS = {"ugkwp_core.cu": ["-fmad=false"], "ugkwp_flux.cu": []}
+UNITS = {"ugkwp_core.cu": ["-fmad=false"], "ugkwp_flux.cu": [], "ugkwp_mlp.cu": []}
 DEPS = ["ugkwp_internal.h", "ugkwp_detmath.cuh"]
 
 

@@ -1178,6 +1178,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     }
     const int F = mesh->dim == 1 ? (periodic_i ? ni : ni + 1) : (ni + 1) * nj + ni * (mesh->periodic_j ? nj : nj + 1);
     ctx.ni = ni; ctx.nj = nj; ctx.periodic_j = mesh->periodic_j;
+    ctx.Kn = Kn; ctx.Ma = Ma;
     StepConsts& K = ctx.k;
     K.C = C; K.F = F; K.dim = mesh->dim; K.n_ref = opts->n_ref; K.wave_only = opts->wave_only;
     K.prec = opts->precision ? 1 : 0;
@@ -1852,3 +1853,4 @@ const char* ugkwp_last_error(const ugkwp_ctx* h)
 }
 
 }  // extern "C"
+

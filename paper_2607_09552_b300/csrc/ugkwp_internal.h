@@ -93,6 +93,7 @@ struct Ctx {
     cudaStream_t stream2 = nullptr;              // wave fluxes, overlapped with the particle kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t step = 0;
+    double Kn = 0.0, Ma = 0.0;                   // case conditions (warm-start features)
     int use_graph = 0;
     cudaGraphExec_t graph = nullptr;
     std::string msg;

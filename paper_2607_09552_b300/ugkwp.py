@@ -22,7 +22,10 @@ EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugk
            "ugkwp_set_field", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
            "ugkwp_set_state", "ugkwp_get_tallies", "ugkwp_get_cell_data", "ugkwp_get_flux", "ugkwp_get_geometry",
            "ugkwp_fixed_exponents", "ugkwp_save", "ugkwp_load", "ugkwp_batch_create", "ugkwp_batch_step",
-           "ugkwp_batch_destroy", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_last_error"]
+           "ugkwp_batch_destroy", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_mlp_create", "ugkwp_mlp_destroy",
+           "ugkwp_mlp_num_params", "ugkwp_mlp_get_params", "ugkwp_mlp_set_params", "ugkwp_mlp_forward",
+           "ugkwp_mlp_grad", "ugkwp_mlp_adam", "ugkwp_mlp_features", "ugkwp_field_accumulate", "ugkwp_mlp_dataset",
+           "ugkwp_warm_start", "ugkwp_last_error"]
 STAGES = ["decompose", "sample", "particles", "wave_flux", "sort", "update"]
 
 
@@ -58,6 +61,8 @@ def load():
         lib.ugkwp_num_particles.restype = C.c_int64
         lib.ugkwp_destroy.restype = None
         lib.ugkwp_batch_destroy.restype = None
+        lib.ugkwp_mlp_destroy.restype = None
+        lib.ugkwp_mlp_num_params.restype = C.c_int64
         _lib = lib
     return _lib
 
@@ -68,6 +73,24 @@ def _p(a, t):
 
 def _d(a):
     return _p(a, C.c_double)
+
+
+class UgkwpFeatureMap(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("cx", "cy", "ell", "ext", "kn_lo", "kn_hi", "ma_lo", "ma_hi", "tw_lo",
+                                          "tw_hi")]
+
+
+def feature_map(fm: dict) -> UgkwpFeatureMap:
+    return UgkwpFeatureMap(*[float(fm[k]) for k, _ in UgkwpFeatureMap._fields_])
+
+
+def _dev(t):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
 
 
 class UgkwpError(RuntimeError):
@@ -219,6 +242,26 @@ class Solver:
         self._check(load().ugkwp_get_flux(self.ctx, _d(out)))
         return out.reshape(self.F, 4)
 
+    def field_accumulate(self, acc, reset: bool = False):
+        """acc (float64 CUDA tensor of 4 C values) = W or acc + W."""
+        if acc.dtype.itemsize != 8 or acc.numel() != 4 * self.C:
+            raise ValueError("acc must hold 4 C float64 values")
+        self._check(load().ugkwp_field_accumulate(self.ctx, _dev(acc), C.c_int32(int(reset))))
+
+    def dataset(self, fmap: dict, W=None, scale: float = 1.0, n_features: int = 64):
+        """(features [C][n_features], targets [C][4]) float32 CUDA tensors of the current field or of W * scale."""
+        import torch
+        feat = torch.empty((self.C, n_features), dtype=torch.float32, device="cuda")
+        targ = torch.empty((self.C, 4), dtype=torch.float32, device="cuda")
+        fm = feature_map(fmap)
+        self._check(load().ugkwp_mlp_dataset(self.ctx, C.byref(fm), _dev(W), C.c_double(scale),
+                                             C.c_int32(n_features), _dev(feat), _dev(targ)))
+        return feat, targ
+
+    def warm_start(self, mlp, fmap: dict):
+        fm = feature_map(fmap)
+        self._check(load().ugkwp_warm_start(self.ctx, mlp.h, C.byref(fm)))
+
 
 class Batch:
     """Several Solver contexts advanced together by one graph launch per step (ugkwp_batch_*)."""
@@ -244,3 +287,82 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+class Mlp:
+    """The warm-start network (ugkwp_mlp_*): parameters, forward, gradient and Adam on the device."""
+
+    def __init__(self, n_features: int = 64, width: int = 256, depth: int = 4, n_out: int = 4, params=None,
+                 stream=None):
+        L = load()
+        self.shape = (n_features, width, depth, n_out)
+        self.h = C.c_void_p()
+        p = None
+        if params is not None:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+        st = L.ugkwp_mlp_create(C.c_int32(n_features), C.c_int32(width), C.c_int32(depth), C.c_int32(n_out),
+                                None if p is None else _p(p, C.c_float), C.c_void_p(stream), C.byref(self.h))
+        if st != 0:
+            raise UgkwpError(st, "ugkwp_mlp_create")
+        self.n = int(L.ugkwp_mlp_num_params(self.h))
+        if p is not None and p.size != self.n:
+            self.close()
+            raise ValueError(f"expected {self.n} parameters, got {p.size}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().ugkwp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    @staticmethod
+    def _check(st, what):
+        if st != 0:
+            raise UgkwpError(st, what)
+
+    def params(self):
+        out = np.zeros(self.n, dtype=np.float32)
+        self._check(load().ugkwp_mlp_get_params(self.h, _p(out, C.c_float), None), "ugkwp_mlp_get_params")
+        return out
+
+    def grad(self):
+        out = np.zeros(self.n, dtype=np.float32)
+        self._check(load().ugkwp_mlp_get_params(self.h, None, _p(out, C.c_float)), "ugkwp_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.n:
+            raise ValueError(f"expected {self.n} parameters, got {p.size}")
+        self._check(load().ugkwp_mlp_set_params(self.h, _p(p, C.c_float)), "ugkwp_mlp_set_params")
+
+    def forward(self, x):
+        import torch
+        y = torch.empty((x.shape[0], self.shape[3]), dtype=torch.float32, device=x.device)
+        self._check(load().ugkwp_mlp_forward(self.h, _dev(x), C.c_int32(x.shape[0]), _dev(y)), "ugkwp_mlp_forward")
+        return y
+
+    def loss_grad(self, x, t, rows=None, want_loss: bool = True):
+        n = x.shape[0] if rows is None else rows.shape[0]
+        loss = C.c_float()
+        self._check(load().ugkwp_mlp_grad(self.h, _dev(x), _dev(t), _dev(rows), C.c_int32(n),
+                                          C.byref(loss) if want_loss else None), "ugkwp_mlp_grad")
+        return loss.value if want_loss else None
+
+    def adam(self, lr: float):
+        self._check(load().ugkwp_mlp_adam(self.h, C.c_float(lr)), "ugkwp_mlp_adam")
+
+
+def mlp_features(fmap: dict, x, y, Kn: float, Ma: float, Tw: float, n_features: int = 64, stream=None):
+    """Feature rows (float32 CUDA tensor [n][n_features]) of the points of float64 CUDA tensors x, y."""
+    import torch
+    feat = torch.empty((x.shape[0], n_features), dtype=torch.float32, device=x.device)
+    fm = feature_map(fmap)
+    st = load().ugkwp_mlp_features(C.byref(fm), _dev(x), _dev(y), C.c_int32(x.shape[0]), C.c_double(Kn),
+                                   C.c_double(Ma), C.c_double(Tw), C.c_int32(n_features), _dev(feat),
+                                   C.c_void_p(stream))
+    if st != 0:
+        raise UgkwpError(st, "ugkwp_mlp_features")
+    return feat

@@ -238,3 +238,28 @@ def batch_sweep(seed: int = 0, n_cases: int = 16, n_plates: int = 4, scale: floa
         c.seed = seed * 1000 + k
         cases.append(c)
     return cases
+
+
+def mlp_init(seed: int, n_features: int = 64, width: int = 256, depth: int = 4, n_out: int = 4) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network (float32): weights uniform in (-a, a) with
+    a = sqrt(6 / fan_in), zero biases. Layout: every layer's weight matrix [out][in] row-major in layer order,
+    then every layer's bias in layer order."""
+    rng = np.random.default_rng(seed)
+    ins = [n_features] + [width] * depth
+    outs = [width] * depth + [n_out]
+    parts = [rng.uniform(-math.sqrt(6.0 / i), math.sqrt(6.0 / i), size=i * o) for i, o in zip(ins, outs)]
+    parts += [np.zeros(o) for o in outs]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def held_out_conditions(seed: int = 1000, n_cyl: int = 4, n_plate: int = 4):
+    """Seeded (geometry, Kn, Ma, T_w) conditions for evaluation cases, drawn from the same ranges as
+    `batch_sweep` but from a different seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_cyl + n_plate):
+        kn = 10.0 ** rng.uniform(math.log10(0.005), math.log10(0.2))
+        ma = rng.uniform(5.0, 15.0)
+        tw = rng.uniform(1.0, 5.0)
+        out.append(("cylinder" if k < n_cyl else "plate", kn, ma, tw))
+    return out
