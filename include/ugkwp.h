@@ -114,6 +114,15 @@ ugkwp_status ugkwp_set_field(ugkwp_ctx* ctx, const double* prim);
 /* W (4 C doubles: rho, rho U, rho V, rho E) and, if Wp != NULL, W^p of the retained particles. */
 ugkwp_status ugkwp_get_field(ugkwp_ctx* ctx, double* W, double* Wp);
 
+/* ugkwp_get_field without allocating: the same values, with the W^p conversion in a fixed device scratch
+ * array instead of a per-call temporary (the paper has no counterpart; it serves callers that must not
+ * allocate, e.g. a monitor sampling a case while a batched launch runs on other streams, since cudaMalloc
+ * and cudaFree synchronise the whole device). Limit: meshes of at most 98304 cells, else EINVAL with a
+ * message. The scratch is shared by all calls on a device: overlapping calls race, callers serialise them.
+ * The first call with Wp != NULL on a device looks the scratch up; make it before any stream capture.
+ * Synchronises. */
+ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* ctx, double* W, double* Wp);
+
 /* out[11]: steps taken, particles, new in the last step, removed (collided), left the domain, face
  * crossings, wall hits, largest crossings + hits of one particle in the last step; then, cumulative since
  * creation, particle-steps processed (retained + new particles of every step) and new particles; then the

@@ -1854,3 +1854,57 @@ const char* ugkwp_last_error(const ugkwp_ctx* h)
 
 }  // extern "C"
 
+// ---- ugkwp_get_field_noalloc: ugkwp_get_field without any allocation ------------------------------------
+// For callers that must not allocate device memory: cudaMalloc and cudaFree synchronise the whole device,
+// so a monitor thread that samples a running case while other cases run on other streams (the batched
+// launch) would stall all of them, and a run whose particle buffers were sized to fill device memory has
+// no room left for a temporary. The W^p conversion goes through a fixed scratch array in device memory
+// instead of a per-call temporary; nothing else differs from ugkwp_get_field (same kernel, same values).
+//
+// Scratch: 4 doubles per cell for at most kNoAllocMaxCells cells (3 MiB per device). Nothing in it needs to
+// start at zero: every element read is first written by the same call. All calls on one device share it, so
+// calls that overlap in time (from several host threads, or for several contexts on one device) race on it:
+// callers serialise them. The scratch address is looked up once per device (cudaGetSymbolAddress) on the
+// first call with a non-NULL Wp on that device; make that first call before any stream capture begins.
+#include <mutex>
+
+namespace {
+constexpr int kNoAllocMaxCells = 98304;
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[4 * kNoAllocMaxCells];
+
+extern "C" ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* h, double* W, double* Wp)
+{
+    if (!h || !W) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C;
+    if (C > kNoAllocMaxCells)
+        return fail(ctx, UGKWP_EINVAL, "ugkwp_get_field_noalloc: the mesh has more than 98304 cells (its scratch limit)");
+    CK(cudaMemcpyAsync(W, ctx.d.W, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    if (Wp) {
+        int dev = -1;
+        CK(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= kNoAllocMaxDevices)
+            return fail(ctx, UGKWP_EINVAL, "ugkwp_get_field_noalloc: device ordinal beyond its table of 64");
+        double* scratch = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(g_noalloc_mu);
+            if (!g_noalloc_ptr[dev]) {
+                void* p = nullptr;
+                const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+                if (e != cudaSuccess || !p)
+                    return fail(ctx, UGKWP_ECUDA, "ugkwp_get_field_noalloc: cudaGetSymbolAddress of the scratch failed");
+                g_noalloc_ptr[dev] = static_cast<double*>(p);
+            }
+            scratch = g_noalloc_ptr[dev];
+        }
+        k_wp_field<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, ctx.k.fx0, ctx.k.fx1, ctx.k.fx4, scratch);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(Wp, scratch, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    }
+    return check_device_error(ctx);
+}

@@ -25,7 +25,7 @@ EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugk
            "ugkwp_batch_destroy", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_mlp_create", "ugkwp_mlp_destroy",
            "ugkwp_mlp_num_params", "ugkwp_mlp_get_params", "ugkwp_mlp_set_params", "ugkwp_mlp_forward",
            "ugkwp_mlp_grad", "ugkwp_mlp_adam", "ugkwp_mlp_features", "ugkwp_field_accumulate", "ugkwp_mlp_dataset",
-           "ugkwp_warm_start", "ugkwp_last_error"]
+           "ugkwp_warm_start", "ugkwp_get_field_noalloc", "ugkwp_last_error"]
 STAGES = ["decompose", "sample", "particles", "wave_flux", "sort", "update"]
 
 
@@ -157,6 +157,13 @@ class Solver:
         Wp = np.zeros(4 * self.C)
         self._check(load().ugkwp_get_field(self.ctx, _d(W), _d(Wp)))
         return W.reshape(self.C, 4), Wp.reshape(self.C, 4)
+
+    def field_noalloc(self, with_wp: bool = True):
+        """As field(), through ugkwp_get_field_noalloc (no device allocation; meshes up to 98304 cells)."""
+        W = np.zeros(4 * self.C)
+        Wp = np.zeros(4 * self.C) if with_wp else None
+        self._check(load().ugkwp_get_field_noalloc(self.ctx, _d(W), None if Wp is None else _d(Wp)))
+        return W.reshape(self.C, 4), (None if Wp is None else Wp.reshape(self.C, 4))
 
     def residual(self):
         out = np.zeros(8)
