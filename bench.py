@@ -296,93 +296,83 @@ def stagnation_pair(case):
     return nj // 2 - 1, nj // 2
 
 
-def steady_step(hist, alpha=2.0 / 1001.0, tol=0.01, window=0.2):
-    """First step after which the EMA (alpha = 2/1001) of a monitored history stays within tol of the mean
-    of its final window (fraction `window` of the run)."""
-    h = np.asarray(hist, dtype=np.float64)
-    ema = np.empty_like(h)
-    e = h[0]
-    for k, v in enumerate(h):
-        e = e + alpha * (v - e) if k else v
-        ema[k] = e
-    ref = ema[int(len(h) * (1 - window)):].mean()
-    bad = np.nonzero(np.abs(ema - ref) > tol * abs(ref))[0]
-    return int(bad[-1] + 1) if bad.size else 0, ema
-
-
 def run_convergence(args):
-    """Steps and wall-clock to convergence, LTS vs GTS, on the bench workload (and the dense-regime
-    cylinder with --case kn001): (i) the deterministic particle-free mode (GKS limit) to a 1e-6 residual;
-    (ii) the full stochastic method to "steady" by the EMA of the stagnation-point pressure and heat flux."""
+    """Steps and wall-clock to convergence, LTS vs GTS, on the bench workload (and the dense-regime cylinder
+    with --case kn001): (i) the deterministic particle-free mode (GKS limit, all FP64) to a 1e-6 residual
+    (GKS convention: relative to the run's first step), with the steps at which 1e-3 .. 1e-6 were crossed;
+    (ii) the full stochastic method (production precision) to "steady": the EMA (alpha = 2/1001) of the
+    drag and heat-load coefficients stays within 1% of its final-window mean."""
     import torch
-    from paper_2607_09552_b300 import ugkwp
+    from paper_2607_09552_b300 import steady, ugkwp
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     case = wl.case_cylinder_kn001() if args.case == "kn001" else bench_case()
     out = {"mode": "convergence", "workload": config_dict(case, 0, "n/a")["workload"] if args.case != "kn001" else
            "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8", "results": {}}
+    geom = steady.wall_geometry(case)
     for ts in ("LTS", "GTS"):
         gts = ts == "GTS"
         r = {}
         out["results"][ts] = r
-        # (i) particle-free, to 1e-6 in every conservative component (checked every 200 steps)
-        s = ugkwp.Solver(case, gts=gts, precision=0, wave_only=True, stream=stream.cuda_stream, use_graph=True)
-        t0 = time.perf_counter()
-        steps, res = 0, 1.0
-        while steps < args.max_wave_steps:
-            s.step(200)
-            steps += 200
-            res = float(np.max(s.residual()[:4]))
-            if res < 1e-6:
-                break
-        r["wave_only_steps_to_1e-6"] = steps if res < 1e-6 else None
-        r["wave_only_wall_s"] = time.perf_counter() - t0
-        r["wave_only_final_residual"] = res
-        s.close()
-        print(json.dumps({"phase": f"{ts} wave_only", **r}), flush=True)
-        # (ii) stochastic: stagnation p and q per step, steady by EMA. GTS keeps far more particles (every
-        # cell samples with the global, smallest, time step), hence the larger particle capacity.
+        if not args.skip_wave:
+            s = ugkwp.Solver(case, gts=gts, precision=1, wave_only=True, stream=stream.cuda_stream, use_graph=True)
+            w = steady.run_to_residual(s, 1e-6, args.max_wave_steps, 500)
+            r["wave_only_fp64"] = {"steps_to_1e-6": w["steps"] if w["converged"] else None,
+                                   "wall_s": w["seconds"], "final_residual": w["residual"],
+                                   "ms_per_step": 1e3 * w["seconds"] / w["steps"],
+                                   "marks": {f"{k:.0e}": v for k, v in w["marks"].items()}}
+            s.close()
+            print(json.dumps({"phase": f"{ts} wave_only", **r}), flush=True)
         n = args.lts_steps if not gts else args.gts_steps
+        # GTS keeps far more particles (every cell samples with the smallest time step): larger capacity
         cap = (32 if gts else 8) * case.n_ref * case.mesh.ncells
         s = ugkwp.Solver(case, gts=gts, precision=0, stream=stream.cuda_stream, use_graph=True, capacity=cap)
         j0, j1 = stagnation_pair(case)
-        hp, hq, hres, hnp = [], [], [], []
+        hcd, hch, hp, hq, hres, hnp, ht = [], [], [], [], [], [], []
         t0 = time.perf_counter()
         try:
             for k in range(n):
                 s.step(1)
-                p, _, q = s.surface(averaged=False)
+                p, tau, q = s.surface(averaged=False)
+                cd, ch = steady.loads(case, p, tau, q, geom)
+                hcd.append(cd)
+                hch.append(ch)
                 hp.append(0.5 * (p[j0] + p[j1]))
                 hq.append(0.5 * (q[j0] + q[j1]))
-                if k % 50 == 0:
+                ht.append(time.perf_counter() - t0)
+                if k % 100 == 0:
                     hres.append(float(np.max(s.residual()[:4])))
                     hnp.append(s.num_particles())
         except ugkwp.UgkwpError as e:
-            r["stochastic_error"] = f"step {len(hp)}: {e}; particles {hnp[-3:]}"
+            r["stochastic_error"] = f"step {len(hcd)}: {e}; particles {hnp[-3:]}"
             print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
             s.close()
             continue
-        wall = time.perf_counter() - t0
-        kp, _ = steady_step(hp)
-        kq, _ = steady_step(hq)
-        k_st = max(kp, kq)
+        kd, _ = steady.steady_step(hcd)
+        kh, _ = steady.steady_step(hch)
+        k_st = max(kd, kh)
         U = wl.freestream_speed(case.Ma)
-        r.update({"stochastic_steps_run": n, "steps_to_steady": k_st, "wall_s_run": wall,
-                  "wall_s_to_steady_est": wall * k_st / n, "ms_per_step": 1e3 * wall / n,
-                  "residual_plateau": float(np.median(hres[len(hres) // 2:])),
-                  "particles_mean": float(np.mean(hnp[len(hnp) // 2:])),
-                  "particles_max": int(np.max(hnp)),
-                  "stagnation_Cp": float((np.mean(hp[-n // 5:]) - 0.5) / (0.5 * U * U)),
-                  "stagnation_CQ": float(np.mean(hq[-n // 5:]) / (0.5 * U ** 3))})
+        tail = slice(int(0.8 * n), n)
+        r["stochastic"] = {"steps_run": n, "steps_to_steady": k_st if k_st < n else None,
+                           "wall_s_to_steady": ht[k_st - 1] if 0 < k_st < n else None, "wall_s_run": ht[-1],
+                           "ms_per_step": 1e3 * ht[-1] / n, "steady_drag_step": kd, "steady_heat_step": kh,
+                           "Cd": float(np.mean(hcd[tail])), "CH": float(np.mean(hch[tail])),
+                           "stagnation_Cp": float((np.mean(hp[tail]) - 0.5) / (0.5 * U * U)),
+                           "stagnation_CQ": float(np.mean(hq[tail]) / (0.5 * U ** 3)),
+                           "residual_plateau": float(np.median(hres[len(hres) // 2:])),
+                           "particles_mean": float(np.mean(hnp[len(hnp) // 2:])), "particles_max": int(np.max(hnp)),
+                           "drag_history_every_500": [round(x, 5) for x in hcd[::500]]}
         s.close()
         print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
     L, G = out["results"]["LTS"], out["results"]["GTS"]
-    if L.get("wave_only_steps_to_1e-6") and G.get("wave_only_steps_to_1e-6"):
-        out["wave_only_speedup_steps"] = G["wave_only_steps_to_1e-6"] / L["wave_only_steps_to_1e-6"]
-        out["wave_only_speedup_wall"] = G["wave_only_wall_s"] / L["wave_only_wall_s"]
-    if L.get("steps_to_steady") and G.get("steps_to_steady"):
-        out["stochastic_speedup_steps"] = G["steps_to_steady"] / max(L["steps_to_steady"], 1)
-        out["stochastic_speedup_wall"] = G["wall_s_to_steady_est"] / max(L["wall_s_to_steady_est"], 1e-9)
+    lw, gw = L.get("wave_only_fp64", {}), G.get("wave_only_fp64", {})
+    if lw.get("steps_to_1e-6") and gw.get("steps_to_1e-6"):
+        out["wave_only_speedup_steps"] = gw["steps_to_1e-6"] / lw["steps_to_1e-6"]
+        out["wave_only_speedup_wall"] = gw["wall_s"] / lw["wall_s"]
+    ls, gs = L.get("stochastic", {}), G.get("stochastic", {})
+    if ls.get("steps_to_steady") and gs.get("steps_to_steady"):
+        out["stochastic_speedup_steps"] = gs["steps_to_steady"] / ls["steps_to_steady"]
+        out["stochastic_speedup_wall"] = gs["wall_s_to_steady"] / ls["wall_s_to_steady"]
     print(json.dumps(out))
 
 
@@ -426,6 +416,150 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+def run_warmstart(args):
+    """Learned warm start (all on the GPU): converged particle-free fields of seeded sweeps of 16 uneven
+    cases (cylinders and plates, batched graph launches) train one network per geometry family; then held-out
+    seeded cases are solved from the freestream and from the network: (i) particle-free, all FP64, to a 1e-6
+    residual (relative to the freestream start's first step), each case alone and, warm-started, all cases in
+    one batched launch; (ii) the stochastic method to steady (drag and heat-load EMA), with the averaged wall
+    p, tau_w, q of the warm-started run against the freestream-started one."""
+    import torch
+    from paper_2607_09552_b300 import steady, ugkwp
+    from paper_2607_09552_b300 import warmstart as ws
+    torch.cuda.set_device(0)
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"mode": "warmstart", "train": {}, "eval": []}
+    sets = {"cylinder": ws.TrainingSet(), "plate": ws.TrainingSet()}
+    t_all = time.perf_counter()
+    for seed in range(args.train_sweeps):
+        cases = wl.batch_sweep(seed)
+        solvers = [ugkwp.Solver(c, precision=0, wave_only=True, stream=st) for c in cases]
+        b = ugkwp.Batch(solvers, stream=st)
+        t0, steps = time.perf_counter(), 0
+        res = [1.0] * len(solvers)
+        while steps < args.train_max_steps:
+            b.step(1000)
+            steps += 1000
+            res = [float(np.max(s.residual()[:4])) for s in solvers]
+            if max(res) < args.train_tol:
+                break
+        for c, sv in zip(cases, solvers):
+            sets[ws.family(c)].add(sv, ws.FAMILY_MAPS[ws.family(c)])
+        b.close()
+        for sv in solvers:
+            sv.close()
+        out["train"][f"sweep{seed}"] = {"steps": steps, "seconds": time.perf_counter() - t0,
+                                        "max_residual": max(res), "median_residual": float(np.median(res))}
+        print(json.dumps({"phase": f"training fields, sweep {seed}", **out["train"][f"sweep{seed}"]}), flush=True)
+    nets = {}
+    for fam, tset in sets.items():
+        feats, targs = tset.tensors()
+        net = ws.new_network(0)
+        t0 = time.perf_counter()
+        hist = ws.train(net, feats, targs, steps=args.train_steps, batch=8192, lr=2e-3, log_every=args.train_steps // 4)
+        torch.cuda.synchronize()
+        nets[fam] = net
+        out["train"][fam] = {"rows": int(feats.shape[0]), "fields": len(tset.sizes), "adam_steps": args.train_steps,
+                             "seconds": time.perf_counter() - t0, "loss": hist}
+        print(json.dumps({"phase": f"train {fam}", **out["train"][fam]}), flush=True)
+        del feats, targs
+    out["train"]["total_seconds"] = time.perf_counter() - t_all
+    # held-out cases
+    cases = []
+    for geo, kn, ma, tw in wl.held_out_conditions(1000, args.eval_cyl, args.eval_plate):
+        if geo == "cylinder":
+            c = wl.case_cylinder(120, 160, 1e-3, 15.0, Kn=kn, Ma=ma, Tw=tw, n_ref=100)
+        else:
+            c = wl.case_plate(Kn=kn, Ma=ma, Tw=tw, n_ref=50)
+        cases.append(c)
+    refs = [steady.first_residual(c, precision=1, wave_only=True, stream=st) for c in cases]
+    # (i) particle-free FP64 to 1e-6: cold alone, warm alone, warm batched
+    cold_total = warm_total = 0.0
+    for c, ref in zip(cases, refs):
+        fam = ws.family(c)
+        e = {"case": c.name, "family": fam, "Kn": c.Kn, "Ma": c.Ma, "Tw": c.Tw}
+        s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st, use_graph=True)
+        rc = steady.run_to_residual(s, 1e-6, args.eval_wave_max, 500, ref)
+        W_cold = s.field()[0]
+        s.close()
+        t0 = time.perf_counter()
+        s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st, use_graph=True)
+        s.warm_start(nets[fam], ws.FAMILY_MAPS[fam])
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
+        rw = steady.run_to_residual(s, 1e-6, args.eval_wave_max, 500, ref)
+        W_warm = s.field()[0]
+        s.close()
+        e["wave_only_fp64"] = {"cold_steps": rc["steps"] if rc["converged"] else None, "cold_s": rc["seconds"],
+                               "warm_steps": rw["steps"] if rw["converged"] else None,
+                               "warm_s": rw["seconds"] + t_inf, "warm_start_s": t_inf,
+                               "cold_final": rc["residual"], "warm_final": rw["residual"],
+                               "state_rel_diff": float(np.max(np.abs(W_warm - W_cold)) / np.max(np.abs(W_cold)))}
+        cold_total += rc["seconds"]
+        warm_total += rw["seconds"] + t_inf
+        out["eval"].append(e)
+        print(json.dumps({"phase": "eval wave-only", **e}), flush=True)
+    t0 = time.perf_counter()
+    solvers = []
+    for c in cases:
+        s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st)
+        s.warm_start(nets[ws.family(c)], ws.FAMILY_MAPS[ws.family(c)])
+        solvers.append(s)
+    b = ugkwp.Batch(solvers, stream=st)
+    done, steps = [None] * len(solvers), 0
+    while steps < args.eval_wave_max and any(d is None for d in done):
+        b.step(500)
+        steps += 500
+        for i, (s, ref) in enumerate(zip(solvers, refs)):
+            if done[i] is None and float(np.max(s.residual()[4:] / ref)) < 1e-6:
+                done[i] = steps
+    batched_s = time.perf_counter() - t0
+    b.close()
+    for s in solvers:
+        s.close()
+    out["wave_only_fp64_totals"] = {"cold_sequential_s": cold_total, "warm_sequential_s": warm_total,
+                                    "warm_batched_s": batched_s, "warm_batched_steps": done,
+                                    "speedup_warm_batched_vs_cold": cold_total / batched_s}
+    print(json.dumps({"phase": "eval wave-only totals", **out["wave_only_fp64_totals"]}), flush=True)
+    # (ii) stochastic method to steady: cold vs warm, averaged surfaces after steady
+    n, navg = args.eval_stoch_steps, 1000
+    for e, c in zip(out["eval"], cases):
+        fam = ws.family(c)
+        geom = steady.wall_geometry(c)
+        res = {}
+        for start in ("cold", "warm"):
+            s = ugkwp.Solver(c, precision=0, stream=st, use_graph=True)
+            if start == "warm":
+                s.warm_start(nets[fam], ws.FAMILY_MAPS[fam])
+            hcd, hch, ht = [], [], []
+            t0 = time.perf_counter()
+            for k in range(n):
+                s.step(1)
+                if k == n - navg:
+                    s.reset_surface()
+                p, tau, q = s.surface(averaged=False)
+                cd, ch = steady.loads(c, p, tau, q, geom)
+                hcd.append(cd)
+                hch.append(ch)
+                ht.append(time.perf_counter() - t0)
+            kd, _ = steady.steady_step(hcd)
+            kh, _ = steady.steady_step(hch)
+            k_st = max(kd, kh)
+            res[start] = {"steps_to_steady": k_st if k_st < n - navg else None,
+                          "wall_s_to_steady": ht[k_st - 1] if 0 < k_st < n - navg else None,
+                          "Cd": float(np.mean(hcd[-navg:])), "CH": float(np.mean(hch[-navg:])),
+                          "surface": s.surface(averaged=True)}
+            s.close()
+        pc, tc, qc = res["cold"].pop("surface")
+        pw, tw_, qw = res["warm"].pop("surface")
+        res["surface_rel_err"] = {"p": float(np.linalg.norm(pw - pc) / np.linalg.norm(pc)),
+                                  "tau_w": float(np.linalg.norm(tw_ - tc) / (np.sqrt(len(tc)) * np.max(np.abs(tc)))),
+                                  "q": float(np.linalg.norm(qw - qc) / np.linalg.norm(qc))}
+        e["stochastic"] = res
+        print(json.dumps({"phase": "eval stochastic", "case": c.name, **res}), flush=True)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,12 +570,21 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch"])
+    ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch", "warmstart"])
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--case", default="kn01", choices=["kn01", "kn001"])
     ap.add_argument("--max-wave-steps", type=int, default=400000)
-    ap.add_argument("--lts-steps", type=int, default=12000)
-    ap.add_argument("--gts-steps", type=int, default=40000)
+    ap.add_argument("--lts-steps", type=int, default=30000)
+    ap.add_argument("--gts-steps", type=int, default=150000)
+    ap.add_argument("--skip-wave", action="store_true")
+    ap.add_argument("--train-sweeps", type=int, default=4)
+    ap.add_argument("--train-tol", type=float, default=1e-5)
+    ap.add_argument("--train-max-steps", type=int, default=60000)
+    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--eval-cyl", type=int, default=4)
+    ap.add_argument("--eval-plate", type=int, default=4)
+    ap.add_argument("--eval-wave-max", type=int, default=200000)
+    ap.add_argument("--eval-stoch-steps", type=int, default=20000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -451,6 +594,8 @@ def main():
         run_convergence(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 

@@ -28,7 +28,13 @@ namespace ugk {
 namespace {
 
 constexpr int kScanBlock = 1024;
-constexpr int kChunk = 256;   // particles per dynamically claimed chunk of k_particles
+#ifndef UGKWP_CHUNK
+#define UGKWP_CHUNK 256
+#endif
+#ifndef UGKWP_PARTICLES_MINB
+#define UGKWP_PARTICLES_MINB 4
+#endif
+constexpr int kChunk = UGKWP_CHUNK;   // particles per dynamically claimed chunk of k_particles
 constexpr int kMaxCells = 1 << 20;
 
 // ------------------------------------------------------------------------------------------ scan
@@ -398,9 +404,12 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     Wp[2] = K.dim == 1 ? 0.0 : ((double)r[2] * s1) / vol;
     Wp[3] = ((double)r[4] * s4) / vol;
     // W^{p,-} of the retained particles is exactly the retained tally of the previous step (same particles,
-    // masses, velocities and cell); k_sample adds the new particles. W^{p,+} and the retained tally of this
-    // step start from the same value (every particle unchanged and kept); k_particles adds the changes.
-    for (int k = 0; k < 5; ++k) { d.wprev[5 * c + k] = r[k]; d.wm[5 * c + k] = r[k]; d.wpl[5 * c + k] = r[k]; }
+    // masses, velocities and cell); k_sample adds the new particles. W^{p,+} starts from the same value
+    // (every particle unchanged) and k_particles adds the changes; the retained tally of this step is
+    // W^{p,+} minus the collided particles that stay (wcol), formed in k_update.
+    for (int k = 0; k < 5; ++k) {
+        d.wprev[5 * c + k] = r[k]; d.wm[5 * c + k] = r[k]; d.wpl[5 * c + k] = r[k]; d.wcol[5 * c + k] = 0;
+    }
     for (int k = 0; k < 4; ++k) { Wh[k] = W[k] - Wp[k]; d.Wh[4 * c + k] = Wh[k]; }
     const double dt = d.dt[c];
     const double x = dt / tau;
@@ -634,7 +643,6 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
         for (int q = 0; q < 5; ++q) {
             d.wm[5 * c + q] += acc[q];
             d.wpl[5 * c + q] += acc[q];
-            d.wrt[5 * c + q] += acc[q];
         }
 }
 
@@ -646,7 +654,7 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
 // the survivors: compacted into the other buffer (warp-aggregated slots), or, on sort steps, written in
 // place for the counting sort.
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const Dev d, ParticleSoA<T> PA,
+__global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const StepConsts K, const Dev d, ParticleSoA<T> PA,
                                                    ParticleSoA<T> PB, const CellFaces<T>* __restrict__ cf,
                                                    PCell<T> pc, const long long* dstep)
 {
@@ -784,11 +792,12 @@ __global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const 
             } else {
                 n_left++;
             }
-            // W^{p,+} and the retained tally started as W^{p,-} (each particle unchanged in its cell and kept).
-            // A particle that crossed a face, met a boundary or left moves its contribution; a collided one
-            // leaves the retained tally. Integer sums: identical to summing every final contribution.
+            // W^{p,+} started as W^{p,-} (each particle unchanged in its cell). A particle that crossed a face,
+            // met a boundary or left moves its contribution; a collided one that stays is added to wcol, and
+            // the retained tally W^{p,+} - wcol is formed in k_update. Integer sums: identical to summing
+            // every final contribution.
             unsigned long long* pl = reinterpret_cast<unsigned long long*>(d.wpl);
-            unsigned long long* rt = reinterpret_cast<unsigned long long*>(d.wrt);
+            unsigned long long* cl = reinterpret_cast<unsigned long long*>(d.wcol);
             if (it > 0) {
                 long long o[5], f[5];
                 fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
@@ -796,15 +805,14 @@ __global__ void __launch_bounds__(256, 4) k_particles(const StepConsts K, const 
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     atomicAdd(pl + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
-                    atomicAdd(rt + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
                     if (alive) atomicAdd(pl + 5 * (size_t)c + k, (unsigned long long)f[k]);
-                    if (kept) atomicAdd(rt + 5 * (size_t)c + k, (unsigned long long)f[k]);
+                    if (alive && collide) atomicAdd(cl + 5 * (size_t)c + k, (unsigned long long)f[k]);
                 }
             } else if (collide) {
                 long long o[5];
                 fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) atomicAdd(rt + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
+                for (int k = 0; k < 5; ++k) atomicAdd(cl + 5 * (size_t)c0 + k, (unsigned long long)o[k]);
             }
         }
         // survivors
@@ -921,6 +929,8 @@ __global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long 
             r2[q] = vol * (r * r);
             W[q] = Wn[q];
         }
+        // retained tally of this step (the next step's W^p): W^{p,+} minus the collided particles that stay
+        for (int k = 0; k < 5; ++k) d.wrt[5 * c + k] = d.wpl[5 * c + k] - d.wcol[5 * c + k];
         const double chi = (((double)d.wpl[5 * c] * sc[0]) / vol) / W[0];
         d.chi_ema[c] = *dstep == 0 ? chi : d.chi_ema[c] + (2.0 / 1001.0) * (chi - d.chi_ema[c]);
     } else if (t < K.C + K.nwall) {
@@ -1295,7 +1305,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         }
         // state and per-step arrays
         CK(dalloc(ctx, &d.W, 4 * C)); CK(dalloc(ctx, &d.wrt, 5 * C)); CK(dalloc(ctx, &d.wprev, 5 * C));
-        CK(dalloc(ctx, &d.wm, 5 * C)); CK(dalloc(ctx, &d.wpl, 5 * C)); CK(dalloc(ctx, &d.cross, 2 * F));
+        CK(dalloc(ctx, &d.wm, 5 * C)); CK(dalloc(ctx, &d.wpl, 5 * C)); CK(dalloc(ctx, &d.wcol, 5 * C)); CK(dalloc(ctx, &d.cross, 2 * F));
         CK(dalloc(ctx, &d.wallt, 3 * std::max(nwall, 1)));
         CK(dalloc(ctx, &d.tau, C)); CK(dalloc(ctx, &d.xr, C)); CK(dalloc(ctx, &d.emx, C)); CK(dalloc(ctx, &d.Wh, 4 * C));
         CK(dalloc(ctx, &d.co, 7 * C)); CK(dalloc(ctx, &d.mnew, C)); CK(dalloc(ctx, &d.samp, 3 * C));

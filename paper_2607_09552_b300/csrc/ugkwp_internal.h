@@ -57,6 +57,7 @@ struct Dev {
     // state
     double* W;                         // [4C]
     long long *wrt, *wprev, *wm, *wpl; // [5C]
+    long long* wcol;                   // [5C] this step's collided particles that stay (retained = W^{p,+} - wcol)
     unsigned int* cross;               // [2F]
     long long* wallt;                  // [3 nwall]
     // per-step cell data

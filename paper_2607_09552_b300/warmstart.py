@@ -15,7 +15,6 @@ order (seeded, on the host) and moves the index arrays to the device. One networ
 from __future__ import annotations
 
 import math
-import time
 
 import numpy as np
 
@@ -35,32 +34,6 @@ FAMILY_MAPS = {
 
 def family(case) -> str:
     return "plate" if case.mesh.kind == wl.MESH_PLATE else "cylinder"
-
-
-def run_to_residual(solver, tol: float = 1e-6, max_steps: int = 200000, chunk: int = 200, ref=None):
-    """Step until every conservative component of the residual is below tol; the residual is the raw one
-    divided by `ref` (4 values; the freestream start's first-step residual, so that runs from different
-    starting fields share one yardstick) or, without ref, the library's first-step normalised residual.
-    Returns (steps, residual, seconds)."""
-    t0 = time.perf_counter()
-    steps, res = 0, math.inf
-    while steps < max_steps:
-        solver.step(chunk)
-        steps += chunk
-        r = solver.residual()
-        res = float(np.max(r[4:] / ref)) if ref is not None else float(np.max(r[:4]))
-        if res < tol:
-            break
-    return steps, res, time.perf_counter() - t0
-
-
-def first_residual(case, **solver_kw):
-    """Raw first-step residual of the freestream start (4 values)."""
-    s = ugkwp.Solver(case, **solver_kw)
-    s.step(1)
-    r = s.residual()[4:].copy()
-    s.close()
-    return r
 
 
 def averaged_field(solver, n_steps: int, every: int = 1):
