@@ -186,6 +186,8 @@ def run_ours(args):
             "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": gpu_launches_per_step(case) * args.steps,
             "wall_s_timed": t_wall,
+            "last_step": {"particles": int(s1[1]), "new": int(s1[2]), "collided_removed": int(s1[3]),
+                          "left_domain": int(s1[4]), "face_crossings": int(s1[5]), "wall_hits": int(s1[6])},
         }
         print(json.dumps(line))
     solver.close()
@@ -416,6 +418,62 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+def _eval_wave(e, c, ref, fam, nets, args, st):
+    """Particle-free FP64 solve of one held-out case from the freestream and from the network."""
+    import torch
+    from paper_2607_09552_b300 import steady, ugkwp
+    from paper_2607_09552_b300 import warmstart as ws
+    s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st, use_graph=True)
+    rc = steady.run_to_residual(s, 1e-6, args.eval_wave_max, 500, ref)
+    W_cold = s.field()[0]
+    s.close()
+    t0 = time.perf_counter()
+    s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st, use_graph=True)
+    s.warm_start(nets[fam], ws.FAMILY_MAPS[fam])
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    rw = steady.run_to_residual(s, 1e-6, args.eval_wave_max, 500, ref)
+    W_warm = s.field()[0]
+    s.close()
+    e["wave_only_fp64"] = {"cold_steps": rc["steps"] if rc["converged"] else None, "cold_s": rc["seconds"],
+                           "warm_steps": rw["steps"] if rw["converged"] else None,
+                           "warm_s": rw["seconds"] + t_inf, "warm_start_s": t_inf,
+                           "cold_final": rc["residual"], "warm_final": rw["residual"],
+                           "cold_marks": {f"{k:.0e}": v for k, v in rc["marks"].items()},
+                           "warm_marks": {f"{k:.0e}": v for k, v in rw["marks"].items()},
+                           "state_rel_diff": float(np.max(np.abs(W_warm - W_cold)) / np.max(np.abs(W_cold)))}
+
+
+def _eval_stoch(c, warm, net, fam, geom, n, navg, st):
+    """Stochastic LTS run of one held-out case (production precision) from the freestream or the network:
+    steps and seconds to steady (drag and heat-load EMA), final-window loads, surfaces averaged over the
+    last navg steps."""
+    from paper_2607_09552_b300 import steady, ugkwp
+    from paper_2607_09552_b300 import warmstart as ws
+    s = ugkwp.Solver(c, precision=0, stream=st, use_graph=True)
+    if warm:
+        s.warm_start(net, ws.FAMILY_MAPS[fam])
+    hcd, hch, ht = [], [], []
+    t0 = time.perf_counter()
+    for k in range(n):
+        s.step(1)
+        if k == n - navg:
+            s.reset_surface()
+        p, tau, q = s.surface(averaged=False)
+        cd, ch = steady.loads(c, p, tau, q, geom)
+        hcd.append(cd)
+        hch.append(ch)
+        ht.append(time.perf_counter() - t0)
+    kd, _ = steady.steady_step(hcd)
+    kh, _ = steady.steady_step(hch)
+    k_st = max(kd, kh)
+    r = {"steps_to_steady": k_st if k_st < n - navg else None,
+         "wall_s_to_steady": ht[k_st - 1] if 0 < k_st < n - navg else None,
+         "Cd": float(np.mean(hcd[-navg:])), "CH": float(np.mean(hch[-navg:])), "surface": s.surface(averaged=True)}
+    s.close()
+    return r
+
+
 def run_warmstart(args):
     """Learned warm start (all on the GPU): converged particle-free fields of seeded sweeps of 16 uneven
     cases (cylinders and plates, batched graph launches) train one network per geometry family; then held-out
@@ -437,19 +495,33 @@ def run_warmstart(args):
         b = ugkwp.Batch(solvers, stream=st)
         t0, steps = time.perf_counter(), 0
         res = [1.0] * len(solvers)
+        failed = {}
         while steps < args.train_max_steps:
             b.step(1000)
             steps += 1000
-            res = [float(np.max(s.residual()[:4])) for s in solvers]
+            for i, sv in enumerate(solvers):
+                if i in failed:
+                    continue
+                try:
+                    res[i] = float(np.max(sv.residual()[:4]))
+                except ugkwp.UgkwpError as e:
+                    failed[i] = str(e)
+                    res[i] = 0.0
             if max(res) < args.train_tol:
                 break
-        for c, sv in zip(cases, solvers):
-            sets[ws.family(c)].add(sv, ws.FAMILY_MAPS[ws.family(c)])
+        used = 0
+        for i, (c, sv) in enumerate(zip(cases, solvers)):
+            # a field still far from steady (or one that failed) would teach the network a transient
+            if i not in failed and res[i] < args.train_accept:
+                sets[ws.family(c)].add(sv, ws.FAMILY_MAPS[ws.family(c)])
+                used += 1
         b.close()
         for sv in solvers:
             sv.close()
         out["train"][f"sweep{seed}"] = {"steps": steps, "seconds": time.perf_counter() - t0,
-                                        "max_residual": max(res), "median_residual": float(np.median(res))}
+                                        "max_residual": max(res), "median_residual": float(np.median(res)),
+                                        "failed": {cases[i].name: m for i, m in failed.items()}, "fields_used": used,
+                                        "residuals": {c.name: r for c, r in zip(cases, res)}}
         print(json.dumps({"phase": f"training fields, sweep {seed}", **out["train"][f"sweep{seed}"]}), flush=True)
     nets = {}
     for fam, tset in sets.items():
@@ -478,26 +550,15 @@ def run_warmstart(args):
     for c, ref in zip(cases, refs):
         fam = ws.family(c)
         e = {"case": c.name, "family": fam, "Kn": c.Kn, "Ma": c.Ma, "Tw": c.Tw}
-        s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st, use_graph=True)
-        rc = steady.run_to_residual(s, 1e-6, args.eval_wave_max, 500, ref)
-        W_cold = s.field()[0]
-        s.close()
-        t0 = time.perf_counter()
-        s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st, use_graph=True)
-        s.warm_start(nets[fam], ws.FAMILY_MAPS[fam])
-        torch.cuda.synchronize()
-        t_inf = time.perf_counter() - t0
-        rw = steady.run_to_residual(s, 1e-6, args.eval_wave_max, 500, ref)
-        W_warm = s.field()[0]
-        s.close()
-        e["wave_only_fp64"] = {"cold_steps": rc["steps"] if rc["converged"] else None, "cold_s": rc["seconds"],
-                               "warm_steps": rw["steps"] if rw["converged"] else None,
-                               "warm_s": rw["seconds"] + t_inf, "warm_start_s": t_inf,
-                               "cold_final": rc["residual"], "warm_final": rw["residual"],
-                               "state_rel_diff": float(np.max(np.abs(W_warm - W_cold)) / np.max(np.abs(W_cold)))}
-        cold_total += rc["seconds"]
-        warm_total += rw["seconds"] + t_inf
         out["eval"].append(e)
+        try:
+            _eval_wave(e, c, ref, fam, nets, args, st)
+        except ugkwp.UgkwpError as err:
+            e["wave_only_fp64"] = {"error": str(err)}
+            print(json.dumps({"phase": "eval wave-only", **e}), flush=True)
+            continue
+        cold_total += e["wave_only_fp64"]["cold_s"]
+        warm_total += e["wave_only_fp64"]["warm_s"]
         print(json.dumps({"phase": "eval wave-only", **e}), flush=True)
     t0 = time.perf_counter()
     solvers = []
@@ -511,8 +572,12 @@ def run_warmstart(args):
         b.step(500)
         steps += 500
         for i, (s, ref) in enumerate(zip(solvers, refs)):
-            if done[i] is None and float(np.max(s.residual()[4:] / ref)) < 1e-6:
-                done[i] = steps
+            if done[i] is None:
+                try:
+                    if float(np.max(s.residual()[4:] / ref)) < 1e-6:
+                        done[i] = steps
+                except ugkwp.UgkwpError as err:
+                    done[i] = f"error: {err}"
     batched_s = time.perf_counter() - t0
     b.close()
     for s in solvers:
@@ -528,33 +593,18 @@ def run_warmstart(args):
         geom = steady.wall_geometry(c)
         res = {}
         for start in ("cold", "warm"):
-            s = ugkwp.Solver(c, precision=0, stream=st, use_graph=True)
-            if start == "warm":
-                s.warm_start(nets[fam], ws.FAMILY_MAPS[fam])
-            hcd, hch, ht = [], [], []
-            t0 = time.perf_counter()
-            for k in range(n):
-                s.step(1)
-                if k == n - navg:
-                    s.reset_surface()
-                p, tau, q = s.surface(averaged=False)
-                cd, ch = steady.loads(c, p, tau, q, geom)
-                hcd.append(cd)
-                hch.append(ch)
-                ht.append(time.perf_counter() - t0)
-            kd, _ = steady.steady_step(hcd)
-            kh, _ = steady.steady_step(hch)
-            k_st = max(kd, kh)
-            res[start] = {"steps_to_steady": k_st if k_st < n - navg else None,
-                          "wall_s_to_steady": ht[k_st - 1] if 0 < k_st < n - navg else None,
-                          "Cd": float(np.mean(hcd[-navg:])), "CH": float(np.mean(hch[-navg:])),
-                          "surface": s.surface(averaged=True)}
-            s.close()
-        pc, tc, qc = res["cold"].pop("surface")
-        pw, tw_, qw = res["warm"].pop("surface")
-        res["surface_rel_err"] = {"p": float(np.linalg.norm(pw - pc) / np.linalg.norm(pc)),
-                                  "tau_w": float(np.linalg.norm(tw_ - tc) / (np.sqrt(len(tc)) * np.max(np.abs(tc)))),
-                                  "q": float(np.linalg.norm(qw - qc) / np.linalg.norm(qc))}
+            try:
+                res[start] = _eval_stoch(c, start == "warm", nets[fam], fam, geom, n, navg, st)
+            except ugkwp.UgkwpError as err:
+                res[start] = {"error": str(err)}
+        if "surface" in res["cold"] and "surface" in res["warm"]:
+            pc, tc, qc = res["cold"].pop("surface")
+            pw, tw_, qw = res["warm"].pop("surface")
+            res["surface_rel_err"] = {"p": float(np.linalg.norm(pw - pc) / np.linalg.norm(pc)),
+                                      "tau_w": float(np.linalg.norm(tw_ - tc) / (np.sqrt(len(tc)) * np.max(np.abs(tc)))),
+                                      "q": float(np.linalg.norm(qw - qc) / np.linalg.norm(qc))}
+        for r_ in res.values():
+            r_.pop("surface", None)
         e["stochastic"] = res
         print(json.dumps({"phase": "eval stochastic", "case": c.name, **res}), flush=True)
     print(json.dumps(out))
@@ -565,7 +615,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--burn", type=int, default=300)
+    ap.add_argument("--burn", type=int, default=3000)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -580,7 +630,8 @@ def main():
     ap.add_argument("--train-sweeps", type=int, default=4)
     ap.add_argument("--train-tol", type=float, default=1e-5)
     ap.add_argument("--train-max-steps", type=int, default=60000)
-    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--train-steps", type=int, default=60000)
+    ap.add_argument("--train-accept", type=float, default=1e-2)
     ap.add_argument("--eval-cyl", type=int, default=4)
     ap.add_argument("--eval-plate", type=int, default=4)
     ap.add_argument("--eval-wave-max", type=int, default=200000)

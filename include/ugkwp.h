@@ -123,13 +123,14 @@ ugkwp_status ugkwp_get_field(ugkwp_ctx* ctx, double* W, double* Wp);
  * Synchronises. */
 ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* ctx, double* W, double* Wp);
 
-/* out[11]: steps taken, particles, new in the last step, removed (collided), left the domain, face
+/* out[12]: steps taken, particles, new in the last step, removed (collided), left the domain, face
  * crossings, wall hits, largest crossings + hits of one particle in the last step; then, cumulative since
  * creation, particle-steps processed (retained + new particles of every step) and new particles; then the
  * cells reset to the vacuum floor in the last step: a cell state outside the realizable set (density
  * above 1e-12, 0.01 min(1, T_w, T_fixed) <= T <= T_cap = 10 max(1 + Ma^2/3, T_w, T_fixed),
  * |U| <= U_inf + 10 sqrt(R T_cap)) restarts from rho = 1e-12 at rest at T_inf; a hydrodynamic part W^h
- * outside that set is not sampled and has no free-transport wave flux. */
+ * outside that set is not sampled and has no free-transport wave flux; last, the new particles of the
+ * last step whose Shakhov acceptance-rejection (Pr != 1) kept a Maxwellian proposal after 64 rejections. */
 ugkwp_status ugkwp_stats(ugkwp_ctx* ctx, int64_t* out);
 int64_t ugkwp_num_particles(ugkwp_ctx* ctx);
 
@@ -172,6 +173,21 @@ void ugkwp_batch_destroy(ugkwp_batch* batch);
  * (the particle draws are keyed by particle id and step). Both synchronise. */
 ugkwp_status ugkwp_save(ugkwp_ctx* ctx, const char* path);
 ugkwp_status ugkwp_load(ugkwp_ctx* ctx, const char* path);
+
+/* Launch parameters of the particle kernels: particles per chunk a warp claims in the transport kernel (a
+ * multiple of 32 in [32, 8192]), its blocks per SM (1..16) and the steps between counting sorts of the
+ * particles by cell (1..64); 0 keeps a value. They change only the speed: chunks and sorts reorder
+ * particles, and every result is an integer sum or a per-particle / per-face quantity. Takes effect at the
+ * next step (a captured step graph is re-captured); a batch keeps the values its contexts had at
+ * ugkwp_batch_create. ugkwp_get_launch fills out[3] in the same order. */
+ugkwp_status ugkwp_set_launch(ugkwp_ctx* ctx, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every);
+ugkwp_status ugkwp_get_launch(ugkwp_ctx* ctx, int32_t* out);
+/* Autotuner: times each combination of chunk {128, 256, 512}, blocks per SM {2, 4, 6} and sort interval
+ * {8, 16} over whole sort periods of at least `steps` steps (real steps of the run: the state advances)
+ * with CUDA events on the context's stream, keeps the fastest and returns it in best[3] (nullable, order of
+ * ugkwp_set_launch) and its milliseconds per step in best_ms (nullable). Synchronises. A particle-free
+ * context keeps its values. */
+ugkwp_status ugkwp_autotune(ugkwp_ctx* ctx, int32_t steps, int32_t* best, double* best_ms);
 
 /* Per-stage device timing with CUDA events recorded on the context's stream around each stage of every
  * step taken while enabled (graph replay is bypassed meanwhile). ugkwp_profile synchronises, returns the

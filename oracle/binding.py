@@ -167,8 +167,9 @@ class Oracle:
         return p, t, q
 
     def stats(self):
-        """[steps, particles, new, removed, left, crossings, wall hits, max iterations, floored cells]"""
-        out = np.zeros(9, dtype=np.int64)
+        """[steps, particles, new, removed, left, crossings, wall hits, max iterations, floored cells,
+        A-R fallbacks]"""
+        out = np.zeros(10, dtype=np.int64)
         lib().oracle_stats(self.ctx, _p(out, C.c_int64))
         return out
 
@@ -217,6 +218,16 @@ class Oracle:
         out = np.zeros(4 * self.F)
         lib().oracle_get_flux(self.ctx, dptr(out))
         return out.reshape(self.F, 4)
+
+
+def ar_sample(precision, seed, case_id, step, pid0, n, ax, ay, M):
+    """n Shakhov acceptance-rejection normal triples (n x 3) and the fallback count (oracle_ar_sample)."""
+    L = lib()
+    L.oracle_ar_sample.restype = C.c_int64
+    z = np.zeros(3 * n)
+    fb = L.oracle_ar_sample(C.c_int32(precision), C.c_uint64(seed), C.c_uint32(case_id), C.c_int64(step),
+                            C.c_uint64(pid0), C.c_int32(n), C.c_double(ax), C.c_double(ay), C.c_double(M), dptr(z))
+    return z.reshape(n, 3), int(fb)
 
 
 def balance_condition(dtL, dtR):

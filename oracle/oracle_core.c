@@ -541,6 +541,8 @@ static void fixed_exponents(or_ctx* cx, double T_fix)
     cx->fx[0] = 61 - ceil_log2(b0);
     cx->fx[1] = 61 - ceil_log2(b0 * speed);
     cx->fx[2] = 61 - ceil_log2(b0 * (0.5 * (speed * speed)));
+    cx->fx[3] = 61 - ceil_log2(b0 * (speed * speed));
+    cx->fx[4] = 61 - ceil_log2(b0 * (speed * speed * speed));
 }
 
 int oracle_fixed_exponents(oracle_ctx* cx, int32_t* out)
@@ -585,6 +587,7 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     cx->tau = zalloc(C, 8); cx->xr_t = zalloc(C, 8); cx->emx = zalloc(C, 8);
     cx->Wp = zalloc(4 * C, 8); cx->Wh = zalloc(4 * C, 8); cx->mnew = zalloc(C, 8); cx->co = zalloc(7 * C, 8);
     cx->samp = zalloc(3 * C, 8);
+    cx->whq = zalloc(9 * C, 8); cx->hq = zalloc(3 * C, 8);
     cx->nhp = zalloc(C, 4); cx->hphys = zalloc(C, 4); cx->nhp_off = zalloc(C + 1, 8);
     cx->wm = zalloc(5 * C, 8); cx->wpl = zalloc(5 * C, 8); cx->wrt = zalloc(5 * C, 8);
     cx->cross = zalloc(2 * F, 8); cx->wallt = zalloc(3 * cx->nwall, 8); cx->frec_d = zalloc(4 * F, 8);
@@ -608,7 +611,7 @@ void oracle_destroy(oracle_ctx* cx)
                     cx->wall_face, cx->dt, cx->ratio, cx->W, cx->wret_prev, cx->tau, cx->xr_t, cx->emx, cx->Wp,
                     cx->Wh, cx->mnew, cx->co, cx->samp, cx->nhp, cx->hphys, cx->nhp_off, cx->wm, cx->wpl,
                     cx->wrt, cx->cross, cx->wallt, cx->frec_d, cx->flux, cx->chi_ema, cx->surf_sum,
-                    cx->surf_last, cx->p};
+                    cx->surf_last, cx->p, cx->whq, cx->hq};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(cx);
 }
@@ -630,9 +633,45 @@ static int realizable(const or_ctx* cx, const double W[4])
 
 /* ------------------------------------------------------------------ a1: decomposition (Sec. IV B) */
 
+/* Shakhov acceptance-rejection weights of cell c (Eqs. 4-5; reading): the heat flux Q_i of the particles
+ * retained in the cell at the start of the step, about the cell velocity U_i, from their raw moments; the
+ * sampled wave part takes its mass share rho^h / rho_i of the correction: accept a proposal c = sqrt(RT^h) z
+ * from the Maxwellian of W^h with probability (1 + psi) / M, psi = (a . z) (|z|^2 - 5),
+ * a = (1 - Pr) Q_i / (5 rho_i (RT^h)^(3/2)), M = 1 + 6 * 31 |a| (|z| <= 6 enforced by rejection). W has no
+ * z-momentum, so Q_z = 0; in 1-D also Q_y = 0. */
+static void shakhov_weights(or_ctx* cx, int c)
+{
+    const int64_t* h = cx->whq + 9 * c;
+    const double s0 = ldexp(1.0, -cx->fx[0]), s1 = ldexp(1.0, -cx->fx[1]), s2 = ldexp(1.0, -cx->fx[3]);
+    const double s3 = ldexp(1.0, -cx->fx[4]);
+    const double Sm = (double)h[0] * s0, Su = (double)h[1] * s1, Sv = (double)h[2] * s1;
+    const double Suu = (double)h[3] * s2, Suv = (double)h[4] * s2, Svv = (double)h[5] * s2, Sq = (double)h[6] * s2;
+    const double Suq = (double)h[7] * s3, Svq = (double)h[8] * s3;
+    const double* W = cx->W + 4 * c;
+    const double U = W[1] / W[0], V = cx->dim == 1 ? 0.0 : W[2] / W[0];
+    const double UU = U * U + V * V;
+    const double Ud = U * Su + V * Sv;
+    /* sum m c_a |c|^2 with c = u - U_i, expanded in the raw moments */
+    const double cx3 = ((((Suq - 2.0 * (U * Suu + V * Suv)) + UU * Su) - U * Sq) + 2.0 * U * Ud) - U * UU * Sm;
+    const double cy3 = ((((Svq - 2.0 * (U * Suv + V * Svv)) + UU * Sv) - V * Sq) + 2.0 * V * Ud) - V * UU * Sm;
+    const double Qx = cx3 / (2.0 * cx->vol[c]);
+    const double Qy = cx->dim == 1 ? 0.0 : cy3 / (2.0 * cx->vol[c]);
+    const double RTh = cx->samp[3 * c + 2];
+    const double den = 5.0 * W[0] * (RTh * sqrt(RTh));
+    const double ax = ((1.0 - cx->Pr) * Qx) / den, ay = ((1.0 - cx->Pr) * Qy) / den;
+    cx->hq[3 * c] = ax;
+    cx->hq[3 * c + 1] = ay;
+    cx->hq[3 * c + 2] = 1.0 + 186.0 * sqrt(ax * ax + ay * ay);
+}
+
 static void decompose(or_ctx* cx)
 {
     const double s0 = ldexp(1.0, -cx->fx[0]), s1 = ldexp(1.0, -cx->fx[1]), s4 = ldexp(1.0, -cx->fx[2]);
+    const int shakhov = cx->Pr != 1.0 && !cx->wave_only;
+    if (shakhov) {
+        memset(cx->whq, 0, 9 * (size_t)cx->C * 8);
+        if (cx->prec == 0) or_heat_tally_f32(cx); else or_heat_tally_f64(cx);
+    }
     for (int c = 0; c < cx->C; ++c) {
         const double* W = cx->W + 4 * c;
         const int64_t* r = cx->wret_prev + 5 * c;
@@ -671,6 +710,7 @@ static void decompose(or_ctx* cx)
                 cx->samp[3 * c] = Uh;
                 cx->samp[3 * c + 1] = Vh;
                 cx->samp[3 * c + 2] = RTh;
+                if (shakhov) shakhov_weights(cx, c);
             }
         }
     }
@@ -718,6 +758,9 @@ static void wave_fluxes(or_ctx* cx)
             face_flux(WL, WR, WhL, WR, cx->hphys[L], 1, cL, cR, frL, cR[3], cx->fdL[f], cx->fdL[f], cx->Pr, F,
                       NULL, NULL, NULL, NULL);
         }
+        /* non-finite flux (reading): extreme near-vacuum neighbours can make the interface density underflow
+         * against its neighbours' and the slopes overflow; such a face carries no wave flux */
+        if (!isfinite(F[0]) || !isfinite(F[1]) || !isfinite(F[2]) || !isfinite(F[3])) F[0] = F[1] = F[2] = F[3] = 0.0;
         /* back to the global frame: momentum = F_n n + F_t t, t = (-n_y, n_x) */
         cx->flux[4 * f + 0] = F[0];
         cx->flux[4 * f + 1] = F[1] * nx - F[2] * ny;
@@ -807,7 +850,7 @@ static int one_step(or_ctx* cx)
     memset(cx->wrt, 0, 5 * (size_t)C * 8);
     memset(cx->cross, 0, 2 * (size_t)cx->F * 8);
     memset(cx->wallt, 0, 3 * (size_t)cx->nwall * 8);
-    for (int k = 2; k < 9; ++k) cx->stats[k] = 0;
+    for (int k = 2; k < 10; ++k) cx->stats[k] = 0;
     /* step 1: decomposition and sampling; step 2: free transport and tallies (Sec. III C, Sec. IV B) */
     decompose(cx);
     if (cx->err) return cx->err;
@@ -883,6 +926,25 @@ int oracle_surface(oracle_ctx* cx, double* p, double* tau, double* q, int32_t n_
         q[i] = src[3 * i + 2] / d;
     }
     return OR_OK;
+}
+
+int64_t oracle_ar_sample(int32_t precision, uint64_t seed, uint32_t case_id, int64_t step, uint64_t pid0, int32_t n,
+                         double ax, double ay, double M, double* z)
+{
+    or_ctx cx;
+    memset(&cx, 0, sizeof cx);
+    cx.seed = seed; cx.case_id = case_id; cx.step = step;
+    int64_t fb = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (precision == 0) {
+            float zf[3];
+            fb += or_new_velocity_f32(&cx, pid0 + (uint64_t)k, 1, (float)ax, (float)ay, (float)M, zf);
+            for (int q = 0; q < 3; ++q) z[3 * (int64_t)k + q] = (double)zf[q];
+        } else {
+            fb += or_new_velocity_f64(&cx, pid0 + (uint64_t)k, 1, ax, ay, M, z + 3 * (int64_t)k);
+        }
+    }
+    return fb;
 }
 
 int oracle_stats(oracle_ctx* cx, int64_t* out)

@@ -33,7 +33,8 @@ struct oracle_ctx {
     int64_t step;
     double Kn, Ma, Tw, cfl, omega, Pr, mu_inf, U_inf;
     double W_inf[4], W_fix[4];
-    int fx[3];                                   /* fixed-point exponents: mass, momentum, energy */
+    int fx[5];                                   /* fixed-point exponents: mass, momentum, energy; second and
+                                                  * third velocity moments (Shakhov heat flux, Pr != 1) */
     double T_cap, U_cap, T_min;                  /* realizability bounds of a cell state */
     /* cells */
     double *vol, *inv_vol, *xc, *yc;
@@ -56,6 +57,9 @@ struct oracle_ctx {
     /* per-step cell data */
     double *tau, *xr_t, *emx, *Wp, *Wh, *mnew, *co;   /* co: [7C] normalised coefficients */
     double* samp;                                /* [3C] U^h, V^h, R T^h for sampling */
+    int64_t* whq;                                /* [9C] retained particles: m (1, u, v, uu, uv, vv, q, uq, vq),
+                                                  * q = |u|^2, fixed point (Pr != 1) */
+    double* hq;                                  /* [3C] A-R weights a_x, a_y and bound M (Pr != 1) */
     double m2RTw, sig_w;                         /* -2 R T_w and sqrt(R T_w) */
     int *nhp, *hphys;
     int64_t *nhp_off;
@@ -72,7 +76,8 @@ struct oracle_ctx {
     double* chi_ema;
     double *surf_sum, *surf_last;
     int64_t nsurf;
-    int64_t stats[9];                            /* [8]: cells set to the vacuum floor in the last step */
+    int64_t stats[10];                           /* [8]: cells set to the vacuum floor in the last step,
+                                                  * [9]: A-R samplings that fell back to the Maxwellian */
     int err;
     char msg[256];
 };
@@ -95,6 +100,10 @@ void   or_sincos2pid(double u, double* s, double* c);
 /* particles (float and double instantiations) */
 void or_particles_step_f32(or_ctx* cx);
 void or_particles_step_f64(or_ctx* cx);
+void or_heat_tally_f32(or_ctx* cx);
+void or_heat_tally_f64(or_ctx* cx);
+int or_new_velocity_f32(const or_ctx* cx, uint64_t pid, int shakhov, float ax, float ay, float M, float z[3]);
+int or_new_velocity_f64(const or_ctx* cx, uint64_t pid, int shakhov, double ax, double ay, double M, double z[3]);
 void or_set_error(or_ctx* cx, int code, const char* msg);
 
 /* Philox draw layout: the first counter word of each draw group */
@@ -102,5 +111,7 @@ void or_set_error(or_ctx* cx, int code, const char* msg);
 #define OR_DRAW_VEL 2u
 #define OR_DRAW_TF 5u
 #define OR_DRAW_WALL(h) (8u + 2u * (uint32_t)(h))
+#define OR_DRAW_AR(a) (1024u + 4u * (uint32_t)(a))   /* Shakhov A-R attempt a: proposal +0, +1; acceptance +2 */
+#define OR_AR_ATTEMPTS 64
 
 #endif

@@ -31,10 +31,12 @@ constexpr int kScanBlock = 1024;
 #ifndef UGKWP_CHUNK
 #define UGKWP_CHUNK 256
 #endif
+#ifndef UGKWP_SORT_EVERY
+#define UGKWP_SORT_EVERY 8   // steps between counting sorts of the particles by cell
+#endif
 #ifndef UGKWP_PARTICLES_MINB
 #define UGKWP_PARTICLES_MINB 4
 #endif
-constexpr int kChunk = UGKWP_CHUNK;   // particles per dynamically claimed chunk of k_particles
 constexpr int kMaxCells = 1 << 20;
 
 // ------------------------------------------------------------------------------------------ scan
@@ -288,6 +290,8 @@ __global__ void k_setup_tables(Dev d, int C, const int* cface, const int* csgn, 
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
+    d.rcp[2 * c] = 1.0 / d.vol[c];
+    d.rcp[2 * c + 1] = 1.0 / d.dt[c];
     CellFaces<float> a;
     CellFaces<double> b;
     for (int k = 0; k < 4; ++k) {
@@ -301,7 +305,7 @@ __global__ void k_setup_tables(Dev d, int C, const int* cface, const int* csgn, 
     }
     d.cf32[c] = a;
     d.cf64[c] = b;
-    // faces next to a wall cell are evaluated in FP64 in production mode
+    // faces of a wall cell apply their time integrals in FP64 in production mode
     for (int k = 0; k < d.nfc[c]; ++k)
         if (cbc[4 * c + k] == UGKWP_BC_WALL)
             for (int q = 0; q < d.nfc[c]; ++q) d.face_f64[cface[4 * c + q]] = 1;
@@ -389,6 +393,35 @@ __device__ void lts_coeffs(double dt, double tau, double e, double* out)
     out[6] = -dt * x * kappa;
 }
 
+// Shakhov acceptance-rejection weights of cell c (Eqs. 4-5): the heat flux Q_i of the particles retained in
+// the cell at the start of the step, about the cell velocity U_i, from their raw moments (whq); the sampled
+// wave part takes its mass share rho^h / rho_i of the correction: proposals c = sqrt(RT^h) z from the
+// Maxwellian of W^h are accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5),
+// a = (1 - Pr) Q_i / (5 rho_i (RT^h)^(3/2)), M = 1 + 6 * 31 |a| (|z| <= 6 enforced by rejection). W has no
+// z-momentum, so Q_z = 0; in 1-D also Q_y = 0. FP64, in the order of the CPU definition.
+__device__ void shakhov_weights(const StepConsts& K, const Dev& d, int c, double RTh)
+{
+    const long long* h = d.whq + 9 * c;
+    const double s0 = ldexp(1.0, -K.fx0), s1 = ldexp(1.0, -K.fx1), s2 = ldexp(1.0, -K.fx_s2);
+    const double s3 = ldexp(1.0, -K.fx_s3);
+    const double Sm = (double)h[0] * s0, Su = (double)h[1] * s1, Sv = (double)h[2] * s1;
+    const double Suu = (double)h[3] * s2, Suv = (double)h[4] * s2, Svv = (double)h[5] * s2, Sq = (double)h[6] * s2;
+    const double Suq = (double)h[7] * s3, Svq = (double)h[8] * s3;
+    const double* W = d.W + 4 * c;
+    const double U = W[1] / W[0], V = K.dim == 1 ? 0.0 : W[2] / W[0];
+    const double UU = U * U + V * V;
+    const double Ud = U * Su + V * Sv;
+    const double cx3 = ((((Suq - 2.0 * (U * Suu + V * Suv)) + UU * Su) - U * Sq) + 2.0 * U * Ud) - U * UU * Sm;
+    const double cy3 = ((((Svq - 2.0 * (U * Suv + V * Svv)) + UU * Sv) - V * Sq) + 2.0 * V * Ud) - V * UU * Sm;
+    const double Qx = cx3 / (2.0 * d.vol[c]);
+    const double Qy = K.dim == 1 ? 0.0 : cy3 / (2.0 * d.vol[c]);
+    const double den = 5.0 * W[0] * (RTh * sqrt(RTh));
+    const double ax = ((1.0 - K.Pr) * Qx) / den, ay = ((1.0 - K.Pr) * Qy) / den;
+    const double M = 1.0 + 186.0 * sqrt(ax * ax + ay * ay);
+    d.hq[3 * c] = ax; d.hq[3 * c + 1] = ay; d.hq[3 * c + 2] = M;
+    d.hq32[3 * c] = (float)ax; d.hq32[3 * c + 1] = (float)ay; d.hq32[3 * c + 2] = (float)M;
+}
+
 __global__ void k_decompose(const StepConsts K, Dev d)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -438,6 +471,7 @@ __global__ void k_decompose(const StepConsts K, Dev d)
             }
         }
     }
+    if (K.shakhov && n > 0) shakhov_weights(K, d, c, RTh);
     d.nhp[c] = n;
     d.mnew[c] = m;
     d.samp[3 * c] = Uh; d.samp[3 * c + 1] = Vh; d.samp[3 * c + 2] = RTh;
@@ -455,9 +489,12 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
     for (int q = t; q < 2 * K.F; q += nt) d.cross[q] = 0u;
     for (int q = t; q < 3 * K.nwall; q += nt) d.wallt[q] = 0;
+    if (K.shakhov)
+        for (int q = t; q < 9 * K.C; q += nt) d.whq[q] = 0;
     if (t == 0) {
         for (int k = 2; k < 8; ++k) d.stats[k] = 0;
         d.stats[11] = 0;
+        d.stats[12] = 0;
         d.counts[2] = 0;
         d.counts[5] = 0;
         *d.nretry = 0;
@@ -469,15 +506,17 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
 // per-cell particle-precision views
 template <typename T> struct PCell;
 template <> struct PCell<float> {
-    const float *tau, *dt, *mnew, *samp;
+    const float *tau, *dt, *mnew, *samp, *hq;
     __device__ float tau_(int c) const { return tau[c]; }
+    __device__ float q_(int c, int k) const { return hq[3 * c + k]; }
     __device__ float dt_(int c) const { return dt[c]; }
     __device__ float m_(int c) const { return mnew[c]; }
     __device__ float s_(int c, int k) const { return samp[3 * c + k]; }
 };
 template <> struct PCell<double> {
-    const double *tau, *dt, *mnew, *samp;
+    const double *tau, *dt, *mnew, *samp, *hq;
     __device__ double tau_(int c) const { return tau[c]; }
+    __device__ double q_(int c, int k) const { return hq[3 * c + k]; }
     __device__ double dt_(int c) const { return dt[c]; }
     __device__ double m_(int c) const { return mnew[c]; }
     __device__ double s_(int c, int k) const { return samp[3 * c + k]; }
@@ -531,6 +570,29 @@ __device__ __forceinline__ void fix5(T m, T u, T v, T w, T s0, T s1, T s4, int* 
     o[4] = fixp(m * e, s4, err);
 }
 
+// Pr != 1: raw velocity moments m (1, u, v, uu, uv, vv, q, uq, vq), q = |u|^2, of the particles retained at
+// the start of the step, per cell, as fixed-point integers (the Shakhov heat flux of the sampling)
+template <typename T>
+__global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const Dev d, ParticleSoA<T> PA,
+                                                    ParticleSoA<T> PB)
+{
+    const ParticleSoA<T> A = *d.bufsel ? PB : PA;
+    const int n = d.counts[0];
+    const T sc[9] = {T(ldexp(1.0, K.fx0)), T(ldexp(1.0, K.fx1)), T(ldexp(1.0, K.fx1)), T(ldexp(1.0, K.fx_s2)),
+                     T(ldexp(1.0, K.fx_s2)), T(ldexp(1.0, K.fx_s2)), T(ldexp(1.0, K.fx_s2)), T(ldexp(1.0, K.fx_s3)),
+                     T(ldexp(1.0, K.fx_s3))};
+    unsigned long long* h = reinterpret_cast<unsigned long long*>(d.whq);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const T m = A.m[i], u = A.u[i], v = A.v[i], w = A.w[i];
+        const T q = (u * u + v * v) + w * w;
+        const T mu = m * u, mv = m * v;
+        const T val[9] = {m, mu, mv, mu * u, mu * v, mv * v, m * q, mu * q, mv * q};
+        const size_t c = (size_t)A.cell[i];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) atomicAdd(h + 9 * c + k, (unsigned long long)fixp(val[k], sc[k], d.err));
+    }
+}
+
 // ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
 // One warp per cell. Velocities: Box-Muller normals shifted and scaled so that the cell's new particles
 // carry exactly the momentum and energy of W^hp (sums in index order, accumulated by lane 0).
@@ -554,48 +616,63 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
     }
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
     const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)c << 11);
+    // sums in a fixed order: lane j adds k = j, j + 32, ... in increasing k, then a butterfly combines the
+    // lanes (j + 16 into j, j + 8 into j, ...; every lane ends with the same value)
     T su = 0, sv = 0, sw = 0;
-    for (int k0 = 0; k0 < N; k0 += 32) {
-        const int k = k0 + lane;
+    int fallbacks = 0;
+    const T ax = K.shakhov ? pc.q_(c, 0) : T(0), ay = K.shakhov ? pc.q_(c, 1) : T(0);
+    const T M = K.shakhov ? pc.q_(c, 2) : T(1);
+    for (int k = lane; k < N; k += 32) {
+        // Pr = 1: Box-Muller of the Maxwellian of W^h. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-
+        // rejection (Sec. III B): Maxwellian proposals accepted with probability (1 + psi) / M,
+        // psi = (a . z)(|z|^2 - 5), |z| > 6 rejected; after kArAttempts rejections the last proposal stays
         T z0 = 0, z1 = 0, z2 = 0;
-        if (k < N) {
+        const int attempts = K.shakhov ? kArAttempts : 1;
+        bool accepted = !K.shakhov;
+        for (int a = 0; a < attempts; ++a) {
             T U[4];
-            Unif<T>::get(g, pbase | (uint64_t)k, DRAW_VEL, 4, U);
+            Unif<T>::get(g, pbase | (uint64_t)k, K.shakhov ? draw_ar(a) : DRAW_VEL, 4, U);
             const T r0 = fsqrt_(T(-2) * dlog(U[0]));
             T s0, c0, s1, c1;
             dsincos2pi(U[1], &s0, &c0);
             const T r1 = fsqrt_(T(-2) * dlog(U[2]));
             dsincos2pi(U[3], &s1, &c1);
             z0 = r0 * c0; z1 = r0 * s0; z2 = r1 * c1;
-            A.u[base_i + k] = z0; A.v[base_i + k] = z1; A.w[base_i + k] = z2;
+            if (!K.shakhov) break;
+            const T s2 = (z0 * z0 + z1 * z1) + z2 * z2;
+            if (s2 <= T(36)) {
+                const T psi = (z0 * ax + z1 * ay) * (s2 - T(5));
+                T Ua[1];
+                Unif<T>::get(g, pbase | (uint64_t)k, draw_ar(a) + 2u, 1, Ua);
+                if (Ua[0] * M < T(1) + psi) { accepted = true; break; }
+            }
         }
-        const int nk = min(32, N - k0);
-        for (int j = 0; j < nk; ++j) {
-            const T a = __shfl_sync(0xffffffffu, z0, j), b = __shfl_sync(0xffffffffu, z1, j),
-                    e = __shfl_sync(0xffffffffu, z2, j);
-            if (lane == 0) { su += a; sv += b; sw += e; }
-        }
+        if (!accepted) fallbacks++;
+        A.u[base_i + k] = z0; A.v[base_i + k] = z1; A.w[base_i + k] = z2;
+        su += z0; sv += z1; sw += z2;
+    }
+    if (K.shakhov) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+        if (lane == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        su = su + __shfl_xor_sync(0xffffffffu, su, o);
+        sv = sv + __shfl_xor_sync(0xffffffffu, sv, o);
+        sw = sw + __shfl_xor_sync(0xffffffffu, sw, o);
     }
     const T inv = T(1) / T(N);
-    T mu = su * inv, mv = sv * inv, mw = sw * inv;
-    mu = __shfl_sync(0xffffffffu, mu, 0); mv = __shfl_sync(0xffffffffu, mv, 0); mw = __shfl_sync(0xffffffffu, mw, 0);
+    const T mu = su * inv, mv = sv * inv, mw = sw * inv;
     T ss = 0;
-    for (int k0 = 0; k0 < N; k0 += 32) {
-        const int k = k0 + lane;
-        T q = 0;
-        if (k < N) {
-            const T du = A.u[base_i + k] - mu, dv = A.v[base_i + k] - mv, dw = A.w[base_i + k] - mw;
-            q = (du * du + dv * dv) + dw * dw;
-        }
-        const int nk = min(32, N - k0);
-        for (int j = 0; j < nk; ++j) {
-            const T a = __shfl_sync(0xffffffffu, q, j);
-            if (lane == 0) ss += a;
-        }
+    for (int k = lane; k < N; k += 32) {
+        const T du = A.u[base_i + k] - mu, dv = A.v[base_i + k] - mv, dw = A.w[base_i + k] - mw;
+        ss += (du * du + dv * dv) + dw * dw;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
     const T Uh = pc.s_(c, 0), Vh = pc.s_(c, 1), RTh = pc.s_(c, 2);
-    T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTh) / ss) : T(0);
-    sc = __shfl_sync(0xffffffffu, sc, 0);
+    const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTh) / ss) : T(0);
     const T m = pc.m_(c);
     const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
     long long acc[5] = {0, 0, 0, 0, 0};
@@ -670,15 +747,15 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
     int max_it = 0;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    // each warp takes chunks of kChunk consecutive particles (of the cell-ordered array) from a global
+    // each warp takes chunks of K.chunk consecutive particles (of the cell-ordered array) from a global
     // counter and walks them 32 at a time, prefetching the next 32 records into L1 while it works on the
     // current ones; dynamic chunks keep all SMs busy when other kernels share the GPU
     for (;;) {
     int wbeg = 0;
-    if (lane == 0) wbeg = atomicAdd(d.counts + 5, kChunk);
+    if (lane == 0) wbeg = atomicAdd(d.counts + 5, K.chunk);
     wbeg = __shfl_sync(0xffffffffu, wbeg, 0);
     if (wbeg >= n) break;
-    const int wend = min(n, wbeg + kChunk);
+    const int wend = min(n, wbeg + K.chunk);
     for (int base = wbeg; base < wend; base += 32) {
         const int i = base + lane;
         const int inext = i + 32;
@@ -906,15 +983,16 @@ __global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long 
                 acc[q] += isL ? tt : -tt;
             }
         }
-        const double vol = d.vol[c], dt = d.dt[c];
-        const double coef = dt / vol;
+        // FP64 throughout; the divisions by Omega_i and dt_i are multiplications by their reciprocals
+        const double vol = d.vol[c], dt = d.dt[c], rvol = d.rcp[2 * c], rdt = d.rcp[2 * c + 1];
+        const double coef = dt * rvol;
         const double sc[4] = {ldexp(1.0, -K.fx0), ldexp(1.0, -K.fx1), ldexp(1.0, -K.fx1), ldexp(1.0, -K.fx4)};
         const int tk[4] = {0, 1, 2, 4};
         double* W = d.W + 4 * c;
         double Wn[4];
         for (int q = 0; q < 4; ++q) {
             const long long dd = d.wpl[5 * c + tk[q]] - d.wm[5 * c + tk[q]];
-            Wn[q] = (W[q] - coef * acc[q]) + ((double)dd * sc[q]) / vol;
+            Wn[q] = (W[q] - coef * acc[q]) + ((double)dd * sc[q]) * rvol;
         }
         if (K.dim == 1) Wn[2] = 0.0;
         if (!isfinite(Wn[0]) || !isfinite(Wn[1]) || !isfinite(Wn[2]) || !isfinite(Wn[3])) atomicOr(d.err, ERR_NONPHYS);
@@ -925,13 +1003,13 @@ __global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long 
             atomicAdd(d.stats + 11, 1ull);
         }
         for (int q = 0; q < 4; ++q) {
-            const double r = (Wn[q] - W[q]) / dt;
+            const double r = (Wn[q] - W[q]) * rdt;
             r2[q] = vol * (r * r);
             W[q] = Wn[q];
         }
         // retained tally of this step (the next step's W^p): W^{p,+} minus the collided particles that stay
         for (int k = 0; k < 5; ++k) d.wrt[5 * c + k] = d.wpl[5 * c + k] - d.wcol[5 * c + k];
-        const double chi = (((double)d.wpl[5 * c] * sc[0]) / vol) / W[0];
+        const double chi = (((double)d.wpl[5 * c] * sc[0]) * rvol) / W[0];
         d.chi_ema[c] = *dstep == 0 ? chi : d.chi_ema[c] + (2.0 / 1001.0) * (chi - d.chi_ema[c]);
     } else if (t < K.C + K.nwall) {
         const int iw = t - K.C;
@@ -939,10 +1017,10 @@ __global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long 
         const double nx = d.fnx[f], ny = d.fny[f], tx = -ny, ty = nx;
         const double* F = d.flux + 4 * (size_t)f;
         const double s1 = ldexp(1.0, -K.fx1), s4 = ldexp(1.0, -K.fx4);
-        const double sdt = d.fs[f] * d.dt[c];
-        const double px = ((double)d.wallt[3 * iw] * s1) / sdt;
-        const double py = ((double)d.wallt[3 * iw + 1] * s1) / sdt;
-        const double pe = ((double)d.wallt[3 * iw + 2] * s4) / sdt;
+        const double rsdt = 1.0 / (d.fs[f] * d.dt[c]);
+        const double px = ((double)d.wallt[3 * iw] * s1) * rsdt;
+        const double py = ((double)d.wallt[3 * iw + 1] * s1) * rsdt;
+        const double pe = ((double)d.wallt[3 * iw + 2] * s4) * rsdt;
         const double p = (F[1] + px) * nx + (F[2] + py) * ny;
         const double tw = (F[1] + px) * tx + (F[2] + py) * ty;
         const double q = F[3] + pe;
@@ -1096,6 +1174,10 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     };
     mark(0, s);
     k_begin_step<<<nblk(2LL * K.F, 256), 256, 0, s>>>(K, d);
+    if (K.shakhov) {
+        if (K.prec == 0) k_heat_tally<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32);
+        else k_heat_tally<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64);
+    }
     k_decompose<<<nblk(C, 128), 128, 0, s>>>(K, d);
     exclusive_scan(d.nhp, d.nhp_off, d.scan_tmp, C, d.counts + 1, s, d.counts, d.err);
     mark(1, s);
@@ -1107,8 +1189,8 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     launch_wave_flux(K, d, ctx.sms, s2);
     mark(7, s2);
     cudaEventRecord(ctx.ev_join, s2);
-    PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32};
-    PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp};
+    PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32, d.hq32};
+    PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp, d.hq};
     mark(2, s);
     if (K.prec == 0) k_sample<float><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
     else k_sample<double><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
@@ -1193,6 +1275,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     K.C = C; K.F = F; K.dim = mesh->dim; K.n_ref = opts->n_ref; K.wave_only = opts->wave_only;
     K.prec = opts->precision ? 1 : 0;
     K.omega = gas->omega; K.Pr = gas->Pr; K.Tw = Tw;
+    K.shakhov = gas->Pr != 1.0 && !opts->wave_only;
     K.mu_inf = (15.0 * sqrt(2.0 * 3.14159265358979323846 * 0.5) * Kn) / (2.0 * (5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega));
     K.U_inf = Ma * sqrt((5.0 / 3.0) * 0.5 * 1.0);
     K.m2RTw = -2.0 * 0.5 * Tw;
@@ -1235,7 +1318,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
             CK(cudaMemcpyAsync(bcjh, mesh->bc_jmax, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
         }
         MeshDev m{ni, nj, mesh->dim, mesh->periodic_j, periodic_i, F, xv, yv, bci, bco, bcjl, bcjh};
-        CK(dalloc(ctx, &d.vol, C)); CK(dalloc(ctx, &d.xc, C)); CK(dalloc(ctx, &d.yc, C)); CK(dalloc(ctx, &d.dt, C));
+        CK(dalloc(ctx, &d.vol, C)); CK(dalloc(ctx, &d.rcp, 2 * C)); CK(dalloc(ctx, &d.xc, C)); CK(dalloc(ctx, &d.yc, C)); CK(dalloc(ctx, &d.dt, C));
         CK(dalloc(ctx, &d.nfc, C)); CK(dalloc(ctx, &d.cf32, C)); CK(dalloc(ctx, &d.cf64, C));
         CK(dalloc(ctx, &d.cshift, 4 * C)); CK(dalloc(ctx, &d.cvx, 4 * C)); CK(dalloc(ctx, &d.cvy, 4 * C));
         CK(dalloc(ctx, &d.fL, F)); CK(dalloc(ctx, &d.fR, F)); CK(dalloc(ctx, &d.fbc, F)); CK(dalloc(ctx, &d.fwall, F));
@@ -1284,6 +1367,8 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         K.fx0 = 61 - ceil_log2(b0);
         K.fx1 = 61 - ceil_log2(b0 * speed);
         K.fx4 = 61 - ceil_log2(b0 * (0.5 * (speed * speed)));
+        K.fx_s2 = 61 - ceil_log2(b0 * (speed * speed));
+        K.fx_s3 = 61 - ceil_log2(b0 * (speed * speed * speed));
         {
             double tab[6][kSeries];
             double f1 = 1.0;   // (k+1)!
@@ -1309,6 +1394,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         CK(dalloc(ctx, &d.wallt, 3 * std::max(nwall, 1)));
         CK(dalloc(ctx, &d.tau, C)); CK(dalloc(ctx, &d.xr, C)); CK(dalloc(ctx, &d.emx, C)); CK(dalloc(ctx, &d.Wh, 4 * C));
         CK(dalloc(ctx, &d.co, 7 * C)); CK(dalloc(ctx, &d.mnew, C)); CK(dalloc(ctx, &d.samp, 3 * C));
+        CK(dalloc(ctx, &d.whq, 9 * C)); CK(dalloc(ctx, &d.hq, 3 * C)); CK(dalloc(ctx, &d.hq32, 3 * C));
         CK(dalloc(ctx, &d.hphys, C)); CK(dalloc(ctx, &d.nhp, C)); CK(dalloc(ctx, &d.nhp_off, C + 1));
         CK(dalloc(ctx, &d.cnt, C)); CK(dalloc(ctx, &d.off, C + 1)); CK(dalloc(ctx, &d.cur, C));
         CK(dalloc(ctx, &d.flux, 4 * F));
@@ -1320,7 +1406,8 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         CK(dalloc(ctx, &d.bufsel, 1)); CK(dalloc(ctx, &d.flags, 4)); CK(dalloc(ctx, &d.nretry, 1));
         CK(dalloc(ctx, &d.retry, F)); CK(dalloc(ctx, &d.done, 1));
         {
-            // faces evaluated in FP64: all in the FP64 mode; otherwise the faces of wall cells
+            // faces evaluated wholly in FP64: all in the FP64 mode, none in production mode (there the faces of
+            // wall cells, flagged in face_f64, weight FP32 moments with FP64 time integrals)
             std::vector<int> ff(F), fb(F);
             CK(cudaMemcpyAsync(ff.data(), d.face_f64, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
             CK(cudaMemcpyAsync(fb.data(), d.fR, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
@@ -1328,7 +1415,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
             std::vector<int> list;
             for (int f = 0; f < F; ++f) {
                 if (K.prec == 1) ff[f] = 1;
-                if (ff[f]) list.push_back(f);
+                if (K.prec == 1) list.push_back(f);
             }
             K.n_f64 = (int)list.size();
             CK(dalloc(ctx, &d.f64list, std::max(K.n_f64, 1)));
@@ -1337,7 +1424,8 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
                 CK(cudaMemcpyAsync(d.f64list, list.data(), sizeof(int) * K.n_f64, cudaMemcpyHostToDevice, ctx.stream));
             CK(cudaStreamSynchronize(ctx.stream));
         }
-        K.sort_every = 8;
+        K.sort_every = UGKWP_SORT_EVERY;
+        K.chunk = UGKWP_CHUNK;
         CK(dalloc(ctx, &d.tau32, C)); CK(dalloc(ctx, &d.dt32, C)); CK(dalloc(ctx, &d.mnew32, C));
         CK(dalloc(ctx, &d.samp32, 3 * C));
         CK(dalloc(ctx, &d.dstep, 1));
@@ -1496,6 +1584,7 @@ ugkwp_status ugkwp_stats(ugkwp_ctx* h, int64_t* out)
     out[8] = (int64_t)s[9];
     out[9] = (int64_t)s[10];
     out[10] = (int64_t)s[11];
+    out[11] = (int64_t)s[12];
     return st;
 }
 
@@ -1917,4 +2006,95 @@ extern "C" ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* h, double* W, double*
         CK(cudaMemcpyAsync(Wp, scratch, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
     }
     return check_device_error(ctx);
+}
+
+// ---- launch parameters and their autotuner ----------------------------------------------------------------
+// The particle kernels' launch shape (chunk of particles a warp claims, blocks per SM) and the counting-sort
+// interval change only the speed of a step: chunks and the sort reorder particles, and every result is an
+// integer sum or a per-particle / per-face quantity, so the state after a step is the same.
+namespace {
+ugkwp_status apply_launch(Ctx& ctx, int chunk, int bps, int sort_every)
+{
+    if (chunk) {
+        if (chunk < 32 || chunk > 8192 || chunk % 32) return fail(ctx, UGKWP_EINVAL, "chunk: a multiple of 32 in [32, 8192]");
+        ctx.k.chunk = chunk;
+    }
+    if (bps) {
+        if (bps < 1 || bps > 16) return fail(ctx, UGKWP_EINVAL, "blocks per SM: 1 to 16");
+        ctx.grid_particles = ctx.sms * bps;
+    }
+    if (sort_every) {
+        if (sort_every < 1 || sort_every > 64) return fail(ctx, UGKWP_EINVAL, "sort interval: 1 to 64 steps");
+        ctx.k.sort_every = sort_every;
+    }
+    if (ctx.graph) {   // the captured step holds the old constants
+        cudaGraphExecDestroy(ctx.graph);
+        ctx.graph = nullptr;
+    }
+    return UGKWP_OK;
+}
+}  // namespace
+
+extern "C" ugkwp_status ugkwp_set_launch(ugkwp_ctx* h, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every)
+{
+    if (!h) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    CK(cudaStreamSynchronize(ctx.stream));
+    return apply_launch(ctx, chunk, blocks_per_sm, sort_every);
+}
+
+extern "C" ugkwp_status ugkwp_get_launch(ugkwp_ctx* h, int32_t* out)
+{
+    if (!h || !out) return UGKWP_EINVAL;
+    const Ctx& ctx = h->c;
+    out[0] = ctx.k.chunk;
+    out[1] = ctx.grid_particles / ctx.sms;
+    out[2] = ctx.k.sort_every;
+    return UGKWP_OK;
+}
+
+extern "C" ugkwp_status ugkwp_autotune(ugkwp_ctx* h, int32_t steps, int32_t* best, double* best_ms)
+{
+    if (!h || steps < 1) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    if (ctx.k.wave_only) {   // no particle kernels to tune
+        if (best) ugkwp_get_launch(h, best);
+        if (best_ms) *best_ms = 0.0;
+        return UGKWP_OK;
+    }
+    static const int chunks[] = {128, 256, 512};
+    static const int bpss[] = {2, 4, 6};
+    static const int sorts[] = {8, 16};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double bms = 1e300;
+    int b[3] = {ctx.k.chunk, ctx.grid_particles / ctx.sms, ctx.k.sort_every};
+    ugkwp_status st = UGKWP_OK;
+    for (int ch : chunks)
+        for (int bp : bpss)
+            for (int so : sorts) {
+                if (st != UGKWP_OK) break;
+                CK(cudaStreamSynchronize(ctx.stream));
+                if ((st = apply_launch(ctx, ch, bp, so)) != UGKWP_OK) break;
+                // untimed steps (graph capture, then up to the next sort step), then whole sort periods
+                const int lead = (int)((so - 1 - ctx.step % so + so) % so) + 1;
+                if ((st = ugkwp_step(h, lead)) != UGKWP_OK) break;
+                const int n = ((steps + so - 1) / so) * so;
+                CK(cudaEventRecord(e0, ctx.stream));
+                if ((st = ugkwp_step(h, n)) != UGKWP_OK) break;
+                CK(cudaEventRecord(e1, ctx.stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms / n < bms) { bms = ms / n; b[0] = ch; b[1] = bp; b[2] = so; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != UGKWP_OK) return st;
+    if ((st = check_device_error(ctx)) != UGKWP_OK) return st;
+    if ((st = apply_launch(ctx, b[0], b[1], b[2])) != UGKWP_OK) return st;
+    if (best) { best[0] = b[0]; best[1] = b[1]; best[2] = b[2]; }
+    if (best_ms) *best_ms = bms;
+    return UGKWP_OK;
 }

@@ -48,6 +48,9 @@ struct Rng {
 // draw groups (first counter word)
 constexpr uint32_t DRAW_POS = 0u, DRAW_VEL = 2u, DRAW_TF = 5u;
 __device__ __forceinline__ uint32_t draw_wall(int h) { return 8u + 2u * (uint32_t)h; }
+// Shakhov acceptance-rejection attempt a: proposal draws +0 (+1 in FP64), acceptance draw +2
+__device__ __forceinline__ uint32_t draw_ar(int a) { return 1024u + 4u * (uint32_t)a; }
+constexpr int kArAttempts = 64;
 
 __device__ __forceinline__ float u01(uint32_t w)
 {

@@ -12,8 +12,9 @@
 //  the density that zeroes the wave mass flux; far-field / fixed ghosts carry their full free-transport
 //  part (no particles are injected) and use the fluid cell's time step on both halves (Sec. IV B); a
 //  symmetry face mirrors L.
-//  The moment algebra is a dense 4x4 closed form per face, so it runs on the FP32/FP64 pipes; faces
-//  flagged face_f64 (next to walls) are always evaluated in FP64.
+//  The moment algebra is a dense 4x4 closed form per face, so it runs on the FP32/FP64 pipes. In production
+//  mode the velocity moments are FP32; the faces of wall cells (flag face_f64) weight them with their FP64
+//  time integrals and sum in FP64.
 #include <cuda_runtime.h>
 #include <cmath>
 #include "ugkwp_internal.h"
@@ -112,10 +113,11 @@ template <typename R> __device__ __forceinline__ void pr_fix(const Prim<R>& p, R
 }
 
 // equilibrium part of Eq. 49 given the interface state W_0 (primitive p0); c[0..2] = dbar_a, dbar_b,
-// dbar_c of each side
-template <typename R>
-__device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], const Prim<R>& p0, const R cL[3],
-                                 const R cR[3], R dL, R dR, R Pr, R F[4])
+// dbar_c of each side. Moments in precision R; the time-integration weights and the weighted sum in
+// precision C (C = double for the faces of wall cells in production mode: FP64 time integrals).
+template <typename R, typename C>
+__device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], const Prim<R>& p0, const C cL[3],
+                                 const C cR[3], R dL, R dR, R Pr, C F[4])
 {
     Mom<R> m0;
     moments(p0, m0);
@@ -137,34 +139,34 @@ __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], co
     R f[4];
     psi_mom(m0.up, m0, 1, 0, 0, f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] = cL[0] * f[k];
+    for (int k = 0; k < 4; ++k) F[k] = cL[0] * C(f[k]);
     psi_mom(m0.um, m0, 1, 0, 0, f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] += cR[0] * f[k];
+    for (int k = 0; k < 4; ++k) F[k] += cR[0] * C(f[k]);
     psi_poly(m0.up, m0, 2, 0, aL, f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] += cL[1] * f[k];
+    for (int k = 0; k < 4; ++k) F[k] += cL[1] * C(f[k]);
     psi_poly(m0.um, m0, 2, 0, aR, f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] += cR[1] * f[k];
+    for (int k = 0; k < 4; ++k) F[k] += cR[1] * C(f[k]);
     psi_poly(m0.up, m0, 1, 0, A, f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] += cL[2] * f[k];
+    for (int k = 0; k < 4; ++k) F[k] += cL[2] * C(f[k]);
     psi_poly(m0.um, m0, 1, 0, A, f);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] = p0.rho * (F[k] + cR[2] * f[k]);
+    for (int k = 0; k < 4; ++k) F[k] = C(p0.rho) * (F[k] + cR[2] * C(f[k]));
 }
 
 // interior-type face; frL/frR weight each side's g^h. Returns false if a side state is not a valid
 // Maxwellian in precision R (the caller then uses FP64).
-template <typename R>
+template <typename R, typename C>
 __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], bool hL, bool hR,
-                          const R cL[3], const R cR[3], R frL, R frR, R dL, R dR, R Pr, R F[4])
+                          const C cL[3], const C cR[3], C frL, C frR, R dL, R dR, R Pr, C F[4])
 {
     Prim<R> pL, pR, p0;
     Mom<R> mL, mR;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] = R(0);
+    for (int k = 0; k < 4; ++k) F[k] = C(0);
     if (!frame_prim(WL, pL) || !frame_prim(WR, pR)) return false;
     moments(pL, mL);
     moments(pR, mR);
@@ -182,19 +184,19 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
         moments(ph, mh);
         psi_mom(mh.up, mh, 1, 0, 0, f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] += frL * ph.rho * f[k];
+        for (int k = 0; k < 4; ++k) F[k] += frL * C(ph.rho * f[k]);
     }
     if (hR && frame_prim(WhR, ph)) {
         moments(ph, mh);
         psi_mom(mh.um, mh, 1, 0, 0, f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] += frR * ph.rho * f[k];
+        for (int k = 0; k < 4; ++k) F[k] += frR * C(ph.rho * f[k]);
     }
     return true;
 }
 
-template <typename R>
-__device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, R caL, R frL, R lam_w, R F[4])
+template <typename R, typename C>
+__device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, C caL, C frL, R lam_w, C F[4])
 {
     Prim<R> p;
     Mom<R> m;
@@ -203,19 +205,19 @@ __device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, R caL, R frL, 
     moments(p, m);
     psi_mom(m.up, m, 1, 0, 0, t);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] = caL * p.rho * t[k];
+    for (int k = 0; k < 4; ++k) F[k] = caL * C(p.rho * t[k]);
     if (hL && frame_prim(WhL, p)) {
         moments(p, m);
         psi_mom(m.up, m, 1, 0, 0, t);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] += frL * p.rho * t[k];
+        for (int k = 0; k < 4; ++k) F[k] += frL * C(p.rho * t[k]);
     }
     p.rho = R(1); p.U = R(0); p.V = R(0); p.lam = lam_w;
     moments(p, m);
     psi_mom(m.um, m, 1, 0, 0, t);
-    const R rw = -F[0] / t[0];
+    const C rw = -F[0] / C(t[0]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] += rw * t[k];
+    for (int k = 0; k < 4; ++k) F[k] += rw * C(t[k]);
     return true;
 }
 
@@ -259,7 +261,7 @@ __device__ double tau_of(const StepConsts& K, const double W[4])
     return mu / (rho * RT);
 }
 
-template <typename R>
+template <typename R, typename C>
 __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4])
 {
     const int L = c.fL[f], Rc = c.fR[f], bc = c.fbc[f];
@@ -272,27 +274,28 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         o[2] = -a * nyr + b * nxr;
         o[3] = R(W[3]);
     };
-    R WL[4], WhL[4], WR[4], WhR[4], F[4];
+    R WL[4], WhL[4], WR[4], WhR[4];
+    C F[4];
     bool ok;
     rot(c.W + 4 * L, WL);
     rot(c.Wh + 4 * L, WhL);
     const double* coL = c.co + 7 * L;
-    const R cL[3] = {R(coL[0]), R(coL[1]), R(coL[2])};
-    const R frL = R(K.wave_only ? coL[3] : coL[5]);
+    const C cL[3] = {C(coL[0]), C(coL[1]), C(coL[2])};
+    const C frL = C(K.wave_only ? coL[3] : coL[5]);
     const bool hL = c.hphys[L] != 0;
     if (bc == 0 || bc == UGKWP_BC_PERIODIC) {
         rot(c.W + 4 * Rc, WR);
         rot(c.Wh + 4 * Rc, WhR);
         const double* coR = c.co + 7 * Rc;
-        const R cR[3] = {R(coR[0]), R(coR[1]), R(coR[2])};
-        const R frR = R(K.wave_only ? coR[3] : coR[5]);
-        ok = face_flux<R>(WL, WR, WhL, WhR, hL, c.hphys[Rc] != 0, cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]),
-                          R(K.Pr), F);
+        const C cR[3] = {C(coR[0]), C(coR[1]), C(coR[2])};
+        const C frR = C(K.wave_only ? coR[3] : coR[5]);
+        ok = face_flux<R, C>(WL, WR, WhL, WhR, hL, c.hphys[Rc] != 0, cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]),
+                             R(K.Pr), F);
     } else if (bc == UGKWP_BC_WALL) {
-        ok = wall_flux<R>(WL, WhL, hL, cL[0], frL, R(0.5 / (kR * K.Tw)), F);
+        ok = wall_flux<R, C>(WL, WhL, hL, cL[0], frL, R(0.5 / (kR * K.Tw)), F);
     } else if (bc == UGKWP_BC_SYMMETRY) {
         const R Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
-        ok = face_flux<R>(WL, Wm, WhL, Whm, hL, hL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
+        ok = face_flux<R, C>(WL, Wm, WhL, Whm, hL, hL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
     } else {
         double Wg[4];
         if (bc == UGKWP_BC_FIXED) {
@@ -305,12 +308,13 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         rot(Wg, WR);
         double cg[4];
         ghost_coeffs(c.dt[L], tau_of(K, Wg), cg);
-        const R cR[3] = {R(cg[0]), R(cg[1]), R(cg[2])};
-        ok = face_flux<R>(WL, WR, WhL, WR, hL, true, cL, cR, frL, R(cg[3]), R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
+        const C cR[3] = {C(cg[0]), C(cg[1]), C(cg[2])};
+        ok = face_flux<R, C>(WL, WR, WhL, WR, hL, true, cL, cR, frL, C(cg[3]), R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
     }
+    const C nxc = C(nx), nyc = C(ny);
     out[0] = double(F[0]);
-    out[1] = double(F[1] * nxr - F[2] * nyr);
-    out[2] = double(F[1] * nyr + F[2] * nxr);
+    out[1] = double(F[1] * nxc - F[2] * nyc);
+    out[2] = double(F[1] * nyc + F[2] * nxc);
     out[3] = double(F[3]);
     return ok && isfinite(out[0]) && isfinite(out[1]) && isfinite(out[2]) && isfinite(out[3]);
 }
@@ -322,21 +326,24 @@ __device__ __forceinline__ void store_flux(const Dev& c, int f, const double out
     o[1] = make_double2(out[2], out[3]);
 }
 
-// interior faces in FP32 (production mode); a face whose FP32 evaluation under- or overflows (near-vacuum
-// neighbours with extreme moments) is queued for the FP64 kernel
+// production mode: every face with FP32 velocity moments; the faces of wall cells apply their time
+// integrals (the normalised coefficients, computed in FP64 in the decomposition) and sum the weighted
+// moments in FP64. A face whose FP32 evaluation under- or overflows (near-vacuum neighbours with extreme
+// moments) is queued for the FP64 kernel.
 __global__ void __launch_bounds__(128) k_wave_flux32(const StepConsts K, const Dev c)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= K.F || c.face_f64[f]) return;
+    if (f >= K.F) return;
     double out[4];
-    if (one_face<float>(K, c, f, out)) store_flux(c, f, out);
+    const bool ok = c.face_f64[f] ? one_face<float, double>(K, c, f, out) : one_face<float, float>(K, c, f, out);
+    if (ok) store_flux(c, f, out);
     else c.retry[atomicAdd(c.nretry, 1)] = f;
 }
 
-// FP64 faces: the static list (faces of wall cells; every face in the FP64 mode), then the faces queued by
-// the FP32 kernel. The FP64 pipe's cost grows with the active lanes of a warp, so in production mode the
-// faces are spread one per warp (lane 0) over one warp per SM sub-partition; in the all-FP64 mode every
-// lane takes a face.
+// FP64 faces: the static list (every face in the FP64 mode, none in production mode), then the faces
+// queued by the FP32 kernel. The FP64 pipe's cost grows with the active lanes of a warp, so in production
+// mode the (rare) queued faces are spread one per warp (lane 0); in the all-FP64 mode every lane takes a
+// face.
 __global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c, int lanes)
 {
     if ((int)threadIdx.x >= lanes) return;
@@ -344,7 +351,11 @@ __global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const De
     for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < n; j += gridDim.x * lanes) {
         const int f = j < K.n_f64 ? c.f64list[j] : c.retry[j - K.n_f64];
         double out[4];
-        one_face<double>(K, c, f, out);
+        one_face<double, double>(K, c, f, out);
+        // a non-finite flux (near-vacuum neighbours: the interface density underflows against theirs and the
+        // slopes overflow) carries nothing through the face
+        if (!isfinite(out[0]) || !isfinite(out[1]) || !isfinite(out[2]) || !isfinite(out[3]))
+            out[0] = out[1] = out[2] = out[3] = 0.0;
         store_flux(c, f, out);
     }
 }

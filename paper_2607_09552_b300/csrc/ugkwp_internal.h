@@ -35,7 +35,9 @@ template <typename T> struct ParticleSoA {
 struct StepConsts {
     int C, F, dim, nwall, n_ref, wave_only, prec;
     int fx0, fx1, fx4;              // fixed-point exponents: mass, momentum, energy
+    int fx_s2, fx_s3, shakhov;      // second / third velocity moments; Shakhov sampling (Pr != 1, particles)
     int n_f64, sort_every;          // faces in f64list; counting sort of the particles every sort_every steps
+    int chunk;                      // particles per dynamically claimed chunk of the transport kernel
     double mu_inf, omega, Pr, Tw, U_inf, m2RTw, sig_w;
     double T_cap, U_cap, T_min;     // realizability bounds of a cell state
     double W_inf[4], W_fix[4];
@@ -46,6 +48,7 @@ struct StepConsts {
 struct Dev {
     // geometry
     double *vol, *xc, *yc, *dt;
+    double* rcp;                       // [2C] 1 / Omega_i, 1 / dt_i
     int* nfc;
     CellFaces<float>* cf32;
     CellFaces<double>* cf64;
@@ -63,6 +66,9 @@ struct Dev {
     // per-step cell data
     double *tau, *xr, *emx, *Wh, *co, *mnew;
     double* samp;                      // [3C] U^h, V^h, R T^h
+    long long* whq;                    // [9C] Pr != 1: raw moments of the retained particles
+    double* hq;                        // [3C] Pr != 1: acceptance-rejection weights a_x, a_y, M
+    float* hq32;
     int *hphys, *nhp, *nhp_off, *cnt, *off, *cur;
     int* scan_tmp;
     double* flux;                      // [4F]

@@ -65,16 +65,20 @@ def loads(case, p, tau, q, geom=None):
 
 
 def steady_step(hist, alpha: float = 2.0 / 1001.0, tol: float = 0.01, window: float = 0.2):
-    """First step after which the EMA of `hist` stays within tol of the mean of its final window (the last
-    `window` fraction of the run); len(hist) if it never settles. Returns (step, ema)."""
+    """First step after which the EMA of `hist` stays within a band around the mean of its final window (the
+    last `window` fraction of the run); len(hist) if it never settles. The band is the larger of tol times
+    that mean and three standard deviations of the EMA over the final window (the particle noise the EMA
+    keeps at steady state). Returns (step, ema)."""
     h = np.asarray(hist, dtype=np.float64)
     ema = np.empty_like(h)
     e = h[0]
     for k, v in enumerate(h):
         e = e + alpha * (v - e) if k else v
         ema[k] = e
-    ref = ema[int(len(h) * (1 - window)):].mean()
-    bad = np.nonzero(np.abs(ema - ref) > tol * abs(ref))[0]
+    tail = ema[int(len(h) * (1 - window)):]
+    ref = tail.mean()
+    band = max(tol * abs(ref), 3.0 * float(tail.std()))
+    bad = np.nonzero(np.abs(ema - ref) > band)[0]
     return (int(bad[-1] + 1) if bad.size else 0), ema
 
 
@@ -107,4 +111,5 @@ def first_residual(case, **solver_kw):
     s.step(1)
     r = s.residual()[4:].copy()
     s.close()
-    return r
+    # a component that does not move in the first step (e.g. by symmetry) is measured against the largest
+    return np.where(r > 0.0, r, max(float(r.max()), 1e-300))

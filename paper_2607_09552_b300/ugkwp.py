@@ -25,7 +25,8 @@ EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugk
            "ugkwp_batch_destroy", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_mlp_create", "ugkwp_mlp_destroy",
            "ugkwp_mlp_num_params", "ugkwp_mlp_get_params", "ugkwp_mlp_set_params", "ugkwp_mlp_forward",
            "ugkwp_mlp_grad", "ugkwp_mlp_adam", "ugkwp_mlp_features", "ugkwp_field_accumulate", "ugkwp_mlp_dataset",
-           "ugkwp_warm_start", "ugkwp_get_field_noalloc", "ugkwp_last_error"]
+           "ugkwp_warm_start", "ugkwp_get_field_noalloc", "ugkwp_set_launch", "ugkwp_get_launch", "ugkwp_autotune",
+           "ugkwp_last_error"]
 STAGES = ["decompose", "sample", "particles", "wave_flux", "sort", "update"]
 
 
@@ -180,8 +181,8 @@ class Solver:
 
     def stats(self):
         """[steps, particles, new, removed, left, crossings, wall hits, max iterations, cumulative
-        particle-steps, cumulative new particles, cells floored in the last step]"""
-        out = np.zeros(11, dtype=np.int64)
+        particle-steps, cumulative new particles, cells floored in the last step, A-R fallbacks]"""
+        out = np.zeros(12, dtype=np.int64)
         self._check(load().ugkwp_stats(self.ctx, _p(out, C.c_int64)))
         return out
 
@@ -190,6 +191,21 @@ class Solver:
 
     def load_checkpoint(self, path: str):
         self._check(load().ugkwp_load(self.ctx, os.fsencode(path)))
+
+    def set_launch(self, chunk: int = 0, blocks_per_sm: int = 0, sort_every: int = 0):
+        self._check(load().ugkwp_set_launch(self.ctx, C.c_int32(chunk), C.c_int32(blocks_per_sm), C.c_int32(sort_every)))
+
+    def launch(self):
+        out = (C.c_int32 * 3)()
+        self._check(load().ugkwp_get_launch(self.ctx, out))
+        return list(out)
+
+    def autotune(self, steps: int = 16):
+        """(best [chunk, blocks_per_sm, sort_every], ms per step) after timing the candidates on real steps."""
+        out = (C.c_int32 * 3)()
+        ms = C.c_double()
+        self._check(load().ugkwp_autotune(self.ctx, C.c_int32(steps), out, C.byref(ms)))
+        return list(out), ms.value
 
     def set_profiling(self, on: bool):
         self._check(load().ugkwp_set_profiling(self.ctx, C.c_int32(int(on))))

@@ -45,6 +45,7 @@ def _compare_step(g, o, prec):
     sg, so = g.stats(), o.stats()
     assert np.array_equal(sg[1:8], so[1:8]), (sg, so)
     assert sg[10] == so[8]
+    assert sg[11] == so[9]
     assert_particles_equal(g.particles(), o.particles())
     Fg, Fo = g.flux(), o.flux()
     assert_field_close(Fg, Fo, 10 * TOL[prec])
@@ -203,3 +204,31 @@ def test_batched_graph_equals_individual_runs(cuda_lib):
         assert_particles_equal(a.particles(), g.particles())
         assert np.array_equal(a.stats()[:8], g.stats()[:8])
     b.close()
+
+
+def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
+    """Chunk size, blocks per SM and the sort interval reorder work and particles only: the state is the same
+    bit for bit (particles compared as sets), also across an autotuning pass that steps the run."""
+    case = CASES["cylinder"]
+    a = cuda_lib.Solver(case, precision=0, use_graph=True)
+    b = cuda_lib.Solver(case, precision=0, use_graph=True)
+    assert b.launch() == [256, 4, 8]
+    b.set_launch(128, 2, 16)
+    assert b.launch() == [128, 2, 16]
+    a.step(21)
+    b.step(21)
+    assert np.array_equal(a.field()[0], b.field()[0])
+    assert_particles_equal(a.particles(), b.particles())
+    best, ms = b.autotune(4)
+    assert best[0] in (128, 256, 512) and best[1] in (2, 4, 6) and best[2] in (8, 16) and ms > 0
+    n = int(b.stats()[0]) - int(a.stats()[0])
+    a.step(n)
+    b.step(5)
+    a.step(5)
+    assert np.array_equal(a.field()[0], b.field()[0])
+    assert_particles_equal(a.particles(), b.particles())
+    ta, tb = a.tallies(), b.tallies()
+    for k in ("wm", "wpl", "wret", "cross"):
+        assert np.array_equal(ta[k], tb[k])
+    with pytest.raises(cuda_lib.UgkwpError):
+        b.set_launch(100, 0, 0)
