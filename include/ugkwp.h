@@ -182,8 +182,8 @@ ugkwp_status ugkwp_load(ugkwp_ctx* ctx, const char* path);
  * ugkwp_batch_create. ugkwp_get_launch fills out[3] in the same order. */
 ugkwp_status ugkwp_set_launch(ugkwp_ctx* ctx, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every);
 ugkwp_status ugkwp_get_launch(ugkwp_ctx* ctx, int32_t* out);
-/* Autotuner: times each combination of chunk {128, 256, 512}, blocks per SM {2, 4, 6} and sort interval
- * {8, 16} over whole sort periods of at least `steps` steps (real steps of the run: the state advances)
+/* Autotuner: times each combination of chunk {128, 256}, blocks per SM {4, 6, 8} and sort interval
+ * {8, 16, 32} over whole sort periods of at least `steps` steps (real steps of the run: the state advances)
  * with CUDA events on the context's stream, keeps the fastest and returns it in best[3] (nullable, order of
  * ugkwp_set_launch) and its milliseconds per step in best_ms (nullable). Synchronises. A particle-free
  * context keeps its values. */

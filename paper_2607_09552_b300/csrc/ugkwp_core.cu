@@ -2062,9 +2062,9 @@ extern "C" ugkwp_status ugkwp_autotune(ugkwp_ctx* h, int32_t steps, int32_t* bes
         if (best_ms) *best_ms = 0.0;
         return UGKWP_OK;
     }
-    static const int chunks[] = {128, 256, 512};
-    static const int bpss[] = {2, 4, 6};
-    static const int sorts[] = {8, 16};
+    static const int chunks[] = {128, 256};
+    static const int bpss[] = {4, 6, 8};
+    static const int sorts[] = {8, 16, 32};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

@@ -220,7 +220,7 @@ def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
     assert np.array_equal(a.field()[0], b.field()[0])
     assert_particles_equal(a.particles(), b.particles())
     best, ms = b.autotune(4)
-    assert best[0] in (128, 256, 512) and best[1] in (2, 4, 6) and best[2] in (8, 16) and ms > 0
+    assert best[0] in (128, 256) and best[1] in (4, 6, 8) and best[2] in (8, 16, 32) and ms > 0
     n = int(b.stats()[0]) - int(a.stats()[0])
     a.step(n)
     b.step(5)
