@@ -226,8 +226,12 @@ def reduce_over_ranks(ms: float, work: float, world: int, device: str):
 
 def gpu_launches_per_step(case):
     # begin-step, decompose, 3 scan kernels, sample, particles, 2 wave-flux kernels, 3 scan kernels and the
-    # scatter (they return at once except on sort steps), update
-    return 13
+    # scatter (they return at once except on sort steps), update; the ghost-source parameter and particle
+    # kernels when the mesh has far-field or fixed faces; the heat-flux tally when Pr != 1
+    m = case.mesh
+    tags = list(m.bc_imin) + list(m.bc_imax) + list(m.bc_jmin) + list(m.bc_jmax)
+    ghosts = any(t in (wl.BC_FARFIELD, wl.BC_FIXED) for t in tags)
+    return 13 + (2 if ghosts else 0) + (1 if case.Pr != 1.0 else 0)
 
 
 def run_e2e(args, solver, stream):
@@ -489,6 +493,17 @@ def _eval_stoch(c, warm, net, fam, geom, n, navg, st):
     return r
 
 
+def scaled_residual(case, solver):
+    """Largest raw residual component in freestream units: sqrt(sum_i Omega_i (dW/dt)^2) divided by
+    (rho U, rho U^2, rho U^2, rho U^3 / 2) / L times the square root of the domain area, so that an O(1)
+    flux imbalance over the whole domain reads about 1 whatever the first step looked like."""
+    r = solver.residual()[4:]
+    U = wl.freestream_speed(case.Ma)
+    area = float(np.sum(solver.geometry()[1]))
+    scale = np.array([U, U * U, U * U, 0.5 * U ** 3]) * np.sqrt(area)
+    return float(np.max(r / scale))
+
+
 def run_warmstart(args):
     """Learned warm start (all on the GPU): converged particle-free fields of seeded sweeps of 16 uneven
     cases (cylinders and plates, batched graph launches) train one network per geometry family; then held-out
@@ -514,11 +529,11 @@ def run_warmstart(args):
         while steps < args.train_max_steps:
             b.step(1000)
             steps += 1000
-            for i, sv in enumerate(solvers):
+            for i, (c, sv) in enumerate(zip(cases, solvers)):
                 if i in failed:
                     continue
                 try:
-                    res[i] = float(np.max(sv.residual()[:4]))
+                    res[i] = scaled_residual(c, sv)
                 except ugkwp.UgkwpError as e:
                     failed[i] = str(e)
                     res[i] = 0.0
@@ -540,6 +555,9 @@ def run_warmstart(args):
         print(json.dumps({"phase": f"training fields, sweep {seed}", **out["train"][f"sweep{seed}"]}), flush=True)
     nets = {}
     for fam, tset in sets.items():
+        if not tset.sizes:
+            out["train"][fam] = {"fields": 0, "note": "no converged training field: this family starts cold"}
+            continue
         feats, targs = tset.tensors()
         net = ws.new_network(0)
         t0 = time.perf_counter()
@@ -566,6 +584,9 @@ def run_warmstart(args):
         fam = ws.family(c)
         e = {"case": c.name, "family": fam, "Kn": c.Kn, "Ma": c.Ma, "Tw": c.Tw}
         out["eval"].append(e)
+        if fam not in nets:
+            e["wave_only_fp64"] = {"note": "no network for this family"}
+            continue
         try:
             _eval_wave(e, c, ref, fam, nets, args, st)
         except ugkwp.UgkwpError as err:
@@ -579,7 +600,8 @@ def run_warmstart(args):
     solvers = []
     for c in cases:
         s = ugkwp.Solver(c, precision=1, wave_only=True, stream=st)
-        s.warm_start(nets[ws.family(c)], ws.FAMILY_MAPS[ws.family(c)])
+        if ws.family(c) in nets:
+            s.warm_start(nets[ws.family(c)], ws.FAMILY_MAPS[ws.family(c)])
         solvers.append(s)
     b = ugkwp.Batch(solvers, stream=st)
     done, steps = [None] * len(solvers), 0
@@ -608,8 +630,11 @@ def run_warmstart(args):
         geom = steady.wall_geometry(c)
         res = {}
         for start in ("cold", "warm"):
+            if start == "warm" and fam not in nets:
+                res[start] = {"note": "no network for this family"}
+                continue
             try:
-                res[start] = _eval_stoch(c, start == "warm", nets[fam], fam, geom, n, navg, st)
+                res[start] = _eval_stoch(c, start == "warm", nets.get(fam), fam, geom, n, navg, st)
             except ugkwp.UgkwpError as err:
                 res[start] = {"error": str(err)}
         if "surface" in res["cold"] and "surface" in res["warm"]:
@@ -648,7 +673,7 @@ def main():
     ap.add_argument("--train-tol", type=float, default=1e-5)
     ap.add_argument("--train-max-steps", type=int, default=60000)
     ap.add_argument("--train-steps", type=int, default=60000)
-    ap.add_argument("--train-accept", type=float, default=1e-2)
+    ap.add_argument("--train-accept", type=float, default=1e-3)
     ap.add_argument("--eval-cyl", type=int, default=4)
     ap.add_argument("--eval-plate", type=int, default=4)
     ap.add_argument("--eval-wave-max", type=int, default=200000)

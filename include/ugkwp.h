@@ -123,14 +123,15 @@ ugkwp_status ugkwp_get_field(ugkwp_ctx* ctx, double* W, double* Wp);
  * Synchronises. */
 ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* ctx, double* W, double* Wp);
 
-/* out[12]: steps taken, particles, new in the last step, removed (collided), left the domain, face
+/* out[13]: steps taken, particles, new in the last step, removed (collided), left the domain, face
  * crossings, wall hits, largest crossings + hits of one particle in the last step; then, cumulative since
  * creation, particle-steps processed (retained + new particles of every step) and new particles; then the
  * cells reset to the vacuum floor in the last step: a cell state outside the realizable set (density
  * above 1e-12, 0.01 min(1, T_w, T_fixed) <= T <= T_cap = 10 max(1 + Ma^2/3, T_w, T_fixed),
  * |U| <= U_inf + 10 sqrt(R T_cap)) restarts from rho = 1e-12 at rest at T_inf; a hydrodynamic part W^h
  * outside that set is not sampled and has no free-transport wave flux; last, the new particles of the
- * last step whose Shakhov acceptance-rejection (Pr != 1) kept a Maxwellian proposal after 64 rejections. */
+ * last step whose Shakhov acceptance-rejection (Pr != 1) kept a Maxwellian proposal after 64 rejections;
+ * last, the particles that entered from far-field / fixed ghost sources in the last step. */
 ugkwp_status ugkwp_stats(ugkwp_ctx* ctx, int64_t* out);
 int64_t ugkwp_num_particles(ugkwp_ctx* ctx);
 
@@ -192,8 +193,10 @@ ugkwp_status ugkwp_autotune(ugkwp_ctx* ctx, int32_t steps, int32_t* best, double
 /* Per-stage device timing with CUDA events recorded on the context's stream around each stage of every
  * step taken while enabled (graph replay is bypassed meanwhile). ugkwp_profile synchronises, returns the
  * summed milliseconds of the 6 stages (ms[0..5]: decomposition + slot scan, new-particle sampling,
- * particle transport, tallies and compaction, wave fluxes, the periodic counting sort of the particles by
- * cell, conservative update + surface quantities + step bookkeeping) and the number of profiled steps, and
+ * particle transport, tallies and compaction, ghost particle sources + wave fluxes (on a second stream,
+ * overlapped with sampling and transport), the periodic counting sort of the particles by cell (after the
+ * second stream joins), conservative update + surface quantities + step bookkeeping) and the number of
+ * profiled steps, and
  * clears the record (ms needs room for 8 values). */
 ugkwp_status ugkwp_set_profiling(ugkwp_ctx* ctx, int32_t enable);
 ugkwp_status ugkwp_profile(ugkwp_ctx* ctx, double* ms, int64_t* steps);

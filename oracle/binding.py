@@ -168,8 +168,8 @@ class Oracle:
 
     def stats(self):
         """[steps, particles, new, removed, left, crossings, wall hits, max iterations, floored cells,
-        A-R fallbacks]"""
-        out = np.zeros(10, dtype=np.int64)
+        A-R fallbacks, particles entering from ghosts]"""
+        out = np.zeros(11, dtype=np.int64)
         lib().oracle_stats(self.ctx, _p(out, C.c_int64))
         return out
 

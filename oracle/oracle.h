@@ -54,7 +54,7 @@ int  oracle_surface(oracle_ctx* cx, double* p, double* tau, double* q, int32_t n
  * acceptance-rejection weights (ax, ay, M) (see shakhov_weights); returns the fallback count */
 int64_t oracle_ar_sample(int32_t precision, uint64_t seed, uint32_t case_id, int64_t step, uint64_t pid0, int32_t n,
                          double ax, double ay, double M, double* z);
-int  oracle_stats(oracle_ctx* cx, int64_t* out);                    /* [10] */
+int  oracle_stats(oracle_ctx* cx, int64_t* out);                    /* [11] */
 int64_t oracle_num_particles(oracle_ctx* cx);
 int  oracle_get_particles(oracle_ctx* cx, int64_t cap, uint64_t* pid, int32_t* cell, double* x, double* y,
                           double* u, double* v, double* w, double* m);

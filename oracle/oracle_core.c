@@ -57,8 +57,9 @@ double oracle_mu_inf(double Kn, double omega)
 
 static double tau_of(const or_ctx* cx, const double W[4])
 {
-    const double rho = W[0], U = W[1] / rho, V = W[2] / rho;
-    const double RT = (W[3] / rho - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+    /* primitive variables through r = 1 / rho */
+    const double rho = W[0], r = 1.0 / rho, U = W[1] * r, V = W[2] * r;
+    const double RT = (W[3] * r - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
     const double T = RT / OR_R;
     const double mu = cx->mu_inf * or_powd(T, cx->omega);
     return mu / (rho * RT);
@@ -342,6 +343,7 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
     cx->fL = zalloc(F, 4); cx->fR = zalloc(F, 4); cx->fbc = zalloc(F, 4); cx->fwall = zalloc(F, 4);
     cx->fnx = zalloc(F, 8); cx->fny = zalloc(F, 8); cx->fs = zalloc(F, 8); cx->fdL = zalloc(F, 8);
     cx->fdR = zalloc(F, 8); cx->finv_s = zalloc(F, 8);
+    cx->fax = zalloc(F, 8); cx->fay = zalloc(F, 8); cx->fex = zalloc(F, 8); cx->fey = zalloc(F, 8);
     double* fd = zalloc(F, 8);
     if (m->dim == 1) {
         const double* xs = m->xv;
@@ -354,6 +356,7 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
         }
         for (int f = 0; f < F; ++f) {
             cx->fnx[f] = 1.0; cx->fny[f] = 0.0; cx->fs[f] = 1.0;
+            cx->fax[f] = xs[f];
             if (f == 0 && periodic_i) {
                 cx->fL[f] = ni - 1; cx->fR[f] = 0; cx->fbc[f] = OR_BC_PERIODIC;
                 cx->fdL[f] = xs[ni] - cx->xc[ni - 1]; cx->fdR[f] = cx->xc[0] - xs[0];
@@ -400,6 +403,7 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
                 const int f = i + (ni + 1) * j;
                 const int a = VID(i, j), b = VID(i, j + 1);
                 const double ex = m->xv[b] - m->xv[a], ey = m->yv[b] - m->yv[a];
+                cx->fax[f] = m->xv[a]; cx->fay[f] = m->yv[a]; cx->fex[f] = ex; cx->fey[f] = ey;
                 const double len = sqrt(ex * ex + ey * ey);
                 double nx = ey / len, ny = -ex / len;
                 cx->fs[f] = len;
@@ -421,6 +425,7 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
                 const int f = joff + i + ni * j;
                 const int a = VID(i, j), b = VID(i + 1, j);
                 const double ex = m->xv[b] - m->xv[a], ey = m->yv[b] - m->yv[a];
+                cx->fax[f] = m->xv[a]; cx->fay[f] = m->yv[a]; cx->fex[f] = ex; cx->fey[f] = ey;
                 const double len = sqrt(ex * ex + ey * ey);
                 double nx = -ey / len, ny = ex / len;
                 cx->fs[f] = len;
@@ -495,6 +500,22 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
     }
     cx->wall_face = zalloc(cx->nwall, 4);
     for (int f = 0; f < F; ++f) if (cx->fwall[f] >= 0) cx->wall_face[cx->fwall[f]] = f;
+    /* far-field and fixed faces: ghost particle sources */
+    cx->n_inj = 0;
+    for (int f = 0; f < F; ++f) if (cx->fbc[f] == OR_BC_FARFIELD || cx->fbc[f] == OR_BC_FIXED) cx->n_inj++;
+    const int ni1 = cx->n_inj > 0 ? cx->n_inj : 1;
+    cx->inj_face = zalloc(ni1, 4); cx->inj_k = zalloc(ni1, 4); cx->inj_n = zalloc(ni1, 4);
+    cx->inj_m = zalloc(ni1, 8); cx->inj_u = zalloc(ni1, 8); cx->inj_v = zalloc(ni1, 8);
+    cx->inj_sig = zalloc(ni1, 8); cx->inj_D = zalloc(ni1, 8);
+    for (int f = 0, j = 0; f < F; ++f) {
+        if (cx->fbc[f] != OR_BC_FARFIELD && cx->fbc[f] != OR_BC_FIXED) continue;
+        const int L = cx->fL[f];
+        int kk = -1;
+        for (int k = 0; k < cx->nfc[L]; ++k) if (cx->cface[4 * L + k] == f) kk = k;
+        cx->inj_face[j] = f;
+        cx->inj_k[j] = kk;
+        j++;
+    }
     return OR_OK;
 }
 
@@ -611,7 +632,9 @@ void oracle_destroy(oracle_ctx* cx)
                     cx->wall_face, cx->dt, cx->ratio, cx->W, cx->wret_prev, cx->tau, cx->xr_t, cx->emx, cx->Wp,
                     cx->Wh, cx->mnew, cx->co, cx->samp, cx->nhp, cx->hphys, cx->nhp_off, cx->wm, cx->wpl,
                     cx->wrt, cx->cross, cx->wallt, cx->frec_d, cx->flux, cx->chi_ema, cx->surf_sum,
-                    cx->surf_last, cx->p, cx->whq, cx->hq};
+                    cx->surf_last, cx->p, cx->whq, cx->hq, cx->fax, cx->fay, cx->fex, cx->fey,
+                    cx->inj_face, cx->inj_k, cx->inj_n, cx->inj_m, cx->inj_u, cx->inj_v, cx->inj_sig,
+                    cx->inj_D};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(cx);
 }
@@ -678,11 +701,12 @@ static void decompose(or_ctx* cx)
         double* Wp = cx->Wp + 4 * c;
         double* Wh = cx->Wh + 4 * c;
         const double tau = tau_of(cx, W);
-        /* W^p from the particles retained at the end of the previous step; W^h = W - W^p (Eq. 24) */
-        Wp[0] = ((double)r[0] * s0) / cx->vol[c];
-        Wp[1] = ((double)r[1] * s1) / cx->vol[c];
-        Wp[2] = cx->dim == 1 ? 0.0 : ((double)r[2] * s1) / cx->vol[c];
-        Wp[3] = ((double)r[4] * s4) / cx->vol[c];
+        /* W^p from the particles retained at the end of the previous step, the factor 1 / Omega_i of Eq. 30
+         * applied to the tally sums; W^h = W - W^p (Eq. 24) */
+        Wp[0] = ((double)r[0] * s0) * cx->inv_vol[c];
+        Wp[1] = ((double)r[1] * s1) * cx->inv_vol[c];
+        Wp[2] = cx->dim == 1 ? 0.0 : ((double)r[2] * s1) * cx->inv_vol[c];
+        Wp[3] = ((double)r[4] * s4) * cx->inv_vol[c];
         for (int k = 0; k < 4; ++k) Wh[k] = W[k] - Wp[k];
         const double x = cx->dt[c] / tau;
         const double e = or_expd(-x);
@@ -705,8 +729,8 @@ static void decompose(or_ctx* cx)
                 }
                 cx->nhp[c] = (int)q;
                 cx->mnew[c] = (rho_hp * cx->vol[c]) / q;
-                const double Uh = Wh[1] / Wh[0], Vh = Wh[2] / Wh[0];
-                const double RTh = (Wh[3] / Wh[0] - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
+                const double rh = 1.0 / Wh[0], Uh = Wh[1] * rh, Vh = Wh[2] * rh;
+                const double RTh = (Wh[3] * rh - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
                 cx->samp[3 * c] = Uh;
                 cx->samp[3 * c + 1] = Vh;
                 cx->samp[3 * c + 2] = RTh;
@@ -717,6 +741,51 @@ static void decompose(or_ctx* cx)
 }
 
 /* ---------------------------------------------------------------------------- a9: wave fluxes */
+
+/* Ghost state behind a far-field / fixed face (S19): the fixed state, or the freestream where it flows in
+ * (U_inf . n < 0, n outward from the fluid cell), else the fluid cell's own state (zero gradient). */
+static void ghost_state(const or_ctx* cx, int f, double Wg[4])
+{
+    const double* src;
+    if (cx->fbc[f] == OR_BC_FIXED) {
+        src = cx->W_fix;
+    } else {
+        const double un_inf = cx->W_inf[1] * cx->fnx[f] + cx->W_inf[2] * cx->fny[f];
+        src = un_inf < 0.0 ? cx->W_inf : cx->W + 4 * cx->fL[f];
+    }
+    for (int k = 0; k < 4; ++k) Wg[k] = src[k];
+}
+
+/* Ghost particle sources (reading; the paper is silent on boundaries): the virtual ghost cell behind a
+ * far-field / fixed face holds the ghost state with the fluid cell's time step dt_L; its collisionless part
+ * e^{-x}, x = dt_L / tau_g, is sampled as particles in a slab of depth D = (max(W_0, 0) + 6 sqrt(RT_g)) dt_L
+ * behind the face (W_0 the ghost's inflow speed), and those that reach the face within dt_L enter the fluid
+ * cell (Sec. III B: collisionless particles fly the whole step). Per face: N = ceil(M / m_ref) particles
+ * (at most 2047) of mass M / N, M = rho_g e^{-x} s D, m_ref = rho_g Omega_L / N_ref. FP64. */
+static void inject_params(or_ctx* cx)
+{
+    for (int j = 0; j < cx->n_inj; ++j) {
+        const int f = cx->inj_face[j], L = cx->fL[f];
+        double Wg[4];
+        ghost_state(cx, f, Wg);
+        const double rho = Wg[0], r = 1.0 / rho, U = Wg[1] * r, V = Wg[2] * r;
+        const double RT = (Wg[3] * r - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+        const double x = cx->dt[L] / tau_of(cx, Wg);
+        const double e = or_expd(-x);
+        const double sig = sqrt(RT);
+        const double W0 = -(U * cx->fnx[f] + V * cx->fny[f]);
+        const double D = ((W0 > 0.0 ? W0 : 0.0) + 6.0 * sig) * cx->dt[L];
+        const double M = ((rho * e) * cx->fs[f]) * D;
+        int n = 0;
+        if (!cx->wave_only && M > 0.0) {
+            const double q = ceil(M / ((rho * cx->vol[L]) / (double)cx->n_ref));
+            n = q > (double)OR_MAX_NEW ? OR_MAX_NEW : (q < 1.0 ? 1 : (int)q);
+        }
+        cx->inj_n[j] = n;
+        cx->inj_m[j] = n > 0 ? M / (double)n : 0.0;
+        cx->inj_u[j] = U; cx->inj_v[j] = V; cx->inj_sig[j] = sig; cx->inj_D[j] = D;
+    }
+}
 
 static void wave_fluxes(or_ctx* cx)
 {
@@ -743,20 +812,17 @@ static void wave_fluxes(or_ctx* cx)
             face_flux(WL, Wm, WhL, Whm, cx->hphys[L], cx->hphys[L], cL, cL, frL, frL, cx->fdL[f], cx->fdL[f],
                       cx->Pr, F, NULL, NULL, NULL, NULL);
         } else {
-            /* far-field / fixed ghost: pure wave, evaluated with the fluid cell's time step (Sec. IV B) */
+            /* far-field / fixed ghost: a virtual cell of the ghost state with the fluid cell's time step
+             * (Sec. IV B). Its collisionless part e^{-x} enters as particles (ghost sources, see the particle
+             * stage), so its wave free-transport weight is dbar_d - e^{-x}, as for an interior side; without
+             * particles (wave-only mode) the whole free-transport part stays in the wave */
             double Wg[4];
-            if (bc == OR_BC_FIXED) {
-                for (int k = 0; k < 4; ++k) Wg[k] = cx->W_fix[k];
-            } else {
-                const double un_inf = cx->W_inf[1] * nx + cx->W_inf[2] * ny;
-                const double* src = un_inf < 0.0 ? cx->W_inf : cx->W + 4 * L;
-                for (int k = 0; k < 4; ++k) Wg[k] = src[k];
-            }
+            ghost_state(cx, f, Wg);
             to_frame(Wg, nx, ny, WR);
             double cR[7];
             lts_coeffs(cx->dt[L], tau_of(cx, Wg), or_expd(-cx->dt[L] / tau_of(cx, Wg)), cR);
-            face_flux(WL, WR, WhL, WR, cx->hphys[L], 1, cL, cR, frL, cR[3], cx->fdL[f], cx->fdL[f], cx->Pr, F,
-                      NULL, NULL, NULL, NULL);
+            face_flux(WL, WR, WhL, WR, cx->hphys[L], 1, cL, cR, frL, cx->wave_only ? cR[3] : cR[5], cx->fdL[f],
+                      cx->fdL[f], cx->Pr, F, NULL, NULL, NULL, NULL);
         }
         /* non-finite flux (reading): extreme near-vacuum neighbours can make the interface density underflow
          * against its neighbours' and the slopes overflow; such a face carries no wave flux */
@@ -850,10 +916,11 @@ static int one_step(or_ctx* cx)
     memset(cx->wrt, 0, 5 * (size_t)C * 8);
     memset(cx->cross, 0, 2 * (size_t)cx->F * 8);
     memset(cx->wallt, 0, 3 * (size_t)cx->nwall * 8);
-    for (int k = 2; k < 10; ++k) cx->stats[k] = 0;
+    for (int k = 2; k < 11; ++k) cx->stats[k] = 0;
     /* step 1: decomposition and sampling; step 2: free transport and tallies (Sec. III C, Sec. IV B) */
     decompose(cx);
     if (cx->err) return cx->err;
+    inject_params(cx);
     if (cx->prec == 0) or_particles_step_f32(cx); else or_particles_step_f64(cx);
     /* step 3: wave fluxes from the step-start W and W^h, then the conservative update (Eq. 53) */
     wave_fluxes(cx);

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
+#include <string.h>
 #include "oracle.h"
 
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_ELIMIT = 4, OR_ENONPHYS = 5, OR_EOVERFLOW = 6 };
@@ -20,8 +21,8 @@ typedef struct {
     int32_t cell;
     uint64_t pid;
     /* per-step scratch */
-    double tf;
-    int32_t is_new, collide, alive, iters;
+    double tf;                   /* free-flight time; for a particle entering from a ghost, its time left */
+    int32_t is_new, collide, alive, iters, entry0;   /* entry0: local face it entered through, or -1 */
 } or_particle;
 
 struct oracle_ctx {
@@ -46,6 +47,11 @@ struct oracle_ctx {
     /* faces */
     int *fL, *fR, *fbc, *fwall;
     double *fnx, *fny, *fs, *fdL, *fdR, *finv_s;
+    double *fax, *fay, *fex, *fey;               /* face start vertex a and edge b - a (1-D: the face point) */
+    int n_inj;                                   /* far-field and fixed faces, in face order: ghost particle sources */
+    int *inj_face, *inj_k;                       /* their face ids and local index in the fluid cell */
+    int* inj_n;                                  /* per source: particles sampled this step */
+    double *inj_m, *inj_u, *inj_v, *inj_sig, *inj_D;   /* per source: mass, ghost U, V, sqrt(RT), slab depth */
     int nwall;
     int *wall_face;
     /* time steps */
@@ -76,8 +82,9 @@ struct oracle_ctx {
     double* chi_ema;
     double *surf_sum, *surf_last;
     int64_t nsurf;
-    int64_t stats[10];                           /* [8]: cells set to the vacuum floor in the last step,
-                                                  * [9]: A-R samplings that fell back to the Maxwellian */
+    int64_t stats[11];                           /* [8]: cells set to the vacuum floor in the last step,
+                                                  * [9]: A-R samplings that fell back to the Maxwellian,
+                                                  * [10]: particles entering from far-field / fixed ghosts */
     int err;
     char msg[256];
 };

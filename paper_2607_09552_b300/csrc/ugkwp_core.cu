@@ -142,6 +142,7 @@ __global__ void k_setup_faces(const MeshDev m, Dev d, double* fd)
     if (m.dim == 1) {
         const double* xs = m.xv;
         d.fnx[f] = 1.0; d.fny[f] = 0.0; d.fs[f] = 1.0;
+        d.fax[f] = xs[f]; d.fay[f] = 0.0; d.fex[f] = 0.0; d.fey[f] = 0.0;
         if (f == 0 && m.periodic_i) { d.fL[f] = ni - 1; d.fR[f] = 0; d.fbc[f] = UGKWP_BC_PERIODIC; fd[f] = xs[0]; }
         else if (f == 0) { d.fL[f] = 0; d.fR[f] = -1; d.fbc[f] = m.bc_imin[0]; d.fnx[f] = -1.0; fd[f] = -xs[0]; }
         else if (f == ni) { d.fL[f] = ni - 1; d.fR[f] = -1; d.fbc[f] = m.bc_imax[0]; fd[f] = xs[ni]; }
@@ -156,6 +157,7 @@ __global__ void k_setup_faces(const MeshDev m, Dev d, double* fd)
         a = vid(m, i, j);
         const int b = vid(m, i, j + 1);
         const double ex = m.xv[b] - m.xv[a], ey = m.yv[b] - m.yv[a];
+        d.fax[f] = m.xv[a]; d.fay[f] = m.yv[a]; d.fex[f] = ex; d.fey[f] = ey;
         len = sqrt(ex * ex + ey * ey);
         nx = ey / len; ny = -ex / len;
         if (i == 0) { nx = -nx; ny = -ny; d.fL[f] = i + ni * j; d.fR[f] = -1; d.fbc[f] = m.bc_imin[j]; }
@@ -166,6 +168,7 @@ __global__ void k_setup_faces(const MeshDev m, Dev d, double* fd)
         a = vid(m, i, j);
         const int b = vid(m, i + 1, j);
         const double ex = m.xv[b] - m.xv[a], ey = m.yv[b] - m.yv[a];
+        d.fax[f] = m.xv[a]; d.fay[f] = m.yv[a]; d.fex[f] = ex; d.fey[f] = ey;
         len = sqrt(ex * ex + ey * ey);
         nx = -ey / len; ny = ex / len;
         if (m.periodic_j) { d.fL[f] = i + ni * ((j + nj - 1) % nj); d.fR[f] = i + ni * j; d.fbc[f] = 0; }
@@ -306,9 +309,12 @@ __global__ void k_setup_tables(Dev d, int C, const int* cface, const int* csgn, 
     d.cf32[c] = a;
     d.cf64[c] = b;
     // faces of a wall cell apply their time integrals in FP64 in production mode
+    d.wallcell[c] = 0;
     for (int k = 0; k < d.nfc[c]; ++k)
-        if (cbc[4 * c + k] == UGKWP_BC_WALL)
+        if (cbc[4 * c + k] == UGKWP_BC_WALL) {
+            d.wallcell[c] = 1;
             for (int q = 0; q < d.nfc[c]; ++q) d.face_f64[cface[4 * c + q]] = 1;
+        }
     (void)prod;
 }
 
@@ -343,8 +349,9 @@ __device__ __forceinline__ bool realizable(const StepConsts& K, const double* W)
 // ------------------------------------------------------------------ a1: decomposition (Sec. IV B)
 __device__ __forceinline__ double tau_of(const StepConsts& K, const double* W)
 {
-    const double rho = W[0], U = W[1] / rho, V = W[2] / rho;
-    const double RT = (W[3] / rho - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+    // primitive variables through r = 1 / rho
+    const double rho = W[0], r = 1.0 / rho, U = W[1] * r, V = W[2] * r;
+    const double RT = (W[3] * r - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
     const double T = RT / kR;
     const double mu = K.mu_inf * dpow(T, K.omega);
     return mu / (rho * RT);
@@ -422,6 +429,42 @@ __device__ void shakhov_weights(const StepConsts& K, const Dev& d, int c, double
     d.hq32[3 * c] = (float)ax; d.hq32[3 * c + 1] = (float)ay; d.hq32[3 * c + 2] = (float)M;
 }
 
+// The same coefficients in FP32 (12 Taylor terms for x < 1, below FP32 resolution), for cells whose faces
+// evaluate their fluxes in FP32 in production mode; the faces of wall cells keep the FP64 time integrals
+constexpr int kSeries32 = 12;
+__constant__ float c_series32[6][kSeries32];
+__device__ void lts_coeffs_f32(float dt, float x, float e, double* out)
+{
+    float phi1, psi2, psi3, chi, beta, kappa;
+    if (x < 1.0f) {
+        const float mx = -x;
+        phi1 = psi2 = psi3 = chi = beta = kappa = 0.0f;
+#pragma unroll
+        for (int k = kSeries32 - 1; k >= 0; --k) {
+            phi1 = fmaf(mx, phi1, c_series32[0][k]);
+            psi2 = fmaf(mx, psi2, c_series32[1][k]);
+            psi3 = fmaf(mx, psi3, c_series32[2][k]);
+            chi = fmaf(mx, chi, c_series32[3][k]);
+            beta = fmaf(mx, beta, c_series32[4][k]);
+            kappa = fmaf(mx, kappa, c_series32[5][k]);
+        }
+    } else {
+        phi1 = (1.0f - e) / x;
+        psi2 = (e - 1.0f + x) / (x * x);
+        psi3 = (0.5f * x * x - x + 1.0f - e) / (x * x * x);
+        chi = (phi1 - e) / x;
+        beta = (1.0f + e - 2.0f * phi1) / (x * x);
+        kappa = (chi - 0.5f * e) / x;
+    }
+    out[0] = x * psi2;
+    out[1] = -dt * x * beta;
+    out[2] = dt * x * psi3;
+    out[3] = phi1;
+    out[4] = -dt * chi;
+    out[5] = x * chi;
+    out[6] = -dt * x * kappa;
+}
+
 __global__ void k_decompose(const StepConsts K, Dev d)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -432,10 +475,12 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     const double s0 = ldexp(1.0, -K.fx0), s1 = ldexp(1.0, -K.fx1), s4 = ldexp(1.0, -K.fx4);
     const double tau = tau_of(K, W);
     double Wp[4], Wh[4];
-    Wp[0] = ((double)r[0] * s0) / vol;
-    Wp[1] = ((double)r[1] * s1) / vol;
-    Wp[2] = K.dim == 1 ? 0.0 : ((double)r[2] * s1) / vol;
-    Wp[3] = ((double)r[4] * s4) / vol;
+    // the factor 1 / Omega_i of Eq. 30 applied to the tally sums
+    const double rvol = d.rcp[2 * c];
+    Wp[0] = ((double)r[0] * s0) * rvol;
+    Wp[1] = ((double)r[1] * s1) * rvol;
+    Wp[2] = K.dim == 1 ? 0.0 : ((double)r[2] * s1) * rvol;
+    Wp[3] = ((double)r[4] * s4) * rvol;
     // W^{p,-} of the retained particles is exactly the retained tally of the previous step (same particles,
     // masses, velocities and cell); k_sample adds the new particles. W^{p,+} starts from the same value
     // (every particle unchanged) and k_particles adds the changes; the retained tally of this step is
@@ -450,7 +495,8 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     d.tau[c] = tau;
     d.xr[c] = x;
     d.emx[c] = e;
-    lts_coeffs(dt, tau, e, d.co + 7 * c);
+    if (K.prec == 0 && !d.wallcell[c]) lts_coeffs_f32((float)dt, (float)x, (float)e, d.co + 7 * c);
+    else lts_coeffs(dt, tau, e, d.co + 7 * c);
     const int phys = realizable(K, Wh);
     d.hphys[c] = phys;
     int n = 0;
@@ -465,9 +511,10 @@ __global__ void k_decompose(const StepConsts K, Dev d)
             } else {
                 n = (int)q;
                 m = (rho_hp * vol) / q;
-                Uh = Wh[1] / Wh[0];
-                Vh = Wh[2] / Wh[0];
-                RTh = (Wh[3] / Wh[0] - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
+                const double rh = 1.0 / Wh[0];
+                Uh = Wh[1] * rh;
+                Vh = Wh[2] * rh;
+                RTh = (Wh[3] * rh - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
             }
         }
     }
@@ -497,6 +544,9 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
         d.stats[12] = 0;
         d.counts[2] = 0;
         d.counts[5] = 0;
+        d.counts[6] = 0;
+        d.counts[7] = 0;
+        d.stats[13] = 0;
         *d.nretry = 0;
         *d.done = 0u;
         d.flags[0] = (int)(*d.dstep % K.sort_every == (long long)(K.sort_every - 1));
@@ -594,35 +644,41 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 }
 
 // ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
-// One warp per cell. Velocities: Box-Muller normals shifted and scaled so that the cell's new particles
-// carry exactly the momentum and energy of W^hp (sums in index order, accumulated by lane 0).
+// Eight lanes per cell (four cells per warp; a cell samples about three particles per step on the bench
+// workload). Velocities: Box-Muller normals (Pr = 1) or Shakhov acceptance-rejection (Pr != 1), shifted and
+// scaled so that the cell's new particles carry exactly the momentum and energy of W^hp. Sums in a fixed
+// order: lane j of the cell's eight adds k = j, j + 8, ... in increasing k, then a butterfly combines the
+// lanes (j + 4 into j, j + 2 into j, j + 1 into j; every lane of the group ends with the same value).
+constexpr int kSampleGroup = 8;
 template <typename T>
 __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
                                                 ParticleSoA<T> PB, PCell<T> pc, const long long* dstep)
 {
     const ParticleSoA<T> A = *d.bufsel ? PB : PA;   // the buffer holding this step's particles
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= K.C) return;
-    const int c = warp;
-    const int N = d.nhp[c];
-    if (N == 0 || d.counts[1] == 0) return;
-    const int nret = d.counts[0];
-    const long long base_i = (long long)nret + d.nhp_off[c];
-    const int cap_left = d.counts[3] - nret;
-    if (d.nhp_off[c] + N > cap_left) {
-        if (lane == 0) atomicOr(d.err, ERR_CAPACITY);
-        return;
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) / kSampleGroup;
+    const int l = threadIdx.x & (kSampleGroup - 1);
+    int N = 0;
+    long long base_i = 0;
+    if (c < K.C && d.counts[1] != 0) {
+        N = d.nhp[c];
+        const int nret = d.counts[0];
+        base_i = (long long)nret + d.nhp_off[c];
+        const int cap_left = d.counts[3] - nret;
+        if (N > 0 && d.nhp_off[c] + N > cap_left) {
+            if (l == 0) atomicOr(d.err, ERR_CAPACITY);
+            N = 0;
+        }
     }
+    // every lane of the warp takes part in the shuffles below; cells without particles add zeros
+    if (!__any_sync(0xffffffffu, N > 0)) return;
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
-    const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)c << 11);
-    // sums in a fixed order: lane j adds k = j, j + 32, ... in increasing k, then a butterfly combines the
-    // lanes (j + 16 into j, j + 8 into j, ...; every lane ends with the same value)
+    const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)(c < K.C ? c : 0) << 11);
     T su = 0, sv = 0, sw = 0;
     int fallbacks = 0;
-    const T ax = K.shakhov ? pc.q_(c, 0) : T(0), ay = K.shakhov ? pc.q_(c, 1) : T(0);
-    const T M = K.shakhov ? pc.q_(c, 2) : T(1);
-    for (int k = lane; k < N; k += 32) {
+    const bool shk = K.shakhov && N > 0;
+    const T ax = shk ? pc.q_(c, 0) : T(0), ay = shk ? pc.q_(c, 1) : T(0);
+    const T M = shk ? pc.q_(c, 2) : T(1);
+    for (int k = l; k < N; k += kSampleGroup) {
         // Pr = 1: Box-Muller of the Maxwellian of W^h. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-
         // rejection (Sec. III B): Maxwellian proposals accepted with probability (1 + psi) / M,
         // psi = (a . z)(|z|^2 - 5), |z| > 6 rejected; after kArAttempts rejections the last proposal stays
@@ -653,74 +709,165 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
     }
     if (K.shakhov) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
-        if (lane == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
+        for (int o = kSampleGroup / 2; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+        if (l == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = kSampleGroup / 2; o > 0; o >>= 1) {
         su = su + __shfl_xor_sync(0xffffffffu, su, o);
         sv = sv + __shfl_xor_sync(0xffffffffu, sv, o);
         sw = sw + __shfl_xor_sync(0xffffffffu, sw, o);
     }
-    const T inv = T(1) / T(N);
+    const T inv = N > 0 ? T(1) / T(N) : T(0);
     const T mu = su * inv, mv = sv * inv, mw = sw * inv;
     T ss = 0;
-    for (int k = lane; k < N; k += 32) {
+    for (int k = l; k < N; k += kSampleGroup) {
         const T du = A.u[base_i + k] - mu, dv = A.v[base_i + k] - mv, dw = A.w[base_i + k] - mw;
         ss += (du * du + dv * dv) + dw * dw;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
-    const T Uh = pc.s_(c, 0), Vh = pc.s_(c, 1), RTh = pc.s_(c, 2);
-    const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTh) / ss) : T(0);
-    const T m = pc.m_(c);
-    const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+    for (int o = kSampleGroup / 2; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
     long long acc[5] = {0, 0, 0, 0, 0};
-    for (int k = lane; k < N; k += 32) {
-        const uint64_t pid = pbase | (uint64_t)k;
-        const long long i = base_i + k;
-        T U[3], x, y;
-        Unif<T>::get(g, pid, DRAW_POS, 3, U);
-        if (K.dim == 1) {
-            const T xa = T(d.cvx[4 * c]), xb = T(d.cvx[4 * c + 1]);
-            x = xa + U[0] * (xb - xa);
-            y = T(0);
-        } else {
-            T X[4], Y[4];
+    if (N > 0) {
+        const T Uh = pc.s_(c, 0), Vh = pc.s_(c, 1), RTh = pc.s_(c, 2);
+        const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTh) / ss) : T(0);
+        const T m = pc.m_(c);
+        const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+        // the cell's vertices in the particle precision and its two triangles' areas (same for every particle)
+        T X[4], Y[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { X[q] = T(d.cvx[4 * c + q]); Y[q] = T(d.cvy[4 * c + q]); }
-            const T A1 = T(0.5) * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
-            const T A2 = T(0.5) * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
-            const bool first = U[0] * (A1 + A2) < A1;
-            const int bi = first ? 1 : 2, ci = first ? 2 : 3;
-            const T sq = fsqrt_(U[1]);
-            const T wa = T(1) - sq, wb = sq * (T(1) - U[2]), wc = sq * U[2];
-            x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
-            y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
+        for (int q = 0; q < 4; ++q) {
+            X[q] = T(d.cvx[4 * c + q]);
+            Y[q] = K.dim == 1 ? T(0) : T(d.cvy[4 * c + q]);
         }
-        const T z0 = A.u[i], z1 = A.v[i], z2 = A.w[i];
-        const T un = Uh + sc * (z0 - mu), vn = Vh + sc * (z1 - mv), wn = sc * (z2 - mw);
-        A.x[i] = x; A.y[i] = y;
-        A.u[i] = un;
-        A.v[i] = vn;
-        A.w[i] = wn;
-        A.m[i] = m;
-        A.cell[i] = c;
-        A.pid[i] = pid;
-        long long f[5];
-        fix5(m, un, vn, wn, s0, s1, s4, d.err, f);
+        const T A1 = T(0.5) * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+        const T A2 = T(0.5) * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+        const T A12 = A1 + A2;
+        for (int k = l; k < N; k += kSampleGroup) {
+            const uint64_t pid = pbase | (uint64_t)k;
+            const long long i = base_i + k;
+            T U[3], x, y;
+            Unif<T>::get(g, pid, DRAW_POS, 3, U);
+            if (K.dim == 1) {
+                x = X[0] + U[0] * (X[1] - X[0]);
+                y = T(0);
+            } else {
+                const bool first = U[0] * A12 < A1;
+                const int bi = first ? 1 : 2, ci = first ? 2 : 3;
+                const T sq = fsqrt_(U[1]);
+                const T wa = T(1) - sq, wb = sq * (T(1) - U[2]), wc = sq * U[2];
+                x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
+                y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
+            }
+            const T z0 = A.u[i], z1 = A.v[i], z2 = A.w[i];
+            const T un = Uh + sc * (z0 - mu), vn = Vh + sc * (z1 - mv), wn = sc * (z2 - mw);
+            A.x[i] = x; A.y[i] = y;
+            A.u[i] = un;
+            A.v[i] = vn;
+            A.w[i] = wn;
+            A.m[i] = m;
+            A.cell[i] = c;
+            A.pid[i] = pid;
+            long long f[5];
+            fix5(m, un, vn, wn, s0, s1, s4, d.err, f);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) acc[q] += f[q];
+            for (int q = 0; q < 5; ++q) acc[q] += f[q];
+        }
     }
-    // W^{p,-} of the new particles: this warp owns the cell, so a butterfly sum and one plain update
+    // W^{p,-} of the new particles: this group owns the cell, so a butterfly sum and one update (atomic for
+    // W^{p,+}: the ghost sources on the second stream may add to the same cell meanwhile)
 #pragma unroll
     for (int q = 0; q < 5; ++q)
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    if (lane == 0)
+        for (int o = kSampleGroup / 2; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (l == 0 && N > 0)
         for (int q = 0; q < 5; ++q) {
             d.wm[5 * c + q] += acc[q];
-            d.wpl[5 * c + q] += acc[q];
+            atomicAdd(reinterpret_cast<unsigned long long*>(d.wpl) + 5 * (size_t)c + q, (unsigned long long)acc[q]);
         }
+}
+
+// Free flight of one particle for the time tr left from cell c (the face `entry` excluded from the first exit
+// test: the face it came in through, or -1): exit time through the cell's faces; at a crossing L -> R the
+// mass and the remaining time scale by dt_R / dt_L (Eqs. 41, 52); diffuse re-emission at walls (wall tallies),
+// specular mirrors, deletion at far-field and fixed ghosts. Returns alive; c is the final cell, it the number
+// of face events.
+template <typename T>
+__device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict__ cf, const Rng& g, T s1, T s4,
+                                    T m2RTw, T sigw, T& x, T& y, T& u, T& v, T& w, T& m, T tr, int& c, int entry,
+                                    uint64_t pid, int& it, unsigned long long& n_cross, unsigned long long& n_hits)
+{
+    int hits = 0;
+    it = 0;
+    bool alive = true;
+    for (;;) {
+        const CellFaces<T>& F = cf[c];
+        const int nf = d.nfc[c];
+        int kb = -1;
+        T best = T(0);
+        for (int k = 0; k < nf; ++k) {
+            if (k == entry) continue;
+            const T un = F.nx[k] * u + F.ny[k] * v;
+            if (!(un > T(0))) continue;
+            T t = (F.d[k] - (F.nx[k] * x + F.ny[k] * y)) / un;
+            if (t < T(0)) t = T(0);
+            if (kb < 0 || t < best) { best = t; kb = k; }
+        }
+        if (kb < 0 || tr <= best) {
+            x = x + u * tr;
+            y = y + v * tr;
+            break;
+        }
+        x = x + u * best;
+        y = y + v * best;
+        tr = tr - best;
+        if (++it > kMaxIters) { atomicOr(d.err, ERR_LIMIT); break; }
+        const int meta = F.meta[kb];
+        const int bc = (meta >> 26) & 7;
+        const int nb = F.nbr[kb];
+        if (nb >= 0) {
+            const int f = meta & 0xffffff, dir = ((meta >> 29) & 1) ? 0 : 1;
+            atomicAdd(d.cross + 2 * f + dir, 1u);
+            n_cross++;
+            const T r = F.ratio[kb];
+            m = m * r;
+            tr = tr * r;
+            if (bc == UGKWP_BC_PERIODIC) x = x + T(d.cshift[4 * c + kb]);
+            entry = (meta >> 24) & 3;
+            c = nb;
+        } else if (bc == UGKWP_BC_WALL) {
+            T U[3];
+            Unif<T>::get(g, pid, draw_wall(hits), 3, U);
+            const T nx = F.nx[kb], ny = F.ny[kb];
+            const T un = fsqrt_(m2RTw * dlog(U[0]));
+            const T rad = fsqrt_(T(-2) * dlog(U[1]));
+            T sn, cs;
+            dsincos2pi(U[2], &sn, &cs);
+            const T vt = sigw * (rad * cs), wz = sigw * (rad * sn);
+            const T tx = -ny, ty = nx;
+            const T uo = vt * tx - un * nx, vo = vt * ty - un * ny;
+            const int iw = d.fwall[meta & 0xffffff];
+            const T ein = T(0.5) * ((u * u + v * v) + w * w);
+            const T eout = T(0.5) * ((uo * uo + vo * vo) + wz * wz);
+            unsigned long long* wa = reinterpret_cast<unsigned long long*>(d.wallt + 3 * (size_t)iw);
+            atomicAdd(wa + 0, (unsigned long long)fixp(m * (u - uo), s1, d.err));
+            atomicAdd(wa + 1, (unsigned long long)fixp(m * (v - vo), s1, d.err));
+            atomicAdd(wa + 2, (unsigned long long)fixp(m * (ein - eout), s4, d.err));
+            u = uo; v = vo; w = wz;
+            entry = kb;
+            hits++;
+            n_hits++;
+        } else if (bc == UGKWP_BC_SYMMETRY) {
+            const T un = F.nx[kb] * u + F.ny[kb] * v;
+            const T t2 = T(2) * un;
+            u = u - t2 * F.nx[kb];
+            v = v - t2 * F.ny[kb];
+            entry = kb;
+        } else {
+            alive = false;
+            break;
+        }
+    }
+    return alive;
 }
 
 // ------------------------------------------------- a3-a6: free flight, transport and tallies
@@ -791,76 +938,9 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
                 collide = a < dtc;
                 tr = collide ? a : dtc;
             }
-            int entry = -1, hits = 0, it = 0;
-            bool alive = true;
-            for (;;) {
-                const CellFaces<T>& F = cf[c];
-                const int nf = d.nfc[c];
-                int kb = -1;
-                T best = T(0);
-                for (int k = 0; k < nf; ++k) {
-                    if (k == entry) continue;
-                    const T un = F.nx[k] * u + F.ny[k] * v;
-                    if (!(un > T(0))) continue;
-                    T t = (F.d[k] - (F.nx[k] * x + F.ny[k] * y)) / un;
-                    if (t < T(0)) t = T(0);
-                    if (kb < 0 || t < best) { best = t; kb = k; }
-                }
-                if (kb < 0 || tr <= best) {
-                    x = x + u * tr;
-                    y = y + v * tr;
-                    break;
-                }
-                x = x + u * best;
-                y = y + v * best;
-                tr = tr - best;
-                if (++it > kMaxIters) { atomicOr(d.err, ERR_LIMIT); break; }
-                const int meta = F.meta[kb];
-                const int bc = (meta >> 26) & 7;
-                const int nb = F.nbr[kb];
-                if (nb >= 0) {
-                    const int f = meta & 0xffffff, dir = ((meta >> 29) & 1) ? 0 : 1;
-                    atomicAdd(d.cross + 2 * f + dir, 1u);
-                    n_cross++;
-                    const T r = F.ratio[kb];
-                    m = m * r;
-                    tr = tr * r;
-                    if (bc == UGKWP_BC_PERIODIC) x = x + T(d.cshift[4 * c + kb]);
-                    entry = (meta >> 24) & 3;
-                    c = nb;
-                } else if (bc == UGKWP_BC_WALL) {
-                    T U[3];
-                    Unif<T>::get(g, pid, draw_wall(hits), 3, U);
-                    const T nx = F.nx[kb], ny = F.ny[kb];
-                    const T un = fsqrt_(m2RTw * dlog(U[0]));
-                    const T rad = fsqrt_(T(-2) * dlog(U[1]));
-                    T sn, cs;
-                    dsincos2pi(U[2], &sn, &cs);
-                    const T vt = sigw * (rad * cs), wz = sigw * (rad * sn);
-                    const T tx = -ny, ty = nx;
-                    const T uo = vt * tx - un * nx, vo = vt * ty - un * ny;
-                    const int iw = d.fwall[meta & 0xffffff];
-                    const T ein = T(0.5) * ((u * u + v * v) + w * w);
-                    const T eout = T(0.5) * ((uo * uo + vo * vo) + wz * wz);
-                    unsigned long long* wa = reinterpret_cast<unsigned long long*>(d.wallt + 3 * (size_t)iw);
-                    atomicAdd(wa + 0, (unsigned long long)fixp(m * (u - uo), s1, d.err));
-                    atomicAdd(wa + 1, (unsigned long long)fixp(m * (v - vo), s1, d.err));
-                    atomicAdd(wa + 2, (unsigned long long)fixp(m * (ein - eout), s4, d.err));
-                    u = uo; v = vo; w = wz;
-                    entry = kb;
-                    hits++;
-                    n_hits++;
-                } else if (bc == UGKWP_BC_SYMMETRY) {
-                    const T un = F.nx[kb] * u + F.ny[kb] * v;
-                    const T t2 = T(2) * un;
-                    u = u - t2 * F.nx[kb];
-                    v = v - t2 * F.ny[kb];
-                    entry = kb;
-                } else {
-                    alive = false;
-                    break;
-                }
-            }
+            int it = 0;
+            const bool alive = fly(d, cf, g, s1, s4, m2RTw, sigw, x, y, u, v, w, m, tr, c, -1, pid, it,
+                                   n_cross, n_hits);
             max_it = max(max_it, it);
             if (alive) {
                 end_cell = c;
@@ -942,6 +1022,149 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
     }
 }
 
+// ------------------------------------------------ ghost particle sources (far-field and fixed faces)
+// The virtual ghost cell behind a far-field / fixed face holds the ghost state with the fluid cell's time step
+// dt_L; its collisionless part e^{-x}, x = dt_L / tau_g, is sampled as particles in a slab of depth
+// D = (max(W_0, 0) + 6 sqrt(RT_g)) dt_L behind the face (W_0 the ghost's inflow speed); those that reach the
+// face within dt_L enter the fluid cell at a uniform point of the face and fly, collisionless, for the rest
+// of the step. Per source: N = ceil(M / m_ref) particles (at most kMaxNew) of mass M / N, M = rho_g e^{-x} s D,
+// m_ref = rho_g Omega_L / N_ref; the ghost's wave free-transport weight is then dbar_d - e^{-x}.
+
+// per source, FP64 (one thread each): ghost state, sample count, mass, ghost velocity, sqrt(RT), slab depth
+__global__ void k_inject_params(const StepConsts K, Dev d)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K.n_inj) return;
+    const int f = d.inj_face[j], L = d.fL[f];
+    const double* Wg;
+    if (d.fbc[f] == UGKWP_BC_FIXED) {
+        Wg = K.W_fix;
+    } else {
+        const double un_inf = K.W_inf[1] * d.fnx[f] + K.W_inf[2] * d.fny[f];
+        Wg = un_inf < 0.0 ? K.W_inf : d.W + 4 * L;
+    }
+    const double rho = Wg[0], r = 1.0 / rho, U = Wg[1] * r, V = Wg[2] * r;
+    const double RT = (Wg[3] * r - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+    const double x = d.dt[L] / tau_of(K, Wg);
+    const double e = dexp(-x);
+    const double sig = sqrt(RT);
+    const double W0 = -(U * d.fnx[f] + V * d.fny[f]);
+    const double D = ((W0 > 0.0 ? W0 : 0.0) + 6.0 * sig) * d.dt[L];
+    const double M = ((rho * e) * d.fs[f]) * D;
+    int n = 0;
+    if (M > 0.0) {
+        const double q = ceil(M / ((rho * d.vol[L]) / (double)K.n_ref));
+        n = q > (double)kMaxNew ? kMaxNew : (q < 1.0 ? 1 : (int)q);
+    }
+    d.inj_n[j] = n;
+    double* P = d.inj_par + 5 * j;
+    P[0] = n > 0 ? M / (double)n : 0.0;
+    P[1] = U; P[2] = V; P[3] = sig; P[4] = D;
+}
+
+// one warp per source: sample, enter, fly, tally W^{p,+}, write the survivors like the transport kernel
+template <typename T>
+__global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB,
+                                                const CellFaces<T>* __restrict__ cf, const long long* dstep)
+{
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= K.n_inj) return;
+    const int N = d.inj_n[j];
+    if (N == 0) return;
+    const int sel = *d.bufsel;
+    const ParticleSoA<T> B = sel ? PA : PB;   // where the transport kernel writes this step's survivors
+    const bool sort_step = d.flags[0] != 0;
+    const int n = d.counts[4], cap = d.counts[3];
+    const int f = d.inj_face[j], L = d.fL[f], kin = d.inj_k[j];
+    const Rng g{K.k0, K.k1, (uint32_t)*dstep};
+    const uint64_t base = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)(K.C + j) << 11);
+    const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+    const T m2RTw = T(K.m2RTw), sigw = T(K.sig_w);
+    const T nx = T(d.fnx[f]), ny = T(d.fny[f]);
+    const double* P = d.inj_par + 5 * j;
+    const T m0 = T(P[0]), Ug = T(P[1]), Vg = T(P[2]), sig = T(P[3]), D = T(P[4]);
+    const T dtL = T(d.dt[L]);
+    const T ax = T(d.fax[f]), ay = T(d.fay[f]), ex = T(d.fex[f]), ey = T(d.fey[f]);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned long long n_cross = 0, n_hits = 0, n_left = 0, n_in = 0;
+    int max_it = 0;
+    unsigned long long* pl = reinterpret_cast<unsigned long long*>(d.wpl);
+    for (int k0 = 0; k0 < N; k0 += 32) {
+        const int k = k0 + lane;
+        bool kept = false;
+        int c = L;
+        T x = 0, y = 0, u = 0, v = 0, w = 0, m = m0;
+        const uint64_t pid = base | (uint64_t)k;
+        if (k < N) {
+            T Up[3], Uv[4];
+            Unif<T>::get(g, pid, DRAW_POS, 3, Up);
+            Unif<T>::get(g, pid, DRAW_VEL, 4, Uv);
+            const T r0 = fsqrt_(T(-2) * dlog(Uv[0]));
+            T sn0, cs0, sn1, cs1;
+            dsincos2pi(Uv[1], &sn0, &cs0);
+            const T r1 = fsqrt_(T(-2) * dlog(Uv[2]));
+            dsincos2pi(Uv[3], &sn1, &cs1);
+            u = Ug + sig * (r0 * cs0);
+            v = Vg + sig * (r0 * sn0);
+            w = sig * (r1 * cs1);
+            const T un = nx * u + ny * v;
+            if (un < T(0)) {
+                const T tc = (Up[0] * D) / (-un);
+                if (tc < dtL) {
+                    n_in++;
+                    x = ax + Up[1] * ex;
+                    y = ay + Up[1] * ey;
+                    int it = 0;
+                    const bool alive = fly(d, cf, g, s1, s4, m2RTw, sigw, x, y, u, v, w, m, dtL - tc, c, kin, pid, it,
+                                           n_cross, n_hits);
+                    max_it = max(max_it, it);
+                    if (alive) {
+                        kept = true;
+                        long long fq[5];
+                        fix5(m, u, v, w, s0, s1, s4, d.err, fq);
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) atomicAdd(pl + 5 * (size_t)c + q, (unsigned long long)fq[q]);
+                    } else {
+                        n_left++;
+                    }
+                }
+            }
+        }
+        // survivors, as in the transport kernel (slots beyond the capacity are an error)
+        const unsigned km = __ballot_sync(0xffffffffu, kept);
+        if (!km) continue;
+        int slot0 = 0;
+        if (lane == 0) slot0 = sort_step ? atomicAdd(d.counts + 7, __popc(km)) : atomicAdd(d.counts + 2, __popc(km));
+        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+        if (kept) {
+            const int jj = (sort_step ? n : 0) + slot0 + __popc(km & lt_mask);
+            if (jj >= cap) {
+                atomicOr(d.err, ERR_CAPACITY);
+            } else {
+                B.x[jj] = x; B.y[jj] = y; B.u[jj] = u; B.v[jj] = v; B.w[jj] = w; B.m[jj] = m;
+                B.cell[jj] = c;
+                B.pid[jj] = pid;
+                if (sort_step) atomicAdd(d.cnt + c, 1);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
+        n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
+        n_left += __shfl_xor_sync(0xffffffffu, n_left, o);
+        n_in += __shfl_xor_sync(0xffffffffu, n_in, o);
+        max_it = max(max_it, __shfl_xor_sync(0xffffffffu, max_it, o));
+    }
+    if (lane == 0) {
+        if (n_left) atomicAdd(d.stats + 4, n_left);
+        if (n_cross) atomicAdd(d.stats + 5, n_cross);
+        if (n_hits) atomicAdd(d.stats + 6, n_hits);
+        if (max_it) atomicMax(d.stats + 7, (unsigned long long)max_it);
+        if (n_in) { atomicAdd(d.stats + 13, n_in); atomicAdd(d.counts + 6, (int)n_in); }
+    }
+}
+
 // --------------------------------------------------------------------- a7: counting sort
 // sort steps only: counting sort of the survivors by cell, from the staging buffer back into the buffer that
 // held this step's particles (which then stays the current one)
@@ -951,7 +1174,7 @@ __global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA,
     if (!d.flags[0]) return;
     const int sel = *d.bufsel;
     const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
-    const int n = d.counts[4];
+    const int n = d.counts[4] + d.counts[7];   // the step's particles, then those that entered from ghosts
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int c = B.cell[i];
         if (c < 0) continue;
@@ -965,7 +1188,8 @@ __global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA,
 // Threads [0, C): conservative update of one cell, residual term, particle-mass-ratio EMA, vacuum floor.
 // Threads [C, C + n_wall): wall pressure, shear stress and heat flux of one wall face (a11, Sec. V A).
 // The last block to finish reduces the residual partials in block order and closes the step.
-__global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long long* dstep)
+constexpr int kUpdateBlock = 256;
+__global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev d, long long* dstep)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     double r2[4] = {0, 0, 0, 0};
@@ -1028,11 +1252,11 @@ __global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long 
         d.surf_sum[3 * iw] += p; d.surf_sum[3 * iw + 1] += tw; d.surf_sum[3 * iw + 2] += q;
     }
     // residual partial sums in a fixed tree order
-    __shared__ double sm[4][256];
+    __shared__ double sm[4][kUpdateBlock];
     __shared__ bool last;
     for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = r2[q];
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
+    for (int s = kUpdateBlock / 2; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s)
             for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
         __syncthreads();
@@ -1060,7 +1284,7 @@ __global__ void __launch_bounds__(256) k_update(const StepConsts K, Dev d, long 
     d.stats[1] = (unsigned long long)kept;
     d.stats[2] = (unsigned long long)d.counts[1];
     d.stats[8] += 1;  // surface samples
-    d.stats[9] += (unsigned long long)d.counts[4];
+    d.stats[9] += (unsigned long long)(d.counts[4] + d.counts[6]);
     d.stats[10] += (unsigned long long)d.counts[1];
 }
 
@@ -1186,28 +1410,37 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     cudaEventRecord(ctx.ev_fork, s);
     cudaStreamWaitEvent(s2, ctx.ev_fork, 0);
     mark(6, s2);
+    // ghost particle sources on the second stream too: they touch only the survivor slots and tallies that the
+    // transport kernel updates atomically (their sort-step slots lie past the step's particles), and they join
+    // before the sort and the update
+    if (K.n_inj > 0 && !K.wave_only) {
+        k_inject_params<<<nblk(K.n_inj, 128), 128, 0, s2>>>(K, d);
+        if (K.prec == 0) k_inject<float><<<nblk(32LL * K.n_inj, 128), 128, 0, s2>>>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
+        else k_inject<double><<<nblk(32LL * K.n_inj, 128), 128, 0, s2>>>(K, d, d.pa64, d.pb64, d.cf64, d.dstep);
+    }
     launch_wave_flux(K, d, ctx.sms, s2);
     mark(7, s2);
     cudaEventRecord(ctx.ev_join, s2);
     PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32, d.hq32};
     PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp, d.hq};
     mark(2, s);
-    if (K.prec == 0) k_sample<float><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
-    else k_sample<double><<<nblk((long long)C * 32, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
+    if (K.prec == 0) k_sample<float><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
+    else k_sample<double><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
     mark(3, s);
     mark(4, s);
     if (K.prec == 0) k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
     else k_particles<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64, d.cf64, pc64, d.dstep);
     mark(5, s);
     mark(8, s);
-    // counting sort every sort_every-th step (kernels return at once on the other steps)
+    // counting sort every sort_every-th step (kernels return at once on the other steps), after the ghost
+    // sources on the second stream have added their survivors
+    cudaStreamWaitEvent(s, ctx.ev_join, 0);
     exclusive_scan(d.cnt, d.off, d.scan_tmp, C, d.counts + 2, s, nullptr, nullptr, d.flags);
     if (K.prec == 0) k_scatter<float><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa32, d.pb32);
     else k_scatter<double><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa64, d.pb64);
     mark(9, s);
-    cudaStreamWaitEvent(s, ctx.ev_join, 0);
     mark(10, s);
-    k_update<<<ctx.res_blocks, 256, 0, s>>>(K, d, d.dstep);
+    k_update<<<ctx.res_blocks, kUpdateBlock, 0, s>>>(K, d, d.dstep);
     mark(11, s);
     if (prof)
         for (int q = 0; q < 2 * kStages; ++q) ctx.prof_events.push_back(ev[q]);
@@ -1318,12 +1551,13 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
             CK(cudaMemcpyAsync(bcjh, mesh->bc_jmax, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
         }
         MeshDev m{ni, nj, mesh->dim, mesh->periodic_j, periodic_i, F, xv, yv, bci, bco, bcjl, bcjh};
-        CK(dalloc(ctx, &d.vol, C)); CK(dalloc(ctx, &d.rcp, 2 * C)); CK(dalloc(ctx, &d.xc, C)); CK(dalloc(ctx, &d.yc, C)); CK(dalloc(ctx, &d.dt, C));
+        CK(dalloc(ctx, &d.vol, C)); CK(dalloc(ctx, &d.rcp, 2 * C)); CK(dalloc(ctx, &d.wallcell, C)); CK(dalloc(ctx, &d.xc, C)); CK(dalloc(ctx, &d.yc, C)); CK(dalloc(ctx, &d.dt, C));
         CK(dalloc(ctx, &d.nfc, C)); CK(dalloc(ctx, &d.cf32, C)); CK(dalloc(ctx, &d.cf64, C));
         CK(dalloc(ctx, &d.cshift, 4 * C)); CK(dalloc(ctx, &d.cvx, 4 * C)); CK(dalloc(ctx, &d.cvy, 4 * C));
         CK(dalloc(ctx, &d.fL, F)); CK(dalloc(ctx, &d.fR, F)); CK(dalloc(ctx, &d.fbc, F)); CK(dalloc(ctx, &d.fwall, F));
         CK(dalloc(ctx, &d.fnx, F)); CK(dalloc(ctx, &d.fny, F)); CK(dalloc(ctx, &d.fs, F));
         CK(dalloc(ctx, &d.fdL, F)); CK(dalloc(ctx, &d.fdR, F)); CK(dalloc(ctx, &d.face_f64, F));
+        CK(dalloc(ctx, &d.fax, F)); CK(dalloc(ctx, &d.fay, F)); CK(dalloc(ctx, &d.fex, F)); CK(dalloc(ctx, &d.fey, F));
         double *fd, *cnx, *cny, *cd, *dtpart;
         int *cface, *csgn, *cnbr, *cnk, *cbc, *flag, *widx;
         CK(dalloc(ctx, &fd, F)); CK(dalloc(ctx, &cnx, 4 * C)); CK(dalloc(ctx, &cny, 4 * C)); CK(dalloc(ctx, &cd, 4 * C));
@@ -1349,6 +1583,34 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         K.nwall = nwall;
         CK(dalloc(ctx, &d.wall_face, nwall));
         k_wall_index<<<nblk(F, 128), 128, 0, ctx.stream>>>(d, F, widx);
+        {
+            // far-field and fixed faces in face order: ghost particle sources, with the face's local index in
+            // its fluid cell
+            std::vector<int> fbc(F), fl(F), cfh(4 * (size_t)C), nfc(C);
+            CK(cudaMemcpyAsync(fbc.data(), d.fbc, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaMemcpyAsync(fl.data(), d.fL, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaMemcpyAsync(cfh.data(), cface, sizeof(int) * 4 * (size_t)C, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaMemcpyAsync(nfc.data(), d.nfc, sizeof(int) * C, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaStreamSynchronize(ctx.stream));
+            std::vector<int> jf, jk;
+            for (int f = 0; f < F; ++f) {
+                if (fbc[f] != UGKWP_BC_FARFIELD && fbc[f] != UGKWP_BC_FIXED) continue;
+                const int L = fl[f];
+                int kk = -1;
+                for (int k = 0; k < nfc[L]; ++k) if (cfh[4 * (size_t)L + k] == f) kk = k;
+                jf.push_back(f);
+                jk.push_back(kk);
+            }
+            K.n_inj = (int)jf.size();
+            const int n1 = std::max(K.n_inj, 1);
+            CK(dalloc(ctx, &d.inj_face, n1)); CK(dalloc(ctx, &d.inj_k, n1)); CK(dalloc(ctx, &d.inj_n, n1));
+            CK(dalloc(ctx, &d.inj_par, 5 * n1));
+            if (K.n_inj) {
+                CK(cudaMemcpyAsync(d.inj_face, jf.data(), sizeof(int) * K.n_inj, cudaMemcpyHostToDevice, ctx.stream));
+                CK(cudaMemcpyAsync(d.inj_k, jk.data(), sizeof(int) * K.n_inj, cudaMemcpyHostToDevice, ctx.stream));
+            }
+            CK(cudaStreamSynchronize(ctx.stream));
+        }
         // fixed-point exponents: per-cell sums stay below 2^61 for up to 1024 x freestream density in the
         // largest cell and speeds up to U_inf + 10 sqrt(R T_max)
         std::vector<double> vol(C);
@@ -1383,8 +1645,14 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
                 tab[5][k] = (double)((k + 1) * (k + 2)) / (2.0 * f3);
             }
             CK(cudaMemcpyToSymbol(c_series, tab, sizeof tab));
-            double tf[4][kSeries];
-            for (int k = 0; k < kSeries; ++k) { tf[0][k] = tab[0][k]; tf[1][k] = tab[1][k]; tf[2][k] = tab[2][k]; tf[3][k] = tab[4][k]; }
+            float tab32[6][kSeries32];
+            for (int q = 0; q < 6; ++q)
+                for (int k = 0; k < kSeries32; ++k) tab32[q][k] = (float)tab[q][k];
+            CK(cudaMemcpyToSymbol(c_series32, tab32, sizeof tab32));
+            double tf[5][kSeries];
+            for (int k = 0; k < kSeries; ++k) {
+                tf[0][k] = tab[0][k]; tf[1][k] = tab[1][k]; tf[2][k] = tab[2][k]; tf[3][k] = tab[4][k]; tf[4][k] = tab[3][k];
+            }
             CK(flux_set_tables(&tf[0][0], ctx.stream));
             CK(cudaStreamSynchronize(ctx.stream));
         }
@@ -1398,7 +1666,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         CK(dalloc(ctx, &d.hphys, C)); CK(dalloc(ctx, &d.nhp, C)); CK(dalloc(ctx, &d.nhp_off, C + 1));
         CK(dalloc(ctx, &d.cnt, C)); CK(dalloc(ctx, &d.off, C + 1)); CK(dalloc(ctx, &d.cur, C));
         CK(dalloc(ctx, &d.flux, 4 * F));
-        ctx.res_blocks = nblk((long long)C + nwall, 256);
+        ctx.res_blocks = nblk((long long)C + nwall, kUpdateBlock);
         CK(dalloc(ctx, &d.res_part, 4 * ctx.res_blocks)); CK(dalloc(ctx, &d.res, 8));
         CK(dalloc(ctx, &d.chi_ema, C));
         CK(dalloc(ctx, &d.surf_sum, 3 * std::max(nwall, 1))); CK(dalloc(ctx, &d.surf_last, 3 * std::max(nwall, 1)));
@@ -1585,6 +1853,7 @@ ugkwp_status ugkwp_stats(ugkwp_ctx* h, int64_t* out)
     out[9] = (int64_t)s[10];
     out[10] = (int64_t)s[11];
     out[11] = (int64_t)s[12];
+    out[12] = (int64_t)s[13];
     return st;
 }
 

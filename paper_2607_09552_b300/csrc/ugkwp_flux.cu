@@ -221,42 +221,45 @@ __device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, C caL, C frL, 
     return true;
 }
 
-// Taylor weights of phi1, psi2, psi3, beta (see the cell decomposition), k = 0..19
+// Taylor weights of phi1, psi2, psi3, beta, chi (see the cell decomposition), k = 0..19
 constexpr int kSeriesF = 20;
-__constant__ double c_series_f[4][kSeriesF];
+__constant__ double c_series_f[5][kSeriesF];
 
-// normalised coefficients (dbar_a, dbar_b, dbar_c, dbar_d) of a ghost side (Eq. 48), FP64
-__device__ void ghost_coeffs(double dt, double tau, double c[4])
+// normalised coefficients (dbar_a, dbar_b, dbar_c, dbar_d, dbar_d - e^{-x}) of a ghost side (Eq. 48), FP64
+__device__ void ghost_coeffs(double dt, double tau, double c[5])
 {
     const double x = dt / tau;
     const double e = dexp(-x);
-    double phi1, psi2, psi3, beta;
+    double phi1, psi2, psi3, beta, chi;
     if (x < 1.0) {
         const double mx = -x;
-        phi1 = psi2 = psi3 = beta = 0.0;
+        phi1 = psi2 = psi3 = beta = chi = 0.0;
 #pragma unroll
         for (int k = kSeriesF - 1; k >= 0; --k) {
             phi1 = fma(mx, phi1, c_series_f[0][k]);
             psi2 = fma(mx, psi2, c_series_f[1][k]);
             psi3 = fma(mx, psi3, c_series_f[2][k]);
             beta = fma(mx, beta, c_series_f[3][k]);
+            chi = fma(mx, chi, c_series_f[4][k]);
         }
     } else {
         phi1 = (1.0 - e) / x;
         psi2 = (e - 1.0 + x) / (x * x);
         psi3 = (0.5 * x * x - x + 1.0 - e) / (x * x * x);
         beta = (1.0 + e - 2.0 * phi1) / (x * x);
+        chi = (phi1 - e) / x;
     }
     c[0] = x * psi2;
     c[1] = -dt * x * beta;
     c[2] = dt * x * psi3;
     c[3] = phi1;
+    c[4] = x * chi;
 }
 
 __device__ double tau_of(const StepConsts& K, const double W[4])
 {
-    const double rho = W[0], U = W[1] / rho, V = W[2] / rho;
-    const double RT = (W[3] / rho - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
+    const double rho = W[0], r = 1.0 / rho, U = W[1] * r, V = W[2] * r;
+    const double RT = (W[3] * r - 0.5 * (U * U + V * V)) * (2.0 / 3.0);
     const double mu = K.mu_inf * dpow(RT / kR, K.omega);
     return mu / (rho * RT);
 }
@@ -306,10 +309,13 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
             for (int k = 0; k < 4; ++k) Wg[k] = src[k];
         }
         rot(Wg, WR);
-        double cg[4];
+        // the ghost's collisionless part e^{-x} enters as particles (ghost sources), so its wave
+        // free-transport weight is dbar_d - e^{-x}; in the particle-free mode the wave keeps all of it
+        double cg[5];
         ghost_coeffs(c.dt[L], tau_of(K, Wg), cg);
         const C cR[3] = {C(cg[0]), C(cg[1]), C(cg[2])};
-        ok = face_flux<R, C>(WL, WR, WhL, WR, hL, true, cL, cR, frL, C(cg[3]), R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
+        ok = face_flux<R, C>(WL, WR, WhL, WR, hL, true, cL, cR, frL, C(K.wave_only ? cg[3] : cg[4]), R(c.fdL[f]),
+                             R(c.fdL[f]), R(K.Pr), F);
     }
     const C nxc = C(nx), nyc = C(ny);
     out[0] = double(F[0]);
@@ -371,7 +377,7 @@ void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s
 
 cudaError_t flux_set_tables(const double* tab, cudaStream_t s)
 {
-    return cudaMemcpyToSymbolAsync(c_series_f, tab, sizeof(double) * 4 * kSeriesF, 0, cudaMemcpyHostToDevice, s);
+    return cudaMemcpyToSymbolAsync(c_series_f, tab, sizeof(double) * 5 * kSeriesF, 0, cudaMemcpyHostToDevice, s);
 }
 
 }  // namespace ugk

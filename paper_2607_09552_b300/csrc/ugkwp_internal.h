@@ -38,6 +38,7 @@ struct StepConsts {
     int fx_s2, fx_s3, shakhov;      // second / third velocity moments; Shakhov sampling (Pr != 1, particles)
     int n_f64, sort_every;          // faces in f64list; counting sort of the particles every sort_every steps
     int chunk;                      // particles per dynamically claimed chunk of the transport kernel
+    int n_inj;                      // ghost particle sources (far-field and fixed faces)
     double mu_inf, omega, Pr, Tw, U_inf, m2RTw, sig_w;
     double T_cap, U_cap, T_min;     // realizability bounds of a cell state
     double W_inf[4], W_fix[4];
@@ -49,6 +50,11 @@ struct Dev {
     // geometry
     double *vol, *xc, *yc, *dt;
     double* rcp;                       // [2C] 1 / Omega_i, 1 / dt_i
+    int* wallcell;                     // [C] 1: the cell has a wall face
+    double *fax, *fay, *fex, *fey;     // [F] face start vertex a and edge b - a (1-D: the face point)
+    int *inj_face, *inj_k;             // [n_inj] far-field / fixed faces (ghost particle sources), local index in L
+    int* inj_n;                        // [n_inj] particles sampled by each source this step
+    double* inj_par;                   // [5 n_inj] mass, ghost U, V, sqrt(R T), slab depth
     int* nfc;
     CellFaces<float>* cf32;
     CellFaces<double>* cf64;
@@ -85,7 +91,8 @@ struct Dev {
     int *nretry, *retry;               // faces whose FP32 flux failed this step (re-evaluated in FP64)
     int* f64list;                      // faces always evaluated in FP64
     unsigned int* done;                // blocks of k_update finished (last-block reduction)
-    int* counts;                       // [0] retained, [1] new this step, [2] kept after the step, [3] capacity
+    int* counts;                       // [0] retained, [1] new this step, [2] kept after the step, [3] capacity,
+                                       // [4] processed, [5] chunk counter, [6] entered from ghosts, [7] their sort slots
     unsigned long long* stats;         // [0..7] per step (see ugkwp_stats), [8] surface samples,
                                        // [9] cumulative particle-steps, [10] cumulative new particles,
                                        // [11] cells set to the vacuum floor in the last step

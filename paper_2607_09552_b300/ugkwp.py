@@ -27,7 +27,7 @@ EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugk
            "ugkwp_mlp_grad", "ugkwp_mlp_adam", "ugkwp_mlp_features", "ugkwp_field_accumulate", "ugkwp_mlp_dataset",
            "ugkwp_warm_start", "ugkwp_get_field_noalloc", "ugkwp_set_launch", "ugkwp_get_launch", "ugkwp_autotune",
            "ugkwp_last_error"]
-STAGES = ["decompose", "sample", "particles", "wave_flux", "sort", "update"]
+STAGES = ["decompose", "sample", "particles", "wave_flux", "sort", "update"]   # wave_flux: ghost sources + wave fluxes
 
 
 class UgkwpMesh(C.Structure):
@@ -181,8 +181,9 @@ class Solver:
 
     def stats(self):
         """[steps, particles, new, removed, left, crossings, wall hits, max iterations, cumulative
-        particle-steps, cumulative new particles, cells floored in the last step, A-R fallbacks]"""
-        out = np.zeros(12, dtype=np.int64)
+        particle-steps, cumulative new particles, cells floored in the last step, A-R fallbacks,
+        particles entered from ghost sources]"""
+        out = np.zeros(13, dtype=np.int64)
         self._check(load().ugkwp_stats(self.ctx, _p(out, C.c_int64)))
         return out
 

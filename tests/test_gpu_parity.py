@@ -46,6 +46,7 @@ def _compare_step(g, o, prec):
     assert np.array_equal(sg[1:8], so[1:8]), (sg, so)
     assert sg[10] == so[8]
     assert sg[11] == so[9]
+    assert sg[12] == so[10]
     assert_particles_equal(g.particles(), o.particles())
     Fg, Fo = g.flux(), o.flux()
     assert_field_close(Fg, Fo, 10 * TOL[prec])
