@@ -172,13 +172,7 @@ def run_ours(args):
         part_ms = stage_ms["particles"] / max(nprof, 1)
         per_launch = prof_psteps / max(nprof, 1)
         achieved = BYTES_PER_PARTICLE_STEP * per_launch / (part_ms * 1e-3) / 1e9
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", "particles_traffic.json")
-        if os.path.exists(tfile):
-            try:
-                traffic = json.load(open(tfile)).get("bytes_per_launch_at_bench_size")
-            except Exception:
-                traffic = None
+        traffic = particles_traffic(per_launch)
         cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
         cfg = config_dict(case, args.burn, "512 MB L2 flush before every timed step, outside the events")
         cfg["launch"] = {"chunk": launch[0], "blocks_per_sm": launch[1], "sort_every": launch[2],
@@ -208,6 +202,22 @@ def run_ours(args):
     solver.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def particles_traffic(per_launch: float):
+    """DRAM bytes (read + written) of one transport-kernel launch: the bytes per particle of the committed ncu
+    capture (profiles/particles_traffic.json) times this launch's particles; None when the kernel source has
+    changed since the capture."""
+    import hashlib
+    tfile = os.path.join(ROOT, "profiles", "particles_traffic.json")
+    try:
+        t = json.load(open(tfile))
+        src = open(os.path.join(ROOT, t["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != t["source_sha256_16"]:
+            return None
+        return float(t["bytes_per_particle"]) * per_launch
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def reduce_over_ranks(ms: float, work: float, world: int, device: str):
