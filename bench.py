@@ -415,7 +415,9 @@ def run_batch(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     cases = wl.batch_sweep(0, scale=args.batch_scale)
-    solvers = [ugkwp.Solver(c, precision=0, stream=stream.cuda_stream, use_graph=True) for c in cases]
+    # room for the start-up transient, whose particle count overshoots the steady one by up to about 3x
+    solvers = [ugkwp.Solver(c, precision=0, stream=stream.cuda_stream, use_graph=True,
+                            capacity=8 * c.n_ref * c.mesh.ncells) for c in cases]
     for s in solvers:
         s.step(args.burn)
     torch.cuda.synchronize()

@@ -786,6 +786,26 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
         }
 }
 
+// The face through which a particle at (x, y) moving with (u, v) leaves its cell first: exit time through face
+// k = (d_k - n_k . x) / (n_k . u) for n_k . u > 0 (negative values, from rounding on a face, count as 0); the
+// smallest wins, ties go to the lower local index; the face `entry` is skipped. Returns the local index, or -1
+// when no face lies ahead, and the exit time in best.
+template <typename T>
+__device__ __forceinline__ int first_exit(const CellFaces<T>& F, int nf, int entry, T x, T y, T u, T v, T& best)
+{
+    int kb = -1;
+    best = T(0);
+    for (int k = 0; k < nf; ++k) {
+        if (k == entry) continue;
+        const T un = F.nx[k] * u + F.ny[k] * v;
+        if (!(un > T(0))) continue;
+        T t = (F.d[k] - (F.nx[k] * x + F.ny[k] * y)) / un;
+        if (t < T(0)) t = T(0);
+        if (kb < 0 || t < best) { best = t; kb = k; }
+    }
+    return kb;
+}
+
 // Free flight of one particle for the time tr left from cell c (the face `entry` excluded from the first exit
 // test: the face it came in through, or -1): exit time through the cell's faces; at a crossing L -> R the
 // mass and the remaining time scale by dt_R / dt_L (Eqs. 41, 52); diffuse re-emission at walls (wall tallies),
@@ -801,17 +821,8 @@ __device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict
     bool alive = true;
     for (;;) {
         const CellFaces<T>& F = cf[c];
-        const int nf = d.nfc[c];
-        int kb = -1;
-        T best = T(0);
-        for (int k = 0; k < nf; ++k) {
-            if (k == entry) continue;
-            const T un = F.nx[k] * u + F.ny[k] * v;
-            if (!(un > T(0))) continue;
-            T t = (F.d[k] - (F.nx[k] * x + F.ny[k] * y)) / un;
-            if (t < T(0)) t = T(0);
-            if (kb < 0 || t < best) { best = t; kb = k; }
-        }
+        T best;
+        const int kb = first_exit(F, d.nfc[c], entry, x, y, u, v, best);
         if (kb < 0 || tr <= best) {
             x = x + u * tr;
             y = y + v * tr;
@@ -886,7 +897,7 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
     const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
     const bool sort_step = d.flags[0] != 0;
     const int nret = d.counts[0];
-    const int n = nret + d.counts[1];
+    const int n = nret + d.counts[1], cap = d.counts[3];
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
     const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
     const T m2RTw = T(K.m2RTw), sigw = T(K.sig_w);
@@ -985,10 +996,15 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
             if (lane == 0 && km) slot0 = atomicAdd(d.counts + 2, __popc(km));
             slot0 = __shfl_sync(0xffffffffu, slot0, 0);
             if (kept) {
+                // the ghost sources on the second stream take slots of the same buffer meanwhile
                 const int j = slot0 + __popc(km & lt_mask);
-                B.x[j] = x; B.y[j] = y; B.u[j] = u; B.v[j] = v; B.w[j] = w; B.m[j] = m;
-                B.cell[j] = end_cell;
-                B.pid[j] = pid;
+                if (j >= cap) {
+                    atomicOr(d.err, ERR_CAPACITY);
+                } else {
+                    B.x[j] = x; B.y[j] = y; B.u[j] = u; B.v[j] = v; B.w[j] = w; B.m[j] = m;
+                    B.cell[j] = end_cell;
+                    B.pid[j] = pid;
+                }
             }
         }
         // survivors per cell for the counting sort (sort steps only), one atomic per run of equal cell
