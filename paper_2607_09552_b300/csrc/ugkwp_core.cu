@@ -35,7 +35,7 @@ constexpr int kScanBlock = 1024;
 #define UGKWP_SORT_EVERY 8   // steps between counting sorts of the particles by cell
 #endif
 #ifndef UGKWP_PARTICLES_MINB
-#define UGKWP_PARTICLES_MINB 4
+#define UGKWP_PARTICLES_MINB 5   // resident 256-thread blocks per SM the transport kernel is compiled for
 #endif
 constexpr int kMaxCells = 1 << 20;
 
@@ -523,6 +523,7 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     d.mnew[c] = m;
     d.samp[3 * c] = Uh; d.samp[3 * c + 1] = Vh; d.samp[3 * c + 2] = RTh;
     d.tau32[c] = (float)tau;
+    d.emx32[c] = (float)e;
     d.dt32[c] = (float)dt;
     d.mnew32[c] = (float)m;
     d.samp32[3 * c] = (float)Uh; d.samp32[3 * c + 1] = (float)Vh; d.samp32[3 * c + 2] = (float)RTh;
@@ -556,16 +557,18 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
 // per-cell particle-precision views
 template <typename T> struct PCell;
 template <> struct PCell<float> {
-    const float *tau, *dt, *mnew, *samp, *hq;
+    const float *tau, *dt, *mnew, *samp, *hq, *emx;
     __device__ float tau_(int c) const { return tau[c]; }
+    __device__ float emx_(int c) const { return emx[c]; }
     __device__ float q_(int c, int k) const { return hq[3 * c + k]; }
     __device__ float dt_(int c) const { return dt[c]; }
     __device__ float m_(int c) const { return mnew[c]; }
     __device__ float s_(int c, int k) const { return samp[3 * c + k]; }
 };
 template <> struct PCell<double> {
-    const double *tau, *dt, *mnew, *samp, *hq;
+    const double *tau, *dt, *mnew, *samp, *hq, *emx;
     __device__ double tau_(int c) const { return tau[c]; }
+    __device__ double emx_(int c) const { return emx[c]; }
     __device__ double q_(int c, int k) const { return hq[3 * c + k]; }
     __device__ double dt_(int c) const { return dt[c]; }
     __device__ double m_(int c) const { return mnew[c]; }
@@ -786,10 +789,26 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
         }
 }
 
+// A particle at (x, y) moving with (u, v) stays in its cell for the time tr when it reaches none of the faces
+// ahead (n_k . u > 0; the face `entry` is skipped): tr (n_k . u) <= d_k - n_k . x for each of them. No
+// division on this path, which almost every particle takes.
+template <typename T>
+__device__ __forceinline__ bool stays_in(const CellFaces<T>& F, int nf, int entry, T x, T y, T u, T v, T tr)
+{
+    bool stays = true;
+    for (int k = 0; k < nf; ++k) {
+        if (k == entry) continue;
+        const T un = F.nx[k] * u + F.ny[k] * v;
+        if (!(un > T(0))) continue;
+        if (tr * un > F.d[k] - (F.nx[k] * x + F.ny[k] * y)) stays = false;
+    }
+    return stays;
+}
+
 // The face through which a particle at (x, y) moving with (u, v) leaves its cell first: exit time through face
 // k = (d_k - n_k . x) / (n_k . u) for n_k . u > 0 (negative values, from rounding on a face, count as 0); the
 // smallest wins, ties go to the lower local index; the face `entry` is skipped. Returns the local index, or -1
-// when no face lies ahead, and the exit time in best.
+// when no face lies ahead, and the exit time in best. Called when stays_in is false, so a face lies ahead.
 template <typename T>
 __device__ __forceinline__ int first_exit(const CellFaces<T>& F, int nf, int entry, T x, T y, T u, T v, T& best)
 {
@@ -821,13 +840,15 @@ __device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict
     bool alive = true;
     for (;;) {
         const CellFaces<T>& F = cf[c];
-        T best;
-        const int kb = first_exit(F, d.nfc[c], entry, x, y, u, v, best);
-        if (kb < 0 || tr <= best) {
+        const int nf = d.nfc[c];
+        if (stays_in(F, nf, entry, x, y, u, v, tr)) {
             x = x + u * tr;
             y = y + v * tr;
             break;
         }
+        T best;
+        const int kb = first_exit(F, nf, entry, x, y, u, v, best);
+        if (best > tr) best = tr;
         x = x + u * best;
         y = y + v * best;
         tr = tr - best;
@@ -943,11 +964,16 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
             if (i >= nret) {
                 tr = dtc;
             } else {
+                // Eq. 27: t_f = -tau_i ln eps falls short of dt_i exactly when eps > e^{-dt_i / tau_i}; the
+                // logarithm only for the colliding particles (t_f capped at dt_i against rounding)
                 T U[1];
                 Unif<T>::get(g, pid, DRAW_TF, 1, U);
-                const T a = -(pc.tau_(c) * dlog(U[0]));
-                collide = a < dtc;
-                tr = collide ? a : dtc;
+                collide = U[0] > pc.emx_(c);
+                tr = dtc;
+                if (collide) {
+                    const T a = -(pc.tau_(c) * dlog(U[0]));
+                    if (a < dtc) tr = a;
+                }
             }
             int it = 0;
             const bool alive = fly(d, cf, g, s1, s4, m2RTw, sigw, x, y, u, v, w, m, tr, c, -1, pid, it,
@@ -1437,8 +1463,8 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     launch_wave_flux(K, d, ctx.sms, s2);
     mark(7, s2);
     cudaEventRecord(ctx.ev_join, s2);
-    PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32, d.hq32};
-    PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp, d.hq};
+    PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32, d.hq32, d.emx32};
+    PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp, d.hq, d.emx};
     mark(2, s);
     if (K.prec == 0) k_sample<float><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
     else k_sample<double><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
@@ -1711,6 +1737,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         K.sort_every = UGKWP_SORT_EVERY;
         K.chunk = UGKWP_CHUNK;
         CK(dalloc(ctx, &d.tau32, C)); CK(dalloc(ctx, &d.dt32, C)); CK(dalloc(ctx, &d.mnew32, C));
+        CK(dalloc(ctx, &d.emx32, C));
         CK(dalloc(ctx, &d.samp32, 3 * C));
         CK(dalloc(ctx, &d.dstep, 1));
         int sms = 148;

@@ -84,7 +84,8 @@ struct Dev {
     // particles: A holds the cell-sorted retained set between steps, B is the staging buffer
     ParticleSoA<float> pa32, pb32;
     ParticleSoA<double> pa64, pb64;
-    float *tau32, *dt32, *mnew32, *samp32;   // particle-precision copies of tau, dt, m_new, (U^h, V^h, R T^h)
+    float *tau32, *dt32, *mnew32, *samp32;   // particle-precision copies of tau, dt, m_new, (U^h, V^h, R T^h),
+    float* emx32;                            // e^{-dt/tau}
     long long* dstep;                  // step counter (Philox counter word)
     int* bufsel;                       // which particle buffer (A: 0, B: 1) holds the current particles
     int* flags;                        // [0]: this step sorts the particles by cell
