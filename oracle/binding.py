@@ -202,9 +202,9 @@ class Oracle:
         wm, wpl, wret = (np.zeros(5 * self.C, dtype=np.int64) for _ in range(3))
         cross = np.zeros(2 * self.F, dtype=np.int64)
         wall = np.zeros(max(3 * self.nwall, 1), dtype=np.int64)
-        frec = np.zeros(4 * self.F)
+        frec = np.zeros(4 * self.F, dtype=np.int64)
         lib().oracle_get_tallies(self.ctx, _p(wm, C.c_int64), _p(wpl, C.c_int64), _p(wret, C.c_int64),
-                                 _p(cross, C.c_int64), _p(wall, C.c_int64), dptr(frec))
+                                 _p(cross, C.c_int64), _p(wall, C.c_int64), _p(frec, C.c_int64))
         return dict(wm=wm.reshape(self.C, 5), wpl=wpl.reshape(self.C, 5), wret=wret.reshape(self.C, 5),
                     cross=cross.reshape(self.F, 2), wall=wall[:3 * self.nwall].reshape(self.nwall, 3),
                     frec=frec.reshape(self.F, 4))

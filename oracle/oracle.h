@@ -37,7 +37,9 @@ typedef struct {
     int32_t n_ref;
     int32_t precision;       /* 0: FP32 particles (production emulation); 1: all FP64 */
     int32_t wave_only;       /* 1: no particles (deterministic GKS limit) */
-    int32_t record_faces;    /* 1: per-face side-recorded crossing masses */
+    int32_t record_faces;    /* 1: per-face side-recorded crossing masses of each step (S33): frec[4 f + 2 d]
+                              * the masses before, frec[4 f + 2 d + 1] after the scaling, d = 0 for L -> R,
+                              * 1 for R -> L, as fixed-point integers of the mass exponent */
     int32_t capacity;        /* particle capacity; 0 = 4 * n_ref * cells */
     double ghost_state[4];   /* (rho, U, V, T) of BC_FIXED ghosts */
 } oracle_opts;

@@ -611,7 +611,7 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     cx->whq = zalloc(9 * C, 8); cx->hq = zalloc(3 * C, 8);
     cx->nhp = zalloc(C, 4); cx->hphys = zalloc(C, 4); cx->nhp_off = zalloc(C + 1, 8);
     cx->wm = zalloc(5 * C, 8); cx->wpl = zalloc(5 * C, 8); cx->wrt = zalloc(5 * C, 8);
-    cx->cross = zalloc(2 * F, 8); cx->wallt = zalloc(3 * cx->nwall, 8); cx->frec_d = zalloc(4 * F, 8);
+    cx->cross = zalloc(2 * F, 8); cx->wallt = zalloc(3 * cx->nwall, 8); cx->frec = zalloc(4 * F, 8);
     cx->flux = zalloc(4 * F, 8);
     cx->chi_ema = zalloc(C, 8);
     cx->surf_sum = zalloc(3 * cx->nwall, 8); cx->surf_last = zalloc(3 * cx->nwall, 8);
@@ -631,7 +631,7 @@ void oracle_destroy(oracle_ctx* cx)
                     cx->fR, cx->fbc, cx->fwall, cx->fnx, cx->fny, cx->fs, cx->fdL, cx->fdR, cx->finv_s,
                     cx->wall_face, cx->dt, cx->ratio, cx->W, cx->wret_prev, cx->tau, cx->xr_t, cx->emx, cx->Wp,
                     cx->Wh, cx->mnew, cx->co, cx->samp, cx->nhp, cx->hphys, cx->nhp_off, cx->wm, cx->wpl,
-                    cx->wrt, cx->cross, cx->wallt, cx->frec_d, cx->flux, cx->chi_ema, cx->surf_sum,
+                    cx->wrt, cx->cross, cx->wallt, cx->frec, cx->flux, cx->chi_ema, cx->surf_sum,
                     cx->surf_last, cx->p, cx->whq, cx->hq, cx->fax, cx->fay, cx->fex, cx->fey,
                     cx->inj_face, cx->inj_k, cx->inj_n, cx->inj_m, cx->inj_u, cx->inj_v, cx->inj_sig,
                     cx->inj_D};
@@ -915,6 +915,7 @@ static int one_step(or_ctx* cx)
     memset(cx->wpl, 0, 5 * (size_t)C * 8);
     memset(cx->wrt, 0, 5 * (size_t)C * 8);
     memset(cx->cross, 0, 2 * (size_t)cx->F * 8);
+    memset(cx->frec, 0, 4 * (size_t)cx->F * 8);
     memset(cx->wallt, 0, 3 * (size_t)cx->nwall * 8);
     for (int k = 2; k < 11; ++k) cx->stats[k] = 0;
     /* step 1: decomposition and sampling; step 2: free transport and tallies (Sec. III C, Sec. IV B) */
@@ -1064,7 +1065,7 @@ int oracle_get_tallies(oracle_ctx* cx, int64_t* wm, int64_t* wpl, int64_t* wret,
     if (wret) memcpy(wret, cx->wrt, 5 * C * 8);
     if (cross) memcpy(cross, cx->cross, 2 * (size_t)cx->F * 8);
     if (wall) memcpy(wall, cx->wallt, 3 * (size_t)cx->nwall * 8);
-    if (frec) memcpy(frec, cx->frec_d, 4 * (size_t)cx->F * 8);
+    if (frec) memcpy(frec, cx->frec, 4 * (size_t)cx->F * 8);
     return OR_OK;
 }
 

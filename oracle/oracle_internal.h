@@ -71,7 +71,7 @@ struct oracle_ctx {
     int64_t *nhp_off;
     /* tallies */
     int64_t *wm, *wpl, *wrt, *cross, *wallt;
-    double* frec_d;                              /* [4F] side-recorded crossing masses (diagnostic) */
+    int64_t* frec;                               /* [4F] side-recorded crossing masses of this step (S33) */
     double *flux;                                /* [4F] */
     /* particles */
     int64_t np, cap;
