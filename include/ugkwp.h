@@ -79,7 +79,10 @@ typedef struct {
     int32_t precision;        /* 0: FP32 particles, FP32 interior wave fluxes, FP64 cell update and wall
                                  fluxes; 1: everything FP64 */
     int32_t wave_only;        /* 1: no particles (GKS limit, deterministic) */
-    int32_t record_faces;     /* reserved (0) */
+    int32_t record_faces;     /* 1: record, per face and step, the masses of the particles crossing it before
+                                 and after the dt_R / dt_L scaling (the side-recorded fluxes of Sec. IV A,
+                                 Eqs. 35-43), read by ugkwp_get_tallies; costs 32 F bytes and two 64-bit
+                                 atomics per crossing. 0: off (the default). */
     int32_t capacity;         /* particle capacity; 0 = 4 n_ref cells */
     double ghost_state[4];    /* (rho, U, V, T) of UGKWP_BC_FIXED ghosts */
     void* stream;             /* cudaStream_t to run on (NULL: the legacy default stream) */
@@ -146,7 +149,9 @@ ugkwp_status ugkwp_set_state(ugkwp_ctx* ctx, int64_t step, const double* W, cons
                              const double* u, const double* v, const double* w, const double* m);
 /* Integer tallies of the last step (any pointer may be NULL): W^{p,-} and W^{p,+} and the retained part
  * (5 C each: sum of m, m u, m v, m w, m |u|^2/2 in fixed point), face crossings (2 F: L->R, R->L),
- * wall momentum/energy transfer (3 per wall face). frec is reserved (NULL). */
+ * wall momentum/energy transfer (3 per wall face), and the side-recorded crossing masses (4 F: per face,
+ * L->R before and after the scaling, then R->L before and after; fixed point of the mass exponent; zeros
+ * unless the context was created with record_faces = 1). */
 ugkwp_status ugkwp_get_tallies(ugkwp_ctx* ctx, int64_t* wm, int64_t* wpl, int64_t* wret, int64_t* cross,
                                int64_t* wall, int64_t* frec);
 /* Per cell (8 C doubles) of the last decomposition: tau, dt/tau, e^{-dt/tau}, N^hp, new-particle mass,

@@ -537,6 +537,8 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
     const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
     for (int q = t; q < 2 * K.F; q += nt) d.cross[q] = 0u;
     for (int q = t; q < 3 * K.nwall; q += nt) d.wallt[q] = 0;
+    if (d.frec)
+        for (int q = t; q < 4 * K.F; q += nt) d.frec[q] = 0;
     if (K.shakhov)
         for (int q = t; q < 9 * K.C; q += nt) d.whq[q] = 0;
     if (t == 0) {
@@ -831,7 +833,7 @@ __device__ __forceinline__ int first_exit(const CellFaces<T>& F, int nf, int ent
 // specular mirrors, deletion at far-field and fixed ghosts. Returns alive; c is the final cell, it the number
 // of face events.
 template <typename T>
-__device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict__ cf, const Rng& g, T s1, T s4,
+__device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict__ cf, const Rng& g, T s0, T s1, T s4,
                                     T m2RTw, T sigw, T& x, T& y, T& u, T& v, T& w, T& m, T tr, int& c, int entry,
                                     uint64_t pid, int& it, unsigned long long& n_cross, unsigned long long& n_hits)
 {
@@ -861,8 +863,13 @@ __device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict
             atomicAdd(d.cross + 2 * f + dir, 1u);
             n_cross++;
             const T r = F.ratio[kb];
+            // record mode (S33): the crossing mass before and after the scaling, fixed point of the mass exponent
+            unsigned long long* rec = d.frec ? reinterpret_cast<unsigned long long*>(d.frec) + 4 * (size_t)f + 2 * dir
+                                             : nullptr;
+            if (rec) atomicAdd(rec, (unsigned long long)fixp(m, s0, d.err));
             m = m * r;
             tr = tr * r;
+            if (rec) atomicAdd(rec + 1, (unsigned long long)fixp(m, s0, d.err));
             if (bc == UGKWP_BC_PERIODIC) x = x + T(d.cshift[4 * c + kb]);
             entry = (meta >> 24) & 3;
             c = nb;
@@ -976,7 +983,7 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
                 }
             }
             int it = 0;
-            const bool alive = fly(d, cf, g, s1, s4, m2RTw, sigw, x, y, u, v, w, m, tr, c, -1, pid, it,
+            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, x, y, u, v, w, m, tr, c, -1, pid, it,
                                    n_cross, n_hits);
             max_it = max(max_it, it);
             if (alive) {
@@ -1158,7 +1165,7 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
                     x = ax + Up[1] * ex;
                     y = ay + Up[1] * ey;
                     int it = 0;
-                    const bool alive = fly(d, cf, g, s1, s4, m2RTw, sigw, x, y, u, v, w, m, dtL - tc, c, kin, pid, it,
+                    const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, x, y, u, v, w, m, dtL - tc, c, kin, pid, it,
                                            n_cross, n_hits);
                     max_it = max(max_it, it);
                     if (alive) {
@@ -1738,6 +1745,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         K.chunk = UGKWP_CHUNK;
         CK(dalloc(ctx, &d.tau32, C)); CK(dalloc(ctx, &d.dt32, C)); CK(dalloc(ctx, &d.mnew32, C));
         CK(dalloc(ctx, &d.emx32, C));
+        if (opts->record_faces && !K.wave_only) CK(dalloc(ctx, &d.frec, 4 * (size_t)F));
         CK(dalloc(ctx, &d.samp32, 3 * C));
         CK(dalloc(ctx, &d.dstep, 1));
         int sms = 148;
@@ -2003,7 +2011,10 @@ ugkwp_status ugkwp_get_tallies(ugkwp_ctx* h, int64_t* wm, int64_t* wpl, int64_t*
         CK(cudaStreamSynchronize(ctx.stream));
         for (size_t i = 0; i < 2 * F; ++i) cross[i] = cr[i];
     }
-    (void)frec;
+    if (frec) {
+        if (ctx.d.frec) CK(cudaMemcpyAsync(frec, ctx.d.frec, 8 * 4 * F, cudaMemcpyDeviceToHost, ctx.stream));
+        else memset(frec, 0, 8 * 4 * F);
+    }
     return check_device_error(ctx);
 }
 

@@ -69,6 +69,8 @@ struct Dev {
     long long* wcol;                   // [5C] this step's collided particles that stay (retained = W^{p,+} - wcol)
     unsigned int* cross;               // [2F]
     long long* wallt;                  // [3 nwall]
+    long long* frec;                   // [4F] record mode only (else null): crossing masses of the step, per face
+                                       // and direction (L -> R, R -> L), before and after the scaling
     // per-step cell data
     double *tau, *xr, *emx, *Wh, *co, *mnew;
     double* samp;                      // [3C] U^h, V^h, R T^h

@@ -104,7 +104,8 @@ class Solver:
     """One UGKWP-LTS context on the current CUDA device for a workload `Case`."""
 
     def __init__(self, case, gts: bool = False, precision: int = 0, wave_only: bool = False, seed: int | None = None,
-                 case_id: int = 0, capacity: int = 0, use_graph: bool = False, stream=None):
+                 case_id: int = 0, capacity: int = 0, use_graph: bool = False, stream=None,
+                 record_faces: bool = False):
         L = load()
         m = case.mesh
         self._keep = [np.ascontiguousarray(m.xv, dtype=np.float64), np.ascontiguousarray(m.yv, dtype=np.float64)]
@@ -112,8 +113,8 @@ class Solver:
         mesh = UgkwpMesh(m.ni, m.nj, m.dim, m.periodic_j, _d(self._keep[0]), _d(self._keep[1]),
                          *[_p(a, C.c_int32) for a in self._keep[2:]])
         gas = UgkwpGas(case.omega, case.Pr)
-        opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only), 0,
-                         capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream), int(use_graph), 0)
+        opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
+                         int(record_faces), capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream), int(use_graph), 0)
         self.ctx = C.c_void_p()
         st = L.ugkwp_create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
                             C.c_double(case.Tw), C.c_double(case.cfl), C.c_int32(GTS if gts else LTS), C.byref(opts),
@@ -251,10 +252,12 @@ class Solver:
         wm, wpl, wret = (np.zeros(5 * self.C, dtype=np.int64) for _ in range(3))
         cross = np.zeros(2 * self.F, dtype=np.int64)
         wall = np.zeros(max(3 * self.nwall, 1), dtype=np.int64)
+        frec = np.zeros(4 * self.F, dtype=np.int64)
         self._check(load().ugkwp_get_tallies(self.ctx, _p(wm, C.c_int64), _p(wpl, C.c_int64), _p(wret, C.c_int64),
-                                             _p(cross, C.c_int64), _p(wall, C.c_int64), None))
+                                             _p(cross, C.c_int64), _p(wall, C.c_int64), _p(frec, C.c_int64)))
         return dict(wm=wm.reshape(self.C, 5), wpl=wpl.reshape(self.C, 5), wret=wret.reshape(self.C, 5),
-                    cross=cross.reshape(self.F, 2), wall=wall[:3 * self.nwall].reshape(self.nwall, 3))
+                    cross=cross.reshape(self.F, 2), wall=wall[:3 * self.nwall].reshape(self.nwall, 3),
+                    frec=frec.reshape(self.F, 4))
 
     def cell_data(self):
         out = np.zeros(8 * self.C)

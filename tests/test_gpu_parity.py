@@ -40,7 +40,7 @@ def _compare_step(g, o, prec):
     cg, co = g.cell_data(), o.cell_data()
     assert np.array_equal(cg, co), np.nonzero(cg != co)
     tg, to = g.tallies(), o.tallies()
-    for k in ("wm", "wpl", "wret", "cross", "wall"):
+    for k in ("wm", "wpl", "wret", "cross", "wall", "frec"):
         assert np.array_equal(tg[k], to[k]), (k, np.nonzero(tg[k] != to[k]))
     sg, so = g.stats(), o.stats()
     assert np.array_equal(sg[1:8], so[1:8]), (sg, so)
@@ -73,6 +73,50 @@ def test_step_from_identical_snapshot(cuda_lib, name, prec, gts):
     g.step(1)
     o.step(1)
     _compare_step(g, o, prec)
+
+
+@pytest.mark.parametrize("name", ["box", "cylinder", "shock1d"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_side_recorded_crossings_bitwise(cuda_lib, name, prec):
+    """Record mode (S33): the per-face crossing masses before and after the dt_R / dt_L scaling, from an
+    identical snapshot, equal the oracle's bit for bit."""
+    case = CASES[name]
+    g = cuda_lib.Solver(case, precision=prec, record_faces=True)
+    o = ob.Oracle(case, precision=prec, record_faces=True)
+    o.step(5)
+    step, W, wret, parts = snapshot(o)
+    g.set_state(step, W, wret, parts)
+    g.step(1)
+    o.step(1)
+    tg, to = g.tallies(), o.tallies()
+    assert np.count_nonzero(to["frec"]) > 0
+    assert np.array_equal(tg["frec"], to["frec"]), np.nonzero(tg["frec"] != to["frec"])
+    assert np.array_equal(tg["cross"], to["cross"])
+    _compare_step(g, o, prec)
+
+
+def test_side_recorded_flux_balance_on_gpu(cuda_lib):
+    """Sec. IV A, Eqs. 35-43 on the GPU: fixed local steps varying 50x over a periodic box, mass scaled by
+    dt_R / dt_L at each crossing; over M steps the recorded sums satisfy sum(m_R) / dt_R = sum(m_L) / dt_L on
+    every face and direction, up to the fixed-point rounding of each record (half a unit per side)."""
+    case = wl.case_periodic_box(ni=10, end_ratio=50.0, n_ref=40, Kn=0.2)
+    g = cuda_lib.Solver(case, precision=1, record_faces=True)
+    dt, _ = g.geometry()
+    M = 30
+    acc = np.zeros((g.F, 4))
+    ncr = np.zeros((g.F, 2))
+    for _ in range(M):
+        g.step(1)
+        t = g.tallies()
+        acc += t["frec"].astype(np.float64)
+        ncr += t["cross"]
+    ni = case.mesh.ni
+    for f in range(g.F):
+        L, R = (ni - 1, 0) if f == 0 else (f - 1, f)
+        for d, (a, b) in enumerate(((L, R), (R, L))):
+            mL, mR = acc[f, 2 * d], acc[f, 2 * d + 1]
+            assert mL > 0 and ncr[f, d] > 0
+            assert abs(mR / dt[b] - mL / dt[a]) <= ncr[f, d] * (0.5 / dt[a] + 0.5 / dt[b]) * (1 + 1e-9)
 
 
 @pytest.mark.parametrize("name", ["shock1d", "cylinder", "plate"])
