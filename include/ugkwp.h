@@ -114,6 +114,12 @@ ugkwp_status ugkwp_reset_surface(ugkwp_ctx* ctx);
 /* Set the cell state from host primitives (rho, U, V, T) per cell (4 C doubles); removes all particles
  * (W^p = 0). The local time steps are unchanged. */
 ugkwp_status ugkwp_set_field(ugkwp_ctx* ctx, const double* prim);
+/* Replace the local time steps (C host doubles, each finite and > 0) from the next step on; the crossing
+ * scaling dt_R / dt_L follows. A study tool for time-varying schedules (Sec. IV A, Eqs. 44-46): the method
+ * itself keeps the steps of Eqs. 33-34 fixed, since stepwise scaling balances the time-averaged particle
+ * fluxes only for fixed steps. Synchronises; EINVAL on a bad value (nothing changed). A captured step graph
+ * stays valid (it reads the steps from device memory). */
+ugkwp_status ugkwp_set_time_steps(ugkwp_ctx* ctx, const double* dt);
 /* W (4 C doubles: rho, rho U, rho V, rho E) and, if Wp != NULL, W^p of the retained particles. */
 ugkwp_status ugkwp_get_field(ugkwp_ctx* ctx, double* W, double* Wp);
 

@@ -145,6 +145,11 @@ class Oracle:
     def step(self, n: int = 1):
         self._check(lib().oracle_step(self.ctx, C.c_int32(n)))
 
+    def set_time_steps(self, dt):
+        """Replace the local time steps (C values > 0) from the next step on (time-varying study, Sec. IV A)."""
+        a = np.ascontiguousarray(dt, dtype=np.float64)
+        self._check(lib().oracle_set_time_steps(self.ctx, dptr(a)))
+
     def set_field(self, prim):
         a = np.ascontiguousarray(prim, dtype=np.float64).reshape(-1)
         self._check(lib().oracle_set_field(self.ctx, dptr(a)))

@@ -63,6 +63,7 @@ int  oracle_get_particles(oracle_ctx* cx, int64_t cap, uint64_t* pid, int32_t* c
 int  oracle_set_state(oracle_ctx* cx, int64_t step, const double* W, const int64_t* wret, int64_t np,
                       const uint64_t* pid, const int32_t* cell, const double* x, const double* y,
                       const double* u, const double* v, const double* w, const double* m);
+int  oracle_set_time_steps(oracle_ctx* cx, const double* dt);       /* C local steps, each > 0 (Sec. IV A) */
 int  oracle_get_tallies(oracle_ctx* cx, int64_t* wm, int64_t* wpl, int64_t* wret, int64_t* cross,
                         int64_t* wall, int64_t* frec);
 int  oracle_get_cell_data(oracle_ctx* cx, double* out);            /* [8 per cell] see oracle_core.c */

@@ -519,6 +519,16 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
     return OR_OK;
 }
 
+/* mass and remaining-time scaling of a crossing from cell c through its local face k: dt_R / dt_L (Eq. 41) */
+static void set_ratios(or_ctx* cx)
+{
+    for (int c = 0; c < cx->C; ++c)
+        for (int k = 0; k < cx->nfc[c]; ++k) {
+            const int q = 4 * c + k;
+            cx->ratio[q] = cx->cnbr[q] >= 0 ? cx->dt[cx->cnbr[q]] / cx->dt[c] : 1.0;
+        }
+}
+
 /* local time steps (Eq. 33) from the initial freestream field, then the global one (Eq. 34) */
 static void init_time_steps(or_ctx* cx)
 {
@@ -532,11 +542,7 @@ static void init_time_steps(or_ctx* cx)
     }
     if (cx->gts)
         for (int c = 0; c < cx->C; ++c) cx->dt[c] = cx->dtG;
-    for (int c = 0; c < cx->C; ++c)
-        for (int k = 0; k < cx->nfc[c]; ++k) {
-            const int q = 4 * c + k;
-            cx->ratio[q] = cx->cnbr[q] >= 0 ? cx->dt[cx->cnbr[q]] / cx->dt[c] : 1.0;
-        }
+    set_ratios(cx);
 }
 
 /* ceil(log2(x)) for x > 0, exact through frexp */
@@ -1053,6 +1059,18 @@ int oracle_set_state(oracle_ctx* cx, int64_t step, const double* W, const int64_
         P->x = x[i]; P->y = y[i]; P->u = u[i]; P->v = v[i]; P->w = w[i]; P->m = m[i];
     }
     cx->np = np;
+    return OR_OK;
+}
+
+/* Time-varying steps (Sec. IV A, Eqs. 44-46; a study tool, the method keeps its steps fixed): replace the
+ * local time steps from the next step on; the crossing scaling follows the current steps. */
+int oracle_set_time_steps(oracle_ctx* cx, const double* dt)
+{
+    if (!cx || !dt) return OR_EINVAL;
+    for (int c = 0; c < cx->C; ++c)
+        if (!(dt[c] > 0.0) || !isfinite(dt[c])) return OR_EINVAL;
+    for (int c = 0; c < cx->C; ++c) cx->dt[c] = dt[c];
+    set_ratios(cx);
     return OR_OK;
 }
 

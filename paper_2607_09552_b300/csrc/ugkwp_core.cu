@@ -1359,6 +1359,21 @@ __global__ void k_get_particles(ParticleSoA<T> A, int n, double* out)
     out[3 * n + i] = double(A.v[i]); out[4 * n + i] = double(A.w[i]); out[5 * n + i] = double(A.m[i]);
 }
 
+// after a replacement of the local time steps: 1 / dt_i and the crossing scaling dt_R / dt_L (Eq. 41) of every
+// face of every cell, by the same formula as at creation
+__global__ void k_set_ratios(Dev d, int C)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    d.rcp[2 * c + 1] = 1.0 / d.dt[c];
+    for (int k = 0; k < d.nfc[c]; ++k) {
+        const int nb = d.cf64[c].nbr[k];
+        const double r = nb >= 0 ? d.dt[nb] / d.dt[c] : 1.0;
+        d.cf64[c].ratio[k] = r;
+        d.cf32[c].ratio[k] = (float)r;
+    }
+}
+
 __global__ void k_set_prim(Dev d, int C, const double* prim)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1872,6 +1887,20 @@ ugkwp_status ugkwp_set_field(ugkwp_ctx* h, const double* prim)
     CK(cudaMemcpyAsync(ctx.d.counts, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
     cudaFree(dp);
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_set_time_steps(ugkwp_ctx* h, const double* dt)
+{
+    if (!h || !dt) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    const int C = ctx.k.C;
+    for (int c = 0; c < C; ++c)
+        if (!(dt[c] > 0.0) || !std::isfinite(dt[c])) return fail(ctx, UGKWP_EINVAL, "time steps must be finite and positive");
+    CK(cudaMemcpyAsync(ctx.d.dt, dt, sizeof(double) * C, cudaMemcpyHostToDevice, ctx.stream));
+    k_set_ratios<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx.stream));
     return UGKWP_OK;
 }
 

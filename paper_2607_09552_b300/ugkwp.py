@@ -19,7 +19,7 @@ LTS, GTS = 0, 1
 
 # every entry point declared in include/ugkwp.h
 EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugkwp_surface", "ugkwp_reset_surface",
-           "ugkwp_set_field", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
+           "ugkwp_set_field", "ugkwp_set_time_steps", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
            "ugkwp_set_state", "ugkwp_get_tallies", "ugkwp_get_cell_data", "ugkwp_get_flux", "ugkwp_get_geometry",
            "ugkwp_fixed_exponents", "ugkwp_save", "ugkwp_load", "ugkwp_batch_create", "ugkwp_batch_step",
            "ugkwp_batch_destroy", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_mlp_create", "ugkwp_mlp_destroy",
@@ -153,6 +153,11 @@ class Solver:
     def set_field(self, prim):
         a = np.ascontiguousarray(prim, dtype=np.float64).reshape(-1)
         self._check(load().ugkwp_set_field(self.ctx, _d(a)))
+
+    def set_time_steps(self, dt):
+        """Replace the local time steps (C values > 0) from the next step on (time-varying study, Sec. IV A)."""
+        a = np.ascontiguousarray(dt, dtype=np.float64)
+        self._check(load().ugkwp_set_time_steps(self.ctx, _d(a)))
 
     def field(self):
         W = np.zeros(4 * self.C)

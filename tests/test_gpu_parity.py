@@ -119,6 +119,44 @@ def test_side_recorded_flux_balance_on_gpu(cuda_lib):
             assert abs(mR / dt[b] - mL / dt[a]) <= ncr[f, d] * (0.5 / dt[a] + 0.5 / dt[b]) * (1 + 1e-9)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_time_varying_steps_parity(cuda_lib, prec):
+    """Replaced local steps (Sec. IV A study tool): from an identical snapshot, both sides given the same new
+    steps (a factor 2 on half of a 50x-stretched periodic box) take the same step bit for bit, records
+    included."""
+    case = CASES["box"]
+    g = cuda_lib.Solver(case, precision=prec, record_faces=True)
+    o = ob.Oracle(case, precision=prec, record_faces=True)
+    o.step(4)
+    step, W, wret, parts = snapshot(o)
+    g.set_state(step, W, wret, parts)
+    d0, _ = o.geometry()
+    dt = d0.copy()
+    dt[: len(dt) // 2] *= 2.0
+    g.set_time_steps(dt)
+    o.set_time_steps(dt)
+    assert np.array_equal(g.geometry()[0], o.geometry()[0])
+    g.step(1)
+    o.step(1)
+    _compare_step(g, o, prec)
+
+
+def test_time_varying_steps_break_the_balance_on_gpu(cuda_lib):
+    """Sec. IV A, Eqs. 44-46 on the GPU: fixed steps keep the two sides' time-averaged particle fluxes equal to
+    the records' rounding; the schedule dt_L = (1, 2, ...), dt_R = 2 does not (the per-step parity of the
+    replaced steps is checked above)."""
+    from tests.test_oracle_invariants import _time_averaged_ratio
+    case = wl.case_periodic_box(ni=10, end_ratio=1.0, n_ref=60, Kn=0.05)
+    g = cuda_lib.Solver(case, precision=1, record_faces=True)
+    d0, _ = g.geometry()
+    fixed = _time_averaged_ratio(g, lambda ell: np.concatenate([d0[:5], 2.0 * d0[5:]]), 20)
+    assert abs(fixed - 1.0) < 1e-11
+    sched = lambda ell: np.concatenate([d0[:5] * (1.0 if ell % 2 == 0 else 2.0), 2.0 * d0[5:]])
+    g2 = cuda_lib.Solver(case, precision=1, record_faces=True)
+    rg = _time_averaged_ratio(g2, sched, 40)
+    assert abs(rg - 1.0) > 1e-2
+
+
 @pytest.mark.parametrize("name", ["shock1d", "cylinder", "plate"])
 def test_short_trajectory_fp64(cuda_lib, name):
     """Whole trajectories from the same freestream start. The two sides' FP64 wave fluxes differ in the last

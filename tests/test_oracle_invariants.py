@@ -94,6 +94,51 @@ def test_time_averaged_particle_flux_balance():
             assert mR / (M * dt[b]) == pytest.approx(mL / (M * dt[a]), rel=1e-11)
 
 
+def _time_averaged_ratio(solver, schedule, M, face=5, L=4, R=5):
+    """F_R / F_L of the side-recorded, time-averaged particle fluxes (Sec. IV A) through `face` in the L -> R
+    direction over M steps, the local steps of step l given by schedule(l)."""
+    sL = sR = dL = dR = 0.0
+    for ell in range(M):
+        dt = schedule(ell)
+        solver.set_time_steps(dt)
+        solver.step(1)
+        rec = solver.tallies()["frec"][face].astype(np.float64)
+        sL += rec[0]
+        sR += rec[1]
+        dL += dt[L]
+        dR += dt[R]
+    return (sR / dR) / (sL / dL)
+
+
+def test_time_varying_steps_break_the_time_averaged_balance():
+    """Sec. IV A, Eqs. 44-46 on a live run: with the stepwise scaling m_R = m_L dt_R,l / dt_L,l, fixed local
+    steps keep the time-averaged particle fluxes of the two sides of a face equal (to the fixed-point rounding
+    of the records), while the paper's schedule dt_L = (1, 2, 1, 2, ...), dt_R = 2 (in units of the initial
+    step) leaves them unequal, because the crossing mass of a step is not proportional to dt_L."""
+    case = wl.case_periodic_box(ni=10, end_ratio=1.0, n_ref=60, Kn=0.05)
+    o = ob.Oracle(case, gts=False, precision=1, record_faces=True)
+    d0, _ = o.geometry()
+    fixed = _time_averaged_ratio(o, lambda ell: np.concatenate([d0[:5], 2.0 * d0[5:]]), 20)
+    assert abs(fixed - 1.0) < 1e-11
+    o2 = ob.Oracle(case, gts=False, precision=1, record_faces=True)
+    varying = _time_averaged_ratio(
+        o2, lambda ell: np.concatenate([d0[:5] * (1.0 if ell % 2 == 0 else 2.0), 2.0 * d0[5:]]), 40)
+    assert abs(varying - 1.0) > 1e-2
+
+
+def test_time_steps_replacement_is_validated():
+    case = wl.case_periodic_box(ni=6, end_ratio=1.0, n_ref=10)
+    o = ob.Oracle(case, precision=1)
+    d0, _ = o.geometry()
+    for bad in (0.0, -1.0, np.inf, np.nan):
+        dt = d0.copy()
+        dt[2] = bad
+        with pytest.raises(ob.OracleError):
+            o.set_time_steps(dt)
+    o.set_time_steps(d0 * 0.5)
+    assert np.array_equal(o.geometry()[0], d0 * 0.5)
+
+
 def test_counterexample_for_time_varying_steps():
     """Sec. IV A: for M = 2, dt_L = (1, 2), dt_R = (2, 2) the two sides of the unweighted balance condition
     are 4/3 and 3/2, so stepwise scaling alone does not balance time-varying steps."""
