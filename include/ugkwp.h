@@ -87,7 +87,9 @@ typedef struct {
     double ghost_state[4];    /* (rho, U, V, T) of UGKWP_BC_FIXED ghosts */
     void* stream;             /* cudaStream_t to run on (NULL: the legacy default stream) */
     int32_t use_graph;        /* 1: capture one step into a CUDA graph on the first ugkwp_step, replay it */
-    int32_t reserved;
+    int32_t order;            /* 2: second-order reconstruction of W and W^h for the wave fluxes (Eq. 12; 1-D van
+                                 Leer, 2-D least squares with Barth-Jespersen limiting; 128 B per cell);
+                                 0 or 1: first order (the default) */
 } ugkwp_opts;
 
 /* Build the context: geometry, fixed local time steps (Eqs. 33-34), uniform freestream state, no

@@ -28,7 +28,7 @@ class OracleGas(C.Structure):
 class OracleOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("case_id", C.c_uint32), ("n_ref", C.c_int32), ("precision", C.c_int32),
                 ("wave_only", C.c_int32), ("record_faces", C.c_int32), ("capacity", C.c_int32),
-                ("ghost_state", C.c_double * 4)]
+                ("ghost_state", C.c_double * 4), ("order", C.c_int32)]
 
 
 def lib():
@@ -107,7 +107,7 @@ class Oracle:
     """One oracle context for a workload `Case` (see paper_2607_09552_b300.workloads)."""
 
     def __init__(self, case, gts: bool = False, precision: int = 0, wave_only: bool = False,
-                 record_faces: bool = False, seed: int | None = None, case_id: int = 0):
+                 record_faces: bool = False, seed: int | None = None, case_id: int = 0, order: int = 1):
         L = lib()
         m = case.mesh
         self._keep = [np.ascontiguousarray(a) for a in (m.xv, m.yv)]
@@ -116,7 +116,7 @@ class Oracle:
                           *[_p(a, C.c_int32) for a in self._keep[2:]])
         gas = OracleGas(case.omega, case.Pr)
         opts = OracleOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
-                          int(record_faces), 0, (C.c_double * 4)(*case.ghost_state))
+                          int(record_faces), 0, (C.c_double * 4)(*case.ghost_state), int(order))
         self.ctx = C.c_void_p()
         st = L.oracle_create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
                              C.c_double(case.Tw), C.c_double(case.cfl), C.c_int32(int(gts)), C.byref(opts),
@@ -218,6 +218,13 @@ class Oracle:
         out = np.zeros(8 * self.C)
         lib().oracle_get_cell_data(self.ctx, dptr(out))
         return out.reshape(self.C, 8)
+
+    def gradients(self):
+        """Order 2: per cell the limited gradients (d/dx, d/dy) of the 4 components of W then of W^h, from the
+        last step's decomposition (C x 8 x 2)."""
+        out = np.zeros(16 * self.C)
+        self._check(lib().oracle_get_gradients(self.ctx, dptr(out)))
+        return out.reshape(self.C, 8, 2)
 
     def flux(self):
         out = np.zeros(4 * self.F)

@@ -42,6 +42,7 @@ typedef struct {
                               * 1 for R -> L, as fixed-point integers of the mass exponent */
     int32_t capacity;        /* particle capacity; 0 = 4 * n_ref * cells */
     double ghost_state[4];   /* (rho, U, V, T) of BC_FIXED ghosts */
+    int32_t order;           /* 2: second-order reconstruction of W and W^h (S6); 0 or 1: first order */
 } oracle_opts;
 
 int  oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, double Ma, double Tw,
@@ -67,6 +68,7 @@ int  oracle_set_time_steps(oracle_ctx* cx, const double* dt);       /* C local s
 int  oracle_get_tallies(oracle_ctx* cx, int64_t* wm, int64_t* wpl, int64_t* wret, int64_t* cross,
                         int64_t* wall, int64_t* frec);
 int  oracle_get_cell_data(oracle_ctx* cx, double* out);            /* [8 per cell] see oracle_core.c */
+int  oracle_get_gradients(oracle_ctx* cx, double* out);             /* [16 per cell], order 2, see oracle_core.c */
 int  oracle_get_flux(oracle_ctx* cx, double* flux);                 /* [4 per face], global frame */
 int  oracle_get_geometry(oracle_ctx* cx, double* dt, double* vol, int32_t* nfaces, int32_t* nwall);
 int  oracle_fixed_exponents(oracle_ctx* cx, int32_t* out);          /* [3] mass, momentum, energy */

@@ -219,9 +219,14 @@ static void pr_fix(const or_prim* p, double a[4], double Pr)
  * on a ghost side or without particles). Returns W_0 and the slopes for the pins. */
 static void face_flux(const double WL[4], const double WR[4], const double WhL[4], const double WhR[4],
                       int hL, int hR, const double cL[7], const double cR[7], double frL, double frR,
-                      double dL, double dR, double Pr, double F[4], double W0o[4], double aLo[4],
-                      double aRo[4], double Ao[4])
+                      double dL, double dR, double Pr, const double WLc[4], const double WRc[4],
+                      const double dhL[4], const double dhR[4], double csL, double csR, double F[4],
+                      double W0o[4], double aLo[4], double aRo[4], double Ao[4])
 {
+    /* WL, WR: the states at the face (the cell states in first order); WLc, WRc: the cell states the
+     * normal slopes of g_0 are taken against (S7), NULL for WL, WR */
+    if (!WLc) WLc = WL;
+    if (!WRc) WRc = WR;
     or_prim pL, pR, p0, phL, phR;
     or_mom mL, mR, m0, mhL, mhR;
     frame_prim(WL, &pL);
@@ -241,8 +246,8 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
     moments(&p0, &m0);
     double dwL[4], dwR[4], aL[4], aR[4], dA[4], A[4];
     for (int k = 0; k < 4; ++k) {
-        dwL[k] = (W0[k] - WL[k]) / (dL * p0.rho);
-        dwR[k] = (WR[k] - W0[k]) / (dR * p0.rho);
+        dwL[k] = (W0[k] - WLc[k]) / (dL * p0.rho);
+        dwR[k] = (WRc[k] - W0[k]) / (dR * p0.rho);
     }
     micro_slope(&p0, dwL, aL);
     micro_slope(&p0, dwR, aR);
@@ -267,15 +272,32 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
     if (aRo) for (int k = 0; k < 4; ++k) aRo[k] = aR[k];
     if (Ao) for (int k = 0; k < 4; ++k) Ao[k] = A[k];
 free_transport:
+    /* free transport of the hydrodynamic wave (Eq. 50): g^h of each side over its half, and with a
+     * second-order reconstruction (Eq. 12) its normal slope term weighted with csL / csR (dhL, dhR: normal
+     * derivatives of W^h in the face frame, NULL for none) */
     if (hL && frame_prim(WhL, &phL)) {
         moments(&phL, &mhL);
         psi_mom(mhL.up, &mhL, 1, 0, 0, t1);
         for (int k = 0; k < 4; ++k) F[k] += frL * phL.rho * t1[k];
+        if (dhL) {
+            double dw[4], a[4];
+            for (int k = 0; k < 4; ++k) dw[k] = dhL[k] / phL.rho;
+            micro_slope(&phL, dw, a);
+            psi_poly_mom(mhL.up, &mhL, 2, 0, a, t1);
+            for (int k = 0; k < 4; ++k) F[k] += csL * phL.rho * t1[k];
+        }
     }
     if (hR && frame_prim(WhR, &phR)) {
         moments(&phR, &mhR);
         psi_mom(mhR.um, &mhR, 1, 0, 0, t2);
         for (int k = 0; k < 4; ++k) F[k] += frR * phR.rho * t2[k];
+        if (dhR) {
+            double dw[4], a[4];
+            for (int k = 0; k < 4; ++k) dw[k] = dhR[k] / phR.rho;
+            micro_slope(&phR, dw, a);
+            psi_poly_mom(mhR.um, &mhR, 2, 0, a, t2);
+            for (int k = 0; k < 4; ++k) F[k] += csR * phR.rho * t2[k];
+        }
     }
 }
 
@@ -283,7 +305,8 @@ void oracle_face_flux_test(const double* WL, const double* WR, const double* WhL
                            const double* cL, const double* cR, double dL, double dR, double Pr,
                            double* F, double* W0, double* aL, double* aR, double* A)
 {
-    face_flux(WL, WR, WhL, WhR, WhL != NULL, WhR != NULL, cL, cR, cL[5], cR[5], dL, dR, Pr, F, W0, aL, aR, A);
+    face_flux(WL, WR, WhL, WhR, WhL != NULL, WhR != NULL, cL, cR, cL[5], cR[5], dL, dR, Pr, NULL, NULL, NULL, NULL,
+              0.0, 0.0, F, W0, aL, aR, A);
 }
 
 /* diffuse isothermal wall (reading): incoming half of the fluid cell's g and g^h, outgoing wall
@@ -588,6 +611,7 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     if (st) { oracle_destroy(cx); return st; }
     const int C = cx->C, F = cx->F;
     cx->prec = opts->precision; cx->wave_only = opts->wave_only; cx->record_faces = opts->record_faces;
+    cx->order = opts->order == 2 ? 2 : 1;
     cx->gts = gts; cx->n_ref = opts->n_ref; cx->seed = opts->seed; cx->case_id = opts->case_id;
     cx->Kn = Kn; cx->Ma = Ma; cx->Tw = Tw; cx->cfl = cfl; cx->omega = gas->omega; cx->Pr = gas->Pr;
     cx->mu_inf = oracle_mu_inf(Kn, gas->omega);
@@ -613,7 +637,7 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     cx->W = zalloc(4 * C, 8); cx->wret_prev = zalloc(5 * C, 8);
     cx->tau = zalloc(C, 8); cx->xr_t = zalloc(C, 8); cx->emx = zalloc(C, 8);
     cx->Wp = zalloc(4 * C, 8); cx->Wh = zalloc(4 * C, 8); cx->mnew = zalloc(C, 8); cx->co = zalloc(7 * C, 8);
-    cx->samp = zalloc(3 * C, 8);
+    cx->samp = zalloc(3 * C, 8); cx->grad = zalloc(16 * (size_t)C, 8);
     cx->whq = zalloc(9 * C, 8); cx->hq = zalloc(3 * C, 8);
     cx->nhp = zalloc(C, 4); cx->hphys = zalloc(C, 4); cx->nhp_off = zalloc(C + 1, 8);
     cx->wm = zalloc(5 * C, 8); cx->wpl = zalloc(5 * C, 8); cx->wrt = zalloc(5 * C, 8);
@@ -636,7 +660,7 @@ void oracle_destroy(oracle_ctx* cx)
                     cx->cbc, cx->cnx, cx->cny, cx->cd, cx->cshift, cx->cvx, cx->cvy, cx->xl, cx->xr, cx->fL,
                     cx->fR, cx->fbc, cx->fwall, cx->fnx, cx->fny, cx->fs, cx->fdL, cx->fdR, cx->finv_s,
                     cx->wall_face, cx->dt, cx->ratio, cx->W, cx->wret_prev, cx->tau, cx->xr_t, cx->emx, cx->Wp,
-                    cx->Wh, cx->mnew, cx->co, cx->samp, cx->nhp, cx->hphys, cx->nhp_off, cx->wm, cx->wpl,
+                    cx->Wh, cx->mnew, cx->co, cx->samp, cx->grad, cx->nhp, cx->hphys, cx->nhp_off, cx->wm, cx->wpl,
                     cx->wrt, cx->cross, cx->wallt, cx->frec, cx->flux, cx->chi_ema, cx->surf_sum,
                     cx->surf_last, cx->p, cx->whq, cx->hq, cx->fax, cx->fay, cx->fex, cx->fey,
                     cx->inj_face, cx->inj_k, cx->inj_n, cx->inj_m, cx->inj_u, cx->inj_v, cx->inj_sig,
@@ -793,6 +817,105 @@ static void inject_params(or_ctx* cx)
     }
 }
 
+/* ----------------------------------------------------------- a8: reconstruction (order 2, S6 reading) */
+
+/* van Leer's limited slope from two one-sided differences */
+static double van_leer(double a, double b) { return a * b > 0.0 ? (2.0 * a * b) / (a + b) : 0.0; }
+
+/* Limited gradients (d/dx, d/dy) of the four components of W (v = 0..3) and of W^h (v = 4..7) per cell.
+ * 1-D: van Leer's limiter of the one-sided slopes to the two neighbours (zero next to a boundary face).
+ * 2-D: least-squares gradient over the neighbours across interior and periodic faces, weights 1 / |dx|^2
+ * (zero with fewer than two neighbours), then Barth and Jespersen's limiter: one factor per component so that
+ * the reconstruction at every face midpoint of the cell stays within the values of the cell and those
+ * neighbours. */
+static void gradients(or_ctx* cx)
+{
+    for (int c = 0; c < cx->C; ++c) {
+        double* g = cx->grad + 16 * (size_t)c;
+        for (int v = 0; v < 8; ++v) {
+            const double* A = v < 4 ? cx->W : cx->Wh;
+            const int comp = v & 3;
+            const double vc = A[4 * c + comp];
+            double gx = 0.0, gy = 0.0;
+            if (cx->dim == 1) {
+                const int ql = 4 * c, qr = 4 * c + 1, nl = cx->cnbr[ql], nr = cx->cnbr[qr];
+                if (nl >= 0 && nr >= 0) {
+                    /* a neighbour across a periodic face, in this cell's frame */
+                    const double xl = cx->xc[nl] - cx->cshift[ql], xr = cx->xc[nr] - cx->cshift[qr];
+                    gx = van_leer((vc - A[4 * nl + comp]) / (cx->xc[c] - xl), (A[4 * nr + comp] - vc) / (xr - cx->xc[c]));
+                }
+            } else {
+                double a11 = 0.0, a12 = 0.0, a22 = 0.0, b1 = 0.0, b2 = 0.0, vmax = vc, vmin = vc;
+                int nn = 0;
+                for (int k = 0; k < cx->nfc[c]; ++k) {
+                    const int nb = cx->cnbr[4 * c + k];
+                    if (nb < 0) continue;
+                    const double dx = cx->xc[nb] - cx->xc[c], dy = cx->yc[nb] - cx->yc[c];
+                    const double w = 1.0 / (dx * dx + dy * dy), dv = A[4 * nb + comp] - vc;
+                    a11 += w * dx * dx; a12 += w * dx * dy; a22 += w * dy * dy;
+                    b1 += w * dx * dv; b2 += w * dy * dv;
+                    if (A[4 * nb + comp] > vmax) vmax = A[4 * nb + comp];
+                    if (A[4 * nb + comp] < vmin) vmin = A[4 * nb + comp];
+                    nn++;
+                }
+                const double det = a11 * a22 - a12 * a12;
+                if (nn >= 2 && det > 1e-12 * (a11 * a22)) {
+                    gx = (a22 * b1 - a12 * b2) / det;
+                    gy = (a11 * b2 - a12 * b1) / det;
+                    double phi = 1.0;
+                    for (int k = 0; k < cx->nfc[c]; ++k) {
+                        const int f = cx->cface[4 * c + k];
+                        const double mx = cx->fax[f] + 0.5 * cx->fex[f], my = cx->fay[f] + 0.5 * cx->fey[f];
+                        const double d2 = gx * (mx - cx->xc[c]) + gy * (my - cx->yc[c]);
+                        double r = 1.0;
+                        if (d2 > 0.0) r = (vmax - vc) / d2;
+                        else if (d2 < 0.0) r = (vmin - vc) / d2;
+                        if (r < phi) phi = r;
+                    }
+                    gx *= phi;
+                    gy *= phi;
+                }
+            }
+            g[2 * v] = gx;
+            g[2 * v + 1] = gy;
+        }
+    }
+}
+
+/* Order 2: the state of cell c's W (which = 0) or W^h (which = 1) at face f (its local face k), W_c + grad .
+ * (x_f - x_c) with x_f the face point (1-D) or midpoint (2-D), and the normal derivative n . grad, both in
+ * the face frame (n, t). Returns 0 (first order for this side) when the reconstructed state is not a
+ * positive density and internal energy. */
+static int face_side(const or_ctx* cx, int c, int k, int f, int which, double Wf[4], double dn[4])
+{
+    const double* g = cx->grad + 16 * (size_t)c + 8 * which;
+    const double* Wc = (which ? cx->Wh : cx->W) + 4 * c;
+    double ddx, ddy;
+    if (cx->dim == 1) {
+        ddx = (k == 0 ? cx->xl[c] : cx->xr[c]) - cx->xc[c];   /* local face 0: left end, 1: right end */
+        ddy = 0.0;
+    } else {
+        ddx = (cx->fax[f] + 0.5 * cx->fex[f]) - cx->xc[c];
+        ddy = (cx->fay[f] + 0.5 * cx->fey[f]) - cx->yc[c];
+    }
+    double W[4], d[4];
+    for (int q = 0; q < 4; ++q) {
+        W[q] = Wc[q] + (g[2 * q] * ddx + g[2 * q + 1] * ddy);
+        d[q] = g[2 * q] * cx->fnx[f] + g[2 * q + 1] * cx->fny[f];
+    }
+    if (!(W[0] > 0.0) || !(W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0] > 0.0)) return 0;
+    to_frame(W, cx->fnx[f], cx->fny[f], Wf);
+    to_frame(d, cx->fnx[f], cx->fny[f], dn);
+    return 1;
+}
+
+static int local_face(const or_ctx* cx, int c, int f)
+{
+    for (int k = 0; k < cx->nfc[c]; ++k)
+        if (cx->cface[4 * c + k] == f) return k;
+    return -1;
+}
+
 static void wave_fluxes(or_ctx* cx)
 {
     for (int f = 0; f < cx->F; ++f) {
@@ -803,20 +926,48 @@ static void wave_fluxes(or_ctx* cx)
         to_frame(cx->Wh + 4 * L, nx, ny, WhL);
         const double* cL = cx->co + 7 * L;
         const double frL = cx->wave_only ? cL[3] : cL[5];
+        /* order 2 (S6): reconstructed face states of W (equilibrium part) and W^h (free-transport wave, with
+         * its normal slope term weighted with dbar_e, or dbar_e + dt e^{-x} / 2 when the collisionless part is
+         * carried by particles, Eq. 50) on interior, periodic and far-field / fixed faces */
+        const int o2 = cx->order == 2 && (bc == 0 || bc == OR_BC_PERIODIC || bc == OR_BC_FARFIELD || bc == OR_BC_FIXED);
+        double dhL[4], dhR[4], dtmp[4], WLc[4], WRc[4];
+        int sL = 0, sR = 0;
+        for (int q = 0; q < 4; ++q) WLc[q] = WL[q];
+        const double csL = cx->wave_only ? cL[4] : cL[6];
+        if (o2) {
+            const int kL = local_face(cx, L, f);
+            double Wf[4];
+            if (face_side(cx, L, kL, f, 0, Wf, dtmp)) for (int q = 0; q < 4; ++q) WL[q] = Wf[q];
+            if (cx->hphys[L] && face_side(cx, L, kL, f, 1, Wf, dhL)) {
+                for (int q = 0; q < 4; ++q) WhL[q] = Wf[q];
+                sL = 1;
+            }
+        }
         if (bc == 0 || bc == OR_BC_PERIODIC) {
             to_frame(cx->W + 4 * R, nx, ny, WR);
             to_frame(cx->Wh + 4 * R, nx, ny, WhR);
+            for (int q = 0; q < 4; ++q) WRc[q] = WR[q];
             const double* cR = cx->co + 7 * R;
             const double frR = cx->wave_only ? cR[3] : cR[5];
+            if (o2) {
+                const int kR = local_face(cx, R, f);
+                double Wf[4];
+                if (face_side(cx, R, kR, f, 0, Wf, dtmp)) for (int q = 0; q < 4; ++q) WR[q] = Wf[q];
+                if (cx->hphys[R] && face_side(cx, R, kR, f, 1, Wf, dhR)) {
+                    for (int q = 0; q < 4; ++q) WhR[q] = Wf[q];
+                    sR = 1;
+                }
+            }
             face_flux(WL, WR, WhL, WhR, cx->hphys[L], cx->hphys[R], cL, cR, frL, frR, cx->fdL[f], cx->fdR[f],
-                      cx->Pr, F, NULL, NULL, NULL, NULL);
+                      cx->Pr, WLc, WRc, sL ? dhL : NULL, sR ? dhR : NULL, csL, cx->wave_only ? cR[4] : cR[6], F,
+                      NULL, NULL, NULL, NULL);
         } else if (bc == OR_BC_WALL) {
             wall_flux(cx, WL, WhL, cx->hphys[L], cL, frL, F);
         } else if (bc == OR_BC_SYMMETRY) {
             /* mirror ghost: same state with the normal velocity reversed, same coefficients */
             double Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
             face_flux(WL, Wm, WhL, Whm, cx->hphys[L], cx->hphys[L], cL, cL, frL, frL, cx->fdL[f], cx->fdL[f],
-                      cx->Pr, F, NULL, NULL, NULL, NULL);
+                      cx->Pr, NULL, NULL, NULL, NULL, 0.0, 0.0, F, NULL, NULL, NULL, NULL);
         } else {
             /* far-field / fixed ghost: a virtual cell of the ghost state with the fluid cell's time step
              * (Sec. IV B). Its collisionless part e^{-x} enters as particles (ghost sources, see the particle
@@ -828,7 +979,7 @@ static void wave_fluxes(or_ctx* cx)
             double cR[7];
             lts_coeffs(cx->dt[L], tau_of(cx, Wg), or_expd(-cx->dt[L] / tau_of(cx, Wg)), cR);
             face_flux(WL, WR, WhL, WR, cx->hphys[L], 1, cL, cR, frL, cx->wave_only ? cR[3] : cR[5], cx->fdL[f],
-                      cx->fdL[f], cx->Pr, F, NULL, NULL, NULL, NULL);
+                      cx->fdL[f], cx->Pr, WLc, NULL, sL ? dhL : NULL, NULL, csL, 0.0, F, NULL, NULL, NULL, NULL);
         }
         /* non-finite flux (reading): extreme near-vacuum neighbours can make the interface density underflow
          * against its neighbours' and the slopes overflow; such a face carries no wave flux */
@@ -929,7 +1080,9 @@ static int one_step(or_ctx* cx)
     if (cx->err) return cx->err;
     inject_params(cx);
     if (cx->prec == 0) or_particles_step_f32(cx); else or_particles_step_f64(cx);
-    /* step 3: wave fluxes from the step-start W and W^h, then the conservative update (Eq. 53) */
+    /* step 3: wave fluxes from the step-start W and W^h (order 2: reconstructed, S6), then the conservative
+     * update (Eq. 53) */
+    if (cx->order == 2) gradients(cx);
     wave_fluxes(cx);
     update(cx);
     surface(cx);
@@ -1095,6 +1248,13 @@ int oracle_get_cell_data(oracle_ctx* cx, double* out)
         o[0] = cx->tau[c]; o[1] = cx->xr_t[c]; o[2] = cx->emx[c]; o[3] = (double)cx->nhp[c];
         o[4] = cx->mnew[c]; o[5] = cx->samp[3 * c]; o[6] = cx->samp[3 * c + 1]; o[7] = cx->samp[3 * c + 2];
     }
+    return OR_OK;
+}
+
+int oracle_get_gradients(oracle_ctx* cx, double* out)
+{
+    if (!cx || !out) return OR_EINVAL;
+    memcpy(out, cx->grad, 16 * (size_t)cx->C * 8);
     return OR_OK;
 }
 

@@ -28,7 +28,7 @@ typedef struct {
 struct oracle_ctx {
     /* configuration */
     int dim, ni, nj, periodic_j, C, F;
-    int prec, wave_only, record_faces, gts, n_ref;
+    int prec, wave_only, record_faces, gts, n_ref, order;
     uint64_t seed;
     uint32_t case_id;
     int64_t step;
@@ -63,6 +63,8 @@ struct oracle_ctx {
     /* per-step cell data */
     double *tau, *xr_t, *emx, *Wp, *Wh, *mnew, *co;   /* co: [7C] normalised coefficients */
     double* samp;                                /* [3C] U^h, V^h, R T^h for sampling */
+    double* grad;                                /* [16C] order 2: limited gradients (d/dx, d/dy) of the 4
+                                                  * components of W, then of W^h (S6) */
     int64_t* whq;                                /* [9C] retained particles: m (1, u, v, uu, uv, vv, q, uq, vq),
                                                   * q = |u|^2, fixed point (Pr != 1) */
     double* hq;                                  /* [3C] A-R weights a_x, a_y and bound M (Pr != 1) */

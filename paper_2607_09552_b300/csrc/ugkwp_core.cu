@@ -531,6 +531,70 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     d.cur[c] = 0;
 }
 
+// ------------------------------------------------- a8: second-order reconstruction (order 2)
+// Limited gradients (d/dx, d/dy) of the four components of W (v = 0..3) and W^h (v = 4..7) of one cell (FP64).
+// 1-D: van Leer's limiter of the one-sided slopes to the two neighbours (zero next to a boundary face).
+// 2-D: least-squares gradient over the neighbours across interior and periodic faces, weights 1 / |dx|^2
+// (zero with fewer than two), then Barth and Jespersen's limiter: one factor per component keeping the
+// reconstruction at every face midpoint within the values of the cell and those neighbours.
+__device__ __forceinline__ double van_leer(double a, double b) { return a * b > 0.0 ? (2.0 * a * b) / (a + b) : 0.0; }
+
+__global__ void k_gradients(const StepConsts K, Dev d)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K.C) return;
+    const CellFaces<double>& F = d.cf64[c];
+    const int nf = d.nfc[c];
+    double* g = d.grad + 16 * (size_t)c;
+    for (int v = 0; v < 8; ++v) {
+        const double* A = v < 4 ? d.W : d.Wh;
+        const int comp = v & 3;
+        const double vc = A[4 * c + comp];
+        double gx = 0.0, gy = 0.0;
+        if (K.dim == 1) {
+            const int nl = F.nbr[0], nr = F.nbr[1];
+            if (nl >= 0 && nr >= 0) {
+                // a neighbour across a periodic face, in this cell's frame
+                const double xl = d.xc[nl] - d.cshift[4 * c], xr = d.xc[nr] - d.cshift[4 * c + 1];
+                gx = van_leer((vc - A[4 * nl + comp]) / (d.xc[c] - xl), (A[4 * nr + comp] - vc) / (xr - d.xc[c]));
+            }
+        } else {
+            double a11 = 0.0, a12 = 0.0, a22 = 0.0, b1 = 0.0, b2 = 0.0, vmax = vc, vmin = vc;
+            int nn = 0;
+            for (int k = 0; k < nf; ++k) {
+                const int nb = F.nbr[k];
+                if (nb < 0) continue;
+                const double dx = d.xc[nb] - d.xc[c], dy = d.yc[nb] - d.yc[c];
+                const double w = 1.0 / (dx * dx + dy * dy), dv = A[4 * nb + comp] - vc;
+                a11 += w * dx * dx; a12 += w * dx * dy; a22 += w * dy * dy;
+                b1 += w * dx * dv; b2 += w * dy * dv;
+                if (A[4 * nb + comp] > vmax) vmax = A[4 * nb + comp];
+                if (A[4 * nb + comp] < vmin) vmin = A[4 * nb + comp];
+                nn++;
+            }
+            const double det = a11 * a22 - a12 * a12;
+            if (nn >= 2 && det > 1e-12 * (a11 * a22)) {
+                gx = (a22 * b1 - a12 * b2) / det;
+                gy = (a11 * b2 - a12 * b1) / det;
+                double phi = 1.0;
+                for (int k = 0; k < nf; ++k) {
+                    const int f = F.meta[k] & 0xffffff;
+                    const double mx = d.fax[f] + 0.5 * d.fex[f], my = d.fay[f] + 0.5 * d.fey[f];
+                    const double d2 = gx * (mx - d.xc[c]) + gy * (my - d.yc[c]);
+                    double r = 1.0;
+                    if (d2 > 0.0) r = (vmax - vc) / d2;
+                    else if (d2 < 0.0) r = (vmin - vc) / d2;
+                    if (r < phi) phi = r;
+                }
+                gx *= phi;
+                gy *= phi;
+            }
+        }
+        g[2 * v] = gx;
+        g[2 * v + 1] = gy;
+    }
+}
+
 // per-step zeroing of face crossings, wall tallies and counters; the sort flag of this step
 __global__ void k_begin_step(const StepConsts K, Dev d)
 {
@@ -1468,6 +1532,7 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     }
     k_decompose<<<nblk(C, 128), 128, 0, s>>>(K, d);
     exclusive_scan(d.nhp, d.nhp_off, d.scan_tmp, C, d.counts + 1, s, d.counts, d.err);
+    if (K.order == 2) k_gradients<<<nblk(C, 128), 128, 0, s>>>(K, d);
     mark(1, s);
     // the wave fluxes depend only on the decomposition: they run on a second stream, alongside the
     // particle kernels, and join before the update
@@ -1553,6 +1618,10 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     *out = nullptr;
     ctx.stream = static_cast<cudaStream_t>(opts->stream);
     ctx.use_graph = opts->use_graph;
+    if (opts->order != 0 && opts->order != 1 && opts->order != 2) {
+        delete h;
+        return UGKWP_EINVAL;
+    }
     if (cudaStreamCreateWithFlags(&ctx.stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx.ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -1571,6 +1640,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     StepConsts& K = ctx.k;
     K.C = C; K.F = F; K.dim = mesh->dim; K.n_ref = opts->n_ref; K.wave_only = opts->wave_only;
     K.prec = opts->precision ? 1 : 0;
+    K.order = opts->order == 2 ? 2 : 1;
     K.omega = gas->omega; K.Pr = gas->Pr; K.Tw = Tw;
     K.shakhov = gas->Pr != 1.0 && !opts->wave_only;
     K.mu_inf = (15.0 * sqrt(2.0 * 3.14159265358979323846 * 0.5) * Kn) / (2.0 * (5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega));
@@ -1761,6 +1831,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         CK(dalloc(ctx, &d.tau32, C)); CK(dalloc(ctx, &d.dt32, C)); CK(dalloc(ctx, &d.mnew32, C));
         CK(dalloc(ctx, &d.emx32, C));
         if (opts->record_faces && !K.wave_only) CK(dalloc(ctx, &d.frec, 4 * (size_t)F));
+        if (K.order == 2) CK(dalloc(ctx, &d.grad, 16 * (size_t)C));
         CK(dalloc(ctx, &d.samp32, 3 * C));
         CK(dalloc(ctx, &d.dstep, 1));
         int sms = 148;

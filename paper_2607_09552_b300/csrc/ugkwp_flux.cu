@@ -6,12 +6,13 @@
 //     (Eq. 20 with the Prandtl fix of Sec. III A), and A from the compatibility condition (Eq. 22); each half
 //     weighted with its own cell's normalised coefficients dbar_{a,b,c} (Eq. 48).
 //   F^fr,wave: the hydrodynamic wave's Maxwellian g^h of each side over its half, weighted with
-//     dbar_d - e^{-dt/tau} (the part not carried by new particles, Eq. 50); first-order reconstruction, so
-//     the slope term of Eq. 50 vanishes.
+//     dbar_d - e^{-dt/tau} (the part not carried by new particles, Eq. 50). First order by default; with the
+//     second-order reconstruction (Eq. 12, order 2) the states at the face are reconstructed from limited
+//     cell gradients and g^h adds its normal slope term, weighted with dbar_e + dt e^{-x} / 2.
 //  Boundary faces (n points out of the fluid cell L): a diffuse wall returns a wall Maxwellian at T_w with
-//  the density that zeroes the wave mass flux; far-field / fixed ghosts carry their full free-transport
-//  part (no particles are injected) and use the fluid cell's time step on both halves (Sec. IV B); a
-//  symmetry face mirrors L.
+//  the density that zeroes the wave mass flux (first order); far-field / fixed ghosts are virtual cells of
+//  the ghost state with the fluid cell's time step on both halves (Sec. IV B), whose collisionless part
+//  enters as particles, so their wave keeps dbar_d - e^{-x}; a symmetry face mirrors L (first order).
 //  The moment algebra is a dense 4x4 closed form per face, so it runs on the FP32/FP64 pipes. In production
 //  mode the velocity moments are FP32; the faces of wall cells (flag face_f64) weight them with their FP64
 //  time integrals and sum in FP64.
@@ -157,11 +158,14 @@ __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], co
     for (int k = 0; k < 4; ++k) F[k] = C(p0.rho) * (F[k] + cR[2] * C(f[k]));
 }
 
-// interior-type face; frL/frR weight each side's g^h. Returns false if a side state is not a valid
-// Maxwellian in precision R (the caller then uses FP64).
+// interior-type face; frL/frR weight each side's g^h. WL, WR: the states at the face (the cell states in
+// first order), WLc, WRc: the cell states the normal slopes of g_0 are taken against; dhL, dhR (nullable):
+// normal derivatives of W^h for the slope term of the free-transport wave, weighted with csL, csR (order 2).
+// Returns false if a side state is not a valid Maxwellian in precision R (the caller then uses FP64).
 template <typename R, typename C>
 __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], bool hL, bool hR,
-                          const C cL[3], const C cR[3], C frL, C frR, R dL, R dR, R Pr, C F[4])
+                          const C cL[3], const C cR[3], C frL, C frR, R dL, R dR, R Pr, const R WLc[4],
+                          const R WRc[4], const R* dhL, const R* dhR, C csL, C csR, C F[4])
 {
     Prim<R> pL, pR, p0;
     Mom<R> mL, mR;
@@ -176,7 +180,7 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
 #pragma unroll
     for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];
     // vacuum interface: no molecule of either side reaches the face, no equilibrium flux
-    if (frame_prim(W0, p0)) equilibrium_part(W0, WL, WR, p0, cL, cR, dL, dR, Pr, F);
+    if (frame_prim(W0, p0)) equilibrium_part(W0, WLc, WRc, p0, cL, cR, dL, dR, Pr, F);
     R f[4];
     Prim<R> ph;
     Mom<R> mh;
@@ -185,12 +189,30 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
         psi_mom(mh.up, mh, 1, 0, 0, f);
 #pragma unroll
         for (int k = 0; k < 4; ++k) F[k] += frL * C(ph.rho * f[k]);
+        if (dhL) {
+            R dw[4], a[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dw[k] = dhL[k] / ph.rho;
+            slope(ph, dw, a);
+            psi_poly(mh.up, mh, 2, 0, a, f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) F[k] += csL * C(ph.rho * f[k]);
+        }
     }
     if (hR && frame_prim(WhR, ph)) {
         moments(ph, mh);
         psi_mom(mh.um, mh, 1, 0, 0, f);
 #pragma unroll
         for (int k = 0; k < 4; ++k) F[k] += frR * C(ph.rho * f[k]);
+        if (dhR) {
+            R dw[4], a[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dw[k] = dhR[k] / ph.rho;
+            slope(ph, dw, a);
+            psi_poly(mh.um, mh, 2, 0, a, f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) F[k] += csR * C(ph.rho * f[k]);
+        }
     }
     return true;
 }
@@ -264,6 +286,32 @@ __device__ double tau_of(const StepConsts& K, const double W[4])
     return mu / (rho * RT);
 }
 
+// Order 2: the state of cell cc's W (which = 0) or W^h (which = 1) at face f, W_c + grad . (x_f - x_c) with x_f
+// the face point (1-D: the cell end of its local face) or midpoint (2-D), and the normal derivative n . grad, in
+// the global frame; false (first order for this side) when the reconstructed state is not a positive density
+// and internal energy.
+__device__ bool face_side(const StepConsts& K, const Dev& c, int cc, int f, int which, double nx, double ny,
+                          double Wf[4], double dn[4])
+{
+    const double* g = c.grad + 16 * (size_t)cc + 8 * which;
+    const double* Wc = (which ? c.Wh : c.W) + 4 * cc;
+    double ddx, ddy;
+    if (K.dim == 1) {
+        const int k = (c.cf64[cc].meta[0] & 0xffffff) == f ? 0 : 1;   // local face 0: left end, 1: right end
+        ddx = c.cvx[4 * cc + k] - c.xc[cc];
+        ddy = 0.0;
+    } else {
+        ddx = (c.fax[f] + 0.5 * c.fex[f]) - c.xc[cc];
+        ddy = (c.fay[f] + 0.5 * c.fey[f]) - c.yc[cc];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        Wf[q] = Wc[q] + (g[2 * q] * ddx + g[2 * q + 1] * ddy);
+        dn[q] = g[2 * q] * nx + g[2 * q + 1] * ny;
+    }
+    return Wf[0] > 0.0 && Wf[3] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2]) / Wf[0] > 0.0;
+}
+
 template <typename R, typename C>
 __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4])
 {
@@ -277,28 +325,59 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         o[2] = -a * nyr + b * nxr;
         o[3] = R(W[3]);
     };
-    R WL[4], WhL[4], WR[4], WhR[4];
+    R WL[4], WhL[4], WR[4], WhR[4], WLc[4], WRc[4], dhL[4], dhR[4];
     C F[4];
     bool ok;
     rot(c.W + 4 * L, WL);
     rot(c.Wh + 4 * L, WhL);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) WLc[q] = WL[q];
     const double* coL = c.co + 7 * L;
     const C cL[3] = {C(coL[0]), C(coL[1]), C(coL[2])};
     const C frL = C(K.wave_only ? coL[3] : coL[5]);
     const bool hL = c.hphys[L] != 0;
+    // order 2: reconstructed face states of W (equilibrium part) and W^h (free-transport wave with its normal
+    // slope term, weighted with dbar_e, or dbar_e + dt e^{-x} / 2 when the collisionless part is carried by
+    // particles, Eq. 50) on interior, periodic and far-field / fixed faces
+    const bool o2 = K.order == 2 && (bc == 0 || bc == UGKWP_BC_PERIODIC || bc == UGKWP_BC_FARFIELD ||
+                                     bc == UGKWP_BC_FIXED);
+    bool sL = false, sR = false;
+    const C csL = C(K.wave_only ? coL[4] : coL[6]);
+    if (o2) {
+        double Wf[4], dn[4];
+        if (face_side(K, c, L, f, 0, nx, ny, Wf, dn)) rot(Wf, WL);
+        if (hL && face_side(K, c, L, f, 1, nx, ny, Wf, dn)) {
+            rot(Wf, WhL);
+            rot(dn, dhL);
+            sL = true;
+        }
+    }
     if (bc == 0 || bc == UGKWP_BC_PERIODIC) {
         rot(c.W + 4 * Rc, WR);
         rot(c.Wh + 4 * Rc, WhR);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) WRc[q] = WR[q];
         const double* coR = c.co + 7 * Rc;
         const C cR[3] = {C(coR[0]), C(coR[1]), C(coR[2])};
         const C frR = C(K.wave_only ? coR[3] : coR[5]);
-        ok = face_flux<R, C>(WL, WR, WhL, WhR, hL, c.hphys[Rc] != 0, cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]),
-                             R(K.Pr), F);
+        const bool hR = c.hphys[Rc] != 0;
+        if (o2) {
+            double Wf[4], dn[4];
+            if (face_side(K, c, Rc, f, 0, nx, ny, Wf, dn)) rot(Wf, WR);
+            if (hR && face_side(K, c, Rc, f, 1, nx, ny, Wf, dn)) {
+                rot(Wf, WhR);
+                rot(dn, dhR);
+                sR = true;
+            }
+        }
+        ok = face_flux<R, C>(WL, WR, WhL, WhR, hL, hR, cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]), R(K.Pr), WLc,
+                             WRc, sL ? dhL : nullptr, sR ? dhR : nullptr, csL, C(K.wave_only ? coR[4] : coR[6]), F);
     } else if (bc == UGKWP_BC_WALL) {
         ok = wall_flux<R, C>(WL, WhL, hL, cL[0], frL, R(0.5 / (kR * K.Tw)), F);
     } else if (bc == UGKWP_BC_SYMMETRY) {
         const R Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
-        ok = face_flux<R, C>(WL, Wm, WhL, Whm, hL, hL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), F);
+        ok = face_flux<R, C>(WL, Wm, WhL, Whm, hL, hL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), WL, Wm,
+                             nullptr, nullptr, C(0), C(0), F);
     } else {
         double Wg[4];
         if (bc == UGKWP_BC_FIXED) {
@@ -315,7 +394,7 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         ghost_coeffs(c.dt[L], tau_of(K, Wg), cg);
         const C cR[3] = {C(cg[0]), C(cg[1]), C(cg[2])};
         ok = face_flux<R, C>(WL, WR, WhL, WR, hL, true, cL, cR, frL, C(K.wave_only ? cg[3] : cg[4]), R(c.fdL[f]),
-                             R(c.fdL[f]), R(K.Pr), F);
+                             R(c.fdL[f]), R(K.Pr), WLc, WR, sL ? dhL : nullptr, nullptr, csL, C(0), F);
     }
     const C nxc = C(nx), nyc = C(ny);
     out[0] = double(F[0]);

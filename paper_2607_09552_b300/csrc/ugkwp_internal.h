@@ -39,6 +39,7 @@ struct StepConsts {
     int n_f64, sort_every;          // faces in f64list; counting sort of the particles every sort_every steps
     int chunk;                      // particles per dynamically claimed chunk of the transport kernel
     int n_inj;                      // ghost particle sources (far-field and fixed faces)
+    int order;                      // 2: second-order reconstruction for the wave fluxes
     double mu_inf, omega, Pr, Tw, U_inf, m2RTw, sig_w;
     double T_cap, U_cap, T_min;     // realizability bounds of a cell state
     double W_inf[4], W_fix[4];
@@ -74,6 +75,7 @@ struct Dev {
     // per-step cell data
     double *tau, *xr, *emx, *Wh, *co, *mnew;
     double* samp;                      // [3C] U^h, V^h, R T^h
+    double* grad;                      // [16C] order 2: limited gradients (d/dx, d/dy) of W's 4 components, then W^h's
     long long* whq;                    // [9C] Pr != 1: raw moments of the retained particles
     double* hq;                        // [3C] Pr != 1: acceptance-rejection weights a_x, a_y, M
     float* hq32;

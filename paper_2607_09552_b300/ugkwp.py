@@ -45,7 +45,7 @@ class UgkwpOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("case_id", C.c_uint32), ("n_ref", C.c_int32), ("precision", C.c_int32),
                 ("wave_only", C.c_int32), ("record_faces", C.c_int32), ("capacity", C.c_int32),
                 ("ghost_state", C.c_double * 4), ("stream", C.c_void_p), ("use_graph", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("order", C.c_int32)]
 
 
 _lib = None
@@ -105,7 +105,7 @@ class Solver:
 
     def __init__(self, case, gts: bool = False, precision: int = 0, wave_only: bool = False, seed: int | None = None,
                  case_id: int = 0, capacity: int = 0, use_graph: bool = False, stream=None,
-                 record_faces: bool = False):
+                 record_faces: bool = False, order: int = 1):
         L = load()
         m = case.mesh
         self._keep = [np.ascontiguousarray(m.xv, dtype=np.float64), np.ascontiguousarray(m.yv, dtype=np.float64)]
@@ -114,7 +114,8 @@ class Solver:
                          *[_p(a, C.c_int32) for a in self._keep[2:]])
         gas = UgkwpGas(case.omega, case.Pr)
         opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
-                         int(record_faces), capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream), int(use_graph), 0)
+                         int(record_faces), capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream),
+                         int(use_graph), int(order))
         self.ctx = C.c_void_p()
         st = L.ugkwp_create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
                             C.c_double(case.Tw), C.c_double(case.cfl), C.c_int32(GTS if gts else LTS), C.byref(opts),
