@@ -70,7 +70,12 @@ typedef struct {
 } ugkwp_mesh;
 
 /* VHS exponent (mu ~ T^omega) and Prandtl number (Prandtl fix of the wave slopes; 1 = BGK) */
-typedef struct { double omega, Pr; } ugkwp_gas;
+typedef struct {
+    double omega, Pr;
+    double wall_specular;     /* Maxwell wall: the fraction 1 - alpha of molecules (and of the incoming wave)
+                                 reflected specularly, the rest re-emitted diffusely at T_w; 0 = fully diffuse
+                                 (the default); in [0, 1] */
+} ugkwp_gas;
 
 typedef struct {
     uint64_t seed;            /* Philox key (low word xor case_id, high word) */

@@ -22,7 +22,7 @@ class OracleMesh(C.Structure):
 
 
 class OracleGas(C.Structure):
-    _fields_ = [("omega", C.c_double), ("Pr", C.c_double)]
+    _fields_ = [("omega", C.c_double), ("Pr", C.c_double), ("wall_specular", C.c_double)]
 
 
 class OracleOpts(C.Structure):
@@ -114,7 +114,7 @@ class Oracle:
         self._keep += [np.ascontiguousarray(a, dtype=np.int32) for a in (m.bc_imin, m.bc_imax, m.bc_jmin, m.bc_jmax)]
         mesh = OracleMesh(m.ni, m.nj, m.dim, m.periodic_j, dptr(self._keep[0]), dptr(self._keep[1]),
                           *[_p(a, C.c_int32) for a in self._keep[2:]])
-        gas = OracleGas(case.omega, case.Pr)
+        gas = OracleGas(case.omega, case.Pr, getattr(case, "wall_specular", 0.0))
         opts = OracleOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
                           int(record_faces), 0, (C.c_double * 4)(*case.ghost_state), int(order))
         self.ctx = C.c_void_p()

@@ -29,7 +29,10 @@ typedef struct {
     const int32_t* bc_jmax;  /* ni tags of the j = nj faces */
 } oracle_mesh;
 
-typedef struct { double omega, Pr; } oracle_gas;
+typedef struct {
+    double omega, Pr;
+    double wall_specular;    /* Maxwell wall: fraction 1 - alpha reflected specularly; 0 = fully diffuse */
+} oracle_gas;
 
 typedef struct {
     uint64_t seed;

@@ -330,7 +330,15 @@ static void wall_flux(const or_ctx* cx, const double WL[4], const double WhL[4],
     moments(&pw, &mw);
     psi_mom(mw.um, &mw, 1, 0, 0, o);
     const double rw = -F[0] / o[0];
-    for (int k = 0; k < 4; ++k) F[k] += rw * o[k];
+    if (cx->ws == 0.0) {
+        for (int k = 0; k < 4; ++k) F[k] += rw * o[k];
+        return;
+    }
+    /* Maxwell wall (reading, §8f f3): the fraction ws of the incoming half is reflected specularly (u_n -> -u_n:
+     * in the face frame the mass, tangential momentum and energy fluxes change sign, the normal momentum flux
+     * keeps it), the rest re-emitted diffusely at T_w with zero net mass */
+    const double sg[4] = {-1.0, 1.0, -1.0, -1.0}, a = 1.0 - cx->ws;
+    for (int k = 0; k < 4; ++k) F[k] = (F[k] + cx->ws * (sg[k] * F[k])) + a * (rw * o[k]);
 }
 
 static void to_frame(const double W[4], double nx, double ny, double out[4])
@@ -606,6 +614,7 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
 {
     if (!mesh || !gas || !opts || !out || mesh->ni <= 0 || mesh->nj <= 0) return OR_EINVAL;
     if (mesh->ni * (int64_t)mesh->nj >= (1 << 21)) return OR_EINVAL;
+    if (!(gas->wall_specular >= 0.0 && gas->wall_specular <= 1.0)) return OR_EINVAL;
     or_ctx* cx = zalloc(1, sizeof(or_ctx));
     int st = build_geometry(cx, mesh);
     if (st) { oracle_destroy(cx); return st; }
@@ -614,6 +623,7 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     cx->order = opts->order == 2 ? 2 : 1;
     cx->gts = gts; cx->n_ref = opts->n_ref; cx->seed = opts->seed; cx->case_id = opts->case_id;
     cx->Kn = Kn; cx->Ma = Ma; cx->Tw = Tw; cx->cfl = cfl; cx->omega = gas->omega; cx->Pr = gas->Pr;
+    cx->ws = gas->wall_specular;
     cx->mu_inf = oracle_mu_inf(Kn, gas->omega);
     cx->U_inf = Ma * sqrt((5.0 / 3.0) * OR_R * 1.0);
     cx->m2RTw = -2.0 * OR_R * Tw;

@@ -33,6 +33,7 @@ struct oracle_ctx {
     uint32_t case_id;
     int64_t step;
     double Kn, Ma, Tw, cfl, omega, Pr, mu_inf, U_inf;
+    double ws;                                   /* Maxwell wall: specular fraction 1 - alpha */
     double W_inf[4], W_fix[4];
     int fx[5];                                   /* fixed-point exponents: mass, momentum, energy; second and
                                                   * third velocity moments (Shakhov heat flux, Pr != 1) */

@@ -495,7 +495,9 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     d.tau[c] = tau;
     d.xr[c] = x;
     d.emx[c] = e;
-    if (K.prec == 0 && !d.wallcell[c]) lts_coeffs_f32((float)dt, (float)x, (float)e, d.co + 7 * c);
+    // order 2 weights the slope term of g^h with dbar_e + dt e^{-x} / 2, whose FP32 closed form loses too many
+    // digits to cancellation: FP64 coefficients for every cell then
+    if (K.prec == 0 && !d.wallcell[c] && K.order != 2) lts_coeffs_f32((float)dt, (float)x, (float)e, d.co + 7 * c);
     else lts_coeffs(dt, tau, e, d.co + 7 * c);
     const int phys = realizable(K, Wh);
     d.hphys[c] = phys;
@@ -898,7 +900,7 @@ __device__ __forceinline__ int first_exit(const CellFaces<T>& F, int nf, int ent
 // of face events.
 template <typename T>
 __device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict__ cf, const Rng& g, T s0, T s1, T s4,
-                                    T m2RTw, T sigw, T& x, T& y, T& u, T& v, T& w, T& m, T tr, int& c, int entry,
+                                    T m2RTw, T sigw, T ws, T& x, T& y, T& u, T& v, T& w, T& m, T tr, int& c, int entry,
                                     uint64_t pid, int& it, unsigned long long& n_cross, unsigned long long& n_hits)
 {
     int hits = 0;
@@ -938,16 +940,28 @@ __device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict
             entry = (meta >> 24) & 3;
             c = nb;
         } else if (bc == UGKWP_BC_WALL) {
-            T U[3];
-            Unif<T>::get(g, pid, draw_wall(hits), 3, U);
+            // Maxwell wall: specular reflection with probability ws (the hit's fourth uniform), else diffuse
+            // re-emission at T_w
+            T U[4];
+            Unif<T>::get(g, pid, draw_wall(hits), 4, U);
             const T nx = F.nx[kb], ny = F.ny[kb];
-            const T un = fsqrt_(m2RTw * dlog(U[0]));
-            const T rad = fsqrt_(T(-2) * dlog(U[1]));
-            T sn, cs;
-            dsincos2pi(U[2], &sn, &cs);
-            const T vt = sigw * (rad * cs), wz = sigw * (rad * sn);
-            const T tx = -ny, ty = nx;
-            const T uo = vt * tx - un * nx, vo = vt * ty - un * ny;
+            T uo, vo, wz;
+            if (ws > T(0) && U[3] < ws) {
+                const T t2 = T(2) * (nx * u + ny * v);
+                uo = u - t2 * nx;
+                vo = v - t2 * ny;
+                wz = w;
+            } else {
+                const T un = fsqrt_(m2RTw * dlog(U[0]));
+                const T rad = fsqrt_(T(-2) * dlog(U[1]));
+                T sn, cs;
+                dsincos2pi(U[2], &sn, &cs);
+                const T vt = sigw * (rad * cs);
+                const T tx = -ny, ty = nx;
+                wz = sigw * (rad * sn);
+                uo = vt * tx - un * nx;
+                vo = vt * ty - un * ny;
+            }
             const int iw = d.fwall[meta & 0xffffff];
             const T ein = T(0.5) * ((u * u + v * v) + w * w);
             const T eout = T(0.5) * ((uo * uo + vo * vo) + wz * wz);
@@ -1047,7 +1061,7 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
                 }
             }
             int it = 0;
-            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, x, y, u, v, w, m, tr, c, -1, pid, it,
+            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, T(K.wall_specular), x, y, u, v, w, m, tr, c, -1, pid, it,
                                    n_cross, n_hits);
             max_it = max(max_it, it);
             if (alive) {
@@ -1229,7 +1243,7 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
                     x = ax + Up[1] * ex;
                     y = ay + Up[1] * ey;
                     int it = 0;
-                    const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, x, y, u, v, w, m, dtL - tc, c, kin, pid, it,
+                    const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, T(K.wall_specular), x, y, u, v, w, m, dtL - tc, c, kin, pid, it,
                                            n_cross, n_hits);
                     max_it = max(max_it, it);
                     if (alive) {
@@ -1608,6 +1622,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     if (!mesh || !gas || !opts || !out || mesh->ni <= 0 || mesh->nj <= 0 || !mesh->xv) return UGKWP_EINVAL;
     if ((long long)mesh->ni * mesh->nj > kMaxCells || opts->n_ref <= 0 || !(cfl > 0.0)) return UGKWP_EINVAL;
     if (mesh->dim != 1 && mesh->dim != 2) return UGKWP_EINVAL;
+    if (!(gas->wall_specular >= 0.0 && gas->wall_specular <= 1.0)) return UGKWP_EINVAL;
     if (mesh->dim == 1 && (mesh->nj != 1 || !mesh->bc_imin || !mesh->bc_imax)) return UGKWP_EINVAL;
     if (mesh->dim == 2 && (!mesh->yv || (mesh->periodic_j && mesh->nj < 2))) return UGKWP_EINVAL;
     int dev_count = 0;
@@ -1642,6 +1657,7 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     K.prec = opts->precision ? 1 : 0;
     K.order = opts->order == 2 ? 2 : 1;
     K.omega = gas->omega; K.Pr = gas->Pr; K.Tw = Tw;
+    K.wall_specular = gas->wall_specular;
     K.shakhov = gas->Pr != 1.0 && !opts->wave_only;
     K.mu_inf = (15.0 * sqrt(2.0 * 3.14159265358979323846 * 0.5) * Kn) / (2.0 * (5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega));
     K.U_inf = Ma * sqrt((5.0 / 3.0) * 0.5 * 1.0);

@@ -218,7 +218,7 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
 }
 
 template <typename R, typename C>
-__device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, C caL, C frL, R lam_w, C F[4])
+__device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, C caL, C frL, R lam_w, C ws, C F[4])
 {
     Prim<R> p;
     Mom<R> m;
@@ -238,8 +238,17 @@ __device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, C caL, C frL, 
     moments(p, m);
     psi_mom(m.um, m, 1, 0, 0, t);
     const C rw = -F[0] / C(t[0]);
+    if (ws == C(0)) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) F[k] += rw * C(t[k]);
+        for (int k = 0; k < 4; ++k) F[k] += rw * C(t[k]);
+        return true;
+    }
+    // Maxwell wall: the fraction ws of the incoming half reflected specularly (in the face frame the mass,
+    // tangential momentum and energy fluxes change sign, the normal momentum flux keeps it), the rest
+    // re-emitted diffusely at T_w with zero net mass
+    const C sg[4] = {C(-1), C(1), C(-1), C(-1)}, a = C(1) - ws;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = (F[k] + ws * (sg[k] * F[k])) + a * (rw * C(t[k]));
     return true;
 }
 
@@ -373,7 +382,7 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         ok = face_flux<R, C>(WL, WR, WhL, WhR, hL, hR, cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]), R(K.Pr), WLc,
                              WRc, sL ? dhL : nullptr, sR ? dhR : nullptr, csL, C(K.wave_only ? coR[4] : coR[6]), F);
     } else if (bc == UGKWP_BC_WALL) {
-        ok = wall_flux<R, C>(WL, WhL, hL, cL[0], frL, R(0.5 / (kR * K.Tw)), F);
+        ok = wall_flux<R, C>(WL, WhL, hL, cL[0], frL, R(0.5 / (kR * K.Tw)), C(K.wall_specular), F);
     } else if (bc == UGKWP_BC_SYMMETRY) {
         const R Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
         ok = face_flux<R, C>(WL, Wm, WhL, Whm, hL, hL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), WL, Wm,

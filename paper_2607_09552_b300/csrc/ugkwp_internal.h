@@ -41,6 +41,7 @@ struct StepConsts {
     int n_inj;                      // ghost particle sources (far-field and fixed faces)
     int order;                      // 2: second-order reconstruction for the wave fluxes
     double mu_inf, omega, Pr, Tw, U_inf, m2RTw, sig_w;
+    double wall_specular;           // Maxwell wall: specular fraction 1 - alpha (0: fully diffuse)
     double T_cap, U_cap, T_min;     // realizability bounds of a cell state
     double W_inf[4], W_fix[4];
     uint32_t k0, k1;                // Philox key

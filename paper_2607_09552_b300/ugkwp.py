@@ -38,7 +38,7 @@ class UgkwpMesh(C.Structure):
 
 
 class UgkwpGas(C.Structure):
-    _fields_ = [("omega", C.c_double), ("Pr", C.c_double)]
+    _fields_ = [("omega", C.c_double), ("Pr", C.c_double), ("wall_specular", C.c_double)]
 
 
 class UgkwpOpts(C.Structure):
@@ -112,7 +112,7 @@ class Solver:
         self._keep += [np.ascontiguousarray(a, dtype=np.int32) for a in (m.bc_imin, m.bc_imax, m.bc_jmin, m.bc_jmax)]
         mesh = UgkwpMesh(m.ni, m.nj, m.dim, m.periodic_j, _d(self._keep[0]), _d(self._keep[1]),
                          *[_p(a, C.c_int32) for a in self._keep[2:]])
-        gas = UgkwpGas(case.omega, case.Pr)
+        gas = UgkwpGas(case.omega, case.Pr, getattr(case, "wall_specular", 0.0))
         opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
                          int(record_faces), capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream),
                          int(use_graph), int(order))

@@ -164,6 +164,7 @@ class Case:
     omega: float = 0.81
     Pr: float = 1.0
     n_ref: int = 100
+    wall_specular: float = 0.0                  # Maxwell wall: specular fraction 1 - alpha (0: fully diffuse)
     seed: int = 0
     ghost_state: tuple = (1.0, 0.0, 0.0, 1.0)   # (rho, U, V, T) used by BC_FIXED faces
     init_prim: np.ndarray | None = None

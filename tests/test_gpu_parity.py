@@ -195,6 +195,32 @@ def test_second_order_wave_only_mode(cuda_lib, name):
     assert_field_close(g.field()[0], o.field()[0], 1e-12)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_maxwell_wall_step_parity(cuda_lib, prec):
+    """Maxwell wall with accommodation 0.85 (the paper's plate value): from an identical snapshot the
+    specular/diffuse choice per hit, the wall tallies and the particles agree bit for bit, the field within
+    the step tolerance."""
+    import dataclasses
+    case = dataclasses.replace(CASES["plate"], wall_specular=0.15)
+    g = cuda_lib.Solver(case, precision=prec)
+    o = ob.Oracle(case, precision=prec)
+    o.step(5)
+    step, W, wret, parts = snapshot(o)
+    g.set_state(step, W, wret, parts)
+    g.step(1)
+    o.step(1)
+    assert o.stats()[6] > 0
+    _compare_step(g, o, prec)
+
+
+def test_specular_walls_conserve_energy_on_gpu(cuda_lib):
+    from tests.test_oracle_wall import _closed_box, _totals
+    g = cuda_lib.Solver(_closed_box(1.0), precision=1)
+    t0 = _totals(g)
+    g.step(40)
+    np.testing.assert_allclose(_totals(g), t0, rtol=1e-12)
+
+
 @pytest.mark.parametrize("name", ["shock1d", "cylinder", "plate"])
 def test_short_trajectory_fp64(cuda_lib, name):
     """Whole trajectories from the same freestream start. The two sides' FP64 wave fluxes differ in the last
