@@ -158,6 +158,29 @@ __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], co
     for (int k = 0; k < 4; ++k) F[k] = C(p0.rho) * (F[k] + cR[2] * C(f[k]));
 }
 
+// Order 2: the normal slope term of a side's g^h, rho^h <psi u_n^2 (a . psi)>_half with a the micro slope of
+// the normal derivative dh of W^h; evaluated in FP64 whatever the face's precision, because its velocity
+// moments cancel strongly where W^h is small against its gradient (particle-dominated cells).
+template <typename R>
+__device__ void gh_slope_term(const R Wh[4], const R dh[4], bool up, double out[4])
+{
+    double W[4], dw[4], a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) W[k] = double(Wh[k]);
+    Prim<double> p;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = 0.0;
+    if (!frame_prim(W, p)) return;
+    Mom<double> m;
+    moments(p, m);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dw[k] = double(dh[k]) / p.rho;
+    slope(p, dw, a);
+    psi_poly(up ? m.up : m.um, m, 2, 0, a, out);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = p.rho * out[k];
+}
+
 // interior-type face; frL/frR weight each side's g^h. WL, WR: the states at the face (the cell states in
 // first order), WLc, WRc: the cell states the normal slopes of g_0 are taken against; dhL, dhR (nullable):
 // normal derivatives of W^h for the slope term of the free-transport wave, weighted with csL, csR (order 2).
@@ -190,13 +213,10 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
 #pragma unroll
         for (int k = 0; k < 4; ++k) F[k] += frL * C(ph.rho * f[k]);
         if (dhL) {
-            R dw[4], a[4];
+            double st[4];
+            gh_slope_term(WhL, dhL, true, st);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dw[k] = dhL[k] / ph.rho;
-            slope(ph, dw, a);
-            psi_poly(mh.up, mh, 2, 0, a, f);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) F[k] += csL * C(ph.rho * f[k]);
+            for (int k = 0; k < 4; ++k) F[k] += csL * C(st[k]);
         }
     }
     if (hR && frame_prim(WhR, ph)) {
@@ -205,13 +225,10 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
 #pragma unroll
         for (int k = 0; k < 4; ++k) F[k] += frR * C(ph.rho * f[k]);
         if (dhR) {
-            R dw[4], a[4];
+            double st[4];
+            gh_slope_term(WhR, dhR, false, st);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dw[k] = dhR[k] / ph.rho;
-            slope(ph, dw, a);
-            psi_poly(mh.um, mh, 2, 0, a, f);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) F[k] += csR * C(ph.rho * f[k]);
+            for (int k = 0; k < 4; ++k) F[k] += csR * C(st[k]);
         }
     }
     return true;

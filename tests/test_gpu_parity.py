@@ -174,9 +174,8 @@ def test_second_order_step_parity(cuda_lib, name, prec):
     if prec == 1:
         _compare_step(g, o, prec)
         return
-    # production: the slope term of g^h, evaluated from FP32 moments, loses more digits than the first-order
-    # terms (noisy W^h gradients); the face fluxes agree to 1e-3 of their scale, the updated field to the
-    # production bar
+    # production: FP32 moments of the reconstructed face states (the g^h slope term in FP64); the face fluxes
+    # agree to 1e-3 of their scale, the updated field to the production bar
     assert np.array_equal(g.cell_data(), o.cell_data())
     tg, to = g.tallies(), o.tallies()
     for k in ("wm", "wpl", "wret", "cross", "wall", "frec"):
