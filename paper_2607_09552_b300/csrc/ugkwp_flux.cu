@@ -158,27 +158,32 @@ __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], co
     for (int k = 0; k < 4; ++k) F[k] = C(p0.rho) * (F[k] + cR[2] * C(f[k]));
 }
 
-// Order 2: the normal slope term of a side's g^h, rho^h <psi u_n^2 (a . psi)>_half with a the micro slope of
-// the normal derivative dh of W^h; evaluated in FP64 whatever the face's precision, because its velocity
-// moments cancel strongly where W^h is small against its gradient (particle-dominated cells).
+// Order 2: a side's free-transport wave from its reconstructed W^h, rho^h <psi u_n>_half (zero) and the
+// normal slope term rho^h <psi u_n^2 (a . psi)>_half (slope) with a the micro slope of the normal derivative
+// dh of W^h; evaluated in FP64 whatever the face's precision: a reconstructed W^h can sit near the edge of the
+// realizable set (small internal energy) and the slope moments cancel strongly where W^h is small against
+// its gradient (particle-dominated cells). Returns false if the state is not a Maxwellian.
 template <typename R>
-__device__ void gh_slope_term(const R Wh[4], const R dh[4], bool up, double out[4])
+__device__ bool gh_terms(const R Wh[4], const R dh[4], bool up, double zero[4], double slp[4])
 {
     double W[4], dw[4], a[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) W[k] = double(Wh[k]);
     Prim<double> p;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = 0.0;
-    if (!frame_prim(W, p)) return;
+    if (!frame_prim(W, p)) return false;
     Mom<double> m;
     moments(p, m);
+    psi_mom(up ? m.up : m.um, m, 1, 0, 0, zero);
 #pragma unroll
     for (int k = 0; k < 4; ++k) dw[k] = double(dh[k]) / p.rho;
     slope(p, dw, a);
-    psi_poly(up ? m.up : m.um, m, 2, 0, a, out);
+    psi_poly(up ? m.up : m.um, m, 2, 0, a, slp);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = p.rho * out[k];
+    for (int k = 0; k < 4; ++k) {
+        zero[k] = p.rho * zero[k];
+        slp[k] = p.rho * slp[k];
+    }
+    return true;
 }
 
 // interior-type face; frL/frR weight each side's g^h. WL, WR: the states at the face (the cell states in
@@ -207,29 +212,32 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
     R f[4];
     Prim<R> ph;
     Mom<R> mh;
-    if (hL && frame_prim(WhL, ph)) {
+    double z[4], sl[4];
+    if (hL && dhL) {
+        if (gh_terms(WhL, dhL, true, z, sl))
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                F[k] += frL * C(z[k]);
+                F[k] += csL * C(sl[k]);
+            }
+    } else if (hL && frame_prim(WhL, ph)) {
         moments(ph, mh);
         psi_mom(mh.up, mh, 1, 0, 0, f);
 #pragma unroll
         for (int k = 0; k < 4; ++k) F[k] += frL * C(ph.rho * f[k]);
-        if (dhL) {
-            double st[4];
-            gh_slope_term(WhL, dhL, true, st);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) F[k] += csL * C(st[k]);
-        }
     }
-    if (hR && frame_prim(WhR, ph)) {
+    if (hR && dhR) {
+        if (gh_terms(WhR, dhR, false, z, sl))
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                F[k] += frR * C(z[k]);
+                F[k] += csR * C(sl[k]);
+            }
+    } else if (hR && frame_prim(WhR, ph)) {
         moments(ph, mh);
         psi_mom(mh.um, mh, 1, 0, 0, f);
 #pragma unroll
         for (int k = 0; k < 4; ++k) F[k] += frR * C(ph.rho * f[k]);
-        if (dhR) {
-            double st[4];
-            gh_slope_term(WhR, dhR, false, st);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) F[k] += csR * C(st[k]);
-        }
     }
     return true;
 }
