@@ -9,13 +9,16 @@
  *  - units rho_inf = T_inf = 1, R = 1/2; monatomic, three velocity components, D = 0;
  *  - mu_inf from Kn by the VHS mean-free-path relation; mu = mu_inf T^omega; tau = mu / p (Sec. II);
  *  - tau_i from the total W^n_i at the start of the step;
- *  - reconstruction is first order (piecewise constant): the initial distribution has no slope; the
- *    equilibrium g_0 has normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on
+ *  - reconstruction is first order (piecewise constant) by default: the initial distribution has no slope;
+ *    the equilibrium g_0 has normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on
  *    u.n < 0, no tangential slope; A from the compatibility condition with both half slopes (Sec. III A);
+ *    order 2 (Eq. 12) reconstructs the face states from limited cell gradients and adds the normal slope
+ *    term of g^h, the slopes of g_0 still taken against the cell states;
  *  - Prandtl fix applied to a through d(lambda)/Pr; wave fluxes use the Maxwellian g_0 (Sec. III A);
  *  - wall faces: incoming half from the fluid cell (first order), outgoing half a wall Maxwellian at T_w
- *    whose density zeroes the wave mass flux; far-field ghost = freestream on inflow, the cell state on
- *    outflow, with the full free-transport coefficient on the ghost side (no particles are injected);
+ *    whose density zeroes the wave mass flux, or with accommodation alpha < 1 the fraction 1 - alpha
+ *    mirrored; far-field / fixed ghosts are virtual cells of the ghost state whose collisionless part
+ *    enters as particles (ghost particle sources), so their wave keeps dbar_d - e^{-x};
  *  - the particle w-momentum (and in 1-D the v-momentum) is not part of W.
  */
 #include "oracle_internal.h"

@@ -463,12 +463,12 @@ __global__ void __launch_bounds__(128) k_wave_flux32(const StepConsts K, const D
 // queued by the FP32 kernel. The FP64 pipe's cost grows with the active lanes of a warp, so in production
 // mode the (rare) queued faces are spread one per warp (lane 0); in the all-FP64 mode every lane takes a
 // face.
-__global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c, int lanes)
+__global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c, int lanes, int all_faces)
 {
     if ((int)threadIdx.x >= lanes) return;
-    const int n = K.n_f64 + *c.nretry;
+    const int n = all_faces ? K.F : K.n_f64 + *c.nretry;
     for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < n; j += gridDim.x * lanes) {
-        const int f = j < K.n_f64 ? c.f64list[j] : c.retry[j - K.n_f64];
+        const int f = all_faces ? j : j < K.n_f64 ? c.f64list[j] : c.retry[j - K.n_f64];
         double out[4];
         one_face<double, double>(K, c, f, out);
         // a non-finite flux (near-vacuum neighbours: the interface density underflows against theirs and the
@@ -483,9 +483,15 @@ __global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const De
 
 void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s)
 {
+    // second-order reconstruction: every face in FP64 (reconstructed states near the edge of the realizable
+    // set and the slope terms lose too many digits in FP32 moments)
+    if (k.order == 2) {
+        k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 1);
+        return;
+    }
     if (k.prec == 0) k_wave_flux32<<<(k.F + 127) / 128, 128, 0, s>>>(k, d);
-    if (k.prec == 0) k_wave_flux64<<<4 * sms, 32, 0, s>>>(k, d, 1);
-    else k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32);
+    if (k.prec == 0) k_wave_flux64<<<4 * sms, 32, 0, s>>>(k, d, 1, 0);
+    else k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 0);
 }
 
 cudaError_t flux_set_tables(const double* tab, cudaStream_t s)

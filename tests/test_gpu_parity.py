@@ -160,8 +160,9 @@ def test_time_varying_steps_break_the_balance_on_gpu(cuda_lib):
 @pytest.mark.parametrize("name", ["shock1d", "cylinder", "plate", "box"])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_second_order_step_parity(cuda_lib, name, prec):
-    """Order 2 (Eq. 12, S6): from an identical snapshot the reconstructed wave fluxes and the updated field
-    agree within the step tolerances; the particles (untouched by the fluxes within a step) bit for bit."""
+    """Order 2 (Eq. 12, S6): from an identical snapshot the reconstructed wave fluxes (FP64 in both modes) and
+    the updated field agree within the step tolerances; the particles (untouched by the fluxes within a step)
+    bit for bit."""
     case = CASES[name]
     g = cuda_lib.Solver(case, precision=prec, order=2)
     o = ob.Oracle(case, precision=prec, order=2)
@@ -171,18 +172,7 @@ def test_second_order_step_parity(cuda_lib, name, prec):
     g.step(1)
     o.step(1)
     assert np.any(o.gradients() != 0.0)
-    if prec == 1:
-        _compare_step(g, o, prec)
-        return
-    # production: FP32 moments of the reconstructed face states (the g^h slope term in FP64); the face fluxes
-    # agree to 1e-3 of their scale, the updated field to the production bar
-    assert np.array_equal(g.cell_data(), o.cell_data())
-    tg, to = g.tallies(), o.tallies()
-    for k in ("wm", "wpl", "wret", "cross", "wall", "frec"):
-        assert np.array_equal(tg[k], to[k]), k
-    assert_particles_equal(g.particles(), o.particles())
-    assert_field_close(g.flux(), o.flux(), 1e-3)
-    assert_field_close(g.field()[0], o.field()[0], TOL[prec])
+    _compare_step(g, o, prec)
 
 
 @pytest.mark.parametrize("name", ["shock1d", "cylinder", "plate", "box"])
