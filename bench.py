@@ -119,7 +119,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     case = bench_case()
     # the product's recommended mode: one captured graph per step, launch shape chosen by the autotuner
-    solver = ugkwp.Solver(case, precision=0, seed=rank, stream=stream.cuda_stream, use_graph=True)
+    solver = ugkwp.Solver(case, precision=0, seed=rank, stream=stream.cuda_stream, use_graph=True, order=args.order)
     solver.step(args.burn)
     launch, tune_ms = solver.autotune(16) if not args.no_autotune else (solver.launch(), None)
     stream.synchronize()
@@ -175,6 +175,7 @@ def run_ours(args):
         traffic = particles_traffic(per_launch)
         cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
         cfg = config_dict(case, args.burn, "512 MB L2 flush before every timed step, outside the events")
+        cfg["reconstruction_order"] = args.order
         cfg["launch"] = {"chunk": launch[0], "blocks_per_sm": launch[1], "sort_every": launch[2],
                          "chosen_by": "autotuner" if not args.no_autotune else "defaults", "graph": True}
         line = {
@@ -677,6 +678,8 @@ def main():
     ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch", "warmstart"])
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--case", default="kn01", choices=["kn01", "kn001"])
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
+                    help="reconstruction order of the wave fluxes (2: second order, FP64 wave fluxes)")
     ap.add_argument("--max-wave-steps", type=int, default=400000)
     ap.add_argument("--lts-steps", type=int, default=30000)
     ap.add_argument("--gts-steps", type=int, default=150000)

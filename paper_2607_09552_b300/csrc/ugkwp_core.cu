@@ -541,14 +541,18 @@ __global__ void k_decompose(const StepConsts K, Dev d)
 // reconstruction at every face midpoint within the values of the cell and those neighbours.
 __device__ __forceinline__ double van_leer(double a, double b) { return a * b > 0.0 ? (2.0 * a * b) / (a + b) : 0.0; }
 
+// one thread per (cell, component): eight independent FP64 chains per cell keep the FP64 pipe busier than
+// one thread walking them in turn
 __global__ void k_gradients(const StepConsts K, Dev d)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= K.C) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8 * K.C) return;
+    const int c = t >> 3;
     const CellFaces<double>& F = d.cf64[c];
     const int nf = d.nfc[c];
     double* g = d.grad + 16 * (size_t)c;
-    for (int v = 0; v < 8; ++v) {
+    {
+        const int v = t & 7;
         const double* A = v < 4 ? d.W : d.Wh;
         const int comp = v & 3;
         const double vc = A[4 * c + comp];
@@ -1546,7 +1550,7 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     }
     k_decompose<<<nblk(C, 128), 128, 0, s>>>(K, d);
     exclusive_scan(d.nhp, d.nhp_off, d.scan_tmp, C, d.counts + 1, s, d.counts, d.err);
-    if (K.order == 2) k_gradients<<<nblk(C, 128), 128, 0, s>>>(K, d);
+    if (K.order == 2) k_gradients<<<nblk(8LL * C, 128), 128, 0, s>>>(K, d);
     mark(1, s);
     // the wave fluxes depend only on the decomposition: they run on a second stream, alongside the
     // particle kernels, and join before the update
