@@ -340,14 +340,16 @@ def run_convergence(args):
     stream = torch.cuda.current_stream()
     case = wl.case_cylinder_kn001() if args.case == "kn001" else bench_case()
     out = {"mode": "convergence", "workload": config_dict(case, 0, "n/a")["workload"] if args.case != "kn001" else
-           "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8", "results": {}}
+           "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8",
+           "reconstruction_order": args.order, "results": {}}
     geom = steady.wall_geometry(case)
     for ts in ("LTS", "GTS"):
         gts = ts == "GTS"
         r = {}
         out["results"][ts] = r
         if not args.skip_wave:
-            s = ugkwp.Solver(case, gts=gts, precision=1, wave_only=True, stream=stream.cuda_stream, use_graph=True)
+            s = ugkwp.Solver(case, gts=gts, precision=1, wave_only=True, stream=stream.cuda_stream, use_graph=True,
+                             order=args.order)
             w = steady.run_to_residual(s, 1e-6, args.max_wave_steps, 500)
             r["wave_only_fp64"] = {"steps_to_1e-6": w["steps"] if w["converged"] else None,
                                    "wall_s": w["seconds"], "final_residual": w["residual"],
@@ -358,7 +360,8 @@ def run_convergence(args):
         n = args.lts_steps if not gts else args.gts_steps
         # GTS keeps far more particles (every cell samples with the smallest time step): larger capacity
         cap = (32 if gts else 8) * case.n_ref * case.mesh.ncells
-        s = ugkwp.Solver(case, gts=gts, precision=0, stream=stream.cuda_stream, use_graph=True, capacity=cap)
+        s = ugkwp.Solver(case, gts=gts, precision=0, stream=stream.cuda_stream, use_graph=True, capacity=cap,
+                         order=args.order)
         j0, j1 = stagnation_pair(case)
         hcd, hch, hp, hq, hres, hnp, ht = [], [], [], [], [], [], []
         t0 = time.perf_counter()
