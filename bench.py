@@ -205,16 +205,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def transport_source_hash(t) -> str:
+    """16 hex digits of the SHA-256 of the transport kernel's source: the region of the core unit between the
+    two markers recorded in the traffic file (the per-cell views, the fixed-point helpers, the sampling, the
+    free flight and k_particles) followed by the deterministic-math header it includes."""
+    import hashlib
+    txt = open(os.path.join(ROOT, t["source"]), encoding="utf-8").read()
+    a, b = txt.index(t["region_start"]), txt.index(t["region_end"])
+    h = hashlib.sha256(txt[a:b].encode())
+    for extra in t.get("extra_sources", []):
+        h.update(open(os.path.join(ROOT, extra), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def particles_traffic(per_launch: float):
     """DRAM bytes (read + written) of one transport-kernel launch: the bytes per particle of the committed ncu
-    capture (profiles/particles_traffic.json) times this launch's particles; None when the kernel source has
-    changed since the capture."""
-    import hashlib
+    capture (profiles/particles_traffic.json) times this launch's particles; None when the transport kernel's
+    source has changed since the capture."""
     tfile = os.path.join(ROOT, "profiles", "particles_traffic.json")
     try:
         t = json.load(open(tfile))
-        src = open(os.path.join(ROOT, t["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != t["source_sha256_16"]:
+        if transport_source_hash(t) != t["region_sha256_16"]:
             return None
         return float(t["bytes_per_particle"]) * per_launch
     except (OSError, KeyError, ValueError):

@@ -838,9 +838,11 @@ static double van_leer(double a, double b) { return a * b > 0.0 ? (2.0 * a * b) 
 /* Limited gradients (d/dx, d/dy) of the four components of W (v = 0..3) and of W^h (v = 4..7) per cell.
  * 1-D: van Leer's limiter of the one-sided slopes to the two neighbours (zero next to a boundary face).
  * 2-D: least-squares gradient over the neighbours across interior and periodic faces, weights 1 / |dx|^2
- * (zero with fewer than two neighbours), then Barth and Jespersen's limiter: one factor per component so that
- * the reconstruction at every face midpoint of the cell stays within the values of the cell and those
- * neighbours. */
+ * (zero with fewer than two neighbours), then Venkatakrishnan's limiter (a smooth form of keeping the
+ * reconstruction at every face midpoint within the values of the cell and those neighbours): one factor per
+ * component, the smallest over the faces and at most 1, with epsilon^2 = (K h)^3 s^2, K = 5, h = sqrt(Omega)
+ * and s the freestream scale of the component (rho_inf; rho_inf (U_inf + sqrt(R T_inf)) for the momenta;
+ * (rho E)_inf), which makes it independent of the units of each component. */
 static void gradients(or_ctx* cx)
 {
     for (int c = 0; c < cx->C; ++c) {
@@ -875,14 +877,19 @@ static void gradients(or_ctx* cx)
                 if (nn >= 2 && det > 1e-12 * (a11 * a22)) {
                     gx = (a22 * b1 - a12 * b2) / det;
                     gy = (a11 * b2 - a12 * b1) / det;
+                    const double sc = comp == 0 ? cx->W_inf[0]
+                                    : comp == 3 ? cx->W_inf[3] : cx->W_inf[0] * (cx->U_inf + sqrt(OR_R));
+                    const double kh = 5.0 * sqrt(cx->vol[c]);
+                    const double eps2 = ((kh * kh) * kh) * (sc * sc);
                     double phi = 1.0;
                     for (int k = 0; k < cx->nfc[c]; ++k) {
                         const int f = cx->cface[4 * c + k];
                         const double mx = cx->fax[f] + 0.5 * cx->fex[f], my = cx->fay[f] + 0.5 * cx->fey[f];
                         const double d2 = gx * (mx - cx->xc[c]) + gy * (my - cx->yc[c]);
-                        double r = 1.0;
-                        if (d2 > 0.0) r = (vmax - vc) / d2;
-                        else if (d2 < 0.0) r = (vmin - vc) / d2;
+                        if (d2 == 0.0) continue;
+                        const double d1 = d2 > 0.0 ? vmax - vc : vmin - vc;
+                        const double r = ((d1 * d1 + eps2) * d2 + (2.0 * d2) * (d2 * d1)) /
+                                         (d2 * (((d1 * d1 + 2.0 * (d2 * d2)) + d1 * d2) + eps2));
                         if (r < phi) phi = r;
                     }
                     gx *= phi;

@@ -537,8 +537,10 @@ __global__ void k_decompose(const StepConsts K, Dev d)
 // Limited gradients (d/dx, d/dy) of the four components of W (v = 0..3) and W^h (v = 4..7) of one cell (FP64).
 // 1-D: van Leer's limiter of the one-sided slopes to the two neighbours (zero next to a boundary face).
 // 2-D: least-squares gradient over the neighbours across interior and periodic faces, weights 1 / |dx|^2
-// (zero with fewer than two), then Barth and Jespersen's limiter: one factor per component keeping the
-// reconstruction at every face midpoint within the values of the cell and those neighbours.
+// (zero with fewer than two), then Venkatakrishnan's limiter (a smooth form of keeping the reconstruction at
+// every face midpoint within the values of the cell and those neighbours), one factor per component, the
+// smallest over the faces and at most 1, epsilon^2 = (K h)^3 s^2 with K = 5, h = sqrt(Omega) and s the
+// component's freestream scale (rho_inf, rho_inf (U_inf + sqrt(R T_inf)), (rho E)_inf).
 __device__ __forceinline__ double van_leer(double a, double b) { return a * b > 0.0 ? (2.0 * a * b) / (a + b) : 0.0; }
 
 // one thread per (cell, component): eight independent FP64 chains per cell keep the FP64 pipe busier than
@@ -582,14 +584,18 @@ __global__ void k_gradients(const StepConsts K, Dev d)
             if (nn >= 2 && det > 1e-12 * (a11 * a22)) {
                 gx = (a22 * b1 - a12 * b2) / det;
                 gy = (a11 * b2 - a12 * b1) / det;
+                const double sc = comp == 0 ? K.W_inf[0] : comp == 3 ? K.W_inf[3] : K.W_inf[0] * (K.U_inf + sqrt(kR));
+                const double kh = 5.0 * sqrt(d.vol[c]);
+                const double eps2 = ((kh * kh) * kh) * (sc * sc);
                 double phi = 1.0;
                 for (int k = 0; k < nf; ++k) {
                     const int f = F.meta[k] & 0xffffff;
                     const double mx = d.fax[f] + 0.5 * d.fex[f], my = d.fay[f] + 0.5 * d.fey[f];
                     const double d2 = gx * (mx - d.xc[c]) + gy * (my - d.yc[c]);
-                    double r = 1.0;
-                    if (d2 > 0.0) r = (vmax - vc) / d2;
-                    else if (d2 < 0.0) r = (vmin - vc) / d2;
+                    if (d2 == 0.0) continue;
+                    const double d1 = d2 > 0.0 ? vmax - vc : vmin - vc;
+                    const double r = ((d1 * d1 + eps2) * d2 + (2.0 * d2) * (d2 * d1)) /
+                                     (d2 * (((d1 * d1 + 2.0 * (d2 * d2)) + d1 * d2) + eps2));
                     if (r < phi) phi = r;
                 }
                 gx *= phi;
