@@ -832,11 +832,14 @@ static void inject_params(or_ctx* cx)
 
 /* ----------------------------------------------------------- a8: reconstruction (order 2, S6 reading) */
 
-/* van Leer's limited slope from two one-sided differences */
-static double van_leer(double a, double b) { return a * b > 0.0 ? (2.0 * a * b) / (a + b) : 0.0; }
+/* smooth (van Albada type) limited slope from the one-sided slopes a, b: ((b^2 + e2) a + (a^2 + e2) b) /
+ * (a^2 + b^2 + 2 e2); exact for a = b, zero for a = -b, and differentiable, so that steady runs converge */
+static double smooth_slope(double a, double b, double e2) { return ((b * b + e2) * a + (a * a + e2) * b) / ((a * a + b * b) + 2.0 * e2); }
 
 /* Limited gradients (d/dx, d/dy) of the four components of W (v = 0..3) and of W^h (v = 4..7) per cell.
- * 1-D: van Leer's limiter of the one-sided slopes to the two neighbours (zero next to a boundary face).
+ * 1-D: a smooth limiter of the one-sided slopes a, b to the two neighbours (zero next to a boundary face),
+ * ((b^2 + e2) a + (a^2 + e2) b) / (a^2 + b^2 + 2 e2) with e2 = K^3 h s^2 (the slope form of Venkatakrishnan's
+ * epsilon below: K = 5, h the cell length, s the component's freestream scale).
  * 2-D: least-squares gradient over the neighbours across interior and periodic faces, weights 1 / |dx|^2
  * (zero with fewer than two neighbours), then Venkatakrishnan's limiter (a smooth form of keeping the
  * reconstruction at every face midpoint within the values of the cell and those neighbours): one factor per
@@ -857,7 +860,10 @@ static void gradients(or_ctx* cx)
                 if (nl >= 0 && nr >= 0) {
                     /* a neighbour across a periodic face, in this cell's frame */
                     const double xl = cx->xc[nl] - cx->cshift[ql], xr = cx->xc[nr] - cx->cshift[qr];
-                    gx = van_leer((vc - A[4 * nl + comp]) / (cx->xc[c] - xl), (A[4 * nr + comp] - vc) / (xr - cx->xc[c]));
+                    const double sc = comp == 0 ? cx->W_inf[0]
+                                    : comp == 3 ? cx->W_inf[3] : cx->W_inf[0] * (cx->U_inf + sqrt(OR_R));
+                    gx = smooth_slope((vc - A[4 * nl + comp]) / (cx->xc[c] - xl), (A[4 * nr + comp] - vc) / (xr - cx->xc[c]),
+                                      (125.0 * cx->vol[c]) * (sc * sc));
                 }
             } else {
                 double a11 = 0.0, a12 = 0.0, a22 = 0.0, b1 = 0.0, b2 = 0.0, vmax = vc, vmin = vc;

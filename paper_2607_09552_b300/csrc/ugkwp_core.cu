@@ -535,13 +535,18 @@ __global__ void k_decompose(const StepConsts K, Dev d)
 
 // ------------------------------------------------- a8: second-order reconstruction (order 2)
 // Limited gradients (d/dx, d/dy) of the four components of W (v = 0..3) and W^h (v = 4..7) of one cell (FP64).
-// 1-D: van Leer's limiter of the one-sided slopes to the two neighbours (zero next to a boundary face).
+// 1-D: a smooth (van Albada type) limiter of the one-sided slopes a, b to the two neighbours (zero next to a
+// boundary face), ((b^2 + e2) a + (a^2 + e2) b) / (a^2 + b^2 + 2 e2), e2 = K^3 h s^2 (K, s as below, h the
+// cell length): exact for a = b, zero for a = -b and differentiable, so that steady runs converge.
 // 2-D: least-squares gradient over the neighbours across interior and periodic faces, weights 1 / |dx|^2
 // (zero with fewer than two), then Venkatakrishnan's limiter (a smooth form of keeping the reconstruction at
 // every face midpoint within the values of the cell and those neighbours), one factor per component, the
 // smallest over the faces and at most 1, epsilon^2 = (K h)^3 s^2 with K = 5, h = sqrt(Omega) and s the
 // component's freestream scale (rho_inf, rho_inf (U_inf + sqrt(R T_inf)), (rho E)_inf).
-__device__ __forceinline__ double van_leer(double a, double b) { return a * b > 0.0 ? (2.0 * a * b) / (a + b) : 0.0; }
+__device__ __forceinline__ double smooth_slope(double a, double b, double e2)
+{
+    return ((b * b + e2) * a + (a * a + e2) * b) / ((a * a + b * b) + 2.0 * e2);
+}
 
 // one thread per (cell, component): eight independent FP64 chains per cell keep the FP64 pipe busier than
 // one thread walking them in turn
@@ -564,7 +569,9 @@ __global__ void k_gradients(const StepConsts K, Dev d)
             if (nl >= 0 && nr >= 0) {
                 // a neighbour across a periodic face, in this cell's frame
                 const double xl = d.xc[nl] - d.cshift[4 * c], xr = d.xc[nr] - d.cshift[4 * c + 1];
-                gx = van_leer((vc - A[4 * nl + comp]) / (d.xc[c] - xl), (A[4 * nr + comp] - vc) / (xr - d.xc[c]));
+                const double sc = comp == 0 ? K.W_inf[0] : comp == 3 ? K.W_inf[3] : K.W_inf[0] * (K.U_inf + sqrt(kR));
+                gx = smooth_slope((vc - A[4 * nl + comp]) / (d.xc[c] - xl), (A[4 * nr + comp] - vc) / (xr - d.xc[c]),
+                                  (125.0 * d.vol[c]) * (sc * sc));
             }
         } else {
             double a11 = 0.0, a12 = 0.0, a22 = 0.0, b1 = 0.0, b2 = 0.0, vmax = vc, vmin = vc;

@@ -48,8 +48,9 @@ def test_gradients_exact_for_linear_fields():
     assert np.all(ratio <= 1.0 + 1e-12) and np.all(ratio > 0.95)
 
 
-def test_van_leer_slopes_1d():
-    """1-D: exact slope of a linear field on a stretched line; zero slope where the data have an extremum."""
+def test_smooth_slopes_1d():
+    """1-D: exact slope of a linear field on a stretched line (equal one-sided slopes); zero next to a boundary
+    face; around an interior maximum the slopes change sign and stay below the larger one-sided slope."""
     ni = 20
     m = wl.line_mesh(ni, 0.0, 1.0, end_ratio=5.0, bc_left=wl.BC_FIXED, bc_right=wl.BC_FIXED)
     xs = m.xv[: ni + 1]
@@ -60,12 +61,25 @@ def test_van_leer_slopes_1d():
     prim[:, 1], prim[:, 3] = 0.5, 1.0
     G = _one_wave_step(case, prim).gradients()
     np.testing.assert_allclose(G[1:-1, 0, 0], 0.5, rtol=1e-10)
-    assert np.all(G[[0, -1], :, :] == 0.0)                 # next to a boundary face
-    prim[:, 0] = 1.0 + 0.3 * np.sin(np.pi * xc)            # one maximum inside
+    assert np.all(G[[0, -1], :, :] == 0.0)
+    prim[:, 0] = 1.0 + 0.3 * np.sin(np.pi * xc)
     G = _one_wave_step(case, prim).gradients()
-    k = int(np.argmax(prim[:, 0]))
-    assert G[k, 0, 0] == 0.0
-    assert np.all(G[1:k, 0, 0] > 0.0) and np.all(G[k + 1:-1, 0, 0] < 0.0)
+    rho = prim[:, 0]
+    k = int(np.argmax(rho))
+    a = (rho[k] - rho[k - 1]) / (xc[k] - xc[k - 1])
+    b = (rho[k + 1] - rho[k]) / (xc[k + 1] - xc[k])
+    assert a > 0.0 > b and abs(G[k, 0, 0]) < max(abs(a), abs(b))
+    assert np.all(G[1:k - 1, 0, 0] > 0.0) and np.all(G[k + 2:-1, 0, 0] < 0.0)
+
+
+def test_second_order_steady_shock_converges():
+    """The smooth limiter keeps the particle-free second-order scheme differentiable: the 1-D Ma 3 shock
+    settles to a steady state (residual below 1e-10), as at first order; with van Leer's limiter the
+    residual stalled near 5e-3."""
+    case = wl.case_shock1d(ni=200, n_ref=20, Pr=1.0)
+    o = ob.Oracle(case, precision=1, wave_only=True, order=2)
+    o.step(12000)
+    assert float(o.residual()[:4].max()) < 1e-10
 
 
 def test_uniform_state_preserved_at_second_order():
