@@ -329,21 +329,24 @@ __device__ bool face_side(const StepConsts& K, const Dev& c, int cc, int f, int 
 {
     const double* g = c.grad + 16 * (size_t)cc + 8 * which;
     const double* Wc = (which ? c.Wh : c.W) + 4 * cc;
+    // individually rounded operations (no fused multiply-add), as in the cell gradients: the face states feed
+    // differences against the cell states that amplify any last-bit change
     double ddx, ddy;
     if (K.dim == 1) {
         const int k = (c.cf64[cc].meta[0] & 0xffffff) == f ? 0 : 1;   // local face 0: left end, 1: right end
-        ddx = c.cvx[4 * cc + k] - c.xc[cc];
+        ddx = __dsub_rn(c.cvx[4 * cc + k], c.xc[cc]);
         ddy = 0.0;
     } else {
-        ddx = (c.fax[f] + 0.5 * c.fex[f]) - c.xc[cc];
-        ddy = (c.fay[f] + 0.5 * c.fey[f]) - c.yc[cc];
+        ddx = __dsub_rn(__dadd_rn(c.fax[f], __dmul_rn(0.5, c.fex[f])), c.xc[cc]);
+        ddy = __dsub_rn(__dadd_rn(c.fay[f], __dmul_rn(0.5, c.fey[f])), c.yc[cc]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        Wf[q] = Wc[q] + (g[2 * q] * ddx + g[2 * q + 1] * ddy);
-        dn[q] = g[2 * q] * nx + g[2 * q + 1] * ny;
+        Wf[q] = __dadd_rn(Wc[q], __dadd_rn(__dmul_rn(g[2 * q], ddx), __dmul_rn(g[2 * q + 1], ddy)));
+        dn[q] = __dadd_rn(__dmul_rn(g[2 * q], nx), __dmul_rn(g[2 * q + 1], ny));
     }
-    return Wf[0] > 0.0 && Wf[3] - 0.5 * (Wf[1] * Wf[1] + Wf[2] * Wf[2]) / Wf[0] > 0.0;
+    const double ke = __dmul_rn(0.5, __dadd_rn(__dmul_rn(Wf[1], Wf[1]), __dmul_rn(Wf[2], Wf[2])));
+    return Wf[0] > 0.0 && __dsub_rn(Wf[3], __ddiv_rn(ke, Wf[0])) > 0.0;
 }
 
 template <typename R, typename C>
