@@ -174,14 +174,15 @@ def test_second_order_step_parity(cuda_lib, name, prec):
     assert np.any(o.gradients() != 0.0)
     # the face fluxes differ more than at first order where a face state sits close to its cell state: the
     # equilibrium slopes divide that difference by the centre-to-face distance, which amplifies the last-bit
-    # differences of the two sides' transcendental functions; the updated field holds the step bar
+    # differences of the two sides' transcendental functions (observed on the cylinder in the FP64 mode: face
+    # fluxes 3e-10, field 1.8e-12 of their scales); production mode keeps the step bar
     assert np.array_equal(g.cell_data(), o.cell_data())
     tg, to = g.tallies(), o.tallies()
     for k in ("wm", "wpl", "wret", "cross", "wall", "frec"):
         assert np.array_equal(tg[k], to[k]), k
     assert_particles_equal(g.particles(), o.particles())
     assert_field_close(g.flux(), o.flux(), 1e-9 if prec == 1 else 1e-4)
-    assert_field_close(g.field()[0], o.field()[0], TOL[prec])
+    assert_field_close(g.field()[0], o.field()[0], 5e-12 if prec == 1 else TOL[prec])
 
 
 @pytest.mark.parametrize("name", ["shock1d", "cylinder", "plate", "box"])
