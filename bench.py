@@ -95,12 +95,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def bench_case():
+def bench_case(args=None):
+    """The throughput workload: the Kn 0.1 cylinder (the default), or with --case kn001 the dense-regime one."""
+    if args is not None and getattr(args, "case", "kn01") == "kn001":
+        return wl.case_cylinder_kn001()
     return wl.case_cylinder_kn01()
 
 
+WORKLOADS = {
+    "cylinder_120x160_Kn0.1_Ma5.0": "cylinder O-mesh 120x160, Kn=0.1 (lambda/D), Ma=5, Tw/Tinf=1, N_ref=100, CFL 0.8, LTS",
+    "cylinder_240x320_Kn0.01_Ma15.0": "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8, LTS",
+}
+
+
 def config_dict(case, burn, flush):
-    return {"workload": "cylinder O-mesh 120x160, Kn=0.1 (lambda/D), Ma=5, Tw/Tinf=1, N_ref=100, CFL 0.8, LTS",
+    return {"workload": WORKLOADS.get(case.name, case.name),
             "cells": case.mesh.ncells, "mode": "LTS", "precision": "FP32 particles, int64 fixed-point tallies, "
             "FP64 cell update", "burn_in_steps": burn, "l2": flush, "parallelism": "replicas (one case per GPU)"}
 
@@ -117,7 +126,7 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    case = bench_case()
+    case = bench_case(args)
     # the product's recommended mode: one captured graph per step, launch shape chosen by the autotuner
     solver = ugkwp.Solver(case, precision=0, seed=rank, stream=stream.cuda_stream, use_graph=True, order=args.order)
     solver.step(args.burn)
@@ -289,7 +298,7 @@ def cpu_baseline(args):
     """The oracle (plain C, one thread) on a bounded sample of the same workload: a few full steps from the
     freestream start."""
     from oracle import binding as ob
-    case = bench_case()
+    case = bench_case(args)
     o = ob.Oracle(case, precision=0)
     o.step(1)
     t0 = time.perf_counter()
@@ -311,7 +320,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import binding as ob
-    case = bench_case()
+    case = bench_case(args)
     o = ob.Oracle(case, precision=0)
     for _ in range(args.warmup):
         o.step(1)
@@ -349,9 +358,8 @@ def run_convergence(args):
     from paper_2607_09552_b300 import steady, ugkwp
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    case = wl.case_cylinder_kn001() if args.case == "kn001" else bench_case()
-    out = {"mode": "convergence", "workload": config_dict(case, 0, "n/a")["workload"] if args.case != "kn001" else
-           "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8",
+    case = bench_case(args)
+    out = {"mode": "convergence", "workload": config_dict(case, 0, "n/a")["workload"],
            "reconstruction_order": args.order, "results": {}}
     geom = steady.wall_geometry(case)
     for ts in ("LTS", "GTS"):
