@@ -300,6 +300,28 @@ def test_capacity_limit_reports_error(cuda_lib):
     assert e.value.status == 4
 
 
+def test_option_validation(cuda_lib):
+    """Bad options are refused with EINVAL (status 1): a reconstruction order other than 1 or 2, a specular
+    wall fraction outside [0, 1], a non-positive or non-finite replacement time step (which leaves the
+    steps unchanged)."""
+    import dataclasses
+    with pytest.raises(cuda_lib.UgkwpError) as e:
+        cuda_lib.Solver(CASES["box"], precision=1, order=3)
+    assert e.value.status == 1
+    with pytest.raises(cuda_lib.UgkwpError) as e:
+        cuda_lib.Solver(dataclasses.replace(CASES["plate"], wall_specular=1.5), precision=1)
+    assert e.value.status == 1
+    g = cuda_lib.Solver(CASES["box"], precision=1)
+    d0, _ = g.geometry()
+    for bad in (0.0, -1.0, np.inf, np.nan):
+        dt = d0.copy()
+        dt[3] = bad
+        with pytest.raises(cuda_lib.UgkwpError) as e:
+            g.set_time_steps(dt)
+        assert e.value.status == 1
+    assert np.array_equal(g.geometry()[0], d0)
+
+
 def test_empty_and_single_particle_cells(cuda_lib):
     """N^hp = 1 cells (the sampled particle takes the mean velocity) and cells without new particles, over
     several steps, each compared from an identical snapshot."""
