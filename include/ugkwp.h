@@ -188,8 +188,10 @@ void ugkwp_batch_destroy(ugkwp_batch* batch);
 
 /* Checkpoint: the whole state (step counter, W, retained tally, particles, residual normalisation,
  * particle-mass-ratio EMA, surface sums and counters) to a binary file, and back into a context created
- * with the same mesh, gas, mode and precision. Steps after ugkwp_load reproduce the uninterrupted run
- * (the particle draws are keyed by particle id and step). Both synchronise. */
+ * with the same mesh, gas, mode, precision and options. Steps after ugkwp_load reproduce the uninterrupted
+ * run (the particle draws are keyed by particle id and step). The local time steps are not part of the
+ * state: a run that replaced them (ugkwp_set_time_steps) replaces them again after loading. Both
+ * synchronise. */
 ugkwp_status ugkwp_save(ugkwp_ctx* ctx, const char* path);
 ugkwp_status ugkwp_load(ugkwp_ctx* ctx, const char* path);
 
