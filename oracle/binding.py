@@ -21,6 +21,12 @@ class OracleMesh(C.Structure):
                 ("bc_jmin", C.POINTER(C.c_int32)), ("bc_jmax", C.POINTER(C.c_int32))]
 
 
+class OracleUMesh(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_cells", C.c_int32), ("xv", C.POINTER(C.c_double)),
+                ("yv", C.POINTER(C.c_double)), ("cells", C.POINTER(C.c_int32)), ("n_boundary", C.c_int32),
+                ("boundary", C.POINTER(C.c_int32))]
+
+
 class OracleGas(C.Structure):
     _fields_ = [("omega", C.c_double), ("Pr", C.c_double), ("wall_specular", C.c_double)]
 
@@ -110,20 +116,28 @@ class Oracle:
                  record_faces: bool = False, seed: int | None = None, case_id: int = 0, order: int = 1):
         L = lib()
         m = case.mesh
-        self._keep = [np.ascontiguousarray(a) for a in (m.xv, m.yv)]
-        self._keep += [np.ascontiguousarray(a, dtype=np.int32) for a in (m.bc_imin, m.bc_imax, m.bc_jmin, m.bc_jmax)]
-        mesh = OracleMesh(m.ni, m.nj, m.dim, m.periodic_j, dptr(self._keep[0]), dptr(self._keep[1]),
-                          *[_p(a, C.c_int32) for a in self._keep[2:]])
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (m.xv, m.yv)]
+        unstructured = hasattr(m, "cells")
+        if unstructured:
+            self._keep += [np.ascontiguousarray(a, dtype=np.int32) for a in (m.cells, m.boundary)]
+            mesh = OracleUMesh(len(m.xv), m.ncells, dptr(self._keep[0]), dptr(self._keep[1]),
+                               _p(self._keep[2], C.c_int32), len(m.boundary), _p(self._keep[3], C.c_int32))
+        else:
+            self._keep += [np.ascontiguousarray(a, dtype=np.int32)
+                           for a in (m.bc_imin, m.bc_imax, m.bc_jmin, m.bc_jmax)]
+            mesh = OracleMesh(m.ni, m.nj, m.dim, m.periodic_j, dptr(self._keep[0]), dptr(self._keep[1]),
+                              *[_p(a, C.c_int32) for a in self._keep[2:]])
         gas = OracleGas(case.omega, case.Pr, getattr(case, "wall_specular", 0.0))
         opts = OracleOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
                           int(record_faces), 0, (C.c_double * 4)(*case.ghost_state), int(order))
         self.ctx = C.c_void_p()
-        st = L.oracle_create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
+        create = L.oracle_create_unstructured if unstructured else L.oracle_create
+        st = create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
                              C.c_double(case.Tw), C.c_double(case.cfl), C.c_int32(int(gts)), C.byref(opts),
                              C.byref(self.ctx))
         if st != 0:
             raise OracleError(f"oracle_create failed with status {st}")
-        self.C = m.ni * m.nj
+        self.C = m.ncells
         nf, nw = C.c_int32(), C.c_int32()
         L.oracle_get_geometry(self.ctx, None, None, C.byref(nf), C.byref(nw))
         self.F, self.nwall = nf.value, nw.value
@@ -183,6 +197,14 @@ class Oracle:
         vol = np.zeros(self.C)
         lib().oracle_get_geometry(self.ctx, dptr(dt), dptr(vol), None, None)
         return dt, vol
+
+    def mesh_tables(self):
+        """Cells (x_c, y_c, area) [C, 3]; faces (L, R, tag) [F, 3] and (n_x, n_y, length, d_L, d_R) [F, 5]."""
+        cells = np.zeros((self.C, 3))
+        faces = np.zeros((self.F, 3), dtype=np.int32)
+        fgeo = np.zeros((self.F, 5))
+        self._check(lib().oracle_get_mesh(self.ctx, dptr(cells), _p(faces, C.c_int32), dptr(fgeo)))
+        return cells, faces, fgeo
 
     def particles(self):
         n = lib().oracle_num_particles(self.ctx)

@@ -29,6 +29,19 @@ typedef struct {
     const int32_t* bc_jmax;  /* ni tags of the j = nj faces */
 } oracle_mesh;
 
+/* Unstructured mesh of triangles and convex quadrilaterals. Local face k of a cell is its edge from vertex k
+ * to vertex k + 1 (mod 3 or 4); faces are numbered in order of first appearance over the cells and their
+ * edges, the first cell naming an edge is its L side and the edge keeps that cell's direction. */
+typedef struct {
+    int32_t n_vertices, n_cells;
+    const double* xv;          /* n_vertices coordinates */
+    const double* yv;
+    const int32_t* cells;      /* 4 vertex indices per cell, counter-clockwise; -1 in the fourth: a triangle */
+    int32_t n_boundary;        /* edges of one cell, each tagged exactly once */
+    const int32_t* boundary;   /* 3 per boundary edge: vertex, vertex (either order), tag (wall, far field,
+                                * fixed or symmetry) */
+} oracle_umesh;
+
 typedef struct {
     double omega, Pr;
     double wall_specular;    /* Maxwell wall: fraction 1 - alpha reflected specularly; 0 = fully diffuse */
@@ -50,6 +63,8 @@ typedef struct {
 
 int  oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, double Ma, double Tw,
                    double cfl, int32_t gts, const oracle_opts* opts, oracle_ctx** out);
+int  oracle_create_unstructured(const oracle_umesh* mesh, const oracle_gas* gas, double Kn, double Ma, double Tw,
+                                double cfl, int32_t gts, const oracle_opts* opts, oracle_ctx** out);
 void oracle_destroy(oracle_ctx* cx);
 int  oracle_step(oracle_ctx* cx, int32_t n_steps);
 int  oracle_set_field(oracle_ctx* cx, const double* prim);          /* 4 per cell: rho, U, V, T */
@@ -67,6 +82,8 @@ int  oracle_get_particles(oracle_ctx* cx, int64_t cap, uint64_t* pid, int32_t* c
 int  oracle_set_state(oracle_ctx* cx, int64_t step, const double* W, const int64_t* wret, int64_t np,
                       const uint64_t* pid, const int32_t* cell, const double* x, const double* y,
                       const double* u, const double* v, const double* w, const double* m);
+/* geometry: per cell (x_c, y_c, area), per face (L, R, tag) and (n_x, n_y, length, d_L, d_R); each nullable */
+int  oracle_get_mesh(oracle_ctx* cx, double* cells, int32_t* faces, double* fgeo);
 int  oracle_set_time_steps(oracle_ctx* cx, const double* dt);       /* C local steps, each > 0 (Sec. IV A) */
 int  oracle_get_tallies(oracle_ctx* cx, int64_t* wm, int64_t* wpl, int64_t* wret, int64_t* cross,
                         int64_t* wall, int64_t* frec);

@@ -354,6 +354,8 @@ static void to_frame(const double W[4], double nx, double ny, double out[4])
 
 /* ------------------------------------------------------------------------------- set-up (a0) */
 
+static int boundary_lists(or_ctx* cx);
+
 static int build_geometry(or_ctx* cx, const oracle_mesh* m)
 {
     const int ni = m->ni, nj = m->nj, C = ni * nj;
@@ -522,6 +524,13 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
 #undef VID
     }
     free(fd);
+    return boundary_lists(cx);
+}
+
+/* areas, wall numbering and ghost sources of a built geometry (both mesh kinds) */
+static int boundary_lists(or_ctx* cx)
+{
+    const int C = cx->C, F = cx->F;
     for (int c = 0; c < C; ++c) {
         if (!(cx->vol[c] > 0.0)) return OR_EINVAL;
         cx->inv_vol[c] = 1.0 / cx->vol[c];
@@ -551,6 +560,143 @@ static int build_geometry(or_ctx* cx, const oracle_mesh* m)
         j++;
     }
     return OR_OK;
+}
+
+/* Unstructured mesh of triangles and convex quadrilaterals (Sec. V: the paper's meshes are unstructured).
+ * Local face k of a cell is its edge from vertex k to vertex k + 1 (mod the vertex count). Faces are numbered
+ * in order of first appearance, walking the cells in order and each cell's edges in order; the cell that
+ * first names an edge is its L side and the edge keeps that cell's direction a -> b, so that the unit normal
+ * (e_y, -e_x) / |e| of a counter-clockwise cell points from L to R. A triangle is stored as the degenerate
+ * quadrilateral (v0, v1, v2, v2): the area and centroid formulas and the position sampling of the
+ * quadrilateral then reduce to the triangle's. */
+static int build_geometry_u(or_ctx* cx, const oracle_umesh* m)
+{
+    const int C = m->n_cells, NV = m->n_vertices;
+    cx->ni = C; cx->nj = 1; cx->C = C; cx->dim = 2; cx->periodic_j = 0;
+    /* cells: vertex indices in range and distinct, counter-clockwise and strictly convex */
+    for (int c = 0; c < C; ++c) {
+        const int32_t* v = m->cells + 4 * (size_t)c;
+        const int n = v[3] < 0 ? 3 : 4;
+        for (int q = 0; q < n; ++q) {
+            if (v[q] < 0 || v[q] >= NV) return OR_EINVAL;
+            for (int r = 0; r < q; ++r) if (v[r] == v[q]) return OR_EINVAL;
+        }
+        for (int q = 0; q < n; ++q) {
+            const int a = v[q], b = v[(q + 1) % n], e = v[(q + 2) % n];
+            const double cr = (m->xv[b] - m->xv[a]) * (m->yv[e] - m->yv[b]) - (m->yv[b] - m->yv[a]) * (m->xv[e] - m->xv[b]);
+            if (!(cr > 0.0)) return OR_EINVAL;
+        }
+    }
+    /* faces: an edge list per lower vertex index, searched linearly */
+    int* fa = zalloc(4 * (size_t)C + 1, 4);
+    int* fb = zalloc(4 * (size_t)C + 1, 4);
+    int* fkL = zalloc(4 * (size_t)C + 1, 4);
+    int* fkR = zalloc(4 * (size_t)C + 1, 4);
+    int* fLt = zalloc(4 * (size_t)C + 1, 4);
+    int* fRt = zalloc(4 * (size_t)C + 1, 4);
+    int* fbct = zalloc(4 * (size_t)C + 1, 4);
+    int* nxt = zalloc(4 * (size_t)C + 1, 4);
+    int* head = zalloc(NV > 0 ? NV : 1, 4);
+    int* cf = zalloc(4 * (size_t)C, 4);
+    int st = OR_OK, F = 0;
+    for (int v = 0; v < NV; ++v) head[v] = -1;
+    for (int c = 0; c < C && !st; ++c) {
+        const int32_t* v = m->cells + 4 * (size_t)c;
+        const int n = v[3] < 0 ? 3 : 4;
+        for (int k = 0; k < n && !st; ++k) {
+            const int a = v[k], b = v[(k + 1) % n];
+            const int lo = a < b ? a : b, hi = a < b ? b : a;
+            int f = -1;
+            for (int g = head[lo]; g >= 0; g = nxt[g])
+                if ((fa[g] < fb[g] ? fb[g] : fa[g]) == hi) { f = g; break; }
+            if (f < 0) {
+                f = F++;
+                fa[f] = a; fb[f] = b; fLt[f] = c; fkL[f] = k; fRt[f] = -1; fkR[f] = -1; fbct[f] = 0;
+                nxt[f] = head[lo]; head[lo] = f;
+            } else if (fRt[f] >= 0 || fa[f] != b) {
+                st = OR_EINVAL;   /* an edge of three cells, or two cells that overlap along it */
+            } else {
+                fRt[f] = c; fkR[f] = k;
+            }
+            cf[4 * (size_t)c + k] = f;
+        }
+    }
+    /* boundary tags: every edge of one cell gets exactly one */
+    for (int e = 0; e < m->n_boundary && !st; ++e) {
+        const int a = m->boundary[3 * e], b = m->boundary[3 * e + 1], tag = m->boundary[3 * e + 2];
+        if (a < 0 || a >= NV || b < 0 || b >= NV) { st = OR_EINVAL; break; }
+        if (tag != OR_BC_WALL && tag != OR_BC_FARFIELD && tag != OR_BC_FIXED && tag != OR_BC_SYMMETRY) { st = OR_EINVAL; break; }
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        int f = -1;
+        for (int g = head[lo]; g >= 0; g = nxt[g])
+            if ((fa[g] < fb[g] ? fb[g] : fa[g]) == hi) { f = g; break; }
+        if (f < 0 || fRt[f] >= 0 || fbct[f] != 0) { st = OR_EINVAL; break; }
+        fbct[f] = tag;
+    }
+    for (int f = 0; f < F && !st; ++f) if (fRt[f] < 0 && fbct[f] == 0) st = OR_EINVAL;
+    if (!st) {
+        cx->F = F;
+        cx->vol = zalloc(C, 8); cx->inv_vol = zalloc(C, 8); cx->xc = zalloc(C, 8); cx->yc = zalloc(C, 8);
+        cx->nfc = zalloc(C, 4);
+        cx->cface = zalloc(4 * C, 4); cx->csgn = zalloc(4 * C, 4); cx->cnbr = zalloc(4 * C, 4);
+        cx->cnk = zalloc(4 * C, 4); cx->cbc = zalloc(4 * C, 4);
+        cx->cnx = zalloc(4 * C, 8); cx->cny = zalloc(4 * C, 8); cx->cd = zalloc(4 * C, 8);
+        cx->cshift = zalloc(4 * C, 8); cx->cvx = zalloc(4 * C, 8); cx->cvy = zalloc(4 * C, 8);
+        cx->xl = zalloc(C, 8); cx->xr = zalloc(C, 8);
+        cx->fL = zalloc(F, 4); cx->fR = zalloc(F, 4); cx->fbc = zalloc(F, 4); cx->fwall = zalloc(F, 4);
+        cx->fnx = zalloc(F, 8); cx->fny = zalloc(F, 8); cx->fs = zalloc(F, 8); cx->fdL = zalloc(F, 8);
+        cx->fdR = zalloc(F, 8); cx->finv_s = zalloc(F, 8);
+        cx->fax = zalloc(F, 8); cx->fay = zalloc(F, 8); cx->fex = zalloc(F, 8); cx->fey = zalloc(F, 8);
+        double* fd = zalloc(F, 8);
+        for (int f = 0; f < F; ++f) {
+            const int a = fa[f], b = fb[f];
+            const double ex = m->xv[b] - m->xv[a], ey = m->yv[b] - m->yv[a];
+            const double len = sqrt(ex * ex + ey * ey);
+            cx->fax[f] = m->xv[a]; cx->fay[f] = m->yv[a]; cx->fex[f] = ex; cx->fey[f] = ey;
+            cx->fs[f] = len;
+            cx->fnx[f] = ey / len; cx->fny[f] = -ex / len;
+            cx->fL[f] = fLt[f]; cx->fR[f] = fRt[f]; cx->fbc[f] = fRt[f] < 0 ? fbct[f] : 0;
+            fd[f] = cx->fnx[f] * m->xv[a] + cx->fny[f] * m->yv[a];
+        }
+        for (int c = 0; c < C; ++c) {
+            const int32_t* v = m->cells + 4 * (size_t)c;
+            const int n = v[3] < 0 ? 3 : 4;
+            double X[4], Y[4];
+            for (int q = 0; q < 4; ++q) {
+                const int vq = q < n ? v[q] : v[2];
+                X[q] = m->xv[vq]; Y[q] = m->yv[vq];
+                cx->cvx[4 * c + q] = X[q]; cx->cvy[4 * c + q] = Y[q];
+            }
+            cx->vol[c] = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[1]) - (X[3] - X[1]) * (Y[2] - Y[0]));
+            const double A1 = 0.5 * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+            const double A2 = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+            cx->xc[c] = (A1 * (X[0] + X[1] + X[2]) + A2 * (X[0] + X[2] + X[3])) / (3.0 * (A1 + A2));
+            cx->yc[c] = (A1 * (Y[0] + Y[1] + Y[2]) + A2 * (Y[0] + Y[2] + Y[3])) / (3.0 * (A1 + A2));
+            cx->nfc[c] = n;
+            for (int k = 0; k < 4; ++k) {
+                const int q = 4 * c + k;
+                if (k >= n) { cx->cnbr[q] = -1; cx->cnk[q] = -1; cx->csgn[q] = 1; continue; }
+                const int f = cf[q];
+                const int isL = fLt[f] == c;
+                cx->cface[q] = f;
+                cx->csgn[q] = isL ? 1 : -1;
+                cx->cnx[q] = isL ? cx->fnx[f] : -cx->fnx[f];
+                cx->cny[q] = isL ? cx->fny[f] : -cx->fny[f];
+                cx->cd[q] = isL ? fd[f] : -fd[f];
+                if (fRt[f] < 0) { cx->cnbr[q] = -1; cx->cnk[q] = -1; cx->cbc[q] = fbct[f]; }
+                else { cx->cnbr[q] = isL ? fRt[f] : fLt[f]; cx->cnk[q] = isL ? fkR[f] : fkL[f]; cx->cbc[q] = 0; }
+            }
+        }
+        for (int f = 0; f < F; ++f) {
+            const int L = cx->fL[f], R = cx->fR[f];
+            cx->fdL[f] = fd[f] - (cx->fnx[f] * cx->xc[L] + cx->fny[f] * cx->yc[L]);
+            cx->fdR[f] = R >= 0 ? (cx->fnx[f] * cx->xc[R] + cx->fny[f] * cx->yc[R]) - fd[f] : cx->fdL[f];
+        }
+        free(fd);
+    }
+    free(fa); free(fb); free(fkL); free(fkR); free(fLt); free(fRt); free(fbct); free(nxt); free(head); free(cf);
+    if (st) return st;
+    return boundary_lists(cx);
 }
 
 /* mass and remaining-time scaling of a crossing from cell c through its local face k: dt_R / dt_L (Eq. 41) */
@@ -612,6 +758,9 @@ int oracle_fixed_exponents(oracle_ctx* cx, int32_t* out)
     return OR_OK;
 }
 
+static int finish_create(or_ctx* cx, const oracle_gas* gas, double Kn, double Ma, double Tw, double cfl,
+                         int32_t gts, const oracle_opts* opts, oracle_ctx** out);
+
 int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, double Ma, double Tw,
                   double cfl, int32_t gts, const oracle_opts* opts, oracle_ctx** out)
 {
@@ -621,6 +770,27 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     or_ctx* cx = zalloc(1, sizeof(or_ctx));
     int st = build_geometry(cx, mesh);
     if (st) { oracle_destroy(cx); return st; }
+    return finish_create(cx, gas, Kn, Ma, Tw, cfl, gts, opts, out);
+}
+
+int oracle_create_unstructured(const oracle_umesh* mesh, const oracle_gas* gas, double Kn, double Ma, double Tw,
+                               double cfl, int32_t gts, const oracle_opts* opts, oracle_ctx** out)
+{
+    if (!mesh || !gas || !opts || !out || mesh->n_cells <= 0 || mesh->n_vertices <= 0 || !mesh->xv || !mesh->yv ||
+        !mesh->cells || mesh->n_boundary < 0 || (mesh->n_boundary > 0 && !mesh->boundary))
+        return OR_EINVAL;
+    if (mesh->n_cells >= (1 << 21)) return OR_EINVAL;
+    if (!(gas->wall_specular >= 0.0 && gas->wall_specular <= 1.0)) return OR_EINVAL;
+    or_ctx* cx = zalloc(1, sizeof(or_ctx));
+    int st = build_geometry_u(cx, mesh);
+    if (st) { oracle_destroy(cx); return st; }
+    return finish_create(cx, gas, Kn, Ma, Tw, cfl, gts, opts, out);
+}
+
+/* everything after the geometry: time steps, bounds, state arrays, the freestream start */
+static int finish_create(or_ctx* cx, const oracle_gas* gas, double Kn, double Ma, double Tw, double cfl,
+                         int32_t gts, const oracle_opts* opts, oracle_ctx** out)
+{
     const int C = cx->C, F = cx->F;
     cx->prec = opts->precision; cx->wave_only = opts->wave_only; cx->record_faces = opts->record_faces;
     cx->order = opts->order == 2 ? 2 : 1;
@@ -1296,6 +1466,22 @@ int oracle_get_geometry(oracle_ctx* cx, double* dt, double* vol, int32_t* nfaces
     if (vol) memcpy(vol, cx->vol, (size_t)cx->C * 8);
     if (nfaces) *nfaces = cx->F;
     if (nwall) *nwall = cx->nwall;
+    return OR_OK;
+}
+
+int oracle_get_mesh(oracle_ctx* cx, double* cells, int32_t* faces, double* fgeo)
+{
+    if (!cx) return OR_EINVAL;
+    for (int c = 0; cells && c < cx->C; ++c) {
+        cells[3 * c] = cx->xc[c]; cells[3 * c + 1] = cx->yc[c]; cells[3 * c + 2] = cx->vol[c];
+    }
+    for (int f = 0; f < cx->F; ++f) {
+        if (faces) { faces[3 * f] = cx->fL[f]; faces[3 * f + 1] = cx->fR[f]; faces[3 * f + 2] = cx->fbc[f]; }
+        if (fgeo) {
+            double* g = fgeo + 5 * f;
+            g[0] = cx->fnx[f]; g[1] = cx->fny[f]; g[2] = cx->fs[f]; g[3] = cx->fdL[f]; g[4] = cx->fdR[f];
+        }
+    }
     return OR_OK;
 }
 

@@ -9,8 +9,9 @@ Non-dimensionalisation (a reading; the paper does not state one): rho_inf = 1, T
 2 R T_inf = 1, and U_inf = Ma * sqrt(gamma R T_inf) with gamma = 5/3 (monatomic gas, three translational
 degrees of freedom, no internal ones; Sec. II "Gas-kinetic theory", eq. (1) with D = 0).
 
-Meshes are structured: ni x nj quadrilaterals with vertex (i, j) stored at index i + (ni + 1) * j. For a
-1-D line mesh nj = 1 and only the x coordinates matter.
+Structured meshes (`Mesh`) are ni x nj quadrilaterals with vertex (i, j) stored at index i + (ni + 1) * j; for
+a 1-D line mesh nj = 1 and only the x coordinates matter. Unstructured meshes (`UMesh`) list triangles and
+convex quadrilaterals by counter-clockwise vertex indices, with a tag for every boundary edge.
 """
 from __future__ import annotations
 
@@ -32,6 +33,7 @@ BC_PERIODIC = 5    # 1-D only: the two ends of the line are joined
 MESH_LINE = 0
 MESH_OMESH = 1
 MESH_PLATE = 2
+MESH_UNSTRUCTURED = 3
 
 
 @dataclass
@@ -52,6 +54,23 @@ class Mesh:
     @property
     def ncells(self) -> int:
         return self.ni * self.nj
+
+
+@dataclass
+class UMesh:
+    """Triangles and convex quadrilaterals: `cells` (C, 4) counter-clockwise vertex indices with -1 in the last
+    column for a triangle; `boundary` (n, 3) rows (vertex, vertex, tag), one per edge of a single cell."""
+    xv: np.ndarray
+    yv: np.ndarray
+    cells: np.ndarray
+    boundary: np.ndarray
+    info: dict = field(default_factory=dict)
+    kind: int = MESH_UNSTRUCTURED
+    dim: int = 2
+
+    @property
+    def ncells(self) -> int:
+        return int(self.cells.shape[0])
 
 
 def freestream_speed(Ma: float) -> float:
@@ -131,6 +150,81 @@ def plate_mesh(ni: int = 240, nj: int = 120, h1: float = 1e-4, ratio: float = 1.
                 bc_jmin, np.full(ni, BC_FARFIELD, np.int32), info={"L": L, "ratio": ratio})
 
 
+def _vid(m: Mesh, i: int, j: int) -> int:
+    return i + (m.ni + 1) * (0 if (m.periodic_j and j == m.nj) else j)
+
+
+def as_unstructured(m: Mesh) -> UMesh:
+    """A 2-D structured mesh restated as an unstructured one: the same vertices, cell c = i + ni j with corners
+    (i, j), (i+1, j), (i+1, j+1), (i, j+1) and the same boundary tags."""
+    assert m.dim == 2
+    cells = np.array([[_vid(m, i, j), _vid(m, i + 1, j), _vid(m, i + 1, j + 1), _vid(m, i, j + 1)]
+                      for j in range(m.nj) for i in range(m.ni)], np.int32)
+    bnd = [(_vid(m, 0, j), _vid(m, 0, j + 1), m.bc_imin[j]) for j in range(m.nj)]
+    bnd += [(_vid(m, m.ni, j), _vid(m, m.ni, j + 1), m.bc_imax[j]) for j in range(m.nj)]
+    if not m.periodic_j:
+        bnd += [(_vid(m, i, 0), _vid(m, i + 1, 0), m.bc_jmin[i]) for i in range(m.ni)]
+        bnd += [(_vid(m, i, m.nj), _vid(m, i + 1, m.nj), m.bc_jmax[i]) for i in range(m.ni)]
+    return UMesh(m.xv.copy(), m.yv.copy(), cells, np.array(bnd, np.int32).reshape(-1, 3), info=dict(m.info))
+
+
+def split_quads(m: Mesh, first_tri_row: int = 0, axis: str = "i") -> UMesh:
+    """A 2-D structured mesh with every quadrilateral from row `first_tri_row` on (rows counted along `axis`)
+    cut into two triangles, the diagonal alternating like a chequerboard; the quadrilaterals before that row
+    stay (a hybrid mesh: quadrilateral layers at the wall, triangles outside)."""
+    u = as_unstructured(m)
+    cells = []
+    for c, q in enumerate(u.cells):
+        i, j = c % m.ni, c // m.ni
+        if (i if axis == "i" else j) < first_tri_row:
+            cells.append(q)
+        elif (i + j) % 2 == 0:
+            cells += [[q[0], q[1], q[2], -1], [q[0], q[2], q[3], -1]]
+        else:
+            cells += [[q[0], q[1], q[3], -1], [q[1], q[2], q[3], -1]]
+    u.cells = np.array(cells, np.int32)
+    u.info["first_tri_row"] = first_tri_row
+    return u
+
+
+def jitter_interior(u: UMesh, seed: int, amount: float) -> UMesh:
+    """Moves every vertex that lies on no boundary edge by a seeded uniform offset of up to `amount` times the
+    shortest edge at that vertex in each coordinate (the cells must stay counter-clockwise and convex)."""
+    rng = np.random.default_rng(seed)
+    on_b = np.zeros(len(u.xv), bool)
+    on_b[u.boundary[:, 0]] = True
+    on_b[u.boundary[:, 1]] = True
+    hmin = np.full(len(u.xv), np.inf)
+    for q in u.cells:
+        vs = [v for v in q if v >= 0]
+        for a, b in zip(vs, vs[1:] + vs[:1]):
+            h = math.hypot(u.xv[b] - u.xv[a], u.yv[b] - u.yv[a])
+            hmin[a] = min(hmin[a], h)
+            hmin[b] = min(hmin[b], h)
+    move = ~on_b & np.isfinite(hmin)
+    dx = rng.uniform(-1.0, 1.0, len(u.xv)) * amount * np.where(move, hmin, 0.0)
+    dy = rng.uniform(-1.0, 1.0, len(u.xv)) * amount * np.where(move, hmin, 0.0)
+    return UMesh(u.xv + dx, u.yv + dy, u.cells.copy(), u.boundary.copy(), info=dict(u.info, jitter=amount))
+
+
+def box_mesh(nx: int, ny: int, x0: float = 0.0, x1: float = 1.0, y0: float = 0.0, y1: float = 1.0,
+             tags=(BC_FARFIELD, BC_FARFIELD, BC_FARFIELD, BC_FARFIELD)) -> Mesh:
+    """Uniform Cartesian nx x ny mesh of [x0, x1] x [y0, y1]; tags of the sides x0, x1, y0, y1."""
+    xs = np.linspace(x0, x1, nx + 1)
+    ys = np.linspace(y0, y1, ny + 1)
+    return Mesh(MESH_PLATE, nx, ny, 2, 0, np.tile(xs, ny + 1), np.repeat(ys, nx + 1),
+                np.full(ny, tags[0], np.int32), np.full(ny, tags[1], np.int32),
+                np.full(nx, tags[2], np.int32), np.full(nx, tags[3], np.int32), info={"box": (x0, x1, y0, y1)})
+
+
+def tri_omesh(n_quad: int, ni: int, nj: int, h1: float, r_out: float, r_cyl: float = 0.5) -> UMesh:
+    """Hybrid cylinder mesh: the O-mesh of `omesh` with its first n_quad radial layers kept as quadrilaterals
+    and the ni - n_quad outer layers cut into triangles; n_quad nj + 2 (ni - n_quad) nj cells."""
+    u = split_quads(omesh(ni, nj, h1, r_out, r_cyl), n_quad, "i")
+    u.info.update({"r_cyl": r_cyl, "r_out": r_out, "h1": h1, "ni": ni, "nj": nj, "n_quad": n_quad})
+    return u
+
+
 def rankine_hugoniot(Ma: float, gamma: float = GAMMA):
     """Downstream (rho, u, T) of a normal shock for upstream (1, U_inf(Ma), 1): textbook jump relations."""
     rho2 = (gamma + 1.0) * Ma ** 2 / ((gamma - 1.0) * Ma ** 2 + 2.0)
@@ -156,7 +250,7 @@ def shock_initial_field(mesh: Mesh, Ma: float) -> np.ndarray:
 @dataclass
 class Case:
     name: str
-    mesh: Mesh
+    mesh: Mesh | UMesh
     Kn: float
     Ma: float
     Tw: float
@@ -193,6 +287,14 @@ def case_cylinder_kn01() -> Case:
 
 def case_cylinder_kn001() -> Case:
     return case_cylinder(240, 320, 1e-4, 20.0, Kn=0.01, Ma=15.0, n_ref=150)
+
+
+def case_cylinder_tri(n_quad: int = 13, ni: int = 33, nj: int = 140, h1: float = 0.005, r_out: float = 15.0,
+                      Kn: float = 0.1, Ma: float = 5.0, Tw: float = 1.0, n_ref: int = 100, cfl: float = 0.8) -> Case:
+    """Hypersonic cylinder on a hybrid unstructured mesh of the size of the paper's Kn = 0.1 case (Sec. V A:
+    7,420 cells, first wall cell 0.01 R): 13 quadrilateral layers at the wall and 20 triangulated layers."""
+    m = tri_omesh(n_quad, ni, nj, h1, r_out)
+    return Case(f"cylinder_tri_{m.ncells}_Kn{Kn}_Ma{Ma}", m, Kn=Kn, Ma=Ma, Tw=Tw, cfl=cfl, n_ref=n_ref)
 
 
 def case_periodic_box(ni: int = 16, end_ratio: float = 50.0, n_ref: int = 50, Kn: float = 0.05,

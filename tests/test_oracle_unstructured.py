@@ -1,0 +1,237 @@
+"""Unstructured meshes of triangles and convex quadrilaterals (§8f f1: the paper's meshes, Sec. V, are
+unstructured), pinned on the CPU oracle.
+
+- the geometry tables (areas, centroids, face normals, lengths, distances) against the shoelace and
+  centroid formulas computed here from the vertices, and the face closure of every cell;
+- a structured O-mesh restated as an unstructured one gives the structured oracle's results (the structured
+  path is pinned elsewhere), in the particle-free mode and with particles;
+- a uniform flow on a jittered triangle mesh stays uniform (free-stream preservation, orders 1 and 2);
+- a closed box of triangles with mirror sides (symmetry, specular walls) conserves mass and energy with particles, and every particle
+  ends a step inside the cell that holds it;
+- malformed meshes are rejected.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import binding as ob
+from paper_2607_09552_b300 import workloads as wl
+
+
+def _tri_box(nx=8, ny=6, tags=(wl.BC_FARFIELD,) * 4, jitter=0.2, seed=3):
+    u = wl.split_quads(wl.box_mesh(nx, ny, tags=tags), 0, "i")
+    return wl.jitter_interior(u, seed, jitter) if jitter else u
+
+
+def _polygon(m, c):
+    vs = [v for v in m.cells[c] if v >= 0]
+    return np.array([[m.xv[v], m.yv[v]] for v in vs])
+
+
+def _shoelace(P):
+    x, y = P[:, 0], P[:, 1]
+    xn, yn = np.roll(x, -1), np.roll(y, -1)
+    cr = x * yn - xn * y
+    A = 0.5 * cr.sum()
+    return A, (x + xn) @ cr / (6 * A), (y + yn) @ cr / (6 * A)
+
+
+def _case(mesh, **kw):
+    args = dict(Kn=0.05, Ma=2.0, Tw=1.0, cfl=0.5, n_ref=30)
+    args.update(kw)
+    return wl.Case("umesh", mesh, **args)
+
+
+@pytest.mark.parametrize("which", ["tri_box", "hybrid_cylinder"])
+def test_geometry_tables(which):
+    m = _tri_box() if which == "tri_box" else wl.tri_omesh(3, 6, 24, 2e-2, 3.0)
+    o = ob.Oracle(_case(m), precision=1, wave_only=True)
+    cells, faces, fg = o.mesh_tables()
+    C = m.ncells
+    nfc = np.where(m.cells[:, 3] < 0, 3, 4)
+    assert o.F == (nfc.sum() + len(m.boundary)) // 2
+    scale = max(np.ptp(m.xv), np.ptp(m.yv))
+    closure = np.zeros((C, 2))
+    for f in range(o.F):
+        L, R, tag = faces[f]
+        nx, ny, s, dL, dR = fg[f]
+        assert abs(math.hypot(nx, ny) - 1.0) < 1e-14
+        # the face is the edge of L whose outward normal it carries: length, normal and distance from L's centroid
+        P = _polygon(m, L)
+        E = np.roll(P, -1, axis=0) - P
+        lens = np.hypot(E[:, 0], E[:, 1])
+        normals = np.stack([E[:, 1], -E[:, 0]], 1) / lens[:, None]
+        k = int(np.argmax(normals @ [nx, ny]))
+        np.testing.assert_allclose([nx, ny], normals[k], atol=1e-14)
+        assert s == pytest.approx(lens[k], rel=1e-14)
+        assert dL == pytest.approx(normals[k] @ (P[k] - cells[L, :2]), rel=1e-12, abs=1e-14 * scale)
+        closure[L] += s * np.array([nx, ny])
+        if R >= 0:
+            assert tag == 0
+            # R names the same edge, reversed
+            Q = _polygon(m, R)
+            assert any(np.allclose(Q[j], P[(k + 1) % len(P)]) and np.allclose(Q[(j + 1) % len(Q)], P[k])
+                       for j in range(len(Q)))
+            assert dR == pytest.approx(np.array([nx, ny]) @ (cells[R, :2] - P[k]), rel=1e-12, abs=1e-14 * scale)
+            assert dL > 0 and dR > 0
+            closure[R] -= s * np.array([nx, ny])
+        else:
+            assert tag in (wl.BC_WALL, wl.BC_FARFIELD, wl.BC_FIXED, wl.BC_SYMMETRY) and dR == dL
+    for c in range(C):
+        A, cx, cy = _shoelace(_polygon(m, c))
+        assert cells[c, 2] == pytest.approx(A, rel=1e-13)
+        np.testing.assert_allclose(cells[c, :2], [cx, cy], rtol=0, atol=1e-13 * scale)
+    per = np.array([np.hypot(*(np.roll(_polygon(m, c), -1, 0) - _polygon(m, c)).T).sum() for c in range(C)])
+    assert np.all(np.hypot(closure[:, 0], closure[:, 1]) < 1e-14 * per)
+    # boundary tags as given
+    tags_in = np.sort(m.boundary[:, 2])
+    assert np.array_equal(np.sort(faces[faces[:, 1] < 0, 2]), tags_in)
+
+
+def test_triangle_centroid_is_vertex_mean():
+    m = _tri_box(4, 3)
+    cells, _, _ = ob.Oracle(_case(m), precision=1, wave_only=True).mesh_tables()
+    for c in range(m.ncells):
+        np.testing.assert_allclose(cells[c, :2], _polygon(m, c).mean(axis=0), rtol=0, atol=1e-15)
+
+
+def _omesh_case(**kw):
+    return wl.case_cylinder(8, 24, 1e-2, 4.0, Kn=0.1, Ma=3.0, n_ref=20, **kw)
+
+
+@pytest.mark.parametrize("gts", [False, True])
+def test_structured_mesh_restated_wave_only(gts):
+    s = _omesh_case()
+    u = _omesh_case()
+    u.mesh = wl.as_unstructured(s.mesh)
+    a = ob.Oracle(s, gts=gts, precision=1, wave_only=True)
+    b = ob.Oracle(u, gts=gts, precision=1, wave_only=True)
+    assert (a.F, a.nwall) == (b.F, b.nwall)
+    np.testing.assert_allclose(b.geometry()[0], a.geometry()[0], rtol=1e-14)
+    a.step(6)
+    b.step(6)
+    Wa, Wb = a.field()[0], b.field()[0]
+    np.testing.assert_allclose(Wb, Wa, rtol=1e-11, atol=1e-12 * np.abs(Wa).max())
+    # same wall faces in the same order
+    np.testing.assert_allclose(b.surface(False)[0], a.surface(False)[0], rtol=1e-10)
+
+
+def test_structured_mesh_restated_with_particles():
+    s = _omesh_case()
+    u = _omesh_case()
+    u.mesh = wl.as_unstructured(s.mesh)
+    a = ob.Oracle(s, precision=1)
+    b = ob.Oracle(u, precision=1)
+    a.step(2)
+    b.step(2)
+    sa, sb = a.stats(), b.stats()
+    assert sa[0] == sb[0] and sa[2] == sb[2]          # retained and kept particle counts
+    Wa, Wb = a.field()[0], b.field()[0]
+    np.testing.assert_allclose(Wb, Wa, rtol=1e-9, atol=1e-10 * np.abs(Wa).max())
+    pa, pb = a.particles(), b.particles()
+    ia, ib = np.argsort(pa["pid"]), np.argsort(pb["pid"])
+    assert np.array_equal(pa["pid"][ia], pb["pid"][ib])
+    assert np.array_equal(pa["cell"][ia], pb["cell"][ib])
+    np.testing.assert_allclose(pb["x"][ib], pa["x"][ia], atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_free_stream_preserved_on_triangles(order):
+    m = _tri_box(10, 8, jitter=0.25)
+    o = ob.Oracle(_case(m, Ma=2.0), precision=1, wave_only=True, order=order)
+    W0 = o.field()[0].copy()
+    o.step(10)
+    W = o.field()[0]
+    scale = np.abs(W0).max(axis=0)
+    scale[2] = scale[1]                                 # V = 0: scale the y momentum by the x momentum
+    assert np.max(np.abs(W - W0) / scale) < 1e-12
+
+
+def _mirror_box_case(n_ref=40):
+    # mirror sides: symmetry at x = 0 and 1, fully specular Maxwell walls at y = 0 and 1
+    m = _tri_box(8, 6, tags=(wl.BC_SYMMETRY, wl.BC_SYMMETRY, wl.BC_WALL, wl.BC_WALL), jitter=0.2)
+    case = _case(m, Ma=0.5, n_ref=n_ref, Kn=0.5, wall_specular=1.0)
+    cells, _, _ = ob.Oracle(case, precision=1, wave_only=True).mesh_tables()
+    x, y = cells[:, 0], cells[:, 1]
+    prim = np.zeros((m.ncells, 4))
+    prim[:, 0] = 1.0 + 0.3 * np.cos(np.pi * x) * np.cos(np.pi * y)
+    prim[:, 1] = 0.2 * np.sin(np.pi * x)
+    prim[:, 2] = -0.1 * np.sin(np.pi * y)
+    prim[:, 3] = 1.0 + 0.1 * x
+    case.init_prim = prim
+    return case
+
+
+def test_mirror_box_of_triangles_conserves_mass_and_energy():
+    # global step: with local steps the cell totals are not conserved while the field changes (the mass
+    # scaling of Eq. 41 only balances them on average at steady state)
+    o = ob.Oracle(_mirror_box_case(), gts=True, precision=1)
+    _, vol = o.geometry()
+
+    def totals():
+        W = o.field()[0]
+        return np.array([vol @ W[:, 0], vol @ W[:, 3]])
+
+    t0 = totals()
+    o.step(10)
+    st = o.stats()
+    assert st[5] > 0 and st[6] > 0                     # particles crossed faces and hit the walls
+    np.testing.assert_allclose(totals(), t0, rtol=1e-12)
+
+
+def _inside(P, x, y, tol):
+    E = np.roll(P, -1, axis=0) - P
+    cr = E[:, 0] * (y - P[:, 1]) - E[:, 1] * (x - P[:, 0])
+    return np.all(cr / np.hypot(E[:, 0], E[:, 1]) >= -tol)
+
+
+@pytest.mark.parametrize("which", ["mirror_box", "hybrid_cylinder"])
+def test_particles_end_inside_their_cells(which):
+    if which == "mirror_box":
+        case = _mirror_box_case(n_ref=20)
+    else:
+        case = wl.Case("hyb", wl.tri_omesh(3, 6, 24, 2e-2, 3.0), Kn=0.1, Ma=3.0, Tw=1.0, cfl=0.8, n_ref=20)
+    o = ob.Oracle(case, precision=1)
+    o.step(3)
+    p = o.particles()
+    assert len(p["pid"]) > 1000
+    m = case.mesh
+    for k in range(len(p["pid"])):
+        assert _inside(_polygon(m, p["cell"][k]), p["x"][k], p["y"][k], 1e-12)
+
+
+def _bad(mesh):
+    with pytest.raises(ob.OracleError):
+        ob.Oracle(_case(mesh), precision=1, wave_only=True)
+
+
+def test_malformed_meshes_rejected():
+    good = _tri_box(2, 2, jitter=0.0)
+    ob.Oracle(_case(good), precision=1, wave_only=True)
+
+    def edit(cells=None, boundary=None):
+        return wl.UMesh(good.xv, good.yv, good.cells if cells is None else cells,
+                        good.boundary if boundary is None else boundary)
+
+    cw = good.cells.copy()
+    cw[0, :3] = cw[0, [0, 2, 1]]                                  # clockwise triangle
+    _bad(edit(cells=cw))
+    oob = good.cells.copy()
+    oob[1, 1] = len(good.xv)                                      # vertex index out of range
+    _bad(edit(cells=oob))
+    _bad(edit(boundary=good.boundary[1:]))                        # a boundary edge without a tag
+    _bad(edit(boundary=np.vstack([good.boundary, good.boundary[:1]])))   # tagged twice
+    per = good.boundary.copy()
+    per[0, 2] = wl.BC_PERIODIC                                    # periodic: 1-D only
+    _bad(edit(boundary=per))
+    inner = np.vstack([good.boundary, [[good.cells[0, 0], good.cells[0, 2], wl.BC_WALL]]])
+    _bad(edit(boundary=inner))                                    # a tag on an interior edge
+    three = np.vstack([good.cells, good.cells[:1]])               # an edge of three cells
+    _bad(edit(cells=three))
+    # a non-convex quadrilateral
+    q = wl.UMesh(np.array([0.0, 1.0, 0.2, 0.0]), np.array([0.0, 0.0, 0.2, 1.0]), np.array([[0, 1, 2, 3]], np.int32),
+                 np.array([[0, 1, 2], [1, 2, 2], [2, 3, 2], [3, 0, 2]], np.int32))
+    _bad(q)
+    ok = wl.UMesh(np.array([0.0, 1.0, 0.6, 0.0]), np.array([0.0, 0.0, 0.6, 1.0]), q.cells, q.boundary)
+    ob.Oracle(_case(ok), precision=1, wave_only=True)
