@@ -96,15 +96,22 @@ class Clocks:
 
 
 def bench_case(args=None):
-    """The throughput workload: the Kn 0.1 cylinder (the default), or with --case kn001 the dense-regime one."""
-    if args is not None and getattr(args, "case", "kn01") == "kn001":
+    """The throughput workload: the Kn 0.1 cylinder (the default), with --case kn001 the dense-regime one, with
+    --case tri the Kn 0.1 cylinder on the hybrid unstructured mesh of the paper's cell count."""
+    which = getattr(args, "case", "kn01") if args is not None else "kn01"
+    if which == "kn001":
         return wl.case_cylinder_kn001()
+    if which == "tri":
+        return wl.case_cylinder_tri()
     return wl.case_cylinder_kn01()
 
 
 WORKLOADS = {
     "cylinder_120x160_Kn0.1_Ma5.0": "cylinder O-mesh 120x160, Kn=0.1 (lambda/D), Ma=5, Tw/Tinf=1, N_ref=100, CFL 0.8, LTS",
     "cylinder_240x320_Kn0.01_Ma15.0": "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8, LTS",
+    "cylinder_tri_7420_Kn0.1_Ma5.0": "cylinder hybrid unstructured mesh, 7420 cells (1820 quadrilaterals in 13 wall "
+                                     "layers, 5600 triangles), wall cell 0.01 R, Kn=0.1 (lambda/D), Ma=5, Tw/Tinf=1, "
+                                     "N_ref=100, CFL 0.8, LTS",
 }
 
 
@@ -184,7 +191,7 @@ def run_ours(args):
         part_ms = stage_ms["particles"] / max(nprof, 1)
         per_launch = prof_psteps / max(nprof, 1)
         achieved = BYTES_PER_PARTICLE_STEP * per_launch / (part_ms * 1e-3) / 1e9
-        traffic = particles_traffic(per_launch)
+        traffic = particles_traffic(per_launch, case.name)
         cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
         cfg = config_dict(case, args.burn, "512 MB L2 flush before every timed step, outside the events")
         cfg["reconstruction_order"] = args.order
@@ -230,14 +237,14 @@ def transport_source_hash(t) -> str:
     return h.hexdigest()[:16]
 
 
-def particles_traffic(per_launch: float):
+def particles_traffic(per_launch: float, workload: str):
     """DRAM bytes (read + written) of one transport-kernel launch: the bytes per particle of the committed ncu
     capture (profiles/particles_traffic.json) times this launch's particles; None when the transport kernel's
-    source has changed since the capture."""
+    source has changed since the capture or the workload is not the captured one."""
     tfile = os.path.join(ROOT, "profiles", "particles_traffic.json")
     try:
         t = json.load(open(tfile))
-        if transport_source_hash(t) != t["region_sha256_16"]:
+        if transport_source_hash(t) != t["region_sha256_16"] or t["workload"] != workload:
             return None
         return float(t["bytes_per_particle"]) * per_launch
     except (OSError, KeyError, ValueError):
@@ -263,7 +270,10 @@ def gpu_launches_per_step(case):
     # scatter (they return at once except on sort steps), update; the ghost-source parameter and particle
     # kernels when the mesh has far-field or fixed faces; the heat-flux tally when Pr != 1
     m = case.mesh
-    tags = list(m.bc_imin) + list(m.bc_imax) + list(m.bc_jmin) + list(m.bc_jmax)
+    if hasattr(m, "cells"):
+        tags = list(m.boundary[:, 2])
+    else:
+        tags = list(m.bc_imin) + list(m.bc_imax) + list(m.bc_jmin) + list(m.bc_jmax)
     ghosts = any(t in (wl.BC_FARFIELD, wl.BC_FIXED) for t in tags)
     return 13 + (2 if ghosts else 0) + (1 if case.Pr != 1.0 else 0)
 
@@ -347,7 +357,7 @@ def run_reference(args):
 
 def stagnation_pair(case):
     """Wall-face indices adjacent to theta = pi (the stagnation point of the +x freestream on the O-mesh)."""
-    nj = case.mesh.nj
+    nj = case.mesh.info["nj"] if hasattr(case.mesh, "cells") else case.mesh.nj
     return nj // 2 - 1, nj // 2
 
 
@@ -702,7 +712,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=400)
     ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch", "warmstart"])
     ap.add_argument("--batch-scale", type=float, default=1.0)
-    ap.add_argument("--case", default="kn01", choices=["kn01", "kn001"])
+    ap.add_argument("--case", default="kn01", choices=["kn01", "kn001", "tri"])
     ap.add_argument("--order", type=int, default=1, choices=[1, 2],
                     help="reconstruction order of the wave fluxes (2: second order, FP64 wave fluxes)")
     ap.add_argument("--max-wave-steps", type=int, default=400000)

@@ -69,6 +69,23 @@ typedef struct {
     const int32_t* bc_jmax;
 } ugkwp_mesh;
 
+/* Unstructured mesh of triangles and convex quadrilaterals (the paper's meshes are unstructured, Sec. V).
+ * cells: 4 vertex indices per cell, counter-clockwise, -1 in the fourth for a triangle. Local face k of a
+ * cell is its edge from vertex k to vertex k + 1 (mod 3 or 4). Faces are numbered in order of first
+ * appearance, walking the cells in order and each cell's edges in order; the first cell naming an edge is
+ * the face's L side and the face keeps that cell's direction a -> b, so that its unit normal
+ * (e_y, -e_x) / |e| points from L to R. boundary: 3 int32 per edge of a single cell (vertex, vertex in
+ * either order, tag: wall, far field, fixed or symmetry), each such edge exactly once. Wall faces are
+ * numbered in face order. Host arrays, read during ugkwp_create_unstructured only. */
+typedef struct {
+    int32_t n_vertices, n_cells;
+    const double* xv;
+    const double* yv;
+    const int32_t* cells;
+    int32_t n_boundary;
+    const int32_t* boundary;
+} ugkwp_umesh;
+
 /* VHS exponent (mu ~ T^omega) and Prandtl number (Prandtl fix of the wave slopes; 1 = BGK) */
 typedef struct {
     double omega, Pr;
@@ -92,9 +109,9 @@ typedef struct {
     double ghost_state[4];    /* (rho, U, V, T) of UGKWP_BC_FIXED ghosts */
     void* stream;             /* cudaStream_t to run on (NULL: the legacy default stream) */
     int32_t use_graph;        /* 1: capture one step into a CUDA graph on the first ugkwp_step, replay it */
-    int32_t order;            /* 2: second-order reconstruction of W and W^h for the wave fluxes (Eq. 12; 1-D van
-                                 Leer, 2-D least squares with Barth-Jespersen limiting; 128 B per cell);
-                                 0 or 1: first order (the default) */
+    int32_t order;            /* 2: second-order reconstruction of W and W^h for the wave fluxes (Eq. 12; 1-D a
+                                 smooth van Albada-type limited slope, 2-D least squares with Venkatakrishnan's
+                                 limiter; 128 B per cell); 0 or 1: first order (the default) */
 } ugkwp_opts;
 
 /* Build the context: geometry, fixed local time steps (Eqs. 33-34), uniform freestream state, no
@@ -102,6 +119,14 @@ typedef struct {
  * Mach number along +x; Tw the wall temperature over T_inf; cfl the CFL number N_CFL of Eq. 33. */
 ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double Kn, double Ma, double Tw,
                           double cfl, ugkwp_tstep mode, const ugkwp_opts* opts, ugkwp_ctx** out);
+/* As ugkwp_create on an unstructured mesh (at most 2^20 cells). UGKWP_EINVAL, with no context made, for a
+ * vertex index out of range, a vertex repeated in a cell, a clockwise or non-convex cell, an edge of three
+ * cells or of two cells running the same way along it, an untagged or twice-tagged boundary edge, a tag on
+ * an interior edge, or a tag other than wall, far field, fixed and symmetry. Every other entry point works
+ * on the context as on a structured one (cells in the given order, faces numbered as above). */
+ugkwp_status ugkwp_create_unstructured(const ugkwp_umesh* mesh, const ugkwp_gas* gas, double Kn, double Ma,
+                                       double Tw, double cfl, ugkwp_tstep mode, const ugkwp_opts* opts,
+                                       ugkwp_ctx** out);
 void ugkwp_destroy(ugkwp_ctx* ctx);
 
 /* Advance n_steps steps (asynchronous). */

@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <vector>
 #include "ugkwp_internal.h"
 #include "ugkwp_detmath.cuh"
@@ -255,6 +256,60 @@ __global__ void k_setup_face_dist(const MeshDev m, Dev d, const double* fd)
     }
     d.fdL[f] = fd[f] - (d.fnx[f] * d.xc[L] + d.fny[f] * d.yc[L]);
     d.fdR[f] = R >= 0 ? (d.fnx[f] * d.xc[R] + d.fny[f] * d.yc[R]) - fd[f] : d.fdL[f];
+}
+
+// ------------------------------------------------------------------ unstructured meshes (triangles, quads)
+// Face and cell connectivity come from the host (ugkwp_create_unstructured); the geometry is computed here.
+// A triangle is the degenerate quadrilateral (v0, v1, v2, v2): the quadrilateral's area, centroid and
+// position-sampling formulas then give the triangle's.
+struct UMeshDev {
+    int C, F;
+    const double *xv, *yv;
+    const int* cv;                      // [4C] vertices, the third repeated in the fourth slot of a triangle
+    const int *fa, *fb, *fl, *fr, *ftag;   // [F] edge a -> b (L's direction), sides, boundary tag
+};
+
+__global__ void k_setup_faces_u(const UMeshDev m, Dev d, double* fd)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= m.F) return;
+    const int a = m.fa[f], b = m.fb[f];
+    const double ex = m.xv[b] - m.xv[a], ey = m.yv[b] - m.yv[a];
+    const double len = sqrt(ex * ex + ey * ey);
+    d.fax[f] = m.xv[a]; d.fay[f] = m.yv[a]; d.fex[f] = ex; d.fey[f] = ey;
+    d.fs[f] = len;
+    const double nx = ey / len, ny = -ex / len;
+    d.fnx[f] = nx; d.fny[f] = ny;
+    d.fL[f] = m.fl[f]; d.fR[f] = m.fr[f]; d.fbc[f] = m.fr[f] < 0 ? m.ftag[f] : 0;
+    fd[f] = nx * m.xv[a] + ny * m.yv[a];
+}
+
+// cell geometry and the outward normals / planes of its local faces (the integer tables are already set)
+__global__ void k_setup_cells_u(const UMeshDev m, Dev d, const double* fd, const int* cface, const int* csgn,
+                                double* cnx, double* cny, double* cd)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.C) return;
+    double X[4], Y[4];
+    for (int q = 0; q < 4; ++q) {
+        X[q] = m.xv[m.cv[4 * c + q]]; Y[q] = m.yv[m.cv[4 * c + q]];
+        d.cvx[4 * c + q] = X[q]; d.cvy[4 * c + q] = Y[q];
+        d.cshift[4 * c + q] = 0.0;
+    }
+    d.vol[c] = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[1]) - (X[3] - X[1]) * (Y[2] - Y[0]));
+    const double A1 = 0.5 * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+    const double A2 = 0.5 * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+    d.xc[c] = (A1 * (X[0] + X[1] + X[2]) + A2 * (X[0] + X[2] + X[3])) / (3.0 * (A1 + A2));
+    d.yc[c] = (A1 * (Y[0] + Y[1] + Y[2]) + A2 * (Y[0] + Y[2] + Y[3])) / (3.0 * (A1 + A2));
+    for (int k = 0; k < 4; ++k) {
+        const int q = 4 * c + k;
+        if (k >= d.nfc[c]) { cnx[q] = 0.0; cny[q] = 0.0; cd[q] = 0.0; continue; }
+        const int f = cface[q];
+        const bool isL = csgn[q] > 0;
+        cnx[q] = isL ? d.fnx[f] : -d.fnx[f];
+        cny[q] = isL ? d.fny[f] : -d.fny[f];
+        cd[q] = isL ? fd[f] : -fd[f];
+    }
 }
 
 // Eq. 33 on the freestream field: dt_i = N_CFL Omega_i / ((|U_inf| + 3 sqrt(R T_inf)) sum_j s_j)
@@ -1629,6 +1684,92 @@ int ceil_log2(double x)
     const double m = frexp(x, &e);
     return m == 0.5 ? e - 1 : e;
 }
+
+// Connectivity of an unstructured mesh: faces in order of first appearance over the cells and their edges
+// (edge k of a cell runs from its vertex k to vertex k + 1), the first cell naming an edge being its L side;
+// per cell the local face tables. Validates the mesh (ugkwp_create_unstructured lists the rules).
+struct UTopo {
+    int C = 0, F = 0;
+    std::vector<int> cv, nfc, cface, csgn, cnbr, cnk, cbc;     // per cell (cv, tables: 4 per cell)
+    std::vector<int> fa, fb, fl, fr, ftag, fkl, fkr;           // per face
+};
+
+bool valid_tag(int t)
+{
+    return t == UGKWP_BC_WALL || t == UGKWP_BC_FARFIELD || t == UGKWP_BC_FIXED || t == UGKWP_BC_SYMMETRY;
+}
+
+ugkwp_status build_topology(const ugkwp_umesh* m, UTopo& t)
+{
+    const int C = m->n_cells, NV = m->n_vertices;
+    t.C = C;
+    t.cv.assign(4 * (size_t)C, 0); t.nfc.assign(C, 0);
+    t.cface.assign(4 * (size_t)C, 0); t.csgn.assign(4 * (size_t)C, 1); t.cnbr.assign(4 * (size_t)C, -1);
+    t.cnk.assign(4 * (size_t)C, 0); t.cbc.assign(4 * (size_t)C, 0);
+    std::unordered_map<uint64_t, int> edge;
+    edge.reserve(4 * (size_t)C);
+    auto key = [NV](int a, int b) { return a < b ? (uint64_t)a * (uint64_t)NV + (uint64_t)b : (uint64_t)b * (uint64_t)NV + (uint64_t)a; };
+    for (int c = 0; c < C; ++c) {
+        const int32_t* v = m->cells + 4 * (size_t)c;
+        const int n = v[3] == -1 ? 3 : 4;
+        t.nfc[c] = n;
+        for (int q = 0; q < n; ++q) {
+            if (v[q] < 0 || v[q] >= NV) return UGKWP_EINVAL;
+            for (int r = 0; r < q; ++r)
+                if (v[r] == v[q]) return UGKWP_EINVAL;
+        }
+        for (int q = 0; q < 4; ++q) t.cv[4 * (size_t)c + q] = v[q < n ? q : 2];
+        // counter-clockwise and strictly convex: every turn to the left
+        for (int q = 0; q < n; ++q) {
+            const int a = v[q], b = v[(q + 1) % n], e = v[(q + 2) % n];
+            const double ux = m->xv[b] - m->xv[a], uy = m->yv[b] - m->yv[a];
+            const double wx = m->xv[e] - m->xv[b], wy = m->yv[e] - m->yv[b];
+            if (!(ux * wy - uy * wx > 0.0)) return UGKWP_EINVAL;
+        }
+        for (int k = 0; k < n; ++k) {
+            const int a = v[k], b = v[(k + 1) % n];
+            auto it = edge.find(key(a, b));
+            int f;
+            if (it == edge.end()) {
+                f = t.F++;
+                edge.emplace(key(a, b), f);
+                t.fa.push_back(a); t.fb.push_back(b); t.fl.push_back(c); t.fr.push_back(-1);
+                t.ftag.push_back(0); t.fkl.push_back(k); t.fkr.push_back(0);
+            } else {
+                f = it->second;
+                if (t.fr[f] >= 0 || t.fa[f] != b) return UGKWP_EINVAL;   // three cells, or overlapping cells
+                t.fr[f] = c;
+                t.fkr[f] = k;
+            }
+            t.cface[4 * (size_t)c + k] = f;
+        }
+    }
+    for (int e = 0; e < m->n_boundary; ++e) {
+        const int a = m->boundary[3 * (size_t)e], b = m->boundary[3 * (size_t)e + 1], tag = m->boundary[3 * (size_t)e + 2];
+        if (a < 0 || a >= NV || b < 0 || b >= NV || !valid_tag(tag)) return UGKWP_EINVAL;
+        auto it = edge.find(key(a, b));
+        if (it == edge.end()) return UGKWP_EINVAL;
+        const int f = it->second;
+        if (t.fr[f] >= 0 || t.ftag[f] != 0) return UGKWP_EINVAL;
+        t.ftag[f] = tag;
+    }
+    for (int f = 0; f < t.F; ++f)
+        if (t.fr[f] < 0 && t.ftag[f] == 0) return UGKWP_EINVAL;
+    for (int c = 0; c < C; ++c)
+        for (int k = 0; k < t.nfc[c]; ++k) {
+            const size_t q = 4 * (size_t)c + k;
+            const int f = t.cface[q];
+            const bool isL = t.fl[f] == c;
+            t.csgn[q] = isL ? 1 : -1;
+            if (t.fr[f] < 0) { t.cnbr[q] = -1; t.cnk[q] = 0; t.cbc[q] = t.ftag[f]; }
+            else { t.cnbr[q] = isL ? t.fr[f] : t.fl[f]; t.cnk[q] = isL ? t.fkr[f] : t.fkl[f]; t.cbc[q] = 0; }
+        }
+    return UGKWP_OK;
+}
+
+ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_umesh* um, const ugkwp_gas* gas,
+                         double Kn, double Ma, double Tw, double cfl, ugkwp_tstep mode, const ugkwp_opts* opts,
+                         ugkwp_ctx** out);
 }  // namespace
 
 extern "C" {
@@ -1642,6 +1783,33 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     if (!(gas->wall_specular >= 0.0 && gas->wall_specular <= 1.0)) return UGKWP_EINVAL;
     if (mesh->dim == 1 && (mesh->nj != 1 || !mesh->bc_imin || !mesh->bc_imax)) return UGKWP_EINVAL;
     if (mesh->dim == 2 && (!mesh->yv || (mesh->periodic_j && mesh->nj < 2))) return UGKWP_EINVAL;
+    if (mesh->dim == 1 && ((mesh->bc_imin[0] == UGKWP_BC_PERIODIC) != (mesh->bc_imax[0] == UGKWP_BC_PERIODIC)))
+        return UGKWP_EINVAL;
+    return create_impl(mesh, nullptr, nullptr, gas, Kn, Ma, Tw, cfl, mode, opts, out);
+}
+
+ugkwp_status ugkwp_create_unstructured(const ugkwp_umesh* mesh, const ugkwp_gas* gas, double Kn, double Ma,
+                                       double Tw, double cfl, ugkwp_tstep mode, const ugkwp_opts* opts,
+                                       ugkwp_ctx** out)
+{
+    if (!mesh || !gas || !opts || !out || mesh->n_cells <= 0 || mesh->n_vertices <= 0 || !mesh->xv || !mesh->yv ||
+        !mesh->cells || mesh->n_boundary < 0 || (mesh->n_boundary > 0 && !mesh->boundary))
+        return UGKWP_EINVAL;
+    if (mesh->n_cells > kMaxCells || opts->n_ref <= 0 || !(cfl > 0.0)) return UGKWP_EINVAL;
+    if (!(gas->wall_specular >= 0.0 && gas->wall_specular <= 1.0)) return UGKWP_EINVAL;
+    UTopo topo;
+    const ugkwp_status st = build_topology(mesh, topo);
+    if (st != UGKWP_OK) return st;
+    return create_impl(nullptr, &topo, mesh, gas, Kn, Ma, Tw, cfl, mode, opts, out);
+}
+
+}  // extern "C"
+
+namespace {
+ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_umesh* um, const ugkwp_gas* gas,
+                         double Kn, double Ma, double Tw, double cfl, ugkwp_tstep mode, const ugkwp_opts* opts,
+                         ugkwp_ctx** out)
+{
     int dev_count = 0;
     if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return UGKWP_ECUDA;
     ugkwp_ctx* h = new (std::nothrow) ugkwp_ctx;
@@ -1660,17 +1828,16 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         delete h;
         return UGKWP_ECUDA;
     }
-    const int ni = mesh->ni, nj = mesh->nj, C = ni * nj;
-    const int periodic_i = mesh->dim == 1 && mesh->bc_imin[0] == UGKWP_BC_PERIODIC;
-    if (mesh->dim == 1 && ((mesh->bc_imin[0] == UGKWP_BC_PERIODIC) != (mesh->bc_imax[0] == UGKWP_BC_PERIODIC))) {
-        delete h;
-        return UGKWP_EINVAL;
-    }
-    const int F = mesh->dim == 1 ? (periodic_i ? ni : ni + 1) : (ni + 1) * nj + ni * (mesh->periodic_j ? nj : nj + 1);
-    ctx.ni = ni; ctx.nj = nj; ctx.periodic_j = mesh->periodic_j;
+    // an unstructured mesh is kept as ni = C, nj = 1 (the structured indices are used only here)
+    const int ni = topo ? topo->C : mesh->ni, nj = topo ? 1 : mesh->nj, C = ni * nj;
+    const int dim = topo ? 2 : mesh->dim;
+    const int periodic_i = !topo && mesh->dim == 1 && mesh->bc_imin[0] == UGKWP_BC_PERIODIC;
+    const int F = topo ? topo->F
+                       : mesh->dim == 1 ? (periodic_i ? ni : ni + 1) : (ni + 1) * nj + ni * (mesh->periodic_j ? nj : nj + 1);
+    ctx.ni = ni; ctx.nj = nj; ctx.periodic_j = topo ? 0 : mesh->periodic_j;
     ctx.Kn = Kn; ctx.Ma = Ma;
     StepConsts& K = ctx.k;
-    K.C = C; K.F = F; K.dim = mesh->dim; K.n_ref = opts->n_ref; K.wave_only = opts->wave_only;
+    K.C = C; K.F = F; K.dim = dim; K.n_ref = opts->n_ref; K.wave_only = opts->wave_only;
     K.prec = opts->precision ? 1 : 0;
     K.order = opts->order == 2 ? 2 : 1;
     K.omega = gas->omega; K.Pr = gas->Pr; K.Tw = Tw;
@@ -1703,21 +1870,25 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     auto build = [&]() -> ugkwp_status {
         Dev& d = ctx.d;
         // host mesh -> device
-        const int nv = mesh->dim == 1 ? ni + 1 : (ni + 1) * (nj + 1);
+        const int nv = topo ? um->n_vertices : mesh->dim == 1 ? ni + 1 : (ni + 1) * (nj + 1);
         double *xv, *yv;
-        int *bci, *bco, *bcjl, *bcjh;
         CK(dalloc(ctx, &xv, nv)); CK(dalloc(ctx, &yv, nv));
-        CK(dalloc(ctx, &bci, nj)); CK(dalloc(ctx, &bco, nj)); CK(dalloc(ctx, &bcjl, ni)); CK(dalloc(ctx, &bcjh, ni));
-        CK(cudaMemcpyAsync(xv, mesh->xv, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx.stream));
-        if (mesh->dim == 2) CK(cudaMemcpyAsync(yv, mesh->yv, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx.stream));
-        CK(cudaMemcpyAsync(bci, mesh->bc_imin, sizeof(int) * nj, cudaMemcpyHostToDevice, ctx.stream));
-        CK(cudaMemcpyAsync(bco, mesh->bc_imax, sizeof(int) * nj, cudaMemcpyHostToDevice, ctx.stream));
-        if (mesh->dim == 2 && !mesh->periodic_j) {
-            if (!mesh->bc_jmin || !mesh->bc_jmax) return fail(ctx, UGKWP_EINVAL, "missing j boundary tags");
-            CK(cudaMemcpyAsync(bcjl, mesh->bc_jmin, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
-            CK(cudaMemcpyAsync(bcjh, mesh->bc_jmax, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
+        CK(cudaMemcpyAsync(xv, topo ? um->xv : mesh->xv, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx.stream));
+        if (dim == 2)
+            CK(cudaMemcpyAsync(yv, topo ? um->yv : mesh->yv, sizeof(double) * nv, cudaMemcpyHostToDevice, ctx.stream));
+        MeshDev m{ni, nj, dim, ctx.periodic_j, periodic_i, F, xv, yv, nullptr, nullptr, nullptr, nullptr};
+        if (!topo) {
+            int *bci, *bco, *bcjl, *bcjh;
+            CK(dalloc(ctx, &bci, nj)); CK(dalloc(ctx, &bco, nj)); CK(dalloc(ctx, &bcjl, ni)); CK(dalloc(ctx, &bcjh, ni));
+            CK(cudaMemcpyAsync(bci, mesh->bc_imin, sizeof(int) * nj, cudaMemcpyHostToDevice, ctx.stream));
+            CK(cudaMemcpyAsync(bco, mesh->bc_imax, sizeof(int) * nj, cudaMemcpyHostToDevice, ctx.stream));
+            if (mesh->dim == 2 && !mesh->periodic_j) {
+                if (!mesh->bc_jmin || !mesh->bc_jmax) return fail(ctx, UGKWP_EINVAL, "missing j boundary tags");
+                CK(cudaMemcpyAsync(bcjl, mesh->bc_jmin, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
+                CK(cudaMemcpyAsync(bcjh, mesh->bc_jmax, sizeof(int) * ni, cudaMemcpyHostToDevice, ctx.stream));
+            }
+            m.bc_imin = bci; m.bc_imax = bco; m.bc_jmin = bcjl; m.bc_jmax = bcjh;
         }
-        MeshDev m{ni, nj, mesh->dim, mesh->periodic_j, periodic_i, F, xv, yv, bci, bco, bcjl, bcjh};
         CK(dalloc(ctx, &d.vol, C)); CK(dalloc(ctx, &d.rcp, 2 * C)); CK(dalloc(ctx, &d.wallcell, C)); CK(dalloc(ctx, &d.xc, C)); CK(dalloc(ctx, &d.yc, C)); CK(dalloc(ctx, &d.dt, C));
         CK(dalloc(ctx, &d.nfc, C)); CK(dalloc(ctx, &d.cf32, C)); CK(dalloc(ctx, &d.cf64, C));
         CK(dalloc(ctx, &d.cshift, 4 * C)); CK(dalloc(ctx, &d.cvx, 4 * C)); CK(dalloc(ctx, &d.cvy, 4 * C));
@@ -1733,8 +1904,24 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
         const int nbdt = nblk(C, 256);
         CK(dalloc(ctx, &dtpart, nbdt));
         CK(dalloc(ctx, &d.scan_tmp, kScanBlock));
-        k_setup_faces<<<nblk(F, 128), 128, 0, ctx.stream>>>(m, d, fd);
-        k_setup_cells<<<nblk(C, 128), 128, 0, ctx.stream>>>(m, d, fd, cface, csgn, cnbr, cnk, cbc, cnx, cny, cd);
+        if (topo) {
+            int *cv, *fa, *fb, *fl, *fr, *ftag;
+            CK(dalloc(ctx, &cv, 4 * C)); CK(dalloc(ctx, &fa, F)); CK(dalloc(ctx, &fb, F)); CK(dalloc(ctx, &fl, F));
+            CK(dalloc(ctx, &fr, F)); CK(dalloc(ctx, &ftag, F));
+            auto up = [&](int* dst, const std::vector<int>& src) {
+                return cudaMemcpyAsync(dst, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, ctx.stream);
+            };
+            CK(up(cv, topo->cv)); CK(up(fa, topo->fa)); CK(up(fb, topo->fb)); CK(up(fl, topo->fl));
+            CK(up(fr, topo->fr)); CK(up(ftag, topo->ftag));
+            CK(up(d.nfc, topo->nfc)); CK(up(cface, topo->cface)); CK(up(csgn, topo->csgn)); CK(up(cnbr, topo->cnbr));
+            CK(up(cnk, topo->cnk)); CK(up(cbc, topo->cbc));
+            const UMeshDev um_d{C, F, xv, yv, cv, fa, fb, fl, fr, ftag};
+            k_setup_faces_u<<<nblk(F, 128), 128, 0, ctx.stream>>>(um_d, d, fd);
+            k_setup_cells_u<<<nblk(C, 128), 128, 0, ctx.stream>>>(um_d, d, fd, cface, csgn, cnx, cny, cd);
+        } else {
+            k_setup_faces<<<nblk(F, 128), 128, 0, ctx.stream>>>(m, d, fd);
+            k_setup_cells<<<nblk(C, 128), 128, 0, ctx.stream>>>(m, d, fd, cface, csgn, cnbr, cnk, cbc, cnx, cny, cd);
+        }
         k_setup_face_dist<<<nblk(F, 128), 128, 0, ctx.stream>>>(m, d, fd);
         const double cs = K.U_inf + 3.0 * sqrt(0.5 * 1.0);
         k_setup_dt<<<nbdt, 256, 0, ctx.stream>>>(d, C, cface, cfl, cs, dtpart);
@@ -1898,6 +2085,9 @@ ugkwp_status ugkwp_create(const ugkwp_mesh* mesh, const ugkwp_gas* gas, double K
     *out = h;
     return UGKWP_OK;
 }
+}  // namespace
+
+extern "C" {
 
 void ugkwp_destroy(ugkwp_ctx* h)
 {

@@ -22,10 +22,24 @@ from . import workloads as wl
 
 def wall_geometry(case):
     """Outward normals (nx, ny) of the fluid cells and lengths s of the wall faces, in the library's
-    wall-face order: i-faces (vertex rows i = const) before j-faces, each in increasing face index."""
+    wall-face order: on a structured mesh i-faces (vertex rows i = const) before j-faces, each in increasing
+    face index; on an unstructured one in order of the cells and their edges."""
     m = case.mesh
     if m.dim != 2:
         return np.zeros(0), np.zeros(0), np.zeros(0)
+    if hasattr(m, "cells"):
+        # unstructured: a boundary edge belongs to one cell, so face order puts it at (cell, local edge)
+        walls = {tuple(sorted((int(a), int(b)))) for a, b, t in m.boundary if t == wl.BC_WALL}
+        out = []
+        for q in m.cells:
+            vs = [int(v) for v in q if v >= 0]
+            for a, b in zip(vs, vs[1:] + vs[:1]):
+                if tuple(sorted((a, b))) in walls:
+                    dx, dy = m.xv[b] - m.xv[a], m.yv[b] - m.yv[a]
+                    s = math.hypot(dx, dy)
+                    out.append((dy / s, -dx / s, s))
+        a = np.array(out).reshape(-1, 3)
+        return a[:, 0], a[:, 1], a[:, 2]
     ni, nj = m.ni, m.nj
     xv, yv = m.xv.reshape(nj + 1, ni + 1), m.yv.reshape(nj + 1, ni + 1)
     out = []

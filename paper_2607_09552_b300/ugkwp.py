@@ -18,7 +18,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ELIMIT", 5: "ENONPH
 LTS, GTS = 0, 1
 
 # every entry point declared in include/ugkwp.h
-EXPORTS = ["ugkwp_create", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugkwp_surface", "ugkwp_reset_surface",
+EXPORTS = ["ugkwp_create", "ugkwp_create_unstructured", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugkwp_surface", "ugkwp_reset_surface",
            "ugkwp_set_field", "ugkwp_set_time_steps", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
            "ugkwp_set_state", "ugkwp_get_tallies", "ugkwp_get_cell_data", "ugkwp_get_flux", "ugkwp_get_geometry",
            "ugkwp_fixed_exponents", "ugkwp_save", "ugkwp_load", "ugkwp_batch_create", "ugkwp_batch_step",
@@ -35,6 +35,12 @@ class UgkwpMesh(C.Structure):
                 ("xv", C.POINTER(C.c_double)), ("yv", C.POINTER(C.c_double)),
                 ("bc_imin", C.POINTER(C.c_int32)), ("bc_imax", C.POINTER(C.c_int32)),
                 ("bc_jmin", C.POINTER(C.c_int32)), ("bc_jmax", C.POINTER(C.c_int32))]
+
+
+class UgkwpUMesh(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_cells", C.c_int32), ("xv", C.POINTER(C.c_double)),
+                ("yv", C.POINTER(C.c_double)), ("cells", C.POINTER(C.c_int32)), ("n_boundary", C.c_int32),
+                ("boundary", C.POINTER(C.c_int32))]
 
 
 class UgkwpGas(C.Structure):
@@ -109,15 +115,23 @@ class Solver:
         L = load()
         m = case.mesh
         self._keep = [np.ascontiguousarray(m.xv, dtype=np.float64), np.ascontiguousarray(m.yv, dtype=np.float64)]
-        self._keep += [np.ascontiguousarray(a, dtype=np.int32) for a in (m.bc_imin, m.bc_imax, m.bc_jmin, m.bc_jmax)]
-        mesh = UgkwpMesh(m.ni, m.nj, m.dim, m.periodic_j, _d(self._keep[0]), _d(self._keep[1]),
-                         *[_p(a, C.c_int32) for a in self._keep[2:]])
+        unstructured = hasattr(m, "cells")
+        if unstructured:
+            self._keep += [np.ascontiguousarray(a, dtype=np.int32) for a in (m.cells, m.boundary)]
+            mesh = UgkwpUMesh(len(m.xv), m.ncells, _d(self._keep[0]), _d(self._keep[1]),
+                              _p(self._keep[2], C.c_int32), len(m.boundary), _p(self._keep[3], C.c_int32))
+        else:
+            self._keep += [np.ascontiguousarray(a, dtype=np.int32)
+                           for a in (m.bc_imin, m.bc_imax, m.bc_jmin, m.bc_jmax)]
+            mesh = UgkwpMesh(m.ni, m.nj, m.dim, m.periodic_j, _d(self._keep[0]), _d(self._keep[1]),
+                             *[_p(a, C.c_int32) for a in self._keep[2:]])
         gas = UgkwpGas(case.omega, case.Pr, getattr(case, "wall_specular", 0.0))
         opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
                          int(record_faces), capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream),
                          int(use_graph), int(order))
         self.ctx = C.c_void_p()
-        st = L.ugkwp_create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
+        create = L.ugkwp_create_unstructured if unstructured else L.ugkwp_create
+        st = create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
                             C.c_double(case.Tw), C.c_double(case.cfl), C.c_int32(GTS if gts else LTS), C.byref(opts),
                             C.byref(self.ctx))
         if st != 0:
@@ -126,7 +140,7 @@ class Solver:
                 L.ugkwp_destroy(self.ctx)
                 self.ctx = None
             raise UgkwpError(st, f"ugkwp_create: {msg}")
-        self.C = m.ni * m.nj
+        self.C = m.ncells
         nf, nw = C.c_int32(), C.c_int32()
         self._check(L.ugkwp_get_geometry(self.ctx, None, None, C.byref(nf), C.byref(nw)))
         self.F, self.nwall = nf.value, nw.value
