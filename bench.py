@@ -97,7 +97,7 @@ class Clocks:
 
 def bench_case(args=None):
     """The throughput workload: the Kn 0.1 cylinder (the default), with --case kn001 the dense-regime one, with
-    --case tri the Kn 0.1 cylinder on the hybrid unstructured mesh of the paper's cell count."""
+    --case tri the cylinder at Kn 0.1 on the radius on the hybrid unstructured mesh of the paper's cell count."""
     which = getattr(args, "case", "kn01") if args is not None else "kn01"
     if which == "kn001":
         return wl.case_cylinder_kn001()
@@ -109,9 +109,9 @@ def bench_case(args=None):
 WORKLOADS = {
     "cylinder_120x160_Kn0.1_Ma5.0": "cylinder O-mesh 120x160, Kn=0.1 (lambda/D), Ma=5, Tw/Tinf=1, N_ref=100, CFL 0.8, LTS",
     "cylinder_240x320_Kn0.01_Ma15.0": "cylinder O-mesh 240x320, Kn=0.01 (lambda/D), Ma=15, Tw/Tinf=1, N_ref=150, CFL 0.8, LTS",
-    "cylinder_tri_7420_Kn0.1_Ma5.0": "cylinder hybrid unstructured mesh, 7420 cells (1820 quadrilaterals in 13 wall "
-                                     "layers, 5600 triangles), wall cell 0.01 R, Kn=0.1 (lambda/D), Ma=5, Tw/Tinf=1, "
-                                     "N_ref=100, CFL 0.8, LTS",
+    "cylinder_tri_7420_Kn0.05_Ma5.0": "cylinder hybrid unstructured mesh, 7420 cells (1820 quadrilaterals in 13 wall "
+                                      "layers, 5600 triangles), wall cell 0.01 R, Kn=0.05 (lambda/D; 0.1 on R), Ma=5, "
+                                      "Tw/Tinf=1, N_ref=100, CFL 0.8, LTS",
 }
 
 

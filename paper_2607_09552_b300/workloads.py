@@ -290,9 +290,10 @@ def case_cylinder_kn001() -> Case:
 
 
 def case_cylinder_tri(n_quad: int = 13, ni: int = 33, nj: int = 140, h1: float = 0.005, r_out: float = 15.0,
-                      Kn: float = 0.1, Ma: float = 5.0, Tw: float = 1.0, n_ref: int = 100, cfl: float = 0.8) -> Case:
-    """Hypersonic cylinder on a hybrid unstructured mesh of the size of the paper's Kn = 0.1 case (Sec. V A:
-    7,420 cells, first wall cell 0.01 R): 13 quadrilateral layers at the wall and 20 triangulated layers."""
+                      Kn: float = 0.05, Ma: float = 5.0, Tw: float = 1.0, n_ref: int = 100, cfl: float = 0.8) -> Case:
+    """Hypersonic cylinder on a hybrid unstructured mesh standing in for the paper's Kn = 0.1 case (Sec. V A:
+    Kn on the radius, 7,420 cells, first wall cell 0.01 R; here Kn is on the diameter, so 0.05):
+    13 quadrilateral layers at the wall and 20 triangulated layers."""
     m = tri_omesh(n_quad, ni, nj, h1, r_out)
     return Case(f"cylinder_tri_{m.ncells}_Kn{Kn}_Ma{Ma}", m, Kn=Kn, Ma=Ma, Tw=Tw, cfl=cfl, n_ref=n_ref)
 

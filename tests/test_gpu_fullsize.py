@@ -17,7 +17,7 @@ FULL = {
     "shock1d_200": lambda: wl.case_shock1d(),
     "cylinder_120x160_kn0.1_ma5": wl.case_cylinder_kn01,
     "cylinder_240x320_kn0.01_ma15": wl.case_cylinder_kn001,
-    "cylinder_tri_7420_kn0.1_ma5": wl.case_cylinder_tri,
+    "cylinder_tri_7420_kn0.05_ma5": wl.case_cylinder_tri,
 }
 
 
