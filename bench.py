@@ -97,12 +97,17 @@ class Clocks:
 
 def bench_case(args=None):
     """The throughput workload: the Kn 0.1 cylinder (the default), with --case kn001 the dense-regime one, with
-    --case tri the cylinder at Kn 0.1 on the radius on the hybrid unstructured mesh of the paper's cell count."""
+    --case tri the cylinder at Kn 0.1 on the radius on the hybrid unstructured mesh of the paper's cell count,
+    with --case tri_kn001 / tri_plate the stand-ins of the paper's other two unstructured meshes."""
     which = getattr(args, "case", "kn01") if args is not None else "kn01"
     if which == "kn001":
         return wl.case_cylinder_kn001()
     if which == "tri":
         return wl.case_cylinder_tri()
+    if which == "tri_kn001":
+        return wl.case_cylinder_tri_kn001()
+    if which == "tri_plate":
+        return wl.case_plate_tri()
     return wl.case_cylinder_kn01()
 
 
@@ -112,6 +117,12 @@ WORKLOADS = {
     "cylinder_tri_7420_Kn0.05_Ma5.0": "cylinder hybrid unstructured mesh, 7420 cells (1820 quadrilaterals in 13 wall "
                                       "layers, 5600 triangles), wall cell 0.01 R, Kn=0.05 (lambda/D; 0.1 on R), Ma=5, "
                                       "Tw/Tinf=1, N_ref=100, CFL 0.8, LTS",
+    "cylinder_tri_16100_Kn0.005_Ma5.0": "cylinder hybrid unstructured mesh, 16100 cells (2100 quadrilaterals in 15 wall "
+                                        "layers, 14000 triangles), wall cell 0.0005 R, Kn=0.005 (lambda/D; 0.01 on R), "
+                                        "Ma=5, Tw/Tinf=1, N_ref=100, CFL 0.8, LTS",
+    "plate_tri_5885_Kn0.0169_Ma20.2": "flat plate hybrid unstructured mesh, 5885 cells (1605 quadrilaterals in 15 wall "
+                                      "rows, 4280 triangles), first cell 1e-5 L, Kn=0.0169 (lambda/L), Ma=20.2, "
+                                      "Tw/Tinf=290/13.32, Maxwell wall alpha=0.85, monatomic, N_ref=200, CFL 0.8, LTS",
 }
 
 
@@ -136,7 +147,7 @@ def run_ours(args):
     case = bench_case(args)
     # the product's recommended mode: one captured graph per step, launch shape chosen by the autotuner
     # the dense-regime cylinder overshoots its steady particle count about 3x in the start-up transient
-    cap = 8 * case.n_ref * case.mesh.ncells if args.case == "kn001" else 0
+    cap = 8 * case.n_ref * case.mesh.ncells if args.case in ("kn001", "tri_kn001") else 0
     solver = ugkwp.Solver(case, precision=0, seed=rank, stream=stream.cuda_stream, use_graph=True, order=args.order,
                           capacity=cap)
     solver.step(args.burn)
@@ -712,7 +723,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=400)
     ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch", "warmstart"])
     ap.add_argument("--batch-scale", type=float, default=1.0)
-    ap.add_argument("--case", default="kn01", choices=["kn01", "kn001", "tri"])
+    ap.add_argument("--case", default="kn01", choices=["kn01", "kn001", "tri", "tri_kn001", "tri_plate"])
     ap.add_argument("--order", type=int, default=1, choices=[1, 2],
                     help="reconstruction order of the wave fluxes (2: second order, FP64 wave fluxes)")
     ap.add_argument("--max-wave-steps", type=int, default=400000)

@@ -150,6 +150,17 @@ def plate_mesh(ni: int = 240, nj: int = 120, h1: float = 1e-4, ratio: float = 1.
                 bc_jmin, np.full(ni, BC_FARFIELD, np.int32), info={"L": L, "ratio": ratio})
 
 
+def tri_plate(ni: int = 107, n_quad: int = 15, nj: int = 35, h1: float = 1e-5, height: float = 1.0, L: float = 1.0,
+              x_lead: float = -0.1, x_trail: float = 1.1) -> UMesh:
+    """Hybrid flat-plate mesh: the Cartesian plate mesh (wall for 0 <= x <= L on y = 0, mirror elsewhere) with
+    rows stretched from h1 to `height`, its first n_quad rows kept as quadrilaterals and the rest cut into
+    triangles; n_quad ni + 2 (nj - n_quad) ni cells."""
+    m = plate_mesh(ni, nj, h1, solve_ratio(nj, h1 * L, height * L), L, x_lead, x_trail)
+    u = split_quads(m, n_quad, "j")
+    u.info.update({"L": L, "h1": h1, "ni": ni, "nj": nj, "n_quad": n_quad})
+    return u
+
+
 def _vid(m: Mesh, i: int, j: int) -> int:
     return i + (m.ni + 1) * (0 if (m.periodic_j and j == m.nj) else j)
 
@@ -296,6 +307,21 @@ def case_cylinder_tri(n_quad: int = 13, ni: int = 33, nj: int = 140, h1: float =
     13 quadrilateral layers at the wall and 20 triangulated layers."""
     m = tri_omesh(n_quad, ni, nj, h1, r_out)
     return Case(f"cylinder_tri_{m.ncells}_Kn{Kn}_Ma{Ma}", m, Kn=Kn, Ma=Ma, Tw=Tw, cfl=cfl, n_ref=n_ref)
+
+
+def case_cylinder_tri_kn001() -> Case:
+    """The paper's dense-regime cylinder (Sec. V A: Ma 5, Kn 0.01 on the radius, 16,100 cells, first wall cell
+    0.0005 R, N_ref 100) on a hybrid stand-in: 15 quadrilateral layers and 50 triangulated ones, 140 around."""
+    return case_cylinder_tri(15, 65, 140, 0.00025, 15.0, Kn=0.005, Ma=5.0, n_ref=100)
+
+
+def case_plate_tri() -> Case:
+    """The paper's hypersonic plate (Sec. V B: Ma 20.2, Kn 0.0169 on L, T_w / T_inf = 290 / 13.32, Maxwell wall
+    with accommodation 0.85, 5,885 cells, first cell 1e-5 L, N_ref 200) on a hybrid stand-in of 107 columns,
+    15 quadrilateral rows and 20 triangulated ones; a monatomic gas (omega 0.81) stands in for nitrogen."""
+    m = tri_plate()
+    return Case(f"plate_tri_{m.ncells}_Kn0.0169_Ma20.2", m, Kn=0.0169, Ma=20.2, Tw=290.0 / 13.32, cfl=0.8,
+                n_ref=200, wall_specular=0.15)
 
 
 def case_periodic_box(ni: int = 16, end_ratio: float = 50.0, n_ref: int = 50, Kn: float = 0.05,

@@ -18,6 +18,8 @@ FULL = {
     "cylinder_120x160_kn0.1_ma5": wl.case_cylinder_kn01,
     "cylinder_240x320_kn0.01_ma15": wl.case_cylinder_kn001,
     "cylinder_tri_7420_kn0.05_ma5": wl.case_cylinder_tri,
+    "cylinder_tri_16100_kn0.005_ma5": wl.case_cylinder_tri_kn001,
+    "plate_tri_5885_kn0.0169_ma20.2": wl.case_plate_tri,
 }
 
 
