@@ -61,3 +61,20 @@ def test_invalid_specular_fraction_rejected():
     for bad in (-0.1, 1.5, float("nan")):
         with pytest.raises(ob.OracleError):
             ob.Oracle(_closed_box(bad), precision=1)
+
+
+@pytest.mark.parametrize("ws", [0.0, 0.5, 1.0])
+@pytest.mark.parametrize("geometry", ["stretched_line", "jittered_triangles"])
+def test_gas_at_rest_at_wall_temperature_stays_in_equilibrium(geometry, ws):
+    """A closed box of gas at rest at T = T_w: the wall wave flux (any accommodation) carries no mass, no
+    tangential momentum and no energy, and its normal momentum is the gas pressure, so the particle-free step
+    (Eq. 53 with the wall fluxes only) leaves every cell unchanged."""
+    if geometry == "stretched_line":
+        m = wl.line_mesh(20, 0.0, 1.0, end_ratio=3.0, bc_left=wl.BC_WALL, bc_right=wl.BC_WALL)
+    else:
+        m = wl.jitter_interior(wl.split_quads(wl.box_mesh(6, 5, tags=(wl.BC_WALL,) * 4), 0, "i"), 1, 0.2)
+    case = wl.Case("rest", m, Kn=0.05, Ma=0.0, Tw=1.0, cfl=0.5, n_ref=30, wall_specular=ws)
+    o = ob.Oracle(case, precision=1, wave_only=True)
+    W0 = o.field()[0].copy()
+    o.step(20)
+    assert np.abs(o.field()[0] - W0).max() < 1e-14
