@@ -19,7 +19,15 @@
  *    whose density zeroes the wave mass flux, or with accommodation alpha < 1 the fraction 1 - alpha
  *    mirrored; far-field / fixed ghosts are virtual cells of the ghost state whose collisionless part
  *    enters as particles (ghost particle sources), so their wave keeps dbar_d - e^{-x};
- *  - the particle w-momentum (and in 1-D the v-momentum) is not part of W.
+ *  - the particle w-momentum (and in 1-D the v-momentum) is not part of W;
+ *  - unstructured meshes (the paper's, Sec. V): convex cells, faces numbered by first appearance over the
+ *    cells and their edges with the first cell as L, a triangle stored as the quadrilateral (v0, v1, v2, v2).
+ *
+ * Parity unpinned (no check independent of this file fixes these; the CUDA library is compared with them as
+ * written): the wall wave flux away from equilibrium (wall_flux: only conservation and the rest equilibrium
+ * at T_w are pinned), the ghost states and ghost particle sources beyond a supersonic uniform flow
+ * (inject_params, inject), the vacuum floor (update), the Shakhov weights' heat-flux estimate
+ * (shakhov_weights) and the limiter constant K = 5 (gradients).
  */
 #include "oracle_internal.h"
 #include <stdio.h>

@@ -294,3 +294,23 @@ def test_brute_force_single_particle_transport(u):
     assert p["cell"][j] == ce
     assert p["x"][j] == pytest.approx(float(xe), rel=1e-13, abs=1e-14)
     assert p["m"][j] == pytest.approx(float(me) * 2.0 ** -20, rel=1e-13)
+
+
+@pytest.mark.parametrize("Kn", [1.0, 0.01])
+def test_supersonic_uniform_flow_kept_by_the_ghost_sources(Kn):
+    """A Ma 2 uniform flow between two far-field ends with particles: the ghost particle sources (the
+    collisionless part of the ghost's Maxwellian entering through the face) keep the time-averaged state of
+    every cell, the boundary cells included, at the freestream (within the 2,000-step average's noise and the
+    ghost treatment's bias, a few percent). Without the sources the boundary cells drop to about 0.6."""
+    m = wl.line_mesh(40, 0.0, 1.0, end_ratio=1.0, bc_left=wl.BC_FARFIELD, bc_right=wl.BC_FARFIELD)
+    case = wl.Case("uniform_ff", m, Kn=Kn, Ma=2.0, Tw=1.0, cfl=0.5, n_ref=100)
+    o = ob.Oracle(case, precision=1)
+    o.step(100)
+    acc = np.zeros((40, 4))
+    for _ in range(2000):
+        o.step(1)
+        acc += o.field()[0]
+    A = acc / 2000
+    assert o.stats()[10] > 0                                  # particles entered from the ghosts
+    np.testing.assert_allclose(A[:, 0], 1.0, atol=0.03)
+    np.testing.assert_allclose(A[:, 1] / A[:, 0] / wl.freestream_speed(2.0), 1.0, atol=0.04)
