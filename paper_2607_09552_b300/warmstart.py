@@ -33,7 +33,10 @@ FAMILY_MAPS = {
 
 
 def family(case) -> str:
-    return "plate" if case.mesh.kind == wl.MESH_PLATE else "cylinder"
+    m = case.mesh
+    # an unstructured plate mesh carries the plate length L in its info, a cylinder mesh the radius
+    plate = m.kind == wl.MESH_PLATE or (m.kind == wl.MESH_UNSTRUCTURED and "L" in m.info)
+    return "plate" if plate else "cylinder"
 
 
 def averaged_field(solver, n_steps: int, every: int = 1):
