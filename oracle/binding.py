@@ -51,6 +51,8 @@ def lib():
         _lib.oracle_logd.argtypes = [C.c_double]
         _lib.oracle_expd.restype = C.c_double
         _lib.oracle_expd.argtypes = [C.c_double]
+        _lib.oracle_expf.restype = C.c_float
+        _lib.oracle_expf.argtypes = [C.c_float]
         _lib.oracle_sincos2pif.argtypes = [C.c_float, C.POINTER(C.c_float), C.POINTER(C.c_float)]
         _lib.oracle_sincos2pid.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib.oracle_mu_inf.restype = C.c_double

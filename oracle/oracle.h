@@ -99,6 +99,7 @@ void   oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* 
 float  oracle_logf(float x);
 double oracle_logd(double x);
 double oracle_expd(double x);
+float  oracle_expf(float x);
 void   oracle_sincos2pif(float u, float* s, float* c);
 void   oracle_sincos2pid(double u, double* s, double* c);
 void   oracle_coeffs(double dt, double tau, double* out);           /* [7] */

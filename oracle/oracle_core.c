@@ -76,6 +76,16 @@ static double tau_of(const or_ctx* cx, const double W[4])
     return mu / (rho * RT);
 }
 
+/* the same in float (production precision, cells without a wall face) */
+static float tau_of_f32(const or_ctx* cx, const double W[4])
+{
+    const float rho = (float)W[0], r = 1.0f / rho, U = (float)W[1] * r, V = (float)W[2] * r;
+    const float RT = ((float)W[3] * r - 0.5f * (U * U + V * V)) * (2.0f / 3.0f);
+    const float T = 2.0f * RT;   /* RT / R, R = 1/2 */
+    const float mu = (float)cx->mu_inf * or_expf((float)cx->omega * or_logf(T));
+    return mu / (rho * RT);
+}
+
 /* ---------------------------------------------- time-integration coefficients (Eq. 16, Eqs. 47-48) */
 
 /* out = (dbar_a, dbar_b, dbar_c, dbar_d, dbar_e, dbar_d - e^{-x}, dbar_e + dt/2 e^{-x}),
@@ -921,7 +931,23 @@ static void decompose(or_ctx* cx)
         const int64_t* r = cx->wret_prev + 5 * c;
         double* Wp = cx->Wp + 4 * c;
         double* Wh = cx->Wh + 4 * c;
-        const double tau = tau_of(cx, W);
+        /* production precision: tau, x = dt / tau and e^{-x} in float, except in cells with a wall face
+         * (stretched, where the wave-flux time integrals need FP64) and at order 2 */
+        int wallcell = 0;
+        for (int k = 0; k < cx->nfc[c]; ++k) if (cx->cbc[4 * c + k] == OR_BC_WALL) wallcell = 1;
+        const int f32 = cx->prec == 0 && !wallcell && cx->order != 2;
+        double tau, x, e;
+        if (f32) {
+            const float t32 = tau_of_f32(cx, W);
+            const float x32 = (float)cx->dt[c] / t32;
+            tau = t32;
+            x = x32;
+            e = or_expf(-x32);
+        } else {
+            tau = tau_of(cx, W);
+            x = cx->dt[c] / tau;
+            e = or_expd(-x);
+        }
         /* W^p from the particles retained at the end of the previous step, the factor 1 / Omega_i of Eq. 30
          * applied to the tally sums; W^h = W - W^p (Eq. 24) */
         Wp[0] = ((double)r[0] * s0) * cx->inv_vol[c];
@@ -929,8 +955,6 @@ static void decompose(or_ctx* cx)
         Wp[2] = cx->dim == 1 ? 0.0 : ((double)r[2] * s1) * cx->inv_vol[c];
         Wp[3] = ((double)r[4] * s4) * cx->inv_vol[c];
         for (int k = 0; k < 4; ++k) Wh[k] = W[k] - Wp[k];
-        const double x = cx->dt[c] / tau;
-        const double e = or_expd(-x);
         cx->tau[c] = tau;
         cx->xr_t[c] = x;
         cx->emx[c] = e;

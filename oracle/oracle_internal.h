@@ -104,6 +104,7 @@ void   or_uniforms_d(const or_ctx* cx, uint64_t pid, uint32_t base, int n, doubl
 float  or_logf(float x);
 double or_logd(double x);
 double or_expd(double x);
+float  or_expf(float x);
 double or_powd(double x, double y);
 void   or_sincos2pif(float u, float* s, float* c);
 void   or_sincos2pid(double u, double* s, double* c);

@@ -10,7 +10,8 @@
  *        (exact products e * hi) and a low part. [Cody & Waite, "Software Manual for the Elementary
  *        Functions", 1980, ch. 5.]
  *  exp : x = k ln2 + r, |r| <= ln2/2 with the same split, Taylor series of e^r (Horner), scaled by 2^k
- *        built from the exponent bits. Results below 2^-1021 are flushed to 0.
+ *        built from the exponent bits. Double: results below 2^-1021 are flushed to 0; float (Taylor to
+ *        r^7): arguments below -87 give 0.
  *  sincos(2 pi u): reduction in turns, u = q/4 + r exactly, |r| <= 1/8, Taylor series of sin and cos of
  *        2 pi r, quadrant by q mod 4.
  * Coefficients are reciprocal factorials and reciprocal odd integers, written as exact divisions.
@@ -24,6 +25,7 @@
 #define OR_LN2_HI_D 0x1.62e42feep-1
 #define OR_LN2_LO_D 0x1.a39ef35793c76p-33
 #define OR_INV_LN2_D 0x1.71547652b82fep+0
+#define OR_INV_LN2_F 0x1.715476p+0f
 #define OR_TWO_PI_F 0x1.921fb6p+2f
 #define OR_TWO_PI_D 0x1.921fb54442d18p+2
 
@@ -104,6 +106,27 @@ double or_expd(double x)
     return p * sc;
 }
 
+float or_expf(float x)
+{
+    if (x < -87.0f) return 0.0f;
+    if (x > 88.0f) return 1.0f / 0.0f;
+    const float kf = rintf(x * OR_INV_LN2_F);
+    const int k = (int)kf;
+    const float r = (x - kf * OR_LN2_HI_F) - kf * OR_LN2_LO_F;
+    float p = 1.0f / 5040.0f;                      /* 1/7! */
+    p = 1.0f / 720.0f + r * p;
+    p = 1.0f / 120.0f + r * p;
+    p = 1.0f / 24.0f + r * p;
+    p = 1.0f / 6.0f + r * p;
+    p = 0.5f + r * p;
+    p = 1.0f + r * p;
+    p = 1.0f + r * p;
+    const uint32_t sb = (uint32_t)(k + 127) << 23;
+    float sc;
+    memcpy(&sc, &sb, 4);
+    return p * sc;
+}
+
 double or_powd(double x, double y)
 {
     return or_expd(y * or_logd(x));
@@ -167,5 +190,6 @@ void or_sincos2pid(double u, double* s, double* c)
 float oracle_logf(float x) { return or_logf(x); }
 double oracle_logd(double x) { return or_logd(x); }
 double oracle_expd(double x) { return or_expd(x); }
+float oracle_expf(float x) { return or_expf(x); }
 void oracle_sincos2pif(float u, float* s, float* c) { or_sincos2pif(u, s, c); }
 void oracle_sincos2pid(double u, double* s, double* c) { or_sincos2pid(u, s, c); }

@@ -402,6 +402,41 @@ __device__ __forceinline__ bool realizable(const StepConsts& K, const double* W)
 }
 
 // ------------------------------------------------------------------ a1: decomposition (Sec. IV B)
+// e^x in float for the production decomposition (its own name: an overload here would hide the double
+// dexp of the deterministic-math header from the calls in this namespace): x = k ln2 + r with ln 2 split in two (k ln2_hi exact),
+// |r| <= ln2 / 2, Taylor series of e^r to r^7 (Horner), scaled by 2^k from the exponent bits; 0 below -87
+// (Cody & Waite, "Software Manual for the Elementary Functions", 1980)
+__device__ __forceinline__ float dexp_f32(float x)
+{
+    if (x < -87.0f) return 0.0f;
+    if (x > 88.0f) return __int_as_float(0x7f800000);
+    const float kf = rintf(__fmul_rn(x, 0x1.715476p+0f));
+    const int k = (int)kf;
+    const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(kf, 0x1.62e4p-1f)), __fmul_rn(kf, 0x1.7f7d1cp-20f));
+    float p = 0x1.a01a02p-13f;                        // 1/7!
+    p = __fadd_rn(0x1.6c16c2p-10f, __fmul_rn(r, p));  // 1/6!
+    p = __fadd_rn(0x1.111112p-7f, __fmul_rn(r, p));   // 1/5!
+    p = __fadd_rn(0x1.555556p-5f, __fmul_rn(r, p));   // 1/4!
+    p = __fadd_rn(0x1.555556p-3f, __fmul_rn(r, p));   // 1/3!
+    p = __fadd_rn(0.5f, __fmul_rn(r, p));
+    p = __fadd_rn(1.0f, __fmul_rn(r, p));
+    p = __fadd_rn(1.0f, __fmul_rn(r, p));
+    return __fmul_rn(p, __int_as_float((k + 127) << 23));
+}
+
+// tau (below) in float (production precision, cells without a wall face); T = RT / R = 2 RT
+__device__ __forceinline__ float tau_of_f32(const StepConsts& K, const double* W)
+{
+    const float rho = (float)W[0], r = __fdiv_rn(1.0f, rho);
+    const float U = __fmul_rn((float)W[1], r), V = __fmul_rn((float)W[2], r);
+    const float RT = __fmul_rn(__fsub_rn(__fmul_rn((float)W[3], r),
+                                         __fmul_rn(0.5f, __fadd_rn(__fmul_rn(U, U), __fmul_rn(V, V)))),
+                               0x1.555556p-1f);   // 2/3
+    const float T = __fmul_rn(2.0f, RT);
+    const float mu = __fmul_rn((float)K.mu_inf, dexp_f32(__fmul_rn((float)K.omega, dlog(T))));
+    return __fdiv_rn(mu, __fmul_rn(rho, RT));
+}
+
 __device__ __forceinline__ double tau_of(const StepConsts& K, const double* W)
 {
     // primitive variables through r = 1 / rho
@@ -528,7 +563,22 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     long long* r = d.wrt + 5 * c;
     const double vol = d.vol[c];
     const double s0 = ldexp(1.0, -K.fx0), s1 = ldexp(1.0, -K.fx1), s4 = ldexp(1.0, -K.fx4);
-    const double tau = tau_of(K, W);
+    // production precision: tau, x = dt / tau and e^{-x} in FP32, except in cells with a wall face (stretched,
+    // where the wave-flux time integrals need FP64) and at order 2 (whose g^h slope weight needs FP64)
+    const bool f32 = K.prec == 0 && !d.wallcell[c] && K.order != 2;
+    const double dt = d.dt[c];
+    double tau, x, e;
+    if (f32) {
+        const float t32 = tau_of_f32(K, W);
+        const float x32 = __fdiv_rn((float)dt, t32);
+        tau = t32;
+        x = x32;
+        e = dexp_f32(-x32);
+    } else {
+        tau = tau_of(K, W);
+        x = dt / tau;
+        e = dexp(-x);
+    }
     double Wp[4], Wh[4];
     // the factor 1 / Omega_i of Eq. 30 applied to the tally sums
     const double rvol = d.rcp[2 * c];
@@ -544,15 +594,12 @@ __global__ void k_decompose(const StepConsts K, Dev d)
         d.wprev[5 * c + k] = r[k]; d.wm[5 * c + k] = r[k]; d.wpl[5 * c + k] = r[k]; d.wcol[5 * c + k] = 0;
     }
     for (int k = 0; k < 4; ++k) { Wh[k] = W[k] - Wp[k]; d.Wh[4 * c + k] = Wh[k]; }
-    const double dt = d.dt[c];
-    const double x = dt / tau;
-    const double e = dexp(-x);
     d.tau[c] = tau;
     d.xr[c] = x;
     d.emx[c] = e;
     // order 2 weights the slope term of g^h with dbar_e + dt e^{-x} / 2, whose FP32 closed form loses too many
     // digits to cancellation: FP64 coefficients for every cell then
-    if (K.prec == 0 && !d.wallcell[c] && K.order != 2) lts_coeffs_f32((float)dt, (float)x, (float)e, d.co + 7 * c);
+    if (f32) lts_coeffs_f32((float)dt, (float)x, (float)e, d.co + 7 * c);
     else lts_coeffs(dt, tau, e, d.co + 7 * c);
     const int phys = realizable(K, Wh);
     d.hphys[c] = phys;

@@ -55,6 +55,21 @@ def test_logd_expd_within_two_ulp():
     assert L.oracle_expd(0.0) == 1.0
 
 
+def test_expf_within_two_ulp():
+    """Float e^x (production decomposition: e^{-dt/tau} and T^omega) against the double-precision exponential,
+    over the arguments the method meets (-87 .. 8), with 0 below -87."""
+    L = ob.lib()
+    rng = np.random.default_rng(4)
+    xs = np.concatenate([rng.uniform(-87.0, 8.0, 20000), rng.uniform(-1.0, 1.0, 5000),
+                         -np.exp(rng.uniform(-20.0, 0.0, 5000))]).astype(np.float32)
+    got = np.array([L.oracle_expf(float(x)) for x in xs], dtype=np.float32)
+    ref = np.exp(xs.astype(np.float64))
+    err = np.abs(got.astype(np.float64) - ref)
+    tol = 2.0 * np.maximum(np.spacing(ref.astype(np.float32)).astype(np.float64), 2.0 ** -149)
+    assert np.all(err <= tol), (xs[err > tol][:5], got[err > tol][:5], ref[err > tol][:5])
+    assert L.oracle_expf(-87.5) == 0.0 and L.oracle_expf(0.0) == 1.0
+
+
 def test_sincos2pi_float_and_double():
     rng = np.random.default_rng(3)
     us = ((rng.integers(0, 2 ** 23, 20000) + 0.5) * 2.0 ** -23).astype(np.float32)
