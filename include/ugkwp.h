@@ -98,8 +98,9 @@ typedef struct {
     uint64_t seed;            /* Philox key (low word xor case_id, high word) */
     uint32_t case_id;
     int32_t n_ref;            /* reference particles per cell, N_ref of Eq. 26 */
-    int32_t precision;        /* 0: FP32 particles, FP32 interior wave fluxes, FP64 cell update and wall
-                                 fluxes; 1: everything FP64 */
+    int32_t precision;        /* 0: FP32 particles, FP32 interior wave fluxes and (first order) FP32 tau,
+                                 e^{-dt/tau} of cells without a wall face; FP64 cell update, wall cells and
+                                 wall fluxes; 1: everything FP64 */
     int32_t wave_only;        /* 1: no particles (GKS limit, deterministic) */
     int32_t record_faces;     /* 1: record, per face and step, the masses of the particles crossing it before
                                  and after the dt_R / dt_L scaling (the side-recorded fluxes of Sec. IV A,

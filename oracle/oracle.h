@@ -51,7 +51,8 @@ typedef struct {
     uint64_t seed;
     uint32_t case_id;
     int32_t n_ref;
-    int32_t precision;       /* 0: FP32 particles (production emulation); 1: all FP64 */
+    int32_t precision;       /* 0: production emulation (FP32 particles; FP32 tau, e^{-x} away from walls at
+                              * first order); 1: all FP64 */
     int32_t wave_only;       /* 1: no particles (deterministic GKS limit) */
     int32_t record_faces;    /* 1: per-face side-recorded crossing masses of each step (S33): frec[4 f + 2 d]
                               * the masses before, frec[4 f + 2 d + 1] after the scaling, d = 0 for L -> R,
