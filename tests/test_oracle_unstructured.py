@@ -235,3 +235,21 @@ def test_malformed_meshes_rejected():
     _bad(q)
     ok = wl.UMesh(np.array([0.0, 1.0, 0.6, 0.0]), np.array([0.0, 0.0, 0.6, 1.0]), q.cells, q.boundary)
     ob.Oracle(_case(ok), precision=1, wave_only=True)
+
+
+def test_faces_numbered_by_first_appearance():
+    """The face numbering both implementations follow: walking the cells in order and each cell's edges in
+    order, a face gets the next number when first met, and the cell that meets it first is its L side."""
+    m = wl.tri_omesh(3, 6, 24, 2e-2, 3.0)
+    o = ob.Oracle(_case(m), precision=1, wave_only=True)
+    _, faces, _ = o.mesh_tables()
+    seen, order = {}, []
+    for c, q in enumerate(m.cells):
+        vs = [int(v) for v in q if v >= 0]
+        for a, b in zip(vs, vs[1:] + vs[:1]):
+            key = (min(a, b), max(a, b))
+            if key not in seen:
+                seen[key] = len(order)
+                order.append(c)
+    assert len(order) == o.F
+    assert np.array_equal(faces[:, 0], np.array(order))
