@@ -242,8 +242,8 @@ def test_faces_numbered_by_first_appearance():
     order, a face gets the next number when first met, and the cell that meets it first is its L side."""
     m = wl.tri_omesh(3, 6, 24, 2e-2, 3.0)
     o = ob.Oracle(_case(m), precision=1, wave_only=True)
-    _, faces, _ = o.mesh_tables()
-    seen, order = {}, []
+    _, faces, fg = o.mesh_tables()
+    seen, order, normals = {}, [], []
     for c, q in enumerate(m.cells):
         vs = [int(v) for v in q if v >= 0]
         for a, b in zip(vs, vs[1:] + vs[:1]):
@@ -251,5 +251,8 @@ def test_faces_numbered_by_first_appearance():
             if key not in seen:
                 seen[key] = len(order)
                 order.append(c)
+                ex, ey = m.xv[b] - m.xv[a], m.yv[b] - m.yv[a]
+                normals.append(np.array([ey, -ex]) / math.hypot(ex, ey))
     assert len(order) == o.F
     assert np.array_equal(faces[:, 0], np.array(order))
+    np.testing.assert_allclose(fg[:, :2], np.array(normals), atol=1e-14)
