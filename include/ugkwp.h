@@ -133,8 +133,13 @@ void ugkwp_destroy(ugkwp_ctx* ctx);
 /* Advance n_steps steps (asynchronous). */
 ugkwp_status ugkwp_step(ugkwp_ctx* ctx, int32_t n_steps);
 
-/* out[0..3]: residual of the last step per conservative component, normalised by the first step's;
- * out[4..7]: raw, sqrt(sum_i Omega_i ((W^{n+1} - W^n) / dt_i)^2). Synchronises. */
+/* out[4..7]: raw residual of the last step per conservative component (rho, rho U, rho V, rho E),
+ * sqrt(sum_i Omega_i ((W^{n+1} - W^n) / dt_i)^2); out[0..3]: the same divided by a freestream scale that
+ * cannot vanish, S_c sqrt(sum_i Omega_i) / L_ref with L_ref = 1, S = (rho c, rho c^2, rho c^2, rho c^3 / 2),
+ * rho_inf = 1 and c = U_inf + sqrt(gamma R T_inf) (an O(1) imbalance of the freestream fluxes over the
+ * whole domain reads about 1). The paper defines no residual (it judges steady state by monitored histories,
+ * Sec. V A); this normalisation does not depend on what the first step changed, so a start whose first step
+ * leaves a component unchanged (a plate's density) still has a meaningful 1e-6. Synchronises. */
 ugkwp_status ugkwp_residual(ugkwp_ctx* ctx, double* out);
 
 /* Wall pressure, shear stress (along t = (-n_y, n_x), n the outward normal of the fluid cell) and heat
@@ -212,7 +217,7 @@ ugkwp_status ugkwp_batch_create(ugkwp_ctx* const* ctxs, int32_t n, void* stream,
 ugkwp_status ugkwp_batch_step(ugkwp_batch* batch, int32_t n_steps);
 void ugkwp_batch_destroy(ugkwp_batch* batch);
 
-/* Checkpoint: the whole state (step counter, W, retained tally, particles, residual normalisation,
+/* Checkpoint: the whole state (step counter, W, retained tally, particles, last residual,
  * particle-mass-ratio EMA, surface sums and counters) to a binary file, and back into a context created
  * with the same mesh, gas, mode, precision and options. Steps after ugkwp_load reproduce the uninterrupted
  * run (the particle draws are keyed by particle id and step). The local time steps are not part of the

@@ -70,7 +70,7 @@ void oracle_destroy(oracle_ctx* cx);
 int  oracle_step(oracle_ctx* cx, int32_t n_steps);
 int  oracle_set_field(oracle_ctx* cx, const double* prim);          /* 4 per cell: rho, U, V, T */
 int  oracle_get_field(oracle_ctx* cx, double* W, double* Wp);       /* 4 per cell each; Wp nullable */
-int  oracle_residual(oracle_ctx* cx, double* out);                  /* [8]: normalised, raw */
+int  oracle_residual(oracle_ctx* cx, double* out);                  /* [8]: freestream-normalised, raw */
 int  oracle_surface(oracle_ctx* cx, double* p, double* tau, double* q, int32_t n_wall, int32_t averaged);
 /* building block: n new-particle normal triples z[3n] of particle ids pid0 + k drawn for a Shakhov cell with
  * acceptance-rejection weights (ax, ay, M) (see shakhov_weights); returns the fallback count */

@@ -1263,10 +1263,6 @@ static void update(or_ctx* cx)
         cx->chi_ema[c] = cx->step == 0 ? chi : cx->chi_ema[c] + alpha * (chi - cx->chi_ema[c]);
     }
     for (int q = 0; q < 4; ++q) cx->res[q] = sqrt(rs[q]);
-    if (!cx->have_res0) {
-        for (int q = 0; q < 4; ++q) cx->res0[q] = cx->res[q] > 0.0 ? cx->res[q] : 1.0;
-        cx->have_res0 = 1;
-    }
 }
 
 /* ------------------------------------------------------------ a11: surface quantities (Sec. V A) */
@@ -1361,10 +1357,29 @@ int oracle_get_field(oracle_ctx* cx, double* W, double* Wp)
     return OR_OK;
 }
 
+/* The paper judges steady state by monitored histories and defines no residual (Sec. V A). Normalised
+ * residual of this library: the raw residual of each component divided by a freestream scale that cannot
+ * vanish, S_c sqrt(sum_i Omega_i) / L_ref with L_ref = 1 and S = (rho c, rho c^2, rho c^2, rho c^3 / 2) at
+ * rho_inf = 1, c = U_inf + sqrt(gamma R T_inf) (the freestream's largest signal speed): an O(1) imbalance of
+ * the freestream fluxes over the whole domain reads about 1, whatever the first step changed. */
+static void residual_scale(const or_ctx* cx, double S[4])
+{
+    double area = 0.0;
+    for (int c = 0; c < cx->C; ++c) area += cx->vol[c];
+    const double cs = cx->U_inf + sqrt((5.0 / 3.0) * OR_R * 1.0);
+    const double ra = sqrt(area);
+    S[0] = cs * ra;
+    S[1] = (cs * cs) * ra;
+    S[2] = S[1];
+    S[3] = (0.5 * ((cs * cs) * cs)) * ra;
+}
+
 int oracle_residual(oracle_ctx* cx, double* out)
 {
+    double S[4];
+    residual_scale(cx, S);
     for (int q = 0; q < 4; ++q) {
-        out[q] = cx->res[q] / cx->res0[q];
+        out[q] = cx->res[q] / S[q];
         out[4 + q] = cx->res[q];
     }
     return OR_OK;

@@ -80,8 +80,7 @@ struct oracle_ctx {
     int64_t np, cap;
     or_particle* p;
     /* diagnostics */
-    double res[4], res0[4];
-    int have_res0;
+    double res[4];
     double* chi_ema;
     double *surf_sum, *surf_last;
     int64_t nsurf;

@@ -1520,8 +1520,6 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
     for (int b = 0; b < (int)gridDim.x; ++b)
         for (int q = 0; q < 4; ++q) s[q] += __ldcg(d.res_part + 4 * b + q);
     for (int q = 0; q < 4; ++q) d.res[q] = sqrt(s[q]);
-    if (*dstep == 0)
-        for (int q = 0; q < 4; ++q) d.res[4 + q] = d.res[q] > 0.0 ? d.res[q] : 1.0;
     const int kept = __ldcg(d.counts + 2);
     d.counts[0] = kept;
     if (!d.flags[0]) *d.bufsel = 1 - *d.bufsel;
@@ -2017,10 +2015,20 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         std::vector<double> vol(C);
         CK(cudaMemcpyAsync(vol.data(), d.vol, sizeof(double) * C, cudaMemcpyDeviceToHost, ctx.stream));
         CK(cudaStreamSynchronize(ctx.stream));
-        double vmax = 0.0;
+        double vmax = 0.0, area = 0.0;
         for (int c = 0; c < C; ++c) {
             if (!(vol[c] > 0.0)) return fail(ctx, UGKWP_EINVAL, "cell with non-positive area");
             if (vol[c] > vmax) vmax = vol[c];
+            area += vol[c];
+        }
+        // residual normalisation (ugkwp_residual): S_c sqrt(sum_i Omega_i) / L_ref, L_ref = 1,
+        // S = (rho c, rho c^2, rho c^2, rho c^3 / 2), rho_inf = 1, c = U_inf + sqrt(gamma R T_inf)
+        {
+            const double cs = K.U_inf + sqrt((5.0 / 3.0) * 0.5 * 1.0), ra = sqrt(area);
+            ctx.res_scale[0] = cs * ra;
+            ctx.res_scale[1] = (cs * cs) * ra;
+            ctx.res_scale[2] = ctx.res_scale[1];
+            ctx.res_scale[3] = (0.5 * ((cs * cs) * cs)) * ra;
         }
         double Tmax = 1.0;
         if (Tw > Tmax) Tmax = Tw;
@@ -2184,7 +2192,7 @@ ugkwp_status ugkwp_residual(ugkwp_ctx* h, double* out)
     double r[8];
     CK(cudaMemcpyAsync(r, ctx.d.res, sizeof r, cudaMemcpyDeviceToHost, ctx.stream));
     ugkwp_status st = check_device_error(ctx);
-    for (int q = 0; q < 4; ++q) { out[q] = r[q] / r[4 + q]; out[4 + q] = r[q]; }
+    for (int q = 0; q < 4; ++q) { out[q] = r[q] / ctx.res_scale[q]; out[4 + q] = r[q]; }
     return st;
 }
 

@@ -83,7 +83,7 @@ struct Dev {
     int *hphys, *nhp, *nhp_off, *cnt, *off, *cur;
     int* scan_tmp;
     double* flux;                      // [4F]
-    double *res_part, *res;            // residual: per-block partials; [8] = raw of this step, first step's
+    double *res_part, *res;            // residual: per-block partials; [8] = raw of this step (4 used)
     double* chi_ema;
     double *surf_sum, *surf_last;      // [3 nwall]
     // particles: A holds the cell-sorted retained set between steps, B is the staging buffer
@@ -114,6 +114,7 @@ struct Ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t step = 0;
     double Kn = 0.0, Ma = 0.0;                   // case conditions (warm-start features)
+    double res_scale[4] = {1.0, 1.0, 1.0, 1.0}; // freestream scale of the residual per component
     int use_graph = 0;
     cudaGraphExec_t graph = nullptr;
     std::string msg;

@@ -5,7 +5,7 @@ The paper judges steady state by exponential-moving-average histories (alpha = 2
 (Sec. V A) and defines no residual. Two yardsticks are provided here:
 - `run_to_residual`: the deterministic particle-free mode (the GKS limit of the method) stepped until every
   conservative component of the residual sqrt(sum_i Omega_i ((W^{n+1} - W^n) / dt_i)^2) falls below a
-  threshold, relative to a reference (by default the run's first step);
+  threshold, relative to a reference (by default the library's freestream scale of each component);
 - `steady_step`: the first step after which the EMA of a monitored history stays within a tolerance of
   the mean of the run's final window; the monitors are integrated wall loads (drag and heat load, `loads`),
   whose particle noise is far below that of any single wall face.
@@ -100,7 +100,7 @@ def run_to_residual(solver, tol: float = 1e-6, max_steps: int = 200000, chunk: i
                     marks=(1e-3, 1e-4, 1e-5, 1e-6)):
     """Step until every conservative component of the residual is below tol; the residual is the raw one
     divided by `ref` (4 values, e.g. the freestream start's first-step residual, so that runs from different
-    starting fields share one yardstick) or, without ref, the library's first-step normalised residual.
+    starting fields share one yardstick) or, without ref, the library's freestream-normalised residual.
     Returns dict(steps, residual, seconds, marks={threshold: (steps, seconds)} for the thresholds crossed)."""
     t0 = time.perf_counter()
     steps, res = 0, math.inf
