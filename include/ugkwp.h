@@ -164,9 +164,12 @@ ugkwp_status ugkwp_get_field(ugkwp_ctx* ctx, double* W, double* Wp);
 /* ugkwp_get_field without allocating: the same values, with the W^p conversion in a fixed device scratch
  * array instead of a per-call temporary (the paper has no counterpart; it serves callers that must not
  * allocate, e.g. a monitor sampling a case while a batched launch runs on other streams, since cudaMalloc
- * and cudaFree synchronise the whole device). Limit: meshes of at most 98304 cells, else EINVAL with a
- * message. The scratch is shared by all calls on a device: overlapping calls race, callers serialise them.
- * The first call with Wp != NULL on a device looks the scratch up; make it before any stream capture.
+ * and cudaFree synchronise the whole device). Limit for Wp != NULL: meshes of at most 98304 cells, else
+ * EINVAL with a message (a W-only call, Wp == NULL, uses no scratch and serves any mesh). The context's
+ * device must be the current device (else EINVAL). The scratch is shared by all calls on a device:
+ * overlapping calls race, callers serialise them. The first call with Wp != NULL on a device looks the
+ * scratch up; make it before any stream capture. Every check runs before a copy is queued, and a CUDA
+ * error after that waits for the queued copies, so the host buffers are free again whenever it returns.
  * Synchronises. */
 ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* ctx, double* W, double* Wp);
 

@@ -2111,7 +2111,8 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         CK(dalloc(ctx, &d.dstep, 1));
         int sms = 148;
         int dev = 0;
-        cudaGetDevice(&dev);
+        CK(cudaGetDevice(&dev));
+        ctx.device = dev;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         ctx.grid_particles = sms * 4;
         ctx.sms = sms;
@@ -2665,7 +2666,8 @@ const char* ugkwp_last_error(const ugkwp_ctx* h)
 // start at zero: every element read is first written by the same call. All calls on one device share it, so
 // calls that overlap in time (from several host threads, or for several contexts on one device) race on it:
 // callers serialise them. The scratch address is looked up once per device (cudaGetSymbolAddress) on the
-// first call with a non-NULL Wp on that device; make that first call before any stream capture begins.
+// first call with a non-NULL Wp on that device; make that first call before any stream capture begins. The
+// context's device must be the current one (the scratch is the current device's).
 #include <mutex>
 
 namespace {
@@ -2682,29 +2684,42 @@ extern "C" ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* h, double* W, double*
     if (!h || !W) return UGKWP_EINVAL;
     Ctx& ctx = h->c;
     const int C = ctx.k.C;
-    if (C > kNoAllocMaxCells)
-        return fail(ctx, UGKWP_EINVAL, "ugkwp_get_field_noalloc: the mesh has more than 98304 cells (its scratch limit)");
-    CK(cudaMemcpyAsync(W, ctx.d.W, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
+    // every check comes before the first copy is queued, so an error return leaves nothing in flight
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != ctx.device)
+        return fail(ctx, UGKWP_EINVAL, "ugkwp_get_field_noalloc: the context's device is not the current device");
+    double* scratch = nullptr;
     if (Wp) {
-        int dev = -1;
-        CK(cudaGetDevice(&dev));
+        if (C > kNoAllocMaxCells)
+            return fail(ctx, UGKWP_EINVAL, "ugkwp_get_field_noalloc: the mesh has more than 98304 cells (its scratch limit)");
         if (dev < 0 || dev >= kNoAllocMaxDevices)
             return fail(ctx, UGKWP_EINVAL, "ugkwp_get_field_noalloc: device ordinal beyond its table of 64");
-        double* scratch = nullptr;
-        {
-            std::lock_guard<std::mutex> lock(g_noalloc_mu);
-            if (!g_noalloc_ptr[dev]) {
-                void* p = nullptr;
-                const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-                if (e != cudaSuccess || !p)
-                    return fail(ctx, UGKWP_ECUDA, "ugkwp_get_field_noalloc: cudaGetSymbolAddress of the scratch failed");
-                g_noalloc_ptr[dev] = static_cast<double*>(p);
-            }
-            scratch = g_noalloc_ptr[dev];
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(ctx, UGKWP_ECUDA, "ugkwp_get_field_noalloc: cudaGetSymbolAddress of the scratch failed");
+            g_noalloc_ptr[dev] = static_cast<double*>(p);
         }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // from here on a failure waits for the copies already queued before it returns, so that the caller may
+    // reuse its host buffers at once
+    const auto queued_fail = [&](cudaError_t e, const char* what) {
+        cudaStreamSynchronize(ctx.stream);
+        ctx.msg = std::string(what) + ": " + cudaGetErrorString(e);
+        return UGKWP_ECUDA;
+    };
+    cudaError_t e = cudaMemcpyAsync(W, ctx.d.W, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream);
+    if (e != cudaSuccess) return queued_fail(e, "ugkwp_get_field_noalloc: W copy");
+    if (Wp) {
         k_wp_field<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, ctx.k.fx0, ctx.k.fx1, ctx.k.fx4, scratch);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(Wp, scratch, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return queued_fail(e, "ugkwp_get_field_noalloc: W^p conversion launch");
+        e = cudaMemcpyAsync(Wp, scratch, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream);
+        if (e != cudaSuccess) return queued_fail(e, "ugkwp_get_field_noalloc: W^p copy");
     }
     return check_device_error(ctx);
 }

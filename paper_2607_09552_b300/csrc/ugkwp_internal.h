@@ -109,6 +109,7 @@ struct Ctx {
     StepConsts k{};
     Dev d{};
     int ni = 0, nj = 0, periodic_j = 0, capacity = 0, res_blocks = 0, grid_particles = 0, sms = 148;
+    int device = -1;                             // the device current at creation (owns every allocation)
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;              // wave fluxes, overlapped with the particle kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
