@@ -39,4 +39,8 @@ def test_noalloc_rejects_meshes_beyond_its_scratch(cuda_lib):
     with pytest.raises(cuda_lib.UgkwpError) as e:
         s.field_noalloc()
     assert e.value.status == 1 and "98304" in str(e.value)
-    s.field()   # the allocating entry point still serves it
+    W, _ = s.field()   # the allocating entry point still serves it
+    # a W-only call uses no scratch, so it serves any mesh
+    W2, none = s.field_noalloc(with_wp=False)
+    assert none is None
+    np.testing.assert_array_equal(W2, W)
