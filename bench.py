@@ -1,15 +1,22 @@
 """Benchmark of the UGKWP-LTS steady-iteration step on B300.
 
-Workload (N = 1): hypersonic flow past a cylinder, Kn = 0.1 (freestream mean free path over the diameter),
-Ma = 5, T_w = T_inf, body-fitted O-mesh 120 radial x 160 circumferential, first layer 1e-3 D, outer
-boundary at 15 D, N_ref = 100 particles per cell (about 1.9 million particles), CFL 0.8, local time
-stepping, production precision (FP32 particles, 64-bit fixed-point tallies, FP64 cell update). The state is
-first advanced `--burn` steps from the uniform freestream so that the particle population is developed;
-then W warm-up steps and K timed steps. One step is one full pass of the method over the domain.
+Workload (N = 1): hypersonic flow past a cylinder in the dense regime, Kn = 0.01 (freestream mean free path
+over the diameter), Ma = 15, T_w = T_inf, body-fitted O-mesh 240 radial x 320 circumferential, first layer
+1e-4 D, outer boundary at 20 D, N_ref = 150 particles per cell, CFL 0.8, local time stepping, production
+precision (FP32 particles, 64-bit fixed-point tallies, FP64 cell update): the largest single-GPU
+configuration. The state is first advanced from the uniform freestream through its start-up transient (about
+5e7 particles at first) until the particle count settles (changes by less than 1% over 1,000 steps, checked
+every 500 steps; about 1.7e7 particles); then W warm-up steps and K timed steps. One step is one full pass
+of the method over the domain.
 
 Timing: every timed step is bracketed by CUDA events on the library's stream, and an L2 flush (a 512 MB
 write) precedes each step outside the events. value = particle-steps / summed step time. The dominant
-kernel (particle transport and tallies) is timed by the library's own stage events over the same steps.
+kernel (particle transport and tallies) is timed by the library's own stage events over a profiled window
+that follows the timed steps (same state, eager launches, every stage on the library's stream).
+
+With N = 1 the line also carries `convergence`: steps and wall-clock to a 1e-6 residual (particle-free
+mode, all FP64) and to a steady drag and heat load (stochastic method), LTS against GTS, on the 120 x 160
+cylinder at Kn 0.1, Ma 5 (the dense cylinder reaches no 1e-6 within minutes); `--no-convergence` skips it.
 
 Under torchrun (N > 1) every rank runs an independent replica (seed = rank) of the workload: no data-path
 collective, weak scaling; the time is the max over ranks and value the sum of their particle-steps.
@@ -96,10 +103,10 @@ class Clocks:
 
 
 def bench_case(args=None):
-    """The throughput workload: the Kn 0.1 cylinder (the default), with --case kn001 the dense-regime one, with
+    """The throughput workload: the dense-regime Kn 0.01 cylinder (the default), with --case kn01 the Kn 0.1 one, with
     --case tri the cylinder at Kn 0.1 on the radius on the hybrid unstructured mesh of the paper's cell count,
     with --case tri_kn001 / tri_plate the stand-ins of the paper's other two unstructured meshes."""
-    which = getattr(args, "case", "kn01") if args is not None else "kn01"
+    which = getattr(args, "case", "kn001") if args is not None else "kn001"
     if which == "kn001":
         return wl.case_cylinder_kn001()
     if which == "tri":
@@ -132,6 +139,25 @@ def config_dict(case, burn, flush):
             "FP64 cell update", "burn_in_steps": burn, "l2": flush, "parallelism": "replicas (one case per GPU)"}
 
 
+def burn_in(solver, args):
+    """Advance the fresh state through its start-up transient: a fixed number of steps (--burn >= 0), or until
+    the particle count changes by less than 1% over 1,000 steps (checked every 500 steps, at least 5,000
+    steps, at most --burn-max)."""
+    if args.burn >= 0:
+        solver.step(args.burn)
+        return args.burn, f"fixed: {args.burn} steps"
+    hist = []
+    steps = 0
+    while steps < args.burn_max:
+        solver.step(500)
+        steps += 500
+        hist.append(solver.num_particles())
+        if steps >= 5000 and len(hist) >= 3 and abs(hist[-1] - hist[-3]) < 0.01 * hist[-1]:
+            break
+    return steps, ("until the particle count changed by less than 1% over 1,000 steps (checked every 500, "
+                   f"at least 5,000, at most {args.burn_max}); counts at the last checks {hist[-3:]}")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -150,7 +176,7 @@ def run_ours(args):
     cap = 8 * case.n_ref * case.mesh.ncells if args.case in ("kn001", "tri_kn001") else 0
     solver = ugkwp.Solver(case, precision=0, seed=rank, stream=stream.cuda_stream, use_graph=True, order=args.order,
                           capacity=cap)
-    solver.step(args.burn)
+    burn, burn_rule = burn_in(solver, args)
     launch, tune_ms = solver.autotune(16) if not args.no_autotune else (solver.launch(), None)
     stream.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -203,10 +229,15 @@ def run_ours(args):
         per_launch = prof_psteps / max(nprof, 1)
         achieved = BYTES_PER_PARTICLE_STEP * per_launch / (part_ms * 1e-3) / 1e9
         traffic = particles_traffic(per_launch, case.name)
-        cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
-        cfg = config_dict(case, args.burn, "512 MB L2 flush before every timed step, outside the events")
+        cpu = cpu_baseline(args, solver) if not args.no_cpu_baseline else None
+        cfg = config_dict(case, burn, "512 MB L2 flush before every timed step, outside the events")
+        cfg["burn_in_rule"] = burn_rule
         cfg["reconstruction_order"] = args.order
-        cfg["launch"] = {"chunk": launch[0], "blocks_per_sm": launch[1], "sort_every": launch[2],
+        tiled = launch[3] == 2
+        cfg["launch"] = {"transport_kernel": "k_particles_tiled (1024-particle tiles, bulk async copies, 2 CTAs/SM)"
+                         if tiled else "k_particles (warp-chunked)",
+                         "chunk": None if tiled else launch[0], "blocks_per_sm": 2 if tiled else launch[1],
+                         "sort_every": launch[2],
                          "chosen_by": "autotuner" if not args.no_autotune else "defaults", "graph": True}
         line = {
             "metric": "particle-steps/s", "value": ps_all / (ms_all * 1e-3), "unit": "particle-steps/s",
@@ -217,10 +248,12 @@ def run_ours(args):
             "cell_updates_per_s": world * ncells_steps / (ms_all * 1e-3),
             "particles_per_step": psteps / args.steps,
             "stage_ms_per_step": {k: v / max(nprof, 1) for k, v in stage_ms.items()},
-            "stage_window": f"{nprof} further steps, eager launches with per-stage events",
+            "stage_window": f"{nprof} further steps, eager launches with per-stage events, every stage on the "
+                            "library's stream (the second stream's ghost sources and wave fluxes not overlapped)",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "kernel": "k_particles (t_f draw, transport with dt_R/dt_L scaling, tallies)",
+                         "kernel": ("k_particles_tiled" if launch[3] == 2 else "k_particles") +
+                                   " (t_f draw, transport with dt_R/dt_L scaling, tallies, compaction)",
                          "algorithmic_bytes_per_launch": BYTES_PER_PARTICLE_STEP * per_launch,
                          "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
@@ -229,8 +262,11 @@ def run_ours(args):
             "last_step": {"particles": int(s1[1]), "new": int(s1[2]), "collided_removed": int(s1[3]),
                           "left_domain": int(s1[4]), "face_crossings": int(s1[5]), "wall_hits": int(s1[6])},
         }
-        print(json.dumps(line))
     solver.close()
+    if rank == 0:
+        if world == 1 and not args.no_convergence:
+            line["convergence"] = convergence_summary(args, stream)
+        print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
 
@@ -318,13 +354,20 @@ def run_e2e(args, solver, stream):
             "d2h_bytes_per_step": out_bytes / args.steps}
 
 
-def cpu_baseline(args):
-    """The oracle (plain C, one thread) on a bounded sample of the same workload: a few full steps from the
-    freestream start."""
+def cpu_baseline(args, solver=None):
+    """The oracle (plain C, one thread) on a bounded sample of the same workload: the device's burned-in state
+    (cell field, retained tally, particles) loaded into the oracle (for timing only), then full steps for
+    about --cpu-seconds."""
     from oracle import binding as ob
     case = bench_case(args)
     o = ob.Oracle(case, precision=0)
-    o.step(1)
+    if solver is not None:
+        W, _ = solver.field()
+        o.set_state(int(solver.stats()[0]), W, solver.tallies()["wret"], solver.particles())
+        what = "the device's burned-in state loaded into the oracle (timing only)"
+    else:
+        o.step(1)
+        what = "the freestream start (after 1 untimed step)"
     t0 = time.perf_counter()
     n0 = 0
     steps = 0
@@ -335,7 +378,8 @@ def cpu_baseline(args):
         steps += 1
     dt = time.perf_counter() - t0
     return {"value": n0 / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full steps of the same workload from the freestream start (after 1 untimed step)"}
+            "sample": f"{steps} full steps ({n0 / max(steps, 1):.3g} particles per step) of the same workload from "
+                      f"{what}"}
 
 
 def run_reference(args):
@@ -373,16 +417,28 @@ def stagnation_pair(case):
 
 
 def run_convergence(args):
-    """Steps and wall-clock to convergence, LTS vs GTS, on the bench workload (and the dense-regime cylinder
-    with --case kn001): (i) the deterministic particle-free mode (GKS limit, all FP64) to a 1e-6 residual
-    (GKS convention: relative to the run's first step), with the steps at which 1e-3 .. 1e-6 were crossed;
-    (ii) the full stochastic method (production precision) to "steady": the EMA (alpha = 2/1001) of the
-    drag and heat-load coefficients stays within 1% of its final-window mean."""
+    """Steps and wall-clock to convergence, LTS vs GTS, on the chosen workload (--case)."""
     import torch
-    from paper_2607_09552_b300 import steady, ugkwp
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    case = bench_case(args)
+    print(json.dumps(converge_case(bench_case(args), args, stream)))
+
+
+def convergence_summary(args, stream):
+    """The convergence comparison of the bench line: the 120 x 160 cylinder at Kn 0.1, Ma 5 (LTS against GTS)."""
+    out = converge_case(wl.case_cylinder_kn01(), args, stream, verbose=False)
+    out["note"] = ("residual: raw / freestream scale (ugkwp_residual); steady: EMA (alpha 2/1001) of drag and "
+                   "heat load within max(1%, 3 sigma) of the final-window mean; wall clock includes a surface "
+                   "read-back every step (both modes); warm start: bench.py --mode warmstart")
+    return out
+
+
+def converge_case(case, args, stream, verbose=True):
+    """(i) the deterministic particle-free mode (GKS limit, all FP64) to a 1e-6 residual (the library's
+    freestream-normalised residual), with the steps at which 1e-3 .. 1e-6 were crossed; (ii) the full
+    stochastic method (production precision) to "steady": the EMA (alpha = 2/1001) of the drag and heat-load
+    coefficients stays within the tolerance of its final-window mean."""
+    from paper_2607_09552_b300 import steady, ugkwp
     out = {"mode": "convergence", "workload": config_dict(case, 0, "n/a")["workload"],
            "reconstruction_order": args.order, "results": {}}
     geom = steady.wall_geometry(case)
@@ -399,7 +455,8 @@ def run_convergence(args):
                                    "ms_per_step": 1e3 * w["seconds"] / w["steps"],
                                    "marks": {f"{k:.0e}": v for k, v in w["marks"].items()}}
             s.close()
-            print(json.dumps({"phase": f"{ts} wave_only", **r}), flush=True)
+            if verbose:
+                print(json.dumps({"phase": f"{ts} wave_only", **r}), flush=True)
         n = args.lts_steps if not gts else args.gts_steps
         # GTS keeps far more particles (every cell samples with the smallest time step): larger capacity
         cap = (32 if gts else 8) * case.n_ref * case.mesh.ncells
@@ -423,7 +480,8 @@ def run_convergence(args):
                     hnp.append(s.num_particles())
         except ugkwp.UgkwpError as e:
             r["stochastic_error"] = f"step {len(hcd)}: {e}; particles {hnp[-3:]}"
-            print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
+            if verbose:
+                print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
             s.close()
             continue
         kd, _ = steady.steady_step(hcd)
@@ -439,9 +497,12 @@ def run_convergence(args):
                            "stagnation_CQ": float(np.mean(hq[tail]) / (0.5 * U ** 3)),
                            "residual_plateau": float(np.median(hres[len(hres) // 2:])),
                            "particles_mean": float(np.mean(hnp[len(hnp) // 2:])), "particles_max": int(np.max(hnp)),
-                           "drag_history_every_500": [round(x, 5) for x in hcd[::500]]}
+                           }
+        if verbose:
+            r["stochastic"]["drag_history_every_500"] = [round(x, 5) for x in hcd[::500]]
         s.close()
-        print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
+        if verbose:
+            print(json.dumps({"phase": f"{ts} stochastic", **r}), flush=True)
     L, G = out["results"]["LTS"], out["results"]["GTS"]
     lw, gw = L.get("wave_only_fp64", {}), G.get("wave_only_fp64", {})
     if lw.get("steps_to_1e-6") and gw.get("steps_to_1e-6"):
@@ -451,7 +512,7 @@ def run_convergence(args):
     if ls.get("steps_to_steady") and gs.get("steps_to_steady"):
         out["stochastic_speedup_steps"] = gs["steps_to_steady"] / ls["steps_to_steady"]
         out["stochastic_speedup_wall"] = gs["wall_s_to_steady"] / ls["wall_s_to_steady"]
-    print(json.dumps(out))
+    return out
 
 
 def run_batch(args):
@@ -466,7 +527,7 @@ def run_batch(args):
     solvers = [ugkwp.Solver(c, precision=0, stream=stream.cuda_stream, use_graph=True,
                             capacity=8 * c.n_ref * c.mesh.ncells) for c in cases]
     for s in solvers:
-        s.step(args.burn)
+        s.step(args.burn if args.burn >= 0 else 3000)
     torch.cuda.synchronize()
     b = ugkwp.Batch(solvers, stream=stream.cuda_stream)
     b.step(args.warmup)
@@ -714,7 +775,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--burn", type=int, default=3000)
+    ap.add_argument("--burn", type=int, default=-1,
+                    help="burn-in steps; -1: until the particle count changes by < 1%% over 1,000 steps")
+    ap.add_argument("--burn-max", type=int, default=40000)
+    ap.add_argument("--no-convergence", action="store_true")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -723,7 +787,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=400)
     ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch", "warmstart"])
     ap.add_argument("--batch-scale", type=float, default=1.0)
-    ap.add_argument("--case", default="kn01", choices=["kn01", "kn001", "tri", "tri_kn001", "tri_plate"])
+    ap.add_argument("--case", default="kn001", choices=["kn01", "kn001", "tri", "tri_kn001", "tri_plate"])
     ap.add_argument("--order", type=int, default=1, choices=[1, 2],
                     help="reconstruction order of the wave fluxes (2: second order, FP64 wave fluxes)")
     ap.add_argument("--max-wave-steps", type=int, default=400000)

@@ -229,29 +229,35 @@ void ugkwp_batch_destroy(ugkwp_batch* batch);
 ugkwp_status ugkwp_save(ugkwp_ctx* ctx, const char* path);
 ugkwp_status ugkwp_load(ugkwp_ctx* ctx, const char* path);
 
-/* Launch parameters of the particle kernels: particles per chunk a warp claims in the transport kernel (a
- * multiple of 32 in [32, 8192]), its blocks per SM (1..16) and the steps between counting sorts of the
- * particles by cell (1..64); 0 keeps a value. They change only the speed: chunks and sorts reorder
- * particles, and every result is an integer sum or a per-particle / per-face quantity. Takes effect at the
- * next step (a captured step graph is re-captured); a batch keeps the values its contexts had at
- * ugkwp_batch_create. ugkwp_get_launch fills out[3] in the same order. */
-ugkwp_status ugkwp_set_launch(ugkwp_ctx* ctx, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every);
+/* Launch parameters of the particle kernels: the transport kernel (1: warp-chunked, every precision; 2:
+ * tile-staged, production precision only: 1024-particle tiles moved into shared memory by bulk asynchronous
+ * copies, double-buffered, with the particles that reach a face or collide queued and flown together; the
+ * default in production precision), the warp-chunked kernel's particles per chunk a warp claims (a multiple
+ * of 32 in [32, 8192]) and blocks per SM (1..16), and the steps between counting sorts of the particles by
+ * cell (1..64); 0 keeps a value. They change only the speed: both kernels perform the same per-particle
+ * operations, chunks, tiles and sorts reorder particles, and every result is an integer sum or a
+ * per-particle / per-face quantity. EINVAL for a value out of range or the tile-staged kernel in the FP64
+ * mode. Takes effect at the next step (a captured step graph is re-captured); a batch keeps the values its
+ * contexts had at ugkwp_batch_create. ugkwp_get_launch fills out[4]: chunk, blocks per SM, sort interval,
+ * transport kernel. */
+ugkwp_status ugkwp_set_launch(ugkwp_ctx* ctx, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every,
+                              int32_t transport);
 ugkwp_status ugkwp_get_launch(ugkwp_ctx* ctx, int32_t* out);
-/* Autotuner: times each combination of chunk {128, 256}, blocks per SM {4, 6, 8} and sort interval
- * {8, 16, 32} over whole sort periods of at least `steps` steps (real steps of the run: the state advances)
- * with CUDA events on the context's stream, keeps the fastest and returns it in best[3] (nullable, order of
- * ugkwp_set_launch) and its milliseconds per step in best_ms (nullable). Synchronises. A particle-free
- * context keeps its values. */
+/* Autotuner: times the tile-staged kernel (production precision) and the warp-chunked kernel with chunk
+ * {128, 256} x blocks per SM {4, 6, 8}, each with sort interval {8, 16, 32}, over whole sort periods of at
+ * least `steps` steps (real steps of the run: the state advances) with CUDA events on the context's stream,
+ * keeps the fastest and returns it in best[4] (nullable, order of ugkwp_get_launch) and its milliseconds per
+ * step in best_ms (nullable). Synchronises. A particle-free context keeps its values. */
 ugkwp_status ugkwp_autotune(ugkwp_ctx* ctx, int32_t steps, int32_t* best, double* best_ms);
 
 /* Per-stage device timing with CUDA events recorded on the context's stream around each stage of every
  * step taken while enabled (graph replay is bypassed meanwhile). ugkwp_profile synchronises, returns the
  * summed milliseconds of the 6 stages (ms[0..5]: decomposition + slot scan, new-particle sampling,
- * particle transport, tallies and compaction, ghost particle sources + wave fluxes (on a second stream,
- * overlapped with sampling and transport), the periodic counting sort of the particles by cell (after the
- * second stream joins), conservative update + surface quantities + step bookkeeping) and the number of
- * profiled steps, and
- * clears the record (ms needs room for 8 values). */
+ * particle transport, tallies and compaction, ghost particle sources + wave fluxes, the periodic counting
+ * sort of the particles by cell, conservative update + surface quantities + step bookkeeping) and the number
+ * of profiled steps, and clears the record (ms needs room for 8 values). Profiled steps run the work of the
+ * second stream (ghost sources and wave fluxes, otherwise overlapped with sampling and transport) on the
+ * context's stream, so that each stage's time is its own; the results are the same. */
 ugkwp_status ugkwp_set_profiling(ugkwp_ctx* ctx, int32_t enable);
 ugkwp_status ugkwp_profile(ugkwp_ctx* ctx, double* ms, int64_t* steps);
 /* ---- Learned warm start -------------------------------------------------------------------------------

@@ -1106,6 +1106,33 @@ __device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict
     return alive;
 }
 
+// W^{p,+} started as W^{p,-} (each particle unchanged in its cell). A particle that crossed a face, met a
+// boundary or left moves its contribution; a collided one that stays is added to wcol, and the retained tally
+// W^{p,+} - wcol is formed in k_update. Integer sums: identical to summing every final contribution.
+template <typename T>
+__device__ __forceinline__ void tally_move(const Dev& d, T s0, T s1, T s4, int it, bool alive, bool collide, int c0,
+                                           T m0, T u0, T v0, T w0, int c, T m, T u, T v, T w)
+{
+    unsigned long long* pl = reinterpret_cast<unsigned long long*>(d.wpl);
+    unsigned long long* cl = reinterpret_cast<unsigned long long*>(d.wcol);
+    if (it > 0) {
+        long long o[5], f[5];
+        fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
+        if (alive) fix5(m, u, v, w, s0, s1, s4, d.err, f);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            atomicAdd(pl + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
+            if (alive) atomicAdd(pl + 5 * (size_t)c + k, (unsigned long long)f[k]);
+            if (alive && collide) atomicAdd(cl + 5 * (size_t)c + k, (unsigned long long)f[k]);
+        }
+    } else if (collide) {
+        long long o[5];
+        fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) atomicAdd(cl + 5 * (size_t)c0 + k, (unsigned long long)o[k]);
+    }
+}
+
 // ------------------------------------------------- a3-a6: free flight, transport and tallies
 // One thread per particle (warp-uniform grid-stride loop). Retained particles draw t_f (Eq. 27 with dt_i),
 // new ones fly the whole dt_i; free transport through the cell faces (Eq. 28) with mass and remaining time
@@ -1190,28 +1217,7 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
             } else {
                 n_left++;
             }
-            // W^{p,+} started as W^{p,-} (each particle unchanged in its cell). A particle that crossed a face,
-            // met a boundary or left moves its contribution; a collided one that stays is added to wcol, and
-            // the retained tally W^{p,+} - wcol is formed in k_update. Integer sums: identical to summing
-            // every final contribution.
-            unsigned long long* pl = reinterpret_cast<unsigned long long*>(d.wpl);
-            unsigned long long* cl = reinterpret_cast<unsigned long long*>(d.wcol);
-            if (it > 0) {
-                long long o[5], f[5];
-                fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
-                if (alive) fix5(m, u, v, w, s0, s1, s4, d.err, f);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    atomicAdd(pl + 5 * (size_t)c0 + k, (unsigned long long)(-o[k]));
-                    if (alive) atomicAdd(pl + 5 * (size_t)c + k, (unsigned long long)f[k]);
-                    if (alive && collide) atomicAdd(cl + 5 * (size_t)c + k, (unsigned long long)f[k]);
-                }
-            } else if (collide) {
-                long long o[5];
-                fix5(m0, u0, v0, w0, s0, s1, s4, d.err, o);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) atomicAdd(cl + 5 * (size_t)c0 + k, (unsigned long long)o[k]);
-            }
+            tally_move(d, s0, s1, s4, it, alive, collide, c0, m0, u0, v0, w0, c, m, u, v, w);
         }
         // survivors
         if (sort_step) {
@@ -1251,6 +1257,317 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
             if ((lane == 31 || next != key) && key >= 0) atomicAdd(d.cnt + key, lane - start + 1);
         }
     }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
+        n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
+        n_removed += __shfl_xor_sync(0xffffffffu, n_removed, o);
+        n_left += __shfl_xor_sync(0xffffffffu, n_left, o);
+        max_it = max(max_it, __shfl_xor_sync(0xffffffffu, max_it, o));
+    }
+    if (lane == 0) {
+        if (n_removed) atomicAdd(d.stats + 3, n_removed);
+        if (n_left) atomicAdd(d.stats + 4, n_left);
+        if (n_cross) atomicAdd(d.stats + 5, n_cross);
+        if (n_hits) atomicAdd(d.stats + 6, n_hits);
+        if (max_it) atomicMax(d.stats + 7, (unsigned long long)max_it);
+    }
+}
+
+// ---------------------------------------- a3-a7, tile-staged: the production-precision transport kernel
+// Persistent CTAs of kTileThreads threads, two per SM, claim tiles of kTile consecutive particles from a
+// global counter. A tile's records (x, y, u, v, w, m, cell, id) arrive in shared memory by bulk asynchronous
+// copies (cp.async.bulk, completion counted on an mbarrier), double-buffered: the next tile is in flight
+// while the current one is processed, so HBM streams independently of the divergent transport. Per tile:
+//  A. one thread per particle, all lanes together: t_f (Eq. 27, computed form as in k_particles) and the
+//     stay test of the start cell; a particle that stays and does not collide moves (x += u t_r) in shared
+//     memory and is done; the others (a face ahead within t_r, or colliding) go to a shared-memory queue.
+//  B. the queue, 32 queued particles per warp at a time: the full free flight of fly() (crossings with the
+//     dt_R / dt_L scaling, walls, exits) and the tallies, exactly as in k_particles.
+//  C. survivors: compacted into the other buffer at one slot range per tile (tile order kept), or on sort
+//     steps written in place with their per-cell run counts for the counting sort.
+// Every per-particle operation is that of k_particles, in the same order, so the results are identical.
+constexpr int kTile = 1024;
+constexpr int kTileThreads = 256;
+constexpr int kTilePer = kTile / kTileThreads;
+constexpr unsigned long long kTileWaitNs = 2000000000ull;   // bounded wait for a tile's copies (2 s)
+
+struct TileRecords {   // one tile of particle records, SoA, every array 16-byte aligned
+    float x[kTile], y[kTile], u[kTile], v[kTile], w[kTile], m[kTile];
+    int cell[kTile];
+    unsigned long long pid[kTile];
+};
+struct TileSmem {
+    TileRecords rec[2];
+    float tr[kTile];                 // queued particles: remaining free-flight time
+    unsigned short queue[kTile];     // queued particles' tile indices
+    unsigned char st[kTile];         // 1 survivor, 0 gone; phase A: 2 queued, 3 queued and colliding
+    int chunk_off[kTilePer * kTileThreads / 32 + 1];
+    int qn, next, base, abort;
+    unsigned long long bar[2];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// waits for the phase of the given parity with a time limit; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0u && global_ns() - t0 > kTileWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// one thread: copy tile t of A into stage r (the record count rounded up to 4, which the buffers' slack
+// covers, so that every copy is a multiple of 16 bytes from a 16-byte aligned address)
+__device__ __forceinline__ void tile_issue(const ParticleSoA<float>& A, int t, int n, TileRecords& r,
+                                           unsigned long long* bar)
+{
+    const int base = t * kTile;
+    const int cnt4 = (min(kTile, n - base) + 3) & ~3;
+    const uint32_t b4 = (uint32_t)cnt4 * 4u, b8 = (uint32_t)cnt4 * 8u;
+    mbar_expect_tx(bar, 7u * b4 + b8);
+    bulk_load(r.x, A.x + base, b4, bar);
+    bulk_load(r.y, A.y + base, b4, bar);
+    bulk_load(r.u, A.u + base, b4, bar);
+    bulk_load(r.v, A.v + base, b4, bar);
+    bulk_load(r.w, A.w + base, b4, bar);
+    bulk_load(r.m, A.m + base, b4, bar);
+    bulk_load(r.cell, A.cell + base, b4, bar);
+    bulk_load(r.pid, A.pid + base, b8, bar);
+}
+
+__global__ void __launch_bounds__(kTileThreads, 2) k_particles_tiled(const StepConsts K, const Dev d,
+                                                                     ParticleSoA<float> PA, ParticleSoA<float> PB,
+                                                                     const CellFaces<float>* __restrict__ cf,
+                                                                     PCell<float> pc, const long long* dstep)
+{
+    extern __shared__ __align__(128) unsigned char tile_smem_raw[];
+    TileSmem& S = *reinterpret_cast<TileSmem*>(tile_smem_raw);
+    const int sel = *d.bufsel;
+    const ParticleSoA<float> A = sel ? PB : PA, B = sel ? PA : PB;
+    const bool sort_step = d.flags[0] != 0;
+    const int nret = d.counts[0];
+    const int n = nret + d.counts[1], cap = d.counts[3];
+    const int ntiles = (n + kTile - 1) / kTile;
+    const Rng g{K.k0, K.k1, (uint32_t)*dstep};
+    const float s0 = float(ldexp(1.0, K.fx0)), s1 = float(ldexp(1.0, K.fx1)), s4 = float(ldexp(1.0, K.fx4));
+    const float m2RTw = float(K.m2RTw), sigw = float(K.sig_w), ws = float(K.wall_specular);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0;
+    int max_it = 0;
+
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.abort = 0;
+        S.next = atomicAdd(d.counts + 5, 1);
+        if (S.next < ntiles) tile_issue(A, S.next, n, S.rec[0], &S.bar[0]);
+    }
+    __syncthreads();
+    int tile = S.next;
+    int b = 0;
+    uint32_t parity[2] = {0u, 0u};
+    uint32_t pending = tile < ntiles ? 1u : 0u;   // stages with copies in flight (bit per stage)
+    while (tile < ntiles) {
+        __syncthreads();   // every thread has read S.next; the other stage is free
+        if (tid == 0) {
+            S.qn = 0;
+            S.next = atomicAdd(d.counts + 5, 1);
+            if (S.next < ntiles) tile_issue(A, S.next, n, S.rec[b ^ 1], &S.bar[b ^ 1]);
+        }
+        if (!mbar_wait_bounded(&S.bar[b], parity[b])) S.abort = 1;
+        __syncthreads();
+        const int nxt = S.next;
+        if (nxt < ntiles) pending |= 1u << (b ^ 1);
+        if (S.abort) break;
+        parity[b] ^= 1u;
+        pending &= ~(1u << b);
+        TileRecords& R = S.rec[b];
+        const int base = tile * kTile, cnt = min(kTile, n - base);
+
+        // A: t_f and the stay test of the start cell for every particle of the tile
+#pragma unroll 1
+        for (int k = 0; k < kTilePer; ++k) {
+            const int j = k * kTileThreads + tid;
+            bool q = false;
+            if (j < cnt) {
+                const int i = base + j;
+                const int c = R.cell[j];
+                const float x = R.x[j], y = R.y[j], u = R.u[j], v = R.v[j];
+                const float dtc = pc.dt_(c);
+                float tr = dtc;
+                bool collide = false;
+                if (i >= nret) {
+                    tr = dtc;
+                } else {
+                    float U[1];
+                    Unif<float>::get(g, R.pid[j], DRAW_TF, 1, U);
+                    collide = U[0] > pc.emx_(c);
+                    if (collide) {
+                        const float a = -(pc.tau_(c) * dlog(U[0]));
+                        if (a < dtc) tr = a;
+                    }
+                }
+                const bool stays = stays_in(cf[c], d.nfc[c], -1, x, y, u, v, tr);
+                if (stays && !collide) {
+                    R.x[j] = x + u * tr;
+                    R.y[j] = y + v * tr;
+                    S.st[j] = 1;
+                } else {
+                    S.tr[j] = tr;
+                    S.st[j] = collide ? 3 : 2;
+                    q = true;
+                }
+            }
+            const unsigned qm = __ballot_sync(0xffffffffu, q);
+            if (qm) {
+                int q0 = 0;
+                if (lane == 0) q0 = atomicAdd(&S.qn, __popc(qm));
+                q0 = __shfl_sync(0xffffffffu, q0, 0);
+                if (q) S.queue[q0 + __popc(qm & lt_mask)] = (unsigned short)j;
+            }
+        }
+        __syncthreads();
+
+        // B: the queued particles' free flight and tallies
+        const int Q = S.qn;
+        for (int k = tid; k < Q; k += kTileThreads) {
+            const int j = S.queue[k];
+            float x = R.x[j], y = R.y[j], u = R.u[j], v = R.v[j], w = R.w[j], m = R.m[j];
+            int c = R.cell[j];
+            const unsigned long long pid = R.pid[j];
+            const bool collide = S.st[j] == 3;
+            const int c0 = c;
+            const float m0 = m, u0 = u, v0 = v, w0 = w;
+            int it = 0;
+            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, ws, x, y, u, v, w, m, S.tr[j], c, -1,
+                                   (uint64_t)pid, it, n_cross, n_hits);
+            max_it = max(max_it, it);
+            if (alive) {
+                if (collide) n_removed++;
+            } else {
+                n_left++;
+            }
+            tally_move(d, s0, s1, s4, it, alive, collide, c0, m0, u0, v0, w0, c, m, u, v, w);
+            R.x[j] = x; R.y[j] = y; R.u[j] = u; R.v[j] = v; R.w[j] = w; R.m[j] = m;
+            R.cell[j] = c;
+            S.st[j] = (alive && !collide) ? 1 : 0;
+        }
+        __syncthreads();
+
+        // C: survivors
+        if (sort_step) {
+#pragma unroll 1
+            for (int k = 0; k < kTilePer; ++k) {
+                const int j = k * kTileThreads + tid;
+                int key = -1;
+                if (j < cnt) {
+                    const int i = base + j;
+                    key = S.st[j] == 1 ? R.cell[j] : -1;
+                    B.x[i] = R.x[j]; B.y[i] = R.y[j]; B.u[i] = R.u[j]; B.v[i] = R.v[j]; B.w[i] = R.w[j];
+                    B.m[i] = R.m[j];
+                    B.cell[i] = key;
+                    B.pid[i] = R.pid[j];
+                }
+                // survivors per cell for the counting sort, one atomic per run of equal cell in the warp
+                const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+                int start = (lane == 0 || prev != key) ? lane : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, start, o);
+                    if (lane >= o) start = max(start, t);
+                }
+                const int nx = __shfl_down_sync(0xffffffffu, key, 1);
+                if ((lane == 31 || nx != key) && key >= 0) atomicAdd(d.cnt + key, lane - start + 1);
+            }
+        } else {
+            // survivors per (round k, warp) chunk, their exclusive offsets in tile order, one slot range per tile
+            unsigned km[kTilePer];
+#pragma unroll
+            for (int k = 0; k < kTilePer; ++k) {
+                const int j = k * kTileThreads + tid;
+                km[k] = __ballot_sync(0xffffffffu, j < cnt && S.st[j] == 1);
+                if (lane == 0) S.chunk_off[k * (kTileThreads / 32) + wid] = __popc(km[k]);
+            }
+            __syncthreads();
+            constexpr int nch = kTilePer * kTileThreads / 32;
+            if (wid == 0) {
+                int v = lane < nch ? S.chunk_off[lane] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (lane < nch) S.chunk_off[lane] = incl - v;
+                if (lane == 31) S.base = incl ? atomicAdd(d.counts + 2, incl) : 0;
+            }
+            __syncthreads();
+            const int sbase = S.base;
+#pragma unroll
+            for (int k = 0; k < kTilePer; ++k) {
+                const int j = k * kTileThreads + tid;
+                if (!((km[k] >> lane) & 1u)) continue;
+                // the ghost sources on the second stream take slots of the same buffer meanwhile
+                const int slot = sbase + S.chunk_off[k * (kTileThreads / 32) + wid] + __popc(km[k] & lt_mask);
+                if (slot >= cap) {
+                    atomicOr(d.err, ERR_CAPACITY);
+                } else {
+                    B.x[slot] = R.x[j]; B.y[slot] = R.y[j]; B.u[slot] = R.u[j]; B.v[slot] = R.v[j];
+                    B.w[slot] = R.w[j]; B.m[slot] = R.m[j];
+                    B.cell[slot] = R.cell[j];
+                    B.pid[slot] = R.pid[j];
+                }
+            }
+        }
+        // this thread's generic-proxy accesses of the stage come before the bulk copy that refills it (issued by
+        // thread 0 after the barrier at the top of the loop)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tile = nxt;
+        b ^= 1;
+    }
+    if (S.abort) {
+        // a tile's copies did not arrive in time: report it, and give the copies still in flight their own
+        // bounded wait before the CTA's shared memory is released
+        if (tid == 0) {
+            atomicOr(d.err, ERR_LIMIT);
+            for (int q = 0; q < 2; ++q)
+                if (pending & (1u << q)) (void)mbar_wait_bounded(&S.bar[q], parity[q]);
+        }
+        return;
     }
     for (int o = 16; o > 0; o >>= 1) {
         n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
@@ -1630,8 +1947,11 @@ template <typename P> cudaError_t dalloc(Ctx& ctx, P** p, size_t n)
     return cudaSuccess;
 }
 
+// 64 elements of slack past the capacity: the tile-staged transport kernel copies a tile's last records in
+// groups of four (16-byte bulk copies) and may read up to three elements past the particle count
 template <typename T> cudaError_t alloc_particles(Ctx& ctx, ParticleSoA<T>& P, size_t cap)
 {
+    cap += 64;
     cudaError_t e;
     if ((e = dalloc(ctx, &P.x, cap)) || (e = dalloc(ctx, &P.y, cap)) || (e = dalloc(ctx, &P.u, cap)) ||
         (e = dalloc(ctx, &P.v, cap)) || (e = dalloc(ctx, &P.w, cap)) || (e = dalloc(ctx, &P.m, cap)) ||
@@ -1655,6 +1975,9 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     auto mark = [&](int q, cudaStream_t st) {
         if (prof) cudaEventRecord(ev[q], st);
     };
+    // profiled steps run the second stream's work on the main stream, so that every stage's events time it
+    // alone (overlapped, each stage's events would also count the other stream's kernels sharing the SMs)
+    if (prof) s2 = s;
     mark(0, s);
     k_begin_step<<<nblk(2LL * K.F, 256), 256, 0, s>>>(K, d);
     if (K.shakhov) {
@@ -1688,7 +2011,9 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     else k_sample<double><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
     mark(3, s);
     mark(4, s);
-    if (K.prec == 0) k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
+    if (K.prec == 0 && ctx.transport == kTransportTiled)
+        k_particles_tiled<<<2 * ctx.sms, kTileThreads, sizeof(TileSmem), s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
+    else if (K.prec == 0) k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
     else k_particles<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64, d.cf64, pc64, d.dstep);
     mark(5, s);
     mark(8, s);
@@ -2116,6 +2441,9 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         ctx.grid_particles = sms * 4;
         ctx.sms = sms;
+        ctx.transport = K.prec == 0 ? kTransportTiled : kTransportWarp;
+        if (K.prec == 0)
+            CK(cudaFuncSetAttribute(k_particles_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem)));
         if (!K.wave_only) {
             if (K.prec == 0) { CK(alloc_particles(ctx, d.pa32, ctx.capacity)); CK(alloc_particles(ctx, d.pb32, ctx.capacity)); }
             else { CK(alloc_particles(ctx, d.pa64, ctx.capacity)); CK(alloc_particles(ctx, d.pb64, ctx.capacity)); }
@@ -2729,8 +3057,15 @@ extern "C" ugkwp_status ugkwp_get_field_noalloc(ugkwp_ctx* h, double* W, double*
 // interval change only the speed of a step: chunks and the sort reorder particles, and every result is an
 // integer sum or a per-particle / per-face quantity, so the state after a step is the same.
 namespace {
-ugkwp_status apply_launch(Ctx& ctx, int chunk, int bps, int sort_every)
+ugkwp_status apply_launch(Ctx& ctx, int chunk, int bps, int sort_every, int transport)
 {
+    if (transport) {
+        if (transport != kTransportWarp && transport != kTransportTiled)
+            return fail(ctx, UGKWP_EINVAL, "transport kernel: 1 (warp-chunked) or 2 (tile-staged)");
+        if (transport == kTransportTiled && ctx.k.prec != 0)
+            return fail(ctx, UGKWP_EINVAL, "the tile-staged transport kernel serves the production precision only");
+        ctx.transport = transport;
+    }
     if (chunk) {
         if (chunk < 32 || chunk > 8192 || chunk % 32) return fail(ctx, UGKWP_EINVAL, "chunk: a multiple of 32 in [32, 8192]");
         ctx.k.chunk = chunk;
@@ -2751,12 +3086,13 @@ ugkwp_status apply_launch(Ctx& ctx, int chunk, int bps, int sort_every)
 }
 }  // namespace
 
-extern "C" ugkwp_status ugkwp_set_launch(ugkwp_ctx* h, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every)
+extern "C" ugkwp_status ugkwp_set_launch(ugkwp_ctx* h, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every,
+                                        int32_t transport)
 {
     if (!h) return UGKWP_EINVAL;
     Ctx& ctx = h->c;
     CK(cudaStreamSynchronize(ctx.stream));
-    return apply_launch(ctx, chunk, blocks_per_sm, sort_every);
+    return apply_launch(ctx, chunk, blocks_per_sm, sort_every, transport);
 }
 
 extern "C" ugkwp_status ugkwp_get_launch(ugkwp_ctx* h, int32_t* out)
@@ -2766,6 +3102,7 @@ extern "C" ugkwp_status ugkwp_get_launch(ugkwp_ctx* h, int32_t* out)
     out[0] = ctx.k.chunk;
     out[1] = ctx.grid_particles / ctx.sms;
     out[2] = ctx.k.sort_every;
+    out[3] = ctx.transport;
     return UGKWP_OK;
 }
 
@@ -2778,39 +3115,47 @@ extern "C" ugkwp_status ugkwp_autotune(ugkwp_ctx* h, int32_t steps, int32_t* bes
         if (best_ms) *best_ms = 0.0;
         return UGKWP_OK;
     }
-    static const int chunks[] = {128, 256};
-    static const int bpss[] = {4, 6, 8};
-    static const int sorts[] = {8, 16, 32};
+    // candidates: the tile-staged kernel (production precision; its tile and 2 CTAs per SM are fixed) and the
+    // warp-chunked kernel with chunk {128, 256} x blocks per SM {4, 6, 8}, each with sort interval {8, 16, 32}
+    struct Cand { int chunk, bps, sort, transport; };
+    std::vector<Cand> cands;
+    for (int so : {8, 16, 32}) {
+        if (ctx.k.prec == 0) cands.push_back({0, 0, so, kTransportTiled});
+        for (int ch : {128, 256})
+            for (int bp : {4, 6, 8}) cands.push_back({ch, bp, so, kTransportWarp});
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double bms = 1e300;
-    int b[3] = {ctx.k.chunk, ctx.grid_particles / ctx.sms, ctx.k.sort_every};
+    int b[4] = {ctx.k.chunk, ctx.grid_particles / ctx.sms, ctx.k.sort_every, ctx.transport};
     ugkwp_status st = UGKWP_OK;
-    for (int ch : chunks)
-        for (int bp : bpss)
-            for (int so : sorts) {
-                if (st != UGKWP_OK) break;
-                CK(cudaStreamSynchronize(ctx.stream));
-                if ((st = apply_launch(ctx, ch, bp, so)) != UGKWP_OK) break;
-                // untimed steps (graph capture, then up to the next sort step), then whole sort periods
-                const int lead = (int)((so - 1 - ctx.step % so + so) % so) + 1;
-                if ((st = ugkwp_step(h, lead)) != UGKWP_OK) break;
-                const int n = ((steps + so - 1) / so) * so;
-                CK(cudaEventRecord(e0, ctx.stream));
-                if ((st = ugkwp_step(h, n)) != UGKWP_OK) break;
-                CK(cudaEventRecord(e1, ctx.stream));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.0f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms / n < bms) { bms = ms / n; b[0] = ch; b[1] = bp; b[2] = so; }
-            }
+    for (const Cand& cd : cands) {
+        if (st != UGKWP_OK) break;
+        CK(cudaStreamSynchronize(ctx.stream));
+        if ((st = apply_launch(ctx, cd.chunk, cd.bps, cd.sort, cd.transport)) != UGKWP_OK) break;
+        const int so = cd.sort;
+        // untimed steps (graph capture, then up to the next sort step), then whole sort periods
+        const int lead = (int)((so - 1 - ctx.step % so + so) % so) + 1;
+        if ((st = ugkwp_step(h, lead)) != UGKWP_OK) break;
+        const int n = ((steps + so - 1) / so) * so;
+        CK(cudaEventRecord(e0, ctx.stream));
+        if ((st = ugkwp_step(h, n)) != UGKWP_OK) break;
+        CK(cudaEventRecord(e1, ctx.stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / n < bms) {
+            bms = ms / n;
+            b[0] = ctx.k.chunk; b[1] = ctx.grid_particles / ctx.sms; b[2] = so; b[3] = cd.transport;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != UGKWP_OK) return st;
     if ((st = check_device_error(ctx)) != UGKWP_OK) return st;
-    if ((st = apply_launch(ctx, b[0], b[1], b[2])) != UGKWP_OK) return st;
-    if (best) { best[0] = b[0]; best[1] = b[1]; best[2] = b[2]; }
+    if ((st = apply_launch(ctx, b[0], b[1], b[2], b[3])) != UGKWP_OK) return st;
+    if (best) { best[0] = b[0]; best[1] = b[1]; best[2] = b[2]; best[3] = b[3]; }
     if (best_ms) *best_ms = bms;
     return UGKWP_OK;
 }

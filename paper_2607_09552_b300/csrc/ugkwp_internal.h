@@ -12,6 +12,7 @@ constexpr int kMaxIters = 256;   // face crossings + wall hits per particle per 
 constexpr int kMaxNew = 2047;    // new particles per cell per step (11-bit index inside the particle id)
 constexpr double kR = 0.5;       // gas constant in the reference units
 constexpr double kRhoFloor = 1e-12;   // vacuum floor of the cell density (units of rho_inf)
+constexpr int kTransportWarp = 1, kTransportTiled = 2;   // transport kernels (launch parameter)
 
 // device error word bits
 enum : int { ERR_LIMIT = 1, ERR_NONPHYS = 2, ERR_OVERFLOW = 4, ERR_CAPACITY = 8 };
@@ -110,6 +111,7 @@ struct Ctx {
     Dev d{};
     int ni = 0, nj = 0, periodic_j = 0, capacity = 0, res_blocks = 0, grid_particles = 0, sms = 148;
     int device = -1;                             // the device current at creation (owns every allocation)
+    int transport = 1;                           // transport kernel: kTransportWarp or kTransportTiled
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;              // wave fluxes, overlapped with the particle kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

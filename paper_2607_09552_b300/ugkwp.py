@@ -214,17 +214,21 @@ class Solver:
     def load_checkpoint(self, path: str):
         self._check(load().ugkwp_load(self.ctx, os.fsencode(path)))
 
-    def set_launch(self, chunk: int = 0, blocks_per_sm: int = 0, sort_every: int = 0):
-        self._check(load().ugkwp_set_launch(self.ctx, C.c_int32(chunk), C.c_int32(blocks_per_sm), C.c_int32(sort_every)))
+    def set_launch(self, chunk: int = 0, blocks_per_sm: int = 0, sort_every: int = 0, transport: int = 0):
+        """Transport kernel 1: warp-chunked, 2: tile-staged (production precision); 0 keeps a value."""
+        self._check(load().ugkwp_set_launch(self.ctx, C.c_int32(chunk), C.c_int32(blocks_per_sm), C.c_int32(sort_every),
+                                            C.c_int32(transport)))
 
     def launch(self):
-        out = (C.c_int32 * 3)()
+        """[chunk, blocks_per_sm, sort_every, transport kernel]"""
+        out = (C.c_int32 * 4)()
         self._check(load().ugkwp_get_launch(self.ctx, out))
         return list(out)
 
     def autotune(self, steps: int = 16):
-        """(best [chunk, blocks_per_sm, sort_every], ms per step) after timing the candidates on real steps."""
-        out = (C.c_int32 * 3)()
+        """(best [chunk, blocks_per_sm, sort_every, transport], ms per step) after timing the candidates on real
+        steps."""
+        out = (C.c_int32 * 4)()
         ms = C.c_double()
         self._check(load().ugkwp_autotune(self.ctx, C.c_int32(steps), out, C.byref(ms)))
         return list(out), ms.value

@@ -375,20 +375,27 @@ def test_batched_graph_equals_individual_runs(cuda_lib):
 
 
 def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
-    """Chunk size, blocks per SM and the sort interval reorder work and particles only: the state is the same
-    bit for bit (particles compared as sets), also across an autotuning pass that steps the run."""
+    """The transport kernel (tile-staged, the production default, against warp-chunked), chunk size, blocks per
+    SM and the sort interval reorder work and particles only: the state is the same bit for bit (particles
+    compared as sets), also across an autotuning pass that steps the run."""
     case = CASES["cylinder"]
     a = cuda_lib.Solver(case, precision=0, use_graph=True)
     b = cuda_lib.Solver(case, precision=0, use_graph=True)
-    assert b.launch() == [256, 4, 8]
-    b.set_launch(128, 2, 16)
-    assert b.launch() == [128, 2, 16]
+    assert a.launch() == [256, 4, 8, 2]
+    b.set_launch(128, 2, 16, 1)
+    assert b.launch() == [128, 2, 16, 1]
     a.step(21)
     b.step(21)
     assert np.array_equal(a.field()[0], b.field()[0])
     assert_particles_equal(a.particles(), b.particles())
+    ta, tb = a.tallies(), b.tallies()
+    for k in ("wm", "wpl", "wret", "cross", "wall"):
+        assert np.array_equal(ta[k], tb[k]), k
+    assert np.array_equal(a.stats()[:8], b.stats()[:8])
     best, ms = b.autotune(4)
-    assert best[0] in (128, 256) and best[1] in (4, 6, 8) and best[2] in (8, 16, 32) and ms > 0
+    assert best[3] in (1, 2) and best[2] in (8, 16, 32) and ms > 0
+    if best[3] == 1:
+        assert best[0] in (128, 256) and best[1] in (4, 6, 8)
     n = int(b.stats()[0]) - int(a.stats()[0])
     a.step(n)
     b.step(5)
@@ -400,3 +407,11 @@ def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
         assert np.array_equal(ta[k], tb[k])
     with pytest.raises(cuda_lib.UgkwpError):
         b.set_launch(100, 0, 0)
+    with pytest.raises(cuda_lib.UgkwpError):
+        b.set_launch(0, 0, 0, 3)
+    # the FP64 mode runs the warp-chunked kernel only
+    f = cuda_lib.Solver(case, precision=1, use_graph=False)
+    assert f.launch()[3] == 1
+    with pytest.raises(cuda_lib.UgkwpError):
+        f.set_launch(0, 0, 0, 2)
+    f.close()
