@@ -174,9 +174,19 @@ def run_ours(args):
     # the product's recommended mode: one captured graph per step, launch shape chosen by the autotuner
     # the dense-regime cylinder overshoots its steady particle count about 3x in the start-up transient
     cap = 8 * case.n_ref * case.mesh.ncells if args.case in ("kn001", "tri_kn001") else 0
+    if args.capacity:
+        cap = args.capacity
     solver = ugkwp.Solver(case, precision=0, seed=rank, stream=stream.cuda_stream, use_graph=True, order=args.order,
                           capacity=cap)
-    burn, burn_rule = burn_in(solver, args)
+    if args.load_state:
+        # a burned-in state saved by an earlier run of this workload (--save-state): the profiling runs start
+        # from it, so that the profiled process launches few kernels before the captured ones
+        solver.load_checkpoint(args.load_state)
+        burn, burn_rule = int(solver.stats()[0]), f"loaded from a checkpoint of a burned-in run ({args.load_state})"
+    else:
+        burn, burn_rule = burn_in(solver, args)
+        if args.save_state:
+            solver.save(args.save_state)
     launch, tune_ms = solver.autotune(16) if not args.no_autotune else (solver.launch(), None)
     stream.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -779,6 +789,9 @@ def main():
                     help="burn-in steps; -1: until the particle count changes by < 1%% over 1,000 steps")
     ap.add_argument("--burn-max", type=int, default=40000)
     ap.add_argument("--no-convergence", action="store_true")
+    ap.add_argument("--capacity", type=int, default=0, help="particle capacity (0: the workload's default)")
+    ap.add_argument("--save-state", default="", help="save the burned-in state (checkpoint) to this file")
+    ap.add_argument("--load-state", default="", help="start from a saved burned-in state instead of burning in")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -107,6 +107,18 @@ def face_flux(WL, WR, WhL, WhR, cL, cR, dL, dR, Pr=1.0):
     return outs
 
 
+def wall_flux(Tw, ws, WL, WhL, cL, frL):
+    """Wall-face flux in the face frame (normal from the fluid cell into the wall): incoming half of the cell's
+    g (weight cL[0]) and g^h (weight frL), outgoing wall part with specular fraction ws."""
+    a = np.ascontiguousarray(WL, dtype=np.float64)
+    h = None if WhL is None else np.ascontiguousarray(WhL, dtype=np.float64)
+    c = np.ascontiguousarray(cL, dtype=np.float64)
+    F = np.zeros(4)
+    lib().oracle_wall_flux_test(C.c_double(Tw), C.c_double(ws), dptr(a), None if h is None else dptr(h), dptr(c),
+                                C.c_double(frL), dptr(F))
+    return F
+
+
 class OracleError(RuntimeError):
     pass
 
@@ -242,6 +254,12 @@ class Oracle:
         out = np.zeros(8 * self.C)
         lib().oracle_get_cell_data(self.ctx, dptr(out))
         return out.reshape(self.C, 8)
+
+    def shakhov_weights(self):
+        """Pr != 1: per cell the acceptance-rejection weights (a_x, a_y, M) of the last step's sampling (C x 3)."""
+        out = np.zeros(3 * self.C)
+        self._check(lib().oracle_get_shakhov(self.ctx, dptr(out)))
+        return out.reshape(self.C, 3)
 
     def gradients(self):
         """Order 2: per cell the limited gradients (d/dx, d/dy) of the 4 components of W then of W^h, from the

@@ -90,6 +90,9 @@ int  oracle_get_tallies(oracle_ctx* cx, int64_t* wm, int64_t* wpl, int64_t* wret
                         int64_t* wall, int64_t* frec);
 int  oracle_get_cell_data(oracle_ctx* cx, double* out);            /* [8 per cell] see oracle_core.c */
 int  oracle_get_gradients(oracle_ctx* cx, double* out);             /* [16 per cell], order 2, see oracle_core.c */
+int  oracle_get_shakhov(oracle_ctx* cx, double* out);               /* [3 per cell]: a_x, a_y, M of the last step */
+void oracle_wall_flux_test(double Tw, double ws, const double* WL, const double* WhL, const double* cL, double frL,
+                           double* F);                               /* wall face flux, face frame (pins) */
 int  oracle_get_flux(oracle_ctx* cx, double* flux);                 /* [4 per face], global frame */
 int  oracle_get_geometry(oracle_ctx* cx, double* dt, double* vol, int32_t* nfaces, int32_t* nwall);
 int  oracle_fixed_exponents(oracle_ctx* cx, int32_t* out);          /* [3] mass, momentum, energy */

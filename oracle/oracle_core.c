@@ -362,6 +362,16 @@ static void wall_flux(const or_ctx* cx, const double WL[4], const double WhL[4],
     for (int k = 0; k < 4; ++k) F[k] = (F[k] + cx->ws * (sg[k] * F[k])) + a * (rw * o[k]);
 }
 
+/* exported for the quadrature pin of the wall flux (face frame: normal from the fluid cell into the wall) */
+void oracle_wall_flux_test(double Tw, double ws, const double* WL, const double* WhL, const double* cL, double frL,
+                           double* F)
+{
+    static or_ctx cx;   /* only Tw and ws are read */
+    cx.Tw = Tw;
+    cx.ws = ws;
+    wall_flux(&cx, WL, WhL, WhL != NULL, cL, frL, F);
+}
+
 static void to_frame(const double W[4], double nx, double ny, double out[4])
 {
     out[0] = W[0];
@@ -1491,6 +1501,13 @@ int oracle_get_cell_data(oracle_ctx* cx, double* out)
         o[0] = cx->tau[c]; o[1] = cx->xr_t[c]; o[2] = cx->emx[c]; o[3] = (double)cx->nhp[c];
         o[4] = cx->mnew[c]; o[5] = cx->samp[3 * c]; o[6] = cx->samp[3 * c + 1]; o[7] = cx->samp[3 * c + 2];
     }
+    return OR_OK;
+}
+
+int oracle_get_shakhov(oracle_ctx* cx, double* out)
+{
+    if (!cx || !out) return OR_EINVAL;
+    memcpy(out, cx->hq, 3 * (size_t)cx->C * 8);
     return OR_OK;
 }
 

@@ -314,3 +314,31 @@ def test_supersonic_uniform_flow_kept_by_the_ghost_sources(Kn):
     assert o.stats()[10] > 0                                  # particles entered from the ghosts
     np.testing.assert_allclose(A[:, 0], 1.0, atol=0.03)
     np.testing.assert_allclose(A[:, 1] / A[:, 0] / wl.freestream_speed(2.0), 1.0, atol=0.04)
+
+
+def test_vacuum_floor_resets_a_non_realizable_cell_and_counts_it():
+    """A cell whose updated state leaves the realizable set (here: a cell at ten times the temperature cap,
+    in pressure balance with its neighbours, whose energy outflow under the freestream's time step overshoots)
+    restarts from the floor state (1e-12, 0, 0, 1e-12 (3/2) R T_inf) and is counted; its neighbours, which
+    receive at most its energy content (equal to theirs: same pressure), stay physical."""
+    m = wl.line_mesh(20, 0.0, 1.0, bc_left=wl.BC_PERIODIC, bc_right=wl.BC_PERIODIC)
+    case = wl.Case("floor_box", m, Kn=0.05, Ma=0.0, Tw=1.0, cfl=0.5, n_ref=20)
+    T_cap = 10.0 * 1.0                                          # 10 max(1 + Ma^2 / 3, T_w, T_fix) at Ma = 0
+    prim = np.tile([1.0, 0.0, 0.0, 1.0], (20, 1))
+    prim[7] = [1.0 / (10.0 * T_cap), 0.0, 0.0, 10.0 * T_cap]
+    case.init_prim = prim
+    o = ob.Oracle(case, wave_only=True, precision=1)
+    o.step(1)
+    W, _ = o.field()
+    assert int(o.stats()[8]) == 1
+    np.testing.assert_array_equal(W[7], [1e-12, 0.0, 0.0, 1e-12 * 0.75])
+    others = np.delete(W, 7, axis=0)
+    rho, U = others[:, 0], others[:, 1] / others[:, 0]
+    T = (others[:, 3] / rho - 0.5 * U * U) / 0.75
+    assert np.all(rho > 0.5) and np.all(T > 0.5) and np.all(T < T_cap)
+    # a state at half the cap is kept (no reset, nothing counted)
+    prim[7] = [1.0 / (0.5 * T_cap), 0.0, 0.0, 0.5 * T_cap]
+    case.init_prim = prim
+    o = ob.Oracle(case, wave_only=True, precision=1)
+    o.step(1)
+    assert int(o.stats()[8]) == 0

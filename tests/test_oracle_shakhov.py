@@ -50,3 +50,35 @@ def test_shakhov_shock_runs_and_counts():
     assert st[2] > 0 and 0 <= st[9] <= st[2] // 10
     W = o.field()[0]
     assert np.all(np.isfinite(W)) and np.all(W[:, 0] > 0)
+
+
+def test_shakhov_weights_carry_the_heat_flux_of_the_retained_particles():
+    """The weights of each sampling cell against Eq. 5 evaluated directly: Q = (1 / (2 Omega_i)) sum m c |c|^2
+    over the particles retained in the cell at the start of the step, c = u - U_i with U_i the cell's (total)
+    velocity; a = (1 - Pr) Q / (5 rho_i (R T^h)^(3/2)), M = 1 + 6 * 31 |a| (reading of Sec. III B). The
+    oracle forms Q from fixed-point raw moments (sums of m, m u, m u u, m u |u|^2, ...) expanded about U_i."""
+    case = wl.case_shock1d(ni=40, n_ref=60)
+    o = ob.Oracle(case, precision=1)
+    o.step(30)
+    W0, _ = o.field()
+    P = o.particles()
+    _, vol = o.geometry()
+    o.step(1)
+    hq = o.shakhov_weights()
+    cd = o.cell_data()
+    rho = W0[:, 0]
+    U = W0[:, 1] / rho
+    c = P["cell"]
+    cu = P["u"] - U[c]
+    c2 = cu * cu + P["v"] ** 2 + P["w"] ** 2
+    Q = np.bincount(c, weights=P["m"] * cu * c2, minlength=o.C) / (2.0 * vol)
+    RTh = cd[:, 7]
+    sampled = cd[:, 3] > 0
+    assert sampled.sum() > 30
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ax = (1.0 - case.Pr) * Q / (5.0 * rho * RTh ** 1.5)
+    scale = np.abs(ax[sampled]).max()
+    assert scale > 1e-4                                           # a shock: heat flux present
+    np.testing.assert_allclose(hq[sampled, 0], ax[sampled], rtol=1e-8, atol=1e-10 * scale)
+    np.testing.assert_array_equal(hq[sampled, 1], 0.0)            # 1-D: no Q_y
+    np.testing.assert_allclose(hq[sampled, 2], 1.0 + 186.0 * np.abs(ax[sampled]), rtol=1e-8)

@@ -78,3 +78,69 @@ def test_gas_at_rest_at_wall_temperature_stays_in_equilibrium(geometry, ws):
     W0 = o.field()[0].copy()
     o.step(20)
     assert np.abs(o.field()[0] - W0).max() < 1e-14
+
+
+# ---- wall wave flux away from equilibrium, by quadrature of its definition --------------------------------
+# Reading of the wall face (Sec. IV B has both halves use the cell's own time step): molecules leaving the
+# fluid cell towards the wall (u_n > 0 in the face frame) carry the cell's g with the weight dbar_a and its
+# hydrodynamic wave g^h with the free-transport weight; the outgoing half holds the fraction ws of the
+# incoming distribution mirrored (u_n -> -u_n) plus 1 - ws of a wall Maxwellian at T_w whose density makes
+# that diffuse part carry exactly the rest of the incoming mass. Here every integral is taken by quadrature.
+
+def _maxwell(W):
+    rho, U, V = W[0], W[1] / W[0], W[2] / W[0]
+    RT = (W[3] / rho - 0.5 * (U * U + V * V)) * 2.0 / 3.0
+    return rho, U, V, RT
+
+
+def _half_moments(W, sign, mirror=False, n_u=400, n_v=40):
+    """int over u sign u > 0 (u the face-normal velocity; mirror: of the distribution reflected u -> -u),
+    v, w of Psi(u, v, w) u f_W(u, v, w): tensor Gauss-Legendre in u (on [0, 12 sigma] from the mean outward)
+    and Gauss-Hermite in v, w."""
+    rho, U, V, RT = _maxwell(W)
+    sig = np.sqrt(RT)
+    x, wx = np.polynomial.legendre.leggauss(n_u)
+    # integrate over the half line of the reflected or direct u
+    Uc = -U if mirror else U
+    lo, hi = (0.0, max(Uc, 0.0) + 14 * sig) if sign > 0 else (min(Uc, 0.0) - 14 * sig, 0.0)
+    u = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
+    wu = 0.5 * (hi - lo) * wx
+    gh, gw = np.polynomial.hermite.hermgauss(n_v)
+    v = V + np.sqrt(2 * RT) * gh
+    w = np.sqrt(2 * RT) * gh
+    wv = gw / np.sqrt(np.pi)
+    fu = rho * np.exp(-(u - Uc) ** 2 / (2 * RT)) / np.sqrt(2 * np.pi * RT) * wu
+    uu, vv, ww = np.meshgrid(u, v, w, indexing="ij")
+    wt = fu[:, None, None] * wv[None, :, None] * wv[None, None, :]
+    psi = np.array([np.ones_like(uu), uu, vv, 0.5 * (uu * uu + vv * vv + ww * ww)])
+    return (psi * uu * wt).sum(axis=(1, 2, 3))
+
+
+def _cons(rho, U, V, T):
+    return np.array([rho, rho * U, rho * V, rho * (0.5 * (U * U + V * V) + 0.75 * T)])
+
+
+@pytest.mark.parametrize("ws", [0.0, 0.15, 1.0])
+@pytest.mark.parametrize("WL,WhL", [
+    (_cons(1.3, 0.7, -0.4, 2.1), _cons(0.4, 1.1, 0.3, 1.6)),     # moving into the wall, non-equilibrium wave
+    (_cons(0.8, -0.5, 0.9, 0.7), _cons(0.2, -0.2, 0.6, 1.2)),    # moving away from the wall
+    (_cons(2.0, 0.0, 0.0, 3.0), None),                           # no free-transport wave
+])
+def test_wall_flux_matches_quadrature_of_its_definition(WL, WhL, ws):
+    Tw = 1.7
+    c = ob.coeffs(0.013, 0.004)
+    fr = c[3] - np.exp(-0.013 / 0.004)
+    F = ob.wall_flux(Tw, ws, WL, WhL, c, fr)
+    inc = c[0] * _half_moments(WL, +1)
+    if WhL is not None:
+        inc = inc + fr * _half_moments(WhL, +1)
+    # specular part: the incoming distributions mirrored onto u_n < 0
+    spec = c[0] * _half_moments(WL, -1, mirror=True)
+    if WhL is not None:
+        spec = spec + fr * _half_moments(WhL, -1, mirror=True)
+    wall = _half_moments(_cons(1.0, 0.0, 0.0, Tw), -1)
+    rho_w = -(1.0 - ws) * inc[0] / wall[0]
+    Fq = inc + ws * spec + rho_w * wall
+    scale = np.abs(inc).max()
+    np.testing.assert_allclose(F, Fq, rtol=0, atol=1e-11 * scale)
+    assert abs(F[0]) <= 1e-13 * scale                            # no net mass through the wall
