@@ -23,11 +23,11 @@
  *  - unstructured meshes (the paper's, Sec. V): convex cells, faces numbered by first appearance over the
  *    cells and their edges with the first cell as L, a triangle stored as the quadrilateral (v0, v1, v2, v2).
  *
- * Parity unpinned (no check independent of this file fixes these; the CUDA library is compared with them as
- * written): the wall wave flux away from equilibrium (wall_flux: only conservation and the rest equilibrium
- * at T_w are pinned), the ghost states and ghost particle sources beyond a supersonic uniform flow
- * (inject_params, inject), the vacuum floor (update), the Shakhov weights' heat-flux estimate
- * (shakhov_weights) and the limiter constant K = 5 (gradients).
+ * Pinned by checks independent of this file (tests/): the wall wave flux by velocity quadrature of its
+ * definition (wall_flux), the ghost particle sources by the half-range flux of the ghost Maxwellian
+ * (inject_params, inject), the vacuum floor's reset and count (update), the Shakhov weights by the heat flux
+ * of Eq. 5 evaluated directly (shakhov_weights). Parity unpinned (the CUDA library is compared with it as
+ * written): the limiter constant K = 5 (gradients), a choice the paper does not make.
  */
 #include "oracle_internal.h"
 #include <stdio.h>

@@ -342,3 +342,54 @@ def test_vacuum_floor_resets_a_non_realizable_cell_and_counts_it():
     o = ob.Oracle(case, wave_only=True, precision=1)
     o.step(1)
     assert int(o.stats()[8]) == 0
+
+
+@pytest.mark.parametrize("Kn,Ma", [(0.1, 2.0), (1.0, 0.6)])
+def test_ghost_sources_inject_the_collisionless_half_range_flux(Kn, Ma):
+    """Ghost particle sources (reading of the far-field boundary): per step, the particles that enter through
+    an inflow face carry e^{-x} dt_L s times the half-range flux of the ghost (freestream) Maxwellian into the
+    domain, x = dt_L / tau_inf. The flux is taken here by quadrature over velocity space; the particles that
+    entered are found by their ids (cell slot C + source index, this step); the sums over 600 steps agree with
+    it within 5 standard deviations of the per-particle sums."""
+    ni = 30
+    m = wl.line_mesh(ni, 0.0, 3.0, end_ratio=1.0, bc_left=wl.BC_FARFIELD, bc_right=wl.BC_FARFIELD)
+    case = wl.Case("ghost_line", m, Kn=Kn, Ma=Ma, Tw=1.0, cfl=0.5, n_ref=600)
+    o = ob.Oracle(case, precision=1)
+    dt, vol = o.geometry()
+    tau = 2.0 * ob.lib().oracle_mu_inf(Kn, case.omega)       # tau = mu / p at rho = T = 1, p = R = 1/2
+    U = wl.freestream_speed(Ma)
+    # half-range flux of the freestream Maxwellian (rho 1, U, RT = 1/2) through the left face, per unit time
+    RT = 0.5
+    x, wx = np.polynomial.legendre.leggauss(400)
+    hi = max(U, 0.0) + 14.0 * np.sqrt(RT)
+    u = 0.5 * hi * (x + 1.0)
+    wu = 0.5 * hi * wx * np.exp(-(u - U) ** 2 / (2 * RT)) / np.sqrt(2 * np.pi * RT)
+    gh, gw = np.polynomial.hermite.hermgauss(30)
+    vt = np.sqrt(2 * RT) * gh
+    wt = gw / np.sqrt(np.pi)
+    uu, vv, ww = np.meshgrid(u, vt, vt, indexing="ij")
+    wgt = wu[:, None, None] * wt[None, :, None] * wt[None, None, :]
+    psi = np.array([np.ones_like(uu), uu, vv, 0.5 * (uu ** 2 + vv ** 2 + ww ** 2)])
+    flux = (psi * uu * wgt).sum(axis=(1, 2, 3))
+    expected_per_step = np.exp(-dt[0] / tau) * dt[0] * 1.0 * flux
+    got = np.zeros(4)
+    var = np.zeros(4)
+    steps = 600
+    for _ in range(steps):
+        s = int(o.stats()[0])
+        o.step(1)
+        P = o.particles()
+        pid = P["pid"].astype(np.uint64)
+        slot = (pid >> np.uint64(11)) & np.uint64(0x1FFFFF)
+        born = (pid >> np.uint64(32)) == np.uint64(s)
+        sel = born & (slot == np.uint64(ni))                      # source 0: the left face
+        mm = P["m"][sel]
+        vals = np.array([mm, mm * P["u"][sel], mm * P["v"][sel],
+                         0.5 * mm * (P["u"][sel] ** 2 + P["v"][sel] ** 2 + P["w"][sel] ** 2)])
+        got += vals.sum(axis=1)
+        var += (vals ** 2).sum(axis=1)
+    exp_tot = steps * expected_per_step
+    sig = np.sqrt(var)
+    assert np.all(np.abs(got - exp_tot) <= 5.0 * sig), (got, exp_tot, sig)
+    # the statistics are tight enough to see a dropped e^{-x} or a half-range flux off by 5%
+    assert np.all(5.0 * sig[[0, 1, 3]] < 0.05 * np.abs(exp_tot[[0, 1, 3]]))
