@@ -235,11 +235,12 @@ static void pr_fix(const or_prim* p, double a[4], double Pr)
 
 /* Time-averaged wave flux through one face in the face frame (normal from L to R):
  * equilibrium part (Eq. 49) from g_0 and its slopes, plus the analytic free-transport part of the
- * hydrodynamic wave (Eq. 50, first order so only its dbar_d - e^{-x} term). cL/cR are the 7 normalised
- * coefficients of each side; frL/frR the coefficient used for each side's g^h (x chi, or the full dbar_d
- * on a ghost side or without particles). Returns W_0 and the slopes for the pins. */
+ * hydrodynamic wave (Eq. 50). cL/cR are the 7 normalised coefficients of each side; frL/frR the weight of
+ * each side's sampled-from part of g^h (dbar_d - e^{-x}, or the full dbar_d where no particles were sampled
+ * or without particles), fdL/fdR the weight of its never-sampled remainder (dbar_d). Returns W_0 and the
+ * slopes for the pins. */
 static void face_flux(const double WL[4], const double WR[4], const double WhL[4], const double WhR[4],
-                      int hL, int hR, const double cL[7], const double cR[7], double frL, double frR,
+                      double fdL, double fdR, const double cL[7], const double cR[7], double frL, double frR,
                       double dL, double dR, double Pr, const double WLc[4], const double WRc[4],
                       const double dhL[4], const double dhR[4], double csL, double csR, double F[4],
                       double W0o[4], double aLo[4], double aRo[4], double Ao[4])
@@ -248,8 +249,8 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
      * normal slopes of g_0 are taken against (S7), NULL for WL, WR */
     if (!WLc) WLc = WL;
     if (!WRc) WRc = WR;
-    or_prim pL, pR, p0, phL, phR;
-    or_mom mL, mR, m0, mhL, mhR;
+    or_prim pL, pR, p0;
+    or_mom mL, mR, m0;
     frame_prim(WL, &pL);
     frame_prim(WR, &pR);
     moments(&pL, &mL);
@@ -293,31 +294,44 @@ static void face_flux(const double WL[4], const double WR[4], const double WhL[4
     if (aRo) for (int k = 0; k < 4; ++k) aRo[k] = aR[k];
     if (Ao) for (int k = 0; k < 4; ++k) Ao[k] = A[k];
 free_transport:
-    /* free transport of the hydrodynamic wave (Eq. 50): g^h of each side over its half, and with a
-     * second-order reconstruction (Eq. 12) its normal slope term weighted with csL / csR (dhL, dhR: normal
-     * derivatives of W^h in the face frame, NULL for none) */
-    if (hL && frame_prim(WhL, &phL)) {
-        moments(&phL, &mhL);
-        psi_mom(mhL.up, &mhL, 1, 0, 0, t1);
-        for (int k = 0; k < 4; ++k) F[k] += frL * phL.rho * t1[k];
-        if (dhL) {
-            double dw[4], a[4];
-            for (int k = 0; k < 4; ++k) dw[k] = dhL[k] / phL.rho;
-            micro_slope(&phL, dw, a);
-            psi_poly_mom(mhL.up, &mhL, 2, 0, a, t1);
-            for (int k = 0; k < 4; ++k) F[k] += csL * phL.rho * t1[k];
+    /* free transport of the hydrodynamic wave (Eq. 50), reading of Sec. III B: the wave W^h of a side is the
+     * local (equilibrium) distribution of the side's total state, carrying the hydrodynamic density rho^h,
+     * plus the remainder dW = W^h - (rho^h / rho) W, which has no mass, represented to first order about the
+     * same Maxwellian, g (a . psi) with <psi g (a . psi)> = dW (Eq. 20 form). The first part is what the new
+     * particles are sampled from (e^{-x} of it, Eq. 26), so its free-transport weight is frL / frR (dbar_d -
+     * e^{-x} when particles were sampled, else dbar_d); the remainder is never sampled and keeps the whole
+     * dbar_d (fdL / fdR). Both parts are linear in W^h, so particle noise in W^h = W - W^p leaves no bias.
+     * Order 2 (Eq. 12): the normal slope term of W^h (dhL, dhR, NULL for none) about the same Maxwellian,
+     * weighted with csL / csR. */
+    {
+        double dw[4], a[4];
+        psi_mom(mL.up, &mL, 1, 0, 0, t1);
+        for (int k = 0; k < 4; ++k) {
+            F[k] += frL * WhL[0] * t1[k];
+            dw[k] = (WhL[k] - (WhL[0] / pL.rho) * WL[k]) / pL.rho;
         }
-    }
-    if (hR && frame_prim(WhR, &phR)) {
-        moments(&phR, &mhR);
-        psi_mom(mhR.um, &mhR, 1, 0, 0, t2);
-        for (int k = 0; k < 4; ++k) F[k] += frR * phR.rho * t2[k];
+        micro_slope(&pL, dw, a);
+        psi_poly_mom(mL.up, &mL, 1, 0, a, t1);
+        for (int k = 0; k < 4; ++k) F[k] += fdL * pL.rho * t1[k];
+        if (dhL) {
+            for (int k = 0; k < 4; ++k) dw[k] = dhL[k] / pL.rho;
+            micro_slope(&pL, dw, a);
+            psi_poly_mom(mL.up, &mL, 2, 0, a, t1);
+            for (int k = 0; k < 4; ++k) F[k] += csL * pL.rho * t1[k];
+        }
+        psi_mom(mR.um, &mR, 1, 0, 0, t2);
+        for (int k = 0; k < 4; ++k) {
+            F[k] += frR * WhR[0] * t2[k];
+            dw[k] = (WhR[k] - (WhR[0] / pR.rho) * WR[k]) / pR.rho;
+        }
+        micro_slope(&pR, dw, a);
+        psi_poly_mom(mR.um, &mR, 1, 0, a, t2);
+        for (int k = 0; k < 4; ++k) F[k] += fdR * pR.rho * t2[k];
         if (dhR) {
-            double dw[4], a[4];
-            for (int k = 0; k < 4; ++k) dw[k] = dhR[k] / phR.rho;
-            micro_slope(&phR, dw, a);
-            psi_poly_mom(mhR.um, &mhR, 2, 0, a, t2);
-            for (int k = 0; k < 4; ++k) F[k] += csR * phR.rho * t2[k];
+            for (int k = 0; k < 4; ++k) dw[k] = dhR[k] / pR.rho;
+            micro_slope(&pR, dw, a);
+            psi_poly_mom(mR.um, &mR, 2, 0, a, t2);
+            for (int k = 0; k < 4; ++k) F[k] += csR * pR.rho * t2[k];
         }
     }
 }
@@ -326,27 +340,30 @@ void oracle_face_flux_test(const double* WL, const double* WR, const double* WhL
                            const double* cL, const double* cR, double dL, double dR, double Pr,
                            double* F, double* W0, double* aL, double* aR, double* A)
 {
-    face_flux(WL, WR, WhL, WhR, WhL != NULL, WhR != NULL, cL, cR, cL[5], cR[5], dL, dR, Pr, NULL, NULL, NULL, NULL,
-              0.0, 0.0, F, W0, aL, aR, A);
+    face_flux(WL, WR, WhL ? WhL : WL, WhR ? WhR : WR, WhL ? cL[3] : 0.0, WhR ? cR[3] : 0.0, cL, cR,
+              WhL ? cL[5] : 0.0, WhR ? cR[5] : 0.0, dL, dR, Pr, NULL, NULL, NULL, NULL, 0.0, 0.0, F, W0, aL, aR, A);
 }
 
-/* diffuse isothermal wall (reading): incoming half of the fluid cell's g and g^h, outgoing wall
- * Maxwellian at T_w with the density that makes the wave mass flux zero */
-static void wall_flux(const or_ctx* cx, const double WL[4], const double WhL[4], int hL, const double cL[7],
+/* diffuse isothermal wall (reading): incoming half of the fluid cell's g and its hydrodynamic wave (as in
+ * face_flux: rho^h times the cell's local distribution with weight frL, the massless remainder with fdL),
+ * outgoing wall Maxwellian at T_w with the density that makes the wave mass flux zero */
+static void wall_flux(const or_ctx* cx, const double WL[4], const double WhL[4], double fdL, const double cL[7],
                       double frL, double F[4])
 {
-    or_prim pL, ph, pw;
-    or_mom mL, mh, mw;
-    double t[4], o[4];
+    or_prim pL, pw;
+    or_mom mL, mw;
+    double t[4], o[4], dw[4], sl[4];
     frame_prim(WL, &pL);
     moments(&pL, &mL);
     psi_mom(mL.up, &mL, 1, 0, 0, t);
-    for (int k = 0; k < 4; ++k) F[k] = cL[0] * pL.rho * t[k];
-    if (hL && frame_prim(WhL, &ph)) {
-        moments(&ph, &mh);
-        psi_mom(mh.up, &mh, 1, 0, 0, t);
-        for (int k = 0; k < 4; ++k) F[k] += frL * ph.rho * t[k];
+    for (int k = 0; k < 4; ++k) {
+        F[k] = cL[0] * pL.rho * t[k];
+        F[k] += frL * WhL[0] * t[k];
+        dw[k] = (WhL[k] - (WhL[0] / pL.rho) * WL[k]) / pL.rho;
     }
+    micro_slope(&pL, dw, sl);
+    psi_poly_mom(mL.up, &mL, 1, 0, sl, t);
+    for (int k = 0; k < 4; ++k) F[k] += fdL * pL.rho * t[k];
     pw.rho = 1.0; pw.U = 0.0; pw.V = 0.0; pw.lam = 0.5 / (OR_R * cx->Tw);
     moments(&pw, &mw);
     psi_mom(mw.um, &mw, 1, 0, 0, o);
@@ -369,7 +386,7 @@ void oracle_wall_flux_test(double Tw, double ws, const double* WL, const double*
     static or_ctx cx;   /* only Tw and ws are read */
     cx.Tw = Tw;
     cx.ws = ws;
-    wall_flux(&cx, WL, WhL, WhL != NULL, cL, frL, F);
+    wall_flux(&cx, WL, WhL ? WhL : WL, WhL ? cL[3] : 0.0, cL, WhL ? frL : 0.0, F);
 }
 
 static void to_frame(const double W[4], double nx, double ny, double out[4])
@@ -850,7 +867,7 @@ static int finish_create(or_ctx* cx, const oracle_gas* gas, double Kn, double Ma
     cx->Wp = zalloc(4 * C, 8); cx->Wh = zalloc(4 * C, 8); cx->mnew = zalloc(C, 8); cx->co = zalloc(7 * C, 8);
     cx->samp = zalloc(3 * C, 8); cx->grad = zalloc(16 * (size_t)C, 8);
     cx->whq = zalloc(9 * C, 8); cx->hq = zalloc(3 * C, 8);
-    cx->nhp = zalloc(C, 4); cx->hphys = zalloc(C, 4); cx->nhp_off = zalloc(C + 1, 8);
+    cx->nhp = zalloc(C, 4); cx->nhp_off = zalloc(C + 1, 8);
     cx->wm = zalloc(5 * C, 8); cx->wpl = zalloc(5 * C, 8); cx->wrt = zalloc(5 * C, 8);
     cx->cross = zalloc(2 * F, 8); cx->wallt = zalloc(3 * cx->nwall, 8); cx->frec = zalloc(4 * F, 8);
     cx->flux = zalloc(4 * F, 8);
@@ -871,7 +888,7 @@ void oracle_destroy(oracle_ctx* cx)
                     cx->cbc, cx->cnx, cx->cny, cx->cd, cx->cshift, cx->cvx, cx->cvy, cx->xl, cx->xr, cx->fL,
                     cx->fR, cx->fbc, cx->fwall, cx->fnx, cx->fny, cx->fs, cx->fdL, cx->fdR, cx->finv_s,
                     cx->wall_face, cx->dt, cx->ratio, cx->W, cx->wret_prev, cx->tau, cx->xr_t, cx->emx, cx->Wp,
-                    cx->Wh, cx->mnew, cx->co, cx->samp, cx->grad, cx->nhp, cx->hphys, cx->nhp_off, cx->wm, cx->wpl,
+                    cx->Wh, cx->mnew, cx->co, cx->samp, cx->grad, cx->nhp, cx->nhp_off, cx->wm, cx->wpl,
                     cx->wrt, cx->cross, cx->wallt, cx->frec, cx->flux, cx->chi_ema, cx->surf_sum,
                     cx->surf_last, cx->p, cx->whq, cx->hq, cx->fax, cx->fay, cx->fex, cx->fey,
                     cx->inj_face, cx->inj_k, cx->inj_n, cx->inj_m, cx->inj_u, cx->inj_v, cx->inj_sig,
@@ -898,11 +915,11 @@ static int realizable(const or_ctx* cx, const double W[4])
 /* ------------------------------------------------------------------ a1: decomposition (Sec. IV B) */
 
 /* Shakhov acceptance-rejection weights of cell c (Eqs. 4-5; reading): the heat flux Q_i of the particles
- * retained in the cell at the start of the step, about the cell velocity U_i, from their raw moments; the
- * sampled wave part takes its mass share rho^h / rho_i of the correction: accept a proposal c = sqrt(RT^h) z
- * from the Maxwellian of W^h with probability (1 + psi) / M, psi = (a . z) (|z|^2 - 5),
- * a = (1 - Pr) Q_i / (5 rho_i (RT^h)^(3/2)), M = 1 + 6 * 31 |a| (|z| <= 6 enforced by rejection). W has no
- * z-momentum, so Q_z = 0; in 1-D also Q_y = 0. */
+ * retained in the cell at the start of the step, about the cell velocity U_i, from their raw moments: the
+ * new particles follow the cell's g^S (Eq. 4 at U_i, T_i, Q_i): accept a proposal c = sqrt(RT_i) z from the
+ * Maxwellian with probability (1 + psi) / M, psi = (a . z) (|z|^2 - 5), a = (1 - Pr) Q_i / (5 rho_i
+ * (RT_i)^(3/2)), M = 1 + 6 * 31 |a| (|z| <= 6 enforced by rejection). W has no z-momentum, so Q_z = 0; in
+ * 1-D also Q_y = 0. */
 static void shakhov_weights(or_ctx* cx, int c)
 {
     const int64_t* h = cx->whq + 9 * c;
@@ -920,8 +937,8 @@ static void shakhov_weights(or_ctx* cx, int c)
     const double cy3 = ((((Svq - 2.0 * (U * Suv + V * Svv)) + UU * Sv) - V * Sq) + 2.0 * V * Ud) - V * UU * Sm;
     const double Qx = cx3 / (2.0 * cx->vol[c]);
     const double Qy = cx->dim == 1 ? 0.0 : cy3 / (2.0 * cx->vol[c]);
-    const double RTh = cx->samp[3 * c + 2];
-    const double den = 5.0 * W[0] * (RTh * sqrt(RTh));
+    const double RTi = cx->samp[3 * c + 2];
+    const double den = 5.0 * W[0] * (RTi * sqrt(RTi));
     const double ax = ((1.0 - cx->Pr) * Qx) / den, ay = ((1.0 - cx->Pr) * Qy) / den;
     cx->hq[3 * c] = ax;
     cx->hq[3 * c + 1] = ay;
@@ -969,28 +986,27 @@ static void decompose(or_ctx* cx)
         cx->xr_t[c] = x;
         cx->emx[c] = e;
         lts_coeffs(cx->dt[c], tau, e, cx->co + 7 * c);
-        cx->hphys[c] = realizable(cx, Wh);
         cx->nhp[c] = 0;
         cx->mnew[c] = 0.0;
         cx->samp[3 * c] = cx->samp[3 * c + 1] = cx->samp[3 * c + 2] = 0.0;
-        if (!cx->wave_only && cx->hphys[c]) {
-            /* W^hp = W^h e^{-dt_i / tau_i}; N^hp = ceil(rho^hp / rho N_ref); m = rho^hp Omega / N^hp (Eq. 26) */
-            const double rho_hp = Wh[0] * e;
-            if (rho_hp > 0.0) {
-                const double q = ceil((rho_hp / W[0]) * (double)cx->n_ref);
-                if (q > (double)OR_MAX_NEW) {
-                    or_set_error(cx, OR_ELIMIT, "more than 2047 new particles in one cell");
-                    continue;
-                }
-                cx->nhp[c] = (int)q;
-                cx->mnew[c] = (rho_hp * cx->vol[c]) / q;
-                const double rh = 1.0 / Wh[0], Uh = Wh[1] * rh, Vh = Wh[2] * rh;
-                const double RTh = (Wh[3] * rh - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
-                cx->samp[3 * c] = Uh;
-                cx->samp[3 * c + 1] = Vh;
-                cx->samp[3 * c + 2] = RTh;
-                if (shakhov) shakhov_weights(cx, c);
+        /* W^hp = W^h e^{-dt_i / tau_i}; for rho^hp > 0: N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp
+         * (Eqs. 25-26). Reading of Sec. III B: the new particles' velocities follow the local distribution of
+         * the cell, at the cell velocity U_i and temperature T_i (not those of W^h, which is a small difference
+         * of noisy tallies where particles dominate); the rest of W^h is transported by the wave (face_flux) */
+        const double rho_hp = Wh[0] * e;
+        if (!cx->wave_only && rho_hp > 0.0) {
+            const double q = ceil((rho_hp / W[0]) * (double)cx->n_ref);
+            if (q > (double)OR_MAX_NEW) {
+                or_set_error(cx, OR_ELIMIT, "more than 2047 new particles in one cell");
+                continue;
             }
+            cx->nhp[c] = (int)q;
+            cx->mnew[c] = (rho_hp * cx->vol[c]) / q;
+            const double rw = 1.0 / W[0], Ui = W[1] * rw, Vi = cx->dim == 1 ? 0.0 : W[2] * rw;
+            cx->samp[3 * c] = Ui;
+            cx->samp[3 * c + 1] = Vi;
+            cx->samp[3 * c + 2] = (W[3] * rw - 0.5 * (Ui * Ui + Vi * Vi)) * (2.0 / 3.0);
+            if (shakhov) shakhov_weights(cx, c);
         }
     }
 }
@@ -1122,8 +1138,8 @@ static void gradients(or_ctx* cx)
 
 /* Order 2: the state of cell c's W (which = 0) or W^h (which = 1) at face f (its local face k), W_c + grad .
  * (x_f - x_c) with x_f the face point (1-D) or midpoint (2-D), and the normal derivative n . grad, both in
- * the face frame (n, t). Returns 0 (first order for this side) when the reconstructed state is not a
- * positive density and internal energy. */
+ * the face frame (n, t). Returns 0 when the reconstructed state is not a positive density and internal
+ * energy (for W: that side stays first order). */
 static int face_side(const or_ctx* cx, int c, int k, int f, int which, double Wf[4], double dn[4])
 {
     const double* g = cx->grad + 16 * (size_t)c + 8 * which;
@@ -1141,10 +1157,9 @@ static int face_side(const or_ctx* cx, int c, int k, int f, int which, double Wf
         W[q] = Wc[q] + (g[2 * q] * ddx + g[2 * q + 1] * ddy);
         d[q] = g[2 * q] * cx->fnx[f] + g[2 * q + 1] * cx->fny[f];
     }
-    if (!(W[0] > 0.0) || !(W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0] > 0.0)) return 0;
     to_frame(W, cx->fnx[f], cx->fny[f], Wf);
     to_frame(d, cx->fnx[f], cx->fny[f], dn);
-    return 1;
+    return W[0] > 0.0 && W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0] > 0.0;
 }
 
 static int local_face(const or_ctx* cx, int c, int f)
@@ -1163,7 +1178,8 @@ static void wave_fluxes(or_ctx* cx)
         to_frame(cx->W + 4 * L, nx, ny, WL);
         to_frame(cx->Wh + 4 * L, nx, ny, WhL);
         const double* cL = cx->co + 7 * L;
-        const double frL = cx->wave_only ? cL[3] : cL[5];
+        /* the sampled-from part of g^h keeps dbar_d - e^{-x} where this step's particles carry e^{-x} of it */
+        const double frL = (cx->wave_only || cx->nhp[L] == 0) ? cL[3] : cL[5];
         /* order 2 (S6): reconstructed face states of W (equilibrium part) and W^h (free-transport wave, with
          * its normal slope term weighted with dbar_e, or dbar_e + dt e^{-x} / 2 when the collisionless part is
          * carried by particles, Eq. 50) on interior, periodic and far-field / fixed faces */
@@ -1173,11 +1189,14 @@ static void wave_fluxes(or_ctx* cx)
         for (int q = 0; q < 4; ++q) WLc[q] = WL[q];
         const double csL = cx->wave_only ? cL[4] : cL[6];
         if (o2) {
+            /* W and W^h are reconstructed together (the remainder of W^h is taken against W at the same
+             * point); a side whose reconstructed W is not a positive density and internal energy stays first
+             * order */
             const int kL = local_face(cx, L, f);
-            double Wf[4];
-            if (face_side(cx, L, kL, f, 0, Wf, dtmp)) for (int q = 0; q < 4; ++q) WL[q] = Wf[q];
-            if (cx->hphys[L] && face_side(cx, L, kL, f, 1, Wf, dhL)) {
-                for (int q = 0; q < 4; ++q) WhL[q] = Wf[q];
+            double Wf[4], Whf[4];
+            if (face_side(cx, L, kL, f, 0, Wf, dtmp)) {
+                face_side(cx, L, kL, f, 1, Whf, dhL);
+                for (int q = 0; q < 4; ++q) { WL[q] = Wf[q]; WhL[q] = Whf[q]; }
                 sL = 1;
             }
         }
@@ -1186,25 +1205,25 @@ static void wave_fluxes(or_ctx* cx)
             to_frame(cx->Wh + 4 * R, nx, ny, WhR);
             for (int q = 0; q < 4; ++q) WRc[q] = WR[q];
             const double* cR = cx->co + 7 * R;
-            const double frR = cx->wave_only ? cR[3] : cR[5];
+            const double frR = (cx->wave_only || cx->nhp[R] == 0) ? cR[3] : cR[5];
             if (o2) {
                 const int kR = local_face(cx, R, f);
-                double Wf[4];
-                if (face_side(cx, R, kR, f, 0, Wf, dtmp)) for (int q = 0; q < 4; ++q) WR[q] = Wf[q];
-                if (cx->hphys[R] && face_side(cx, R, kR, f, 1, Wf, dhR)) {
-                    for (int q = 0; q < 4; ++q) WhR[q] = Wf[q];
+                double Wf[4], Whf[4];
+                if (face_side(cx, R, kR, f, 0, Wf, dtmp)) {
+                    face_side(cx, R, kR, f, 1, Whf, dhR);
+                    for (int q = 0; q < 4; ++q) { WR[q] = Wf[q]; WhR[q] = Whf[q]; }
                     sR = 1;
                 }
             }
-            face_flux(WL, WR, WhL, WhR, cx->hphys[L], cx->hphys[R], cL, cR, frL, frR, cx->fdL[f], cx->fdR[f],
+            face_flux(WL, WR, WhL, WhR, cL[3], cR[3], cL, cR, frL, frR, cx->fdL[f], cx->fdR[f],
                       cx->Pr, WLc, WRc, sL ? dhL : NULL, sR ? dhR : NULL, csL, cx->wave_only ? cR[4] : cR[6], F,
                       NULL, NULL, NULL, NULL);
         } else if (bc == OR_BC_WALL) {
-            wall_flux(cx, WL, WhL, cx->hphys[L], cL, frL, F);
+            wall_flux(cx, WL, WhL, cL[3], cL, frL, F);
         } else if (bc == OR_BC_SYMMETRY) {
             /* mirror ghost: same state with the normal velocity reversed, same coefficients */
             double Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
-            face_flux(WL, Wm, WhL, Whm, cx->hphys[L], cx->hphys[L], cL, cL, frL, frL, cx->fdL[f], cx->fdL[f],
+            face_flux(WL, Wm, WhL, Whm, cL[3], cL[3], cL, cL, frL, frL, cx->fdL[f], cx->fdL[f],
                       cx->Pr, NULL, NULL, NULL, NULL, 0.0, 0.0, F, NULL, NULL, NULL, NULL);
         } else {
             /* far-field / fixed ghost: a virtual cell of the ghost state with the fluid cell's time step
@@ -1216,7 +1235,7 @@ static void wave_fluxes(or_ctx* cx)
             to_frame(Wg, nx, ny, WR);
             double cR[7];
             lts_coeffs(cx->dt[L], tau_of(cx, Wg), or_expd(-cx->dt[L] / tau_of(cx, Wg)), cR);
-            face_flux(WL, WR, WhL, WR, cx->hphys[L], 1, cL, cR, frL, cx->wave_only ? cR[3] : cR[5], cx->fdL[f],
+            face_flux(WL, WR, WhL, WR, cL[3], cR[3], cL, cR, frL, cx->wave_only ? cR[3] : cR[5], cx->fdL[f],
                       cx->fdL[f], cx->Pr, WLc, NULL, sL ? dhL : NULL, NULL, csL, 0.0, F, NULL, NULL, NULL, NULL);
         }
         /* non-finite flux (reading): extreme near-vacuum neighbours can make the interface density underflow

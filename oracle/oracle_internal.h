@@ -63,14 +63,14 @@ struct oracle_ctx {
     int64_t *wret_prev;                          /* [5C] retained tally of the previous step */
     /* per-step cell data */
     double *tau, *xr_t, *emx, *Wp, *Wh, *mnew, *co;   /* co: [7C] normalised coefficients */
-    double* samp;                                /* [3C] U^h, V^h, R T^h for sampling */
+    double* samp;                                /* [3C] U_i, V_i, R T_i of the sampling (cell state) */
     double* grad;                                /* [16C] order 2: limited gradients (d/dx, d/dy) of the 4
                                                   * components of W, then of W^h (S6) */
     int64_t* whq;                                /* [9C] retained particles: m (1, u, v, uu, uv, vv, q, uq, vq),
                                                   * q = |u|^2, fixed point (Pr != 1) */
     double* hq;                                  /* [3C] A-R weights a_x, a_y and bound M (Pr != 1) */
     double m2RTw, sig_w;                         /* -2 R T_w and sqrt(R T_w) */
-    int *nhp, *hphys;
+    int *nhp;
     int64_t *nhp_off;
     /* tallies */
     int64_t *wm, *wpl, *wrt, *cross, *wallt;

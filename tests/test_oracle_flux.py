@@ -105,8 +105,15 @@ def test_face_flux_against_quadrature(WL, WR, Pr):
     for side, c, a in ((+1, cL, aL), (-1, cR, aR)):
         Fq += vec_integral(W0, lambda u, v, w: psi(u, v, w) * u * (c[0] + c[1] * u * poly(a, u, v, w)
                                                                    + c[2] * poly(A, u, v, w)), side)
-    Fq += cL[5] * vec_integral(WhL, lambda u, v, w: psi(u, v, w) * u, +1)
-    Fq += cR[5] * vec_integral(WhR, lambda u, v, w: psi(u, v, w) * u, -1)
+    # Eq. 50 with the hydrodynamic wave of a side as rho^h times the side's local Maxwellian (weight
+    # dbar_d - e^{-x}) plus the massless remainder W^h - (rho^h / rho) W as g (a . psi) about the same
+    # Maxwellian (weight dbar_d); a from the moment system taken by quadrature
+    for side, W, Wh, c in ((+1, WL, WhL, cL), (-1, WR, WhR, cR)):
+        Fq += c[5] * (Wh[0] / W[0]) * vec_integral(W, lambda u, v, w: psi(u, v, w) * u, side)
+        G = np.stack([vec_integral(W, lambda u, v, w, k=k: psi(u, v, w) * psi(u, v, w)[k], 0) for k in range(4)],
+                     axis=1)
+        a = np.linalg.solve(G, Wh - (Wh[0] / W[0]) * W)
+        Fq += c[3] * vec_integral(W, lambda u, v, w: psi(u, v, w) * u * poly(a, u, v, w), side)
     np.testing.assert_allclose(F, Fq, rtol=1e-9, atol=1e-9 * np.abs(Fq).max())
 
 

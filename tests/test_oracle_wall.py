@@ -83,9 +83,12 @@ def test_gas_at_rest_at_wall_temperature_stays_in_equilibrium(geometry, ws):
 # ---- wall wave flux away from equilibrium, by quadrature of its definition --------------------------------
 # Reading of the wall face (Sec. IV B has both halves use the cell's own time step): molecules leaving the
 # fluid cell towards the wall (u_n > 0 in the face frame) carry the cell's g with the weight dbar_a and its
-# hydrodynamic wave g^h with the free-transport weight; the outgoing half holds the fraction ws of the
-# incoming distribution mirrored (u_n -> -u_n) plus 1 - ws of a wall Maxwellian at T_w whose density makes
-# that diffuse part carry exactly the rest of the incoming mass. Here every integral is taken by quadrature.
+# hydrodynamic wave: rho^h times the cell's local Maxwellian with the weight of the part the new particles are
+# sampled from, plus the massless remainder W^h - (rho^h / rho) W as g (a . psi) about the same Maxwellian with
+# the weight dbar_d; the outgoing half holds the fraction ws of the incoming distribution mirrored
+# (u_n -> -u_n) plus 1 - ws of a wall Maxwellian at T_w whose density makes that diffuse part carry exactly the
+# rest of the incoming mass. Here every integral is taken by quadrature, the remainder's a from its moment
+# system by quadrature too.
 
 def _maxwell(W):
     rho, U, V = W[0], W[1] / W[0], W[2] / W[0]
@@ -93,16 +96,21 @@ def _maxwell(W):
     return rho, U, V, RT
 
 
-def _half_moments(W, sign, mirror=False, n_u=400, n_v=40):
+def _half_moments(W, sign, mirror=False, n_u=400, n_v=40, poly=None):
     """int over u sign u > 0 (u the face-normal velocity; mirror: of the distribution reflected u -> -u),
-    v, w of Psi(u, v, w) u f_W(u, v, w): tensor Gauss-Legendre in u (on [0, 12 sigma] from the mean outward)
-    and Gauss-Hermite in v, w."""
+    v, w of Psi(u, v, w) u f(u, v, w), f the Maxwellian of W times (a . psi) when poly = a is given (the
+    polynomial taken at the unreflected velocity): tensor Gauss-Legendre in u (on [0, 14 sigma] from the mean
+    outward) and Gauss-Hermite in v, w. sign = 0: the whole line, without the factor u."""
     rho, U, V, RT = _maxwell(W)
     sig = np.sqrt(RT)
     x, wx = np.polynomial.legendre.leggauss(n_u)
-    # integrate over the half line of the reflected or direct u
     Uc = -U if mirror else U
-    lo, hi = (0.0, max(Uc, 0.0) + 14 * sig) if sign > 0 else (min(Uc, 0.0) - 14 * sig, 0.0)
+    if sign > 0:
+        lo, hi = 0.0, max(Uc, 0.0) + 14 * sig
+    elif sign < 0:
+        lo, hi = min(Uc, 0.0) - 14 * sig, 0.0
+    else:
+        lo, hi = Uc - 14 * sig, Uc + 14 * sig
     u = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
     wu = 0.5 * (hi - lo) * wx
     gh, gw = np.polynomial.hermite.hermgauss(n_v)
@@ -113,7 +121,20 @@ def _half_moments(W, sign, mirror=False, n_u=400, n_v=40):
     uu, vv, ww = np.meshgrid(u, v, w, indexing="ij")
     wt = fu[:, None, None] * wv[None, :, None] * wv[None, None, :]
     psi = np.array([np.ones_like(uu), uu, vv, 0.5 * (uu * uu + vv * vv + ww * ww)])
-    return (psi * uu * wt).sum(axis=(1, 2, 3))
+    if poly is not None:
+        us = -uu if mirror else uu
+        wt = wt * (poly[0] + poly[1] * us + poly[2] * vv + poly[3] * 0.5 * (us * us + vv * vv + ww * ww))
+    return (psi * (uu if sign != 0 else 1.0) * wt).sum(axis=(1, 2, 3))
+
+
+def _remainder_slope(W, Wh):
+    """a with int psi f_W (a . psi) = W^h - (rho^h / rho) W, by quadrature of the 4 x 4 moment system."""
+    G = np.zeros((4, 4))
+    for k in range(4):
+        e = np.zeros(4)
+        e[k] = 1.0
+        G[:, k] = _half_moments(W, 0, poly=e)
+    return np.linalg.solve(G, Wh - (Wh[0] / W[0]) * W)
 
 
 def _cons(rho, U, V, T):
@@ -132,12 +153,12 @@ def test_wall_flux_matches_quadrature_of_its_definition(WL, WhL, ws):
     fr = c[3] - np.exp(-0.013 / 0.004)
     F = ob.wall_flux(Tw, ws, WL, WhL, c, fr)
     inc = c[0] * _half_moments(WL, +1)
+    spec = c[0] * _half_moments(WL, -1, mirror=True)          # specular part: mirrored onto u_n < 0
     if WhL is not None:
-        inc = inc + fr * _half_moments(WhL, +1)
-    # specular part: the incoming distributions mirrored onto u_n < 0
-    spec = c[0] * _half_moments(WL, -1, mirror=True)
-    if WhL is not None:
-        spec = spec + fr * _half_moments(WhL, -1, mirror=True)
+        a = _remainder_slope(WL, WhL)
+        inc = inc + fr * (WhL[0] / WL[0]) * _half_moments(WL, +1) + c[3] * _half_moments(WL, +1, poly=a)
+        spec = (spec + fr * (WhL[0] / WL[0]) * _half_moments(WL, -1, mirror=True)
+                + c[3] * _half_moments(WL, -1, mirror=True, poly=a))
     wall = _half_moments(_cons(1.0, 0.0, 0.0, Tw), -1)
     rho_w = -(1.0 - ws) * inc[0] / wall[0]
     Fq = inc + ws * spec + rho_w * wall
