@@ -491,12 +491,12 @@ __device__ void lts_coeffs(double dt, double tau, double e, double* out)
 }
 
 // Shakhov acceptance-rejection weights of cell c (Eqs. 4-5): the heat flux Q_i of the particles retained in
-// the cell at the start of the step, about the cell velocity U_i, from their raw moments (whq); the sampled
-// wave part takes its mass share rho^h / rho_i of the correction: proposals c = sqrt(RT^h) z from the
-// Maxwellian of W^h are accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5),
-// a = (1 - Pr) Q_i / (5 rho_i (RT^h)^(3/2)), M = 1 + 6 * 31 |a| (|z| <= 6 enforced by rejection). W has no
-// z-momentum, so Q_z = 0; in 1-D also Q_y = 0. FP64, in the order of the CPU definition.
-__device__ void shakhov_weights(const StepConsts& K, const Dev& d, int c, double RTh)
+// the cell at the start of the step, about the cell velocity U_i, from their raw moments (whq). The new
+// particles follow the cell's g^S (Eq. 4 at U_i, T_i, Q_i): proposals c = sqrt(RT_i) z from the Maxwellian
+// are accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5), a = (1 - Pr) Q_i / (5 rho_i
+// (RT_i)^(3/2)), M = 1 + 6 * 31 |a| (|z| <= 6 enforced by rejection). W has no z-momentum, so Q_z = 0; in 1-D
+// also Q_y = 0. FP64, in the order of the CPU definition.
+__device__ void shakhov_weights(const StepConsts& K, const Dev& d, int c, double RTi)
 {
     const long long* h = d.whq + 9 * c;
     const double s0 = ldexp(1.0, -K.fx0), s1 = ldexp(1.0, -K.fx1), s2 = ldexp(1.0, -K.fx_s2);
@@ -512,7 +512,7 @@ __device__ void shakhov_weights(const StepConsts& K, const Dev& d, int c, double
     const double cy3 = ((((Svq - 2.0 * (U * Suv + V * Svv)) + UU * Sv) - V * Sq) + 2.0 * V * Ud) - V * UU * Sm;
     const double Qx = cx3 / (2.0 * d.vol[c]);
     const double Qy = K.dim == 1 ? 0.0 : cy3 / (2.0 * d.vol[c]);
-    const double den = 5.0 * W[0] * (RTh * sqrt(RTh));
+    const double den = 5.0 * W[0] * (RTi * sqrt(RTi));
     const double ax = ((1.0 - K.Pr) * Qx) / den, ay = ((1.0 - K.Pr) * Qy) / den;
     const double M = 1.0 + 186.0 * sqrt(ax * ax + ay * ay);
     d.hq[3 * c] = ax; d.hq[3 * c + 1] = ay; d.hq[3 * c + 2] = M;
@@ -601,36 +601,34 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     // digits to cancellation: FP64 coefficients for every cell then
     if (f32) lts_coeffs_f32((float)dt, (float)x, (float)e, d.co + 7 * c);
     else lts_coeffs(dt, tau, e, d.co + 7 * c);
-    const int phys = realizable(K, Wh);
-    d.hphys[c] = phys;
     int n = 0;
-    double m = 0.0, Uh = 0.0, Vh = 0.0, RTh = 0.0;
-    if (!K.wave_only && phys) {
-        // W^hp = W^h e^{-dt_i/tau_i}, N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp (Eq. 26)
-        const double rho_hp = Wh[0] * e;
-        if (rho_hp > 0.0) {
-            const double q = ceil((rho_hp / W[0]) * (double)K.n_ref);
-            if (q > (double)kMaxNew) {
-                atomicOr(d.err, ERR_LIMIT);
-            } else {
-                n = (int)q;
-                m = (rho_hp * vol) / q;
-                const double rh = 1.0 / Wh[0];
-                Uh = Wh[1] * rh;
-                Vh = Wh[2] * rh;
-                RTh = (Wh[3] * rh - 0.5 * (Uh * Uh + Vh * Vh)) * (2.0 / 3.0);
-            }
+    double m = 0.0, Ui = 0.0, Vi = 0.0, RTi = 0.0;
+    // W^hp = W^h e^{-dt_i/tau_i}; for rho^hp > 0: N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp
+    // (Eqs. 25-26). The new particles' velocities follow the local distribution of the cell (Sec. III B), at
+    // the cell velocity U_i and temperature T_i of the total W; the rest of W^h travels with the wave
+    const double rho_hp = Wh[0] * e;
+    if (!K.wave_only && rho_hp > 0.0) {
+        const double q = ceil((rho_hp / W[0]) * (double)K.n_ref);
+        if (q > (double)kMaxNew) {
+            atomicOr(d.err, ERR_LIMIT);
+        } else {
+            n = (int)q;
+            m = (rho_hp * vol) / q;
+            const double rw = 1.0 / W[0];
+            Ui = W[1] * rw;
+            Vi = K.dim == 1 ? 0.0 : W[2] * rw;
+            RTi = (W[3] * rw - 0.5 * (Ui * Ui + Vi * Vi)) * (2.0 / 3.0);
         }
     }
-    if (K.shakhov && n > 0) shakhov_weights(K, d, c, RTh);
+    if (K.shakhov && n > 0) shakhov_weights(K, d, c, RTi);
     d.nhp[c] = n;
     d.mnew[c] = m;
-    d.samp[3 * c] = Uh; d.samp[3 * c + 1] = Vh; d.samp[3 * c + 2] = RTh;
+    d.samp[3 * c] = Ui; d.samp[3 * c + 1] = Vi; d.samp[3 * c + 2] = RTi;
     d.tau32[c] = (float)tau;
     d.emx32[c] = (float)e;
     d.dt32[c] = (float)dt;
     d.mnew32[c] = (float)m;
-    d.samp32[3 * c] = (float)Uh; d.samp32[3 * c + 1] = (float)Vh; d.samp32[3 * c + 2] = (float)RTh;
+    d.samp32[3 * c] = (float)Ui; d.samp32[3 * c + 1] = (float)Vi; d.samp32[3 * c + 2] = (float)RTi;
     d.cnt[c] = 0;
     d.cur[c] = 0;
 }
@@ -835,8 +833,9 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 
 // ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
 // Eight lanes per cell (four cells per warp; a cell samples about three particles per step on the bench
-// workload). Velocities: Box-Muller normals (Pr = 1) or Shakhov acceptance-rejection (Pr != 1), shifted and
-// scaled so that the cell's new particles carry exactly the momentum and energy of W^hp. Sums in a fixed
+// workload). Velocities from the local distribution of the cell at U_i, T_i (Sec. III B): Box-Muller normals
+// (Pr = 1) or Shakhov acceptance-rejection (Pr != 1), shifted and scaled so that the cell's new particles
+// carry exactly the momentum U_i and energy (3/2) R T_i per unit mass of that distribution. Sums in a fixed
 // order: lane j of the cell's eight adds k = j, j + 8, ... in increasing k, then a butterfly combines the
 // lanes (j + 4 into j, j + 2 into j, j + 1 into j; every lane of the group ends with the same value).
 constexpr int kSampleGroup = 8;
@@ -919,8 +918,8 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
     for (int o = kSampleGroup / 2; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
     long long acc[5] = {0, 0, 0, 0, 0};
     if (N > 0) {
-        const T Uh = pc.s_(c, 0), Vh = pc.s_(c, 1), RTh = pc.s_(c, 2);
-        const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTh) / ss) : T(0);
+        const T Ui = pc.s_(c, 0), Vi = pc.s_(c, 1), RTi = pc.s_(c, 2);
+        const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTi) / ss) : T(0);
         const T m = pc.m_(c);
         const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
         // the cell's vertices in the particle precision and its two triangles' areas (same for every particle)
@@ -950,7 +949,16 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
                 y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
             }
             const T z0 = A.u[i], z1 = A.v[i], z2 = A.w[i];
-            const T un = Uh + sc * (z0 - mu), vn = Vh + sc * (z1 - mv), wn = sc * (z2 - mw);
+            T un, vn, wn;
+            if (N == 1) {
+                // a single particle keeps the direction of its draw at the thermal speed sqrt(3 R T_i) about
+                // U_i: the energy exactly, the momentum without bias
+                const T zz = (z0 * z0 + z1 * z1) + z2 * z2;
+                const T s1 = zz > T(0) ? fsqrt_((T(3) * RTi) / zz) : T(0);
+                un = Ui + s1 * z0; vn = Vi + s1 * z1; wn = s1 * z2;
+            } else {
+                un = Ui + sc * (z0 - mu); vn = Vi + sc * (z1 - mv); wn = sc * (z2 - mw);
+            }
             A.x[i] = x; A.y[i] = y;
             A.u[i] = un;
             A.v[i] = vn;
@@ -2397,7 +2405,7 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         CK(dalloc(ctx, &d.tau, C)); CK(dalloc(ctx, &d.xr, C)); CK(dalloc(ctx, &d.emx, C)); CK(dalloc(ctx, &d.Wh, 4 * C));
         CK(dalloc(ctx, &d.co, 7 * C)); CK(dalloc(ctx, &d.mnew, C)); CK(dalloc(ctx, &d.samp, 3 * C));
         CK(dalloc(ctx, &d.whq, 9 * C)); CK(dalloc(ctx, &d.hq, 3 * C)); CK(dalloc(ctx, &d.hq32, 3 * C));
-        CK(dalloc(ctx, &d.hphys, C)); CK(dalloc(ctx, &d.nhp, C)); CK(dalloc(ctx, &d.nhp_off, C + 1));
+        CK(dalloc(ctx, &d.nhp, C)); CK(dalloc(ctx, &d.nhp_off, C + 1));
         CK(dalloc(ctx, &d.cnt, C)); CK(dalloc(ctx, &d.off, C + 1)); CK(dalloc(ctx, &d.cur, C));
         CK(dalloc(ctx, &d.flux, 4 * F));
         ctx.res_blocks = nblk((long long)C + nwall, kUpdateBlock);

@@ -5,10 +5,14 @@
 //     (Eq. 17); its normal slopes a^L = (W_0 - W_L)/d_L on u.n > 0 and a^R = (W_R - W_0)/d_R on u.n < 0
 //     (Eq. 20 with the Prandtl fix of Sec. III A), and A from the compatibility condition (Eq. 22); each half
 //     weighted with its own cell's normalised coefficients dbar_{a,b,c} (Eq. 48).
-//   F^fr,wave: the hydrodynamic wave's Maxwellian g^h of each side over its half, weighted with
-//     dbar_d - e^{-dt/tau} (the part not carried by new particles, Eq. 50). First order by default; with the
+//   F^fr,wave: the hydrodynamic wave of each side over its half (Eq. 50), read as in Sec. III B: rho^h times
+//     the side's local distribution (the Maxwellian of the total W, which the new particles are sampled
+//     from), weighted with dbar_d - e^{-dt/tau} where this step's particles carry e^{-x} of it (else
+//     dbar_d), plus the massless remainder W^h - (rho^h / rho) W, represented to first order about the same
+//     Maxwellian (Eq. 20 form) and never sampled, weighted with dbar_d. First order by default; with the
 //     second-order reconstruction (Eq. 12, order 2) the states at the face are reconstructed from limited
-//     cell gradients and g^h adds its normal slope term, weighted with dbar_e + dt e^{-x} / 2.
+//     cell gradients and the wave adds the normal slope term of W^h about the same Maxwellian, weighted with
+//     dbar_e + dt e^{-x} / 2.
 //  Boundary faces (n points out of the fluid cell L): a diffuse wall returns a wall Maxwellian at T_w with
 //  the density that zeroes the wave mass flux (first order); far-field / fixed ghosts are virtual cells of
 //  the ghost state with the fluid cell's time step on both halves (Sec. IV B), whose collisionless part
@@ -25,7 +29,7 @@ namespace ugk {
 namespace {
 
 template <typename R> struct Prim { R rho, U, V, lam; };
-template <typename R> struct Mom { R up[9], um[9], v[7], xi2, xi4; };
+template <typename R> struct Mom { R up[9], um[9], v[7], xi2, xi4, g0; };   // g0: density at u = 0
 
 template <typename R> __device__ __forceinline__ bool frame_prim(const R W[4], Prim<R>& p)
 {
@@ -61,6 +65,7 @@ template <typename R> __device__ __forceinline__ void moments(const Prim<R>& p, 
     for (int k = 2; k < 7; ++k) M.v[k] = V * M.v[k - 1] + R(k - 1) * th * M.v[k - 2];
     M.xi2 = th;
     M.xi4 = R(3) * th * th;
+    M.g0 = ex / th;
 }
 
 // <psi u^a v^b w^(2c)>, psi = (1, u, v, |u|^2/2)
@@ -158,42 +163,78 @@ __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], co
     for (int k = 0; k < 4; ++k) F[k] = C(p0.rho) * (F[k] + cR[2] * C(f[k]));
 }
 
-// Order 2: a side's free-transport wave from its reconstructed W^h, rho^h <psi u_n>_half (zero) and the
-// normal slope term rho^h <psi u_n^2 (a . psi)>_half (slope) with a the micro slope of the normal derivative
-// dh of W^h; evaluated in FP64 whatever the face's precision: a reconstructed W^h can sit near the edge of the
-// realizable set (small internal energy) and the slope moments cancel strongly where W^h is small against
-// its gradient (particle-dominated cells). Returns false if the state is not a Maxwellian.
-template <typename R>
-__device__ bool gh_terms(const R Wh[4], const R dh[4], bool up, double zero[4], double slp[4])
+// Free transport of one side's hydrodynamic wave over its half (Eq. 50) about the Maxwellian p (moments m) of
+// the side's state W: rho^h <psi u_n>_half weighted with fr (the part the new particles are sampled from),
+// the remainder dW = W^h - (rho^h / rho) W as rho <psi u_n (a . psi)>_half with <psi g (a . psi)> = dW / rho,
+// weighted with fd, and with order 2 the normal slope dh of W^h as rho <psi u_n^2 (a . psi)>_half, weighted
+// with cs. Linear in W^h, so the noise of W^h = W - W^p biases nothing.
+// g (a . psi) is the derivative of the Maxwellian in the direction dW, so the remainder's flux is the
+// directional derivative of the half-range flux rho <psi u_n>_half. With FP32 moments (R = float) it is
+// evaluated in that form, from the primitive perturbation dp = (d rho, dU, dV, d theta), theta = R T, formed in
+// FP64 (prim_perturbation): the moment solve in the absolute frame cancels terms of order |U|^2 / RT (about
+// 300 at Ma 20), which FP32 cannot afford. The half-range moments M_k = <u^k>_half obey dM_k/dU = k M_{k-1} and
+// dM_k/dtheta = k (k - 1) / 2 M_{k-2} (k >= 1, 2), dM_1/dtheta = +-g(0) / 2 (+ for u > 0).
+template <typename R, typename C>
+__device__ __forceinline__ void wave_part(const Prim<R>& p, const Mom<R>& m, bool up, const R W[4], const R Wh[4],
+                                          const double dp[4], C fr, C fd, const R* dh, C cs, C F[4])
 {
-    double W[4], dw[4], a[4];
+    const R* Mu = up ? m.up : m.um;
+    R t[4], dw[4], a[4];
+    psi_mom(Mu, m, 1, 0, 0, t);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) W[k] = double(Wh[k]);
-    Prim<double> p;
-    if (!frame_prim(W, p)) return false;
-    Mom<double> m;
-    moments(p, m);
-    psi_mom(up ? m.up : m.um, m, 1, 0, 0, zero);
+    for (int k = 0; k < 4; ++k) F[k] += fr * C(Wh[0] * t[k]);
+    if (sizeof(R) == 4) {
+        const R dr = R(dp[0]), dU = R(dp[1]), dV = R(dp[2]), dth = R(dp[3]);
+        const R th = m.xi2, V = p.V, s = V * V + R(2) * th, hg = (up ? R(0.5) : R(-0.5)) * m.g0;
+        t[0] = dr * Mu[1] + p.rho * (Mu[0] * dU + hg * dth);
+        t[1] = dr * Mu[2] + p.rho * (R(2) * Mu[1] * dU + Mu[0] * dth);
+        t[2] = dr * Mu[1] * V + p.rho * ((Mu[0] * V) * dU + Mu[1] * dV + (hg * V) * dth);
+        t[3] = R(0.5) * (dr * (Mu[3] + Mu[1] * s) +
+                         p.rho * ((R(3) * Mu[2] + Mu[0] * s) * dU + (R(2) * V * Mu[1]) * dV + (R(5) * Mu[1] + hg * s) * dth));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) dw[k] = double(dh[k]) / p.rho;
-    slope(p, dw, a);
-    psi_poly(up ? m.up : m.um, m, 2, 0, a, slp);
+        for (int k = 0; k < 4; ++k) F[k] += fd * C(t[k]);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        zero[k] = p.rho * zero[k];
-        slp[k] = p.rho * slp[k];
+        for (int k = 0; k < 4; ++k) dw[k] = (Wh[k] - (Wh[0] / p.rho) * W[k]) / p.rho;
+        slope(p, dw, a);
+        psi_poly(Mu, m, 1, 0, a, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) F[k] += fd * C(p.rho * t[k]);
     }
-    return true;
+    if (dh) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dw[k] = dh[k] / p.rho;
+        slope(p, dw, a);
+        psi_poly(Mu, m, 2, 0, a, t);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) F[k] += cs * C(p.rho * t[k]);
+    }
 }
 
-// interior-type face; frL/frR weight each side's g^h. WL, WR: the states at the face (the cell states in
-// first order), WLc, WRc: the cell states the normal slopes of g_0 are taken against; dhL, dhR (nullable):
-// normal derivatives of W^h for the slope term of the free-transport wave, weighted with csL, csR (order 2).
-// Returns false if a side state is not a valid Maxwellian in precision R (the caller then uses FP64).
+// The primitive perturbation (d rho, dU, dV, d theta) of the Maxwellian of W (face frame, FP64) that carries the
+// remainder dW = W^h - (rho^h / rho) W of the hydrodynamic wave: W = (rho, rho U, rho V, rho (|U|^2 + 3 theta) / 2)
+__device__ __forceinline__ void prim_perturbation(const double W[4], const double Wh[4], double dp[4])
+{
+    const double rho = W[0], U = W[1] / rho, V = W[2] / rho, q = Wh[0] / rho;
+    const double th = (W[3] / rho - 0.5 * (U * U + V * V)) / 1.5;
+    double dW[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dW[k] = Wh[k] - q * W[k];
+    dp[0] = dW[0];
+    dp[1] = (dW[1] - U * dW[0]) / rho;
+    dp[2] = (dW[2] - V * dW[0]) / rho;
+    dp[3] = ((dW[3] - dW[0] * (0.5 * (U * U + V * V) + 1.5 * th)) - rho * (U * dp[1] + V * dp[2])) / (1.5 * rho);
+}
+
+// interior-type face; frL/frR weight each side's sampled-from wave part, fdL/fdR its remainder. WL, WR: the
+// states at the face (the cell states in first order), WLc, WRc: the cell states the normal slopes of g_0 are
+// taken against; dhL, dhR (nullable): normal derivatives of W^h for the slope term of the free-transport wave,
+// weighted with csL, csR (order 2). Returns false if a side state is not a valid Maxwellian in precision R
+// (the caller then uses FP64).
 template <typename R, typename C>
-__device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], bool hL, bool hR,
-                          const C cL[3], const C cR[3], C frL, C frR, R dL, R dR, R Pr, const R WLc[4],
-                          const R WRc[4], const R* dhL, const R* dhR, C csL, C csR, C F[4])
+__device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], const double dpL[4],
+                          const double dpR[4], C fdL, C fdR, const C cL[3], const C cR[3], C frL, C frR, R dL, R dR,
+                          R Pr, const R WLc[4], const R WRc[4], const R* dhL, const R* dhR, C csL, C csR, C F[4])
 {
     Prim<R> pL, pR, p0;
     Mom<R> mL, mR;
@@ -209,41 +250,17 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
     for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];
     // vacuum interface: no molecule of either side reaches the face, no equilibrium flux
     if (frame_prim(W0, p0)) equilibrium_part(W0, WLc, WRc, p0, cL, cR, dL, dR, Pr, F);
-    R f[4];
-    Prim<R> ph;
-    Mom<R> mh;
-    double z[4], sl[4];
-    if (hL && dhL) {
-        if (gh_terms(WhL, dhL, true, z, sl))
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                F[k] += frL * C(z[k]);
-                F[k] += csL * C(sl[k]);
-            }
-    } else if (hL && frame_prim(WhL, ph)) {
-        moments(ph, mh);
-        psi_mom(mh.up, mh, 1, 0, 0, f);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] += frL * C(ph.rho * f[k]);
-    }
-    if (hR && dhR) {
-        if (gh_terms(WhR, dhR, false, z, sl))
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                F[k] += frR * C(z[k]);
-                F[k] += csR * C(sl[k]);
-            }
-    } else if (hR && frame_prim(WhR, ph)) {
-        moments(ph, mh);
-        psi_mom(mh.um, mh, 1, 0, 0, f);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] += frR * C(ph.rho * f[k]);
-    }
+    wave_part<R, C>(pL, mL, true, WL, WhL, dpL, frL, fdL, dhL, csL, F);
+    wave_part<R, C>(pR, mR, false, WR, WhR, dpR, frR, fdR, dhR, csR, F);
     return true;
 }
 
+// diffuse (or Maxwell) isothermal wall: the incoming half of the fluid cell's g and of its hydrodynamic wave
+// (as in face_flux: weights frL and fdL), the outgoing wall Maxwellian at T_w with the density that makes the
+// wave mass flux zero
 template <typename R, typename C>
-__device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, C caL, C frL, R lam_w, C ws, C F[4])
+__device__ bool wall_flux(const R WL[4], const R WhL[4], const double dpL[4], C fdL, C caL, C frL, R lam_w, C ws,
+                          C F[4])
 {
     Prim<R> p;
     Mom<R> m;
@@ -253,12 +270,7 @@ __device__ bool wall_flux(const R WL[4], const R WhL[4], bool hL, C caL, C frL, 
     psi_mom(m.up, m, 1, 0, 0, t);
 #pragma unroll
     for (int k = 0; k < 4; ++k) F[k] = caL * C(p.rho * t[k]);
-    if (hL && frame_prim(WhL, p)) {
-        moments(p, m);
-        psi_mom(m.up, m, 1, 0, 0, t);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] += frL * C(p.rho * t[k]);
-    }
+    wave_part<R, C>(p, m, true, WL, WhL, dpL, frL, fdL, nullptr, C(0), F);
     p.rho = R(1); p.U = R(0); p.V = R(0); p.lam = lam_w;
     moments(p, m);
     psi_mom(m.um, m, 1, 0, 0, t);
@@ -362,28 +374,46 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         o[2] = -a * nyr + b * nxr;
         o[3] = R(W[3]);
     };
+    // FP32 moments: the primitive perturbation carrying a side's wave remainder, from the FP64 cell states, in
+    // the face frame (d rho and d theta are invariant, (dU, dV) rotate like the velocity); unused in FP64
+    auto prim_pert = [&](int cc, double o[4]) {
+        if (sizeof(R) != 4) return;
+        double g[4];
+        prim_perturbation(c.W + 4 * cc, c.Wh + 4 * cc, g);
+        o[0] = g[0];
+        o[1] = g[1] * nx + g[2] * ny;
+        o[2] = -g[1] * ny + g[2] * nx;
+        o[3] = g[3];
+    };
     R WL[4], WhL[4], WR[4], WhR[4], WLc[4], WRc[4], dhL[4], dhR[4];
+    double dpL[4] = {0.0, 0.0, 0.0, 0.0}, dpR[4] = {0.0, 0.0, 0.0, 0.0};
     C F[4];
     bool ok;
     rot(c.W + 4 * L, WL);
     rot(c.Wh + 4 * L, WhL);
+    prim_pert(L, dpL);
 #pragma unroll
     for (int q = 0; q < 4; ++q) WLc[q] = WL[q];
     const double* coL = c.co + 7 * L;
     const C cL[3] = {C(coL[0]), C(coL[1]), C(coL[2])};
-    const C frL = C(K.wave_only ? coL[3] : coL[5]);
-    const bool hL = c.hphys[L] != 0;
+    // the sampled-from part of a side's wave keeps dbar_d - e^{-x} where this step's particles carry e^{-x} of
+    // it; its remainder keeps dbar_d
+    const C frL = C((K.wave_only || c.nhp[L] == 0) ? coL[3] : coL[5]);
+    const C fdL = C(coL[3]);
     // order 2: reconstructed face states of W (equilibrium part) and W^h (free-transport wave with its normal
     // slope term, weighted with dbar_e, or dbar_e + dt e^{-x} / 2 when the collisionless part is carried by
-    // particles, Eq. 50) on interior, periodic and far-field / fixed faces
+    // particles, Eq. 50) on interior, periodic and far-field / fixed faces; W and W^h are reconstructed
+    // together, and a side whose reconstructed W is not a positive density and internal energy stays first
+    // order
     const bool o2 = K.order == 2 && (bc == 0 || bc == UGKWP_BC_PERIODIC || bc == UGKWP_BC_FARFIELD ||
                                      bc == UGKWP_BC_FIXED);
     bool sL = false, sR = false;
     const C csL = C(K.wave_only ? coL[4] : coL[6]);
     if (o2) {
         double Wf[4], dn[4];
-        if (face_side(K, c, L, f, 0, nx, ny, Wf, dn)) rot(Wf, WL);
-        if (hL && face_side(K, c, L, f, 1, nx, ny, Wf, dn)) {
+        if (face_side(K, c, L, f, 0, nx, ny, Wf, dn)) {
+            rot(Wf, WL);
+            face_side(K, c, L, f, 1, nx, ny, Wf, dn);
             rot(Wf, WhL);
             rot(dn, dhL);
             sL = true;
@@ -392,28 +422,30 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
     if (bc == 0 || bc == UGKWP_BC_PERIODIC) {
         rot(c.W + 4 * Rc, WR);
         rot(c.Wh + 4 * Rc, WhR);
+        prim_pert(Rc, dpR);
 #pragma unroll
         for (int q = 0; q < 4; ++q) WRc[q] = WR[q];
         const double* coR = c.co + 7 * Rc;
         const C cR[3] = {C(coR[0]), C(coR[1]), C(coR[2])};
-        const C frR = C(K.wave_only ? coR[3] : coR[5]);
-        const bool hR = c.hphys[Rc] != 0;
+        const C frR = C((K.wave_only || c.nhp[Rc] == 0) ? coR[3] : coR[5]);
         if (o2) {
             double Wf[4], dn[4];
-            if (face_side(K, c, Rc, f, 0, nx, ny, Wf, dn)) rot(Wf, WR);
-            if (hR && face_side(K, c, Rc, f, 1, nx, ny, Wf, dn)) {
+            if (face_side(K, c, Rc, f, 0, nx, ny, Wf, dn)) {
+                rot(Wf, WR);
+                face_side(K, c, Rc, f, 1, nx, ny, Wf, dn);
                 rot(Wf, WhR);
                 rot(dn, dhR);
                 sR = true;
             }
         }
-        ok = face_flux<R, C>(WL, WR, WhL, WhR, hL, hR, cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]), R(K.Pr), WLc,
+        ok = face_flux<R, C>(WL, WR, WhL, WhR, dpL, dpR, fdL, C(coR[3]), cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]), R(K.Pr), WLc,
                              WRc, sL ? dhL : nullptr, sR ? dhR : nullptr, csL, C(K.wave_only ? coR[4] : coR[6]), F);
     } else if (bc == UGKWP_BC_WALL) {
-        ok = wall_flux<R, C>(WL, WhL, hL, cL[0], frL, R(0.5 / (kR * K.Tw)), C(K.wall_specular), F);
+        ok = wall_flux<R, C>(WL, WhL, dpL, fdL, cL[0], frL, R(0.5 / (kR * K.Tw)), C(K.wall_specular), F);
     } else if (bc == UGKWP_BC_SYMMETRY) {
         const R Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
-        ok = face_flux<R, C>(WL, Wm, WhL, Whm, hL, hL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), WL, Wm,
+        dpR[0] = dpL[0]; dpR[1] = -dpL[1]; dpR[2] = dpL[2]; dpR[3] = dpL[3];
+        ok = face_flux<R, C>(WL, Wm, WhL, Whm, dpL, dpR, fdL, fdL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), WL, Wm,
                              nullptr, nullptr, C(0), C(0), F);
     } else {
         double Wg[4];
@@ -430,7 +462,8 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         double cg[5];
         ghost_coeffs(c.dt[L], tau_of(K, Wg), cg);
         const C cR[3] = {C(cg[0]), C(cg[1]), C(cg[2])};
-        ok = face_flux<R, C>(WL, WR, WhL, WR, hL, true, cL, cR, frL, C(K.wave_only ? cg[3] : cg[4]), R(c.fdL[f]),
+        // the ghost's wave is its whole state (no remainder: dpR = 0)
+        ok = face_flux<R, C>(WL, WR, WhL, WR, dpL, dpR, fdL, C(cg[3]), cL, cR, frL, C(K.wave_only ? cg[3] : cg[4]), R(c.fdL[f]),
                              R(c.fdL[f]), R(K.Pr), WLc, WR, sL ? dhL : nullptr, nullptr, csL, C(0), F);
     }
     const C nxc = C(nx), nyc = C(ny);

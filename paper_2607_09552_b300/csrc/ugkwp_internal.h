@@ -81,7 +81,7 @@ struct Dev {
     long long* whq;                    // [9C] Pr != 1: raw moments of the retained particles
     double* hq;                        // [3C] Pr != 1: acceptance-rejection weights a_x, a_y, M
     float* hq32;
-    int *hphys, *nhp, *nhp_off, *cnt, *off, *cur;
+    int *nhp, *nhp_off, *cnt, *off, *cur;
     int* scan_tmp;
     double* flux;                      // [4F]
     double *res_part, *res;            // residual: per-block partials; [8] = raw of this step (4 used)
