@@ -187,6 +187,8 @@ def run_ours(args):
         burn, burn_rule = burn_in(solver, args)
         if args.save_state:
             solver.save(args.save_state)
+    if args.launch:
+        solver.set_launch(*[int(v) for v in args.launch.split(",")])
     launch, tune_ms = solver.autotune(16) if not args.no_autotune else (solver.launch(), None)
     stream.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -243,12 +245,14 @@ def run_ours(args):
         cfg = config_dict(case, burn, "512 MB L2 flush before every timed step, outside the events")
         cfg["burn_in_rule"] = burn_rule
         cfg["reconstruction_order"] = args.order
-        tiled = launch[3] == 2
-        cfg["launch"] = {"transport_kernel": "k_particles_tiled (1024-particle tiles, bulk async copies, 2 CTAs/SM)"
-                         if tiled else "k_particles (warp-chunked)",
-                         "chunk": None if tiled else launch[0], "blocks_per_sm": 2 if tiled else launch[1],
+        kname = {1: "k_particles (warp-chunked)",
+                 2: f"k_particles_warp ({launch[0]}-particle warp tiles, bulk async copies, {launch[1]} CTAs/SM, "
+                    "records updated in place)"}
+        cfg["launch"] = {"transport_kernel": kname[launch[3]],
+                         "chunk": launch[0], "blocks_per_sm": launch[1],
                          "sort_every": launch[2],
-                         "chosen_by": "autotuner" if not args.no_autotune else "defaults", "graph": True}
+                         "chosen_by": "autotuner" if not args.no_autotune else
+                         ("--launch" if args.launch else "defaults"), "graph": True}
         line = {
             "metric": "particle-steps/s", "value": ps_all / (ms_all * 1e-3), "unit": "particle-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_all / args.steps,
@@ -262,7 +266,7 @@ def run_ours(args):
                             "library's stream (the second stream's ghost sources and wave fluxes not overlapped)",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "kernel": ("k_particles_tiled" if launch[3] == 2 else "k_particles") +
+                         "kernel": {1: "k_particles", 2: "k_particles_warp"}[launch[3]] +
                                    " (t_f draw, transport with dt_R/dt_L scaling, tallies, compaction)",
                          "algorithmic_bytes_per_launch": BYTES_PER_PARTICLE_STEP * per_launch,
                          "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
@@ -797,6 +801,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch", default="", help="chunk,blocks_per_sm,sort_every,transport set before the "
+                    "(optional) autotuning pass; with --no-autotune the launch shape that is timed")
     ap.add_argument("--profile-steps", type=int, default=400)
     ap.add_argument("--mode", default="throughput", choices=["throughput", "convergence", "batch", "warmstart"])
     ap.add_argument("--batch-scale", type=float, default=1.0)

@@ -627,6 +627,7 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     d.tau32[c] = (float)tau;
     d.emx32[c] = (float)e;
     d.dt32[c] = (float)dt;
+    if (d.cst32) d.cst32[c] = make_float4((float)dt, (float)e, (float)tau, __int_as_float(d.nfc[c]));
     d.mnew32[c] = (float)m;
     d.samp32[3 * c] = (float)Ui; d.samp32[3 * c + 1] = (float)Vi; d.samp32[3 * c + 2] = (float)RTi;
     d.cnt[c] = 0;
@@ -735,7 +736,10 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
         d.stats[13] = 0;
         *d.nretry = 0;
         *d.done = 0u;
-        d.flags[0] = (int)(*d.dstep % K.sort_every == (long long)(K.sort_every - 1));
+        // a counting sort every sort_every-th step, and whenever holes (removed particles, updated in place)
+        // fill more than a quarter of the slots
+        const long long slots = d.counts[0], alive = (long long)d.stats[1];
+        d.flags[0] = (int)(*d.dstep % K.sort_every == (long long)(K.sort_every - 1) || 4 * (slots - alive) > slots);
     }
 }
 
@@ -821,11 +825,13 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
                      T(ldexp(1.0, K.fx_s3))};
     unsigned long long* h = reinterpret_cast<unsigned long long*>(d.whq);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = A.cell[i];
+        if (ci < 0) continue;   // a hole
         const T m = A.m[i], u = A.u[i], v = A.v[i], w = A.w[i];
         const T q = (u * u + v * v) + w * w;
         const T mu = m * u, mv = m * v;
         const T val[9] = {m, mu, mv, mu * u, mu * v, mv * v, m * q, mu * q, mv * q};
-        const size_t c = (size_t)A.cell[i];
+        const size_t c = (size_t)ci;
 #pragma unroll
         for (int k = 0; k < 9; ++k) atomicAdd(h + 9 * c + k, (unsigned long long)fixp(val[k], sc[k], d.err));
     }
@@ -1000,6 +1006,26 @@ __device__ __forceinline__ bool stays_in(const CellFaces<T>& F, int nf, int entr
     return stays;
 }
 
+// stays_in for the first transport test of a particle in its start cell (no entry face), FP32: the cell's
+// outward normals and plane offsets in three 16-byte loads and the faces unrolled (faces past nf skipped), the
+// same per-face operations as stays_in
+__device__ __forceinline__ bool stays_in_start(const CellFaces<float>& F, int nf, float x, float y, float u, float v,
+                                               float tr)
+{
+    const float4 NX = *reinterpret_cast<const float4*>(F.nx);
+    const float4 NY = *reinterpret_cast<const float4*>(F.ny);
+    const float4 D = *reinterpret_cast<const float4*>(F.d);
+    const float nxa[4] = {NX.x, NX.y, NX.z, NX.w}, nya[4] = {NY.x, NY.y, NY.z, NY.w}, da[4] = {D.x, D.y, D.z, D.w};
+    bool stays = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float un = nxa[k] * u + nya[k] * v;
+        const bool ahead = k < nf && un > 0.0f;
+        if (ahead && tr * un > da[k] - (nxa[k] * x + nya[k] * y)) stays = false;
+    }
+    return stays;
+}
+
 // The face through which a particle at (x, y) moving with (u, v) leaves its cell first: exit time through face
 // k = (d_k - n_k . x) / (n_k . u) for n_k . u > 0 (negative values, from rounding on a face, count as 0); the
 // smallest wins, ties go to the lower local index; the face `entry` is skipped. Returns the local index, or -1
@@ -1141,30 +1167,62 @@ __device__ __forceinline__ void tally_move(const Dev& d, T s0, T s1, T s4, int i
     }
 }
 
+// Survivors per cell for the counting sort (sort steps only): one atomic per run of equal cell in the warp
+// (key -1: no survivor in this lane). Every lane of the warp takes part.
+__device__ __forceinline__ void count_runs(const Dev& d, int key)
+{
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    int start = (lane == 0 || prev != key) ? lane : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start = max(start, t);
+    }
+    const int nx = __shfl_down_sync(0xffffffffu, key, 1);
+    if ((lane == 31 || nx != key) && key >= 0) atomicAdd(d.cnt + key, lane - start + 1);
+}
+
+// A particle's record after transport, in place (slot i of the buffer that holds the step's particles): one
+// that stayed in its start cell without a face event and without colliding has only moved (x, y written back);
+// one that crossed or met a boundary writes its whole record but its id; a removed one (collided, or left the
+// domain) becomes a hole (cell -1), squeezed out by the next counting sort.
+template <typename T>
+__device__ __forceinline__ void write_in_place(const ParticleSoA<T>& A, int i, bool moved_only, bool kept, T x, T y,
+                                               T u, T v, T w, T m, int c)
+{
+    if (!kept) {
+        A.cell[i] = -1;
+        return;
+    }
+    A.x[i] = x; A.y[i] = y;
+    if (!moved_only) {
+        A.u[i] = u; A.v[i] = v; A.w[i] = w; A.m[i] = m;
+        A.cell[i] = c;
+    }
+}
+
 // ------------------------------------------------- a3-a6: free flight, transport and tallies
 // One thread per particle (warp-uniform grid-stride loop). Retained particles draw t_f (Eq. 27 with dt_i),
 // new ones fly the whole dt_i; free transport through the cell faces (Eq. 28) with mass and remaining time
 // scaled by dt_R / dt_L at every crossing (Eqs. 41, 52), diffuse re-emission at walls, specular mirrors,
-// deletion at far-field and fixed ghosts. Then W^{p,+} and the retained tally (run-reduced per warp) and
-// the survivors: compacted into the other buffer (warp-aggregated slots), or, on sort steps, written in
-// place for the counting sort.
+// deletion at far-field and fixed ghosts. Then W^{p,+} and the retained tally, and the particle's record in
+// place (holes, cell -1, are skipped); on sort steps the survivors per cell for the counting sort.
 template <typename T>
 __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const StepConsts K, const Dev d, ParticleSoA<T> PA,
                                                    ParticleSoA<T> PB, const CellFaces<T>* __restrict__ cf,
                                                    PCell<T> pc, const long long* dstep)
 {
-    const int sel = *d.bufsel;
-    const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
+    const ParticleSoA<T> A = *d.bufsel ? PB : PA;
     const bool sort_step = d.flags[0] != 0;
     const int nret = d.counts[0];
-    const int n = nret + d.counts[1], cap = d.counts[3];
+    const int n = nret + d.counts[1];
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
     const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
     const T m2RTw = T(K.m2RTw), sigw = T(K.sig_w);
-    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0;
+    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0, n_kept = 0;
     int max_it = 0;
     const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
     // each warp takes chunks of K.chunk consecutive particles (of the cell-ordered array) from a global
     // counter and walks them 32 at a time, prefetching the next 32 records into L1 while it works on the
     // current ones; dynamic chunks keep all SMs busy when other kernels share the GPU
@@ -1182,19 +1240,15 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
             asm volatile("prefetch.global.L1 [%0];" ::"l"(A.y + inext));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(A.u + inext));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(A.v + inext));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.w + inext));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(A.m + inext));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(A.cell + inext));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(A.pid + inext));
         }
         int end_cell = -1;
         bool kept = false;
-        T x = 0, y = 0, u = 0, v = 0, w = 0, m = 0;
-        uint64_t pid = 0;
-        if (i < wend) {
-            x = A.x[i]; y = A.y[i]; u = A.u[i]; v = A.v[i]; w = A.w[i]; m = A.m[i];
-            int c = A.cell[i];
-            pid = A.pid[i];
+        int c = i < wend ? A.cell[i] : -1;
+        if (c >= 0) {
+            T x = A.x[i], y = A.y[i], u = A.u[i], v = A.v[i], w = A.w[i], m = A.m[i];
+            const uint64_t pid = A.pid[i];
             const int c0 = c;
             const T m0 = m, u0 = u, v0 = v, w0 = w;
             const T dtc = pc.dt_(c);
@@ -1226,44 +1280,10 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
                 n_left++;
             }
             tally_move(d, s0, s1, s4, it, alive, collide, c0, m0, u0, v0, w0, c, m, u, v, w);
+            write_in_place(A, i, it == 0 && !collide, kept, x, y, u, v, w, m, c);
+            n_kept += kept ? 1 : 0;
         }
-        // survivors
-        if (sort_step) {
-            if (i < wend) {
-                B.x[i] = x; B.y[i] = y; B.u[i] = u; B.v[i] = v; B.w[i] = w; B.m[i] = m;
-                B.cell[i] = kept ? end_cell : -1;
-                B.pid[i] = pid;
-            }
-        } else {
-            const unsigned km = __ballot_sync(0xffffffffu, kept);
-            int slot0 = 0;
-            if (lane == 0 && km) slot0 = atomicAdd(d.counts + 2, __popc(km));
-            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-            if (kept) {
-                // the ghost sources on the second stream take slots of the same buffer meanwhile
-                const int j = slot0 + __popc(km & lt_mask);
-                if (j >= cap) {
-                    atomicOr(d.err, ERR_CAPACITY);
-                } else {
-                    B.x[j] = x; B.y[j] = y; B.u[j] = u; B.v[j] = v; B.w[j] = w; B.m[j] = m;
-                    B.cell[j] = end_cell;
-                    B.pid[j] = pid;
-                }
-            }
-        }
-        // survivors per cell for the counting sort (sort steps only), one atomic per run of equal cell
-        if (sort_step) {
-            const int key = kept ? end_cell : -1;
-            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-            int start = (lane == 0 || prev != key) ? lane : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, start, o);
-                if (lane >= o) start = max(start, t);
-            }
-            const int next = __shfl_down_sync(0xffffffffu, key, 1);
-            if ((lane == 31 || next != key) && key >= 0) atomicAdd(d.cnt + key, lane - start + 1);
-        }
+        if (sort_step) count_runs(d, kept ? end_cell : -1);
     }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -1271,6 +1291,7 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
         n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
         n_removed += __shfl_xor_sync(0xffffffffu, n_removed, o);
         n_left += __shfl_xor_sync(0xffffffffu, n_left, o);
+        n_kept += __shfl_xor_sync(0xffffffffu, n_kept, o);
         max_it = max(max_it, __shfl_xor_sync(0xffffffffu, max_it, o));
     }
     if (lane == 0) {
@@ -1279,41 +1300,12 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
         if (n_cross) atomicAdd(d.stats + 5, n_cross);
         if (n_hits) atomicAdd(d.stats + 6, n_hits);
         if (max_it) atomicMax(d.stats + 7, (unsigned long long)max_it);
+        if (n_kept) atomicAdd(d.counts + 2, (int)n_kept);
     }
 }
 
-// ---------------------------------------- a3-a7, tile-staged: the production-precision transport kernel
-// Persistent CTAs of kTileThreads threads, two per SM, claim tiles of kTile consecutive particles from a
-// global counter. A tile's records (x, y, u, v, w, m, cell, id) arrive in shared memory by bulk asynchronous
-// copies (cp.async.bulk, completion counted on an mbarrier), double-buffered: the next tile is in flight
-// while the current one is processed, so HBM streams independently of the divergent transport. Per tile:
-//  A. one thread per particle, all lanes together: t_f (Eq. 27, computed form as in k_particles) and the
-//     stay test of the start cell; a particle that stays and does not collide moves (x += u t_r) in shared
-//     memory and is done; the others (a face ahead within t_r, or colliding) go to a shared-memory queue.
-//  B. the queue, 32 queued particles per warp at a time: the full free flight of fly() (crossings with the
-//     dt_R / dt_L scaling, walls, exits) and the tallies, exactly as in k_particles.
-//  C. survivors: compacted into the other buffer at one slot range per tile (tile order kept), or on sort
-//     steps written in place with their per-cell run counts for the counting sort.
-// Every per-particle operation is that of k_particles, in the same order, so the results are identical.
-constexpr int kTile = 1024;
-constexpr int kTileThreads = 256;
-constexpr int kTilePer = kTile / kTileThreads;
-constexpr unsigned long long kTileWaitNs = 2000000000ull;   // bounded wait for a tile's copies (2 s)
-
-struct TileRecords {   // one tile of particle records, SoA, every array 16-byte aligned
-    float x[kTile], y[kTile], u[kTile], v[kTile], w[kTile], m[kTile];
-    int cell[kTile];
-    unsigned long long pid[kTile];
-};
-struct TileSmem {
-    TileRecords rec[2];
-    float tr[kTile];                 // queued particles: remaining free-flight time
-    unsigned short queue[kTile];     // queued particles' tile indices
-    unsigned char st[kTile];         // 1 survivor, 0 gone; phase A: 2 queued, 3 queued and colliding
-    int chunk_off[kTilePer * kTileThreads / 32 + 1];
-    int qn, next, base, abort;
-    unsigned long long bar[2];
-};
+// ---------------------------------------- bulk asynchronous copies into shared memory, with mbarriers
+constexpr unsigned long long kCopyWaitNs = 2000000000ull;   // bounded wait for a tile's copies (2 s)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count)
@@ -1345,7 +1337,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint3
     const unsigned long long t0 = global_ns();
     for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0u && global_ns() - t0 > kTileWaitNs) return false;
+        if ((it & 63u) == 0u && global_ns() - t0 > kCopyWaitNs) return false;
     }
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, unsigned long long* bar)
@@ -1356,132 +1348,93 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-// one thread: copy tile t of A into stage r (the record count rounded up to 4, which the buffers' slack
-// covers, so that every copy is a multiple of 16 bytes from a 16-byte aligned address)
-__device__ __forceinline__ void tile_issue(const ParticleSoA<float>& A, int t, int n, TileRecords& r,
-                                           unsigned long long* bar)
+// ---------------------------------------- a3-a7, warp-staged: the production-precision transport kernel
+// Every warp works alone (no block-wide barrier): it claims tiles of WT consecutive particle slots from a
+// global counter and has the fields that the stay test reads (cell, x, y, u, v, id) copied into its own
+// shared memory by bulk asynchronous copies (cp.async.bulk, completion counted on the warp's mbarrier),
+// double-buffered, so that the next tile streams in while the warp works on the current one. Per tile:
+//  A1. t_f (Eq. 27, computed form as in k_particles) and the stay test of the start cell, 32 particles at a
+//      time with no warp-wide operation between them (their loads and Philox chains overlap). A particle
+//      that stays and does not collide has only moved: its x, y are written back in place (8 bytes), the rest
+//      of its record is left untouched. Holes (cell -1) are skipped.
+//  A2. the others (a face ahead within t_r, or colliding) are queued in the warp's shared memory; whenever 32
+//      are queued the warp flies them together (B): the full free flight of fly() (crossings with the
+//      dt_R / dt_L scaling, walls, exits) and the tallies, exactly as in k_particles, then their records in
+//      place (the whole record but the id, or a hole).
+// On sort steps the survivors are counted per cell for the counting sort. Every per-particle operation is
+// that of k_particles, in the same order, so the results are identical.
+constexpr int kWWarps = 4;     // warps per CTA
+constexpr int kWQueue = 64;    // queued particles per warp: at most 31 left over + 32 added by one round
+
+template <int WT> struct alignas(16) WarpSmem {
+    float x[2][WT], y[2][WT], u[2][WT], v[2][WT];   // two stages of tile fields
+    int cell[2][WT];
+    unsigned long long pid[2][WT];
+    float qx[kWQueue], qy[kWQueue], qu[kWQueue], qv[kWQueue], qt[kWQueue];
+    int qc[kWQueue], qi[kWQueue];
+    unsigned long long qp[kWQueue];
+    unsigned long long bar[2];
+    float tq[WT];             // phase A: remaining free-flight time of a queued particle
+    unsigned char st[WT];     // phase A: 0 hole, 1 moved only, 2 queued, 3 queued and colliding
+    unsigned char qcol[kWQueue];
+};
+
+// lane 0: copy the stay-test fields of tile t of A into stage b of the warp's shared memory (the slot count
+// rounded up to 4, which the buffers' slack covers, so that every copy is a multiple of 16 bytes from a
+// 16-byte aligned address)
+template <int WT>
+__device__ __forceinline__ void wtile_issue(const ParticleSoA<float>& A, int t, int n, WarpSmem<WT>& S, int b)
 {
-    const int base = t * kTile;
-    const int cnt4 = (min(kTile, n - base) + 3) & ~3;
+    const int base = t * WT;
+    const int cnt4 = (min(WT, n - base) + 3) & ~3;
     const uint32_t b4 = (uint32_t)cnt4 * 4u, b8 = (uint32_t)cnt4 * 8u;
-    mbar_expect_tx(bar, 7u * b4 + b8);
-    bulk_load(r.x, A.x + base, b4, bar);
-    bulk_load(r.y, A.y + base, b4, bar);
-    bulk_load(r.u, A.u + base, b4, bar);
-    bulk_load(r.v, A.v + base, b4, bar);
-    bulk_load(r.w, A.w + base, b4, bar);
-    bulk_load(r.m, A.m + base, b4, bar);
-    bulk_load(r.cell, A.cell + base, b4, bar);
-    bulk_load(r.pid, A.pid + base, b8, bar);
+    unsigned long long* bar = &S.bar[b];
+    mbar_expect_tx(bar, 5u * b4 + b8);
+    bulk_load(S.x[b], A.x + base, b4, bar);
+    bulk_load(S.y[b], A.y + base, b4, bar);
+    bulk_load(S.u[b], A.u + base, b4, bar);
+    bulk_load(S.v[b], A.v + base, b4, bar);
+    bulk_load(S.cell[b], A.cell + base, b4, bar);
+    bulk_load(S.pid[b], A.pid + base, b8, bar);
 }
 
-__global__ void __launch_bounds__(kTileThreads, 2) k_particles_tiled(const StepConsts K, const Dev d,
-                                                                     ParticleSoA<float> PA, ParticleSoA<float> PB,
-                                                                     const CellFaces<float>* __restrict__ cf,
-                                                                     PCell<float> pc, const long long* dstep)
+template <int WT, int MINB>
+__global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const StepConsts K, const Dev d,
+                                                                       ParticleSoA<float> PA, ParticleSoA<float> PB,
+                                                                       const CellFaces<float>* __restrict__ cf,
+                                                                       PCell<float> pc, const long long* dstep)
 {
-    extern __shared__ __align__(128) unsigned char tile_smem_raw[];
-    TileSmem& S = *reinterpret_cast<TileSmem*>(tile_smem_raw);
-    const int sel = *d.bufsel;
-    const ParticleSoA<float> A = sel ? PB : PA, B = sel ? PA : PB;
+    extern __shared__ __align__(128) unsigned char warp_smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpSmem<WT>& S = reinterpret_cast<WarpSmem<WT>*>(warp_smem_raw)[wid];
+    const ParticleSoA<float> A = *d.bufsel ? PB : PA;
     const bool sort_step = d.flags[0] != 0;
     const int nret = d.counts[0];
-    const int n = nret + d.counts[1], cap = d.counts[3];
-    const int ntiles = (n + kTile - 1) / kTile;
+    const int n = nret + d.counts[1];
+    const int ntiles = (n + WT - 1) / WT;
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
     const float s0 = float(ldexp(1.0, K.fx0)), s1 = float(ldexp(1.0, K.fx1)), s4 = float(ldexp(1.0, K.fx4));
     const float m2RTw = float(K.m2RTw), sigw = float(K.sig_w), ws = float(K.wall_specular);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0;
+    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0, n_kept = 0;
     int max_it = 0;
 
-    if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        S.abort = 0;
-        S.next = atomicAdd(d.counts + 5, 1);
-        if (S.next < ntiles) tile_issue(A, S.next, n, S.rec[0], &S.bar[0]);
-    }
-    __syncthreads();
-    int tile = S.next;
-    int b = 0;
-    uint32_t parity[2] = {0u, 0u};
-    uint32_t pending = tile < ntiles ? 1u : 0u;   // stages with copies in flight (bit per stage)
-    while (tile < ntiles) {
-        __syncthreads();   // every thread has read S.next; the other stage is free
-        if (tid == 0) {
-            S.qn = 0;
-            S.next = atomicAdd(d.counts + 5, 1);
-            if (S.next < ntiles) tile_issue(A, S.next, n, S.rec[b ^ 1], &S.bar[b ^ 1]);
-        }
-        if (!mbar_wait_bounded(&S.bar[b], parity[b])) S.abort = 1;
-        __syncthreads();
-        const int nxt = S.next;
-        if (nxt < ntiles) pending |= 1u << (b ^ 1);
-        if (S.abort) break;
-        parity[b] ^= 1u;
-        pending &= ~(1u << b);
-        TileRecords& R = S.rec[b];
-        const int base = tile * kTile, cnt = min(kTile, n - base);
-
-        // A: t_f and the stay test of the start cell for every particle of the tile
-#pragma unroll 1
-        for (int k = 0; k < kTilePer; ++k) {
-            const int j = k * kTileThreads + tid;
-            bool q = false;
-            if (j < cnt) {
-                const int i = base + j;
-                const int c = R.cell[j];
-                const float x = R.x[j], y = R.y[j], u = R.u[j], v = R.v[j];
-                const float dtc = pc.dt_(c);
-                float tr = dtc;
-                bool collide = false;
-                if (i >= nret) {
-                    tr = dtc;
-                } else {
-                    float U[1];
-                    Unif<float>::get(g, R.pid[j], DRAW_TF, 1, U);
-                    collide = U[0] > pc.emx_(c);
-                    if (collide) {
-                        const float a = -(pc.tau_(c) * dlog(U[0]));
-                        if (a < dtc) tr = a;
-                    }
-                }
-                const bool stays = stays_in(cf[c], d.nfc[c], -1, x, y, u, v, tr);
-                if (stays && !collide) {
-                    R.x[j] = x + u * tr;
-                    R.y[j] = y + v * tr;
-                    S.st[j] = 1;
-                } else {
-                    S.tr[j] = tr;
-                    S.st[j] = collide ? 3 : 2;
-                    q = true;
-                }
-            }
-            const unsigned qm = __ballot_sync(0xffffffffu, q);
-            if (qm) {
-                int q0 = 0;
-                if (lane == 0) q0 = atomicAdd(&S.qn, __popc(qm));
-                q0 = __shfl_sync(0xffffffffu, q0, 0);
-                if (q) S.queue[q0 + __popc(qm & lt_mask)] = (unsigned short)j;
-            }
-        }
-        __syncthreads();
-
-        // B: the queued particles' free flight and tallies
-        const int Q = S.qn;
-        for (int k = tid; k < Q; k += kTileThreads) {
-            const int j = S.queue[k];
-            float x = R.x[j], y = R.y[j], u = R.u[j], v = R.v[j], w = R.w[j], m = R.m[j];
-            int c = R.cell[j];
-            const unsigned long long pid = R.pid[j];
-            const bool collide = S.st[j] == 3;
+    // the queued particles e0 .. e0 + 31 (lanes past qn - e0 idle): free flight, tallies, records in place
+    auto fly_queue = [&](int e0, int qn) {
+        const int e = e0 + lane;
+        const bool act = e < qn;
+        int c = -1;
+        bool kept = false;
+        if (act) {
+            const int i = S.qi[e];
+            float x = S.qx[e], y = S.qy[e], u = S.qu[e], v = S.qv[e], w = A.w[i], m = A.m[i];
+            c = S.qc[e];
+            const unsigned long long pid = S.qp[e];
+            const bool collide = S.qcol[e] != 0;
             const int c0 = c;
             const float m0 = m, u0 = u, v0 = v, w0 = w;
             int it = 0;
-            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, ws, x, y, u, v, w, m, S.tr[j], c, -1,
+            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, ws, x, y, u, v, w, m, S.qt[e], c, -1,
                                    (uint64_t)pid, it, n_cross, n_hits);
             max_it = max(max_it, it);
             if (alive) {
@@ -1490,98 +1443,139 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_particles_tiled(const StepC
                 n_left++;
             }
             tally_move(d, s0, s1, s4, it, alive, collide, c0, m0, u0, v0, w0, c, m, u, v, w);
-            R.x[j] = x; R.y[j] = y; R.u[j] = u; R.v[j] = v; R.w[j] = w; R.m[j] = m;
-            R.cell[j] = c;
-            S.st[j] = (alive && !collide) ? 1 : 0;
+            kept = alive && !collide;
+            write_in_place(A, i, it == 0 && !collide, kept, x, y, u, v, w, m, c);
+            n_kept += kept ? 1 : 0;
         }
-        __syncthreads();
+        if (sort_step) count_runs(d, kept ? c : -1);
+    };
 
-        // C: survivors
+    if (lane == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // tiles are claimed one ahead of the copies: the claim of the tile after next is in flight while the warp
+    // works, so its latency is hidden (lane 0 holds the claims)
+    int tile = 0, ahead = 0;
+    if (lane == 0) {
+        tile = atomicAdd(d.counts + 5, 1);
+        ahead = atomicAdd(d.counts + 5, 1);
+        if (tile < ntiles) wtile_issue<WT>(A, tile, n, S, 0);
+    }
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    int b = 0, qn = 0;
+    uint32_t parity[2] = {0u, 0u};
+    uint32_t pending = tile < ntiles ? 1u : 0u;   // stages with copies in flight (bit per stage)
+    bool abort = false;
+    while (tile < ntiles) {
+        // start the next tile's copies into the other stage (released at the end of the last tile), claim the
+        // one after
+        const int nxt = __shfl_sync(0xffffffffu, ahead, 0);
+        if (lane == 0 && nxt < ntiles) {
+            wtile_issue<WT>(A, nxt, n, S, b ^ 1);
+            ahead = atomicAdd(d.counts + 5, 1);
+        }
+        if (nxt < ntiles) pending |= 1u << (b ^ 1);
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&S.bar[b], parity[b]))) {
+            abort = true;
+            break;
+        }
+        parity[b] ^= 1u;
+        pending &= ~(1u << b);
+        const int base = tile * WT, cnt = min(WT, n - base);
+
+        // A1: t_f and the stay test of the start cell for the whole tile; particles that only move are done
+#pragma unroll
+        for (int r = 0; r < WT / 32; ++r) {
+            const int j = r * 32 + lane;
+            const int c = j < cnt ? S.cell[b][j] : -1;
+            if (c >= 0) {
+                const int i = base + j;
+                const float4 cd = d.cst32[c];   // dt, e^{-x}, tau, face count
+                const float x = S.x[b][j], y = S.y[b][j], u = S.u[b][j], v = S.v[b][j];
+                const float dtc = cd.x;
+                float tr = dtc;
+                bool collide = false;
+                if (i < nret) {
+                    float U[1];
+                    Unif<float>::get(g, S.pid[b][j], DRAW_TF, 1, U);
+                    collide = U[0] > cd.y;
+                    if (collide) {
+                        const float a = -(cd.z * dlog(U[0]));
+                        if (a < dtc) tr = a;
+                    }
+                }
+                const bool stays = stays_in_start(cf[c], __float_as_int(cd.w), x, y, u, v, tr);
+                if (stays && !collide) {
+                    A.x[i] = x + u * tr;
+                    A.y[i] = y + v * tr;
+                    S.st[j] = 1;
+                    n_kept++;
+                } else {
+                    S.tq[j] = tr;
+                    S.st[j] = collide ? 3 : 2;
+                }
+            } else if (j < cnt) {
+                S.st[j] = 0;
+            }
+        }
+        __syncwarp();
+        // A2: queue the others, 32 at a time; B: whenever 32 are queued, fly them together
+#pragma unroll 1
+        for (int r = 0; r < WT / 32; ++r) {
+            const int j = r * 32 + lane;
+            const int stj = j < cnt ? S.st[j] : 0;
+            const bool q = stj >= 2;
+            const unsigned qmask = __ballot_sync(0xffffffffu, q);
+            if (!qmask) continue;
+            if (q) {
+                const int e = qn + __popc(qmask & lt_mask);
+                S.qx[e] = S.x[b][j]; S.qy[e] = S.y[b][j]; S.qu[e] = S.u[b][j]; S.qv[e] = S.v[b][j];
+                S.qt[e] = S.tq[j]; S.qc[e] = S.cell[b][j]; S.qi[e] = base + j; S.qp[e] = S.pid[b][j];
+                S.qcol[e] = stj == 3 ? 1 : 0;
+            }
+            qn += __popc(qmask);
+            __syncwarp();
+            if (qn >= 32) {
+                fly_queue(qn - 32, qn);
+                qn -= 32;
+                __syncwarp();
+            }
+        }
+        // sort steps: the tile's particles that only moved, per cell (the queued ones count when they fly)
         if (sort_step) {
 #pragma unroll 1
-            for (int k = 0; k < kTilePer; ++k) {
-                const int j = k * kTileThreads + tid;
-                int key = -1;
-                if (j < cnt) {
-                    const int i = base + j;
-                    key = S.st[j] == 1 ? R.cell[j] : -1;
-                    B.x[i] = R.x[j]; B.y[i] = R.y[j]; B.u[i] = R.u[j]; B.v[i] = R.v[j]; B.w[i] = R.w[j];
-                    B.m[i] = R.m[j];
-                    B.cell[i] = key;
-                    B.pid[i] = R.pid[j];
-                }
-                // survivors per cell for the counting sort, one atomic per run of equal cell in the warp
-                const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-                int start = (lane == 0 || prev != key) ? lane : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, start, o);
-                    if (lane >= o) start = max(start, t);
-                }
-                const int nx = __shfl_down_sync(0xffffffffu, key, 1);
-                if ((lane == 31 || nx != key) && key >= 0) atomicAdd(d.cnt + key, lane - start + 1);
-            }
-        } else {
-            // survivors per (round k, warp) chunk, their exclusive offsets in tile order, one slot range per tile
-            unsigned km[kTilePer];
-#pragma unroll
-            for (int k = 0; k < kTilePer; ++k) {
-                const int j = k * kTileThreads + tid;
-                km[k] = __ballot_sync(0xffffffffu, j < cnt && S.st[j] == 1);
-                if (lane == 0) S.chunk_off[k * (kTileThreads / 32) + wid] = __popc(km[k]);
-            }
-            __syncthreads();
-            constexpr int nch = kTilePer * kTileThreads / 32;
-            if (wid == 0) {
-                int v = lane < nch ? S.chunk_off[lane] : 0;
-                int incl = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                if (lane < nch) S.chunk_off[lane] = incl - v;
-                if (lane == 31) S.base = incl ? atomicAdd(d.counts + 2, incl) : 0;
-            }
-            __syncthreads();
-            const int sbase = S.base;
-#pragma unroll
-            for (int k = 0; k < kTilePer; ++k) {
-                const int j = k * kTileThreads + tid;
-                if (!((km[k] >> lane) & 1u)) continue;
-                // the ghost sources on the second stream take slots of the same buffer meanwhile
-                const int slot = sbase + S.chunk_off[k * (kTileThreads / 32) + wid] + __popc(km[k] & lt_mask);
-                if (slot >= cap) {
-                    atomicOr(d.err, ERR_CAPACITY);
-                } else {
-                    B.x[slot] = R.x[j]; B.y[slot] = R.y[j]; B.u[slot] = R.u[j]; B.v[slot] = R.v[j];
-                    B.w[slot] = R.w[j]; B.m[slot] = R.m[j];
-                    B.cell[slot] = R.cell[j];
-                    B.pid[slot] = R.pid[j];
-                }
+            for (int r = 0; r < WT / 32; ++r) {
+                const int j = r * 32 + lane;
+                count_runs(d, (j < cnt && S.st[j] == 1) ? S.cell[b][j] : -1);
             }
         }
-        // this thread's generic-proxy accesses of the stage come before the bulk copy that refills it (issued by
-        // thread 0 after the barrier at the top of the loop)
+        // this lane's generic-proxy accesses of the stage come before the bulk copy that refills it (issued by
+        // lane 0 at the top of the next iteration)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
         tile = nxt;
         b ^= 1;
     }
-    if (S.abort) {
+    if (abort) {
         // a tile's copies did not arrive in time: report it, and give the copies still in flight their own
-        // bounded wait before the CTA's shared memory is released
-        if (tid == 0) {
+        // bounded wait before the warp's shared memory is released
+        if (lane == 0) {
             atomicOr(d.err, ERR_LIMIT);
             for (int q = 0; q < 2; ++q)
                 if (pending & (1u << q)) (void)mbar_wait_bounded(&S.bar[q], parity[q]);
         }
         return;
     }
+    if (qn > 0) fly_queue(0, qn);
     for (int o = 16; o > 0; o >>= 1) {
         n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
         n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
         n_removed += __shfl_xor_sync(0xffffffffu, n_removed, o);
         n_left += __shfl_xor_sync(0xffffffffu, n_left, o);
+        n_kept += __shfl_xor_sync(0xffffffffu, n_kept, o);
         max_it = max(max_it, __shfl_xor_sync(0xffffffffu, max_it, o));
     }
     if (lane == 0) {
@@ -1590,6 +1584,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_particles_tiled(const StepC
         if (n_cross) atomicAdd(d.stats + 5, n_cross);
         if (n_hits) atomicAdd(d.stats + 6, n_hits);
         if (max_it) atomicMax(d.stats + 7, (unsigned long long)max_it);
+        if (n_kept) atomicAdd(d.counts + 2, (int)n_kept);
     }
 }
 
@@ -1643,8 +1638,9 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
     if (j >= K.n_inj) return;
     const int N = d.inj_n[j];
     if (N == 0) return;
-    const int sel = *d.bufsel;
-    const ParticleSoA<T> B = sel ? PA : PB;   // where the transport kernel writes this step's survivors
+    // the entering particles that survive are appended past the step's slots of the buffer that holds the
+    // step's particles (the transport kernel updates slots below n in place meanwhile)
+    const ParticleSoA<T> B = *d.bufsel ? PB : PA;
     const bool sort_step = d.flags[0] != 0;
     const int n = d.counts[4], cap = d.counts[3];
     const int f = d.inj_face[j], L = d.fL[f], kin = d.inj_k[j];
@@ -1702,14 +1698,17 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
                 }
             }
         }
-        // survivors, as in the transport kernel (slots beyond the capacity are an error)
+        // survivors (slots beyond the capacity are an error)
         const unsigned km = __ballot_sync(0xffffffffu, kept);
         if (!km) continue;
         int slot0 = 0;
-        if (lane == 0) slot0 = sort_step ? atomicAdd(d.counts + 7, __popc(km)) : atomicAdd(d.counts + 2, __popc(km));
+        if (lane == 0) {
+            slot0 = atomicAdd(d.counts + 7, __popc(km));
+            atomicAdd(d.counts + 2, __popc(km));
+        }
         slot0 = __shfl_sync(0xffffffffu, slot0, 0);
         if (kept) {
-            const int jj = (sort_step ? n : 0) + slot0 + __popc(km & lt_mask);
+            const int jj = n + slot0 + __popc(km & lt_mask);
             if (jj >= cap) {
                 atomicOr(d.err, ERR_CAPACITY);
             } else {
@@ -1737,21 +1736,21 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
 }
 
 // --------------------------------------------------------------------- a7: counting sort
-// sort steps only: counting sort of the survivors by cell, from the staging buffer back into the buffer that
-// held this step's particles (which then stays the current one)
+// sort steps only: counting sort of the survivors by cell (holes dropped), from the buffer that holds the
+// step's particles into the other one, which becomes the current one at the end of the step
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB)
 {
     if (!d.flags[0]) return;
     const int sel = *d.bufsel;
     const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
-    const int n = d.counts[4] + d.counts[7];   // the step's particles, then those that entered from ghosts
+    const int n = d.counts[4] + d.counts[7];   // the step's slots, then those of particles that entered from ghosts
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = B.cell[i];
+        const int c = A.cell[i];
         if (c < 0) continue;
         const int slot = d.off[c] + atomicAdd(d.cur + c, 1);
-        A.x[slot] = B.x[i]; A.y[slot] = B.y[i]; A.u[slot] = B.u[i]; A.v[slot] = B.v[i]; A.w[slot] = B.w[i];
-        A.m[slot] = B.m[i]; A.cell[slot] = c; A.pid[slot] = B.pid[i];
+        B.x[slot] = A.x[i]; B.y[slot] = A.y[i]; B.u[slot] = A.u[i]; B.v[slot] = A.v[i]; B.w[slot] = A.w[i];
+        B.m[slot] = A.m[i]; B.cell[slot] = c; B.pid[slot] = A.pid[i];
     }
 }
 
@@ -1845,9 +1844,15 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
     for (int b = 0; b < (int)gridDim.x; ++b)
         for (int q = 0; q < 4; ++q) s[q] += __ldcg(d.res_part + 4 * b + q);
     for (int q = 0; q < 4; ++q) d.res[q] = sqrt(s[q]);
+    // the next step's slots: the particles and holes of this step and the entered ones; after a counting sort
+    // the survivors alone, in the other buffer
     const int kept = __ldcg(d.counts + 2);
-    d.counts[0] = kept;
-    if (!d.flags[0]) *d.bufsel = 1 - *d.bufsel;
+    if (d.flags[0]) {
+        d.counts[0] = kept;
+        *d.bufsel = 1 - *d.bufsel;
+    } else {
+        d.counts[0] = __ldcg(d.counts + 4) + __ldcg(d.counts + 7);
+    }
     *dstep += 1;
     d.stats[0] = (unsigned long long)*dstep;
     d.stats[1] = (unsigned long long)kept;
@@ -1968,6 +1973,34 @@ template <typename T> cudaError_t alloc_particles(Ctx& ctx, ParticleSoA<T>& P, s
     return cudaSuccess;
 }
 
+// the warp-staged transport kernel: tile WT = ctx.k.chunk (128 particles per warp tile, else 64), CTAs per SM =
+// grid_particles / sms (4, 5 or 6 with 128-particle tiles, 4 or 6 with 64: the instantiation compiled for that
+// many resident CTAs)
+template <int WT, int MINB> void launch_warp_variant(Ctx& ctx, cudaStream_t s, const PCell<float>& pc)
+{
+    const StepConsts& K = ctx.k;
+    Dev& d = ctx.d;
+    k_particles_warp<WT, MINB><<<MINB * ctx.sms, kWWarps * 32, kWWarps * sizeof(WarpSmem<WT>), s>>>(
+        K, d, d.pa32, d.pb32, d.cf32, pc, d.dstep);
+}
+void launch_particles_warp(Ctx& ctx, cudaStream_t s, const PCell<float>& pc)
+{
+    const int bps = ctx.grid_particles / ctx.sms;
+    if (ctx.k.chunk == 128) {
+        if (bps >= 6) launch_warp_variant<128, 6>(ctx, s, pc);
+        else if (bps == 5) launch_warp_variant<128, 5>(ctx, s, pc);
+        else launch_warp_variant<128, 4>(ctx, s, pc);
+    } else {
+        if (bps >= 6) launch_warp_variant<64, 6>(ctx, s, pc);
+        else launch_warp_variant<64, 4>(ctx, s, pc);
+    }
+}
+template <int WT, int MINB> cudaError_t warp_variant_attr()
+{
+    return cudaFuncSetAttribute(k_particles_warp<WT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kWWarps * sizeof(WarpSmem<WT>)));
+}
+
 }  // namespace
 
 // the per-step kernel sequence (enqueued on s; capturable)
@@ -2019,8 +2052,8 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     else k_sample<double><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
     mark(3, s);
     mark(4, s);
-    if (K.prec == 0 && ctx.transport == kTransportTiled)
-        k_particles_tiled<<<2 * ctx.sms, kTileThreads, sizeof(TileSmem), s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
+    if (K.prec == 0 && ctx.transport == kTransportStaged)
+        launch_particles_warp(ctx, s, pc32);
     else if (K.prec == 0) k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
     else k_particles<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64, d.cf64, pc64, d.dstep);
     mark(5, s);
@@ -2437,7 +2470,7 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         K.sort_every = UGKWP_SORT_EVERY;
         K.chunk = UGKWP_CHUNK;
         CK(dalloc(ctx, &d.tau32, C)); CK(dalloc(ctx, &d.dt32, C)); CK(dalloc(ctx, &d.mnew32, C));
-        CK(dalloc(ctx, &d.emx32, C));
+        CK(dalloc(ctx, &d.emx32, C)); CK(dalloc(ctx, &d.cst32, C));
         if (opts->record_faces && !K.wave_only) CK(dalloc(ctx, &d.frec, 4 * (size_t)F));
         if (K.order == 2) CK(dalloc(ctx, &d.grad, 16 * (size_t)C));
         CK(dalloc(ctx, &d.samp32, 3 * C));
@@ -2449,9 +2482,15 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         ctx.grid_particles = sms * 4;
         ctx.sms = sms;
-        ctx.transport = K.prec == 0 ? kTransportTiled : kTransportWarp;
-        if (K.prec == 0)
-            CK(cudaFuncSetAttribute(k_particles_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem)));
+        ctx.transport = K.prec == 0 ? kTransportStaged : kTransportWarp;
+        if (K.prec == 0) {
+            ctx.k.chunk = 128;
+            CK((warp_variant_attr<64, 4>()));
+            CK((warp_variant_attr<64, 6>()));
+            CK((warp_variant_attr<128, 4>()));
+            CK((warp_variant_attr<128, 5>()));
+            CK((warp_variant_attr<128, 6>()));
+        }
         if (!K.wave_only) {
             if (K.prec == 0) { CK(alloc_particles(ctx, d.pa32, ctx.capacity)); CK(alloc_particles(ctx, d.pb32, ctx.capacity)); }
             else { CK(alloc_particles(ctx, d.pa64, ctx.capacity)); CK(alloc_particles(ctx, d.pb64, ctx.capacity)); }
@@ -2623,14 +2662,15 @@ ugkwp_status ugkwp_stats(ugkwp_ctx* h, int64_t* out)
     return st;
 }
 
+// particles alive (the slots of the particle buffer also hold holes between counting sorts)
 int64_t ugkwp_num_particles(ugkwp_ctx* h)
 {
     if (!h) return -1;
     Ctx& ctx = h->c;
-    int n = 0;
-    if (cudaMemcpyAsync(&n, ctx.d.counts, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream) != cudaSuccess) return -1;
+    unsigned long long n = 0;
+    if (cudaMemcpyAsync(&n, ctx.d.stats + 1, sizeof n, cudaMemcpyDeviceToHost, ctx.stream) != cudaSuccess) return -1;
     if (cudaStreamSynchronize(ctx.stream) != cudaSuccess) return -1;
-    return n;
+    return (int64_t)n;
 }
 
 ugkwp_status ugkwp_get_particles(ugkwp_ctx* h, int64_t cap, uint64_t* pid, int32_t* cell, double* x, double* y,
@@ -2642,27 +2682,42 @@ ugkwp_status ugkwp_get_particles(ugkwp_ctx* h, int64_t cap, uint64_t* pid, int32
     if (n < 0) return fail(ctx, UGKWP_ECUDA, "reading the particle count");
     if (cap < n) return fail(ctx, UGKWP_EINVAL, "host arrays too short");
     if (n == 0) return UGKWP_OK;
-    double* tmp = nullptr;
-    int sel = 0;
+    int slots = 0, sel = 0;
+    CK(cudaMemcpyAsync(&slots, ctx.d.counts, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaMemcpyAsync(&sel, ctx.d.bufsel, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
-    CK(cudaMalloc(&tmp, sizeof(double) * 6 * n));
+    // every slot to the host, then the particles (cell >= 0) in slot order
+    const size_t ns = (size_t)slots;
+    std::vector<double> hv(6 * ns);
+    std::vector<uint64_t> hp(ns);
+    std::vector<int32_t> hc(ns);
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, sizeof(double) * 6 * ns));
     if (ctx.k.prec == 0) {
         const ParticleSoA<float>& A = sel ? ctx.d.pb32 : ctx.d.pa32;
-        k_get_particles<float><<<nblk(n, 256), 256, 0, ctx.stream>>>(A, (int)n, tmp);
-        CK(cudaMemcpyAsync(pid, A.pid, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
-        CK(cudaMemcpyAsync(cell, A.cell, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
+        k_get_particles<float><<<nblk(slots, 256), 256, 0, ctx.stream>>>(A, slots, tmp);
+        CK(cudaMemcpyAsync(hp.data(), A.pid, sizeof(uint64_t) * ns, cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaMemcpyAsync(hc.data(), A.cell, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, ctx.stream));
     } else {
         const ParticleSoA<double>& A = sel ? ctx.d.pb64 : ctx.d.pa64;
-        k_get_particles<double><<<nblk(n, 256), 256, 0, ctx.stream>>>(A, (int)n, tmp);
-        CK(cudaMemcpyAsync(pid, A.pid, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
-        CK(cudaMemcpyAsync(cell, A.cell, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx.stream));
+        k_get_particles<double><<<nblk(slots, 256), 256, 0, ctx.stream>>>(A, slots, tmp);
+        CK(cudaMemcpyAsync(hp.data(), A.pid, sizeof(uint64_t) * ns, cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaMemcpyAsync(hc.data(), A.cell, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, ctx.stream));
     }
-    double* dst[6] = {x, y, u, v, w, m};
-    for (int k = 0; k < 6; ++k)
-        CK(cudaMemcpyAsync(dst[k], tmp + (size_t)k * n, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(hv.data(), tmp, sizeof(double) * 6 * ns, cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
     cudaFree(tmp);
+    double* dst[6] = {x, y, u, v, w, m};
+    int64_t o = 0;
+    for (size_t i = 0; i < ns; ++i) {
+        if (hc[i] < 0) continue;
+        if (o >= n) return fail(ctx, UGKWP_ECUDA, "more live particle slots than the particle count");
+        pid[o] = hp[i];
+        cell[o] = hc[i];
+        for (int k = 0; k < 6; ++k) dst[k][o] = hv[(size_t)k * ns + i];
+        ++o;
+    }
+    if (o != n) return fail(ctx, UGKWP_ECUDA, "fewer live particle slots than the particle count");
     return UGKWP_OK;
 }
 
@@ -2681,7 +2736,9 @@ ugkwp_status ugkwp_set_state(ugkwp_ctx* h, int64_t step, const double* W, const 
     long long st = step;
     CK(cudaMemcpyAsync(ctx.d.dstep, &st, sizeof st, cudaMemcpyHostToDevice, ctx.stream));
     int n32 = (int)np, zero = 0;
+    const unsigned long long alive = (unsigned long long)np;
     CK(cudaMemcpyAsync(ctx.d.counts, &n32, sizeof(int), cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(ctx.d.stats + 1, &alive, sizeof alive, cudaMemcpyHostToDevice, ctx.stream));
     CK(cudaMemcpyAsync(ctx.d.bufsel, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx.stream));
     if (np > 0) {
         double* tmp = nullptr;
@@ -3068,10 +3125,10 @@ namespace {
 ugkwp_status apply_launch(Ctx& ctx, int chunk, int bps, int sort_every, int transport)
 {
     if (transport) {
-        if (transport != kTransportWarp && transport != kTransportTiled)
-            return fail(ctx, UGKWP_EINVAL, "transport kernel: 1 (warp-chunked) or 2 (tile-staged)");
-        if (transport == kTransportTiled && ctx.k.prec != 0)
-            return fail(ctx, UGKWP_EINVAL, "the tile-staged transport kernel serves the production precision only");
+        if (transport != kTransportWarp && transport != kTransportStaged)
+            return fail(ctx, UGKWP_EINVAL, "transport kernel: 1 (warp-chunked) or 2 (warp-staged)");
+        if (transport == kTransportStaged && ctx.k.prec != 0)
+            return fail(ctx, UGKWP_EINVAL, "the warp-staged transport kernel serves the production precision only");
         ctx.transport = transport;
     }
     if (chunk) {
@@ -3128,7 +3185,13 @@ extern "C" ugkwp_status ugkwp_autotune(ugkwp_ctx* h, int32_t steps, int32_t* bes
     struct Cand { int chunk, bps, sort, transport; };
     std::vector<Cand> cands;
     for (int so : {8, 16, 32}) {
-        if (ctx.k.prec == 0) cands.push_back({0, 0, so, kTransportTiled});
+        if (ctx.k.prec == 0) {
+            cands.push_back({64, 4, so, kTransportStaged});
+            cands.push_back({64, 6, so, kTransportStaged});
+            cands.push_back({128, 4, so, kTransportStaged});
+            cands.push_back({128, 5, so, kTransportStaged});
+            cands.push_back({128, 6, so, kTransportStaged});
+        }
         for (int ch : {128, 256})
             for (int bp : {4, 6, 8}) cands.push_back({ch, bp, so, kTransportWarp});
     }

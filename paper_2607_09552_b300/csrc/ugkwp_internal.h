@@ -12,7 +12,7 @@ constexpr int kMaxIters = 256;   // face crossings + wall hits per particle per 
 constexpr int kMaxNew = 2047;    // new particles per cell per step (11-bit index inside the particle id)
 constexpr double kR = 0.5;       // gas constant in the reference units
 constexpr double kRhoFloor = 1e-12;   // vacuum floor of the cell density (units of rho_inf)
-constexpr int kTransportWarp = 1, kTransportTiled = 2;   // transport kernels (launch parameter)
+constexpr int kTransportWarp = 1, kTransportStaged = 2;   // transport kernels (launch parameter)
 
 // device error word bits
 enum : int { ERR_LIMIT = 1, ERR_NONPHYS = 2, ERR_OVERFLOW = 4, ERR_CAPACITY = 8 };
@@ -90,8 +90,10 @@ struct Dev {
     // particles: A holds the cell-sorted retained set between steps, B is the staging buffer
     ParticleSoA<float> pa32, pb32;
     ParticleSoA<double> pa64, pb64;
-    float *tau32, *dt32, *mnew32, *samp32;   // particle-precision copies of tau, dt, m_new, (U^h, V^h, R T^h),
+    float *tau32, *dt32, *mnew32, *samp32;   // particle-precision copies of tau, dt, m_new, (U_i, V_i, R T_i),
     float* emx32;                            // e^{-dt/tau}
+    float4* cst32;                           // per cell: (dt, e^{-dt/tau}, tau, face count as int bits), the
+                                             // stay test's cell data in one 16-byte load
     long long* dstep;                  // step counter (Philox counter word)
     int* bufsel;                       // which particle buffer (A: 0, B: 1) holds the current particles
     int* flags;                        // [0]: this step sorts the particles by cell
@@ -111,7 +113,7 @@ struct Ctx {
     Dev d{};
     int ni = 0, nj = 0, periodic_j = 0, capacity = 0, res_blocks = 0, grid_particles = 0, sms = 148;
     int device = -1;                             // the device current at creation (owns every allocation)
-    int transport = 1;                           // transport kernel: kTransportWarp or kTransportTiled
+    int transport = 1;                           // transport kernel: kTransportWarp or kTransportStaged
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;              // wave fluxes, overlapped with the particle kernels
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

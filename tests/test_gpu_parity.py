@@ -375,13 +375,13 @@ def test_batched_graph_equals_individual_runs(cuda_lib):
 
 
 def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
-    """The transport kernel (tile-staged, the production default, against warp-chunked), chunk size, blocks per
+    """The transport kernel (warp-staged, the production default, against warp-chunked), chunk size, blocks per
     SM and the sort interval reorder work and particles only: the state is the same bit for bit (particles
     compared as sets), also across an autotuning pass that steps the run."""
     case = CASES["cylinder"]
     a = cuda_lib.Solver(case, precision=0, use_graph=True)
     b = cuda_lib.Solver(case, precision=0, use_graph=True)
-    assert a.launch() == [256, 4, 8, 2]
+    assert a.launch() == [128, 4, 8, 2]
     b.set_launch(128, 2, 16, 1)
     assert b.launch() == [128, 2, 16, 1]
     a.step(21)
@@ -415,3 +415,27 @@ def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
     with pytest.raises(cuda_lib.UgkwpError):
         f.set_launch(0, 0, 0, 2)
     f.close()
+
+
+@pytest.mark.parametrize("name", ["cylinder", "plate", "shock1d", "cylinder_dense"])
+@pytest.mark.parametrize("tile,bps,sort", [(64, 4, 8), (64, 6, 16), (128, 4, 8), (128, 6, 32)])
+def test_warp_staged_transport_equals_warp_chunked(cuda_lib, name, tile, bps, sort):
+    """The warp-staged transport kernel (per-warp bulk-copied tiles, crossing particles queued and flown 32 at a
+    time, records updated in place) gives the state of the warp-chunked kernel bit for bit (particles compared as
+    sets) over steps that include counting-sort steps, with and without graph replay."""
+    case = CASES[name]
+    a = cuda_lib.Solver(case, precision=0, use_graph=True)
+    a.set_launch(256, 4, 8, 1)
+    b = cuda_lib.Solver(case, precision=0, use_graph=(bps == 6))
+    b.set_launch(tile, bps, sort, 2)
+    assert b.launch() == [tile, bps, sort, 2]
+    a.step(19)
+    b.step(19)
+    assert np.array_equal(a.field()[0], b.field()[0])
+    assert_particles_equal(a.particles(), b.particles())
+    ta, tb = a.tallies(), b.tallies()
+    for k in ("wm", "wpl", "wret", "cross", "wall"):
+        assert np.array_equal(ta[k], tb[k]), k
+    assert np.array_equal(a.stats()[:8], b.stats()[:8])
+    a.close()
+    b.close()
