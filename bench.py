@@ -271,7 +271,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": BYTES_PER_PARTICLE_STEP * per_launch,
                          "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
-            "gpu_launches": gpu_launches_per_step(case) * args.steps,
+            "gpu_launches": gpu_launches_per_step(case, args.order) * args.steps,
             "wall_s_timed": t_wall,
             "last_step": {"particles": int(s1[1]), "new": int(s1[2]), "collided_removed": int(s1[3]),
                           "left_domain": int(s1[4]), "face_crossings": int(s1[5]), "wall_hits": int(s1[6])},
@@ -326,17 +326,21 @@ def reduce_over_ranks(ms: float, work: float, world: int, device: str):
     return float(t[0]), float(w[0])
 
 
-def gpu_launches_per_step(case):
-    # begin-step, decompose, 3 scan kernels, sample, particles, 2 wave-flux kernels, 3 scan kernels and the
-    # scatter (they return at once except on sort steps), update; the ghost-source parameter and particle
-    # kernels when the mesh has far-field or fixed faces; the heat-flux tally when Pr != 1
+def gpu_launches_per_step(case, order=1):
+    # begin-step, decompose, 3 scan kernels, sample, particles, the wave fluxes (first order, production: the
+    # per-cell FP32 preparation, the wall-cell faces when the mesh has walls, the FP32 faces and the FP64
+    # retry; order 2: the gradients and one FP64 kernel), 3 scan kernels and the scatter (they return at once
+    # except on sort steps), update; the ghost-source parameter and particle kernels when the mesh has
+    # far-field or fixed faces; the heat-flux tally when Pr != 1
     m = case.mesh
     if hasattr(m, "cells"):
         tags = list(m.boundary[:, 2])
     else:
         tags = list(m.bc_imin) + list(m.bc_imax) + list(m.bc_jmin) + list(m.bc_jmax)
     ghosts = any(t in (wl.BC_FARFIELD, wl.BC_FIXED) for t in tags)
-    return 13 + (2 if ghosts else 0) + (1 if case.Pr != 1.0 else 0)
+    walls = any(t == wl.BC_WALL for t in tags)
+    flux = 2 if order == 2 else 3 + (1 if walls else 0)
+    return 11 + flux + (2 if ghosts else 0) + (1 if case.Pr != 1.0 else 0)
 
 
 def run_e2e(args, solver, stream):

@@ -1772,9 +1772,10 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
             const int f = meta & 0xffffff;
             const bool isL = (meta >> 29) & 1;
             const double s = d.fs[f];
+            // one fused multiply-add per term (B300's FP64 pipe is narrow); the sum stays FP64
             for (int q = 0; q < 4; ++q) {
-                const double tt = d.flux[4 * (size_t)f + q] * s;
-                acc[q] += isL ? tt : -tt;
+                const double fq = d.flux[4 * (size_t)f + q];
+                acc[q] = __fma_rn(isL ? fq : -fq, s, acc[q]);
             }
         }
         // FP64 throughout; the divisions by Omega_i and dt_i are multiplications by their reciprocals
@@ -1803,8 +1804,10 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
         }
         // retained tally of this step (the next step's W^p): W^{p,+} minus the collided particles that stay
         for (int k = 0; k < 5; ++k) d.wrt[5 * c + k] = d.wpl[5 * c + k] - d.wcol[5 * c + k];
-        const double chi = (((double)d.wpl[5 * c] * sc[0]) * rvol) / W[0];
-        d.chi_ema[c] = *dstep == 0 ? chi : d.chi_ema[c] + (2.0 / 1001.0) * (chi - d.chi_ema[c]);
+        // particle mass fraction chi^p and its EMA (a diagnostic: FP32 arithmetic)
+        const float chi = (((float)d.wpl[5 * c] * (float)sc[0]) * (float)rvol) / (float)W[0];
+        const float ce = (float)d.chi_ema[c];
+        d.chi_ema[c] = *dstep == 0 ? chi : ce + (2.0f / 1001.0f) * (chi - ce);
     } else if (t < K.C + K.nwall) {
         const int iw = t - K.C;
         const int f = d.wall_face[iw], c = d.fL[f];
@@ -1960,7 +1963,7 @@ template <typename P> cudaError_t dalloc(Ctx& ctx, P** p, size_t n)
     return cudaSuccess;
 }
 
-// 64 elements of slack past the capacity: the tile-staged transport kernel copies a tile's last records in
+// 64 elements of slack past the capacity: the warp-staged transport kernel copies a tile's last records in
 // groups of four (16-byte bulk copies) and may read up to three elements past the particle count
 template <typename T> cudaError_t alloc_particles(Ctx& ctx, ParticleSoA<T>& P, size_t cap)
 {
@@ -2455,13 +2458,18 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
             CK(cudaMemcpyAsync(ff.data(), d.face_f64, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
             CK(cudaMemcpyAsync(fb.data(), d.fR, sizeof(int) * F, cudaMemcpyDeviceToHost, ctx.stream));
             CK(cudaStreamSynchronize(ctx.stream));
-            std::vector<int> list;
+            std::vector<int> list, mix;
             for (int f = 0; f < F; ++f) {
                 if (K.prec == 1) ff[f] = 1;
                 if (K.prec == 1) list.push_back(f);
+                else if (ff[f]) mix.push_back(f);
             }
             K.n_f64 = (int)list.size();
+            K.n_mix = (int)mix.size();
             CK(dalloc(ctx, &d.f64list, std::max(K.n_f64, 1)));
+            CK(dalloc(ctx, &d.mixlist, std::max(K.n_mix, 1)));
+            if (K.n_mix)
+                CK(cudaMemcpyAsync(d.mixlist, mix.data(), sizeof(int) * K.n_mix, cudaMemcpyHostToDevice, ctx.stream));
             CK(cudaMemcpyAsync(d.face_f64, ff.data(), sizeof(int) * F, cudaMemcpyHostToDevice, ctx.stream));
             if (K.n_f64)
                 CK(cudaMemcpyAsync(d.f64list, list.data(), sizeof(int) * K.n_f64, cudaMemcpyHostToDevice, ctx.stream));
@@ -2471,6 +2479,10 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         K.chunk = UGKWP_CHUNK;
         CK(dalloc(ctx, &d.tau32, C)); CK(dalloc(ctx, &d.dt32, C)); CK(dalloc(ctx, &d.mnew32, C));
         CK(dalloc(ctx, &d.emx32, C)); CK(dalloc(ctx, &d.cst32, C));
+        if (K.prec == 0) {
+            CK(dalloc(ctx, &d.w32, C)); CK(dalloc(ctx, &d.wh32, C)); CK(dalloc(ctx, &d.dp32, C));
+            CK(dalloc(ctx, &d.co32, 8 * (size_t)C));
+        }
         if (opts->record_faces && !K.wave_only) CK(dalloc(ctx, &d.frec, 4 * (size_t)F));
         if (K.order == 2) CK(dalloc(ctx, &d.grad, 16 * (size_t)C));
         CK(dalloc(ctx, &d.samp32, 3 * C));

@@ -171,12 +171,12 @@ __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], co
 // g (a . psi) is the derivative of the Maxwellian in the direction dW, so the remainder's flux is the
 // directional derivative of the half-range flux rho <psi u_n>_half. With FP32 moments (R = float) it is
 // evaluated in that form, from the primitive perturbation dp = (d rho, dU, dV, d theta), theta = R T, formed in
-// FP64 (prim_perturbation): the moment solve in the absolute frame cancels terms of order |U|^2 / RT (about
-// 300 at Ma 20), which FP32 cannot afford. The half-range moments M_k = <u^k>_half obey dM_k/dU = k M_{k-1} and
+// FP64 once per cell (prim_perturbation, k_flux_prep) and rotated into the face frame: the moment solve in the
+// absolute frame cancels terms of order |U|^2 / RT (about 300 at Ma 20), which FP32 cannot afford. The half-range moments M_k = <u^k>_half obey dM_k/dU = k M_{k-1} and
 // dM_k/dtheta = k (k - 1) / 2 M_{k-2} (k >= 1, 2), dM_1/dtheta = +-g(0) / 2 (+ for u > 0).
 template <typename R, typename C>
 __device__ __forceinline__ void wave_part(const Prim<R>& p, const Mom<R>& m, bool up, const R W[4], const R Wh[4],
-                                          const double dp[4], C fr, C fd, const R* dh, C cs, C F[4])
+                                          const R dp[4], C fr, C fd, const R* dh, C cs, C F[4])
 {
     const R* Mu = up ? m.up : m.um;
     R t[4], dw[4], a[4];
@@ -184,7 +184,7 @@ __device__ __forceinline__ void wave_part(const Prim<R>& p, const Mom<R>& m, boo
 #pragma unroll
     for (int k = 0; k < 4; ++k) F[k] += fr * C(Wh[0] * t[k]);
     if (sizeof(R) == 4) {
-        const R dr = R(dp[0]), dU = R(dp[1]), dV = R(dp[2]), dth = R(dp[3]);
+        const R dr = dp[0], dU = dp[1], dV = dp[2], dth = dp[3];
         const R th = m.xi2, V = p.V, s = V * V + R(2) * th, hg = (up ? R(0.5) : R(-0.5)) * m.g0;
         t[0] = dr * Mu[1] + p.rho * (Mu[0] * dU + hg * dth);
         t[1] = dr * Mu[2] + p.rho * (R(2) * Mu[1] * dU + Mu[0] * dth);
@@ -232,8 +232,8 @@ __device__ __forceinline__ void prim_perturbation(const double W[4], const doubl
 // weighted with csL, csR (order 2). Returns false if a side state is not a valid Maxwellian in precision R
 // (the caller then uses FP64).
 template <typename R, typename C>
-__device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], const double dpL[4],
-                          const double dpR[4], C fdL, C fdR, const C cL[3], const C cR[3], C frL, C frR, R dL, R dR,
+__device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], const R dpL[4],
+                          const R dpR[4], C fdL, C fdR, const C cL[3], const C cR[3], C frL, C frR, R dL, R dR,
                           R Pr, const R WLc[4], const R WRc[4], const R* dhL, const R* dhR, C csL, C csR, C F[4])
 {
     Prim<R> pL, pR, p0;
@@ -259,7 +259,7 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
 // (as in face_flux: weights frL and fdL), the outgoing wall Maxwellian at T_w with the density that makes the
 // wave mass flux zero
 template <typename R, typename C>
-__device__ bool wall_flux(const R WL[4], const R WhL[4], const double dpL[4], C fdL, C caL, C frL, R lam_w, C ws,
+__device__ bool wall_flux(const R WL[4], const R WhL[4], const R dpL[4], C fdL, C caL, C frL, R lam_w, C ws,
                           C F[4])
 {
     Prim<R> p;
@@ -364,6 +364,7 @@ __device__ bool face_side(const StepConsts& K, const Dev& c, int cc, int f, int 
 template <typename R, typename C>
 __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4])
 {
+    constexpr bool f32 = sizeof(R) == 4;   // FP32 moments: the per-cell FP32 copies of k_flux_prep
     const int L = c.fL[f], Rc = c.fR[f], bc = c.fbc[f];
     const double nx = c.fnx[f], ny = c.fny[f];
     const R nxr = R(nx), nyr = R(ny);
@@ -374,32 +375,51 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         o[2] = -a * nyr + b * nxr;
         o[3] = R(W[3]);
     };
-    // FP32 moments: the primitive perturbation carrying a side's wave remainder, from the FP64 cell states, in
-    // the face frame (d rho and d theta are invariant, (dU, dV) rotate like the velocity); unused in FP64
-    auto prim_pert = [&](int cc, double o[4]) {
-        if (sizeof(R) != 4) return;
-        double g[4];
-        prim_perturbation(c.W + 4 * cc, c.Wh + 4 * cc, g);
-        o[0] = g[0];
-        o[1] = g[1] * nx + g[2] * ny;
-        o[2] = -g[1] * ny + g[2] * nx;
-        o[3] = g[3];
+    auto rot4 = [&](const float4 w, R o[4]) {
+        o[0] = R(w.x);
+        o[1] = R(w.y) * nxr + R(w.z) * nyr;
+        o[2] = -R(w.y) * nyr + R(w.z) * nxr;
+        o[3] = R(w.w);
+    };
+    // a cell's W and W^h in the face frame, precision R
+    auto state = [&](int cc, R W[4], R Wh[4]) {
+        if constexpr (f32) {
+            rot4(c.w32[cc], W);
+            rot4(c.wh32[cc], Wh);
+        } else {
+            rot(c.W + 4 * cc, W);
+            rot(c.Wh + 4 * cc, Wh);
+        }
+    };
+    // normalised coefficient k of cell cc in the precision C of the time integrals
+    auto coef = [&](int cc, int k) -> C {
+        if constexpr (sizeof(C) == 4) return c.co32[8 * cc + k];
+        else return C(c.co[7 * cc + k]);
+    };
+    // FP32 moments: the primitive perturbation carrying a side's wave remainder, in the face frame (d rho and
+    // d theta are invariant, (dU, dV) rotate like the velocity); unused in FP64
+    auto prim_pert = [&](int cc, R o[4]) {
+        if constexpr (f32) {
+            const float4 g = c.dp32[cc];
+            o[0] = R(g.x);
+            o[1] = R(g.y) * nxr + R(g.z) * nyr;
+            o[2] = -R(g.y) * nyr + R(g.z) * nxr;
+            o[3] = R(g.w);
+        }
     };
     R WL[4], WhL[4], WR[4], WhR[4], WLc[4], WRc[4], dhL[4], dhR[4];
-    double dpL[4] = {0.0, 0.0, 0.0, 0.0}, dpR[4] = {0.0, 0.0, 0.0, 0.0};
+    R dpL[4] = {R(0), R(0), R(0), R(0)}, dpR[4] = {R(0), R(0), R(0), R(0)};
     C F[4];
     bool ok;
-    rot(c.W + 4 * L, WL);
-    rot(c.Wh + 4 * L, WhL);
+    state(L, WL, WhL);
     prim_pert(L, dpL);
 #pragma unroll
     for (int q = 0; q < 4; ++q) WLc[q] = WL[q];
-    const double* coL = c.co + 7 * L;
-    const C cL[3] = {C(coL[0]), C(coL[1]), C(coL[2])};
+    const C cL[3] = {coef(L, 0), coef(L, 1), coef(L, 2)};
     // the sampled-from part of a side's wave keeps dbar_d - e^{-x} where this step's particles carry e^{-x} of
     // it; its remainder keeps dbar_d
-    const C frL = C((K.wave_only || c.nhp[L] == 0) ? coL[3] : coL[5]);
-    const C fdL = C(coL[3]);
+    const C frL = (K.wave_only || c.nhp[L] == 0) ? coef(L, 3) : coef(L, 5);
+    const C fdL = coef(L, 3);
     // order 2: reconstructed face states of W (equilibrium part) and W^h (free-transport wave with its normal
     // slope term, weighted with dbar_e, or dbar_e + dt e^{-x} / 2 when the collisionless part is carried by
     // particles, Eq. 50) on interior, periodic and far-field / fixed faces; W and W^h are reconstructed
@@ -408,7 +428,7 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
     const bool o2 = K.order == 2 && (bc == 0 || bc == UGKWP_BC_PERIODIC || bc == UGKWP_BC_FARFIELD ||
                                      bc == UGKWP_BC_FIXED);
     bool sL = false, sR = false;
-    const C csL = C(K.wave_only ? coL[4] : coL[6]);
+    const C csL = K.wave_only ? coef(L, 4) : coef(L, 6);
     if (o2) {
         double Wf[4], dn[4];
         if (face_side(K, c, L, f, 0, nx, ny, Wf, dn)) {
@@ -420,14 +440,12 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         }
     }
     if (bc == 0 || bc == UGKWP_BC_PERIODIC) {
-        rot(c.W + 4 * Rc, WR);
-        rot(c.Wh + 4 * Rc, WhR);
+        state(Rc, WR, WhR);
         prim_pert(Rc, dpR);
 #pragma unroll
         for (int q = 0; q < 4; ++q) WRc[q] = WR[q];
-        const double* coR = c.co + 7 * Rc;
-        const C cR[3] = {C(coR[0]), C(coR[1]), C(coR[2])};
-        const C frR = C((K.wave_only || c.nhp[Rc] == 0) ? coR[3] : coR[5]);
+        const C cR[3] = {coef(Rc, 0), coef(Rc, 1), coef(Rc, 2)};
+        const C frR = (K.wave_only || c.nhp[Rc] == 0) ? coef(Rc, 3) : coef(Rc, 5);
         if (o2) {
             double Wf[4], dn[4];
             if (face_side(K, c, Rc, f, 0, nx, ny, Wf, dn)) {
@@ -438,8 +456,9 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
                 sR = true;
             }
         }
-        ok = face_flux<R, C>(WL, WR, WhL, WhR, dpL, dpR, fdL, C(coR[3]), cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]), R(K.Pr), WLc,
-                             WRc, sL ? dhL : nullptr, sR ? dhR : nullptr, csL, C(K.wave_only ? coR[4] : coR[6]), F);
+        ok = face_flux<R, C>(WL, WR, WhL, WhR, dpL, dpR, fdL, coef(Rc, 3), cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]),
+                             R(K.Pr), WLc, WRc, sL ? dhL : nullptr, sR ? dhR : nullptr, csL,
+                             K.wave_only ? coef(Rc, 4) : coef(Rc, 6), F);
     } else if (bc == UGKWP_BC_WALL) {
         ok = wall_flux<R, C>(WL, WhL, dpL, fdL, cL[0], frL, R(0.5 / (kR * K.Tw)), C(K.wall_specular), F);
     } else if (bc == UGKWP_BC_SYMMETRY) {
@@ -481,6 +500,26 @@ __device__ __forceinline__ void store_flux(const Dev& c, int f, const double out
     o[1] = make_double2(out[2], out[3]);
 }
 
+// production mode, once per cell before the faces: FP32 copies of W, W^h and the normalised coefficients, and
+// the primitive perturbation that carries W^h's remainder (FP64, rounded once), so that the FP32 faces read
+// 16-byte FP32 loads and run no FP64 work (B300's FP64 pipe is narrow)
+__global__ void __launch_bounds__(256) k_flux_prep(const StepConsts K, const Dev c)
+{
+    const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cc >= K.C) return;
+    const double* W = c.W + 4 * cc;
+    const double* Wh = c.Wh + 4 * cc;
+    c.w32[cc] = make_float4(float(W[0]), float(W[1]), float(W[2]), float(W[3]));
+    c.wh32[cc] = make_float4(float(Wh[0]), float(Wh[1]), float(Wh[2]), float(Wh[3]));
+    double dp[4];
+    prim_perturbation(W, Wh, dp);
+    c.dp32[cc] = make_float4(float(dp[0]), float(dp[1]), float(dp[2]), float(dp[3]));
+    const double* co = c.co + 7 * cc;
+    float4* o = reinterpret_cast<float4*>(c.co32 + 8 * (size_t)cc);
+    o[0] = make_float4(float(co[0]), float(co[1]), float(co[2]), float(co[3]));
+    o[1] = make_float4(float(co[4]), float(co[5]), float(co[6]), 0.0f);
+}
+
 // production mode: every face with FP32 velocity moments; the faces of wall cells apply their time
 // integrals (the normalised coefficients, computed in FP64 in the decomposition) and sum the weighted
 // moments in FP64. A face whose FP32 evaluation under- or overflows (near-vacuum neighbours with extreme
@@ -488,10 +527,20 @@ __device__ __forceinline__ void store_flux(const Dev& c, int f, const double out
 __global__ void __launch_bounds__(128) k_wave_flux32(const StepConsts K, const Dev c)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= K.F) return;
+    if (f >= K.F || c.face_f64[f]) return;
     double out[4];
-    const bool ok = c.face_f64[f] ? one_face<float, double>(K, c, f, out) : one_face<float, float>(K, c, f, out);
-    if (ok) store_flux(c, f, out);
+    if (one_face<float, float>(K, c, f, out)) store_flux(c, f, out);
+    else c.retry[atomicAdd(c.nretry, 1)] = f;
+}
+
+// the faces of wall cells in production mode: FP32 moments weighted with their FP64 time integrals
+__global__ void __launch_bounds__(128) k_wave_flux_mixed(const StepConsts K, const Dev c)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K.n_mix) return;
+    const int f = c.mixlist[j];
+    double out[4];
+    if (one_face<float, double>(K, c, f, out)) store_flux(c, f, out);
     else c.retry[atomicAdd(c.nretry, 1)] = f;
 }
 
@@ -525,7 +574,11 @@ void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s
         k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 1);
         return;
     }
-    if (k.prec == 0) k_wave_flux32<<<(k.F + 127) / 128, 128, 0, s>>>(k, d);
+    if (k.prec == 0) {
+        k_flux_prep<<<(k.C + 255) / 256, 256, 0, s>>>(k, d);
+        if (k.n_mix) k_wave_flux_mixed<<<(k.n_mix + 127) / 128, 128, 0, s>>>(k, d);
+        k_wave_flux32<<<(k.F + 127) / 128, 128, 0, s>>>(k, d);
+    }
     if (k.prec == 0) k_wave_flux64<<<4 * sms, 32, 0, s>>>(k, d, 1, 0);
     else k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 0);
 }

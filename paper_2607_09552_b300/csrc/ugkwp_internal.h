@@ -38,6 +38,7 @@ struct StepConsts {
     int fx0, fx1, fx4;              // fixed-point exponents: mass, momentum, energy
     int fx_s2, fx_s3, shakhov;      // second / third velocity moments; Shakhov sampling (Pr != 1, particles)
     int n_f64, sort_every;          // faces in f64list; counting sort of the particles every sort_every steps
+    int n_mix;                      // faces in mixlist
     int chunk;                      // particles per dynamically claimed chunk of the transport kernel
     int n_inj;                      // ghost particle sources (far-field and fixed faces)
     int order;                      // 2: second-order reconstruction for the wave fluxes
@@ -76,7 +77,11 @@ struct Dev {
                                        // and direction (L -> R, R -> L), before and after the scaling
     // per-step cell data
     double *tau, *xr, *emx, *Wh, *co, *mnew;
-    double* samp;                      // [3C] U^h, V^h, R T^h
+    double* samp;                      // [3C] U_i, V_i, R T_i of the new particles' distribution
+    // production-mode wave fluxes: FP32 copies per cell, written once per step by k_flux_prep (second stream)
+    float4 *w32, *wh32;                // W, W^h
+    float4* dp32;                      // primitive perturbation (d rho, dU, dV, d theta) carrying W^h's remainder
+    float* co32;                       // [8C] the 7 normalised coefficients (padded)
     double* grad;                      // [16C] order 2: limited gradients (d/dx, d/dy) of W's 4 components, then W^h's
     long long* whq;                    // [9C] Pr != 1: raw moments of the retained particles
     double* hq;                        // [3C] Pr != 1: acceptance-rejection weights a_x, a_y, M
@@ -99,6 +104,7 @@ struct Dev {
     int* flags;                        // [0]: this step sorts the particles by cell
     int *nretry, *retry;               // faces whose FP32 flux failed this step (re-evaluated in FP64)
     int* f64list;                      // faces always evaluated in FP64
+    int* mixlist;                      // production mode: the faces of wall cells (FP32 moments, FP64 time integrals)
     unsigned int* done;                // blocks of k_update finished (last-block reduction)
     int* counts;                       // [0] retained, [1] new this step, [2] kept after the step, [3] capacity,
                                        // [4] processed, [5] chunk counter, [6] entered from ghosts, [7] their sort slots
