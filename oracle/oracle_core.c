@@ -904,11 +904,12 @@ void oracle_destroy(oracle_ctx* cx)
 static int realizable(const or_ctx* cx, const double W[4])
 {
     if (!(W[0] > OR_RHO_FLOOR)) return 0;
-    const double U = W[1] / W[0], V = W[2] / W[0];
+    const double r = 1.0 / W[0];
+    const double U = W[1] * r, V = W[2] * r;
     const double q = U * U + V * V;
-    const double e = W[3] / W[0] - 0.5 * q;
+    const double e = W[3] * r - 0.5 * q;
     if (!(e > 0.0)) return 0;
-    const double T = (e * (2.0 / 3.0)) / OR_R;
+    const double T = (e * (2.0 / 3.0)) * (1.0 / OR_R);
     return T >= cx->T_min && T <= cx->T_cap && q <= cx->U_cap * cx->U_cap;
 }
 

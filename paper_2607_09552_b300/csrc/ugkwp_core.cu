@@ -29,6 +29,17 @@ namespace ugk {
 namespace {
 
 constexpr int kScanBlock = 1024;
+
+// 2^e (|e| < 1022) from its exponent bits: the fixed-point scales with no FP64 arithmetic (B300's FP64 pipe is
+// narrow); equal to ldexp(1.0, e)
+__host__ __device__ __forceinline__ double pow2(int e)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)(e + 1023) << 52);
+#else
+    return ldexp(1.0, e);
+#endif
+}
 #ifndef UGKWP_CHUNK
 #define UGKWP_CHUNK 256
 #endif
@@ -393,11 +404,12 @@ __global__ void k_wall_index(Dev d, int F, const int* idx)
 __device__ __forceinline__ bool realizable(const StepConsts& K, const double* W)
 {
     if (!(W[0] > kRhoFloor)) return false;
-    const double U = W[1] / W[0], V = W[2] / W[0];
+    const double r = 1.0 / W[0];   // one reciprocal (B300's FP64 pipe is narrow), as the CPU definition
+    const double U = W[1] * r, V = W[2] * r;
     const double q = U * U + V * V;
-    const double e = W[3] / W[0] - 0.5 * q;
+    const double e = W[3] * r - 0.5 * q;
     if (!(e > 0.0)) return false;
-    const double T = (e * (2.0 / 3.0)) / kR;
+    const double T = (e * (2.0 / 3.0)) * (1.0 / kR);
     return T >= K.T_min && T <= K.T_cap && q <= K.U_cap * K.U_cap;
 }
 
@@ -499,8 +511,8 @@ __device__ void lts_coeffs(double dt, double tau, double e, double* out)
 __device__ void shakhov_weights(const StepConsts& K, const Dev& d, int c, double RTi)
 {
     const long long* h = d.whq + 9 * c;
-    const double s0 = ldexp(1.0, -K.fx0), s1 = ldexp(1.0, -K.fx1), s2 = ldexp(1.0, -K.fx_s2);
-    const double s3 = ldexp(1.0, -K.fx_s3);
+    const double s0 = pow2(-K.fx0), s1 = pow2(-K.fx1), s2 = pow2(-K.fx_s2);
+    const double s3 = pow2(-K.fx_s3);
     const double Sm = (double)h[0] * s0, Su = (double)h[1] * s1, Sv = (double)h[2] * s1;
     const double Suu = (double)h[3] * s2, Suv = (double)h[4] * s2, Svv = (double)h[5] * s2, Sq = (double)h[6] * s2;
     const double Suq = (double)h[7] * s3, Svq = (double)h[8] * s3;
@@ -558,11 +570,12 @@ __device__ void lts_coeffs_f32(float dt, float x, float e, double* out)
 __global__ void k_decompose(const StepConsts K, Dev d)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned am = __ballot_sync(0xffffffffu, c < K.C);   // the warp's lanes with a cell
     if (c >= K.C) return;
     const double* W = d.W + 4 * c;
     long long* r = d.wrt + 5 * c;
     const double vol = d.vol[c];
-    const double s0 = ldexp(1.0, -K.fx0), s1 = ldexp(1.0, -K.fx1), s4 = ldexp(1.0, -K.fx4);
+    const double s0 = pow2(-K.fx0), s1 = pow2(-K.fx1), s4 = pow2(-K.fx4);
     // production precision: tau, x = dt / tau and e^{-x} in FP32, except in cells with a wall face (stretched,
     // where the wave-flux time integrals need FP64) and at order 2 (whose g^h slope weight needs FP64)
     const bool f32 = K.prec == 0 && !d.wallcell[c] && K.order != 2;
@@ -621,6 +634,15 @@ __global__ void k_decompose(const StepConsts K, Dev d)
         }
     }
     if (K.shakhov && n > 0) shakhov_weights(K, d, c, RTi);
+    // the cells that sample: appended to the list of k_sample, one slot range per warp
+    const unsigned sm = __ballot_sync(am, n > 0);
+    if (sm) {
+        const int leader = __ffs(am) - 1, lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(d.nscell, __popc(sm));
+        base = __shfl_sync(am, base, leader);
+        if (n > 0) d.scells[base + __popc(sm & ((1u << lane) - 1u))] = c;
+    }
     d.nhp[c] = n;
     d.mnew[c] = m;
     d.samp[3 * c] = Ui; d.samp[3 * c + 1] = Vi; d.samp[3 * c + 2] = RTi;
@@ -735,6 +757,7 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
         d.counts[7] = 0;
         d.stats[13] = 0;
         *d.nretry = 0;
+        *d.nscell = 0;
         *d.done = 0u;
         // a counting sort every sort_every-th step, and whenever holes (removed particles, updated in place)
         // fill more than a quarter of the slots
@@ -820,9 +843,9 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 {
     const ParticleSoA<T> A = *d.bufsel ? PB : PA;
     const int n = d.counts[0];
-    const T sc[9] = {T(ldexp(1.0, K.fx0)), T(ldexp(1.0, K.fx1)), T(ldexp(1.0, K.fx1)), T(ldexp(1.0, K.fx_s2)),
-                     T(ldexp(1.0, K.fx_s2)), T(ldexp(1.0, K.fx_s2)), T(ldexp(1.0, K.fx_s2)), T(ldexp(1.0, K.fx_s3)),
-                     T(ldexp(1.0, K.fx_s3))};
+    const T sc[9] = {T(pow2(K.fx0)), T(pow2(K.fx1)), T(pow2(K.fx1)), T(pow2(K.fx_s2)),
+                     T(pow2(K.fx_s2)), T(pow2(K.fx_s2)), T(pow2(K.fx_s2)), T(pow2(K.fx_s3)),
+                     T(pow2(K.fx_s3))};
     unsigned long long* h = reinterpret_cast<unsigned long long*>(d.whq);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int ci = A.cell[i];
@@ -845,13 +868,11 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 // order: lane j of the cell's eight adds k = j, j + 8, ... in increasing k, then a butterfly combines the
 // lanes (j + 4 into j, j + 2 into j, j + 1 into j; every lane of the group ends with the same value).
 constexpr int kSampleGroup = 8;
+// One cell c (c = K.C: none) per 8-lane group; every lane of the warp calls it together.
 template <typename T>
-__global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
-                                                ParticleSoA<T> PB, PCell<T> pc, const long long* dstep)
+__device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, const ParticleSoA<T>& A,
+                                            const PCell<T>& pc, const long long* dstep, int c, int l)
 {
-    const ParticleSoA<T> A = *d.bufsel ? PB : PA;   // the buffer holding this step's particles
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) / kSampleGroup;
-    const int l = threadIdx.x & (kSampleGroup - 1);
     int N = 0;
     long long base_i = 0;
     if (c < K.C && d.counts[1] != 0) {
@@ -865,7 +886,7 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
         }
     }
     // every lane of the warp takes part in the shuffles below; cells without particles add zeros
-    if (!__any_sync(0xffffffffu, N > 0)) return;
+    if (!__any_sync(0xffffffffu, N > 0)) return;   // (the whole warp)
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
     const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)(c < K.C ? c : 0) << 11);
     T su = 0, sv = 0, sw = 0;
@@ -927,7 +948,7 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
         const T Ui = pc.s_(c, 0), Vi = pc.s_(c, 1), RTi = pc.s_(c, 2);
         const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTi) / ss) : T(0);
         const T m = pc.m_(c);
-        const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+        const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
         // the cell's vertices in the particle precision and its two triangles' areas (same for every particle)
         T X[4], Y[4];
 #pragma unroll
@@ -988,6 +1009,24 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
             d.wm[5 * c + q] += acc[q];
             atomicAdd(reinterpret_cast<unsigned long long*>(d.wpl) + 5 * (size_t)c + q, (unsigned long long)acc[q]);
         }
+}
+
+
+// the cells that sample new particles this step (listed by the decomposition, in any order: each cell's
+// particles, ids and slots depend on the cell alone), four per warp, grid-stride over the list
+template <typename T>
+__global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
+                                                ParticleSoA<T> PB, PCell<T> pc, const long long* dstep)
+{
+    const ParticleSoA<T> A = *d.bufsel ? PB : PA;   // the buffer holding this step's particles
+    const int l = threadIdx.x & (kSampleGroup - 1);
+    const int grp = (threadIdx.x & 31) / kSampleGroup;
+    const int nact = *d.nscell;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; 4 * w < nact; w += nwarps) {
+        const int j = 4 * w + grp;
+        sample_cell(K, d, A, pc, dstep, j < nact ? d.scells[j] : K.C, l);
+    }
 }
 
 // A particle at (x, y) moving with (u, v) stays in its cell for the time tr when it reaches none of the faces
@@ -1218,7 +1257,7 @@ __global__ void __launch_bounds__(256, UGKWP_PARTICLES_MINB) k_particles(const S
     const int nret = d.counts[0];
     const int n = nret + d.counts[1];
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
-    const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+    const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
     const T m2RTw = T(K.m2RTw), sigw = T(K.sig_w);
     unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0, n_kept = 0;
     int max_it = 0;
@@ -1413,7 +1452,7 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
     const int n = nret + d.counts[1];
     const int ntiles = (n + WT - 1) / WT;
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
-    const float s0 = float(ldexp(1.0, K.fx0)), s1 = float(ldexp(1.0, K.fx1)), s4 = float(ldexp(1.0, K.fx4));
+    const float s0 = float(pow2(K.fx0)), s1 = float(pow2(K.fx1)), s4 = float(pow2(K.fx4));
     const float m2RTw = float(K.m2RTw), sigw = float(K.sig_w), ws = float(K.wall_specular);
     const unsigned lt_mask = (1u << lane) - 1u;
     unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0, n_kept = 0;
@@ -1646,7 +1685,7 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
     const int f = d.inj_face[j], L = d.fL[f], kin = d.inj_k[j];
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
     const uint64_t base = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)(K.C + j) << 11);
-    const T s0 = T(ldexp(1.0, K.fx0)), s1 = T(ldexp(1.0, K.fx1)), s4 = T(ldexp(1.0, K.fx4));
+    const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
     const T m2RTw = T(K.m2RTw), sigw = T(K.sig_w);
     const T nx = T(d.fnx[f]), ny = T(d.fny[f]);
     const double* P = d.inj_par + 5 * j;
@@ -1745,10 +1784,32 @@ __global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA,
     const int sel = *d.bufsel;
     const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
     const int n = d.counts[4] + d.counts[7];   // the step's slots, then those of particles that entered from ghosts
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = A.cell[i];
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    // warp-uniform loop; the slots of a run of equal cells in the warp (the particles stay grouped by cell
+    // between sorts) are reserved with one atomic by the run's first lane
+    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const int i = i0 + lane;
+        const int c = i < n ? A.cell[i] : -1;
+        const int prev = __shfl_up_sync(0xffffffffu, c, 1);
+        int start = (lane == 0 || prev != c) ? lane : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, start, o);
+            if (lane >= o) start = max(start, t);
+        }
+        const int nx = __shfl_down_sync(0xffffffffu, c, 1);
+        int end = (lane == 31 || nx != c) ? lane : 31;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_down_sync(0xffffffffu, end, o);
+            if (lane + o < 32) end = min(end, t);
+        }
+        int base = 0;
+        if (lane == start && c >= 0) base = atomicAdd(d.cur + c, end - start + 1);
+        base = __shfl_sync(0xffffffffu, base, start);
         if (c < 0) continue;
-        const int slot = d.off[c] + atomicAdd(d.cur + c, 1);
+        const int slot = d.off[c] + base + (lane - start);
         B.x[slot] = A.x[i]; B.y[slot] = A.y[i]; B.u[slot] = A.u[i]; B.v[slot] = A.v[i]; B.w[slot] = A.w[i];
         B.m[slot] = A.m[i]; B.cell[slot] = c; B.pid[slot] = A.pid[i];
     }
@@ -1781,7 +1842,7 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
         // FP64 throughout; the divisions by Omega_i and dt_i are multiplications by their reciprocals
         const double vol = d.vol[c], dt = d.dt[c], rvol = d.rcp[2 * c], rdt = d.rcp[2 * c + 1];
         const double coef = dt * rvol;
-        const double sc[4] = {ldexp(1.0, -K.fx0), ldexp(1.0, -K.fx1), ldexp(1.0, -K.fx1), ldexp(1.0, -K.fx4)};
+        const double sc[4] = {pow2(-K.fx0), pow2(-K.fx1), pow2(-K.fx1), pow2(-K.fx4)};
         const int tk[4] = {0, 1, 2, 4};
         double* W = d.W + 4 * c;
         double Wn[4];
@@ -1813,7 +1874,7 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
         const int f = d.wall_face[iw], c = d.fL[f];
         const double nx = d.fnx[f], ny = d.fny[f], tx = -ny, ty = nx;
         const double* F = d.flux + 4 * (size_t)f;
-        const double s1 = ldexp(1.0, -K.fx1), s4 = ldexp(1.0, -K.fx4);
+        const double s1 = pow2(-K.fx1), s4 = pow2(-K.fx4);
         const double rsdt = 1.0 / (d.fs[f] * d.dt[c]);
         const double px = ((double)d.wallt[3 * iw] * s1) * rsdt;
         const double py = ((double)d.wallt[3 * iw + 1] * s1) * rsdt;
@@ -1840,13 +1901,22 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
         last = atomicAdd(d.done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    // the step's last block: residual (partials summed in block order), counters, next step
+    if (!last) return;
+    // the step's last block: residual (the block partials summed by all its threads in a fixed order: thread t
+    // takes blocks t, t + 256, ..., then the same tree as above), counters, next step
     __threadfence();
     double s[4] = {0, 0, 0, 0};
-    for (int b = 0; b < (int)gridDim.x; ++b)
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kUpdateBlock)
         for (int q = 0; q < 4; ++q) s[q] += __ldcg(d.res_part + 4 * b + q);
-    for (int q = 0; q < 4; ++q) d.res[q] = sqrt(s[q]);
+    for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int h = kUpdateBlock / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 4; ++q) d.res[q] = sqrt(sm[q][0]);
     // the next step's slots: the particles and holes of this step and the entered ones; after a counting sort
     // the survivors alone, in the other buffer
     const int kept = __ldcg(d.counts + 2);
@@ -1928,10 +1998,10 @@ __global__ void k_wp_field(Dev d, int C, int fx0, int fx1, int fx4, double* out)
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     const long long* r = d.wrt + 5 * c;
-    out[4 * c] = ((double)r[0] * ldexp(1.0, -fx0)) / d.vol[c];
-    out[4 * c + 1] = ((double)r[1] * ldexp(1.0, -fx1)) / d.vol[c];
-    out[4 * c + 2] = ((double)r[2] * ldexp(1.0, -fx1)) / d.vol[c];
-    out[4 * c + 3] = ((double)r[4] * ldexp(1.0, -fx4)) / d.vol[c];
+    out[4 * c] = ((double)r[0] * pow2(-fx0)) / d.vol[c];
+    out[4 * c + 1] = ((double)r[1] * pow2(-fx1)) / d.vol[c];
+    out[4 * c + 2] = ((double)r[2] * pow2(-fx1)) / d.vol[c];
+    out[4 * c + 3] = ((double)r[4] * pow2(-fx4)) / d.vol[c];
 }
 
 // ---------------------------------------------------------------------------- host helpers
@@ -2051,8 +2121,8 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32, d.hq32, d.emx32};
     PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp, d.hq, d.emx};
     mark(2, s);
-    if (K.prec == 0) k_sample<float><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
-    else k_sample<double><<<nblk((long long)C * kSampleGroup, 128), 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
+    if (K.prec == 0) k_sample<float><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
+    else k_sample<double><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
     mark(3, s);
     mark(4, s);
     if (K.prec == 0 && ctx.transport == kTransportStaged)
@@ -2442,6 +2512,7 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         CK(dalloc(ctx, &d.co, 7 * C)); CK(dalloc(ctx, &d.mnew, C)); CK(dalloc(ctx, &d.samp, 3 * C));
         CK(dalloc(ctx, &d.whq, 9 * C)); CK(dalloc(ctx, &d.hq, 3 * C)); CK(dalloc(ctx, &d.hq32, 3 * C));
         CK(dalloc(ctx, &d.nhp, C)); CK(dalloc(ctx, &d.nhp_off, C + 1));
+        CK(dalloc(ctx, &d.scells, C)); CK(dalloc(ctx, &d.nscell, 1));
         CK(dalloc(ctx, &d.cnt, C)); CK(dalloc(ctx, &d.off, C + 1)); CK(dalloc(ctx, &d.cur, C));
         CK(dalloc(ctx, &d.flux, 4 * F));
         ctx.res_blocks = nblk((long long)C + nwall, kUpdateBlock);

@@ -87,6 +87,7 @@ struct Dev {
     double* hq;                        // [3C] Pr != 1: acceptance-rejection weights a_x, a_y, M
     float* hq32;
     int *nhp, *nhp_off, *cnt, *off, *cur;
+    int *scells, *nscell;              // cells with N^hp > 0 this step (in any order) and their number
     int* scan_tmp;
     double* flux;                      // [4F]
     double *res_part, *res;            // residual: per-block partials; [8] = raw of this step (4 used)
