@@ -246,8 +246,8 @@ def run_ours(args):
         cfg["burn_in_rule"] = burn_rule
         cfg["reconstruction_order"] = args.order
         kname = {1: "k_particles (warp-chunked)",
-                 2: f"k_particles_warp ({launch[0]}-particle warp tiles, bulk async copies, {launch[1]} CTAs/SM, "
-                    "records updated in place)"}
+                 2: f"k_particles_warp + k_particles_fly ({launch[0]}-particle warp tiles, bulk async copies, "
+                    f"{launch[1]} CTAs/SM, records updated in place; crossing particles in a flight pass)"}
         cfg["launch"] = {"transport_kernel": kname[launch[3]],
                          "chunk": launch[0], "blocks_per_sm": launch[1],
                          "sort_every": launch[2],
@@ -266,7 +266,7 @@ def run_ours(args):
                             "library's stream (the second stream's ghost sources and wave fluxes not overlapped)",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "kernel": {1: "k_particles", 2: "k_particles_warp"}[launch[3]] +
+                         "kernel": {1: "k_particles", 2: "k_particles_warp + k_particles_fly"}[launch[3]] +
                                    " (t_f draw, transport with dt_R/dt_L scaling, tallies, compaction)",
                          "algorithmic_bytes_per_launch": BYTES_PER_PARTICLE_STEP * per_launch,
                          "peak_source": f"{which} (MEASURED_PEAKS.json hbm_gbs)"},
@@ -340,7 +340,8 @@ def gpu_launches_per_step(case, order=1):
     ghosts = any(t in (wl.BC_FARFIELD, wl.BC_FIXED) for t in tags)
     walls = any(t == wl.BC_WALL for t in tags)
     flux = 2 if order == 2 else 3 + (1 if walls else 0)
-    return 11 + flux + (2 if ghosts else 0) + (1 if case.Pr != 1.0 else 0)
+    # the warp-staged transport is two kernels (stay pass, flight pass)
+    return 12 + flux + (2 if ghosts else 0) + (1 if case.Pr != 1.0 else 0)
 
 
 def run_e2e(args, solver, stream):

@@ -758,6 +758,7 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
         d.stats[13] = 0;
         *d.nretry = 0;
         *d.nscell = 0;
+        if (d.nxq) *d.nxq = 0;
         *d.done = 0u;
         // a counting sort every sort_every-th step, and whenever holes (removed particles, updated in place)
         // fill more than a quarter of the slots
@@ -1387,35 +1388,28 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-// ---------------------------------------- a3-a7, warp-staged: the production-precision transport kernel
-// Every warp works alone (no block-wide barrier): it claims tiles of WT consecutive particle slots from a
-// global counter and has the fields that the stay test reads (cell, x, y, u, v, id) copied into its own
-// shared memory by bulk asynchronous copies (cp.async.bulk, completion counted on the warp's mbarrier),
-// double-buffered, so that the next tile streams in while the warp works on the current one. Per tile:
-//  A1. t_f (Eq. 27, computed form as in k_particles) and the stay test of the start cell, 32 particles at a
-//      time with no warp-wide operation between them (their loads and Philox chains overlap). A particle
-//      that stays and does not collide has only moved: its x, y are written back in place (8 bytes), the rest
-//      of its record is left untouched. Holes (cell -1) are skipped.
-//  A2. the others (a face ahead within t_r, or colliding) are queued in the warp's shared memory; whenever 32
-//      are queued the warp flies them together (B): the full free flight of fly() (crossings with the
-//      dt_R / dt_L scaling, walls, exits) and the tallies, exactly as in k_particles, then their records in
-//      place (the whole record but the id, or a hole).
+// ---------------------------------------- a3-a7, warp-staged: the production-precision transport kernels
+// Two passes. The stay pass (k_particles_warp): every warp works alone (no block-wide barrier); it claims
+// tiles of WT consecutive particle slots from a global counter and has the fields that the stay test reads
+// (cell, x, y, u, v, id) copied into its own shared memory by bulk asynchronous copies (cp.async.bulk,
+// completion counted on the warp's mbarrier), double-buffered, so that the next tile streams in while the
+// warp works on the current one. Per particle: t_f (Eq. 27, computed form as in k_particles) and the stay test
+// of the start cell, 32 particles at a time with no warp-wide operation between them (their loads and Philox
+// chains overlap). A particle that stays and does not collide has only moved: its x, y are written back in
+// place (8 bytes), the rest of its record is left untouched. Holes (cell -1) are skipped. The others (a face
+// ahead within t_r, or colliding; a few percent) go to a global queue as (slot, t_r, collide).
+// The flight pass (k_particles_fly): one thread per queued particle, at full occupancy and with nothing else
+// waiting on it: the full free flight of fly() (crossings with the dt_R / dt_L scaling, walls, exits) and the
+// tallies, exactly as in k_particles, then the record in place (the whole record but the id, or a hole).
 // On sort steps the survivors are counted per cell for the counting sort. Every per-particle operation is
 // that of k_particles, in the same order, so the results are identical.
-constexpr int kWWarps = 4;     // warps per CTA
-constexpr int kWQueue = 64;    // queued particles per warp: at most 31 left over + 32 added by one round
+constexpr int kWWarps = 4;     // warps per CTA of the stay pass
 
 template <int WT> struct alignas(16) WarpSmem {
     float x[2][WT], y[2][WT], u[2][WT], v[2][WT];   // two stages of tile fields
     int cell[2][WT];
     unsigned long long pid[2][WT];
-    float qx[kWQueue], qy[kWQueue], qu[kWQueue], qv[kWQueue], qt[kWQueue];
-    int qc[kWQueue], qi[kWQueue];
-    unsigned long long qp[kWQueue];
     unsigned long long bar[2];
-    float tq[WT];             // phase A: remaining free-flight time of a queued particle
-    unsigned char st[WT];     // phase A: 0 hole, 1 moved only, 2 queued, 3 queued and colliding
-    unsigned char qcol[kWQueue];
 };
 
 // lane 0: copy the stay-test fields of tile t of A into stage b of the warp's shared memory (the slot count
@@ -1452,42 +1446,8 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
     const int n = nret + d.counts[1];
     const int ntiles = (n + WT - 1) / WT;
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
-    const float s0 = float(pow2(K.fx0)), s1 = float(pow2(K.fx1)), s4 = float(pow2(K.fx4));
-    const float m2RTw = float(K.m2RTw), sigw = float(K.sig_w), ws = float(K.wall_specular);
     const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0, n_kept = 0;
-    int max_it = 0;
-
-    // the queued particles e0 .. e0 + 31 (lanes past qn - e0 idle): free flight, tallies, records in place
-    auto fly_queue = [&](int e0, int qn) {
-        const int e = e0 + lane;
-        const bool act = e < qn;
-        int c = -1;
-        bool kept = false;
-        if (act) {
-            const int i = S.qi[e];
-            float x = S.qx[e], y = S.qy[e], u = S.qu[e], v = S.qv[e], w = A.w[i], m = A.m[i];
-            c = S.qc[e];
-            const unsigned long long pid = S.qp[e];
-            const bool collide = S.qcol[e] != 0;
-            const int c0 = c;
-            const float m0 = m, u0 = u, v0 = v, w0 = w;
-            int it = 0;
-            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, ws, x, y, u, v, w, m, S.qt[e], c, -1,
-                                   (uint64_t)pid, it, n_cross, n_hits);
-            max_it = max(max_it, it);
-            if (alive) {
-                if (collide) n_removed++;
-            } else {
-                n_left++;
-            }
-            tally_move(d, s0, s1, s4, it, alive, collide, c0, m0, u0, v0, w0, c, m, u, v, w);
-            kept = alive && !collide;
-            write_in_place(A, i, it == 0 && !collide, kept, x, y, u, v, w, m, c);
-            n_kept += kept ? 1 : 0;
-        }
-        if (sort_step) count_runs(d, kept ? c : -1);
-    };
+    unsigned long long n_kept = 0;
 
     if (lane == 0) {
         mbar_init(&S.bar[0], 1);
@@ -1504,7 +1464,7 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
         if (tile < ntiles) wtile_issue<WT>(A, tile, n, S, 0);
     }
     tile = __shfl_sync(0xffffffffu, tile, 0);
-    int b = 0, qn = 0;
+    int b = 0;
     uint32_t parity[2] = {0u, 0u};
     uint32_t pending = tile < ntiles ? 1u : 0u;   // stages with copies in flight (bit per stage)
     bool abort = false;
@@ -1525,11 +1485,16 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
         pending &= ~(1u << b);
         const int base = tile * WT, cnt = min(WT, n - base);
 
-        // A1: t_f and the stay test of the start cell for the whole tile; particles that only move are done
+        // t_f and the stay test of the start cell for the whole tile; particles that only move are done, the
+        // others are queued for the flight pass
+        int code[WT / 32];      // 0 hole, 1 moved only, 2 queued, 3 queued and colliding
+        float trq[WT / 32];
 #pragma unroll
         for (int r = 0; r < WT / 32; ++r) {
             const int j = r * 32 + lane;
             const int c = j < cnt ? S.cell[b][j] : -1;
+            code[r] = 0;
+            trq[r] = 0.0f;
             if (c >= 0) {
                 const int i = base + j;
                 const float4 cd = d.cst32[c];   // dt, e^{-x}, tau, face count
@@ -1550,45 +1515,42 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
                 if (stays && !collide) {
                     A.x[i] = x + u * tr;
                     A.y[i] = y + v * tr;
-                    S.st[j] = 1;
+                    code[r] = 1;
                     n_kept++;
                 } else {
-                    S.tq[j] = tr;
-                    S.st[j] = collide ? 3 : 2;
+                    trq[r] = tr;
+                    code[r] = collide ? 3 : 2;
                 }
-            } else if (j < cnt) {
-                S.st[j] = 0;
             }
         }
-        __syncwarp();
-        // A2: queue the others, 32 at a time; B: whenever 32 are queued, fly them together
-#pragma unroll 1
+        // the queued particles of the tile: one slot range of the global queue per tile
+        unsigned qm[WT / 32];
+        int tot = 0;
+#pragma unroll
         for (int r = 0; r < WT / 32; ++r) {
-            const int j = r * 32 + lane;
-            const int stj = j < cnt ? S.st[j] : 0;
-            const bool q = stj >= 2;
-            const unsigned qmask = __ballot_sync(0xffffffffu, q);
-            if (!qmask) continue;
-            if (q) {
-                const int e = qn + __popc(qmask & lt_mask);
-                S.qx[e] = S.x[b][j]; S.qy[e] = S.y[b][j]; S.qu[e] = S.u[b][j]; S.qv[e] = S.v[b][j];
-                S.qt[e] = S.tq[j]; S.qc[e] = S.cell[b][j]; S.qi[e] = base + j; S.qp[e] = S.pid[b][j];
-                S.qcol[e] = stj == 3 ? 1 : 0;
-            }
-            qn += __popc(qmask);
-            __syncwarp();
-            if (qn >= 32) {
-                fly_queue(qn - 32, qn);
-                qn -= 32;
-                __syncwarp();
+            qm[r] = __ballot_sync(0xffffffffu, code[r] >= 2);
+            tot += __popc(qm[r]);
+        }
+        if (tot) {
+            int qb = 0;
+            if (lane == 0) qb = atomicAdd(d.nxq, tot);
+            qb = __shfl_sync(0xffffffffu, qb, 0);
+#pragma unroll
+            for (int r = 0; r < WT / 32; ++r) {
+                if (code[r] >= 2) {
+                    const int e = qb + __popc(qm[r] & lt_mask);
+                    d.xq_i[e] = (base + r * 32 + lane) | (code[r] == 3 ? (int)0x80000000u : 0);
+                    d.xq_t[e] = trq[r];
+                }
+                qb += __popc(qm[r]);
             }
         }
         // sort steps: the tile's particles that only moved, per cell (the queued ones count when they fly)
         if (sort_step) {
-#pragma unroll 1
+#pragma unroll
             for (int r = 0; r < WT / 32; ++r) {
                 const int j = r * 32 + lane;
-                count_runs(d, (j < cnt && S.st[j] == 1) ? S.cell[b][j] : -1);
+                count_runs(d, code[r] == 1 ? S.cell[b][j] : -1);
             }
         }
         // this lane's generic-proxy accesses of the stage come before the bulk copy that refills it (issued by
@@ -1608,7 +1570,54 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
         }
         return;
     }
-    if (qn > 0) fly_queue(0, qn);
+    for (int o = 16; o > 0; o >>= 1) n_kept += __shfl_xor_sync(0xffffffffu, n_kept, o);
+    if (lane == 0 && n_kept) atomicAdd(d.counts + 2, (int)n_kept);
+}
+
+// the flight pass: the queued particles of the stay pass, one per thread (warp-uniform grid-stride loop)
+__global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const Dev d, ParticleSoA<float> PA,
+                                                       ParticleSoA<float> PB, const CellFaces<float>* __restrict__ cf,
+                                                       const long long* dstep)
+{
+    const ParticleSoA<float> A = *d.bufsel ? PB : PA;
+    const bool sort_step = d.flags[0] != 0;
+    const int nq = *d.nxq;
+    const Rng g{K.k0, K.k1, (uint32_t)*dstep};
+    const float s0 = float(pow2(K.fx0)), s1 = float(pow2(K.fx1)), s4 = float(pow2(K.fx4));
+    const float m2RTw = float(K.m2RTw), sigw = float(K.sig_w), ws = float(K.wall_specular);
+    const int lane = threadIdx.x & 31;
+    unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0, n_kept = 0;
+    int max_it = 0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < nq; e0 += stride) {
+        const int e = e0 + lane;
+        int c = -1;
+        bool kept = false;
+        if (e < nq) {
+            const int code = d.xq_i[e];
+            const int i = code & 0x7fffffff;
+            const bool collide = code < 0;
+            float x = A.x[i], y = A.y[i], u = A.u[i], v = A.v[i], w = A.w[i], m = A.m[i];
+            c = A.cell[i];
+            const unsigned long long pid = A.pid[i];
+            const int c0 = c;
+            const float m0 = m, u0 = u, v0 = v, w0 = w;
+            int it = 0;
+            const bool alive = fly(d, cf, g, s0, s1, s4, m2RTw, sigw, ws, x, y, u, v, w, m, d.xq_t[e], c, -1,
+                                   (uint64_t)pid, it, n_cross, n_hits);
+            max_it = max(max_it, it);
+            if (alive) {
+                if (collide) n_removed++;
+            } else {
+                n_left++;
+            }
+            tally_move(d, s0, s1, s4, it, alive, collide, c0, m0, u0, v0, w0, c, m, u, v, w);
+            kept = alive && !collide;
+            write_in_place(A, i, it == 0 && !collide, kept, x, y, u, v, w, m, c);
+            n_kept += kept ? 1 : 0;
+        }
+        if (sort_step) count_runs(d, kept ? c : -1);
+    }
     for (int o = 16; o > 0; o >>= 1) {
         n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
         n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
@@ -2046,26 +2055,27 @@ template <typename T> cudaError_t alloc_particles(Ctx& ctx, ParticleSoA<T>& P, s
     return cudaSuccess;
 }
 
-// the warp-staged transport kernel: tile WT = ctx.k.chunk (128 particles per warp tile, else 64), CTAs per SM =
-// grid_particles / sms (4, 5 or 6 with 128-particle tiles, 4 or 6 with 64: the instantiation compiled for that
-// many resident CTAs)
+// the warp-staged transport kernels: the stay pass with tile WT = ctx.k.chunk (128 particles per warp tile,
+// else 64) and grid_particles / sms CTAs per SM (4, 6 or 8 with 128-particle tiles, 6 or 8 with 64: the
+// instantiation compiled for that many resident CTAs), then the flight pass
 template <int WT, int MINB> void launch_warp_variant(Ctx& ctx, cudaStream_t s, const PCell<float>& pc)
 {
     const StepConsts& K = ctx.k;
     Dev& d = ctx.d;
     k_particles_warp<WT, MINB><<<MINB * ctx.sms, kWWarps * 32, kWWarps * sizeof(WarpSmem<WT>), s>>>(
         K, d, d.pa32, d.pb32, d.cf32, pc, d.dstep);
+    k_particles_fly<<<5 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
 }
 void launch_particles_warp(Ctx& ctx, cudaStream_t s, const PCell<float>& pc)
 {
     const int bps = ctx.grid_particles / ctx.sms;
     if (ctx.k.chunk == 128) {
-        if (bps >= 6) launch_warp_variant<128, 6>(ctx, s, pc);
-        else if (bps == 5) launch_warp_variant<128, 5>(ctx, s, pc);
+        if (bps >= 7) launch_warp_variant<128, 8>(ctx, s, pc);
+        else if (bps >= 5) launch_warp_variant<128, 6>(ctx, s, pc);
         else launch_warp_variant<128, 4>(ctx, s, pc);
     } else {
-        if (bps >= 6) launch_warp_variant<64, 6>(ctx, s, pc);
-        else launch_warp_variant<64, 4>(ctx, s, pc);
+        if (bps >= 7) launch_warp_variant<64, 8>(ctx, s, pc);
+        else launch_warp_variant<64, 6>(ctx, s, pc);
     }
 }
 template <int WT, int MINB> cudaError_t warp_variant_attr()
@@ -2121,22 +2131,26 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     PCell<float> pc32{d.tau32, d.dt32, d.mnew32, d.samp32, d.hq32, d.emx32};
     PCell<double> pc64{d.tau, d.dt, d.mnew, d.samp, d.hq, d.emx};
     mark(2, s);
-    if (K.prec == 0) k_sample<float><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
-    else k_sample<double><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
+    // the particle kernels only where there are particle buffers (not in the particle-free mode)
+    const bool parts = !K.wave_only;
+    if (parts && K.prec == 0) k_sample<float><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
+    else if (parts) k_sample<double><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
     mark(3, s);
     mark(4, s);
-    if (K.prec == 0 && ctx.transport == kTransportStaged)
+    if (parts && K.prec == 0 && ctx.transport == kTransportStaged)
         launch_particles_warp(ctx, s, pc32);
-    else if (K.prec == 0) k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
-    else k_particles<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64, d.cf64, pc64, d.dstep);
+    else if (parts && K.prec == 0)
+        k_particles<float><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, pc32, d.dstep);
+    else if (parts)
+        k_particles<double><<<ctx.grid_particles, 256, 0, s>>>(K, d, d.pa64, d.pb64, d.cf64, pc64, d.dstep);
     mark(5, s);
     mark(8, s);
     // counting sort every sort_every-th step (kernels return at once on the other steps), after the ghost
     // sources on the second stream have added their survivors
     cudaStreamWaitEvent(s, ctx.ev_join, 0);
     exclusive_scan(d.cnt, d.off, d.scan_tmp, C, d.counts + 2, s, nullptr, nullptr, d.flags);
-    if (K.prec == 0) k_scatter<float><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa32, d.pb32);
-    else k_scatter<double><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa64, d.pb64);
+    if (parts && K.prec == 0) k_scatter<float><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa32, d.pb32);
+    else if (parts) k_scatter<double><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa64, d.pb64);
     mark(9, s);
     mark(10, s);
     k_update<<<ctx.res_blocks, kUpdateBlock, 0, s>>>(K, d, d.dstep);
@@ -2568,14 +2582,19 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         ctx.transport = K.prec == 0 ? kTransportStaged : kTransportWarp;
         if (K.prec == 0) {
             ctx.k.chunk = 128;
-            CK((warp_variant_attr<64, 4>()));
+            ctx.grid_particles = sms * 8;
             CK((warp_variant_attr<64, 6>()));
+            CK((warp_variant_attr<64, 8>()));
             CK((warp_variant_attr<128, 4>()));
-            CK((warp_variant_attr<128, 5>()));
             CK((warp_variant_attr<128, 6>()));
+            CK((warp_variant_attr<128, 8>()));
         }
         if (!K.wave_only) {
-            if (K.prec == 0) { CK(alloc_particles(ctx, d.pa32, ctx.capacity)); CK(alloc_particles(ctx, d.pb32, ctx.capacity)); }
+            if (K.prec == 0) {
+                CK(alloc_particles(ctx, d.pa32, ctx.capacity)); CK(alloc_particles(ctx, d.pb32, ctx.capacity));
+                CK(dalloc(ctx, &d.xq_i, (size_t)ctx.capacity)); CK(dalloc(ctx, &d.xq_t, (size_t)ctx.capacity));
+                CK(dalloc(ctx, &d.nxq, 1));
+            }
             else { CK(alloc_particles(ctx, d.pa64, ctx.capacity)); CK(alloc_particles(ctx, d.pb64, ctx.capacity)); }
         }
         const int cnt_init[8] = {0, 0, 0, K.wave_only ? 0 : ctx.capacity, 0, 0, 0, 0};
@@ -3269,11 +3288,11 @@ extern "C" ugkwp_status ugkwp_autotune(ugkwp_ctx* h, int32_t steps, int32_t* bes
     std::vector<Cand> cands;
     for (int so : {8, 16, 32}) {
         if (ctx.k.prec == 0) {
-            cands.push_back({64, 4, so, kTransportStaged});
             cands.push_back({64, 6, so, kTransportStaged});
+            cands.push_back({64, 8, so, kTransportStaged});
             cands.push_back({128, 4, so, kTransportStaged});
-            cands.push_back({128, 5, so, kTransportStaged});
             cands.push_back({128, 6, so, kTransportStaged});
+            cands.push_back({128, 8, so, kTransportStaged});
         }
         for (int ch : {128, 256})
             for (int bp : {4, 6, 8}) cands.push_back({ch, bp, so, kTransportWarp});

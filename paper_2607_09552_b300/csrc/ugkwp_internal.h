@@ -88,6 +88,9 @@ struct Dev {
     float* hq32;
     int *nhp, *nhp_off, *cnt, *off, *cur;
     int *scells, *nscell;              // cells with N^hp > 0 this step (in any order) and their number
+    int *xq_i, *nxq;                   // production transport: slots queued by the stay pass for the flight pass
+                                       // (bit 31: colliding) and their number
+    float* xq_t;                       // their remaining free-flight times
     int* scan_tmp;
     double* flux;                      // [4F]
     double *res_part, *res;            // residual: per-block partials; [8] = raw of this step (4 used)

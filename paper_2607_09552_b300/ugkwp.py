@@ -216,7 +216,7 @@ class Solver:
 
     def set_launch(self, chunk: int = 0, blocks_per_sm: int = 0, sort_every: int = 0, transport: int = 0):
         """Transport kernel 1: warp-chunked, 2: warp-staged (production precision; chunk 64 or 128 is its warp tile,
-        4 or 6 CTAs per SM); 0 keeps a value."""
+        4, 6 or 8 CTAs per SM); 0 keeps a value."""
         self._check(load().ugkwp_set_launch(self.ctx, C.c_int32(chunk), C.c_int32(blocks_per_sm), C.c_int32(sort_every),
                                             C.c_int32(transport)))
 

@@ -381,7 +381,7 @@ def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
     case = CASES["cylinder"]
     a = cuda_lib.Solver(case, precision=0, use_graph=True)
     b = cuda_lib.Solver(case, precision=0, use_graph=True)
-    assert a.launch() == [128, 4, 8, 2]
+    assert a.launch() == [128, 8, 8, 2]
     b.set_launch(128, 2, 16, 1)
     assert b.launch() == [128, 2, 16, 1]
     a.step(21)
@@ -418,7 +418,7 @@ def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
 
 
 @pytest.mark.parametrize("name", ["cylinder", "plate", "shock1d", "cylinder_dense"])
-@pytest.mark.parametrize("tile,bps,sort", [(64, 4, 8), (64, 6, 16), (128, 4, 8), (128, 6, 32)])
+@pytest.mark.parametrize("tile,bps,sort", [(64, 6, 8), (64, 8, 16), (128, 4, 8), (128, 8, 32)])
 def test_warp_staged_transport_equals_warp_chunked(cuda_lib, name, tile, bps, sort):
     """The warp-staged transport kernel (per-warp bulk-copied tiles, crossing particles queued and flown 32 at a
     time, records updated in place) gives the state of the warp-chunked kernel bit for bit (particles compared as
@@ -426,7 +426,7 @@ def test_warp_staged_transport_equals_warp_chunked(cuda_lib, name, tile, bps, so
     case = CASES[name]
     a = cuda_lib.Solver(case, precision=0, use_graph=True)
     a.set_launch(256, 4, 8, 1)
-    b = cuda_lib.Solver(case, precision=0, use_graph=(bps == 6))
+    b = cuda_lib.Solver(case, precision=0, use_graph=(bps == 8))
     b.set_launch(tile, bps, sort, 2)
     assert b.launch() == [tile, bps, sort, 2]
     a.step(19)
