@@ -1397,7 +1397,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // of the start cell, 32 particles at a time with no warp-wide operation between them (their loads and Philox
 // chains overlap). A particle that stays and does not collide has only moved: its x, y are written back in
 // place (8 bytes), the rest of its record is left untouched. Holes (cell -1) are skipped. The others (a face
-// ahead within t_r, or colliding; a few percent) go to a global queue as (slot, t_r, collide).
+// ahead within t_r, or colliding; a few percent) go to a global queue: slot, t_r, collide and the fields the
+// warp holds, so that the flight pass reads them contiguously and gathers only w and m.
 // The flight pass (k_particles_fly): one thread per queued particle, at full occupancy and with nothing else
 // waiting on it: the full free flight of fly() (crossings with the dt_R / dt_L scaling, walls, exits) and the
 // tallies, exactly as in k_particles, then the record in place (the whole record but the id, or a hole).
@@ -1538,9 +1539,11 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
 #pragma unroll
             for (int r = 0; r < WT / 32; ++r) {
                 if (code[r] >= 2) {
-                    const int e = qb + __popc(qm[r] & lt_mask);
-                    d.xq_i[e] = (base + r * 32 + lane) | (code[r] == 3 ? (int)0x80000000u : 0);
+                    const int e = qb + __popc(qm[r] & lt_mask), j = r * 32 + lane;
+                    d.xq_i[e] = (base + j) | (code[r] == 3 ? (int)0x80000000u : 0);
                     d.xq_t[e] = trq[r];
+                    d.xq.x[e] = S.x[b][j]; d.xq.y[e] = S.y[b][j]; d.xq.u[e] = S.u[b][j]; d.xq.v[e] = S.v[b][j];
+                    d.xq.cell[e] = S.cell[b][j]; d.xq.pid[e] = S.pid[b][j];
                 }
                 qb += __popc(qm[r]);
             }
@@ -1597,9 +1600,9 @@ __global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const
             const int code = d.xq_i[e];
             const int i = code & 0x7fffffff;
             const bool collide = code < 0;
-            float x = A.x[i], y = A.y[i], u = A.u[i], v = A.v[i], w = A.w[i], m = A.m[i];
-            c = A.cell[i];
-            const unsigned long long pid = A.pid[i];
+            float x = d.xq.x[e], y = d.xq.y[e], u = d.xq.u[e], v = d.xq.v[e], w = A.w[i], m = A.m[i];
+            c = d.xq.cell[e];
+            const unsigned long long pid = d.xq.pid[e];
             const int c0 = c;
             const float m0 = m, u0 = u, v0 = v, w0 = w;
             int it = 0;
@@ -2593,6 +2596,9 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
             if (K.prec == 0) {
                 CK(alloc_particles(ctx, d.pa32, ctx.capacity)); CK(alloc_particles(ctx, d.pb32, ctx.capacity));
                 CK(dalloc(ctx, &d.xq_i, (size_t)ctx.capacity)); CK(dalloc(ctx, &d.xq_t, (size_t)ctx.capacity));
+                CK(dalloc(ctx, &d.xq.x, (size_t)ctx.capacity)); CK(dalloc(ctx, &d.xq.y, (size_t)ctx.capacity));
+                CK(dalloc(ctx, &d.xq.u, (size_t)ctx.capacity)); CK(dalloc(ctx, &d.xq.v, (size_t)ctx.capacity));
+                CK(dalloc(ctx, &d.xq.cell, (size_t)ctx.capacity)); CK(dalloc(ctx, &d.xq.pid, (size_t)ctx.capacity));
                 CK(dalloc(ctx, &d.nxq, 1));
             }
             else { CK(alloc_particles(ctx, d.pa64, ctx.capacity)); CK(alloc_particles(ctx, d.pb64, ctx.capacity)); }

@@ -91,6 +91,8 @@ struct Dev {
     int *xq_i, *nxq;                   // production transport: slots queued by the stay pass for the flight pass
                                        // (bit 31: colliding) and their number
     float* xq_t;                       // their remaining free-flight times
+    ParticleSoA<float> xq;             // their records as the stay pass read them (x, y, u, v, cell, id; w and m
+                                       // unused), so that the flight pass reads them contiguously
     int* scan_tmp;
     double* flux;                      // [4F]
     double *res_part, *res;            // residual: per-block partials; [8] = raw of this step (4 used)
