@@ -47,7 +47,7 @@ __host__ __device__ __forceinline__ double pow2(int e)
 #define UGKWP_SORT_EVERY 8   // steps between counting sorts of the particles by cell
 #endif
 #ifndef UGKWP_PARTICLES_MINB
-#define UGKWP_PARTICLES_MINB 5   // resident 256-thread blocks per SM the transport kernel is compiled for
+#define UGKWP_PARTICLES_MINB 4   // resident 256-thread blocks per SM the warp-chunked transport kernel is compiled for
 #endif
 constexpr int kMaxCells = 1 << 20;
 
@@ -1030,15 +1030,33 @@ __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d,
     }
 }
 
+// A cell's outward normals and plane offsets (the stay and exit tests), copied into registers by 16-byte loads
+// issued together: one memory round trip per cell visited
+template <typename T> struct FaceGeo { T nx[4], ny[4], d[4]; };
+template <typename T>
+__device__ __forceinline__ FaceGeo<T> load_geo(const CellFaces<T>* __restrict__ cf, int c)
+{
+    constexpr int nw = sizeof(FaceGeo<T>) / 16;
+    static_assert(sizeof(FaceGeo<T>) % 16 == 0, "normals and offsets of whole 16-byte words");
+    const uint4* src = reinterpret_cast<const uint4*>(cf + c);
+    uint4 w[nw];
+#pragma unroll
+    for (int k = 0; k < nw; ++k) w[k] = __ldg(src + k);
+    FaceGeo<T> G;
+    memcpy(&G, w, sizeof G);
+    return G;
+}
+
 // A particle at (x, y) moving with (u, v) stays in its cell for the time tr when it reaches none of the faces
 // ahead (n_k . u > 0; the face `entry` is skipped): tr (n_k . u) <= d_k - n_k . x for each of them. No
 // division on this path, which almost every particle takes.
 template <typename T>
-__device__ __forceinline__ bool stays_in(const CellFaces<T>& F, int nf, int entry, T x, T y, T u, T v, T tr)
+__device__ __forceinline__ bool stays_in(const FaceGeo<T>& F, int nf, int entry, T x, T y, T u, T v, T tr)
 {
     bool stays = true;
-    for (int k = 0; k < nf; ++k) {
-        if (k == entry) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k >= nf || k == entry) continue;
         const T un = F.nx[k] * u + F.ny[k] * v;
         if (!(un > T(0))) continue;
         if (tr * un > F.d[k] - (F.nx[k] * x + F.ny[k] * y)) stays = false;
@@ -1071,12 +1089,13 @@ __device__ __forceinline__ bool stays_in_start(const CellFaces<float>& F, int nf
 // smallest wins, ties go to the lower local index; the face `entry` is skipped. Returns the local index, or -1
 // when no face lies ahead, and the exit time in best. Called when stays_in is false, so a face lies ahead.
 template <typename T>
-__device__ __forceinline__ int first_exit(const CellFaces<T>& F, int nf, int entry, T x, T y, T u, T v, T& best)
+__device__ __forceinline__ int first_exit(const FaceGeo<T>& F, int nf, int entry, T x, T y, T u, T v, T& best)
 {
     int kb = -1;
     best = T(0);
-    for (int k = 0; k < nf; ++k) {
-        if (k == entry) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k >= nf || k == entry) continue;
         const T un = F.nx[k] * u + F.ny[k] * v;
         if (!(un > T(0))) continue;
         T t = (F.d[k] - (F.nx[k] * x + F.ny[k] * y)) / un;
@@ -1100,15 +1119,16 @@ __device__ __forceinline__ bool fly(const Dev& d, const CellFaces<T>* __restrict
     it = 0;
     bool alive = true;
     for (;;) {
-        const CellFaces<T>& F = cf[c];
+        const FaceGeo<T> G = load_geo(cf, c);
         const int nf = d.nfc[c];
-        if (stays_in(F, nf, entry, x, y, u, v, tr)) {
+        if (stays_in(G, nf, entry, x, y, u, v, tr)) {
             x = x + u * tr;
             y = y + v * tr;
             break;
         }
         T best;
-        const int kb = first_exit(F, nf, entry, x, y, u, v, best);
+        const int kb = first_exit(G, nf, entry, x, y, u, v, best);
+        const CellFaces<T>& F = cf[c];   // the exit face's data (in L1: the same lines as the normals)
         if (best > tr) best = tr;
         x = x + u * best;
         y = y + v * best;
