@@ -535,7 +535,7 @@ __device__ void shakhov_weights(const StepConsts& K, const Dev& d, int c, double
 // evaluate their fluxes in FP32 in production mode; the faces of wall cells keep the FP64 time integrals
 constexpr int kSeries32 = 12;
 __constant__ float c_series32[6][kSeries32];
-__device__ void lts_coeffs_f32(float dt, float x, float e, double* out)
+__device__ void lts_coeffs_f32(float dt, float x, float e, float* out)
 {
     float phi1, psi2, psi3, chi, beta, kappa;
     if (x < 1.0f) {
@@ -580,13 +580,16 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     // where the wave-flux time integrals need FP64) and at order 2 (whose g^h slope weight needs FP64)
     const bool f32 = K.prec == 0 && !d.wallcell[c] && K.order != 2;
     const double dt = d.dt[c];
+    const float dt32 = (float)dt;
     double tau, x, e;
+    float t32 = 0.0f, x32 = 0.0f, e32 = 0.0f;
     if (f32) {
-        const float t32 = tau_of_f32(K, W);
-        const float x32 = __fdiv_rn((float)dt, t32);
+        t32 = tau_of_f32(K, W);
+        x32 = __fdiv_rn(dt32, t32);
+        e32 = dexp_f32(-x32);
         tau = t32;
         x = x32;
-        e = dexp_f32(-x32);
+        e = e32;
     } else {
         tau = tau_of(K, W);
         x = dt / tau;
@@ -607,13 +610,20 @@ __global__ void k_decompose(const StepConsts K, Dev d)
         d.wprev[5 * c + k] = r[k]; d.wm[5 * c + k] = r[k]; d.wpl[5 * c + k] = r[k]; d.wcol[5 * c + k] = 0;
     }
     for (int k = 0; k < 4; ++k) { Wh[k] = W[k] - Wp[k]; d.Wh[4 * c + k] = Wh[k]; }
-    d.tau[c] = tau;
-    d.xr[c] = x;
-    d.emx[c] = e;
-    // order 2 weights the slope term of g^h with dbar_e + dt e^{-x} / 2, whose FP32 closed form loses too many
-    // digits to cancellation: FP64 coefficients for every cell then
-    if (f32) lts_coeffs_f32((float)dt, (float)x, (float)e, d.co + 7 * c);
-    else lts_coeffs(dt, tau, e, d.co + 7 * c);
+    // FP32 cells keep tau, x, e^{-x} and the coefficients in FP32 only (the FP64 copies would cost conversions
+    // on B300's narrow FP64 pipe; the cell-data read-back rebuilds them from the FP32 values). Order 2 weights
+    // the slope term of g^h with dbar_e + dt e^{-x} / 2, whose FP32 closed form loses too many digits to
+    // cancellation: FP64 coefficients for every cell then
+    if (f32) {
+        lts_coeffs_f32(dt32, x32, e32, d.co32 + 8 * (size_t)c);
+    } else {
+        d.tau[c] = tau;
+        d.xr[c] = x;
+        d.emx[c] = e;
+        lts_coeffs(dt, tau, e, d.co + 7 * c);
+        if (d.co32)
+            for (int k = 0; k < 7; ++k) d.co32[8 * (size_t)c + k] = (float)d.co[7 * c + k];
+    }
     int n = 0;
     double m = 0.0, Ui = 0.0, Vi = 0.0, RTi = 0.0;
     // W^hp = W^h e^{-dt_i/tau_i}; for rho^hp > 0: N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp
@@ -646,12 +656,21 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     d.nhp[c] = n;
     d.mnew[c] = m;
     d.samp[3 * c] = Ui; d.samp[3 * c + 1] = Vi; d.samp[3 * c + 2] = RTi;
-    d.tau32[c] = (float)tau;
-    d.emx32[c] = (float)e;
-    d.dt32[c] = (float)dt;
-    if (d.cst32) d.cst32[c] = make_float4((float)dt, (float)e, (float)tau, __int_as_float(d.nfc[c]));
-    d.mnew32[c] = (float)m;
-    d.samp32[3 * c] = (float)Ui; d.samp32[3 * c + 1] = (float)Vi; d.samp32[3 * c + 2] = (float)RTi;
+    if (!f32) {
+        t32 = (float)tau;
+        e32 = (float)e;
+    }
+    d.tau32[c] = t32;
+    d.emx32[c] = e32;
+    d.dt32[c] = dt32;
+    if (d.cst32) d.cst32[c] = make_float4(dt32, e32, t32, __int_as_float(d.nfc[c]));
+    if (n > 0) {
+        d.mnew32[c] = (float)m;
+        d.samp32[3 * c] = (float)Ui; d.samp32[3 * c + 1] = (float)Vi; d.samp32[3 * c + 2] = (float)RTi;
+    } else {
+        d.mnew32[c] = 0.0f;
+        d.samp32[3 * c] = 0.0f; d.samp32[3 * c + 1] = 0.0f; d.samp32[3 * c + 2] = 0.0f;
+    }
     d.cnt[c] = 0;
     d.cur[c] = 0;
 }
@@ -2016,12 +2035,18 @@ __global__ void k_set_prim(Dev d, int C, const double* prim)
     for (int k = 0; k < 5; ++k) d.wrt[5 * c + k] = 0;
 }
 
-__global__ void k_cell_data(Dev d, int C, double* out)
+__global__ void k_cell_data(const StepConsts K, Dev d, int C, double* out)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     double* o = out + 8 * c;
-    o[0] = d.tau[c]; o[1] = d.xr[c]; o[2] = d.emx[c]; o[3] = (double)d.nhp[c]; o[4] = d.mnew[c];
+    if (K.prec == 0 && !d.wallcell[c] && K.order != 2) {
+        // an FP32 cell of the decomposition: its FP32 values (x = dt / tau by the same FP32 division)
+        o[0] = d.tau32[c]; o[1] = __fdiv_rn(d.dt32[c], d.tau32[c]); o[2] = d.emx32[c];
+    } else {
+        o[0] = d.tau[c]; o[1] = d.xr[c]; o[2] = d.emx[c];
+    }
+    o[3] = (double)d.nhp[c]; o[4] = d.mnew[c];
     o[5] = d.samp[3 * c]; o[6] = d.samp[3 * c + 1]; o[7] = d.samp[3 * c + 2];
 }
 
@@ -2925,7 +2950,7 @@ ugkwp_status ugkwp_get_cell_data(ugkwp_ctx* h, double* out)
     const int C = ctx.k.C;
     double* tmp = nullptr;
     CK(cudaMalloc(&tmp, sizeof(double) * 8 * C));
-    k_cell_data<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, tmp);
+    k_cell_data<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.k, ctx.d, C, tmp);
     CK(cudaMemcpyAsync(out, tmp, sizeof(double) * 8 * C, cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
     cudaFree(tmp);

@@ -391,10 +391,15 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
             rot(c.Wh + 4 * cc, Wh);
         }
     };
-    // normalised coefficient k of cell cc in the precision C of the time integrals
+    // normalised coefficient k of cell cc in the precision C of the time integrals (production mode: the FP32
+    // cells of the decomposition hold theirs in FP32 only)
     auto coef = [&](int cc, int k) -> C {
-        if constexpr (sizeof(C) == 4) return c.co32[8 * cc + k];
-        else return C(c.co[7 * cc + k]);
+        if constexpr (sizeof(C) == 4) {
+            return c.co32[8 * cc + k];
+        } else {
+            if (K.prec == 0 && K.order != 2 && !c.wallcell[cc]) return C(c.co32[8 * cc + k]);
+            return C(c.co[7 * cc + k]);
+        }
     };
     // FP32 moments: the primitive perturbation carrying a side's wave remainder, in the face frame (d rho and
     // d theta are invariant, (dU, dV) rotate like the velocity); unused in FP64
@@ -500,9 +505,9 @@ __device__ __forceinline__ void store_flux(const Dev& c, int f, const double out
     o[1] = make_double2(out[2], out[3]);
 }
 
-// production mode, once per cell before the faces: FP32 copies of W, W^h and the normalised coefficients, and
-// the primitive perturbation that carries W^h's remainder (FP64, rounded once), so that the FP32 faces read
-// 16-byte FP32 loads and run no FP64 work (B300's FP64 pipe is narrow)
+// production mode, once per cell before the faces: FP32 copies of W and W^h and the primitive perturbation that
+// carries W^h's remainder (FP64, rounded once), so that the FP32 faces read 16-byte FP32 loads and run no FP64
+// work (B300's FP64 pipe is narrow); the decomposition wrote the FP32 coefficients
 __global__ void __launch_bounds__(256) k_flux_prep(const StepConsts K, const Dev c)
 {
     const int cc = blockIdx.x * blockDim.x + threadIdx.x;
@@ -514,10 +519,6 @@ __global__ void __launch_bounds__(256) k_flux_prep(const StepConsts K, const Dev
     double dp[4];
     prim_perturbation(W, Wh, dp);
     c.dp32[cc] = make_float4(float(dp[0]), float(dp[1]), float(dp[2]), float(dp[3]));
-    const double* co = c.co + 7 * cc;
-    float4* o = reinterpret_cast<float4*>(c.co32 + 8 * (size_t)cc);
-    o[0] = make_float4(float(co[0]), float(co[1]), float(co[2]), float(co[3]));
-    o[1] = make_float4(float(co[4]), float(co[5]), float(co[6]), 0.0f);
 }
 
 // production mode: every face with FP32 velocity moments; the faces of wall cells apply their time
