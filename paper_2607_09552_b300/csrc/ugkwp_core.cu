@@ -881,43 +881,34 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 }
 
 // ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
-// Eight lanes per cell (four cells per warp; a cell samples about three particles per step on the bench
-// workload). Velocities from the local distribution of the cell at U_i, T_i (Sec. III B): Box-Muller normals
-// (Pr = 1) or Shakhov acceptance-rejection (Pr != 1), shifted and scaled so that the cell's new particles
-// carry exactly the momentum U_i and energy (3/2) R T_i per unit mass of that distribution. Sums in a fixed
-// order: lane j of the cell's eight adds k = j, j + 8, ... in increasing k, then a butterfly combines the
-// lanes (j + 4 into j, j + 2 into j, j + 1 into j; every lane of the group ends with the same value).
-constexpr int kSampleGroup = 8;
-// One cell c (c = K.C: none) per 8-lane group; every lane of the warp calls it together.
+// One warp per sampling cell (the cells listed by the decomposition). Velocities from the local distribution
+// of the cell at U_i, T_i (Sec. III B): Box-Muller normals (Pr = 1) or Shakhov acceptance-rejection (Pr != 1),
+// shifted and scaled so that the cell's new particles carry exactly the momentum U_i and energy (3/2) R T_i per
+// unit mass of that distribution. The draws, positions and tallies run on all 32 lanes (particle k on lane
+// k mod 32); the sums of the shift and scale keep a fixed order: lane j < 8 adds k = j, j + 8, ... in increasing
+// k, then a butterfly combines those eight partial sums (j + 4 into j, j + 2 into j, j + 1 into j).
 template <typename T>
 __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, const ParticleSoA<T>& A,
-                                            const PCell<T>& pc, const long long* dstep, int c, int l)
+                                            const PCell<T>& pc, const long long* dstep, int c)
 {
-    int N = 0;
-    long long base_i = 0;
-    if (c < K.C && d.counts[1] != 0) {
-        N = d.nhp[c];
-        const int nret = d.counts[0];
-        base_i = (long long)nret + d.nhp_off[c];
-        const int cap_left = d.counts[3] - nret;
-        if (N > 0 && d.nhp_off[c] + N > cap_left) {
-            if (l == 0) atomicOr(d.err, ERR_CAPACITY);
-            N = 0;
-        }
+    const int l = threadIdx.x & 31;
+    int N = d.nhp[c];
+    const int nret = d.counts[0];
+    const long long base_i = (long long)nret + d.nhp_off[c];
+    if (N > 0 && d.nhp_off[c] + N > d.counts[3] - nret) {
+        if (l == 0) atomicOr(d.err, ERR_CAPACITY);
+        N = 0;
     }
-    // every lane of the warp takes part in the shuffles below; cells without particles add zeros
-    if (!__any_sync(0xffffffffu, N > 0)) return;   // (the whole warp)
+    if (N == 0) return;   // (the whole warp)
     const Rng g{K.k0, K.k1, (uint32_t)*dstep};
-    const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)(c < K.C ? c : 0) << 11);
-    T su = 0, sv = 0, sw = 0;
+    const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)c << 11);
     int fallbacks = 0;
-    const bool shk = K.shakhov && N > 0;
-    const T ax = shk ? pc.q_(c, 0) : T(0), ay = shk ? pc.q_(c, 1) : T(0);
-    const T M = shk ? pc.q_(c, 2) : T(1);
-    for (int k = l; k < N; k += kSampleGroup) {
-        // Pr = 1: Box-Muller of the Maxwellian of W^h. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-
-        // rejection (Sec. III B): Maxwellian proposals accepted with probability (1 + psi) / M,
-        // psi = (a . z)(|z|^2 - 5), |z| > 6 rejected; after kArAttempts rejections the last proposal stays
+    const T ax = K.shakhov ? pc.q_(c, 0) : T(0), ay = K.shakhov ? pc.q_(c, 1) : T(0);
+    const T M = K.shakhov ? pc.q_(c, 2) : T(1);
+    for (int k = l; k < N; k += 32) {
+        // Pr = 1: Box-Muller normals. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-rejection (Sec. III B):
+        // Maxwellian proposals accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5), |z| > 6
+        // rejected; after kArAttempts rejections the last proposal stays
         T z0 = 0, z1 = 0, z2 = 0;
         const int attempts = K.shakhov ? kArAttempts : 1;
         bool accepted = !K.shakhov;
@@ -941,112 +932,116 @@ __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, c
         }
         if (!accepted) fallbacks++;
         A.u[base_i + k] = z0; A.v[base_i + k] = z1; A.w[base_i + k] = z2;
-        su += z0; sv += z1; sw += z2;
     }
     if (K.shakhov) {
 #pragma unroll
-        for (int o = kSampleGroup / 2; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
         if (l == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
     }
+    __syncwarp();
+    // the eight strided partial sums (lanes 8-31 hold zeros), the butterfly, lane 0's value for every lane
+    T su = 0, sv = 0, sw = 0;
+    if (l < 8)
+        for (int k = l; k < N; k += 8) { su += A.u[base_i + k]; sv += A.v[base_i + k]; sw += A.w[base_i + k]; }
 #pragma unroll
-    for (int o = kSampleGroup / 2; o > 0; o >>= 1) {
+    for (int o = 4; o > 0; o >>= 1) {
         su = su + __shfl_xor_sync(0xffffffffu, su, o);
         sv = sv + __shfl_xor_sync(0xffffffffu, sv, o);
         sw = sw + __shfl_xor_sync(0xffffffffu, sw, o);
     }
-    const T inv = N > 0 ? T(1) / T(N) : T(0);
+    su = __shfl_sync(0xffffffffu, su, 0);
+    sv = __shfl_sync(0xffffffffu, sv, 0);
+    sw = __shfl_sync(0xffffffffu, sw, 0);
+    const T inv = T(1) / T(N);
     const T mu = su * inv, mv = sv * inv, mw = sw * inv;
     T ss = 0;
-    for (int k = l; k < N; k += kSampleGroup) {
-        const T du = A.u[base_i + k] - mu, dv = A.v[base_i + k] - mv, dw = A.w[base_i + k] - mw;
-        ss += (du * du + dv * dv) + dw * dw;
-    }
+    if (l < 8)
+        for (int k = l; k < N; k += 8) {
+            const T du = A.u[base_i + k] - mu, dv = A.v[base_i + k] - mv, dw = A.w[base_i + k] - mw;
+            ss += (du * du + dv * dv) + dw * dw;
+        }
 #pragma unroll
-    for (int o = kSampleGroup / 2; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
+    for (int o = 4; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
+    ss = __shfl_sync(0xffffffffu, ss, 0);
+    __syncwarp();
     long long acc[5] = {0, 0, 0, 0, 0};
-    if (N > 0) {
-        const T Ui = pc.s_(c, 0), Vi = pc.s_(c, 1), RTi = pc.s_(c, 2);
-        const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTi) / ss) : T(0);
-        const T m = pc.m_(c);
-        const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
-        // the cell's vertices in the particle precision and its two triangles' areas (same for every particle)
-        T X[4], Y[4];
+    const T Ui = pc.s_(c, 0), Vi = pc.s_(c, 1), RTi = pc.s_(c, 2);
+    const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTi) / ss) : T(0);
+    const T m = pc.m_(c);
+    const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
+    // the cell's vertices in the particle precision and its two triangles' areas (same for every particle)
+    T X[4], Y[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            X[q] = T(d.cvx[4 * c + q]);
-            Y[q] = K.dim == 1 ? T(0) : T(d.cvy[4 * c + q]);
-        }
-        const T A1 = T(0.5) * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
-        const T A2 = T(0.5) * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
-        const T A12 = A1 + A2;
-        for (int k = l; k < N; k += kSampleGroup) {
-            const uint64_t pid = pbase | (uint64_t)k;
-            const long long i = base_i + k;
-            T U[3], x, y;
-            Unif<T>::get(g, pid, DRAW_POS, 3, U);
-            if (K.dim == 1) {
-                x = X[0] + U[0] * (X[1] - X[0]);
-                y = T(0);
-            } else {
-                const bool first = U[0] * A12 < A1;
-                const int bi = first ? 1 : 2, ci = first ? 2 : 3;
-                const T sq = fsqrt_(U[1]);
-                const T wa = T(1) - sq, wb = sq * (T(1) - U[2]), wc = sq * U[2];
-                x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
-                y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
-            }
-            const T z0 = A.u[i], z1 = A.v[i], z2 = A.w[i];
-            T un, vn, wn;
-            if (N == 1) {
-                // a single particle keeps the direction of its draw at the thermal speed sqrt(3 R T_i) about
-                // U_i: the energy exactly, the momentum without bias
-                const T zz = (z0 * z0 + z1 * z1) + z2 * z2;
-                const T s1 = zz > T(0) ? fsqrt_((T(3) * RTi) / zz) : T(0);
-                un = Ui + s1 * z0; vn = Vi + s1 * z1; wn = s1 * z2;
-            } else {
-                un = Ui + sc * (z0 - mu); vn = Vi + sc * (z1 - mv); wn = sc * (z2 - mw);
-            }
-            A.x[i] = x; A.y[i] = y;
-            A.u[i] = un;
-            A.v[i] = vn;
-            A.w[i] = wn;
-            A.m[i] = m;
-            A.cell[i] = c;
-            A.pid[i] = pid;
-            long long f[5];
-            fix5(m, un, vn, wn, s0, s1, s4, d.err, f);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) acc[q] += f[q];
-        }
+    for (int q = 0; q < 4; ++q) {
+        X[q] = T(d.cvx[4 * c + q]);
+        Y[q] = K.dim == 1 ? T(0) : T(d.cvy[4 * c + q]);
     }
-    // W^{p,-} of the new particles: this group owns the cell, so a butterfly sum and one update (atomic for
+    const T A1 = T(0.5) * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+    const T A2 = T(0.5) * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+    const T A12 = A1 + A2;
+    for (int k = l; k < N; k += 32) {
+        const uint64_t pid = pbase | (uint64_t)k;
+        const long long i = base_i + k;
+        T U[3], x, y;
+        Unif<T>::get(g, pid, DRAW_POS, 3, U);
+        if (K.dim == 1) {
+            x = X[0] + U[0] * (X[1] - X[0]);
+            y = T(0);
+        } else {
+            const bool first = U[0] * A12 < A1;
+            const int bi = first ? 1 : 2, ci = first ? 2 : 3;
+            const T sq = fsqrt_(U[1]);
+            const T wa = T(1) - sq, wb = sq * (T(1) - U[2]), wc = sq * U[2];
+            x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
+            y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
+        }
+        const T z0 = A.u[i], z1 = A.v[i], z2 = A.w[i];
+        T un, vn, wn;
+        if (N == 1) {
+            // a single particle keeps the direction of its draw at the thermal speed sqrt(3 R T_i) about U_i:
+            // the energy exactly, the momentum without bias
+            const T zz = (z0 * z0 + z1 * z1) + z2 * z2;
+            const T s1n = zz > T(0) ? fsqrt_((T(3) * RTi) / zz) : T(0);
+            un = Ui + s1n * z0; vn = Vi + s1n * z1; wn = s1n * z2;
+        } else {
+            un = Ui + sc * (z0 - mu); vn = Vi + sc * (z1 - mv); wn = sc * (z2 - mw);
+        }
+        A.x[i] = x; A.y[i] = y;
+        A.u[i] = un;
+        A.v[i] = vn;
+        A.w[i] = wn;
+        A.m[i] = m;
+        A.cell[i] = c;
+        A.pid[i] = pid;
+        long long f[5];
+        fix5(m, un, vn, wn, s0, s1, s4, d.err, f);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] += f[q];
+    }
+    // W^{p,-} of the new particles: this warp owns the cell, so a butterfly sum and one update (atomic for
     // W^{p,+}: the ghost sources on the second stream may add to the same cell meanwhile)
 #pragma unroll
     for (int q = 0; q < 5; ++q)
-        for (int o = kSampleGroup / 2; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    if (l == 0 && N > 0)
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (l == 0)
         for (int q = 0; q < 5; ++q) {
             d.wm[5 * c + q] += acc[q];
             atomicAdd(reinterpret_cast<unsigned long long*>(d.wpl) + 5 * (size_t)c + q, (unsigned long long)acc[q]);
         }
 }
 
-
 // the cells that sample new particles this step (listed by the decomposition, in any order: each cell's
-// particles, ids and slots depend on the cell alone), four per warp, grid-stride over the list
+// particles, ids and slots depend on the cell alone), one per warp, grid-stride over the list
 template <typename T>
 __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
                                                 ParticleSoA<T> PB, PCell<T> pc, const long long* dstep)
 {
     const ParticleSoA<T> A = *d.bufsel ? PB : PA;   // the buffer holding this step's particles
-    const int l = threadIdx.x & (kSampleGroup - 1);
-    const int grp = (threadIdx.x & 31) / kSampleGroup;
+    if (d.counts[1] == 0) return;
     const int nact = *d.nscell;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; 4 * w < nact; w += nwarps) {
-        const int j = 4 * w + grp;
-        sample_cell(K, d, A, pc, dstep, j < nact ? d.scells[j] : K.C, l);
-    }
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nact; w += nwarps)
+        sample_cell(K, d, A, pc, dstep, d.scells[w]);
 }
 
 // A cell's outward normals and plane offsets (the stay and exit tests), copied into registers by 16-byte loads
@@ -2181,8 +2176,8 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     mark(2, s);
     // the particle kernels only where there are particle buffers (not in the particle-free mode)
     const bool parts = !K.wave_only;
-    if (parts && K.prec == 0) k_sample<float><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
-    else if (parts) k_sample<double><<<4 * ctx.sms, 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
+    if (parts && K.prec == 0) k_sample<float><<<16 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, pc32, d.dstep);
+    else if (parts) k_sample<double><<<16 * ctx.sms, 128, 0, s>>>(K, d, d.pa64, d.pb64, pc64, d.dstep);
     mark(3, s);
     mark(4, s);
     if (parts && K.prec == 0 && ctx.transport == kTransportStaged)
