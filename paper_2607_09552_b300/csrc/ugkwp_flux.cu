@@ -28,26 +28,39 @@
 namespace ugk {
 namespace {
 
-template <typename R> struct Prim { R rho, U, V, lam; };
+template <typename R> struct Prim { R rho, U, V, lam, th; };   // th = R T = 1 / (2 lambda)
 template <typename R> struct Mom { R up[9], um[9], v[7], xi2, xi4, g0; };   // g0: density at u = 0
 
+// FP32 (R = float) trades divisions for one reciprocal and multiplications (a few ulps, far inside the
+// production tolerance); FP64 keeps the divisions of the CPU definition
 template <typename R> __device__ __forceinline__ bool frame_prim(const R W[4], Prim<R>& p)
 {
     p.rho = W[0];
     if (!(W[0] > R(0))) return false;
-    p.U = W[1] / W[0];
-    p.V = W[2] / W[0];
-    const R e = W[3] / W[0] - R(0.5) * (p.U * p.U + p.V * p.V);
+    R e;
+    if constexpr (sizeof(R) == 4) {
+        const R r = R(1) / W[0];
+        p.U = W[1] * r;
+        p.V = W[2] * r;
+        e = W[3] * r - R(0.5) * (p.U * p.U + p.V * p.V);
+    } else {
+        p.U = W[1] / W[0];
+        p.V = W[2] / W[0];
+        e = W[3] / W[0] - R(0.5) * (p.U * p.U + p.V * p.V);
+    }
     if (!(e > R(0))) return false;
     p.lam = R(0.75) / e;
+    p.th = sizeof(R) == 4 ? e * R(2.0 / 3.0) : R(0.5) / p.lam;
     return true;
 }
 
 template <typename R> __device__ __forceinline__ void moments(const Prim<R>& p, Mom<R>& M)
 {
-    const R U = p.U, V = p.V, lam = p.lam, th = R(0.5) / lam;
+    const R U = p.U, V = p.V, lam = p.lam, th = p.th;
     const R sl = sqrt(lam);
-    const R ex = exp(-lam * U * U) / (R(2) * sqrt(R(3.14159265358979323846) * lam));
+    R ex;
+    if constexpr (sizeof(R) == 4) ex = expf(-lam * U * U) * (0.5f * rsqrtf(3.14159265358979323846f * lam));
+    else ex = exp(-lam * U * U) / (R(2) * sqrt(R(3.14159265358979323846) * lam));
     // one erfc per Maxwellian: the smaller half-range mass from erfc(sqrt(lambda)|U|), the other as 1 - it
     const R small = R(0.5) * erfc(sl * fabs(U));
     M.up[0] = U >= R(0) ? R(1) - small : small;
@@ -65,7 +78,7 @@ template <typename R> __device__ __forceinline__ void moments(const Prim<R>& p, 
     for (int k = 2; k < 7; ++k) M.v[k] = V * M.v[k - 1] + R(k - 1) * th * M.v[k - 2];
     M.xi2 = th;
     M.xi4 = R(3) * th * th;
-    M.g0 = ex / th;
+    M.g0 = sizeof(R) == 4 ? ex * (R(2) * lam) : ex / th;
 }
 
 // <psi u^a v^b w^(2c)>, psi = (1, u, v, |u|^2/2)
@@ -97,11 +110,14 @@ __device__ __forceinline__ void psi_poly(const R* Mu, const Mom<R>& M, int a, in
 template <typename R> __device__ __forceinline__ void slope(const Prim<R>& p, const R dw[4], R a[4])
 {
     const R U = p.U, V = p.V, lam = p.lam;
-    const R R4 = R(2) * dw[3] - R(2) * U * dw[1] - R(2) * V * dw[2] + (U * U + V * V) * dw[0] - (R(1.5) / lam) * dw[0];
+    // 1.5 / lambda = 3 th and 0.75 / lambda = 1.5 th in FP32
+    const R i15 = sizeof(R) == 4 ? R(3) * p.th : R(1.5) / lam;
+    const R R4 = R(2) * dw[3] - R(2) * U * dw[1] - R(2) * V * dw[2] + (U * U + V * V) * dw[0] - i15 * dw[0];
     a[3] = (R(4) * lam * lam / R(3)) * R4;
     a[1] = R(2) * lam * (dw[1] - U * dw[0]) - a[3] * U;
     a[2] = R(2) * lam * (dw[2] - V * dw[0]) - a[3] * V;
-    a[0] = dw[0] - a[3] * R(0.75) / lam - a[1] * U - a[2] * V - a[3] * R(0.5) * (U * U + V * V);
+    const R q = sizeof(R) == 4 ? a[3] * (R(1.5) * p.th) : a[3] * R(0.75) / lam;
+    a[0] = dw[0] - q - a[1] * U - a[2] * V - a[3] * R(0.5) * (U * U + V * V);
 }
 
 template <typename R> __device__ __forceinline__ void pr_fix(const Prim<R>& p, R a[4], R Pr)
@@ -129,12 +145,22 @@ __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], co
     moments(p0, m0);
     R t1[4], t2[4];
     R dw[4], aL[4], aR[4], A[4];
+    if constexpr (sizeof(R) == 4) {
+        const R rl = R(1) / (dL * p0.rho), rr = R(1) / (dR * p0.rho);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) dw[k] = (W0[k] - WL[k]) / (dL * p0.rho);
-    slope(p0, dw, aL);
+        for (int k = 0; k < 4; ++k) dw[k] = (W0[k] - WL[k]) * rl;
+        slope(p0, dw, aL);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) dw[k] = (WR[k] - W0[k]) / (dR * p0.rho);
-    slope(p0, dw, aR);
+        for (int k = 0; k < 4; ++k) dw[k] = (WR[k] - W0[k]) * rr;
+        slope(p0, dw, aR);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dw[k] = (W0[k] - WL[k]) / (dL * p0.rho);
+        slope(p0, dw, aL);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dw[k] = (WR[k] - W0[k]) / (dR * p0.rho);
+        slope(p0, dw, aR);
+    }
     pr_fix(p0, aL, Pr);
     pr_fix(p0, aR, Pr);
     psi_poly(m0.up, m0, 1, 0, aL, t1);
@@ -271,7 +297,7 @@ __device__ bool wall_flux(const R WL[4], const R WhL[4], const R dpL[4], C fdL, 
 #pragma unroll
     for (int k = 0; k < 4; ++k) F[k] = caL * C(p.rho * t[k]);
     wave_part<R, C>(p, m, true, WL, WhL, dpL, frL, fdL, nullptr, C(0), F);
-    p.rho = R(1); p.U = R(0); p.V = R(0); p.lam = lam_w;
+    p.rho = R(1); p.U = R(0); p.V = R(0); p.lam = lam_w; p.th = R(0.5) / lam_w;
     moments(p, m);
     psi_mom(m.um, m, 1, 0, 0, t);
     const C rw = -F[0] / C(t[0]);
