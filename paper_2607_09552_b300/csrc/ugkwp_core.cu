@@ -2144,7 +2144,8 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     };
     // profiled steps run the second stream's work on the main stream, so that every stage's events time it
     // alone (overlapped, each stage's events would also count the other stream's kernels sharing the SMs)
-    if (prof) s2 = s;
+    cudaStream_t s3 = ctx.stream3;
+    if (prof) s2 = s3 = s;
     mark(0, s);
     k_begin_step<<<nblk(2LL * K.F, 256), 256, 0, s>>>(K, d);
     if (K.shakhov) {
@@ -2160,13 +2161,15 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     cudaEventRecord(ctx.ev_fork, s);
     cudaStreamWaitEvent(s2, ctx.ev_fork, 0);
     mark(6, s2);
-    // ghost particle sources on the second stream too: they touch only the survivor slots and tallies that the
-    // transport kernel updates atomically (their sort-step slots lie past the step's particles), and they join
-    // before the sort and the update
-    if (K.n_inj > 0 && !K.wave_only) {
-        k_inject_params<<<nblk(K.n_inj, 128), 128, 0, s2>>>(K, d);
-        if (K.prec == 0) k_inject<float><<<nblk(32LL * K.n_inj, 128), 128, 0, s2>>>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
-        else k_inject<double><<<nblk(32LL * K.n_inj, 128), 128, 0, s2>>>(K, d, d.pa64, d.pb64, d.cf64, d.dstep);
+    // ghost particle sources on a third stream: they touch only the slots past the step's particles and the
+    // tallies that the transport kernels update atomically, and they join before the sort and the update
+    const bool inj = K.n_inj > 0 && !K.wave_only;
+    if (inj) {
+        if (s3 != s2) cudaStreamWaitEvent(s3, ctx.ev_fork, 0);
+        k_inject_params<<<nblk(K.n_inj, 128), 128, 0, s3>>>(K, d);
+        if (K.prec == 0) k_inject<float><<<nblk(32LL * K.n_inj, 128), 128, 0, s3>>>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
+        else k_inject<double><<<nblk(32LL * K.n_inj, 128), 128, 0, s3>>>(K, d, d.pa64, d.pb64, d.cf64, d.dstep);
+        if (s3 != s) cudaEventRecord(ctx.ev_join3, s3);
     }
     launch_wave_flux(K, d, ctx.sms, s2);
     mark(7, s2);
@@ -2191,6 +2194,7 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     // counting sort every sort_every-th step (kernels return at once on the other steps), after the ghost
     // sources on the second stream have added their survivors
     cudaStreamWaitEvent(s, ctx.ev_join, 0);
+    if (inj && s3 != s) cudaStreamWaitEvent(s, ctx.ev_join3, 0);
     exclusive_scan(d.cnt, d.off, d.scan_tmp, C, d.counts + 2, s, nullptr, nullptr, d.flags);
     if (parts && K.prec == 0) k_scatter<float><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa32, d.pb32);
     else if (parts) k_scatter<double><<<ctx.grid_particles, 256, 0, s>>>(d, d.pa64, d.pb64);
@@ -2364,8 +2368,10 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         return UGKWP_EINVAL;
     }
     if (cudaStreamCreateWithFlags(&ctx.stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx.stream3, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx.ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx.ev_join3, cudaEventDisableTiming) != cudaSuccess) {
         delete h;
         return UGKWP_ECUDA;
     }
@@ -2677,10 +2683,13 @@ void ugkwp_destroy(ugkwp_ctx* h)
     if (ctx.graph) cudaGraphExecDestroy(ctx.graph);
     for (cudaEvent_t e : ctx.prof_events) cudaEventDestroy(e);
     if (ctx.stream2) cudaStreamSynchronize(ctx.stream2);
+    if (ctx.stream3) cudaStreamSynchronize(ctx.stream3);
     for (void* p : ctx.allocs) cudaFree(p);
     if (ctx.stream2) cudaStreamDestroy(ctx.stream2);
+    if (ctx.stream3) cudaStreamDestroy(ctx.stream3);
     if (ctx.ev_fork) cudaEventDestroy(ctx.ev_fork);
     if (ctx.ev_join) cudaEventDestroy(ctx.ev_join);
+    if (ctx.ev_join3) cudaEventDestroy(ctx.ev_join3);
     delete h;
 }
 

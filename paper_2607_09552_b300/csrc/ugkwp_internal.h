@@ -128,7 +128,8 @@ struct Ctx {
     int transport = 1;                           // transport kernel: kTransportWarp or kTransportStaged
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;              // wave fluxes, overlapped with the particle kernels
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t stream3 = nullptr;              // ghost particle sources, overlapped with both
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
     int64_t step = 0;
     double Kn = 0.0, Ma = 0.0;                   // case conditions (warm-start features)
     double res_scale[4] = {1.0, 1.0, 1.0, 1.0}; // freestream scale of the residual per component
