@@ -1865,7 +1865,7 @@ __global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA,
 // Threads [0, C): conservative update of one cell, residual term, particle-mass-ratio EMA, vacuum floor.
 // Threads [C, C + n_wall): wall pressure, shear stress and heat flux of one wall face (a11, Sec. V A).
 // The last block to finish reduces the residual partials in block order and closes the step.
-constexpr int kUpdateBlock = 256;
+constexpr int kUpdateBlock = 128;
 __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev d, long long* dstep)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
