@@ -33,15 +33,27 @@ def assert_particles_equal(pg, po):
         assert bad.size == 0, (k, bad[:5], a[k][bad[:5]], b[k][bad[:5]])
 
 
-def assert_field_close(Wg, Wo, tol):
-    """max_i |W_gpu - W_oracle| <= tol * max_i |W_oracle| per conservative component."""
-    for c in range(4):
+def assert_field_close(Wg, Wo, tol, floor=None):
+    """Per conservative component c: every element within tol of the oracle's value relative to
+    max(|W_oracle|, floor * max_i |W_oracle|) (per element; the floor keeps components that cross zero and
+    near-vacuum cells, which hold no weight in the step, from a division by nearly nothing), and
+    max_i |W_gpu - W_oracle| <= tol * max_i |W_oracle|. Default floor: 0.1 of the component's scale in production
+    precision (FP32 wave-flux moments; measured worst element 0.63 tol), 0.01 in the all-FP64 mode (last-bit
+    differences of the two sides' transcendental functions, amplified in low-density cells; measured worst
+    element 0.26 tol)."""
+    if floor is None:
+        floor = 1e-1 if tol > 1e-8 else 1e-2
+    for c in range(Wo.shape[1]):
         scale = np.abs(Wo[:, c]).max()
         if scale == 0.0:
             assert np.abs(Wg[:, c]).max() == 0.0
             continue
-        err = np.abs(Wg[:, c] - Wo[:, c]).max()
-        assert err <= tol * scale, (c, err / scale)
+        err = np.abs(Wg[:, c] - Wo[:, c])
+        assert err.max() <= tol * scale, (c, err.max() / scale)
+        den = np.maximum(np.abs(Wo[:, c]), floor * scale)
+        rel = err / den
+        k = int(np.argmax(rel))
+        assert rel[k] <= tol, (c, k, rel[k], Wg[k, c], Wo[k, c])
 
 
 def snapshot(o):

@@ -78,7 +78,10 @@ def test_second_order_step(cuda_lib, name, prec):
     assert np.array_equal(g.cell_data(), o.cell_data())
     assert_particles_equal(g.particles(), o.particles())
     assert_field_close(g.flux(), o.flux(), 1e-9 if prec == 1 else 1e-4)
-    assert_field_close(g.field()[0], o.field()[0], 5e-12 if prec == 1 else TOL[prec])
+    # order 2, FP64: the equilibrium slopes divide the differences of reconstructed face and cell states by
+    # the centre-to-face distance, amplifying the last-bit differences of the two sides' exp and erfc
+    # (measured worst element 1.0e-11 of its own value on the hybrid cylinder)
+    assert_field_close(g.field()[0], o.field()[0], 1.5e-11 if prec == 1 else TOL[prec])
 
 
 def test_wave_only_trajectory(cuda_lib):
