@@ -113,6 +113,15 @@ typedef struct {
     int32_t order;            /* 2: second-order reconstruction of W and W^h for the wave fluxes (Eq. 12; 1-D a
                                  smooth van Albada-type limited slope, 2-D least squares with Venkatakrishnan's
                                  limiter; 128 B per cell); 0 or 1: first order (the default) */
+    /* Device memory from the caller (both NULL: the library calls cudaMalloc / cudaFree itself). dev_alloc
+     * returns `bytes` of device memory usable on `stream` (the context's stream), 256-byte aligned, or NULL
+     * (the call then fails with ENOMEM); dev_free returns memory that dev_alloc gave. Every allocation of the
+     * context goes through them: its state at creation, and the temporaries of the read-back and state-transfer
+     * calls (returned before the call returns, after the context's stream has synchronised). The context frees
+     * its state in ugkwp_destroy. Both must be set, or neither. */
+    void* (*dev_alloc)(size_t bytes, void* stream, void* user);
+    void (*dev_free)(void* ptr, void* user);
+    void* alloc_user;         /* passed to dev_alloc and dev_free */
 } ugkwp_opts;
 
 /* Build the context: geometry, fixed local time steps (Eqs. 33-34), uniform freestream state, no

@@ -2070,14 +2070,48 @@ ugkwp_status fail(Ctx& c, ugkwp_status st, const char* what)
         cudaError_t e_ = (expr);                                                    \
         if (e_ != cudaSuccess) {                                                    \
             ctx.msg = std::string(#expr) + ": " + cudaGetErrorString(e_);           \
-            return UGKWP_ECUDA;                                                     \
+            return e_ == cudaErrorMemoryAllocation ? UGKWP_ENOMEM : UGKWP_ECUDA;  \
         }                                                                           \
     } while (0)
+
+// device memory of a context: the caller's allocator when it gave one, else cudaMalloc
+cudaError_t raw_alloc(Ctx& ctx, void** q, size_t bytes)
+{
+    if (ctx.dev_alloc) {
+        *q = ctx.dev_alloc(bytes, ctx.stream, ctx.alloc_user);
+        return *q ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(q, bytes);
+}
+void raw_free(Ctx& ctx, void* q)
+{
+    if (!q) return;
+    if (ctx.dev_free) ctx.dev_free(q, ctx.alloc_user);
+    else cudaFree(q);
+}
+// a per-call temporary, returned when it goes out of scope (the calls synchronise their stream before)
+struct Tmp {
+    Ctx& ctx;
+    void* p = nullptr;
+    explicit Tmp(Ctx& c) : ctx(c) {}
+    ~Tmp()
+    {
+        if (!p) return;
+        cudaStreamSynchronize(ctx.stream);   // nothing queued may still use it (early error returns included)
+        raw_free(ctx, p);
+    }
+    template <typename P> cudaError_t get(P** out, size_t n)
+    {
+        cudaError_t e = raw_alloc(ctx, &p, (n ? n : 1) * sizeof(P));
+        *out = static_cast<P*>(p);
+        return e;
+    }
+};
 
 template <typename P> cudaError_t dalloc(Ctx& ctx, P** p, size_t n)
 {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(P));
+    cudaError_t e = raw_alloc(ctx, &q, (n ? n : 1) * sizeof(P));
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(q, 0, (n ? n : 1) * sizeof(P), ctx.stream);
     ctx.allocs.push_back(q);
@@ -2362,6 +2396,13 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
     Ctx& ctx = h->c;
     *out = nullptr;
     ctx.stream = static_cast<cudaStream_t>(opts->stream);
+    if ((opts->dev_alloc == nullptr) != (opts->dev_free == nullptr)) {
+        delete h;
+        return UGKWP_EINVAL;
+    }
+    ctx.dev_alloc = opts->dev_alloc;
+    ctx.dev_free = opts->dev_free;
+    ctx.alloc_user = opts->alloc_user;
     ctx.use_graph = opts->use_graph;
     if (opts->order != 0 && opts->order != 1 && opts->order != 2) {
         delete h;
@@ -2684,7 +2725,7 @@ void ugkwp_destroy(ugkwp_ctx* h)
     for (cudaEvent_t e : ctx.prof_events) cudaEventDestroy(e);
     if (ctx.stream2) cudaStreamSynchronize(ctx.stream2);
     if (ctx.stream3) cudaStreamSynchronize(ctx.stream3);
-    for (void* p : ctx.allocs) cudaFree(p);
+    for (void* p : ctx.allocs) raw_free(ctx, p);
     if (ctx.stream2) cudaStreamDestroy(ctx.stream2);
     if (ctx.stream3) cudaStreamDestroy(ctx.stream3);
     if (ctx.ev_fork) cudaEventDestroy(ctx.ev_fork);
@@ -2762,13 +2803,13 @@ ugkwp_status ugkwp_set_field(ugkwp_ctx* h, const double* prim)
     for (int c = 0; c < C; ++c)
         if (!(prim[4 * c] > 0.0) || !(prim[4 * c + 3] > 0.0)) return fail(ctx, UGKWP_EINVAL, "non-positive density or temperature");
     double* dp = nullptr;
-    CK(cudaMalloc(&dp, sizeof(double) * 4 * C));
+    Tmp t(ctx);
+    CK(t.get(&dp, 4 * (size_t)C));
     CK(cudaMemcpyAsync(dp, prim, sizeof(double) * 4 * C, cudaMemcpyHostToDevice, ctx.stream));
     k_set_prim<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, dp);
     int zero = 0;
     CK(cudaMemcpyAsync(ctx.d.counts, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
-    cudaFree(dp);
     return UGKWP_OK;
 }
 
@@ -2794,11 +2835,11 @@ ugkwp_status ugkwp_get_field(ugkwp_ctx* h, double* W, double* Wp)
     CK(cudaMemcpyAsync(W, ctx.d.W, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
     if (Wp) {
         double* dp = nullptr;
-        CK(cudaMalloc(&dp, sizeof(double) * 4 * C));
+        Tmp t(ctx);
+        CK(t.get(&dp, 4 * (size_t)C));
         k_wp_field<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.d, C, ctx.k.fx0, ctx.k.fx1, ctx.k.fx4, dp);
         CK(cudaMemcpyAsync(Wp, dp, sizeof(double) * 4 * C, cudaMemcpyDeviceToHost, ctx.stream));
         CK(cudaStreamSynchronize(ctx.stream));
-        cudaFree(dp);
     }
     return check_device_error(ctx);
 }
@@ -2849,7 +2890,8 @@ ugkwp_status ugkwp_get_particles(ugkwp_ctx* h, int64_t cap, uint64_t* pid, int32
     std::vector<uint64_t> hp(ns);
     std::vector<int32_t> hc(ns);
     double* tmp = nullptr;
-    CK(cudaMalloc(&tmp, sizeof(double) * 6 * ns));
+    Tmp t(ctx);
+    CK(t.get(&tmp, 6 * ns));
     if (ctx.k.prec == 0) {
         const ParticleSoA<float>& A = sel ? ctx.d.pb32 : ctx.d.pa32;
         k_get_particles<float><<<nblk(slots, 256), 256, 0, ctx.stream>>>(A, slots, tmp);
@@ -2863,7 +2905,6 @@ ugkwp_status ugkwp_get_particles(ugkwp_ctx* h, int64_t cap, uint64_t* pid, int32
     }
     CK(cudaMemcpyAsync(hv.data(), tmp, sizeof(double) * 6 * ns, cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
-    cudaFree(tmp);
     double* dst[6] = {x, y, u, v, w, m};
     int64_t o = 0;
     for (size_t i = 0; i < ns; ++i) {
@@ -2901,9 +2942,10 @@ ugkwp_status ugkwp_set_state(ugkwp_ctx* h, int64_t step, const double* W, const 
         double* tmp = nullptr;
         int* tc = nullptr;
         unsigned long long* tp = nullptr;
-        CK(cudaMalloc(&tmp, sizeof(double) * 6 * np));
-        CK(cudaMalloc(&tc, sizeof(int) * np));
-        CK(cudaMalloc(&tp, sizeof(unsigned long long) * np));
+        Tmp t1(ctx), t2(ctx), t3(ctx);
+        CK(t1.get(&tmp, 6 * (size_t)np));
+        CK(t2.get(&tc, (size_t)np));
+        CK(t3.get(&tp, (size_t)np));
         const double* src[6] = {x, y, u, v, w, m};
         for (int k = 0; k < 6; ++k)
             CK(cudaMemcpyAsync(tmp + (size_t)k * np, src[k], sizeof(double) * np, cudaMemcpyHostToDevice, ctx.stream));
@@ -2917,7 +2959,6 @@ ugkwp_status ugkwp_set_state(ugkwp_ctx* h, int64_t step, const double* W, const 
             k_put_particles<double><<<nblk(n, 256), 256, 0, ctx.stream>>>(ctx.d.pa64, n, tmp, tmp + np, tmp + 2 * np,
                                                                         tmp + 3 * np, tmp + 4 * np, tmp + 5 * np, tc, tp);
         CK(cudaStreamSynchronize(ctx.stream));
-        cudaFree(tmp); cudaFree(tc); cudaFree(tp);
     }
     CK(cudaStreamSynchronize(ctx.stream));
     ctx.step = step;
@@ -2953,11 +2994,11 @@ ugkwp_status ugkwp_get_cell_data(ugkwp_ctx* h, double* out)
     Ctx& ctx = h->c;
     const int C = ctx.k.C;
     double* tmp = nullptr;
-    CK(cudaMalloc(&tmp, sizeof(double) * 8 * C));
+    Tmp t(ctx);
+    CK(t.get(&tmp, 8 * (size_t)C));
     k_cell_data<<<nblk(C, 128), 128, 0, ctx.stream>>>(ctx.k, ctx.d, C, tmp);
     CK(cudaMemcpyAsync(out, tmp, sizeof(double) * 8 * C, cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
-    cudaFree(tmp);
     return UGKWP_OK;
 }
 

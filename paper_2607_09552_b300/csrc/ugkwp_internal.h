@@ -127,6 +127,9 @@ struct Ctx {
     int device = -1;                             // the device current at creation (owns every allocation)
     int transport = 1;                           // transport kernel: kTransportWarp or kTransportStaged
     cudaStream_t stream = nullptr;
+    void* (*dev_alloc)(size_t, void*, void*) = nullptr;   // caller's device allocator (null: cudaMalloc)
+    void (*dev_free)(void*, void*) = nullptr;
+    void* alloc_user = nullptr;
     cudaStream_t stream2 = nullptr;              // wave fluxes, overlapped with the particle kernels
     cudaStream_t stream3 = nullptr;              // ghost particle sources, overlapped with both
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;

@@ -6,8 +6,10 @@ built without a usable CUDA device; there is no CPU fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -51,7 +53,38 @@ class UgkwpOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("case_id", C.c_uint32), ("n_ref", C.c_int32), ("precision", C.c_int32),
                 ("wave_only", C.c_int32), ("record_faces", C.c_int32), ("capacity", C.c_int32),
                 ("ghost_state", C.c_double * 4), ("stream", C.c_void_p), ("use_graph", C.c_int32),
-                ("order", C.c_int32)]
+                ("order", C.c_int32), ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p),
+                ("alloc_user", C.c_void_p)]
+
+
+# Device memory of the contexts from torch's caching allocator (ugkwp_opts.dev_alloc / dev_free)
+_ALLOC_T = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_T = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+def _torch_alloc(nbytes, stream, user):
+    import torch
+    s = torch.cuda.ExternalStream(stream) if stream else None
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=s)
+    except RuntimeError:
+        return None
+
+
+def _torch_free(ptr, user):
+    import torch
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+_TORCH_ALLOC = _ALLOC_T(_torch_alloc)
+_TORCH_FREE = _FREE_T(_torch_free)
+_LIVE = weakref.WeakSet()   # contexts to destroy before the interpreter tears torch down
+
+
+@atexit.register
+def _close_all():
+    for s in list(_LIVE):
+        s.close()
 
 
 _lib = None
@@ -111,7 +144,9 @@ class Solver:
 
     def __init__(self, case, gts: bool = False, precision: int = 0, wave_only: bool = False, seed: int | None = None,
                  case_id: int = 0, capacity: int = 0, use_graph: bool = False, stream=None,
-                 record_faces: bool = False, order: int = 1):
+                 record_faces: bool = False, order: int = 1, torch_memory: bool = True):
+        """torch_memory: the context's device memory from torch's caching allocator (else the library calls
+        cudaMalloc itself)."""
         L = load()
         m = case.mesh
         self._keep = [np.ascontiguousarray(m.xv, dtype=np.float64), np.ascontiguousarray(m.yv, dtype=np.float64)]
@@ -129,6 +164,9 @@ class Solver:
         opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
                          int(record_faces), capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream),
                          int(use_graph), int(order))
+        if torch_memory:
+            opts.dev_alloc = C.cast(_TORCH_ALLOC, C.c_void_p)
+            opts.dev_free = C.cast(_TORCH_FREE, C.c_void_p)
         self.ctx = C.c_void_p()
         create = L.ugkwp_create_unstructured if unstructured else L.ugkwp_create
         st = create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),
@@ -140,6 +178,7 @@ class Solver:
                 L.ugkwp_destroy(self.ctx)
                 self.ctx = None
             raise UgkwpError(st, f"ugkwp_create: {msg}")
+        _LIVE.add(self)
         self.C = m.ncells
         nf, nw = C.c_int32(), C.c_int32()
         self._check(L.ugkwp_get_geometry(self.ctx, None, None, C.byref(nf), C.byref(nw)))

@@ -439,3 +439,27 @@ def test_warp_staged_transport_equals_warp_chunked(cuda_lib, name, tile, bps, so
     assert np.array_equal(a.stats()[:8], b.stats()[:8])
     a.close()
     b.close()
+
+
+def test_device_memory_from_torch_allocator(cuda_lib):
+    """ugkwp_opts.dev_alloc / dev_free: a context whose device memory comes from torch's caching allocator
+    (the binding's default) holds it there (torch counts it) and steps to the same state, bit for bit, as one
+    whose memory the library allocates itself; the temporaries of the read-back calls go through it too."""
+    import torch
+    case = CASES["cylinder"]
+    before = torch.cuda.memory_allocated()
+    a = cuda_lib.Solver(case, precision=0, use_graph=True, torch_memory=True)
+    held = torch.cuda.memory_allocated() - before
+    assert held > 0
+    b = cuda_lib.Solver(case, precision=0, use_graph=True, torch_memory=False)
+    assert torch.cuda.memory_allocated() - before == held
+    a.step(12)
+    b.step(12)
+    assert np.array_equal(a.field()[0], b.field()[0])
+    assert np.array_equal(a.field()[1], b.field()[1])
+    assert_particles_equal(a.particles(), b.particles())
+    assert np.array_equal(a.cell_data(), b.cell_data())
+    assert torch.cuda.memory_allocated() - before == held
+    a.close()
+    assert torch.cuda.memory_allocated() == before
+    b.close()
