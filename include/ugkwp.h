@@ -157,6 +157,15 @@ ugkwp_status ugkwp_residual(ugkwp_ctx* ctx, double* out);
 ugkwp_status ugkwp_surface(ugkwp_ctx* ctx, double* p, double* tau_w, double* q, int32_t n_wall,
                            int32_t averaged);
 ugkwp_status ugkwp_reset_surface(ugkwp_ctx* ctx);
+/* Monitored wall loads of the last step (Sec. V A: EMA histories of wall quantities judge the steady state;
+ * Sec. V B: the drag coefficient), computed on the device at the end of every step: out[0] C_d = F_x /
+ * (rho_inf U_inf^2 / 2) and out[1] C_H = Q / (rho_inf U_inf^3 / 2) with F = sum_j s_j (p_j n_j + tau_j t_j),
+ * t = (-n_y, n_x), Q = sum_j s_j q_j over the wall faces (L_ref = 1); out[2] C_p = (p - p_inf) /
+ * (rho_inf U_inf^2 / 2) and out[3] C_Q = q / (rho_inf U_inf^3 / 2) at the stagnation point, the mean of the
+ * two wall faces whose normals face the freestream most (NaN when none faces it within 60 degrees, e.g. a
+ * plate along the flow); out[4..7] their EMAs with alpha = 2/1001 from the first surface sample after
+ * creation or ugkwp_reset_surface. NaN before the first step. Synchronises. out: 8 host doubles. */
+ugkwp_status ugkwp_monitors(ugkwp_ctx* ctx, double* out);
 
 /* Set the cell state from host primitives (rho, U, V, T) per cell (4 C doubles); removes all particles
  * (W^p = 0). The local time steps are unchanged. */
@@ -230,7 +239,7 @@ ugkwp_status ugkwp_batch_step(ugkwp_batch* batch, int32_t n_steps);
 void ugkwp_batch_destroy(ugkwp_batch* batch);
 
 /* Checkpoint: the whole state (step counter, W, retained tally, particles, last residual,
- * particle-mass-ratio EMA, surface sums and counters) to a binary file, and back into a context created
+ * particle-mass-ratio EMA, surface sums, monitors and counters) to a binary file, and back into a context created
  * with the same mesh, gas, mode, precision and options. Steps after ugkwp_load reproduce the uninterrupted
  * run (the particle draws are keyed by particle id and step). The local time steps are not part of the
  * state: a run that replaced them (ugkwp_set_time_steps) replaces them again after loading. Both

@@ -199,6 +199,12 @@ class Oracle:
                                          C.c_int32(int(averaged))))
         return p, t, q
 
+    def monitors(self):
+        """[C_d, C_H, stagnation C_p, C_Q, then their EMAs] of the last step"""
+        out = np.zeros(8)
+        self._check(lib().oracle_monitors(self.ctx, dptr(out)))
+        return out
+
     def stats(self):
         """[steps, particles, new, removed, left, crossings, wall hits, max iterations, floored cells,
         A-R fallbacks, particles entering from ghosts]"""

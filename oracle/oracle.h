@@ -72,6 +72,9 @@ int  oracle_set_field(oracle_ctx* cx, const double* prim);          /* 4 per cel
 int  oracle_get_field(oracle_ctx* cx, double* W, double* Wp);       /* 4 per cell each; Wp nullable */
 int  oracle_residual(oracle_ctx* cx, double* out);                  /* [8]: freestream-normalised, raw */
 int  oracle_surface(oracle_ctx* cx, double* p, double* tau, double* q, int32_t n_wall, int32_t averaged);
+/* monitored wall loads of the last step: C_d, C_H, stagnation C_p, C_Q (NaN without a stagnation point), then
+ * their EMAs (alpha = 2/1001) from the first step on */
+int  oracle_monitors(oracle_ctx* cx, double* out);
 /* building block: n new-particle normal triples z[3n] of particle ids pid0 + k drawn for a Shakhov cell with
  * acceptance-rejection weights (ax, ay, M) (see shakhov_weights); returns the fallback count */
 int64_t oracle_ar_sample(int32_t precision, uint64_t seed, uint32_t case_id, int64_t step, uint64_t pid0, int32_t n,

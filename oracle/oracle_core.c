@@ -49,6 +49,8 @@ static void* zalloc(size_t n, size_t sz)
     return p;
 }
 
+static void find_stagnation(or_ctx* cx);
+
 /* ---------------------------------------------------------------- kinetic model helpers (Sec. II) */
 
 /* conservative (rho, rho U, rho V, rho E) of a primitive state; E = |U|^2/2 + (3/2) R T */
@@ -873,6 +875,8 @@ static int finish_create(or_ctx* cx, const oracle_gas* gas, double Kn, double Ma
     cx->flux = zalloc(4 * F, 8);
     cx->chi_ema = zalloc(C, 8);
     cx->surf_sum = zalloc(3 * cx->nwall, 8); cx->surf_last = zalloc(3 * cx->nwall, 8);
+    find_stagnation(cx);
+    for (int k = 0; k < 8; ++k) cx->mon[k] = NAN;
     cx->cap = 1024;
     cx->p = zalloc(cx->cap, sizeof(or_particle));
     for (int c = 0; c < C; ++c)
@@ -1297,6 +1301,8 @@ static void update(or_ctx* cx)
 
 /* ------------------------------------------------------------ a11: surface quantities (Sec. V A) */
 
+static void monitors(or_ctx* cx);
+
 static void surface(or_ctx* cx)
 {
     const double s1 = ldexp(1.0, -cx->fx[1]), s4 = ldexp(1.0, -cx->fx[2]);
@@ -1314,7 +1320,64 @@ static void surface(or_ctx* cx)
         cx->surf_last[3 * iw] = p; cx->surf_last[3 * iw + 1] = tw; cx->surf_last[3 * iw + 2] = q;
         cx->surf_sum[3 * iw] += p; cx->surf_sum[3 * iw + 1] += tw; cx->surf_sum[3 * iw + 2] += q;
     }
+    monitors(cx);
     cx->nsurf += 1;
+}
+
+/* Monitored wall loads (Sec. V A, V B; reading of their definitions, L_ref = 1): drag coefficient
+ * C_d = F_x / (rho_inf U_inf^2 / 2) and heat-load coefficient C_H = Q / (rho_inf U_inf^3 / 2), with
+ * F = sum_j s_j (p_j n_j + tau_j t_j), t = (-n_y, n_x), Q = sum_j s_j q_j over the wall faces in order (n: the
+ * fluid cell's outward normal); at the stagnation point, the mean of the two wall faces adjacent to it (S29),
+ * C_p = (p - p_inf) / (rho_inf U_inf^2 / 2) and C_Q = q / (rho_inf U_inf^3 / 2); each followed by its EMA
+ * (alpha = 2/1001, the monitor of Sec. V A) from the first surface sample on. */
+static void monitors(or_ctx* cx)
+{
+    const double U = cx->W_inf[1] / cx->W_inf[0];
+    const double qd = 0.5 * cx->W_inf[0] * (U * U), qh = 0.5 * cx->W_inf[0] * ((U * U) * U);
+    const double p_inf = cx->W_inf[0] * OR_R;   /* T_inf = 1 */
+    double fx = 0.0, Q = 0.0;
+    for (int iw = 0; iw < cx->nwall; ++iw) {
+        const int f = cx->wall_face[iw];
+        const double* sv = cx->surf_last + 3 * iw;
+        fx += cx->fs[f] * (sv[0] * cx->fnx[f] - sv[1] * cx->fny[f]);
+        Q += cx->fs[f] * sv[2];
+    }
+    double v[4] = {fx / qd, Q / qh, NAN, NAN};
+    if (cx->stag[0] >= 0) {
+        const double ps = 0.5 * (cx->surf_last[3 * cx->stag[0]] + cx->surf_last[3 * cx->stag[1]]);
+        const double qs = 0.5 * (cx->surf_last[3 * cx->stag[0] + 2] + cx->surf_last[3 * cx->stag[1] + 2]);
+        v[2] = (ps - p_inf) / qd;
+        v[3] = qs / qh;
+    }
+    const double alpha = 2.0 / 1001.0;
+    for (int k = 0; k < 4; ++k) {
+        cx->mon[k] = v[k];
+        cx->mon[4 + k] = cx->nsurf == 0 ? v[k] : cx->mon[4 + k] + alpha * (v[k] - cx->mon[4 + k]);
+    }
+}
+
+/* the stagnation point's two wall faces (reading): the two whose fluid-cell normals face the freestream
+ * (+x) most, ties to the lower index, when the best of them is within 60 degrees of it (a blunt body);
+ * none otherwise (e.g. a flat plate along the flow) */
+static void find_stagnation(or_ctx* cx)
+{
+    int a = -1, b = -1;
+    for (int iw = 0; iw < cx->nwall; ++iw) {
+        const double nx = cx->fnx[cx->wall_face[iw]];
+        if (a < 0 || nx > cx->fnx[cx->wall_face[a]]) { b = a; a = iw; }
+        else if (b < 0 || nx > cx->fnx[cx->wall_face[b]]) b = iw;
+    }
+    cx->stag[0] = cx->stag[1] = -1;
+    if (a >= 0 && b >= 0 && cx->fnx[cx->wall_face[a]] > 0.5) {
+        cx->stag[0] = a < b ? a : b;
+        cx->stag[1] = a < b ? b : a;
+    }
+}
+
+int oracle_monitors(oracle_ctx* cx, double* out)
+{
+    for (int k = 0; k < 8; ++k) out[k] = cx->mon[k];
+    return cx->err;
 }
 
 /* ----------------------------------------------------------------------------------- one step */

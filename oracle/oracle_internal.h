@@ -84,6 +84,8 @@ struct oracle_ctx {
     double* chi_ema;
     double *surf_sum, *surf_last;
     int64_t nsurf;
+    double mon[8];                               /* C_d, C_H, stagnation C_p and C_Q, then their EMAs */
+    int stag[2];                                 /* wall faces of the stagnation point (-1: none) */
     int64_t stats[11];                           /* [8]: cells set to the vacuum floor in the last step,
                                                   * [9]: A-R samplings that fell back to the Maxwellian,
                                                   * [10]: particles entering from far-field / fixed ghosts */

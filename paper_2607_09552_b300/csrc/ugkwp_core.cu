@@ -16,6 +16,7 @@
 //   k_update      a10, a11  per cell: Eq. 53, residual, particle-mass-ratio EMA; per wall face: p, tau_w, q;
 //                      the last block closes the step
 #include <cuda_runtime.h>
+#include <math_constants.h>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1961,8 +1962,48 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
             for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + h];
         __syncthreads();
     }
+    // monitored wall loads (Sec. V A, V B): F_x = sum_j s_j (p_j n_x - tau_j n_y), Q = sum_j s_j q_j over the
+    // wall faces, summed by the block like the residual (thread t: faces t, t + 128, ..., then the tree)
+    double fx = 0.0, fq = 0.0;
+    for (int iw = threadIdx.x; iw < K.nwall; iw += kUpdateBlock) {
+        const int f = d.wall_face[iw];
+        const double* sv = d.surf_last + 3 * (size_t)iw;
+        fx += d.fs[f] * (sv[0] * d.fnx[f] - sv[1] * d.fny[f]);
+        fq += d.fs[f] * sv[2];
+    }
+    __syncthreads();
+    const double rs0 = sm[0][0], rs1 = sm[1][0], rs2 = sm[2][0], rs3 = sm[3][0];
+    __syncthreads();
+    sm[0][threadIdx.x] = fx;
+    sm[1][threadIdx.x] = fq;
+    __syncthreads();
+    for (int h = kUpdateBlock / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sm[0][threadIdx.x] += sm[0][threadIdx.x + h];
+            sm[1][threadIdx.x] += sm[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
     if (threadIdx.x != 0) return;
-    for (int q = 0; q < 4; ++q) d.res[q] = sqrt(sm[q][0]);
+    d.res[0] = sqrt(rs0); d.res[1] = sqrt(rs1); d.res[2] = sqrt(rs2); d.res[3] = sqrt(rs3);
+    {
+        // C_d, C_H; stagnation C_p = (p - p_inf) / (rho U^2 / 2), C_Q = q / (rho U^3 / 2) from the mean of
+        // the stagnation point's two faces; each EMA (alpha = 2/1001) from the first surface sample on
+        const double U = K.W_inf[1] / K.W_inf[0];
+        const double qd = 0.5 * K.W_inf[0] * (U * U), qh = 0.5 * K.W_inf[0] * ((U * U) * U);
+        double v[4] = {sm[0][0] / qd, sm[1][0] / qh, CUDART_NAN, CUDART_NAN};
+        if (K.stag0 >= 0) {
+            const double* a = d.surf_last + 3 * (size_t)K.stag0;
+            const double* b = d.surf_last + 3 * (size_t)K.stag1;
+            v[2] = (0.5 * (a[0] + b[0]) - K.W_inf[0] * kR) / qd;
+            v[3] = (0.5 * (a[2] + b[2])) / qh;
+        }
+        const bool first = d.stats[8] == 0;
+        for (int q = 0; q < 4; ++q) {
+            d.mon[q] = v[q];
+            d.mon[4 + q] = first ? v[q] : d.mon[4 + q] + (2.0 / 1001.0) * (v[q] - d.mon[4 + q]);
+        }
+    }
     // the next step's slots: the particles and holes of this step and the entered ones; after a counting sort
     // the survivors alone, in the other buffer
     const int kept = __ldcg(d.counts + 2);
@@ -2526,6 +2567,26 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         CK(dalloc(ctx, &d.wall_face, nwall));
         k_wall_index<<<nblk(F, 128), 128, 0, ctx.stream>>>(d, F, widx);
         {
+            // the stagnation point of the monitors: the two wall faces whose fluid-cell normals face the
+            // freestream (+x) most, ties to the lower index, if the best is within 60 degrees of it
+            std::vector<int> wf(std::max(nwall, 1));
+            std::vector<double> fnx(F);
+            CK(cudaMemcpyAsync(wf.data(), d.wall_face, sizeof(int) * nwall, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaMemcpyAsync(fnx.data(), d.fnx, sizeof(double) * F, cudaMemcpyDeviceToHost, ctx.stream));
+            CK(cudaStreamSynchronize(ctx.stream));
+            int a = -1, b = -1;
+            for (int iw = 0; iw < nwall; ++iw) {
+                const double nx = fnx[wf[iw]];
+                if (a < 0 || nx > fnx[wf[a]]) { b = a; a = iw; }
+                else if (b < 0 || nx > fnx[wf[b]]) b = iw;
+            }
+            K.stag0 = K.stag1 = -1;
+            if (a >= 0 && b >= 0 && fnx[wf[a]] > 0.5) {
+                K.stag0 = std::min(a, b);
+                K.stag1 = std::max(a, b);
+            }
+        }
+        {
             // far-field and fixed faces in face order: ghost particle sources, with the face's local index in
             // its fluid cell
             std::vector<int> fbc(F), fl(F), cfh(4 * (size_t)C), nfc(C);
@@ -2621,6 +2682,12 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         CK(dalloc(ctx, &d.flux, 4 * F));
         ctx.res_blocks = nblk((long long)C + nwall, kUpdateBlock);
         CK(dalloc(ctx, &d.res_part, 4 * ctx.res_blocks)); CK(dalloc(ctx, &d.res, 8));
+        CK(dalloc(ctx, &d.mon, 8));
+        {
+            const double nan8[8] = {NAN, NAN, NAN, NAN, NAN, NAN, NAN, NAN};
+            CK(cudaMemcpyAsync(d.mon, nan8, sizeof nan8, cudaMemcpyHostToDevice, ctx.stream));
+            CK(cudaStreamSynchronize(ctx.stream));
+        }
         CK(dalloc(ctx, &d.chi_ema, C));
         CK(dalloc(ctx, &d.surf_sum, 3 * std::max(nwall, 1))); CK(dalloc(ctx, &d.surf_last, 3 * std::max(nwall, 1)));
         CK(dalloc(ctx, &d.counts, 8)); CK(dalloc(ctx, &d.stats, 16)); CK(dalloc(ctx, &d.err, 1));
@@ -2784,6 +2851,14 @@ ugkwp_status ugkwp_surface(ugkwp_ctx* h, double* p, double* tau, double* q, int3
     const double dv = averaged && st_h[8] > 0 ? (double)st_h[8] : 1.0;
     for (int i = 0; i < n_wall; ++i) { p[i] = s[3 * i] / dv; tau[i] = s[3 * i + 1] / dv; q[i] = s[3 * i + 2] / dv; }
     return st;
+}
+
+ugkwp_status ugkwp_monitors(ugkwp_ctx* h, double* out)
+{
+    if (!h || !out) return UGKWP_EINVAL;
+    Ctx& ctx = h->c;
+    CK(cudaMemcpyAsync(out, ctx.d.mon, sizeof(double) * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    return check_device_error(ctx);
 }
 
 ugkwp_status ugkwp_reset_surface(ugkwp_ctx* h)
@@ -3163,7 +3238,7 @@ ugkwp_status ugkwp_save(ugkwp_ctx* h, const char* path)
     if (np < 0) return fail(ctx, UGKWP_ECUDA, "reading the particle count");
     CkptHeader hd{};
     memcpy(hd.magic, "UGKWPCK1", 8);
-    hd.version = 1; hd.C = C; hd.F = ctx.k.F; hd.nwall = nw; hd.prec = ctx.k.prec; hd.wave_only = ctx.k.wave_only;
+    hd.version = 2; hd.C = C; hd.F = ctx.k.F; hd.nwall = nw; hd.prec = ctx.k.prec; hd.wave_only = ctx.k.wave_only;
     long long step = 0;
     CK(cudaMemcpyAsync(&step, ctx.d.dstep, sizeof step, cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
@@ -3177,6 +3252,8 @@ ugkwp_status ugkwp_save(ugkwp_ctx* h, const char* path)
     CK(cudaMemcpyAsync(chi.data(), ctx.d.chi_ema, 8 * (size_t)C, cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaMemcpyAsync(ss.data(), ctx.d.surf_sum, 8 * ss.size(), cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaMemcpyAsync(st, ctx.d.stats, sizeof st, cudaMemcpyDeviceToHost, ctx.stream));
+    double mon[8];
+    CK(cudaMemcpyAsync(mon, ctx.d.mon, sizeof mon, cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
     std::vector<uint64_t> pid(np > 0 ? np : 1);
     std::vector<int32_t> cell(np > 0 ? np : 1);
@@ -3191,7 +3268,7 @@ ugkwp_status ugkwp_save(ugkwp_ctx* h, const char* path)
     bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(W.data(), 8, W.size(), f) == W.size() &&
               fwrite(wr.data(), 8, wr.size(), f) == wr.size() && fwrite(res.data(), 8, 8, f) == 8 &&
               fwrite(chi.data(), 8, chi.size(), f) == chi.size() && fwrite(ss.data(), 8, ss.size(), f) == ss.size() &&
-              fwrite(st, sizeof st, 1, f) == 1;
+              fwrite(st, sizeof st, 1, f) == 1 && fwrite(mon, sizeof mon, 1, f) == 1;
     if (ok && np > 0)
         ok = fwrite(pid.data(), 8, np, f) == (size_t)np && fwrite(cell.data(), 4, np, f) == (size_t)np &&
              fwrite(pv.data(), 8, 6 * np, f) == (size_t)(6 * np);
@@ -3207,7 +3284,7 @@ ugkwp_status ugkwp_load(ugkwp_ctx* h, const char* path)
     FILE* f = fopen(path, "rb");
     if (!f) return fail(ctx, UGKWP_EINVAL, "cannot open the checkpoint file");
     CkptHeader hd{};
-    bool ok = fread(&hd, sizeof hd, 1, f) == 1 && memcmp(hd.magic, "UGKWPCK1", 8) == 0 && hd.version == 1 &&
+    bool ok = fread(&hd, sizeof hd, 1, f) == 1 && memcmp(hd.magic, "UGKWPCK1", 8) == 0 && hd.version == 2 &&
               hd.C == C && hd.F == ctx.k.F && hd.nwall == nw && hd.prec == ctx.k.prec &&
               hd.fx[0] == ctx.k.fx0 && hd.fx[1] == ctx.k.fx1 && hd.fx[2] == ctx.k.fx4 && hd.np >= 0 &&
               hd.np <= ctx.capacity;
@@ -3216,12 +3293,14 @@ ugkwp_status ugkwp_load(ugkwp_ctx* h, const char* path)
     std::vector<double> W(4 * (size_t)C), res(8), chi(C), ss(3 * (size_t)std::max(nw, 1));
     std::vector<long long> wr(5 * (size_t)C);
     unsigned long long st[16];
+    double mon[8];
     std::vector<uint64_t> pid(np > 0 ? np : 1);
     std::vector<int32_t> cell(np > 0 ? np : 1);
     std::vector<double> pv(6 * (size_t)(np > 0 ? np : 1));
     ok = fread(W.data(), 8, W.size(), f) == W.size() && fread(wr.data(), 8, wr.size(), f) == wr.size() &&
          fread(res.data(), 8, 8, f) == 8 && fread(chi.data(), 8, chi.size(), f) == chi.size() &&
-         fread(ss.data(), 8, ss.size(), f) == ss.size() && fread(st, sizeof st, 1, f) == 1;
+         fread(ss.data(), 8, ss.size(), f) == ss.size() && fread(st, sizeof st, 1, f) == 1 &&
+         fread(mon, sizeof mon, 1, f) == 1;
     if (ok && np > 0)
         ok = fread(pid.data(), 8, np, f) == (size_t)np && fread(cell.data(), 4, np, f) == (size_t)np &&
              fread(pv.data(), 8, 6 * np, f) == (size_t)(6 * np);
@@ -3235,6 +3314,7 @@ ugkwp_status ugkwp_load(ugkwp_ctx* h, const char* path)
     CK(cudaMemcpyAsync(ctx.d.chi_ema, chi.data(), 8 * (size_t)C, cudaMemcpyHostToDevice, ctx.stream));
     CK(cudaMemcpyAsync(ctx.d.surf_sum, ss.data(), 8 * ss.size(), cudaMemcpyHostToDevice, ctx.stream));
     CK(cudaMemcpyAsync(ctx.d.stats, st, sizeof st, cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(ctx.d.mon, mon, sizeof mon, cudaMemcpyHostToDevice, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
     return UGKWP_OK;
 }

@@ -42,6 +42,7 @@ struct StepConsts {
     int chunk;                      // particles per dynamically claimed chunk of the transport kernel
     int n_inj;                      // ghost particle sources (far-field and fixed faces)
     int order;                      // 2: second-order reconstruction for the wave fluxes
+    int stag0, stag1;               // wall faces of the stagnation point (-1: none), for the monitors
     double mu_inf, omega, Pr, Tw, U_inf, m2RTw, sig_w;
     double wall_specular;           // Maxwell wall: specular fraction 1 - alpha (0: fully diffuse)
     double T_cap, U_cap, T_min;     // realizability bounds of a cell state
@@ -98,6 +99,8 @@ struct Dev {
     double *res_part, *res;            // residual: per-block partials; [8] = raw of this step (4 used)
     double* chi_ema;
     double *surf_sum, *surf_last;      // [3 nwall]
+    double* mon;                       // [8] monitored loads of the last step (C_d, C_H, stagnation C_p, C_Q) and
+                                       // their EMAs
     // particles: A holds the cell-sorted retained set between steps, B is the staging buffer
     ParticleSoA<float> pa32, pb32;
     ParticleSoA<double> pa64, pb64;

@@ -20,7 +20,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ELIMIT", 5: "ENONPH
 LTS, GTS = 0, 1
 
 # every entry point declared in include/ugkwp.h
-EXPORTS = ["ugkwp_create", "ugkwp_create_unstructured", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugkwp_surface", "ugkwp_reset_surface",
+EXPORTS = ["ugkwp_create", "ugkwp_create_unstructured", "ugkwp_destroy", "ugkwp_step", "ugkwp_residual", "ugkwp_surface", "ugkwp_reset_surface", "ugkwp_monitors",
            "ugkwp_set_field", "ugkwp_set_time_steps", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
            "ugkwp_set_state", "ugkwp_get_tallies", "ugkwp_get_cell_data", "ugkwp_get_flux", "ugkwp_get_geometry",
            "ugkwp_fixed_exponents", "ugkwp_save", "ugkwp_load", "ugkwp_batch_create", "ugkwp_batch_step",
@@ -238,6 +238,12 @@ class Solver:
 
     def reset_surface(self):
         self._check(load().ugkwp_reset_surface(self.ctx))
+
+    def monitors(self):
+        """[C_d, C_H, stagnation C_p, C_Q (NaN without a stagnation point), then their EMAs] of the last step"""
+        out = np.zeros(8)
+        self._check(load().ugkwp_monitors(self.ctx, _d(out)))
+        return out
 
     def stats(self):
         """[steps, particles, new, removed, left, crossings, wall hits, max iterations, cumulative

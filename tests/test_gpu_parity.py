@@ -272,6 +272,24 @@ def test_surface_quantities(cuda_lib):
             np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-12 * np.abs(b).max())
 
 
+@pytest.mark.parametrize("name", ["cylinder", "plate"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_monitors(cuda_lib, name, prec):
+    """The device's monitored wall loads (C_d, C_H, stagnation C_p, C_Q and their EMAs, ugkwp_monitors)
+    against the oracle's step by step: 1e-9 in the all-FP64 mode, 1e-4 in production precision (FP32 wave-flux
+    moments in the wall pressure of interior-facing sums); the plate has no stagnation point on either side."""
+    g, o = _pair(cuda_lib, CASES[name], prec)
+    assert np.isnan(g.monitors()).all()
+    for _ in range(5):
+        g.step(1)
+        o.step(1)
+        mg, mo = g.monitors(), o.monitors()
+        assert np.array_equal(np.isnan(mg), np.isnan(mo))
+        ok = ~np.isnan(mo)
+        np.testing.assert_allclose(mg[ok], mo[ok], rtol=1e-9 if prec == 1 else 1e-4)
+    assert (name == "cylinder") == bool(np.isfinite(mg[2]))
+
+
 def test_residual(cuda_lib):
     g, o = _pair(cuda_lib, CASES["plate"], 1)
     g.step(3)

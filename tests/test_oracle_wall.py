@@ -165,3 +165,35 @@ def test_wall_flux_matches_quadrature_of_its_definition(WL, WhL, ws):
     scale = np.abs(inc).max()
     np.testing.assert_allclose(F, Fq, rtol=0, atol=1e-11 * scale)
     assert abs(F[0]) <= 1e-13 * scale                            # no net mass through the wall
+
+
+def test_monitors_restate_the_wall_load_definitions():
+    """Monitored loads of the oracle (Sec. V A, V B) against their definitions restated here from the
+    per-face surface values and the wall geometry: C_d = sum_j s_j (p_j n_x - tau_j n_y) / (rho U^2 / 2),
+    C_H = sum_j s_j q_j / (rho U^3 / 2), stagnation C_p and C_Q from the mean of the two wall faces facing the
+    freestream most, and each EMA (alpha = 2/1001) from the first step; a flat plate has no stagnation point."""
+    from paper_2607_09552_b300 import steady
+    case = wl.case_cylinder(ni=12, nj=16, h1=2e-3, r_out=4.0, Kn=0.1, Ma=5.0, n_ref=20)
+    o = ob.Oracle(case, precision=1)
+    nx, ny, s = steady.wall_geometry(case)
+    U = wl.freestream_speed(case.Ma)
+    j = np.argsort(-nx, kind="stable")[:2]
+    assert nx[j[0]] > 0.9
+    ema = None
+    for k in range(6):
+        o.step(1)
+        p, tau, q = o.surface(averaged=False)
+        cd, ch = steady.loads(case, p, tau, q, (nx, ny, s))
+        cp = (0.5 * (p[j[0]] + p[j[1]]) - 0.5) / (0.5 * U * U)
+        cq = 0.5 * (q[j[0]] + q[j[1]]) / (0.5 * U ** 3)
+        v = np.array([cd, ch, cp, cq])
+        ema = v.copy() if ema is None else ema + (2.0 / 1001.0) * (v - ema)
+        m = o.monitors()
+        np.testing.assert_allclose(m[:4], v, rtol=1e-12)
+        np.testing.assert_allclose(m[4:], ema, rtol=1e-12)
+    plate = wl.Case("plate_small", wl.plate_mesh(ni=27, nj=13, h1=2e-3, ratio=1.25), Kn=0.05, Ma=5.0, Tw=2.0,
+                    cfl=0.8, n_ref=29)
+    o = ob.Oracle(plate, precision=1)
+    o.step(2)
+    m = o.monitors()
+    assert np.isfinite(m[[0, 1, 4, 5]]).all() and np.isnan(m[[2, 3, 6, 7]]).all()
