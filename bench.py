@@ -429,12 +429,6 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def stagnation_pair(case):
-    """Wall-face indices adjacent to theta = pi (the stagnation point of the +x freestream on the O-mesh)."""
-    nj = case.mesh.info["nj"] if hasattr(case.mesh, "cells") else case.mesh.nj
-    return nj // 2 - 1, nj // 2
-
-
 def run_convergence(args):
     """Steps and wall-clock to convergence, LTS vs GTS, on the chosen workload (--case)."""
     import torch
@@ -447,8 +441,9 @@ def convergence_summary(args, stream):
     """The convergence comparison of the bench line: the 120 x 160 cylinder at Kn 0.1, Ma 5 (LTS against GTS)."""
     out = converge_case(wl.case_cylinder_kn01(), args, stream, verbose=False)
     out["note"] = ("residual: raw / freestream scale (ugkwp_residual); steady: EMA (alpha 2/1001) of drag and "
-                   "heat load within max(1%, 3 sigma) of the final-window mean; wall clock includes a surface "
-                   "read-back every step (both modes); warm start: bench.py --mode warmstart")
+                   "heat load (device monitors, ugkwp_monitors) within max(1%, 3 sigma) of the final-window mean; "
+                   "wall clock includes a monitor read-back every step (both modes); warm start: bench.py --mode "
+                   "warmstart")
     return out
 
 
@@ -460,7 +455,6 @@ def converge_case(case, args, stream, verbose=True):
     from paper_2607_09552_b300 import steady, ugkwp
     out = {"mode": "convergence", "workload": config_dict(case, 0, "n/a")["workload"],
            "reconstruction_order": args.order, "results": {}}
-    geom = steady.wall_geometry(case)
     for ts in ("LTS", "GTS"):
         gts = ts == "GTS"
         r = {}
@@ -481,18 +475,16 @@ def converge_case(case, args, stream, verbose=True):
         cap = (32 if gts else 8) * case.n_ref * case.mesh.ncells
         s = ugkwp.Solver(case, gts=gts, precision=0, stream=stream.cuda_stream, use_graph=True, capacity=cap,
                          order=args.order)
-        j0, j1 = stagnation_pair(case)
         hcd, hch, hp, hq, hres, hnp, ht = [], [], [], [], [], [], []
         t0 = time.perf_counter()
         try:
             for k in range(n):
                 s.step(1)
-                p, tau, q = s.surface(averaged=False)
-                cd, ch = steady.loads(case, p, tau, q, geom)
-                hcd.append(cd)
-                hch.append(ch)
-                hp.append(0.5 * (p[j0] + p[j1]))
-                hq.append(0.5 * (q[j0] + q[j1]))
+                mon = s.monitors()   # the device's monitored loads (C_d, C_H, stagnation C_p, C_Q)
+                hcd.append(mon[0])
+                hch.append(mon[1])
+                hp.append(mon[2])
+                hq.append(mon[3])
                 ht.append(time.perf_counter() - t0)
                 if k % 100 == 0:
                     hres.append(float(np.max(s.residual()[:4])))
@@ -506,14 +498,13 @@ def converge_case(case, args, stream, verbose=True):
         kd, _ = steady.steady_step(hcd)
         kh, _ = steady.steady_step(hch)
         k_st = max(kd, kh)
-        U = wl.freestream_speed(case.Ma)
         tail = slice(int(0.8 * n), n)
         r["stochastic"] = {"steps_run": n, "steps_to_steady": k_st if k_st < n else None,
                            "wall_s_to_steady": ht[k_st - 1] if 0 < k_st < n else None, "wall_s_run": ht[-1],
                            "ms_per_step": 1e3 * ht[-1] / n, "steady_drag_step": kd, "steady_heat_step": kh,
                            "Cd": float(np.mean(hcd[tail])), "CH": float(np.mean(hch[tail])),
-                           "stagnation_Cp": float((np.mean(hp[tail]) - 0.5) / (0.5 * U * U)),
-                           "stagnation_CQ": float(np.mean(hq[tail]) / (0.5 * U ** 3)),
+                           "stagnation_Cp": float(np.mean(hp[tail])),
+                           "stagnation_CQ": float(np.mean(hq[tail])),
                            "residual_plateau": float(np.median(hres[len(hres) // 2:])),
                            "particles_mean": float(np.mean(hnp[len(hnp) // 2:])), "particles_max": int(np.max(hnp)),
                            }
@@ -602,7 +593,7 @@ def _eval_wave(e, c, ref, fam, nets, args, st):
                            "state_rel_diff": float(np.max(np.abs(W_warm - W_cold)) / np.max(np.abs(W_cold)))}
 
 
-def _eval_stoch(c, warm, net, fam, geom, n, navg, st):
+def _eval_stoch(c, warm, net, fam, n, navg, st):
     """Stochastic LTS run of one held-out case (production precision) from the freestream or the network:
     steps and seconds to steady (drag and heat-load EMA), final-window loads, surfaces averaged over the
     last navg steps."""
@@ -617,10 +608,9 @@ def _eval_stoch(c, warm, net, fam, geom, n, navg, st):
         s.step(1)
         if k == n - navg:
             s.reset_surface()
-        p, tau, q = s.surface(averaged=False)
-        cd, ch = steady.loads(c, p, tau, q, geom)
-        hcd.append(cd)
-        hch.append(ch)
+        mon = s.monitors()
+        hcd.append(mon[0])
+        hch.append(mon[1])
         ht.append(time.perf_counter() - t0)
     kd, _ = steady.steady_step(hcd)
     kh, _ = steady.steady_step(hch)
@@ -766,14 +756,13 @@ def run_warmstart(args):
     n, navg = args.eval_stoch_steps, 1000
     for e, c in zip(out["eval"], cases):
         fam = ws.family(c)
-        geom = steady.wall_geometry(c)
         res = {}
         for start in ("cold", "warm"):
             if start == "warm" and fam not in nets:
                 res[start] = {"note": "no network for this family"}
                 continue
             try:
-                res[start] = _eval_stoch(c, start == "warm", nets.get(fam), fam, geom, n, navg, st)
+                res[start] = _eval_stoch(c, start == "warm", nets.get(fam), fam, n, navg, st)
             except ugkwp.UgkwpError as err:
                 res[start] = {"error": str(err)}
         if "surface" in res["cold"] and "surface" in res["warm"]:
