@@ -199,6 +199,9 @@ class Oracle:
                                          C.c_int32(int(averaged))))
         return p, t, q
 
+    def reset_surface(self):
+        self._check(lib().oracle_reset_surface(self.ctx))
+
     def monitors(self):
         """[C_d, C_H, stagnation C_p, C_Q, then their EMAs] of the last step"""
         out = np.zeros(8)

@@ -75,6 +75,7 @@ int  oracle_surface(oracle_ctx* cx, double* p, double* tau, double* q, int32_t n
 /* monitored wall loads of the last step: C_d, C_H, stagnation C_p, C_Q (NaN without a stagnation point), then
  * their EMAs (alpha = 2/1001) from the first step on */
 int  oracle_monitors(oracle_ctx* cx, double* out);
+int  oracle_reset_surface(oracle_ctx* cx);
 /* building block: n new-particle normal triples z[3n] of particle ids pid0 + k drawn for a Shakhov cell with
  * acceptance-rejection weights (ax, ay, M) (see shakhov_weights); returns the fallback count */
 int64_t oracle_ar_sample(int32_t precision, uint64_t seed, uint32_t case_id, int64_t step, uint64_t pid0, int32_t n,

@@ -1374,6 +1374,14 @@ static void find_stagnation(or_ctx* cx)
     }
 }
 
+/* restart the surface averages (and the monitors' EMAs) at the next step */
+int oracle_reset_surface(oracle_ctx* cx)
+{
+    memset(cx->surf_sum, 0, 3 * (size_t)cx->nwall * sizeof(double));
+    cx->nsurf = 0;
+    return cx->err;
+}
+
 int oracle_monitors(oracle_ctx* cx, double* out)
 {
     for (int k = 0; k < 8; ++k) out[k] = cx->mon[k];
