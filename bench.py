@@ -526,8 +526,10 @@ def converge_case(case, args, stream, verbose=True):
 
 
 def run_batch(args):
-    """The seeded 16-case sweep (cylinders and plates, Kn, Ma, T_w drawn from seed 0) advanced by one graph
-    launch per step, against the same cases stepped one after another (each with its own graph)."""
+    """The seeded 16-case sweep (cylinders and plates, Kn, Ma, T_w drawn from seed 0) advanced together: one
+    graph of per-case streams per step, the batched persistent kernel (4 and 6 CTAs per SM), and the same cases
+    stepped one after another (each with its own graph); same states throughout (the cases continue from one
+    timing to the next)."""
     import torch
     from paper_2607_09552_b300 import ugkwp
     torch.cuda.set_device(0)
@@ -539,31 +541,42 @@ def run_batch(args):
     for s in solvers:
         s.step(args.burn if args.burn >= 0 else 3000)
     torch.cuda.synchronize()
-    b = ugkwp.Batch(solvers, stream=stream.cuda_stream)
-    b.step(args.warmup)
-    torch.cuda.synchronize()
-    p0 = sum(int(s.stats()[8]) for s in solvers)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1)
-    p1 = sum(int(s.stats()[8]) for s in solvers)
-    e0.record(stream)
-    for _ in range(args.steps):
-        for s in solvers:
-            s.step(1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_s = e0.elapsed_time(e1)
-    p2 = sum(int(s.stats()[8]) for s in solvers)
+
+    def timed(run):
+        """(particle-steps/s, ms per step) of args.steps steps after args.warmup untimed ones"""
+        run(args.warmup)
+        torch.cuda.synchronize()
+        p0 = sum(int(s.stats()[8]) for s in solvers)
+        e0.record(stream)
+        run(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        p1 = sum(int(s.stats()[8]) for s in solvers)
+        return (p1 - p0) / (ms * 1e-3), ms / args.steps
+
+    def sequential(n):
+        for _ in range(n):
+            for s in solvers:
+                s.step(1)
+
+    out = {"mode": "batch", "steps": args.steps, "warmup": args.warmup}
+    b = ugkwp.Batch(solvers, stream=stream.cuda_stream)
+    out["graph_particle_steps_per_s"], out["graph_ms_per_step"] = timed(b.step)
     b.close()
-    out = {"mode": "batch", "cases": [{"name": c.name, "Kn": c.Kn, "Ma": c.Ma, "Tw": c.Tw, "n_ref": c.n_ref,
-                                       "particles": s.num_particles()} for c, s in zip(cases, solvers)],
-           "steps": args.steps, "batched_particle_steps_per_s": (p1 - p0) / (ms_b * 1e-3),
-           "sequential_particle_steps_per_s": (p2 - p1) / (ms_s * 1e-3),
-           "batched_ms_per_step": ms_b / args.steps, "sequential_ms_per_step": ms_s / args.steps}
+    for cps in (4, 6):
+        b = ugkwp.Batch(solvers, stream=stream.cuda_stream, persistent=True, ctas_per_sm=cps)
+        plan = b.plan()
+        out[f"persistent{cps}_particle_steps_per_s"], out[f"persistent{cps}_ms_per_step"] = timed(b.step)
+        st = b.status()
+        b.close()
+        if st[0] != 0:
+            raise RuntimeError(f"persistent batch stopped: {st}")
+        out[f"persistent{cps}_plan"] = {"items_per_step": plan[1], "ctas": plan[2], "ctas_per_sm": plan[3]}
+    out["sequential_particle_steps_per_s"], out["sequential_ms_per_step"] = timed(sequential)
+    out["cases"] = [{"name": c.name, "cells": c.mesh.ncells, "Kn": c.Kn, "Ma": c.Ma, "Tw": c.Tw, "n_ref": c.n_ref,
+                     "particles": s.num_particles()} for c, s in zip(cases, solvers)]
     print(json.dumps(out))
 
 

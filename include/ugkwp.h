@@ -235,7 +235,33 @@ ugkwp_status ugkwp_fixed_exponents(ugkwp_ctx* ctx, int32_t* out);
  * is launched on. Cases may differ in mesh, gas, Kn, Ma, T_w, mode and particle count. */
 typedef struct ugkwp_batch ugkwp_batch;
 ugkwp_status ugkwp_batch_create(ugkwp_ctx* const* ctxs, int32_t n, void* stream, ugkwp_batch** out);
+/* Batched persistent kernel: one launch (captured in a CUDA graph) advances every listed context by one step.
+ * The step's work is a device list of items (case, stage, blocks of that stage) in the step order of the
+ * method (Sec. III C, Sec. IV B: decomposition, new particles, transport, sort, wave fluxes, update); the
+ * launch's CTAs (ctas_per_sm x SMs; ctas_per_sm 4 or 6, 0 for 4) take items from a counter, and an item waits
+ * (bounded, see ugkwp_batch_set_wait_limit) until its case's previous stage has finished, so that the stage
+ * boundaries of one case overlap with other cases' work. Each item runs the same per-block arithmetic as the
+ * step's own kernels: the results equal those of ugkwp_step on each context (particles as sets). Scope: every
+ * context in production precision, first-order reconstruction, the warp-staged transport with 128-particle
+ * tiles (ugkwp_set_launch transport 2, chunk 128), no per-stage profiling, all on one device, at most 64;
+ * EINVAL otherwise (ugkwp_batch_create serves any context). The stage sizes that walk particles are planned from
+ * each case's particle count at creation (any count gives the same results, only the balance changes).
+ * Device memory (plan and control words) comes from the first context's allocator. */
+ugkwp_status ugkwp_batch_create_persistent(ugkwp_ctx* const* ctxs, int32_t n, void* stream, int32_t ctas_per_sm,
+                                           ugkwp_batch** out);
 ugkwp_status ugkwp_batch_step(ugkwp_batch* batch, int32_t n_steps);
+/* Persistent batches: the time limit of an item's wait for its case's previous stage (default 2 s); when it
+ * runs out the CTA stops the batch: no CTA takes further items, every case's error word gets the limit bit
+ * (their calls then report ELIMIT), the launch returns, and ugkwp_batch_status reports ELIMIT. The cases are
+ * then in the middle of a step: restore them (ugkwp_load) before stepping again. `stall` != 0 is a test hook:
+ * the step's last item then waits for one item more than its case's previous stage has, so that the limit is
+ * sure to run out. Synchronises the batch's stream. */
+ugkwp_status ugkwp_batch_set_wait_limit(ugkwp_batch* batch, int64_t limit_ns, int32_t stall);
+/* Synchronises the batch's stream; ELIMIT (and in *where, nullable, case * 20 + stage of the wait that ran
+ * out) once a persistent batch has stopped, else OK. */
+ugkwp_status ugkwp_batch_status(ugkwp_batch* batch, int32_t* where);
+/* out[4]: 1 for a persistent batch, its items per step, CTAs per launch, CTAs per SM (0 for a graph batch). */
+ugkwp_status ugkwp_batch_plan(const ugkwp_batch* batch, int32_t* out);
 void ugkwp_batch_destroy(ugkwp_batch* batch);
 
 /* Checkpoint: the whole state (step counter, W, retained tally, particles, last residual,

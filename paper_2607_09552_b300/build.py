@@ -1,7 +1,8 @@
 """Compile libugkwp.so (the CUDA kernels and the C ABI of include/ugkwp.h) in-tree for sm_103a.
 
-ugkwp_core.cu is compiled with -fmad=false so that the particle path and the cell decomposition are
-sequences of individually rounded IEEE operations; the wave-flux unit keeps fused multiply-adds.
+ugkwp_core.cu (which includes the wave fluxes, ugkwp_flux.cuh) is compiled with -fmad=false so that every
+floating-point operation of the step is an individually rounded IEEE operation (fused multiply-adds only where
+the code asks for them), the same in the step's kernels and in the batched persistent kernel.
 """
 from __future__ import annotations
 
@@ -15,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libugkwp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
-UNITS = {"ugkwp_core.cu": ["-fmad=false"], "ugkwp_flux.cu": [], "ugkwp_mlp.cu": []}
-DEPS = ["ugkwp_internal.h", "ugkwp_detmath.cuh"]
+UNITS = {"ugkwp_core.cu": ["-fmad=false"], "ugkwp_mlp.cu": []}
+DEPS = ["ugkwp_internal.h", "ugkwp_detmath.cuh", "ugkwp_flux.cuh"]
 
 
 def _nvcc() -> str:

@@ -17,6 +17,7 @@
 //                      the last block closes the step
 #include <cuda_runtime.h>
 #include <math_constants.h>
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -25,6 +26,7 @@
 #include <vector>
 #include "ugkwp_internal.h"
 #include "ugkwp_detmath.cuh"
+#include "ugkwp_flux.cuh"
 
 namespace ugk {
 namespace {
@@ -568,9 +570,9 @@ __device__ void lts_coeffs_f32(float dt, float x, float e, float* out)
     out[6] = -dt * x * kappa;
 }
 
-__global__ void k_decompose(const StepConsts K, Dev d)
+__device__ __forceinline__ void decompose_body(const VB vb, const StepConsts& K, const Dev& d)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = vb.b * blockDim.x + threadIdx.x;
     const unsigned am = __ballot_sync(0xffffffffu, c < K.C);   // the warp's lanes with a cell
     if (c >= K.C) return;
     const double* W = d.W + 4 * c;
@@ -675,6 +677,7 @@ __global__ void k_decompose(const StepConsts K, Dev d)
     d.cnt[c] = 0;
     d.cur[c] = 0;
 }
+__global__ void k_decompose(const StepConsts K, Dev d) { decompose_body(UGKWP_VB_LAUNCH, K, d); }
 
 // ------------------------------------------------- a8: second-order reconstruction (order 2)
 // Limited gradients (d/dx, d/dy) of the four components of W (v = 0..3) and W^h (v = 4..7) of one cell (FP64).
@@ -758,9 +761,9 @@ __global__ void k_gradients(const StepConsts K, Dev d)
 }
 
 // per-step zeroing of face crossings, wall tallies and counters; the sort flag of this step
-__global__ void k_begin_step(const StepConsts K, Dev d)
+__device__ __forceinline__ void begin_body(const VB vb, const StepConsts& K, const Dev& d)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int t = vb.b * blockDim.x + threadIdx.x, nt = vb.n * blockDim.x;
     for (int q = t; q < 2 * K.F; q += nt) d.cross[q] = 0u;
     for (int q = t; q < 3 * K.nwall; q += nt) d.wallt[q] = 0;
     if (d.frec)
@@ -780,12 +783,15 @@ __global__ void k_begin_step(const StepConsts K, Dev d)
         *d.nscell = 0;
         if (d.nxq) *d.nxq = 0;
         *d.done = 0u;
-        // a counting sort every sort_every-th step, and whenever holes (removed particles, updated in place)
-        // fill more than a quarter of the slots
-        const long long slots = d.counts[0], alive = (long long)d.stats[1];
-        d.flags[0] = (int)(*d.dstep % K.sort_every == (long long)(K.sort_every - 1) || 4 * (slots - alive) > slots);
+        // a counting sort every sort_every-th step, whenever holes (removed particles, updated in place) fill
+        // more than a quarter of the slots, and whenever the slots fill more than seven eighths of the capacity
+        // (so that holes do not use up room the new particles need)
+        const long long slots = d.counts[0], alive = (long long)d.stats[1], cap = d.counts[3];
+        d.flags[0] = (int)(*d.dstep % K.sort_every == (long long)(K.sort_every - 1) || 4 * (slots - alive) > slots ||
+                           8 * slots > 7 * cap);
     }
 }
+__global__ void k_begin_step(const StepConsts K, Dev d) { begin_body(UGKWP_VB_LAUNCH, K, d); }
 
 // per-cell particle-precision views
 template <typename T> struct PCell;
@@ -859,8 +865,8 @@ __device__ __forceinline__ void fix5(T m, T u, T v, T w, T s0, T s1, T s4, int* 
 // Pr != 1: raw velocity moments m (1, u, v, uu, uv, vv, q, uq, vq), q = |u|^2, of the particles retained at
 // the start of the step, per cell, as fixed-point integers (the Shakhov heat flux of the sampling)
 template <typename T>
-__global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const Dev d, ParticleSoA<T> PA,
-                                                    ParticleSoA<T> PB)
+__device__ __forceinline__ void heat_body(const VB vb, const StepConsts& K, const Dev& d, const ParticleSoA<T>& PA,
+                                          const ParticleSoA<T>& PB)
 {
     const ParticleSoA<T> A = *d.bufsel ? PB : PA;
     const int n = d.counts[0];
@@ -868,7 +874,7 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
                      T(pow2(K.fx_s2)), T(pow2(K.fx_s2)), T(pow2(K.fx_s2)), T(pow2(K.fx_s3)),
                      T(pow2(K.fx_s3))};
     unsigned long long* h = reinterpret_cast<unsigned long long*>(d.whq);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = vb.b * blockDim.x + threadIdx.x; i < n; i += vb.n * blockDim.x) {
         const int ci = A.cell[i];
         if (ci < 0) continue;   // a hole
         const T m = A.m[i], u = A.u[i], v = A.v[i], w = A.w[i];
@@ -879,6 +885,11 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 #pragma unroll
         for (int k = 0; k < 9; ++k) atomicAdd(h + 9 * c + k, (unsigned long long)fixp(val[k], sc[k], d.err));
     }
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB)
+{
+    heat_body<T>(UGKWP_VB_LAUNCH, K, d, PA, PB);
 }
 
 // ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
@@ -1034,15 +1045,21 @@ __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, c
 // the cells that sample new particles this step (listed by the decomposition, in any order: each cell's
 // particles, ids and slots depend on the cell alone), one per warp, grid-stride over the list
 template <typename T>
-__global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
-                                                ParticleSoA<T> PB, PCell<T> pc, const long long* dstep)
+__device__ __forceinline__ void sample_body(const VB vb, const StepConsts& K, const Dev& d, const ParticleSoA<T>& PA,
+                                            const ParticleSoA<T>& PB, const PCell<T>& pc, const long long* dstep)
 {
     const ParticleSoA<T> A = *d.bufsel ? PB : PA;   // the buffer holding this step's particles
     if (d.counts[1] == 0) return;
     const int nact = *d.nscell;
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nact; w += nwarps)
+    const int nwarps = vb.n * (blockDim.x >> 5);
+    for (int w = (vb.b * blockDim.x + threadIdx.x) >> 5; w < nact; w += nwarps)
         sample_cell(K, d, A, pc, dstep, d.scells[w]);
+}
+template <typename T>
+__global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
+                                                ParticleSoA<T> PB, PCell<T> pc, const long long* dstep)
+{
+    sample_body<T>(UGKWP_VB_LAUNCH, K, d, PA, PB, pc, dstep);
 }
 
 // A cell's outward normals and plane offsets (the stay and exit tests), copied into registers by 16-byte loads
@@ -1387,6 +1404,10 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t coun
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
@@ -1467,11 +1488,12 @@ __device__ __forceinline__ void wtile_issue(const ParticleSoA<float>& A, int t, 
     bulk_load(S.pid[b], A.pid + base, b8, bar);
 }
 
-template <int WT, int MINB>
-__global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const StepConsts K, const Dev d,
-                                                                       ParticleSoA<float> PA, ParticleSoA<float> PB,
-                                                                       const CellFaces<float>* __restrict__ cf,
-                                                                       PCell<float> pc, const long long* dstep)
+// false when a tile's copies did not arrive in time (ERR_LIMIT set; the copies in flight were given their own
+// bounded wait)
+template <int WT>
+__device__ __forceinline__ bool stay_body(const StepConsts& K, const Dev& d, const ParticleSoA<float>& PA,
+                                          const ParticleSoA<float>& PB, const CellFaces<float>* __restrict__ cf,
+                                          const long long* dstep)
 {
     extern __shared__ __align__(128) unsigned char warp_smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1606,16 +1628,31 @@ __global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const Ste
             for (int q = 0; q < 2; ++q)
                 if (pending & (1u << q)) (void)mbar_wait_bounded(&S.bar[q], parity[q]);
         }
-        return;
+        return false;
     }
     for (int o = 16; o > 0; o >>= 1) n_kept += __shfl_xor_sync(0xffffffffu, n_kept, o);
-    if (lane == 0 && n_kept) atomicAdd(d.counts + 2, (int)n_kept);
+    if (lane == 0) {
+        if (n_kept) atomicAdd(d.counts + 2, (int)n_kept);
+        // every copy has completed: the barriers are retired, so that the shared memory can hold new ones
+        mbar_inval(&S.bar[0]);
+        mbar_inval(&S.bar[1]);
+    }
+    __syncwarp();
+    return true;
+}
+template <int WT, int MINB>
+__global__ void __launch_bounds__(kWWarps * 32, MINB) k_particles_warp(const StepConsts K, const Dev d,
+                                                                       ParticleSoA<float> PA, ParticleSoA<float> PB,
+                                                                       const CellFaces<float>* __restrict__ cf,
+                                                                       const long long* dstep)
+{
+    (void)stay_body<WT>(K, d, PA, PB, cf, dstep);
 }
 
 // the flight pass: the queued particles of the stay pass, one per thread (warp-uniform grid-stride loop)
-__global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const Dev d, ParticleSoA<float> PA,
-                                                       ParticleSoA<float> PB, const CellFaces<float>* __restrict__ cf,
-                                                       const long long* dstep)
+__device__ __forceinline__ void fly_body(const VB vb, const StepConsts& K, const Dev& d, const ParticleSoA<float>& PA,
+                                         const ParticleSoA<float>& PB, const CellFaces<float>* __restrict__ cf,
+                                         const long long* dstep)
 {
     const ParticleSoA<float> A = *d.bufsel ? PB : PA;
     const bool sort_step = d.flags[0] != 0;
@@ -1626,8 +1663,8 @@ __global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const
     const int lane = threadIdx.x & 31;
     unsigned long long n_cross = 0, n_hits = 0, n_removed = 0, n_left = 0, n_kept = 0;
     int max_it = 0;
-    const int stride = gridDim.x * blockDim.x;
-    for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < nq; e0 += stride) {
+    const int stride = vb.n * blockDim.x;
+    for (int e0 = vb.b * blockDim.x + (threadIdx.x & ~31); e0 < nq; e0 += stride) {
         const int e = e0 + lane;
         int c = -1;
         bool kept = false;
@@ -1673,6 +1710,12 @@ __global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const
         if (n_kept) atomicAdd(d.counts + 2, (int)n_kept);
     }
 }
+__global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const Dev d, ParticleSoA<float> PA,
+                                                       ParticleSoA<float> PB, const CellFaces<float>* __restrict__ cf,
+                                                       const long long* dstep)
+{
+    fly_body(UGKWP_VB_LAUNCH, K, d, PA, PB, cf, dstep);
+}
 
 // ------------------------------------------------ ghost particle sources (far-field and fixed faces)
 // The virtual ghost cell behind a far-field / fixed face holds the ghost state with the fluid cell's time step
@@ -1683,9 +1726,9 @@ __global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const
 // m_ref = rho_g Omega_L / N_ref; the ghost's wave free-transport weight is then dbar_d - e^{-x}.
 
 // per source, FP64 (one thread each): ghost state, sample count, mass, ghost velocity, sqrt(RT), slab depth
-__global__ void k_inject_params(const StepConsts K, Dev d)
+__device__ __forceinline__ void injp_body(const VB vb, const StepConsts& K, const Dev& d)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = vb.b * blockDim.x + threadIdx.x;
     if (j >= K.n_inj) return;
     const int f = d.inj_face[j], L = d.fL[f];
     const double* Wg;
@@ -1713,13 +1756,15 @@ __global__ void k_inject_params(const StepConsts K, Dev d)
     P[0] = n > 0 ? M / (double)n : 0.0;
     P[1] = U; P[2] = V; P[3] = sig; P[4] = D;
 }
+__global__ void k_inject_params(const StepConsts K, Dev d) { injp_body(UGKWP_VB_LAUNCH, K, d); }
 
 // one warp per source: sample, enter, fly, tally W^{p,+}, write the survivors like the transport kernel
 template <typename T>
-__global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB,
-                                                const CellFaces<T>* __restrict__ cf, const long long* dstep)
+__device__ __forceinline__ void inject_body(const VB vb, const StepConsts& K, const Dev& d, const ParticleSoA<T>& PA,
+                                            const ParticleSoA<T>& PB, const CellFaces<T>* __restrict__ cf,
+                                            const long long* dstep)
 {
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int j = (vb.b * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= K.n_inj) return;
     const int N = d.inj_n[j];
@@ -1784,26 +1829,25 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
                 }
             }
         }
-        // survivors (slots beyond the capacity are an error)
+        // survivors: slots reserved past n; those at or beyond the capacity are not written (an error), and
+        // the bookkeeping of k_update and k_scatter counts the reserved slots only up to the capacity, so that
+        // no later kernel touches a slot past it
         const unsigned km = __ballot_sync(0xffffffffu, kept);
         if (!km) continue;
         int slot0 = 0;
-        if (lane == 0) {
-            slot0 = atomicAdd(d.counts + 7, __popc(km));
-            atomicAdd(d.counts + 2, __popc(km));
-        }
+        if (lane == 0) slot0 = atomicAdd(d.counts + 7, __popc(km));
         slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-        if (kept) {
-            const int jj = n + slot0 + __popc(km & lt_mask);
-            if (jj >= cap) {
-                atomicOr(d.err, ERR_CAPACITY);
-            } else {
-                B.x[jj] = x; B.y[jj] = y; B.u[jj] = u; B.v[jj] = v; B.w[jj] = w; B.m[jj] = m;
-                B.cell[jj] = c;
-                B.pid[jj] = pid;
-                if (sort_step) atomicAdd(d.cnt + c, 1);
-            }
+        const int jj = n + slot0 + __popc(km & lt_mask);
+        const bool stored = kept && jj < cap;
+        if (kept && !stored) atomicOr(d.err, ERR_CAPACITY);
+        if (stored) {
+            B.x[jj] = x; B.y[jj] = y; B.u[jj] = u; B.v[jj] = v; B.w[jj] = w; B.m[jj] = m;
+            B.cell[jj] = c;
+            B.pid[jj] = pid;
+            if (sort_step) atomicAdd(d.cnt + c, 1);
         }
+        const unsigned sm = __ballot_sync(0xffffffffu, stored);
+        if (lane == 0 && sm) atomicAdd(d.counts + 2, __popc(sm));
     }
     for (int o = 16; o > 0; o >>= 1) {
         n_cross += __shfl_xor_sync(0xffffffffu, n_cross, o);
@@ -1820,22 +1864,29 @@ __global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d,
         if (n_in) { atomicAdd(d.stats + 13, n_in); atomicAdd(d.counts + 6, (int)n_in); }
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(128) k_inject(const StepConsts K, const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB,
+                                                const CellFaces<T>* __restrict__ cf, const long long* dstep)
+{
+    inject_body<T>(UGKWP_VB_LAUNCH, K, d, PA, PB, cf, dstep);
+}
 
 // --------------------------------------------------------------------- a7: counting sort
 // sort steps only: counting sort of the survivors by cell (holes dropped), from the buffer that holds the
 // step's particles into the other one, which becomes the current one at the end of the step
 template <typename T>
-__global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB)
+__device__ __forceinline__ void scatter_body(const VB vb, const Dev& d, const ParticleSoA<T>& PA, const ParticleSoA<T>& PB)
 {
     if (!d.flags[0]) return;
     const int sel = *d.bufsel;
     const ParticleSoA<T> A = sel ? PB : PA, B = sel ? PA : PB;
-    const int n = d.counts[4] + d.counts[7];   // the step's slots, then those of particles that entered from ghosts
+    // the step's slots, then those of particles that entered from ghosts (reserved slots up to the capacity)
+    const int n = min(d.counts[4] + d.counts[7], d.counts[3]);
     const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
+    const int stride = vb.n * blockDim.x;
     // warp-uniform loop; the slots of a run of equal cells in the warp (the particles stay grouped by cell
     // between sorts) are reserved with one atomic by the run's first lane
-    for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+    for (int i0 = vb.b * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
         const int i = i0 + lane;
         const int c = i < n ? A.cell[i] : -1;
         const int prev = __shfl_up_sync(0xffffffffu, c, 1);
@@ -1861,15 +1912,20 @@ __global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA,
         B.m[slot] = A.m[i]; B.cell[slot] = c; B.pid[slot] = A.pid[i];
     }
 }
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(const Dev d, ParticleSoA<T> PA, ParticleSoA<T> PB)
+{
+    scatter_body<T>(UGKWP_VB_LAUNCH, d, PA, PB);
+}
 
 // ---------------------------------------------------------------- a10: update (Eq. 53)
 // Threads [0, C): conservative update of one cell, residual term, particle-mass-ratio EMA, vacuum floor.
 // Threads [C, C + n_wall): wall pressure, shear stress and heat flux of one wall face (a11, Sec. V A).
 // The last block to finish reduces the residual partials in block order and closes the step.
 constexpr int kUpdateBlock = 128;
-__global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev d, long long* dstep)
+__device__ __forceinline__ void update_body(const VB vb, const StepConsts& K, const Dev& d, long long* dstep)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = vb.b * blockDim.x + threadIdx.x;
     double r2[4] = {0, 0, 0, 0};
     if (t < K.C) {
         const int c = t;
@@ -1943,9 +1999,9 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        for (int q = 0; q < 4; ++q) d.res_part[4 * blockIdx.x + q] = sm[q][0];
+        for (int q = 0; q < 4; ++q) d.res_part[4 * vb.b + q] = sm[q][0];
         __threadfence();
-        last = atomicAdd(d.done, 1u) == gridDim.x - 1;
+        last = atomicAdd(d.done, 1u) == (unsigned)vb.n - 1u;
     }
     __syncthreads();
     if (!last) return;
@@ -1953,7 +2009,7 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
     // takes blocks t, t + 256, ..., then the same tree as above), counters, next step
     __threadfence();
     double s[4] = {0, 0, 0, 0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kUpdateBlock)
+    for (int b = threadIdx.x; b < vb.n; b += kUpdateBlock)
         for (int q = 0; q < 4; ++q) s[q] += __ldcg(d.res_part + 4 * b + q);
     for (int q = 0; q < 4; ++q) sm[q][threadIdx.x] = s[q];
     __syncthreads();
@@ -2006,20 +2062,28 @@ __global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev
     }
     // the next step's slots: the particles and holes of this step and the entered ones; after a counting sort
     // the survivors alone, in the other buffer
+    // (reserved slots of entered particles count up to the capacity: those past it were not stored)
     const int kept = __ldcg(d.counts + 2);
     if (d.flags[0]) {
         d.counts[0] = kept;
         *d.bufsel = 1 - *d.bufsel;
     } else {
-        d.counts[0] = __ldcg(d.counts + 4) + __ldcg(d.counts + 7);
+        d.counts[0] = min(__ldcg(d.counts + 4) + __ldcg(d.counts + 7), d.counts[3]);
     }
+    // particle-steps of this step: the particles alive at its start, the new ones and those that entered from
+    // ghost sources (holes are not particles)
+    const unsigned long long alive0 = d.stats[1];
     *dstep += 1;
     d.stats[0] = (unsigned long long)*dstep;
     d.stats[1] = (unsigned long long)kept;
     d.stats[2] = (unsigned long long)d.counts[1];
     d.stats[8] += 1;  // surface samples
-    d.stats[9] += (unsigned long long)(d.counts[4] + d.counts[6]);
+    d.stats[9] += alive0 + (unsigned long long)(d.counts[1] + d.counts[6]);
     d.stats[10] += (unsigned long long)d.counts[1];
+}
+__global__ void __launch_bounds__(kUpdateBlock) k_update(const StepConsts K, Dev d, long long* dstep)
+{
+    update_body(UGKWP_VB_LAUNCH, K, d, dstep);
 }
 
 // ------------------------------------------------------------------ state transfer helpers
@@ -2181,7 +2245,7 @@ template <int WT, int MINB> void launch_warp_variant(Ctx& ctx, cudaStream_t s, c
     const StepConsts& K = ctx.k;
     Dev& d = ctx.d;
     k_particles_warp<WT, MINB><<<MINB * ctx.sms, kWWarps * 32, kWWarps * sizeof(WarpSmem<WT>), s>>>(
-        K, d, d.pa32, d.pb32, d.cf32, pc, d.dstep);
+        K, d, d.pa32, d.pb32, d.cf32, d.dstep);
     k_particles_fly<<<5 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
 }
 void launch_particles_warp(Ctx& ctx, cudaStream_t s, const PCell<float>& pc)
@@ -2280,6 +2344,295 @@ static void enqueue_step(Ctx& ctx, cudaStream_t s, cudaStream_t s2, bool prof)
     if (prof)
         for (int q = 0; q < 2 * kStages; ++q) ctx.prof_events.push_back(ev[q]);
 }
+
+namespace {
+// ------------------------------------------------------------- batched persistent step kernel
+// One launch advances every case of a batch by one step. The work of a step is a list of items (case, stage,
+// blocks b0..b1 of that stage), built on the host in stage-major order: every case's first stage, then every
+// case's second stage, and so on, the stages in the order of the step (the algorithm of Sec. III C: decompose,
+// sample, transport, then the update; the wave fluxes between decomposition and update). The CTAs of the
+// launch take items from a global counter and run each as the blocks of the standalone kernel it stands for
+// (same block size, same per-block arithmetic), one block after another. An item waits until every item of
+// its case's previous stage has finished; items of other cases do not wait for it, so one case's stage
+// boundaries overlap with other cases' work instead of idling the GPU as a grid-wide barrier would.
+// No deadlock: an item waits only for items that come earlier in the list, and an item is taken only by a
+// running CTA, so the earliest unfinished item can always make progress. Each wait is bounded (a time limit);
+// on expiry the CTA raises the batch's abort flag, every CTA stops taking items, and the step reports ELIMIT.
+// Scope: production precision, first-order reconstruction and the warp-staged transport with 128-particle
+// tiles (the batch falls back to per-case streams for any other case).
+enum MkStage : int {
+    MS_BEGIN, MS_HEAT, MS_DECOMP, MS_NSCAN_B, MS_NSCAN_T, MS_NSCAN_A, MS_FPREP, MS_FMIX, MS_F32, MS_F64, MS_INJP,
+    MS_INJ, MS_SAMPLE, MS_STAY, MS_FLY, MS_CSCAN_B, MS_CSCAN_T, MS_CSCAN_A, MS_SCATTER, MS_UPDATE, MS_COUNT
+};
+constexpr int kMkThreads = 128;
+constexpr int kMkScanTile = 1024;   // elements per scan block (that of exclusive_scan)
+constexpr int kMkMaxCases = 64;
+
+struct MkCase {
+    StepConsts K;
+    Dev d;
+    int nv[MS_COUNT];                 // blocks of each stage (0: the stage does not run for this case)
+};
+// control words of a batch (device): take counter, CTAs finished, abort flag, where a wait ran out, limit
+struct MkCtl {
+    int next, exited, abort, where;
+    unsigned long long limit_ns;
+    int stall;                        // test hook: the first wait of the step also waits for a flag nothing sets
+    int pad;
+};
+
+// exclusive scan of a kMkScanTile-element tile of `in` by 128 threads (eight consecutive elements each); the
+// tile's total to tmp[b]. Same outputs as k_scan_blocks (integer sums).
+__device__ __forceinline__ void mk_scan_blocks(const VB vb, const int* in, int* out, int* tmp, int n, const int* active)
+{
+    if (active && !*active) return;
+    constexpr int per = kMkScanTile / kMkThreads;
+    const int i0 = vb.b * kMkScanTile + threadIdx.x * per;
+    int v[per], s = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        v[k] = i0 + k < n ? in[i0 + k] : 0;
+        s += v[k];
+    }
+    int tot;
+    int e = block_excl_scan(s, &tot);
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        if (i0 + k < n) out[i0 + k] = e;
+        e += v[k];
+    }
+    if (threadIdx.x == 0) tmp[vb.b] = tot;
+}
+// k_scan_tops by 128 threads (nb <= 1024 block totals, eight per thread)
+__device__ __forceinline__ void mk_scan_tops(int* tmp, int nb, int* out, int n, int* total, int* cap, int* err,
+                                             const int* active)
+{
+    if (active && !*active) return;
+    constexpr int per = kMkScanTile / kMkThreads;
+    const int i0 = threadIdx.x * per;
+    int v[per], s = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        v[k] = i0 + k < nb ? tmp[i0 + k] : 0;
+        s += v[k];
+    }
+    int tot;
+    int e = block_excl_scan(s, &tot);
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+        if (i0 + k < nb) tmp[i0 + k] = e;
+        e += v[k];
+    }
+    if (threadIdx.x == 0) {
+        out[n] = tot;
+        if (cap) {
+            if ((long long)cap[0] + tot > (long long)cap[3]) {
+                atomicOr(err, ERR_CAPACITY);
+                tot = 0;
+            }
+            cap[4] = cap[0] + tot;
+        }
+        if (total) *total = tot;
+    }
+}
+__device__ __forceinline__ void mk_scan_add(const VB vb, int* out, const int* tmp, int n, const int* active)
+{
+    if (active && !*active) return;
+    const int add = tmp[vb.b];
+    for (int k = threadIdx.x; k < kMkScanTile; k += kMkThreads) {
+        const int i = vb.b * kMkScanTile + k;
+        if (i < n) out[i] += add;
+    }
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// one block b of stage st of a case: the body of the standalone kernel that the stage stands for
+__device__ __forceinline__ bool mk_run_block(const MkCase& mc, int st, int b)
+{
+    const StepConsts& K = mc.K;
+    const Dev& d = mc.d;
+    const VB vb{b, mc.nv[st]};
+    const int nbC = (K.C + kMkScanTile - 1) / kMkScanTile;
+    switch (st) {
+    case MS_BEGIN: begin_body(vb, K, d); break;
+    case MS_HEAT: heat_body<float>(vb, K, d, d.pa32, d.pb32); break;
+    case MS_DECOMP: decompose_body(vb, K, d); break;
+    case MS_NSCAN_B: mk_scan_blocks(vb, d.nhp, d.nhp_off, d.scan_tmp, K.C, nullptr); break;
+    case MS_NSCAN_T: mk_scan_tops(d.scan_tmp, nbC, d.nhp_off, K.C, d.counts + 1, d.counts, d.err, nullptr); break;
+    case MS_NSCAN_A: mk_scan_add(vb, d.nhp_off, d.scan_tmp, K.C, nullptr); break;
+    case MS_FPREP: wf::flux_prep_body(vb, K, d); break;
+    case MS_FMIX: wf::fluxmix_body(vb, K, d); break;
+    case MS_F32: wf::flux32_body(vb, K, d); break;
+    case MS_F64:
+        // the queued faces one per warp (lane 0), as the standalone launch of 32-thread blocks
+        wf::flux64_body(K, d, (int)(threadIdx.x & 31), 4 * b + (int)(threadIdx.x >> 5), 4 * vb.n, 1, 0);
+        break;
+    case MS_INJP: injp_body(vb, K, d); break;
+    case MS_INJ: inject_body<float>(vb, K, d, d.pa32, d.pb32, d.cf32, d.dstep); break;
+    case MS_SAMPLE: {
+        const PCell<float> pc{d.tau32, d.dt32, d.mnew32, d.samp32, d.hq32, d.emx32};
+        sample_body<float>(vb, K, d, d.pa32, d.pb32, pc, d.dstep);
+        break;
+    }
+    case MS_STAY: return stay_body<128>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
+    case MS_FLY: fly_body(vb, K, d, d.pa32, d.pb32, d.cf32, d.dstep); break;
+    case MS_CSCAN_B: mk_scan_blocks(vb, d.cnt, d.off, d.scan_tmp, K.C, d.flags); break;
+    case MS_CSCAN_T: mk_scan_tops(d.scan_tmp, nbC, d.off, K.C, d.counts + 2, nullptr, nullptr, d.flags); break;
+    case MS_CSCAN_A: mk_scan_add(vb, d.off, d.scan_tmp, K.C, d.flags); break;
+    case MS_SCATTER: scatter_body<float>(vb, d, d.pa32, d.pb32); break;
+    case MS_UPDATE: update_body(vb, K, d, d.dstep); break;
+    default: break;
+    }
+    return true;
+}
+
+// items: (case, stage, first block, end block); dep[case * MS_COUNT + stage] = (stage waited for, items of it),
+// stage -1 for none; done[case * MS_COUNT + stage] counts the finished items of the step
+template <int MB>
+__global__ void __launch_bounds__(kMkThreads, MB) k_persist_step(const MkCase* __restrict__ cases,
+                                                                 const int4* __restrict__ items, int n_items,
+                                                                 const int2* __restrict__ dep, int* done, int n_done,
+                                                                 MkCtl* ctl, int n_cases)
+{
+    __shared__ int s_item, s_last;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int i = ld_relaxed_gpu(&ctl->abort) ? n_items : atomicAdd(&ctl->next, 1);
+            if (i < n_items) {
+                const int4 it = items[i];
+                const int2 dp = dep[it.x * MS_COUNT + it.y];
+                // (test hook: with ctl->stall the step's last item waits for one item more than its stage has)
+                const int need = dp.y + ((ctl->stall && i == n_items - 1) ? 1 : 0);
+                if (dp.x >= 0) {
+                    const int* w = done + it.x * MS_COUNT + dp.x;
+                    unsigned long long t0 = 0;
+                    for (unsigned k = 0;; ++k) {
+                        if (ld_acquire_gpu(w) >= need) break;
+                        if (ld_relaxed_gpu(&ctl->abort)) { i = n_items; break; }
+                        if ((k & 15u) == 15u) {
+                            const unsigned long long t = global_ns();
+                            if (t0 == 0) {
+                                t0 = t;
+                            } else if (t - t0 > ctl->limit_ns) {
+                                // the wait ran out: stop the batch, record where, flag every case
+                                if (atomicCAS(&ctl->abort, 0, 1) == 0) atomicExch(&ctl->where, it.x * MS_COUNT + it.y);
+                                for (int q = 0; q < n_cases; ++q) atomicOr(cases[q].d.err, ERR_LIMIT);
+                                i = n_items;
+                                break;
+                            }
+                        }
+                        __nanosleep(64);
+                    }
+                    __threadfence();
+                }
+            }
+            s_item = i;
+        }
+        __syncthreads();
+        const int i = s_item;
+        if (i >= n_items) break;
+        const int4 it = items[i];
+        const MkCase& mc = cases[it.x];
+        bool ok = true;
+        for (int b = it.z; b < it.w && ok; ++b) ok = mk_run_block(mc, it.y, b);
+        // a stay-pass tile whose copies did not arrive in time: that warp's shared memory may still be written
+        // by them, so this CTA takes no further item and the batch stops
+        const bool bad = __syncthreads_or(!ok) != 0;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + it.x * MS_COUNT + it.y, 1);
+            if (bad) {
+                if (atomicCAS(&ctl->abort, 0, 1) == 0) atomicExch(&ctl->where, it.x * MS_COUNT + it.y);
+                for (int q = 0; q < n_cases; ++q) atomicOr(cases[q].d.err, ERR_LIMIT);
+            }
+        }
+        if (bad) break;
+    }
+    // the last CTA to finish resets the step's counters for the next launch (the abort flag stays)
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&ctl->exited, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int k = threadIdx.x; k < n_done; k += kMkThreads) done[k] = 0;
+        if (threadIdx.x == 0) {
+            ctl->next = 0;
+            ctl->exited = 0;
+        }
+    }
+}
+
+// blocks of each stage per work item (light per-block work is grouped so that taking an item costs little
+// against running it)
+constexpr int kMkPer[MS_COUNT] = {4, 1, 2, 2, 1, 4, 4, 1, 1, 1, 4, 2, 1, 1, 1, 2, 1, 4, 1, 2};
+
+// blocks of each stage of one case (np: its particle count when the batch is made, which sizes the stages
+// whose blocks walk the particles in grid-stride loops or claim tiles; any count gives the same results)
+void mk_plan_case(const Ctx& ctx, int G, long long np, MkCase& mc)
+{
+    const StepConsts& K = ctx.k;
+    const bool parts = !K.wave_only;
+    const bool inj = K.n_inj > 0 && parts;
+    auto up = [](long long a, long long b) { return (int)((a + b - 1) / b); };
+    auto clampG = [&](long long x) { return (int)std::max(1LL, std::min<long long>(G, x)); };
+    for (int s = 0; s < MS_COUNT; ++s) mc.nv[s] = 0;
+    long long zero = std::max<long long>(2LL * K.F, 3LL * K.nwall);
+    if (ctx.d.frec) zero = std::max<long long>(zero, 4LL * K.F);
+    if (K.shakhov) zero = std::max<long long>(zero, 9LL * K.C);
+    const int nbC = up(K.C, kMkScanTile);
+    mc.nv[MS_BEGIN] = clampG(up(zero, 8 * kMkThreads));
+    if (K.shakhov) mc.nv[MS_HEAT] = clampG(up(np, 32768));
+    mc.nv[MS_DECOMP] = up(K.C, kMkThreads);
+    mc.nv[MS_NSCAN_B] = nbC;
+    mc.nv[MS_NSCAN_T] = 1;
+    mc.nv[MS_NSCAN_A] = nbC;
+    mc.nv[MS_FPREP] = up(K.C, kMkThreads);
+    if (K.n_mix) mc.nv[MS_FMIX] = up(K.n_mix, kMkThreads);
+    mc.nv[MS_F32] = up(K.F, kMkThreads);
+    mc.nv[MS_F64] = 4;
+    if (inj) {
+        mc.nv[MS_INJP] = up(K.n_inj, kMkThreads);
+        mc.nv[MS_INJ] = up(32LL * K.n_inj, kMkThreads);
+    }
+    if (parts) {
+        mc.nv[MS_SAMPLE] = clampG(up(K.C, 256));
+        mc.nv[MS_STAY] = clampG(up(np, 16384));
+        mc.nv[MS_FLY] = clampG(up(np, 65536));
+        mc.nv[MS_SCATTER] = clampG(up(np, 16384));
+    }
+    mc.nv[MS_CSCAN_B] = nbC;
+    mc.nv[MS_CSCAN_T] = 1;
+    mc.nv[MS_CSCAN_A] = nbC;
+    mc.nv[MS_UPDATE] = ctx.res_blocks;
+}
+
+template <int MB> cudaError_t mk_occupancy(int* blocks)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_persist_step<MB>, kMkThreads,
+                                                         kWWarps * sizeof(WarpSmem<128>));
+}
+template <int MB>
+void mk_launch(int grid, cudaStream_t s, const MkCase* cases, const int4* items, int n_items, const int2* dep,
+               int* done, int n_done, MkCtl* ctl, int n_cases)
+{
+    k_persist_step<MB><<<grid, kMkThreads, kWWarps * sizeof(WarpSmem<128>), s>>>(cases, items, n_items, dep, done,
+                                                                               n_done, ctl, n_cases);
+}
+}  // namespace
 
 }  // namespace ugk
 
@@ -3144,6 +3497,15 @@ struct ugkwp_batch {
     std::vector<cudaEvent_t> joins;
     cudaGraphExec_t graph = nullptr;
     std::string msg;
+    // the persistent kernel (ugkwp_batch_create_persistent): device plan and control words, allocated through
+    // the first case's allocator
+    bool persistent = false;
+    MkCase* mk_cases = nullptr;
+    int4* mk_items = nullptr;
+    int2* mk_dep = nullptr;
+    int* mk_done = nullptr;
+    MkCtl* mk_ctl = nullptr;
+    int n_items = 0, grid = 0, ctas_per_sm = 0;
 };
 
 ugkwp_status ugkwp_batch_create(ugkwp_ctx* const* ctxs, int32_t n, void* stream, ugkwp_batch** out)
@@ -3217,7 +3579,155 @@ void ugkwp_batch_destroy(ugkwp_batch* b)
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (!b->cases.empty()) {
+        Ctx& c0 = b->cases[0]->c;
+        raw_free(c0, b->mk_cases);
+        raw_free(c0, b->mk_items);
+        raw_free(c0, b->mk_dep);
+        raw_free(c0, b->mk_done);
+        raw_free(c0, b->mk_ctl);
+    }
     delete b;
+}
+
+ugkwp_status ugkwp_batch_create_persistent(ugkwp_ctx* const* ctxs, int32_t n, void* stream, int32_t ctas_per_sm,
+                                           ugkwp_batch** out)
+{
+    if (!ctxs || n <= 0 || n > kMkMaxCases || !out || (ctas_per_sm != 0 && ctas_per_sm != 4 && ctas_per_sm != 6))
+        return UGKWP_EINVAL;
+    *out = nullptr;
+    int dev = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!ctxs[i]) return UGKWP_EINVAL;
+        for (int32_t j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return UGKWP_EINVAL;
+        const Ctx& c = ctxs[i]->c;
+        // the kernel's scope: production precision, first order, the warp-staged transport with 128-particle
+        // tiles, no per-stage profiling
+        if (c.k.prec != 0 || c.k.order != 1 || c.transport != kTransportStaged || c.k.chunk != 128 || c.profiling)
+            return UGKWP_EINVAL;
+        if (i == 0) dev = c.device;
+        else if (c.device != dev) return UGKWP_EINVAL;
+    }
+    ugkwp_batch* b = new (std::nothrow) ugkwp_batch;
+    if (!b) return UGKWP_ENOMEM;
+    b->root = static_cast<cudaStream_t>(stream);
+    b->persistent = true;
+    for (int32_t i = 0; i < n; ++i) b->cases.push_back(ctxs[i]);
+    auto bail = [&](ugkwp_status st) { ugkwp_batch_destroy(b); return st; };
+    Ctx& c0 = ctxs[0]->c;
+    const int mb = ctas_per_sm ? ctas_per_sm : 4;
+    int occ = 0;
+    if ((mb == 4 ? mk_occupancy<4>(&occ) : mk_occupancy<6>(&occ)) != cudaSuccess || occ < 1) return bail(UGKWP_ECUDA);
+    b->ctas_per_sm = std::min(occ, mb);
+    b->grid = b->ctas_per_sm * c0.sms;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return bail(UGKWP_ECUDA);
+    // per case: its descriptor and stage sizes (particle count from the device)
+    std::vector<MkCase> mc(n);
+    for (int32_t i = 0; i < n; ++i) {
+        Ctx& c = ctxs[i]->c;
+        unsigned long long alive = 0;
+        if (cudaMemcpyAsync(&alive, c.d.stats + 1, sizeof alive, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+            cudaStreamSynchronize(c.stream) != cudaSuccess)
+            return bail(UGKWP_ECUDA);
+        const long long np = std::max<long long>((long long)alive, (long long)c.k.n_ref * c.k.C);
+        mc[i].K = c.k;
+        mc[i].d = c.d;
+        mk_plan_case(c, b->grid, np, mc[i]);
+    }
+    // the items in stage-major order, and each (case, stage)'s wait: the case's previous stage that runs
+    std::vector<int4> items;
+    std::vector<int2> dep((size_t)n * MS_COUNT, make_int2(-1, 0));
+    std::vector<int> nitems((size_t)n * MS_COUNT, 0);
+    for (int st = 0; st < MS_COUNT; ++st)
+        for (int32_t i = 0; i < n; ++i) {
+            const int nv = mc[i].nv[st];
+            for (int b0 = 0; b0 < nv; b0 += kMkPer[st]) {
+                items.push_back(make_int4(i, st, b0, std::min(nv, b0 + kMkPer[st])));
+                nitems[(size_t)i * MS_COUNT + st]++;
+            }
+        }
+    for (int32_t i = 0; i < n; ++i) {
+        int prev = -1;
+        for (int st = 0; st < MS_COUNT; ++st) {
+            if (!mc[i].nv[st]) continue;
+            if (prev >= 0) dep[(size_t)i * MS_COUNT + st] = make_int2(prev, nitems[(size_t)i * MS_COUNT + prev]);
+            prev = st;
+        }
+    }
+    b->n_items = (int)items.size();
+    const MkCtl ctl0{0, 0, 0, -1, 2000000000ull, 0, 0};
+    if (raw_alloc(c0, (void**)&b->mk_cases, sizeof(MkCase) * n) != cudaSuccess ||
+        raw_alloc(c0, (void**)&b->mk_items, sizeof(int4) * items.size()) != cudaSuccess ||
+        raw_alloc(c0, (void**)&b->mk_dep, sizeof(int2) * dep.size()) != cudaSuccess ||
+        raw_alloc(c0, (void**)&b->mk_done, sizeof(int) * dep.size()) != cudaSuccess ||
+        raw_alloc(c0, (void**)&b->mk_ctl, sizeof(MkCtl)) != cudaSuccess)
+        return bail(UGKWP_ENOMEM);
+    if (cudaMemcpyAsync(b->mk_cases, mc.data(), sizeof(MkCase) * n, cudaMemcpyHostToDevice, c0.stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->mk_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, c0.stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->mk_dep, dep.data(), sizeof(int2) * dep.size(), cudaMemcpyHostToDevice, c0.stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(b->mk_done, 0, sizeof(int) * dep.size(), c0.stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->mk_ctl, &ctl0, sizeof ctl0, cudaMemcpyHostToDevice, c0.stream) != cudaSuccess ||
+        cudaStreamSynchronize(c0.stream) != cudaSuccess)
+        return bail(UGKWP_ECUDA);
+    // the launch, captured once
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return bail(UGKWP_ECUDA);
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        if (mb == 4)
+            mk_launch<4>(b->grid, cap, b->mk_cases, b->mk_items, b->n_items, b->mk_dep, b->mk_done, (int)dep.size(),
+                         b->mk_ctl, n);
+        else
+            mk_launch<6>(b->grid, cap, b->mk_cases, b->mk_items, b->n_items, b->mk_dep, b->mk_done, (int)dep.size(),
+                         b->mk_ctl, n);
+        ok = cudaStreamEndCapture(cap, &g) == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (!ok) return bail(UGKWP_ECUDA);
+    *out = b;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_batch_set_wait_limit(ugkwp_batch* b, int64_t limit_ns, int32_t stall)
+{
+    if (!b || !b->persistent || limit_ns <= 0) return UGKWP_EINVAL;
+    const unsigned long long lim = (unsigned long long)limit_ns;
+    const int st = stall ? 1 : 0;
+    cudaStream_t s = b->root;
+    if (cudaMemcpyAsync(&b->mk_ctl->limit_ns, &lim, sizeof lim, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(&b->mk_ctl->stall, &st, sizeof st, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return UGKWP_ECUDA;
+    return UGKWP_OK;
+}
+
+ugkwp_status ugkwp_batch_status(ugkwp_batch* b, int32_t* where)
+{
+    if (!b) return UGKWP_EINVAL;
+    if (where) *where = -1;
+    if (cudaStreamSynchronize(b->root) != cudaSuccess) return UGKWP_ECUDA;
+    if (!b->persistent) return UGKWP_OK;
+    MkCtl h;
+    if (cudaMemcpy(&h, b->mk_ctl, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return UGKWP_ECUDA;
+    if (!h.abort) return UGKWP_OK;
+    if (where) *where = h.where;
+    return UGKWP_ELIMIT;
+}
+
+ugkwp_status ugkwp_batch_plan(const ugkwp_batch* b, int32_t* out)
+{
+    if (!b || !out) return UGKWP_EINVAL;
+    out[0] = b->persistent ? 1 : 0;
+    out[1] = b->n_items;
+    out[2] = b->grid;
+    out[3] = b->ctas_per_sm;
+    return UGKWP_OK;
 }
 
 namespace {

@@ -20,13 +20,16 @@
 //  The moment algebra is a dense 4x4 closed form per face, so it runs on the FP32/FP64 pipes. In production
 //  mode the velocity moments are FP32; the faces of wall cells (flag face_f64) weight them with their FP64
 //  time integrals and sum in FP64.
+// Included by the core unit (compiled with -fmad=false), so that the step's kernels and the batched persistent
+// kernel evaluate the same individually rounded operations.
+#pragma once
 #include <cuda_runtime.h>
 #include <cmath>
 #include "ugkwp_internal.h"
 #include "ugkwp_detmath.cuh"
 
 namespace ugk {
-namespace {
+namespace wf {
 
 template <typename R> struct Prim { R rho, U, V, lam, th; };   // th = R T = 1 / (2 lambda)
 template <typename R> struct Mom { R up[9], um[9], v[7], xi2, xi4, g0; };   // g0: density at u = 0
@@ -534,9 +537,9 @@ __device__ __forceinline__ void store_flux(const Dev& c, int f, const double out
 // production mode, once per cell before the faces: FP32 copies of W and W^h and the primitive perturbation that
 // carries W^h's remainder (FP64, rounded once), so that the FP32 faces read 16-byte FP32 loads and run no FP64
 // work (B300's FP64 pipe is narrow); the decomposition wrote the FP32 coefficients
-__global__ void __launch_bounds__(256) k_flux_prep(const StepConsts K, const Dev c)
+__device__ __forceinline__ void flux_prep_body(const VB vb, const StepConsts& K, const Dev& c)
 {
-    const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cc = vb.b * blockDim.x + threadIdx.x;
     if (cc >= K.C) return;
     const double* W = c.W + 4 * cc;
     const double* Wh = c.Wh + 4 * cc;
@@ -551,35 +554,40 @@ __global__ void __launch_bounds__(256) k_flux_prep(const StepConsts K, const Dev
 // integrals (the normalised coefficients, computed in FP64 in the decomposition) and sum the weighted
 // moments in FP64. A face whose FP32 evaluation under- or overflows (near-vacuum neighbours with extreme
 // moments) is queued for the FP64 kernel.
-__global__ void __launch_bounds__(128) k_wave_flux32(const StepConsts K, const Dev c)
+__device__ __forceinline__ void flux32_body(const VB vb, const StepConsts& K, const Dev& c)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = vb.b * blockDim.x + threadIdx.x;
     if (f >= K.F || c.face_f64[f]) return;
     double out[4];
     if (one_face<float, float>(K, c, f, out)) store_flux(c, f, out);
     else c.retry[atomicAdd(c.nretry, 1)] = f;
 }
+__global__ void __launch_bounds__(256) k_flux_prep(const StepConsts K, const Dev c) { flux_prep_body(UGKWP_VB_LAUNCH, K, c); }
+__global__ void __launch_bounds__(128) k_wave_flux32(const StepConsts K, const Dev c) { flux32_body(UGKWP_VB_LAUNCH, K, c); }
 
 // the faces of wall cells in production mode: FP32 moments weighted with their FP64 time integrals
-__global__ void __launch_bounds__(128) k_wave_flux_mixed(const StepConsts K, const Dev c)
+__device__ __forceinline__ void fluxmix_body(const VB vb, const StepConsts& K, const Dev& c)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = vb.b * blockDim.x + threadIdx.x;
     if (j >= K.n_mix) return;
     const int f = c.mixlist[j];
     double out[4];
     if (one_face<float, double>(K, c, f, out)) store_flux(c, f, out);
     else c.retry[atomicAdd(c.nretry, 1)] = f;
 }
+__global__ void __launch_bounds__(128) k_wave_flux_mixed(const StepConsts K, const Dev c) { fluxmix_body(UGKWP_VB_LAUNCH, K, c); }
 
 // FP64 faces: the static list (every face in the FP64 mode, none in production mode), then the faces
 // queued by the FP32 kernel. The FP64 pipe's cost grows with the active lanes of a warp, so in production
 // mode the (rare) queued faces are spread one per warp (lane 0); in the all-FP64 mode every lane takes a
 // face.
-__global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c, int lanes, int all_faces)
+// (the body: lane tx of the 32-thread block vb of nvb)
+__device__ __forceinline__ void flux64_body(const StepConsts& K, const Dev& c, int tx, int vb, int nvb, int lanes,
+                                            int all_faces)
 {
-    if ((int)threadIdx.x >= lanes) return;
+    if (tx >= lanes) return;
     const int n = all_faces ? K.F : K.n_f64 + *c.nretry;
-    for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < n; j += gridDim.x * lanes) {
+    for (int j = tx * nvb + vb; j < n; j += nvb * lanes) {
         const int f = all_faces ? j : j < K.n_f64 ? c.f64list[j] : c.retry[j - K.n_f64];
         double out[4];
         one_face<double, double>(K, c, f, out);
@@ -590,29 +598,33 @@ __global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const De
         store_flux(c, f, out);
     }
 }
+__global__ void __launch_bounds__(32) k_wave_flux64(const StepConsts K, const Dev c, int lanes, int all_faces)
+{
+    flux64_body(K, c, (int)threadIdx.x, (int)blockIdx.x, (int)gridDim.x, lanes, all_faces);
+}
 
-}  // namespace
+}  // namespace wf
 
-void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s)
+inline void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s)
 {
     // second-order reconstruction: every face in FP64 (reconstructed states near the edge of the realizable
     // set and the slope terms lose too many digits in FP32 moments)
     if (k.order == 2) {
-        k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 1);
+        wf::k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 1);
         return;
     }
     if (k.prec == 0) {
-        k_flux_prep<<<(k.C + 255) / 256, 256, 0, s>>>(k, d);
-        if (k.n_mix) k_wave_flux_mixed<<<(k.n_mix + 127) / 128, 128, 0, s>>>(k, d);
-        k_wave_flux32<<<(k.F + 127) / 128, 128, 0, s>>>(k, d);
+        wf::k_flux_prep<<<(k.C + 255) / 256, 256, 0, s>>>(k, d);
+        if (k.n_mix) wf::k_wave_flux_mixed<<<(k.n_mix + 127) / 128, 128, 0, s>>>(k, d);
+        wf::k_wave_flux32<<<(k.F + 127) / 128, 128, 0, s>>>(k, d);
     }
-    if (k.prec == 0) k_wave_flux64<<<4 * sms, 32, 0, s>>>(k, d, 1, 0);
-    else k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 0);
+    if (k.prec == 0) wf::k_wave_flux64<<<4 * sms, 32, 0, s>>>(k, d, 1, 0);
+    else wf::k_wave_flux64<<<(k.F + 31) / 32, 32, 0, s>>>(k, d, 32, 0);
 }
 
-cudaError_t flux_set_tables(const double* tab, cudaStream_t s)
+inline cudaError_t flux_set_tables(const double* tab, cudaStream_t s)
 {
-    return cudaMemcpyToSymbolAsync(c_series_f, tab, sizeof(double) * 5 * kSeriesF, 0, cudaMemcpyHostToDevice, s);
+    return cudaMemcpyToSymbolAsync(wf::c_series_f, tab, sizeof(double) * 5 * wf::kSeriesF, 0, cudaMemcpyHostToDevice, s);
 }
 
 }  // namespace ugk

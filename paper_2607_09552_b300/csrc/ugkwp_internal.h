@@ -123,6 +123,15 @@ struct Dev {
     int* err;
 };
 
+// A block of a step kernel: its index and the number of blocks it is one of. A standalone launch passes
+// (blockIdx.x, gridDim.x); the batched persistent kernel runs a case's stage as the same blocks, one after
+// another on whichever CTA takes the work item, so that every per-block result (the residual partials) is that
+// of the standalone launch.
+struct VB {
+    int b, n;
+};
+#define UGKWP_VB_LAUNCH (::ugk::VB{(int)blockIdx.x, (int)gridDim.x})
+
 struct Ctx {
     StepConsts k{};
     Dev d{};
@@ -150,8 +159,8 @@ struct Ctx {
 constexpr int kStages = 6;   // decompose+scan, sample, particles, wave flux, sort, update+surface+close
 
 // launchers implemented in ugkwp_flux.cu
-void launch_wave_flux(const StepConsts& k, const Dev& d, int sms, cudaStream_t s);
-cudaError_t flux_set_tables(const double* tab, cudaStream_t s);   // [4][20]: phi1, psi2, psi3, beta weights
+// the wave-flux unit (ugkwp_flux.cuh, included by the core unit): launch_wave_flux(k, d, sms, stream) and
+// flux_set_tables(tab, stream) with tab [5][20] the Taylor weights of phi1, psi2, psi3, beta, chi
 
 }  // namespace ugk
 

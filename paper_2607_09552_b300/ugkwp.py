@@ -24,6 +24,7 @@ EXPORTS = ["ugkwp_create", "ugkwp_create_unstructured", "ugkwp_destroy", "ugkwp_
            "ugkwp_set_field", "ugkwp_set_time_steps", "ugkwp_get_field", "ugkwp_stats", "ugkwp_num_particles", "ugkwp_get_particles",
            "ugkwp_set_state", "ugkwp_get_tallies", "ugkwp_get_cell_data", "ugkwp_get_flux", "ugkwp_get_geometry",
            "ugkwp_fixed_exponents", "ugkwp_save", "ugkwp_load", "ugkwp_batch_create", "ugkwp_batch_step",
+           "ugkwp_batch_create_persistent", "ugkwp_batch_set_wait_limit", "ugkwp_batch_status", "ugkwp_batch_plan",
            "ugkwp_batch_destroy", "ugkwp_set_profiling", "ugkwp_profile", "ugkwp_mlp_create", "ugkwp_mlp_destroy",
            "ugkwp_mlp_num_params", "ugkwp_mlp_get_params", "ugkwp_mlp_set_params", "ugkwp_mlp_forward",
            "ugkwp_mlp_grad", "ugkwp_mlp_adam", "ugkwp_mlp_features", "ugkwp_field_accumulate", "ugkwp_mlp_dataset",
@@ -361,21 +362,45 @@ class Solver:
 
 
 class Batch:
-    """Several Solver contexts advanced together by one graph launch per step (ugkwp_batch_*)."""
+    """Several Solver contexts advanced together by one graph launch per step (ugkwp_batch_*): per-case streams
+    of the step kernels, or (persistent=True) the batched persistent kernel with `ctas_per_sm` CTAs per SM."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, persistent: bool = False, ctas_per_sm: int = 0):
         L = load()
         self.solvers = list(solvers)
         arr = (C.c_void_p * len(self.solvers))(*[s.ctx.value for s in self.solvers])
         self.h = C.c_void_p()
-        st = L.ugkwp_batch_create(arr, C.c_int32(len(self.solvers)), C.c_void_p(stream), C.byref(self.h))
+        if persistent:
+            st = L.ugkwp_batch_create_persistent(arr, C.c_int32(len(self.solvers)), C.c_void_p(stream),
+                                                 C.c_int32(ctas_per_sm), C.byref(self.h))
+        else:
+            st = L.ugkwp_batch_create(arr, C.c_int32(len(self.solvers)), C.c_void_p(stream), C.byref(self.h))
         if st != 0:
-            raise UgkwpError(st, "ugkwp_batch_create")
+            raise UgkwpError(st, "ugkwp_batch_create_persistent" if persistent else "ugkwp_batch_create")
 
     def step(self, n: int = 1):
         st = load().ugkwp_batch_step(self.h, C.c_int32(n))
         if st != 0:
             raise UgkwpError(st, "ugkwp_batch_step")
+
+    def set_wait_limit(self, limit_ns: int, stall: bool = False):
+        st = load().ugkwp_batch_set_wait_limit(self.h, C.c_int64(limit_ns), C.c_int32(int(stall)))
+        if st != 0:
+            raise UgkwpError(st, "ugkwp_batch_set_wait_limit")
+
+    def status(self):
+        """(status, where): 0 or ELIMIT (4) once a persistent batch stopped; where = case * 20 + stage."""
+        w = C.c_int32(-1)
+        st = load().ugkwp_batch_status(self.h, C.byref(w))
+        return st, w.value
+
+    def plan(self):
+        """[persistent, items per step, CTAs per launch, CTAs per SM]"""
+        out = (C.c_int32 * 4)()
+        st = load().ugkwp_batch_plan(self.h, out)
+        if st != 0:
+            raise UgkwpError(st, "ugkwp_batch_plan")
+        return list(out)
 
     def close(self):
         if getattr(self, "h", None):

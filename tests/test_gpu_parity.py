@@ -318,6 +318,19 @@ def test_capacity_limit_reports_error(cuda_lib):
     assert e.value.status == 4
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_capacity_limit_with_ghost_sources_reports_error(cuda_lib, prec):
+    """Far-field ghost sources that enter more particles than the capacity holds: the slots past it are
+    neither written nor counted, so the following steps (several, in one graph launch each) stay within the
+    buffers, and the error is reported (ELIMIT, status 4)."""
+    case = CASES["cylinder"]
+    g = cuda_lib.Solver(case, precision=prec, capacity=300, use_graph=True)
+    g.step(6)
+    with pytest.raises(cuda_lib.UgkwpError) as e:
+        g.field()
+    assert e.value.status == 4
+
+
 def test_option_validation(cuda_lib):
     """Bad options are refused with EINVAL (status 1): a reconstruction order other than 1 or 2, a specular
     wall fraction outside [0, 1], a non-positive or non-finite replacement time step (which leaves the
@@ -392,13 +405,75 @@ def test_batched_graph_equals_individual_runs(cuda_lib):
     b.close()
 
 
+@pytest.mark.parametrize("ctas_per_sm", [4, 6])
+def test_persistent_batch_equals_individual_runs(cuda_lib, ctas_per_sm):
+    """The batched persistent kernel (one launch per step for all cases, work items taken from a device counter,
+    each waiting for its case's previous stage) gives each case exactly its own trajectory: cell states bit for
+    bit, particles as sets, tallies, counters, residual and monitors."""
+    names = ["cylinder", "plate", "shock1d", "box", "cylinder_dense"]
+    solo = [cuda_lib.Solver(CASES[n], precision=0) for n in names]
+    for s in solo:
+        s.step(7)
+    grouped = [cuda_lib.Solver(CASES[n], precision=0) for n in names]
+    grouped[0].step(1)     # uneven start: the cases need not be at the same step
+    b = cuda_lib.Batch(grouped[1:] + grouped[:1], persistent=True, ctas_per_sm=ctas_per_sm)
+    plan = b.plan()
+    assert plan[0] == 1 and plan[1] > 0 and plan[3] == ctas_per_sm and plan[2] % ctas_per_sm == 0
+    b.step(3)
+    b.step(3)
+    assert b.status() == (0, -1)
+    b.close()
+    for g in grouped[1:]:
+        g.step(1)          # the contexts keep stepping on their own after batched steps
+    for a, g in zip(solo, grouped):
+        assert int(a.stats()[0]) == int(g.stats()[0])
+        assert np.array_equal(a.field()[0], g.field()[0])
+        assert_particles_equal(a.particles(), g.particles())
+        assert np.array_equal(a.stats()[:8], g.stats()[:8])
+        ta, tg = a.tallies(), g.tallies()
+        for k in ("wm", "wpl", "wret", "cross", "wall"):
+            assert np.array_equal(ta[k], tg[k]), k
+        assert np.array_equal(a.residual(), g.residual())
+        assert np.array_equal(a.monitors(), g.monitors(), equal_nan=True)
+
+
+def test_persistent_batch_scope_and_wait_limit(cuda_lib):
+    """Cases outside the persistent kernel's scope are refused (EINVAL); a stage wait that runs out stops the
+    batch with ELIMIT (the test hook makes the step's last item wait for an item that does not exist), flags every
+    case, and leaves the device usable."""
+    with pytest.raises(cuda_lib.UgkwpError) as e:
+        cuda_lib.Batch([cuda_lib.Solver(CASES["box"], precision=1)], persistent=True)
+    assert e.value.status == 1
+    names = ["cylinder", "plate", "shock1d"]
+    grouped = [cuda_lib.Solver(CASES[n], precision=0) for n in names]
+    b = cuda_lib.Batch(grouped, persistent=True)
+    b.step(1)
+    assert b.status() == (0, -1)
+    b.set_wait_limit(2_000_000, stall=True)   # 2 ms
+    b.step(1)
+    st, where = b.status()
+    assert st == 4 and where == (len(names) - 1) * 20 + 19   # the last case's update stage
+    for g in grouped:
+        with pytest.raises(cuda_lib.UgkwpError) as e:
+            g.field()
+        assert e.value.status == 4
+    b.step(1)                                  # a stopped batch does nothing
+    assert b.status()[0] == 4
+    b.close()
+    fresh = cuda_lib.Solver(CASES["cylinder"], precision=0)
+    fresh.step(2)
+    assert np.all(np.isfinite(fresh.field()[0]))
+
+
 def test_launch_parameters_and_autotuner_leave_results_unchanged(cuda_lib):
     """The transport kernel (warp-staged, the production default, against warp-chunked), chunk size, blocks per
     SM and the sort interval reorder work and particles only: the state is the same bit for bit (particles
     compared as sets), also across an autotuning pass that steps the run."""
     case = CASES["cylinder"]
-    a = cuda_lib.Solver(case, precision=0, use_graph=True)
-    b = cuda_lib.Solver(case, precision=0, use_graph=True)
+    # the autotuning pass steps through the start-up transient (particle count up to about 3x the steady one)
+    cap = 8 * case.n_ref * case.mesh.ncells
+    a = cuda_lib.Solver(case, precision=0, use_graph=True, capacity=cap)
+    b = cuda_lib.Solver(case, precision=0, use_graph=True, capacity=cap)
     assert a.launch() == [128, 8, 8, 2]
     b.set_launch(128, 2, 16, 1)
     assert b.launch() == [128, 2, 16, 1]
