@@ -122,6 +122,14 @@ typedef struct {
     void* (*dev_alloc)(size_t bytes, void* stream, void* user);
     void (*dev_free)(void* ptr, void* user);
     void* alloc_user;         /* passed to dev_alloc and dev_free */
+    double emx_cutoff;        /* particle cutoff (a reading of Sec. V A's cost discussion, which ties the cost of a
+                                 step to the mass carried by particles): a cell whose collisionless fraction
+                                 e^{-dt_i/tau_i} is below emx_cutoff samples no new particles that step, and its
+                                 whole hydrodynamic part W^h then travels with the wave (free-transport weight
+                                 dbar_d, as for a cell with rho^hp = 0). Such cells are wave-dominated: the ceil of
+                                 Eq. 26 would give each of them one particle of negligible mass per step. Particles
+                                 already in the cell (or arriving) are unaffected. 0: off (the default); in
+                                 [0, 1), EINVAL otherwise. */
 } ugkwp_opts;
 
 /* Build the context: geometry, fixed local time steps (Eqs. 33-34), uniform freestream state, no

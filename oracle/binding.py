@@ -34,7 +34,7 @@ class OracleGas(C.Structure):
 class OracleOpts(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("case_id", C.c_uint32), ("n_ref", C.c_int32), ("precision", C.c_int32),
                 ("wave_only", C.c_int32), ("record_faces", C.c_int32), ("capacity", C.c_int32),
-                ("ghost_state", C.c_double * 4), ("order", C.c_int32)]
+                ("ghost_state", C.c_double * 4), ("order", C.c_int32), ("emx_cutoff", C.c_double)]
 
 
 def lib():
@@ -51,6 +51,8 @@ def lib():
         _lib.oracle_logd.argtypes = [C.c_double]
         _lib.oracle_expd.restype = C.c_double
         _lib.oracle_expd.argtypes = [C.c_double]
+        _lib.oracle_erfcd.restype = C.c_double
+        _lib.oracle_erfcd.argtypes = [C.c_double]
         _lib.oracle_expf.restype = C.c_float
         _lib.oracle_expf.argtypes = [C.c_float]
         _lib.oracle_sincos2pif.argtypes = [C.c_float, C.POINTER(C.c_float), C.POINTER(C.c_float)]
@@ -127,7 +129,8 @@ class Oracle:
     """One oracle context for a workload `Case` (see paper_2607_09552_b300.workloads)."""
 
     def __init__(self, case, gts: bool = False, precision: int = 0, wave_only: bool = False,
-                 record_faces: bool = False, seed: int | None = None, case_id: int = 0, order: int = 1):
+                 record_faces: bool = False, seed: int | None = None, case_id: int = 0, order: int = 1,
+                 emx_cutoff: float = 0.0):
         L = lib()
         m = case.mesh
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (m.xv, m.yv)]
@@ -143,7 +146,8 @@ class Oracle:
                               *[_p(a, C.c_int32) for a in self._keep[2:]])
         gas = OracleGas(case.omega, case.Pr, getattr(case, "wall_specular", 0.0))
         opts = OracleOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
-                          int(record_faces), 0, (C.c_double * 4)(*case.ghost_state), int(order))
+                          int(record_faces), 0, (C.c_double * 4)(*case.ghost_state), int(order),
+                          float(emx_cutoff))
         self.ctx = C.c_void_p()
         create = L.oracle_create_unstructured if unstructured else L.oracle_create
         st = create(C.byref(mesh), C.byref(gas), C.c_double(case.Kn), C.c_double(case.Ma),

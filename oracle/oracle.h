@@ -60,6 +60,7 @@ typedef struct {
     int32_t capacity;        /* particle capacity; 0 = 4 * n_ref * cells */
     double ghost_state[4];   /* (rho, U, V, T) of BC_FIXED ghosts */
     int32_t order;           /* 2: second-order reconstruction of W and W^h (S6); 0 or 1: first order */
+    double emx_cutoff;       /* cells with e^{-dt_i/tau_i} below it sample no new particles (0: off) */
 } oracle_opts;
 
 int  oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, double Ma, double Tw,

@@ -164,12 +164,12 @@ static int frame_prim(const double W[4], or_prim* p)
 static void moments(const or_prim* p, or_mom* M)
 {
     const double U = p->U, V = p->V, lam = p->lam, th = 0.5 / lam;
-    const double ex = exp(-lam * U * U) / (2.0 * sqrt(OR_PI * lam));
+    const double ex = or_expd(-lam * U * U) / (2.0 * sqrt(OR_PI * lam));
     M->uf[0] = 1.0;
     M->uf[1] = U;
-    M->up[0] = 0.5 * erfc(-sqrt(lam) * U);
+    M->up[0] = 0.5 * or_erfcd(-sqrt(lam) * U);
     M->up[1] = U * M->up[0] + ex;
-    M->um[0] = 0.5 * erfc(sqrt(lam) * U);
+    M->um[0] = 0.5 * or_erfcd(sqrt(lam) * U);
     M->um[1] = U * M->um[0] - ex;
     for (int k = 2; k < 9; ++k) {
         M->uf[k] = U * M->uf[k - 1] + (double)(k - 1) * th * M->uf[k - 2];
@@ -814,6 +814,7 @@ int oracle_create(const oracle_mesh* mesh, const oracle_gas* gas, double Kn, dou
     if (!mesh || !gas || !opts || !out || mesh->ni <= 0 || mesh->nj <= 0) return OR_EINVAL;
     if (mesh->ni * (int64_t)mesh->nj >= (1 << 21)) return OR_EINVAL;
     if (!(gas->wall_specular >= 0.0 && gas->wall_specular <= 1.0)) return OR_EINVAL;
+    if (!(opts->emx_cutoff >= 0.0 && opts->emx_cutoff < 1.0)) return OR_EINVAL;
     or_ctx* cx = zalloc(1, sizeof(or_ctx));
     int st = build_geometry(cx, mesh);
     if (st) { oracle_destroy(cx); return st; }
@@ -828,6 +829,7 @@ int oracle_create_unstructured(const oracle_umesh* mesh, const oracle_gas* gas, 
         return OR_EINVAL;
     if (mesh->n_cells >= (1 << 21)) return OR_EINVAL;
     if (!(gas->wall_specular >= 0.0 && gas->wall_specular <= 1.0)) return OR_EINVAL;
+    if (!(opts->emx_cutoff >= 0.0 && opts->emx_cutoff < 1.0)) return OR_EINVAL;
     or_ctx* cx = zalloc(1, sizeof(or_ctx));
     int st = build_geometry_u(cx, mesh);
     if (st) { oracle_destroy(cx); return st; }
@@ -841,6 +843,7 @@ static int finish_create(or_ctx* cx, const oracle_gas* gas, double Kn, double Ma
     const int C = cx->C, F = cx->F;
     cx->prec = opts->precision; cx->wave_only = opts->wave_only; cx->record_faces = opts->record_faces;
     cx->order = opts->order == 2 ? 2 : 1;
+    cx->emx_cutoff = opts->emx_cutoff;
     cx->gts = gts; cx->n_ref = opts->n_ref; cx->seed = opts->seed; cx->case_id = opts->case_id;
     cx->Kn = Kn; cx->Ma = Ma; cx->Tw = Tw; cx->cfl = cfl; cx->omega = gas->omega; cx->Pr = gas->Pr;
     cx->ws = gas->wall_specular;
@@ -997,9 +1000,11 @@ static void decompose(or_ctx* cx)
         /* W^hp = W^h e^{-dt_i / tau_i}; for rho^hp > 0: N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp
          * (Eqs. 25-26). Reading of Sec. III B: the new particles' velocities follow the local distribution of
          * the cell, at the cell velocity U_i and temperature T_i (not those of W^h, which is a small difference
-         * of noisy tallies where particles dominate); the rest of W^h is transported by the wave (face_flux) */
+         * of noisy tallies where particles dominate); the rest of W^h is transported by the wave (face_flux).
+         * Particle cutoff (reading of Sec. V A's cost discussion): a cell with e^{-x} below emx_cutoff samples
+         * nothing, and all of its W^h travels with the wave */
         const double rho_hp = Wh[0] * e;
-        if (!cx->wave_only && rho_hp > 0.0) {
+        if (!cx->wave_only && rho_hp > 0.0 && !(e < cx->emx_cutoff)) {
             const double q = ceil((rho_hp / W[0]) * (double)cx->n_ref);
             if (q > (double)OR_MAX_NEW) {
                 or_set_error(cx, OR_ELIMIT, "more than 2047 new particles in one cell");
@@ -1282,10 +1287,35 @@ static void update(or_ctx* cx)
         if (cx->dim == 1) Wn[2] = 0.0;
         if (!isfinite(Wn[0]) || !isfinite(Wn[1]) || !isfinite(Wn[2]) || !isfinite(Wn[3]))
             or_set_error(cx, OR_ENONPHYS, "non-finite cell state after the update");
-        /* vacuum floor (reading): a cell emptied of particles whose small wave remainder the outflow drove
-         * out of the realizable set restarts from a near-vacuum state at rest at T_inf */
+        /* realizability floor (reading): statistical noise can leave the wave's share W - W^p of a cell
+         * negative and drive the updated state out of the realizable set. Such a cell restarts from its
+         * particle content W^{p,+} / Omega_i (so that the next step's W^h = W - W^p, the mass of the collided
+         * particles, is not negative), its speed limited to U_cap and its temperature clamped to
+         * [T_min, T_cap]; a cell without particles restarts from the near-vacuum state at rest at T_inf.
+         * (Restarting a cell that holds particles from vacuum instead leaves W^h = -W^p, whose wave flux
+         * drives the neighbours out of the realizable set in turn.) */
         if (!realizable(cx, Wn)) {
-            Wn[0] = OR_RHO_FLOOR; Wn[1] = 0.0; Wn[2] = 0.0; Wn[3] = OR_RHO_FLOOR * (1.5 * OR_R);
+            double P[4];
+            for (int q = 0; q < 4; ++q) P[q] = ((double)cx->wpl[5 * c + tk[q]] * sc[q]) / cx->vol[c];
+            if (cx->dim == 1) P[2] = 0.0;
+            if (P[0] > OR_RHO_FLOOR) {
+                const double r = 1.0 / P[0];
+                double U = P[1] * r, V = P[2] * r;
+                double q2 = U * U + V * V;
+                if (q2 > cx->U_cap * cx->U_cap) {
+                    const double f = cx->U_cap / sqrt(q2);
+                    U = U * f;
+                    V = V * f;
+                    q2 = U * U + V * V;
+                }
+                double e = P[3] * r - 0.5 * q2;
+                const double emin = (1.5 * OR_R) * cx->T_min, emax = (1.5 * OR_R) * cx->T_cap;
+                if (!(e >= emin)) e = emin;
+                if (e > emax) e = emax;
+                Wn[0] = P[0]; Wn[1] = P[0] * U; Wn[2] = P[0] * V; Wn[3] = P[0] * (e + 0.5 * q2);
+            } else {
+                Wn[0] = OR_RHO_FLOOR; Wn[1] = 0.0; Wn[2] = 0.0; Wn[3] = OR_RHO_FLOOR * (1.5 * OR_R);
+            }
             cx->stats[8] += 1;
         }
         for (int q = 0; q < 4; ++q) {

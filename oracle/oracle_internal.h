@@ -29,6 +29,7 @@ struct oracle_ctx {
     /* configuration */
     int dim, ni, nj, periodic_j, C, F;
     int prec, wave_only, record_faces, gts, n_ref, order;
+    double emx_cutoff;                           /* cells with e^{-x} below it sample no new particles */
     uint64_t seed;
     uint32_t case_id;
     int64_t step;
@@ -105,6 +106,7 @@ void   or_uniforms_d(const or_ctx* cx, uint64_t pid, uint32_t base, int n, doubl
 float  or_logf(float x);
 double or_logd(double x);
 double or_expd(double x);
+double or_erfcd(double x);
 float  or_expf(float x);
 double or_powd(double x, double y);
 void   or_sincos2pif(float u, float* s, float* c);

@@ -50,6 +50,9 @@ __host__ __device__ __forceinline__ double pow2(int e)
 #define UGKWP_SORT_EVERY 8   // steps between counting sorts of the particles by cell
 #endif
 #ifndef UGKWP_PARTICLES_MINB
+#ifndef UGKWP_FLY_MINB
+#define UGKWP_FLY_MINB 6         // resident 128-thread blocks per SM the flight pass is compiled and launched for
+#endif
 #define UGKWP_PARTICLES_MINB 4   // resident 256-thread blocks per SM the warp-chunked transport kernel is compiled for
 #endif
 constexpr int kMaxCells = 1 << 20;
@@ -631,9 +634,10 @@ __device__ __forceinline__ void decompose_body(const VB vb, const StepConsts& K,
     double m = 0.0, Ui = 0.0, Vi = 0.0, RTi = 0.0;
     // W^hp = W^h e^{-dt_i/tau_i}; for rho^hp > 0: N^hp = ceil(rho^hp / rho N_ref), m = rho^hp Omega / N^hp
     // (Eqs. 25-26). The new particles' velocities follow the local distribution of the cell (Sec. III B), at
-    // the cell velocity U_i and temperature T_i of the total W; the rest of W^h travels with the wave
+    // the cell velocity U_i and temperature T_i of the total W; the rest of W^h travels with the wave. A cell
+    // whose e^{-x} is below the particle cutoff samples nothing (its W^h all travels with the wave)
     const double rho_hp = Wh[0] * e;
-    if (!K.wave_only && rho_hp > 0.0) {
+    if (!K.wave_only && rho_hp > 0.0 && !(e < K.emx_cutoff)) {
         const double q = ceil((rho_hp / W[0]) * (double)K.n_ref);
         if (q > (double)kMaxNew) {
             atomicOr(d.err, ERR_LIMIT);
@@ -893,12 +897,11 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 }
 
 // ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
-// One warp per sampling cell (the cells listed by the decomposition). Velocities from the local distribution
-// of the cell at U_i, T_i (Sec. III B): Box-Muller normals (Pr = 1) or Shakhov acceptance-rejection (Pr != 1),
-// shifted and scaled so that the cell's new particles carry exactly the momentum U_i and energy (3/2) R T_i per
-// unit mass of that distribution. The draws, positions and tallies run on all 32 lanes (particle k on lane
-// k mod 32); the sums of the shift and scale keep a fixed order: lane j < 8 adds k = j, j + 8, ... in increasing
-// k, then a butterfly combines those eight partial sums (j + 4 into j, j + 2 into j, j + 1 into j).
+// One warp per sampling cell (the cells listed by the decomposition), particle k on lane k mod 32. Velocities
+// are independent draws from the local distribution of the cell at U_i, T_i (Sec. III B): U_i + sqrt(R T_i) z
+// with z Box-Muller normals (Pr = 1) or from the Shakhov acceptance-rejection (Pr != 1); no per-cell moment
+// matching (forcing a few particles onto the cell's exact momentum and energy changes their speed
+// distribution, and with it the speed-weighted fluxes such as the energy carried to a wall).
 template <typename T>
 __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, const ParticleSoA<T>& A,
                                             const PCell<T>& pc, const long long* dstep, int c)
@@ -917,68 +920,8 @@ __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, c
     int fallbacks = 0;
     const T ax = K.shakhov ? pc.q_(c, 0) : T(0), ay = K.shakhov ? pc.q_(c, 1) : T(0);
     const T M = K.shakhov ? pc.q_(c, 2) : T(1);
-    for (int k = l; k < N; k += 32) {
-        // Pr = 1: Box-Muller normals. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-rejection (Sec. III B):
-        // Maxwellian proposals accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5), |z| > 6
-        // rejected; after kArAttempts rejections the last proposal stays
-        T z0 = 0, z1 = 0, z2 = 0;
-        const int attempts = K.shakhov ? kArAttempts : 1;
-        bool accepted = !K.shakhov;
-        for (int a = 0; a < attempts; ++a) {
-            T U[4];
-            Unif<T>::get(g, pbase | (uint64_t)k, K.shakhov ? draw_ar(a) : DRAW_VEL, 4, U);
-            const T r0 = fsqrt_(T(-2) * dlog(U[0]));
-            T s0, c0, s1, c1;
-            dsincos2pi(U[1], &s0, &c0);
-            const T r1 = fsqrt_(T(-2) * dlog(U[2]));
-            dsincos2pi(U[3], &s1, &c1);
-            z0 = r0 * c0; z1 = r0 * s0; z2 = r1 * c1;
-            if (!K.shakhov) break;
-            const T s2 = (z0 * z0 + z1 * z1) + z2 * z2;
-            if (s2 <= T(36)) {
-                const T psi = (z0 * ax + z1 * ay) * (s2 - T(5));
-                T Ua[1];
-                Unif<T>::get(g, pbase | (uint64_t)k, draw_ar(a) + 2u, 1, Ua);
-                if (Ua[0] * M < T(1) + psi) { accepted = true; break; }
-            }
-        }
-        if (!accepted) fallbacks++;
-        A.u[base_i + k] = z0; A.v[base_i + k] = z1; A.w[base_i + k] = z2;
-    }
-    if (K.shakhov) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
-        if (l == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
-    }
-    __syncwarp();
-    // the eight strided partial sums (lanes 8-31 hold zeros), the butterfly, lane 0's value for every lane
-    T su = 0, sv = 0, sw = 0;
-    if (l < 8)
-        for (int k = l; k < N; k += 8) { su += A.u[base_i + k]; sv += A.v[base_i + k]; sw += A.w[base_i + k]; }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        su = su + __shfl_xor_sync(0xffffffffu, su, o);
-        sv = sv + __shfl_xor_sync(0xffffffffu, sv, o);
-        sw = sw + __shfl_xor_sync(0xffffffffu, sw, o);
-    }
-    su = __shfl_sync(0xffffffffu, su, 0);
-    sv = __shfl_sync(0xffffffffu, sv, 0);
-    sw = __shfl_sync(0xffffffffu, sw, 0);
-    const T inv = T(1) / T(N);
-    const T mu = su * inv, mv = sv * inv, mw = sw * inv;
-    T ss = 0;
-    if (l < 8)
-        for (int k = l; k < N; k += 8) {
-            const T du = A.u[base_i + k] - mu, dv = A.v[base_i + k] - mv, dw = A.w[base_i + k] - mw;
-            ss += (du * du + dv * dv) + dw * dw;
-        }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) ss = ss + __shfl_xor_sync(0xffffffffu, ss, o);
-    ss = __shfl_sync(0xffffffffu, ss, 0);
-    __syncwarp();
     long long acc[5] = {0, 0, 0, 0, 0};
-    const T Ui = pc.s_(c, 0), Vi = pc.s_(c, 1), RTi = pc.s_(c, 2);
-    const T sc = (N > 1 && ss > T(0)) ? fsqrt_(((T(3) * T(N)) * RTi) / ss) : T(0);
+    const T Ui = pc.s_(c, 0), Vi = pc.s_(c, 1), sig = fsqrt_(pc.s_(c, 2));
     const T m = pc.m_(c);
     const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
     // the cell's vertices in the particle precision and its two triangles' areas (same for every particle)
@@ -993,6 +936,31 @@ __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, c
     const T A12 = A1 + A2;
     for (int k = l; k < N; k += 32) {
         const uint64_t pid = pbase | (uint64_t)k;
+        // Pr = 1: Box-Muller normals. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-rejection (Sec. III B):
+        // Maxwellian proposals accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5), |z| > 6
+        // rejected; after kArAttempts rejections the last proposal stays
+        T z0 = 0, z1 = 0, z2 = 0;
+        const int attempts = K.shakhov ? kArAttempts : 1;
+        bool accepted = !K.shakhov;
+        for (int a = 0; a < attempts; ++a) {
+            T U[4];
+            Unif<T>::get(g, pid, K.shakhov ? draw_ar(a) : DRAW_VEL, 4, U);
+            const T r0 = fsqrt_(T(-2) * dlog(U[0]));
+            T sn0, cs0, sn1, cs1;
+            dsincos2pi(U[1], &sn0, &cs0);
+            const T r1 = fsqrt_(T(-2) * dlog(U[2]));
+            dsincos2pi(U[3], &sn1, &cs1);
+            z0 = r0 * cs0; z1 = r0 * sn0; z2 = r1 * cs1;
+            if (!K.shakhov) break;
+            const T s2 = (z0 * z0 + z1 * z1) + z2 * z2;
+            if (s2 <= T(36)) {
+                const T psi = (z0 * ax + z1 * ay) * (s2 - T(5));
+                T Ua[1];
+                Unif<T>::get(g, pid, draw_ar(a) + 2u, 1, Ua);
+                if (Ua[0] * M < T(1) + psi) { accepted = true; break; }
+            }
+        }
+        if (!accepted) fallbacks++;
         const long long i = base_i + k;
         T U[3], x, y;
         Unif<T>::get(g, pid, DRAW_POS, 3, U);
@@ -1007,17 +975,7 @@ __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, c
             x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
             y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
         }
-        const T z0 = A.u[i], z1 = A.v[i], z2 = A.w[i];
-        T un, vn, wn;
-        if (N == 1) {
-            // a single particle keeps the direction of its draw at the thermal speed sqrt(3 R T_i) about U_i:
-            // the energy exactly, the momentum without bias
-            const T zz = (z0 * z0 + z1 * z1) + z2 * z2;
-            const T s1n = zz > T(0) ? fsqrt_((T(3) * RTi) / zz) : T(0);
-            un = Ui + s1n * z0; vn = Vi + s1n * z1; wn = s1n * z2;
-        } else {
-            un = Ui + sc * (z0 - mu); vn = Vi + sc * (z1 - mv); wn = sc * (z2 - mw);
-        }
+        const T un = Ui + sig * z0, vn = Vi + sig * z1, wn = sig * z2;
         A.x[i] = x; A.y[i] = y;
         A.u[i] = un;
         A.v[i] = vn;
@@ -1029,6 +987,11 @@ __device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, c
         fix5(m, un, vn, wn, s0, s1, s4, d.err, f);
 #pragma unroll
         for (int q = 0; q < 5; ++q) acc[q] += f[q];
+    }
+    if (K.shakhov) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+        if (l == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
     }
     // W^{p,-} of the new particles: this warp owns the cell, so a butterfly sum and one update (atomic for
     // W^{p,+}: the ghost sources on the second stream may add to the same cell meanwhile)
@@ -1710,7 +1673,7 @@ __device__ __forceinline__ void fly_body(const VB vb, const StepConsts& K, const
         if (n_kept) atomicAdd(d.counts + 2, (int)n_kept);
     }
 }
-__global__ void __launch_bounds__(128) k_particles_fly(const StepConsts K, const Dev d, ParticleSoA<float> PA,
+__global__ void __launch_bounds__(128, UGKWP_FLY_MINB) k_particles_fly(const StepConsts K, const Dev d, ParticleSoA<float> PA,
                                                        ParticleSoA<float> PB, const CellFaces<float>* __restrict__ cf,
                                                        const long long* dstep)
 {
@@ -1955,10 +1918,33 @@ __device__ __forceinline__ void update_body(const VB vb, const StepConsts& K, co
         }
         if (K.dim == 1) Wn[2] = 0.0;
         if (!isfinite(Wn[0]) || !isfinite(Wn[1]) || !isfinite(Wn[2]) || !isfinite(Wn[3])) atomicOr(d.err, ERR_NONPHYS);
-        // vacuum floor: a cell emptied of particles whose small wave remainder the outflow drove out of the
-        // realizable set restarts from a near-vacuum state at rest at T_inf
+        // realizability floor: statistical noise can leave the wave's share W - W^p of a cell negative and
+        // drive the updated state out of the realizable set. Such a cell restarts from its particle content
+        // W^{p,+} / Omega_i (the next step's W^h = W - W^p is then the collided particles' mass, not negative),
+        // speed limited to U_cap, temperature clamped to [T_min, T_cap]; a cell without particles restarts from
+        // the near-vacuum state at rest at T_inf
         if (!realizable(K, Wn)) {
-            Wn[0] = kRhoFloor; Wn[1] = 0.0; Wn[2] = 0.0; Wn[3] = kRhoFloor * (1.5 * kR);
+            double P[4];
+            for (int q = 0; q < 4; ++q) P[q] = ((double)d.wpl[5 * c + tk[q]] * sc[q]) * rvol;
+            if (K.dim == 1) P[2] = 0.0;
+            if (P[0] > kRhoFloor) {
+                const double r = 1.0 / P[0];
+                double U = P[1] * r, V = P[2] * r;
+                double q2 = U * U + V * V;
+                if (q2 > K.U_cap * K.U_cap) {
+                    const double f = K.U_cap / sqrt(q2);
+                    U = U * f;
+                    V = V * f;
+                    q2 = U * U + V * V;
+                }
+                double e = P[3] * r - 0.5 * q2;
+                const double emin = (1.5 * kR) * K.T_min, emax = (1.5 * kR) * K.T_cap;
+                if (!(e >= emin)) e = emin;
+                if (e > emax) e = emax;
+                Wn[0] = P[0]; Wn[1] = P[0] * U; Wn[2] = P[0] * V; Wn[3] = P[0] * (e + 0.5 * q2);
+            } else {
+                Wn[0] = kRhoFloor; Wn[1] = 0.0; Wn[2] = 0.0; Wn[3] = kRhoFloor * (1.5 * kR);
+            }
             atomicAdd(d.stats + 11, 1ull);
         }
         for (int q = 0; q < 4; ++q) {
@@ -2246,7 +2232,7 @@ template <int WT, int MINB> void launch_warp_variant(Ctx& ctx, cudaStream_t s, c
     Dev& d = ctx.d;
     k_particles_warp<WT, MINB><<<MINB * ctx.sms, kWWarps * 32, kWWarps * sizeof(WarpSmem<WT>), s>>>(
         K, d, d.pa32, d.pb32, d.cf32, d.dstep);
-    k_particles_fly<<<5 * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
+    k_particles_fly<<<UGKWP_FLY_MINB * ctx.sms, 128, 0, s>>>(K, d, d.pa32, d.pb32, d.cf32, d.dstep);
 }
 void launch_particles_warp(Ctx& ctx, cudaStream_t s, const PCell<float>& pc)
 {
@@ -2802,6 +2788,10 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
         delete h;
         return UGKWP_EINVAL;
     }
+    if (!(opts->emx_cutoff >= 0.0 && opts->emx_cutoff < 1.0)) {
+        delete h;
+        return UGKWP_EINVAL;
+    }
     if (cudaStreamCreateWithFlags(&ctx.stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx.stream3, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -2824,6 +2814,7 @@ ugkwp_status create_impl(const ugkwp_mesh* mesh, const UTopo* topo, const ugkwp_
     K.order = opts->order == 2 ? 2 : 1;
     K.omega = gas->omega; K.Pr = gas->Pr; K.Tw = Tw;
     K.wall_specular = gas->wall_specular;
+    K.emx_cutoff = opts->emx_cutoff;
     K.shakhov = gas->Pr != 1.0 && !opts->wave_only;
     K.mu_inf = (15.0 * sqrt(2.0 * 3.14159265358979323846 * 0.5) * Kn) / (2.0 * (5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega));
     K.U_inf = Ma * sqrt((5.0 / 3.0) * 0.5 * 1.0);

@@ -57,15 +57,24 @@ template <typename R> __device__ __forceinline__ bool frame_prim(const R W[4], P
     return true;
 }
 
-template <typename R> __device__ __forceinline__ void moments(const Prim<R>& p, Mom<R>& M)
+// kDet (FP64 only, the all-FP64 mode): e^x and erfc from IEEE operations (dexp, derfc) instead of CUDA's
+// library functions, so that the moments do not depend on a math library's last bits
+template <typename R, bool kDet = false> __device__ __forceinline__ void moments(const Prim<R>& p, Mom<R>& M)
 {
     const R U = p.U, V = p.V, lam = p.lam, th = p.th;
     const R sl = sqrt(lam);
-    R ex;
-    if constexpr (sizeof(R) == 4) ex = expf(-lam * U * U) * (0.5f * rsqrtf(3.14159265358979323846f * lam));
-    else ex = exp(-lam * U * U) / (R(2) * sqrt(R(3.14159265358979323846) * lam));
+    R ex, small;
     // one erfc per Maxwellian: the smaller half-range mass from erfc(sqrt(lambda)|U|), the other as 1 - it
-    const R small = R(0.5) * erfc(sl * fabs(U));
+    if constexpr (sizeof(R) == 4) {
+        ex = expf(-lam * U * U) * (0.5f * rsqrtf(3.14159265358979323846f * lam));
+        small = R(0.5) * erfc(sl * fabs(U));
+    } else if constexpr (kDet) {
+        ex = dexp(-lam * U * U) / (R(2) * sqrt(R(3.14159265358979323846) * lam));
+        small = R(0.5) * derfc(sl * fabs(U));
+    } else {
+        ex = exp(-lam * U * U) / (R(2) * sqrt(R(3.14159265358979323846) * lam));
+        small = R(0.5) * erfc(sl * fabs(U));
+    }
     M.up[0] = U >= R(0) ? R(1) - small : small;
     M.um[0] = U >= R(0) ? small : R(1) - small;
     M.up[1] = U * M.up[0] + ex;
@@ -140,12 +149,12 @@ template <typename R> __device__ __forceinline__ void pr_fix(const Prim<R>& p, R
 // equilibrium part of Eq. 49 given the interface state W_0 (primitive p0); c[0..2] = dbar_a, dbar_b,
 // dbar_c of each side. Moments in precision R; the time-integration weights and the weighted sum in
 // precision C (C = double for the faces of wall cells in production mode: FP64 time integrals).
-template <typename R, typename C>
+template <typename R, typename C, bool kDet = false>
 __device__ void equilibrium_part(const R W0[4], const R WL[4], const R WR[4], const Prim<R>& p0, const C cL[3],
                                  const C cR[3], R dL, R dR, R Pr, C F[4])
 {
     Mom<R> m0;
-    moments(p0, m0);
+    moments<R, kDet>(p0, m0);
     R t1[4], t2[4];
     R dw[4], aL[4], aR[4], A[4];
     if constexpr (sizeof(R) == 4) {
@@ -260,7 +269,7 @@ __device__ __forceinline__ void prim_perturbation(const double W[4], const doubl
 // taken against; dhL, dhR (nullable): normal derivatives of W^h for the slope term of the free-transport wave,
 // weighted with csL, csR (order 2). Returns false if a side state is not a valid Maxwellian in precision R
 // (the caller then uses FP64).
-template <typename R, typename C>
+template <typename R, typename C, bool kDet = false>
 __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R WhR[4], const R dpL[4],
                           const R dpR[4], C fdL, C fdR, const C cL[3], const C cR[3], C frL, C frR, R dL, R dR,
                           R Pr, const R WLc[4], const R WRc[4], const R* dhL, const R* dhR, C csL, C csR, C F[4])
@@ -270,15 +279,15 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
 #pragma unroll
     for (int k = 0; k < 4; ++k) F[k] = C(0);
     if (!frame_prim(WL, pL) || !frame_prim(WR, pR)) return false;
-    moments(pL, mL);
-    moments(pR, mR);
+    moments<R, kDet>(pL, mL);
+    moments<R, kDet>(pR, mR);
     R t1[4], t2[4], W0[4];
     psi_mom(mL.up, mL, 0, 0, 0, t1);
     psi_mom(mR.um, mR, 0, 0, 0, t2);
 #pragma unroll
     for (int k = 0; k < 4; ++k) W0[k] = pL.rho * t1[k] + pR.rho * t2[k];
     // vacuum interface: no molecule of either side reaches the face, no equilibrium flux
-    if (frame_prim(W0, p0)) equilibrium_part(W0, WLc, WRc, p0, cL, cR, dL, dR, Pr, F);
+    if (frame_prim(W0, p0)) equilibrium_part<R, C, kDet>(W0, WLc, WRc, p0, cL, cR, dL, dR, Pr, F);
     wave_part<R, C>(pL, mL, true, WL, WhL, dpL, frL, fdL, dhL, csL, F);
     wave_part<R, C>(pR, mR, false, WR, WhR, dpR, frR, fdR, dhR, csR, F);
     return true;
@@ -287,7 +296,7 @@ __device__ bool face_flux(const R WL[4], const R WR[4], const R WhL[4], const R 
 // diffuse (or Maxwell) isothermal wall: the incoming half of the fluid cell's g and of its hydrodynamic wave
 // (as in face_flux: weights frL and fdL), the outgoing wall Maxwellian at T_w with the density that makes the
 // wave mass flux zero
-template <typename R, typename C>
+template <typename R, typename C, bool kDet = false>
 __device__ bool wall_flux(const R WL[4], const R WhL[4], const R dpL[4], C fdL, C caL, C frL, R lam_w, C ws,
                           C F[4])
 {
@@ -295,13 +304,13 @@ __device__ bool wall_flux(const R WL[4], const R WhL[4], const R dpL[4], C fdL, 
     Mom<R> m;
     R t[4];
     if (!frame_prim(WL, p)) return false;
-    moments(p, m);
+    moments<R, kDet>(p, m);
     psi_mom(m.up, m, 1, 0, 0, t);
 #pragma unroll
     for (int k = 0; k < 4; ++k) F[k] = caL * C(p.rho * t[k]);
     wave_part<R, C>(p, m, true, WL, WhL, dpL, frL, fdL, nullptr, C(0), F);
     p.rho = R(1); p.U = R(0); p.V = R(0); p.lam = lam_w; p.th = R(0.5) / lam_w;
-    moments(p, m);
+    moments<R, kDet>(p, m);
     psi_mom(m.um, m, 1, 0, 0, t);
     const C rw = -F[0] / C(t[0]);
     if (ws == C(0)) {
@@ -390,7 +399,7 @@ __device__ bool face_side(const StepConsts& K, const Dev& c, int cc, int f, int 
     return Wf[0] > 0.0 && __dsub_rn(Wf[3], __ddiv_rn(ke, Wf[0])) > 0.0;
 }
 
-template <typename R, typename C>
+template <typename R, typename C, bool kDet = false>
 __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4])
 {
     constexpr bool f32 = sizeof(R) == 4;   // FP32 moments: the per-cell FP32 copies of k_flux_prep
@@ -490,15 +499,15 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
                 sR = true;
             }
         }
-        ok = face_flux<R, C>(WL, WR, WhL, WhR, dpL, dpR, fdL, coef(Rc, 3), cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]),
+        ok = face_flux<R, C, kDet>(WL, WR, WhL, WhR, dpL, dpR, fdL, coef(Rc, 3), cL, cR, frL, frR, R(c.fdL[f]), R(c.fdR[f]),
                              R(K.Pr), WLc, WRc, sL ? dhL : nullptr, sR ? dhR : nullptr, csL,
                              K.wave_only ? coef(Rc, 4) : coef(Rc, 6), F);
     } else if (bc == UGKWP_BC_WALL) {
-        ok = wall_flux<R, C>(WL, WhL, dpL, fdL, cL[0], frL, R(0.5 / (kR * K.Tw)), C(K.wall_specular), F);
+        ok = wall_flux<R, C, kDet>(WL, WhL, dpL, fdL, cL[0], frL, R(0.5 / (kR * K.Tw)), C(K.wall_specular), F);
     } else if (bc == UGKWP_BC_SYMMETRY) {
         const R Wm[4] = {WL[0], -WL[1], WL[2], WL[3]}, Whm[4] = {WhL[0], -WhL[1], WhL[2], WhL[3]};
         dpR[0] = dpL[0]; dpR[1] = -dpL[1]; dpR[2] = dpL[2]; dpR[3] = dpL[3];
-        ok = face_flux<R, C>(WL, Wm, WhL, Whm, dpL, dpR, fdL, fdL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), WL, Wm,
+        ok = face_flux<R, C, kDet>(WL, Wm, WhL, Whm, dpL, dpR, fdL, fdL, cL, cL, frL, frL, R(c.fdL[f]), R(c.fdL[f]), R(K.Pr), WL, Wm,
                              nullptr, nullptr, C(0), C(0), F);
     } else {
         double Wg[4];
@@ -516,7 +525,7 @@ __device__ bool one_face(const StepConsts& K, const Dev& c, int f, double out[4]
         ghost_coeffs(c.dt[L], tau_of(K, Wg), cg);
         const C cR[3] = {C(cg[0]), C(cg[1]), C(cg[2])};
         // the ghost's wave is its whole state (no remainder: dpR = 0)
-        ok = face_flux<R, C>(WL, WR, WhL, WR, dpL, dpR, fdL, C(cg[3]), cL, cR, frL, C(K.wave_only ? cg[3] : cg[4]), R(c.fdL[f]),
+        ok = face_flux<R, C, kDet>(WL, WR, WhL, WR, dpL, dpR, fdL, C(cg[3]), cL, cR, frL, C(K.wave_only ? cg[3] : cg[4]), R(c.fdL[f]),
                              R(c.fdL[f]), R(K.Pr), WLc, WR, sL ? dhL : nullptr, nullptr, csL, C(0), F);
     }
     const C nxc = C(nx), nyc = C(ny);
@@ -578,7 +587,8 @@ __device__ __forceinline__ void fluxmix_body(const VB vb, const StepConsts& K, c
 __global__ void __launch_bounds__(128) k_wave_flux_mixed(const StepConsts K, const Dev c) { fluxmix_body(UGKWP_VB_LAUNCH, K, c); }
 
 // FP64 faces: the static list (every face in the FP64 mode, none in production mode), then the faces
-// queued by the FP32 kernel. The FP64 pipe's cost grows with the active lanes of a warp, so in production
+// queued by the FP32 kernel. In the all-FP64 mode the moments take e^x and erfc from IEEE operations (dexp,
+// derfc); production-mode faces (second order, FP32 failures) keep CUDA's exp and erfc. The FP64 pipe's cost grows with the active lanes of a warp, so in production
 // mode the (rare) queued faces are spread one per warp (lane 0); in the all-FP64 mode every lane takes a
 // face.
 // (the body: lane tx of the 32-thread block vb of nvb)
@@ -590,7 +600,8 @@ __device__ __forceinline__ void flux64_body(const StepConsts& K, const Dev& c, i
     for (int j = tx * nvb + vb; j < n; j += nvb * lanes) {
         const int f = all_faces ? j : j < K.n_f64 ? c.f64list[j] : c.retry[j - K.n_f64];
         double out[4];
-        one_face<double, double>(K, c, f, out);
+        if (K.prec == 1) one_face<double, double, true>(K, c, f, out);
+        else one_face<double, double, false>(K, c, f, out);
         // a non-finite flux (near-vacuum neighbours: the interface density underflows against theirs and the
         // slopes overflow) carries nothing through the face
         if (!isfinite(out[0]) || !isfinite(out[1]) || !isfinite(out[2]) || !isfinite(out[3]))

@@ -45,6 +45,7 @@ struct StepConsts {
     int stag0, stag1;               // wall faces of the stagnation point (-1: none), for the monitors
     double mu_inf, omega, Pr, Tw, U_inf, m2RTw, sig_w;
     double wall_specular;           // Maxwell wall: specular fraction 1 - alpha (0: fully diffuse)
+    double emx_cutoff;              // cells with e^{-x} below it sample no new particles (0: off)
     double T_cap, U_cap, T_min;     // realizability bounds of a cell state
     double W_inf[4], W_fix[4];
     uint32_t k0, k1;                // Philox key

@@ -55,7 +55,7 @@ class UgkwpOpts(C.Structure):
                 ("wave_only", C.c_int32), ("record_faces", C.c_int32), ("capacity", C.c_int32),
                 ("ghost_state", C.c_double * 4), ("stream", C.c_void_p), ("use_graph", C.c_int32),
                 ("order", C.c_int32), ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p),
-                ("alloc_user", C.c_void_p)]
+                ("alloc_user", C.c_void_p), ("emx_cutoff", C.c_double)]
 
 
 # Device memory of the contexts from torch's caching allocator (ugkwp_opts.dev_alloc / dev_free)
@@ -145,9 +145,9 @@ class Solver:
 
     def __init__(self, case, gts: bool = False, precision: int = 0, wave_only: bool = False, seed: int | None = None,
                  case_id: int = 0, capacity: int = 0, use_graph: bool = False, stream=None,
-                 record_faces: bool = False, order: int = 1, torch_memory: bool = True):
+                 record_faces: bool = False, order: int = 1, torch_memory: bool = True, emx_cutoff: float = 0.0):
         """torch_memory: the context's device memory from torch's caching allocator (else the library calls
-        cudaMalloc itself)."""
+        cudaMalloc itself). emx_cutoff: cells with e^{-dt/tau} below it sample no new particles (0: off)."""
         L = load()
         m = case.mesh
         self._keep = [np.ascontiguousarray(m.xv, dtype=np.float64), np.ascontiguousarray(m.yv, dtype=np.float64)]
@@ -165,6 +165,7 @@ class Solver:
         opts = UgkwpOpts(case.seed if seed is None else seed, case_id, case.n_ref, precision, int(wave_only),
                          int(record_faces), capacity, (C.c_double * 4)(*case.ghost_state), C.c_void_p(stream),
                          int(use_graph), int(order))
+        opts.emx_cutoff = float(emx_cutoff)
         if torch_memory:
             opts.dev_alloc = C.cast(_TORCH_ALLOC, C.c_void_p)
             opts.dev_free = C.cast(_TORCH_FREE, C.c_void_p)

@@ -38,9 +38,9 @@ def assert_field_close(Wg, Wo, tol, floor=None):
     max(|W_oracle|, floor * max_i |W_oracle|) (per element; the floor keeps components that cross zero and
     near-vacuum cells, which hold no weight in the step, from a division by nearly nothing), and
     max_i |W_gpu - W_oracle| <= tol * max_i |W_oracle|. Default floor: 0.1 of the component's scale in production
-    precision (FP32 wave-flux moments; measured worst element 0.63 tol), 0.01 in the all-FP64 mode (last-bit
-    differences of the two sides' transcendental functions, amplified in low-density cells; measured worst
-    element 0.26 tol)."""
+    precision (FP32 wave-flux moments; measured worst element 0.63 tol), 0.01 in the all-FP64 mode (both sides
+    evaluate e^x and erfc by their own IEEE-operation implementations; the remaining few-ulp differences, of
+    operation order, are amplified in low-density cells: measured worst element 0.02 tol per step)."""
     if floor is None:
         floor = 1e-1 if tol > 1e-8 else 1e-2
     for c in range(Wo.shape[1]):

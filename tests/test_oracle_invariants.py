@@ -432,3 +432,75 @@ def test_uniform_ma5_flow_kept_within_5_sigma(gts, ends):
     z = np.abs(mean - 1.0) / se
     assert z.max() < 5.0, (z.max(), np.unravel_index(z.argmax(), z.shape))
     assert np.all(np.abs(mean.mean(axis=1) - 1.0) < 0.015), mean.mean(axis=1)
+
+
+def test_particle_cutoff_leaves_the_steady_shock_within_noise():
+    """Particle cutoff (opts.emx_cutoff): cells whose e^{-dt/tau} is below 0.05 sample no new particles and
+    their W^h travels with the wave. On a 1-D Ma 3 shock at Kn 0.05 (100 cells, the coarse ones wave-dominated,
+    about 17 of them cut) the field averaged over 600 steps, mean of 4 seeds, stays as close to the uncut
+    mean as two independent 4-seed means are expected to be (5 standard errors of the difference, per
+    component in the L2 norm), and fewer particles are carried."""
+    case = wl.case_shock1d(ni=100, n_ref=50)
+    case.Kn = 0.05
+
+    def run(seed, cut):
+        o = ob.Oracle(case, precision=0, seed=seed, emx_cutoff=cut)
+        o.step(600)
+        W = 0.0
+        for _ in range(60):
+            o.step(10)
+            W = W + o.field()[0]
+        return W / 60.0, o.stats()[1], o.cell_data()[:, 3]
+
+    none = [run(s, 0.0) for s in range(4)]
+    cut = [run(10 + s, 0.05) for s in range(4)]
+    o = ob.Oracle(case, precision=0, emx_cutoff=0.05)
+    o.step(300)
+    assert (o.cell_data()[:, 2] < 0.05).sum() >= 5
+    A = np.array([r[0] for r in none])
+    B = np.array([r[0] for r in cut])
+    for k in (0, 1, 3):
+        d = np.linalg.norm(A[:, :, k].mean(0) - B[:, :, k].mean(0))
+        # squared distance of one seed from its group mean, summed over cells: variance estimate per group
+        va = ((A[:, :, k] - A[:, :, k].mean(0)) ** 2).sum() / (len(A) - 1)
+        vb = ((B[:, :, k] - B[:, :, k].mean(0)) ** 2).sum() / (len(B) - 1)
+        se = np.sqrt(va / len(A) + vb / len(B))
+        assert d <= 5.0 * se, (k, d, se)
+    assert np.mean([r[1] for r in cut]) < np.mean([r[1] for r in none])
+
+
+def test_realizability_floor_restarts_a_cell_from_its_particle_content():
+    """A cell that holds particles but whose updated state leaves the realizable set (here: its W loaded far
+    below the mass of its particles, so that the particles leaving it within the step drive W negative)
+    restarts from its particle content W^{p,+} / Omega_i: mass that of the tally exactly, momentum to the
+    rounding of U = (rho U) / rho, the
+    internal energy that of the tally clamped to [(3/2) R T_min, (3/2) R T_cap]; the event is counted and the
+    next step's W^h = W - W^p of the cell is not negative."""
+    case = wl.case_periodic_box(ni=20, end_ratio=1.0, n_ref=40, Kn=1.0)
+    o = ob.Oracle(case, precision=1)
+    o.step(3)
+    step, W0, wret, parts = snapshot_of(o)
+    for c in range(20):   # the first cell whose particles leave faster than others arrive
+        W = W0.copy()
+        W[c] = [1e-3, 0.0, 0.0, 1e-3 * 0.75]
+        o = ob.Oracle(case, precision=1)
+        o.set_state(step, W, wret, parts)
+        o.step(1)
+        if int(o.stats()[8]) >= 1:
+            break
+    assert int(o.stats()[8]) == 1
+    Wn, Wp = o.field()
+    t = o.tallies()["wpl"]
+    _, vol = o.geometry()
+    fx = o.fx
+    P = np.array([t[c, 0] * 2.0 ** -fx[0], t[c, 1] * 2.0 ** -fx[1], 0.0, t[c, 4] * 2.0 ** -fx[2]]) / vol[c]
+    assert P[0] > 1e-12 and Wn[c, 0] == P[0] and abs(Wn[c, 1] - P[1]) <= 1e-15 * abs(P[1]) and Wn[c, 2] == 0.0
+    e = Wn[c, 3] / Wn[c, 0] - 0.5 * (Wn[c, 1] / Wn[c, 0]) ** 2
+    e_tally = P[3] / P[0] - 0.5 * (P[1] / P[0]) ** 2
+    assert abs(e - min(max(e_tally, 0.75 * 0.01), 0.75 * 10.0)) <= 1e-12 * max(e, 1.0)
+    assert Wn[c, 0] - Wp[c, 0] >= 0.0   # the next step's W^h: the collided particles' mass
+
+
+def snapshot_of(o):
+    W, _ = o.field()
+    return int(o.stats()[0]), W.copy(), o.tallies()["wret"].copy(), o.particles()

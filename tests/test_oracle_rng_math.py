@@ -86,3 +86,28 @@ def test_sincos2pi_float_and_double():
         assert abs(c - float(mpmath.cos(a))) <= 3e-16
 
 
+
+
+def test_erfcd_against_multiprecision():
+    """FP64 erfc of the wave flux's half-range moments (series of A&S 7.1.6 below 3/2, Laplace's continued
+    fraction A&S 7.1.14 above) against 40-digit mpmath over [-6, 27]: within 2e-14 relative where e^{-x^2} is
+    at least 1e-30 (the rounding of x^2 sets a floor of about x^2 ulp beyond that, checked at 1e-13), with
+    erfc(-x) = 2 - erfc(x), erfc(0) = 1 and 0 where e^{-x^2} is flushed (x^2 > 708, as the exponential)."""
+    import mpmath
+    mpmath.mp.dps = 40
+    L = ob.lib()
+    xs = np.concatenate([np.linspace(-6.0, 6.0, 2401), np.linspace(6.0, 27.0, 211), [1.5 - 2 ** -40, 1.5]])
+    for x in xs:
+        x = float(x)
+        ref = float(mpmath.erfc(mpmath.mpf(x)))
+        g = L.oracle_erfcd(x)
+        if x * x > 708.0:
+            assert g == 0.0, x
+            continue
+        bar = 2e-14 if x * x < 69.0 else 1e-13
+        assert abs(g - ref) <= bar * ref, (x, g, ref)
+        if x > 0:
+            assert L.oracle_erfcd(-x) == 2.0 - g
+    assert L.oracle_erfcd(0.0) == 1.0
+    assert L.oracle_erfcd(30.0) == 0.0
+    assert L.oracle_erfcd(-30.0) == 2.0

@@ -197,3 +197,30 @@ def test_monitors_restate_the_wall_load_definitions():
     o.step(2)
     m = o.monitors()
     assert np.isfinite(m[[0, 1, 4, 5]]).all() and np.isnan(m[[2, 3, 6, 7]]).all()
+
+
+@pytest.mark.parametrize("gts", [False, True])
+def test_gas_at_rest_between_diffuse_walls_keeps_the_wall_temperature_with_particles(gts):
+    """Gas at rest at T_w between two diffuse walls at T_w (1-D, 16 cells stretched 10x, Kn 1: particles carry
+    almost all of the gas) is the exact steady state: with the stochastic method its temperature (total energy
+    over total mass, 30 samples over 600 steps after 200) averaged over 6 seeds stays within 5 standard errors
+    of T_w. New particles drawn with per-cell moment matching (a lone particle at the thermal speed
+    sqrt(3 R T)) carry too little energy to the walls per unit mass, and the walls then heat the gas to about
+    1.13 T_w here (14 standard errors)."""
+    means = []
+    for seed in range(6):
+        m = wl.line_mesh(16, 0.0, 1.0, end_ratio=10.0, bc_left=wl.BC_WALL, bc_right=wl.BC_WALL)
+        c = wl.Case("wall_rest", m, Kn=1.0, Ma=0.0, Tw=1.0, cfl=0.5, n_ref=50, seed=seed)
+        o = ob.Oracle(c, gts=gts, precision=0)
+        o.step(200)
+        _, vol = o.geometry()
+        Ts = []
+        for _ in range(30):
+            o.step(20)
+            W, _ = o.field()
+            Ts.append((W[:, 3] * vol).sum() / (W[:, 0] * vol).sum() / 0.75)   # e = (3/2) R T, R = 1/2
+        means.append(np.mean(Ts))
+    means = np.array(means)
+    se = means.std(ddof=1) / np.sqrt(len(means))
+    assert abs(means.mean() - 1.0) <= 5.0 * se, (means, se)
+    assert abs(means.mean() - 1.0) <= 0.03, means
