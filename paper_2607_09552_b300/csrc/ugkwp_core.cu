@@ -897,126 +897,136 @@ __global__ void __launch_bounds__(256) k_heat_tally(const StepConsts K, const De
 }
 
 // ----------------------------------------------------- a2: new collisionless particles (Eq. 26)
-// One warp per sampling cell (the cells listed by the decomposition), particle k on lane k mod 32. Velocities
-// are independent draws from the local distribution of the cell at U_i, T_i (Sec. III B): U_i + sqrt(R T_i) z
-// with z Box-Muller normals (Pr = 1) or from the Shakhov acceptance-rejection (Pr != 1); no per-cell moment
-// matching (forcing a few particles onto the cell's exact momentum and energy changes their speed
-// distribution, and with it the speed-weighted fluxes such as the energy carried to a wall).
-template <typename T>
-__device__ __forceinline__ void sample_cell(const StepConsts& K, const Dev& d, const ParticleSoA<T>& A,
-                                            const PCell<T>& pc, const long long* dstep, int c)
-{
-    const int l = threadIdx.x & 31;
-    int N = d.nhp[c];
-    const int nret = d.counts[0];
-    const long long base_i = (long long)nret + d.nhp_off[c];
-    if (N > 0 && d.nhp_off[c] + N > d.counts[3] - nret) {
-        if (l == 0) atomicOr(d.err, ERR_CAPACITY);
-        N = 0;
-    }
-    if (N == 0) return;   // (the whole warp)
-    const Rng g{K.k0, K.k1, (uint32_t)*dstep};
-    const uint64_t pbase = ((uint64_t)(uint32_t)*dstep << 32) | ((uint64_t)c << 11);
-    int fallbacks = 0;
-    const T ax = K.shakhov ? pc.q_(c, 0) : T(0), ay = K.shakhov ? pc.q_(c, 1) : T(0);
-    const T M = K.shakhov ? pc.q_(c, 2) : T(1);
-    long long acc[5] = {0, 0, 0, 0, 0};
-    const T Ui = pc.s_(c, 0), Vi = pc.s_(c, 1), sig = fsqrt_(pc.s_(c, 2));
-    const T m = pc.m_(c);
-    const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
-    // the cell's vertices in the particle precision and its two triangles' areas (same for every particle)
-    T X[4], Y[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        X[q] = T(d.cvx[4 * c + q]);
-        Y[q] = K.dim == 1 ? T(0) : T(d.cvy[4 * c + q]);
-    }
-    const T A1 = T(0.5) * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
-    const T A2 = T(0.5) * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
-    const T A12 = A1 + A2;
-    for (int k = l; k < N; k += 32) {
-        const uint64_t pid = pbase | (uint64_t)k;
-        // Pr = 1: Box-Muller normals. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-rejection (Sec. III B):
-        // Maxwellian proposals accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5), |z| > 6
-        // rejected; after kArAttempts rejections the last proposal stays
-        T z0 = 0, z1 = 0, z2 = 0;
-        const int attempts = K.shakhov ? kArAttempts : 1;
-        bool accepted = !K.shakhov;
-        for (int a = 0; a < attempts; ++a) {
-            T U[4];
-            Unif<T>::get(g, pid, K.shakhov ? draw_ar(a) : DRAW_VEL, 4, U);
-            const T r0 = fsqrt_(T(-2) * dlog(U[0]));
-            T sn0, cs0, sn1, cs1;
-            dsincos2pi(U[1], &sn0, &cs0);
-            const T r1 = fsqrt_(T(-2) * dlog(U[2]));
-            dsincos2pi(U[3], &sn1, &cs1);
-            z0 = r0 * cs0; z1 = r0 * sn0; z2 = r1 * cs1;
-            if (!K.shakhov) break;
-            const T s2 = (z0 * z0 + z1 * z1) + z2 * z2;
-            if (s2 <= T(36)) {
-                const T psi = (z0 * ax + z1 * ay) * (s2 - T(5));
-                T Ua[1];
-                Unif<T>::get(g, pid, draw_ar(a) + 2u, 1, Ua);
-                if (Ua[0] * M < T(1) + psi) { accepted = true; break; }
-            }
-        }
-        if (!accepted) fallbacks++;
-        const long long i = base_i + k;
-        T U[3], x, y;
-        Unif<T>::get(g, pid, DRAW_POS, 3, U);
-        if (K.dim == 1) {
-            x = X[0] + U[0] * (X[1] - X[0]);
-            y = T(0);
-        } else {
-            const bool first = U[0] * A12 < A1;
-            const int bi = first ? 1 : 2, ci = first ? 2 : 3;
-            const T sq = fsqrt_(U[1]);
-            const T wa = T(1) - sq, wb = sq * (T(1) - U[2]), wc = sq * U[2];
-            x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
-            y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
-        }
-        const T un = Ui + sig * z0, vn = Vi + sig * z1, wn = sig * z2;
-        A.x[i] = x; A.y[i] = y;
-        A.u[i] = un;
-        A.v[i] = vn;
-        A.w[i] = wn;
-        A.m[i] = m;
-        A.cell[i] = c;
-        A.pid[i] = pid;
-        long long f[5];
-        fix5(m, un, vn, wn, s0, s1, s4, d.err, f);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) acc[q] += f[q];
-    }
-    if (K.shakhov) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
-        if (l == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
-    }
-    // W^{p,-} of the new particles: this warp owns the cell, so a butterfly sum and one update (atomic for
-    // W^{p,+}: the ghost sources on the second stream may add to the same cell meanwhile)
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-    if (l == 0)
-        for (int q = 0; q < 5; ++q) {
-            d.wm[5 * c + q] += acc[q];
-            atomicAdd(reinterpret_cast<unsigned long long*>(d.wpl) + 5 * (size_t)c + q, (unsigned long long)acc[q]);
-        }
-}
-
-// the cells that sample new particles this step (listed by the decomposition, in any order: each cell's
-// particles, ids and slots depend on the cell alone), one per warp, grid-stride over the list
+// One thread per new particle over the step's flat range of new particles (cell c's N^hp particles take the
+// slots nhp_off[c] .. nhp_off[c] + N^hp - 1 after the retained ones, in cell order); a thread finds its cell by
+// a binary search of the exclusive scan nhp_off. Velocities are independent draws from the local distribution
+// of the cell at U_i, T_i (Sec. III B): U_i + sqrt(R T_i) z with z Box-Muller normals (Pr = 1) or from the
+// Shakhov acceptance-rejection (Pr != 1); no per-cell moment matching (forcing a few particles onto the cell's
+// exact momentum and energy changes their speed distribution, and with it the speed-weighted fluxes such as the
+// energy carried to a wall). W^{p,-} and W^{p,+} of the new particles: per warp, sums over each run of lanes
+// holding the same cell (a segmented scan by shuffles), one 64-bit atomic add per run and moment.
 template <typename T>
 __device__ __forceinline__ void sample_body(const VB vb, const StepConsts& K, const Dev& d, const ParticleSoA<T>& PA,
                                             const ParticleSoA<T>& PB, const PCell<T>& pc, const long long* dstep)
 {
     const ParticleSoA<T> A = *d.bufsel ? PB : PA;   // the buffer holding this step's particles
-    if (d.counts[1] == 0) return;
-    const int nact = *d.nscell;
-    const int nwarps = vb.n * (blockDim.x >> 5);
-    for (int w = (vb.b * blockDim.x + threadIdx.x) >> 5; w < nact; w += nwarps)
-        sample_cell(K, d, A, pc, dstep, d.scells[w]);
+    const int total = d.counts[1];
+    if (total == 0) return;
+    const int nret = d.counts[0];
+    const int room = d.counts[3] - nret;
+    const int lane = threadIdx.x & 31;
+    const Rng g{K.k0, K.k1, (uint32_t)*dstep};
+    const uint64_t step_hi = (uint64_t)(uint32_t)*dstep << 32;
+    const T s0 = T(pow2(K.fx0)), s1 = T(pow2(K.fx1)), s4 = T(pow2(K.fx4));
+    int fallbacks = 0;
+    const int stride = vb.n * blockDim.x;
+    for (int k0 = vb.b * blockDim.x + (threadIdx.x & ~31); k0 < total; k0 += stride) {
+        const int k = k0 + lane;
+        int c = -1;
+        long long acc[5] = {0, 0, 0, 0, 0};
+        if (k < total) {
+            // the last cell whose range starts at or before k (nhp_off[C] read as the total)
+            int lo = 0, hi = K.C;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(d.nhp_off + mid) <= k) lo = mid;
+                else hi = mid;
+            }
+            c = lo;
+        }
+        if (k < total && k >= room) {
+            atomicOr(d.err, ERR_CAPACITY);
+        } else if (k < total) {
+            const int kl = k - __ldg(d.nhp_off + c);
+            const uint64_t pid = step_hi | ((uint64_t)c << 11) | (uint64_t)kl;
+            // Pr = 1: Box-Muller normals. Pr != 1: the Shakhov g^S of Eq. 4 by acceptance-rejection (Sec. III B):
+            // Maxwellian proposals accepted with probability (1 + psi) / M, psi = (a . z)(|z|^2 - 5), |z| > 6
+            // rejected; after kArAttempts rejections the last proposal stays
+            T z0 = 0, z1 = 0, z2 = 0;
+            const T ax = K.shakhov ? pc.q_(c, 0) : T(0), ay = K.shakhov ? pc.q_(c, 1) : T(0);
+            const T M = K.shakhov ? pc.q_(c, 2) : T(1);
+            const int attempts = K.shakhov ? kArAttempts : 1;
+            bool accepted = !K.shakhov;
+            for (int a = 0; a < attempts; ++a) {
+                T U[4];
+                Unif<T>::get(g, pid, K.shakhov ? draw_ar(a) : DRAW_VEL, 4, U);
+                const T r0 = fsqrt_(T(-2) * dlog(U[0]));
+                T sn0, cs0, sn1, cs1;
+                dsincos2pi(U[1], &sn0, &cs0);
+                const T r1 = fsqrt_(T(-2) * dlog(U[2]));
+                dsincos2pi(U[3], &sn1, &cs1);
+                z0 = r0 * cs0; z1 = r0 * sn0; z2 = r1 * cs1;
+                if (!K.shakhov) break;
+                const T s2 = (z0 * z0 + z1 * z1) + z2 * z2;
+                if (s2 <= T(36)) {
+                    const T psi = (z0 * ax + z1 * ay) * (s2 - T(5));
+                    T Ua[1];
+                    Unif<T>::get(g, pid, draw_ar(a) + 2u, 1, Ua);
+                    if (Ua[0] * M < T(1) + psi) { accepted = true; break; }
+                }
+            }
+            if (!accepted) fallbacks++;
+            // uniform position: 1-D on the segment; 2-D the quad split along its 0-2 diagonal, a triangle chosen
+            // by area, then barycentric (sqrt(U1), U2)
+            T X[4], Y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                X[q] = T(d.cvx[4 * c + q]);
+                Y[q] = K.dim == 1 ? T(0) : T(d.cvy[4 * c + q]);
+            }
+            T U[3], x, y;
+            Unif<T>::get(g, pid, DRAW_POS, 3, U);
+            if (K.dim == 1) {
+                x = X[0] + U[0] * (X[1] - X[0]);
+                y = T(0);
+            } else {
+                const T A1 = T(0.5) * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+                const T A2 = T(0.5) * ((X[2] - X[0]) * (Y[3] - Y[0]) - (X[3] - X[0]) * (Y[2] - Y[0]));
+                const bool first = U[0] * (A1 + A2) < A1;
+                const int bi = first ? 1 : 2, ci = first ? 2 : 3;
+                const T sq = fsqrt_(U[1]);
+                const T wa = T(1) - sq, wb = sq * (T(1) - U[2]), wc = sq * U[2];
+                x = (wa * X[0] + wb * X[bi]) + wc * X[ci];
+                y = (wa * Y[0] + wb * Y[bi]) + wc * Y[ci];
+            }
+            const T sig = fsqrt_(pc.s_(c, 2));
+            const T un = pc.s_(c, 0) + sig * z0, vn = pc.s_(c, 1) + sig * z1, wn = sig * z2;
+            const T m = pc.m_(c);
+            const long long i = (long long)nret + k;
+            A.x[i] = x; A.y[i] = y;
+            A.u[i] = un;
+            A.v[i] = vn;
+            A.w[i] = wn;
+            A.m[i] = m;
+            A.cell[i] = c;
+            A.pid[i] = pid;
+            fix5(m, un, vn, wn, s0, s1, s4, d.err, acc);
+        }
+        // runs of lanes holding the same cell are contiguous: inclusive segmented sums, then the run's last lane
+        // adds them to W^{p,-} and W^{p,+} (atomic: a cell's particles can span warps; W^{p,+} also takes the
+        // ghost sources' particles on the second stream)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int co = __shfl_up_sync(0xffffffffu, c, o);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const long long v = __shfl_up_sync(0xffffffffu, acc[q], o);
+                if (lane >= o && co == c) acc[q] += v;
+            }
+        }
+        const int cn = __shfl_down_sync(0xffffffffu, c, 1);
+        if (c >= 0 && (lane == 31 || cn != c))
+            for (int q = 0; q < 5; ++q)
+                if (acc[q]) {
+                    atomicAdd(reinterpret_cast<unsigned long long*>(d.wm) + 5 * (size_t)c + q, (unsigned long long)acc[q]);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(d.wpl) + 5 * (size_t)c + q, (unsigned long long)acc[q]);
+                }
+    }
+    if (K.shakhov) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fallbacks += __shfl_xor_sync(0xffffffffu, fallbacks, o);
+        if (lane == 0 && fallbacks) atomicAdd(d.stats + 12, (unsigned long long)fallbacks);
+    }
 }
 template <typename T>
 __global__ void __launch_bounds__(128) k_sample(const StepConsts K, const Dev d, ParticleSoA<T> PA,
