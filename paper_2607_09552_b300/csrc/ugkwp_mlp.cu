@@ -7,8 +7,8 @@
 // kept in FP32 (master copy, Adam state) and used in every product as BF16 values (round to nearest even);
 // activations and accumulation are FP32. Activations are point-major [n][width].
 //
-// Products are tiled FP32 SIMT GEMMs (64 x 64 output tiles, 16-deep shared-memory slabs, 4 x 4 outputs per
-// thread). Weight gradients split the point range over blockIdx.z into partial sums that a second kernel adds
+// Products run on the tensor cores (mma.sync, BF16 operands with FP32 operands split into two BF16 terms,
+// FP32 accumulation; 64 x 64 output tiles). Weight gradients split the point range over blockIdx.z into partial sums that a second kernel adds
 // in a fixed order, so gradients are deterministic run to run.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -20,58 +20,130 @@
 
 namespace {
 
-constexpr int kTile = 64, kSlab = 16;
+constexpr int kTile = 64;
 constexpr int kMaxSplit = 32;          // partial sums of a weight gradient
 constexpr int kPointsPerSplit = 512;
 constexpr int kFeatUsed = 37;          // 32 Fourier features, x^, y^, Kn, Ma, T_w
 
-// Y[n][N] = act(X[rows][K] W^T + b); pre-activations kept in Z for the backward pass. rows == nullptr: rows 0..n-1
-__global__ void __launch_bounds__(256) k_linear_fwd(const float* __restrict__ X, const int* __restrict__ rows,
-                                                    const __nv_bfloat16* __restrict__ W, const float* __restrict__ b,
-                                                    float* __restrict__ Z, float* __restrict__ Y, int n, int K, int N,
-                                                    int silu)
+// The three products run on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation). A block
+// computes a 64 x 64 output tile with 4 warps (2 x 2, 32 x 32 each: 2 x 4 MMA tiles), stepping the contraction
+// 16 at a time through shared memory. Weights are BF16 values already, so they enter exactly; an FP32 operand
+// (activations, back-propagated gradients, inputs) is split as v = hi + lo with hi = bf16(v), lo =
+// bf16(v - hi), which keeps about 16 bits of its significand (relative error below 2^-17). Products with a
+// weight take hi*W + lo*W; the weight gradient, whose operands are both FP32, takes hi*hi + hi*lo + lo*hi
+// (the dropped lo*lo is below 2^-16 of the product). Every product of two BF16 values is exact in FP32, so
+// the results stay within a few FP32 roundings of the FP32 products with BF16 weights that the network
+// defines.
+constexpr int kMmaThreads = 128;
+constexpr int kKs = 16;              // contraction step
+constexpr int kSmStride = kKs + 8;   // shared row stride in BF16 elements (48 B: conflict-free fragment loads)
+
+struct MmaTiles {
+    __nv_bfloat16 a_hi[kTile][kSmStride], a_lo[kTile][kSmStride];
+    __nv_bfloat16 b_hi[kTile][kSmStride], b_lo[kTile][kSmStride];
+};
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo)
 {
-    __shared__ float xs[kSlab][kTile + 1];
-    __shared__ float ws[kSlab][kTile + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Stage rows r0..r0+63, contraction k0..k0+15 of an operand: thread t loads row t / 2, 8 consecutive k
+// (zero outside the bounds), splits them and stores 16 bytes into each of hi and lo (lo skipped when null).
+template <class Get>
+__device__ __forceinline__ void stage_tile(Get get, __nv_bfloat16 (*hi)[kSmStride], __nv_bfloat16 (*lo)[kSmStride])
+{
+    const int r = threadIdx.x >> 1, kk = (threadIdx.x & 1) * 8;
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) split_bf16(get(r, kk + q), h[q], l[q]);
+    *reinterpret_cast<uint4*>(&hi[r][kk]) = *reinterpret_cast<const uint4*>(h);
+    if (lo) *reinterpret_cast<uint4*>(&lo[r][kk]) = *reinterpret_cast<const uint4*>(l);
+}
+
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// acc += A(64 x 16) B(64 x 16)^T from the staged tiles: 2 terms (B exact) or 3 (both split)
+__device__ __forceinline__ void mma_step(const MmaTiles& S, bool b_split, float (&acc)[2][4][4])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = (warp >> 1) * 32, n0 = (warp & 1) * 32;
+    uint32_t ah[2][4], al[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r = m0 + mt * 16 + g;
+        ah[mt][0] = lds32(&S.a_hi[r][2 * t]);     ah[mt][1] = lds32(&S.a_hi[r + 8][2 * t]);
+        ah[mt][2] = lds32(&S.a_hi[r][2 * t + 8]); ah[mt][3] = lds32(&S.a_hi[r + 8][2 * t + 8]);
+        al[mt][0] = lds32(&S.a_lo[r][2 * t]);     al[mt][1] = lds32(&S.a_lo[r + 8][2 * t]);
+        al[mt][2] = lds32(&S.a_lo[r][2 * t + 8]); al[mt][3] = lds32(&S.a_lo[r + 8][2 * t + 8]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int c = n0 + nt * 8 + g;
+        const uint32_t bh0 = lds32(&S.b_hi[c][2 * t]), bh1 = lds32(&S.b_hi[c][2 * t + 8]);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            mma_bf16(acc[mt][nt], al[mt], bh0, bh1);
+            if (b_split) mma_bf16(acc[mt][nt], ah[mt], lds32(&S.b_lo[c][2 * t]), lds32(&S.b_lo[c][2 * t + 8]));
+            mma_bf16(acc[mt][nt], ah[mt], bh0, bh1);
+        }
+    }
+}
+
+// the output element (row, col) of accumulator register q of MMA tile (mt, nt) of this thread
+__device__ __forceinline__ void acc_coord(int mt, int nt, int q, int& row, int& col)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    row = (warp >> 1) * 32 + mt * 16 + (lane >> 2) + (q >> 1) * 8;
+    col = (warp & 1) * 32 + nt * 8 + (lane & 3) * 2 + (q & 1);
+}
+
+// Y[n][N] = act(X[rows][K] W^T + b); pre-activations kept in Z for the backward pass. rows == nullptr: rows 0..n-1
+__global__ void __launch_bounds__(kMmaThreads) k_linear_fwd(const float* __restrict__ X, const int* __restrict__ rows,
+                                                            const __nv_bfloat16* __restrict__ W,
+                                                            const float* __restrict__ b, float* __restrict__ Z,
+                                                            float* __restrict__ Y, int n, int K, int N, int silu)
+{
+    __shared__ __align__(16) MmaTiles S;
     const int row0 = blockIdx.y * kTile, col0 = blockIdx.x * kTile;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += kSlab) {
-        for (int q = threadIdx.x; q < kSlab * kTile; q += 256) {
-            const int kk = q % kSlab, r = q / kSlab;
-            const int gr = row0 + r, gk = k0 + kk;
-            float xv = 0.0f;
-            if (gr < n && gk < K) xv = X[(size_t)(rows ? rows[gr] : gr) * K + gk];
-            xs[kk][r] = xv;
-            const int gc = col0 + r;
-            ws[kk][r] = (gc < N && gk < K) ? __bfloat162float(W[(size_t)gc * K + gk]) : 0.0f;
-        }
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += kKs) {
+        stage_tile([&](int r, int k) {
+            const int gr = row0 + r, gk = k0 + k;
+            return (gr < n && gk < K) ? X[(size_t)(rows ? rows[gr] : gr) * K + gk] : 0.0f;
+        }, S.a_hi, S.a_lo);
+        stage_tile([&](int r, int k) {
+            const int gc = col0 + r, gk = k0 + k;
+            return (gc < N && gk < K) ? __bfloat162float(W[(size_t)gc * K + gk]) : 0.0f;
+        }, S.b_hi, nullptr);
         __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kSlab; ++kk) {
-            float a[4], w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { a[i] = xs[kk][ty * 4 + i]; w[i] = ws[kk][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-        }
+        mma_step(S, false, acc);
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = row0 + ty * 4 + i;
-        if (r >= n) continue;
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = col0 + tx * 4 + j;
-            if (c >= N) continue;
-            const float z = acc[i][j] + b[c];
-            if (Z) Z[(size_t)r * N + c] = z;
-            Y[(size_t)r * N + c] = silu ? z / (1.0f + expf(-z)) : z;
-        }
-    }
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int r, c;
+                acc_coord(mt, nt, q, r, c);
+                r += row0; c += col0;
+                if (r >= n || c >= N) continue;
+                const float z = acc[mt][nt][q] + b[c];
+                if (Z) Z[(size_t)r * N + c] = z;
+                Y[(size_t)r * N + c] = silu ? z / (1.0f + expf(-z)) : z;
+            }
 }
 
 // dZ = dY * act'(Z)
@@ -86,96 +158,81 @@ __global__ void k_act_bwd(const float* __restrict__ Z, const float* __restrict__
 }
 
 // dX[n][K] = dZ[n][N] W[N][K]
-__global__ void __launch_bounds__(256) k_linear_dx(const float* __restrict__ dZ, const __nv_bfloat16* __restrict__ W,
-                                                   float* __restrict__ dX, int n, int K, int N)
+__global__ void __launch_bounds__(kMmaThreads) k_linear_dx(const float* __restrict__ dZ,
+                                                           const __nv_bfloat16* __restrict__ W, float* __restrict__ dX,
+                                                           int n, int K, int N)
 {
-    __shared__ float zs[kSlab][kTile + 1];
-    __shared__ float ws[kSlab][kTile + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    __shared__ __align__(16) MmaTiles S;
     const int row0 = blockIdx.y * kTile, col0 = blockIdx.x * kTile;
-    float acc[4][4] = {};
-    for (int j0 = 0; j0 < N; j0 += kSlab) {
-        for (int q = threadIdx.x; q < kSlab * kTile; q += 256) {
-            const int jj = q % kSlab, r = q / kSlab;
-            const int gr = row0 + r, gj = j0 + jj;
-            zs[jj][r] = (gr < n && gj < N) ? dZ[(size_t)gr * N + gj] : 0.0f;
-            const int gk = col0 + r;
-            ws[jj][r] = (gk < K && gj < N) ? __bfloat162float(W[(size_t)gj * K + gk]) : 0.0f;
-        }
+    float acc[2][4][4] = {};
+    for (int j0 = 0; j0 < N; j0 += kKs) {
+        stage_tile([&](int r, int j) {
+            const int gr = row0 + r, gj = j0 + j;
+            return (gr < n && gj < N) ? dZ[(size_t)gr * N + gj] : 0.0f;
+        }, S.a_hi, S.a_lo);
+        stage_tile([&](int r, int j) {
+            const int gk = col0 + r, gj = j0 + j;
+            return (gk < K && gj < N) ? __bfloat162float(W[(size_t)gj * K + gk]) : 0.0f;
+        }, S.b_hi, nullptr);
         __syncthreads();
-#pragma unroll
-        for (int jj = 0; jj < kSlab; ++jj) {
-            float a[4], w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { a[i] = zs[jj][ty * 4 + i]; w[i] = ws[jj][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-        }
+        mma_step(S, false, acc);
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = row0 + ty * 4 + i;
-        if (r >= n) continue;
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = col0 + tx * 4 + j;
-            if (c < K) dX[(size_t)r * K + c] = acc[i][j];
-        }
-    }
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int r, c;
+                acc_coord(mt, nt, q, r, c);
+                r += row0; c += col0;
+                if (r < n && c < K) dX[(size_t)r * K + c] = acc[mt][nt][q];
+            }
 }
 
 // Partial weight and bias gradients over the point range of split z = blockIdx.z:
-// part[z][N*K + N] holds dW[N][K] = sum_p dZ[p][N] X[p][K] and db[N] = sum_p dZ[p][N]
-__global__ void __launch_bounds__(256) k_linear_dw(const float* __restrict__ dZ, const float* __restrict__ X,
-                                                   const int* __restrict__ rows, float* __restrict__ part, int n,
-                                                   int K, int N, int per_split)
+// part[z][N*K + N] holds dW[N][K] = sum_p dZ[p][N] X[p][K] and db[N] = sum_p dZ[p][N] (the bias by the first
+// column of blocks, one thread per output unit, points in order)
+__global__ void __launch_bounds__(kMmaThreads) k_linear_dw(const float* __restrict__ dZ, const float* __restrict__ X,
+                                                           const int* __restrict__ rows, float* __restrict__ part,
+                                                           int n, int K, int N, int per_split)
 {
-    __shared__ float zs[kSlab][kTile + 1];
-    __shared__ float xs[kSlab][kTile + 1];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    __shared__ __align__(16) MmaTiles S;
     const int n0 = blockIdx.y * kTile, k0 = blockIdx.x * kTile;
     const int p_begin = blockIdx.z * per_split;
     const int p_end = min(n, p_begin + per_split);
     float* out = part + (size_t)blockIdx.z * ((size_t)N * K + N);
-    float acc[4][4] = {};
-    float bacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const bool do_bias = blockIdx.x == 0 && tx == 0;
-    for (int p0 = p_begin; p0 < p_end; p0 += kSlab) {
-        for (int q = threadIdx.x; q < kSlab * kTile; q += 256) {
-            const int pp = q % kSlab, r = q / kSlab;
+    float acc[2][4][4] = {};
+    for (int p0 = p_begin; p0 < p_end; p0 += kKs) {
+        stage_tile([&](int r, int pp) {
             const int gp = p0 + pp;
-            const bool ok = gp < p_end;
-            zs[pp][r] = (ok && n0 + r < N) ? dZ[(size_t)gp * N + n0 + r] : 0.0f;
-            xs[pp][r] = (ok && k0 + r < K) ? X[(size_t)(rows ? rows[gp] : gp) * K + k0 + r] : 0.0f;
-        }
+            return (gp < p_end && n0 + r < N) ? dZ[(size_t)gp * N + n0 + r] : 0.0f;
+        }, S.a_hi, S.a_lo);
+        stage_tile([&](int r, int pp) {
+            const int gp = p0 + pp;
+            return (gp < p_end && k0 + r < K) ? X[(size_t)(rows ? rows[gp] : gp) * K + k0 + r] : 0.0f;
+        }, S.b_hi, S.b_lo);
         __syncthreads();
-#pragma unroll
-        for (int pp = 0; pp < kSlab; ++pp) {
-            float a[4], w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { a[i] = zs[pp][ty * 4 + i]; w[i] = xs[pp][tx * 4 + i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
-                if (do_bias) bacc[i] += a[i];
-            }
-        }
+        mma_step(S, true, acc);
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = n0 + ty * 4 + i;
-        if (r >= N) continue;
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = k0 + tx * 4 + j;
-            if (c < K) out[(size_t)r * K + c] = acc[i][j];
-        }
-        if (do_bias) out[(size_t)N * K + r] = bacc[i];
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int r, c;
+                acc_coord(mt, nt, q, r, c);
+                r += n0; c += k0;
+                if (r < N && c < K) out[(size_t)r * K + c] = acc[mt][nt][q];
+            }
+    if (blockIdx.x == 0 && threadIdx.x < kTile && n0 + (int)threadIdx.x < N) {
+        const int r = n0 + threadIdx.x;
+        float s = 0.0f;
+        for (int p = p_begin; p < p_end; ++p) s += dZ[(size_t)p * N + r];
+        out[(size_t)N * K + r] = s;
     }
 }
 
@@ -383,7 +440,7 @@ void forward(ugkwp_mlp* M, const float* X, const int* rows, int n, float* Yout, 
         const int K = M->in[l], N = M->out[l];
         float* y = (l == M->L && Yout) ? Yout : act_of(M, l + 1);
         dim3 grid(nb(N, kTile), nb(n, kTile));
-        k_linear_fwd<<<grid, 256, 0, M->s>>>(x, l == 0 ? rows : nullptr, M->wb + M->woff[l], M->p + M->boff[l],
+        k_linear_fwd<<<grid, kMmaThreads, 0, M->s>>>(x, l == 0 ? rows : nullptr, M->wb + M->woff[l], M->p + M->boff[l],
                                             keep ? pre_of(M, l) : nullptr, y, n, K, N, l < M->L ? 1 : 0);
         x = y;
     }
@@ -504,13 +561,13 @@ ugkwp_status ugkwp_mlp_grad(ugkwp_mlp* M, const float* x_dev, const float* t_dev
         k_act_bwd<<<nb(cnt, 256), 256, 0, M->s>>>(pre_of(M, l), dY, M->dpre, cnt, l < L ? 1 : 0);
         const float* X = l == 0 ? x_dev : act_of(M, l);
         dim3 gw(nb(K, kTile), nb(N, kTile), splits);
-        k_linear_dw<<<gw, 256, 0, M->s>>>(M->dpre, X, l == 0 ? rows_dev : nullptr, M->part, n, K, N, per_split);
+        k_linear_dw<<<gw, kMmaThreads, 0, M->s>>>(M->dpre, X, l == 0 ? rows_dev : nullptr, M->part, n, K, N, per_split);
         k_reduce_splits<<<nb((size_t)N * K + N, 256), 256, 0, M->s>>>(M->part, splits, N, K, M->g + M->woff[l],
                                                                       M->g + M->boff[l]);
         if (l > 0) {
             float* dX = (dY == M->dbuf) ? M->dbuf + (size_t)M->cap * M->H : M->dbuf;
             dim3 gx(nb(K, kTile), nb(n, kTile));
-            k_linear_dx<<<gx, 256, 0, M->s>>>(M->dpre, M->wb + M->woff[l], dX, n, K, N);
+            k_linear_dx<<<gx, kMmaThreads, 0, M->s>>>(M->dpre, M->wb + M->woff[l], dX, n, K, N);
             dY = dX;
         }
     }
