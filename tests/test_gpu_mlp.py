@@ -1,9 +1,10 @@
 """GPU parity of the warm-start network kernels against the float64 oracle (oracle/mlp.py), and the warm
 start's effect on the steady iteration.
 
-Tolerances: the GPU uses the same BF16-rounded weights as the oracle, FP32 activations and FP32
-accumulation (at most 256-term dot products forward, up to 4096-point sums in the weight gradients), so
-outputs agree to about 1e-6 relative and gradients per tensor to about 1e-5; the bars below are 1e-4.
+Tolerances: the GPU uses the same BF16-rounded weights as the oracle; its tensor-core products take each
+FP32 activation or gradient as two BF16 terms (relative error below 2^-17) and accumulate in FP32 (at most
+256-term dot products forward, up to 4096-point sums in the weight gradients), so outputs agree to about
+1e-5 relative and gradients per tensor to about 1e-5; the bars below are 1e-4.
 Features are computed in float64 and rounded once to float32 (1e-6 absolute bar)."""
 import numpy as np
 import pytest
@@ -84,6 +85,32 @@ def test_gradient_matches_oracle(cuda_lib, n):
     assert abs(loss - lref) <= 1e-5 * lref
     Ws, bs = om.unpack(g.astype(np.float64), 64, 256, 4)
     Wr, br = om.unpack(gref, 64, 256, 4)
+    for a, b in zip(Ws + bs, Wr + br):
+        assert _rel(a, b) <= 1e-4, _rel(a, b)
+
+
+@pytest.mark.parametrize("shape,n", [((37, 48, 2, 4), 300), ((45, 72, 3, 4), 1031)])
+def test_ragged_shapes_match_oracle(cuda_lib, shape, n):
+    """Inputs, widths and point counts off the 16-deep contraction steps and the 64 x 64 output tiles: the
+    zero padding of partial tiles and the guarded epilogues, forward and every gradient."""
+    torch = _torch()
+    nf, width, depth, n_out = shape
+    rng = np.random.default_rng(n)
+    p = wl.mlp_init(11, nf, width, depth, n_out)
+    nb = depth * width + n_out
+    p[-nb:] = rng.normal(0, 0.1, nb).astype(np.float32)
+    net = cuda_lib.Mlp(nf, width, depth, n_out, params=p)
+    X = rng.normal(size=(n, nf)).astype(np.float32)
+    T = rng.normal(size=(n, n_out)).astype(np.float32)
+    y = net.forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    ref = om.forward(p, X, nf, width, depth)
+    assert y.shape == ref.shape
+    assert _rel(y, ref) <= 1e-4, _rel(y, ref)
+    loss = net.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"))
+    lref, gref = om.loss_and_grad(p, X, T, nf, width, depth)
+    assert abs(loss - lref) <= 1e-5 * lref
+    Ws, bs = om.unpack(net.grad().astype(np.float64), nf, width, depth)
+    Wr, br = om.unpack(gref, nf, width, depth)
     for a, b in zip(Ws + bs, Wr + br):
         assert _rel(a, b) <= 1e-4, _rel(a, b)
 
