@@ -471,6 +471,8 @@ def converge_case(case, args, stream, verbose=True):
             s.close()
             if verbose:
                 print(json.dumps({"phase": f"{ts} wave_only", **r}), flush=True)
+        if args.skip_stochastic:
+            continue
         n = args.lts_steps if not gts else args.gts_steps
         # GTS keeps far more particles (every cell samples with the smallest time step): larger capacity
         cap = (32 if gts else 8) * case.n_ref * case.mesh.ncells
@@ -821,6 +823,9 @@ def main():
     ap.add_argument("--lts-steps", type=int, default=30000)
     ap.add_argument("--gts-steps", type=int, default=150000)
     ap.add_argument("--skip-wave", action="store_true")
+    ap.add_argument("--skip-stochastic", action="store_true",
+                    help="convergence mode: the particle-free FP64 runs only (the dense cylinder's GTS stochastic "
+                         "run outgrows any capacity)")
     ap.add_argument("--train-sweeps", type=int, default=4)
     ap.add_argument("--train-tol", type=float, default=1e-5)
     ap.add_argument("--train-max-steps", type=int, default=60000)
