@@ -282,21 +282,24 @@ ugkwp_status ugkwp_save(ugkwp_ctx* ctx, const char* path);
 ugkwp_status ugkwp_load(ugkwp_ctx* ctx, const char* path);
 
 /* Launch parameters of the particle kernels: the transport kernel (1: warp-chunked, every precision; 2:
- * tile-staged, production precision only: 1024-particle tiles moved into shared memory by bulk asynchronous
- * copies, double-buffered, with the particles that reach a face or collide queued and flown together; the
- * default in production precision), the warp-chunked kernel's particles per chunk a warp claims (a multiple
- * of 32 in [32, 8192]) and blocks per SM (1..16), and the steps between counting sorts of the particles by
+ * warp-staged, production precision only, the default there: a stay pass in which each warp has the stay-test
+ * fields of tiles of 128 particles (chunk 128; 64 otherwise) copied into its shared memory by bulk asynchronous
+ * copies, double-buffered, and finishes the particles that only move, then a flight pass that flies the
+ * queued rest, those with a face ahead or colliding, one per thread), the particles per chunk a warp claims (a
+ * multiple of 32 in [32, 8192]; the warp-staged kernel's tile) and blocks per SM (1..16; the warp-staged stay
+ * pass runs 4, 6 or 8), and the steps between counting sorts of the particles by
  * cell (1..64); 0 keeps a value. They change only the speed: both kernels perform the same per-particle
  * operations, chunks, tiles and sorts reorder particles, and every result is an integer sum or a
- * per-particle / per-face quantity. EINVAL for a value out of range or the tile-staged kernel in the FP64
+ * per-particle / per-face quantity. EINVAL for a value out of range or the warp-staged kernel in the FP64
  * mode. Takes effect at the next step (a captured step graph is re-captured); a batch keeps the values its
  * contexts had at ugkwp_batch_create. ugkwp_get_launch fills out[4]: chunk, blocks per SM, sort interval,
  * transport kernel. */
 ugkwp_status ugkwp_set_launch(ugkwp_ctx* ctx, int32_t chunk, int32_t blocks_per_sm, int32_t sort_every,
                               int32_t transport);
 ugkwp_status ugkwp_get_launch(ugkwp_ctx* ctx, int32_t* out);
-/* Autotuner: times the tile-staged kernel (production precision) and the warp-chunked kernel with chunk
- * {128, 256} x blocks per SM {4, 6, 8}, each with sort interval {8, 16, 32}, over whole sort periods of at
+/* Autotuner: times the warp-staged kernel (production precision; tiles of 64 particles at 6 or 8 blocks per SM,
+ * of 128 at 4, 6 or 8) and the warp-chunked kernel with chunk {128, 256} x blocks per SM {4, 6, 8}, each with
+ * sort interval {8, 16, 32}, over whole sort periods of at
  * least `steps` steps (real steps of the run: the state advances) with CUDA events on the context's stream,
  * keeps the fastest and returns it in best[4] (nullable, order of ugkwp_get_launch) and its milliseconds per
  * step in best_ms (nullable). Synchronises. A particle-free context keeps its values. */

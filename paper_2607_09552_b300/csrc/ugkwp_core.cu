@@ -3969,8 +3969,8 @@ extern "C" ugkwp_status ugkwp_autotune(ugkwp_ctx* h, int32_t steps, int32_t* bes
         if (best_ms) *best_ms = 0.0;
         return UGKWP_OK;
     }
-    // candidates: the tile-staged kernel (production precision; its tile and 2 CTAs per SM are fixed) and the
-    // warp-chunked kernel with chunk {128, 256} x blocks per SM {4, 6, 8}, each with sort interval {8, 16, 32}
+    // candidates: the warp-staged kernel (production precision; 64-particle tiles at 6 or 8 CTAs per SM,
+    // 128-particle tiles at 4, 6 or 8) and the warp-chunked kernel with chunk {128, 256} x blocks per SM {4, 6, 8}, each with sort interval {8, 16, 32}
     struct Cand { int chunk, bps, sort, transport; };
     std::vector<Cand> cands;
     for (int so : {8, 16, 32}) {
